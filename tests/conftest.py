@@ -1,0 +1,12 @@
+"""Shared pytest set-up: the ``gpu`` marker and import paths."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built libhelm")
+    config.addinivalue_line("markers", "slow: oracle test that takes more than a few seconds")
