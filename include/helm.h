@@ -1,0 +1,160 @@
+/*
+ * helm.h - C ABI of libhelm: batched 2D Helmholtz solves on one GB300
+ * (sm_103a) for frequency-domain full waveform inversion.
+ *
+ * What is solved (Sec. 3.1, Eq. 3.1-3.2): for a medium kappa = 1/c (s/m,
+ * squared slowness m = kappa^2) and an absorbing-layer profile gamma,
+ *
+ *     H(m, w) u = -Lap_h u - w^2 m (1 - i gamma) u = g
+ *
+ * with the second-order five-point Laplacian on a node grid of spacings
+ * (hx, hz) and zero values on the ghost nodes outside the grid.  The solver
+ * is restarted flexible GMRES preconditioned by a shifted-Laplacian multigrid
+ * V-cycle (Sec. 3.4, Eq. 3.12) or by the encoder-solver network followed by
+ * that V-cycle (M_VU, Eq. 3.14).  Adjoint systems H^* x = b are solved with
+ * the same operator through conjugation (Sec. 4.3, Eq. 4.8).
+ *
+ * Layout.  Every field is row-major [nz][nx] (x fastest); a batch of fields
+ * is [nrhs][nz][nx].  Complex values are interleaved (re, im).
+ *
+ * Pointers.  Array arguments may be device pointers or host pointers; the
+ * library detects which (cudaPointerGetAttributes) and stages host data
+ * through its own device buffers on the context's stream.  The caller keeps
+ * ownership of every buffer it passes; the library owns the context, the
+ * multigrid hierarchy and all Krylov workspace.
+ *
+ * Errors.  Every function returns an int status (HELM_OK = 0); nothing is
+ * thrown across the ABI.  helm_last_error() returns a thread-local message
+ * describing the most recent failure on the calling thread.
+ *
+ * Streams.  All device work of a context is issued on opts.stream (a
+ * cudaStream_t, NULL for the legacy default stream).  helm_solve blocks the
+ * host until the batch has converged (it reads per-RHS convergence flags
+ * once per restart cycle).  A context must not be used from two host
+ * threads at once.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { float re, im; } helm_c64;
+typedef struct { double re, im; } helm_c128;
+
+typedef struct helm_ctx helm_ctx;     /* opaque, library-owned */
+typedef struct cnn_model cnn_model;   /* opaque, library-owned */
+
+enum {
+    HELM_OK = 0,
+    HELM_EINVAL = 1,        /* bad argument: sizes, pointers, options          */
+    HELM_ENOMEM = 2,        /* device or host allocation failed                */
+    HELM_ECUDA = 3,         /* a CUDA runtime call failed                      */
+    HELM_ENOCONV = 4,       /* some RHS missed tol within max_iter (others ok) */
+    HELM_EBREAKDOWN = 5,    /* NaN/Inf appeared for some RHS                   */
+    HELM_ETIMEOUT = 6,      /* a bounded device wait expired                   */
+    HELM_EUNSUPPORTED = 7   /* option combination not implemented              */
+};
+
+enum { HELM_PC_NONE = 0, HELM_PC_MG = 1, HELM_PC_CNN = 2 };
+enum { HELM_COARSE_GMRES = 0, HELM_COARSE_JACOBI = 1 };
+enum { HELM_OP_H = 0, HELM_OP_SL = 1 };
+enum { HELM_SOLVE_ADJOINT = 1, HELM_SOLVE_ZERO_X0 = 2 };   /* helm_solve flags */
+
+/* Solver options.  helm_default_opts() fills the defaults shown. */
+typedef struct {
+    int   restart;          /* FGMRES restart length k                     (10)  */
+    int   max_iter;         /* total FGMRES steps per RHS (Sec. 5.7 cap)  (300)  */
+    int   mg_levels;        /* V-cycle levels, >= 2                          (3)  */
+    int   pre, post;        /* damped-Jacobi sweeps before / after          (2,2) */
+    float jacobi_w;         /* Jacobi damping                              (0.8)  */
+    float sl_beta;          /* shift beta of Eq. 3.12, alpha = 1           (0.5)  */
+    int   sl_include_gamma; /* 1: shift w^2 m (1 - i(beta+gamma)); 0: Eq. 3.12 literal (1) */
+    int   coarse_kind;      /* HELM_COARSE_GMRES or HELM_COARSE_JACOBI           */
+    int   coarse_iters;     /* steps of the coarsest-level solve            (10)  */
+    int   precond;          /* HELM_PC_MG, HELM_PC_CNN or HELM_PC_NONE          */
+    int   max_rhs;          /* RHS per device batch; larger calls are chunked (256) */
+    void* stream;           /* cudaStream_t for all work of the context   (NULL) */
+} helm_opts;
+
+/* Per-RHS results of helm_solve, caller-allocated HOST arrays of nrhs entries
+ * (any pointer may be NULL). */
+typedef struct {
+    int*    iters;          /* FGMRES steps taken                              */
+    double* rel_res;        /* final ||b - H x||_2 / ||b||_2, evaluated in FP64 */
+    int*    status;         /* HELM_OK, HELM_ENOCONV or HELM_EBREAKDOWN         */
+} helm_stats;
+
+void helm_default_opts(helm_opts* opts);
+
+/* Create a context for one medium and a set of angular frequencies.
+ *   kappa, gamma : float32 [nz][nx] (kappa = 1/c in s/m; gamma >= 0 absorbing layer)
+ *   omegas       : float32 [nfreq], angular frequencies w = 2 pi f (rad/s), host or device
+ *   hx, hz       : grid spacings (m)
+ *   net          : encoder-solver network for HELM_PC_CNN (its encoder runs here, once per
+ *                  frequency, Eq. 3.13); NULL for the multigrid preconditioner
+ * nx and nz must be divisible by 2^(mg_levels-1).  Builds the Galerkin multigrid
+ * hierarchy of the shifted Laplacian for every frequency (Sec. 3.4) on the device.
+ * Returns HELM_EINVAL on bad sizes/options, HELM_ENOMEM if the workspace for
+ * opts.max_rhs right-hand sides does not fit. */
+int helm_setup(helm_ctx** out, const float* kappa, const float* gamma, int nx, int nz,
+               float hx, float hz, const float* omegas, int nfreq,
+               const cnn_model* net, const helm_opts* opts);
+
+/* Replace the medium (and the frequencies, same count) of an existing context and
+ * rebuild its multigrid hierarchy on the device: the per-medium set-up of Sec. 3.4
+ * without reallocating the workspace (FWI changes the medium every iteration). */
+int helm_set_medium(helm_ctx* ctx, const float* kappa, const float* gamma,
+                    const float* omegas, int nfreq);
+
+/* Solve H(m, w_f) x = rhs, or H^* x = rhs with flags & HELM_SOLVE_ADJOINT (Eq. 4.8)
+ * for nrhs right-hand sides, to ||b - H x||_2 <= tol ||b||_2 with the residual
+ * evaluated in FP64 from the FP64 iterate.
+ *   rhs      : complex64 [nrhs][nz][nx]
+ *   x        : complex128 [nrhs][nz][nx]; in: initial guess (not read when
+ *              flags & HELM_SOLVE_ZERO_X0: the guess is then zero); out: solution.
+ *              The iterate is kept in complex128 because the complex64 rounding
+ *              of a point-source solution alone leaves a relative residual near 1e-6.
+ *   freq_idx : host int32 [nrhs], index into the context's omegas per RHS (NULL: all 0)
+ * Returns HELM_OK when every RHS converged, HELM_ENOCONV / HELM_EBREAKDOWN when some
+ * did not (see stats), or an error code. */
+int helm_solve(helm_ctx* ctx, const helm_c64* rhs, helm_c128* x, int nrhs,
+               const int* freq_idx, double tol, int flags, helm_stats* stats);
+
+/* y = A x for A = H(m, w_f) (op = HELM_OP_H, Eq. 3.2) or the fine shifted Laplacian
+ * P (op = HELM_OP_SL, Eq. 3.12 with the context's shift options); complex64 in/out. */
+int helm_apply(helm_ctx* ctx, const helm_c64* x, helm_c64* y, int nrhs,
+               const int* freq_idx, int op);
+
+/* u = V-cycle(P, f, u0): one multigrid cycle of the context's hierarchy on P u = f
+ * from the initial guess u0 (NULL: zero), Sec. 3.4 / Eq. 3.14.  complex64. */
+int helm_vcycle(helm_ctx* ctx, const helm_c64* f, const helm_c64* u0, helm_c64* u,
+                int nrhs, const int* freq_idx);
+
+void helm_destroy(helm_ctx* ctx);
+
+/* Per-kernel-class timing: when enabled, every kernel launch of the context is
+ * bracketed by CUDA events on its stream and the main kernels add the
+ * algorithmic bytes they move (the minimum DRAM traffic of their definition:
+ * complex64 vectors read and written once per grid point, coefficients shared
+ * by the batch not counted) to a device counter of their class.  Enabling
+ * resets the totals.  helm_profile_read fills up to max entries of class names
+ * (static strings), total milliseconds, launch counts and algorithmic bytes,
+ * and the number of entries written (any output pointer may be NULL). */
+int helm_profile_enable(helm_ctx* ctx, int on);
+int helm_profile_read(helm_ctx* ctx, int max, const char** names, double* ms, long long* launches,
+                      double* bytes, int* count);
+
+/* Number of kernels the library has launched in this process (all contexts). */
+long long helm_launch_count(void);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* helm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_H */

@@ -1,0 +1,244 @@
+// Shifted-Laplacian multigrid kernels (Sec. 3.4, Eq. 3.12): damped Jacobi,
+// full-weighting restriction of the residual, bilinear prolongation with
+// correction, and the Galerkin coarse operators R P 4R^T.  Coarse node (J, I)
+// of a level sits on node (2J+1, 2I+1) of the level above; values outside a
+// grid are zero.  All kernels are batched over right-hand sides (blockIdx.z)
+// and skip right-hand sides whose mask entry is zero.
+#include <type_traits>
+
+#include "helm_internal.cuh"
+
+namespace helm {
+
+namespace {
+
+// u_out = u_in + w D^-1 (f - A u_in)    (u_in == nullptr: u_in = 0)
+template <class Op>
+__global__ void jacobi_kernel(Op op, float2* __restrict__ u_out, const float2* __restrict__ u_in,
+                              const float2* __restrict__ f, float w, int nx, int nz, const int* mask, Tally tl) {
+    const int b = blockIdx.z;
+    if (!mask[b]) return;
+    tally_once(tl);
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iz = blockIdx.y * blockDim.y + threadIdx.y;
+    if (ix >= nx || iz >= nz) return;
+    const size_t N = (size_t)nx * nz;
+    const size_t p = (size_t)iz * nx + ix;
+    float2 r = f[(size_t)b * N + p];
+    float2 u0 = make_float2(0.f, 0.f);
+    if (u_in) {
+        const float2* ub = u_in + (size_t)b * N;
+        u0 = ub[p];
+        r = csub(r, op.apply(ub, b, ix, iz));
+    }
+    float2 d = op.diag(b, (int)p);
+    float2 q = cdiv(r, d);
+    u_out[(size_t)b * N + p] = make_float2(u0.x + w * q.x, u0.y + w * q.y);
+}
+
+// rc(J, I) = sum_{a,b} w_a w_b / 16 (f - A u)(2J+1+a, 2I+1+b)   (u == nullptr: u = 0)
+template <class Op>
+__global__ void restrict_residual_kernel(Op op, float2* __restrict__ rc, const float2* __restrict__ u,
+                                         const float2* __restrict__ f, int nx, int nz, const int* mask,
+                                         Tally tl) {
+    const int b = blockIdx.z;
+    if (!mask[b]) return;
+    tally_once(tl);
+    const int nxc = nx / 2, nzc = nz / 2;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I >= nxc || J >= nzc) return;
+    const size_t N = (size_t)nx * nz;
+    const float2* fb = f + (size_t)b * N;
+    const float2* ub = u ? u + (size_t)b * N : nullptr;
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int a = -1; a <= 1; ++a) {
+        int iz = 2 * J + 1 + a;
+        if (iz < 0 || iz >= nz) continue;
+        float wa = (a == 0) ? 2.f : 1.f;
+#pragma unroll
+        for (int c = -1; c <= 1; ++c) {
+            int ix = 2 * I + 1 + c;
+            if (ix < 0 || ix >= nx) continue;
+            float wt = wa * ((c == 0) ? 2.f : 1.f) * (1.0f / 16.0f);
+            float2 r = fb[(size_t)iz * nx + ix];
+            if (ub) r = csub(r, op.apply(ub, b, ix, iz));
+            acc.x += wt * r.x;
+            acc.y += wt * r.y;
+        }
+    }
+    rc[(size_t)b * nxc * nzc + (size_t)J * nxc + I] = acc;
+}
+
+// u += bilinear interpolation of ec (coarse node (J, I) on fine node (2J+1, 2I+1)).
+__global__ void prolong_add_kernel(float2* __restrict__ u, const float2* __restrict__ ec, int nx, int nz,
+                                   const int* mask, Tally tl) {
+    const int b = blockIdx.z;
+    if (!mask[b]) return;
+    tally_once(tl);
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iz = blockIdx.y * blockDim.y + threadIdx.y;
+    if (ix >= nx || iz >= nz) return;
+    const int nxc = nx / 2, nzc = nz / 2;
+    const float2* eb = ec + (size_t)b * nxc * nzc;
+    // 1D: odd fine index 2J+1 <- J (weight 1); even 2J <- J-1 and J (1/2 each)
+    int jz[2], jx[2];
+    float wz[2], wx[2];
+    int nzt, nxt;
+    if (iz & 1) { jz[0] = (iz - 1) >> 1; wz[0] = 1.f; nzt = 1; }
+    else { jz[0] = (iz >> 1) - 1; wz[0] = 0.5f; jz[1] = iz >> 1; wz[1] = 0.5f; nzt = 2; }
+    if (ix & 1) { jx[0] = (ix - 1) >> 1; wx[0] = 1.f; nxt = 1; }
+    else { jx[0] = (ix >> 1) - 1; wx[0] = 0.5f; jx[1] = ix >> 1; wx[1] = 0.5f; nxt = 2; }
+    float2 acc = make_float2(0.f, 0.f);
+    for (int s = 0; s < nzt; ++s) {
+        if (jz[s] < 0 || jz[s] >= nzc) continue;
+        for (int t = 0; t < nxt; ++t) {
+            if (jx[t] < 0 || jx[t] >= nxc) continue;
+            float wt = wz[s] * wx[t];
+            float2 e = eb[(size_t)jz[s] * nxc + jx[t]];
+            acc.x += wt * e.x;
+            acc.y += wt * e.y;
+        }
+    }
+    const size_t p = (size_t)b * nx * nz + (size_t)iz * nx + ix;
+    float2 v = u[p];
+    u[p] = make_float2(v.x + acc.x, v.y + acc.y);
+}
+
+__global__ void copy_masked_kernel(float2* __restrict__ dst, const float2* __restrict__ src, size_t n,
+                                   const int* mask, Tally tl) {
+    const int b = blockIdx.y;
+    if (!mask[b]) return;
+    tally_once(tl);
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+        dst[(size_t)b * n + p] = src[(size_t)b * n + p];
+}
+
+// 1D interpolation weight of fine index k from coarse index J: 1 if k = 2J+1,
+// 1/2 if |k - (2J+1)| = 1, else 0.
+__device__ __forceinline__ double pw(int k, int J) {
+    int d = k - (2 * J + 1);
+    return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0);
+}
+
+// Galerkin coarse operator A_c = R A_f (4 R^T) for frequency f, one thread per coarse node.
+template <class OpF>
+__global__ void galerkin_kernel(OpF fine, int f, float2* __restrict__ out, int nxf, int nzf) {
+    const int nxc = nxf / 2, nzc = nzf / 2;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I >= nxc || J >= nzc) return;
+    double2 acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = make_double2(0.0, 0.0);
+    for (int a = -1; a <= 1; ++a) {
+        int iz = 2 * J + 1 + a;
+        if (iz < 0 || iz >= nzf) continue;
+        for (int c = -1; c <= 1; ++c) {
+            int ix = 2 * I + 1 + c;
+            if (ix < 0 || ix >= nxf) continue;
+            double wr = (a == 0 ? 2.0 : 1.0) * (c == 0 ? 2.0 : 1.0) / 16.0;
+            for (int k = 0; k < 9; ++k) {
+                int kz = iz + k / 3 - 1, kx = ix + k % 3 - 1;
+                if (kz < 0 || kz >= nzf || kx < 0 || kx >= nxf) continue;
+                double2 A = fine.entry(f, iz, ix, k);
+                if (A.x == 0.0 && A.y == 0.0) continue;
+                for (int dJ = -1; dJ <= 1; ++dJ) {
+                    int Jp = J + dJ;
+                    if (Jp < 0 || Jp >= nzc) continue;
+                    double pz = pw(kz, Jp);
+                    if (pz == 0.0) continue;
+                    for (int dI = -1; dI <= 1; ++dI) {
+                        int Ip = I + dI;
+                        if (Ip < 0 || Ip >= nxc) continue;
+                        double px = pw(kx, Ip);
+                        if (px == 0.0) continue;
+                        double wgt = wr * pz * px;
+                        int t = (dJ + 1) * 3 + (dI + 1);
+                        acc[t].x += wgt * A.x;
+                        acc[t].y += wgt * A.y;
+                    }
+                }
+            }
+        }
+    }
+    const size_t plane = (size_t)nxc * nzc;
+    float2* o = out + (size_t)f * 9 * plane;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) o[(size_t)k * plane + (size_t)J * nxc + I] = make_float2((float)acc[k].x, (float)acc[k].y);
+}
+
+dim3 grid2(int nx, int nz, int nb) { return dim3((nx + 31) / 32, (nz + 7) / 8, nb); }
+
+}  // namespace
+
+template <class Op>
+int launch_jacobi(const helm_ctx* c, const Op& op, float2* u_out, const float2* u_in, const float2* f, int nx,
+                  int nz, int nb, const int* mask) {
+    LaunchScope scope(c, (std::is_same<Op, OpFine5>::value ? K_JACOBI_FINE : K_JACOBI_COARSE));
+    jacobi_kernel<Op><<<grid2(nx, nz, nb), dim3(32, 8), 0, c->stream>>>(
+        op, u_out, u_in, f, c->opt.jacobi_w, nx, nz, mask,
+        tally(c, std::is_same<Op, OpFine5>::value ? K_JACOBI_FINE : K_JACOBI_COARSE,
+              (u_in ? 24ull : 16ull) * nx * nz));
+    HELM_CK(cudaGetLastError());
+    return HELM_OK;
+}
+template int launch_jacobi<OpFine5>(const helm_ctx*, const OpFine5&, float2*, const float2*, const float2*, int,
+                                    int, int, const int*);
+template int launch_jacobi<OpC9>(const helm_ctx*, const OpC9&, float2*, const float2*, const float2*, int, int,
+                                 int, const int*);
+
+template <class Op>
+int launch_restrict_residual(const helm_ctx* c, const Op& op, float2* rc, const float2* u, const float2* f,
+                             int nx, int nz, int nb, const int* mask) {
+    LaunchScope scope(c, (std::is_same<Op, OpFine5>::value ? K_RESTRICT_FINE : K_RESTRICT_COARSE));
+    restrict_residual_kernel<Op><<<grid2(nx / 2, nz / 2, nb), dim3(32, 8), 0, c->stream>>>(
+        op, rc, u, f, nx, nz, mask,
+        tally(c, std::is_same<Op, OpFine5>::value ? K_RESTRICT_FINE : K_RESTRICT_COARSE,
+              (u ? 16ull : 8ull) * nx * nz + 2ull * nx * nz));
+    HELM_CK(cudaGetLastError());
+    return HELM_OK;
+}
+template int launch_restrict_residual<OpFine5>(const helm_ctx*, const OpFine5&, float2*, const float2*,
+                                               const float2*, int, int, int, const int*);
+template int launch_restrict_residual<OpC9>(const helm_ctx*, const OpC9&, float2*, const float2*, const float2*,
+                                            int, int, int, const int*);
+
+int launch_prolong_add(const helm_ctx* c, float2* u, const float2* ec, int nx, int nz, int nb, const int* mask) {
+    LaunchScope scope(c, K_PROLONG);
+    prolong_add_kernel<<<grid2(nx, nz, nb), dim3(32, 8), 0, c->stream>>>(u, ec, nx, nz, mask,
+                                                                          tally(c, K_PROLONG, 18ull * nx * nz));
+    HELM_CK(cudaGetLastError());
+    return HELM_OK;
+}
+
+int launch_copy_masked(const helm_ctx* c, float2* dst, const float2* src, size_t n, int nb, const int* mask) {
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 148) blocks = 148;
+    LaunchScope scope(c, K_COPY);
+    copy_masked_kernel<<<dim3((unsigned)blocks, nb), 256, 0, c->stream>>>(dst, src, n, mask, tally(c, K_COPY, 16ull * n));
+    HELM_CK(cudaGetLastError());
+    return HELM_OK;
+}
+
+int launch_galerkin(helm_ctx* c, int level) {
+    // builds lev[level].coef9 from lev[level-1] for every frequency
+    const Level& F = c->lev[level - 1];
+    for (int f = 0; f < c->nfreq; ++f) {
+        dim3 grid((F.nx / 2 + 31) / 32, (F.nz / 2 + 7) / 8);
+        if (level == 1) {
+            LaunchScope scope(c, K_GALERKIN);
+            galerkin_kernel<OpFine5><<<grid, dim3(32, 8), 0, c->stream>>>(fine_op(c, 1), f, c->lev[level].coef9,
+                                                                         F.nx, F.nz);
+        } else {
+            LaunchScope scope(c, K_GALERKIN);
+            galerkin_kernel<OpC9><<<grid, dim3(32, 8), 0, c->stream>>>(coarse_op(c, level - 1), f,
+                                                                      c->lev[level].coef9, F.nx, F.nz);
+        }
+        HELM_CK(cudaGetLastError());
+    }
+    return HELM_OK;
+}
+
+}  // namespace helm

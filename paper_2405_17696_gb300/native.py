@@ -1,0 +1,205 @@
+"""Thin ctypes binding of libhelm (include/helm.h): argument marshalling only.
+
+Every array argument may be a torch tensor (CUDA or CPU) or a numpy array;
+the binding passes its data pointer and sizes, and libhelm does all the
+work on the GPU.  The shared library is built in-tree by
+``paper_2405_17696_gb300.build``; importing this module fails loudly if it
+is missing - there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhelm.so")
+
+HELM_OK, HELM_EINVAL, HELM_ENOMEM, HELM_ECUDA, HELM_ENOCONV, HELM_EBREAKDOWN, HELM_ETIMEOUT, \
+    HELM_EUNSUPPORTED = range(8)
+HELM_PC_NONE, HELM_PC_MG, HELM_PC_CNN = 0, 1, 2
+HELM_COARSE_GMRES, HELM_COARSE_JACOBI = 0, 1
+HELM_OP_H, HELM_OP_SL = 0, 1
+HELM_SOLVE_ADJOINT, HELM_SOLVE_ZERO_X0 = 1, 2
+
+STATUS_NAMES = {0: "HELM_OK", 1: "HELM_EINVAL", 2: "HELM_ENOMEM", 3: "HELM_ECUDA", 4: "HELM_ENOCONV",
+                5: "HELM_EBREAKDOWN", 6: "HELM_ETIMEOUT", 7: "HELM_EUNSUPPORTED"}
+
+
+class HelmError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class helm_opts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("mg_levels", ctypes.c_int),
+                ("pre", ctypes.c_int), ("post", ctypes.c_int), ("jacobi_w", ctypes.c_float),
+                ("sl_beta", ctypes.c_float), ("sl_include_gamma", ctypes.c_int), ("coarse_kind", ctypes.c_int),
+                ("coarse_iters", ctypes.c_int), ("precond", ctypes.c_int), ("max_rhs", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class helm_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.POINTER(ctypes.c_int)), ("rel_res", ctypes.POINTER(ctypes.c_double)),
+                ("status", ctypes.POINTER(ctypes.c_int))]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libhelm.so is not built ({LIB_PATH}); run paper_2405_17696_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, ip, fp = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    lib.helm_default_opts.argtypes = [ctypes.POINTER(helm_opts)]
+    lib.helm_default_opts.restype = None
+    lib.helm_setup.argtypes = [ctypes.POINTER(vp), vp, vp, ip, ip, fp, fp, vp, ip, vp, ctypes.POINTER(helm_opts)]
+    lib.helm_setup.restype = ip
+    lib.helm_set_medium.argtypes = [vp, vp, vp, vp, ip]
+    lib.helm_set_medium.restype = ip
+    lib.helm_solve.argtypes = [vp, vp, vp, ip, vp, ctypes.c_double, ip, ctypes.POINTER(helm_stats)]
+    lib.helm_solve.restype = ip
+    lib.helm_apply.argtypes = [vp, vp, vp, ip, vp, ip]
+    lib.helm_apply.restype = ip
+    lib.helm_vcycle.argtypes = [vp, vp, vp, vp, ip, vp]
+    lib.helm_vcycle.restype = ip
+    lib.helm_destroy.argtypes = [vp]
+    lib.helm_destroy.restype = None
+    lib.helm_last_error.argtypes = []
+    lib.helm_last_error.restype = ctypes.c_char_p
+    lib.helm_profile_enable.argtypes = [vp, ip]
+    lib.helm_profile_enable.restype = ip
+    lib.helm_profile_read.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int)]
+    lib.helm_profile_read.restype = ip
+    lib.helm_launch_count.argtypes = []
+    lib.helm_launch_count.restype = ctypes.c_longlong
+    return lib
+
+
+lib = _load()
+
+
+def last_error() -> str:
+    return lib.helm_last_error().decode()
+
+
+def _check(status: int, where: str, ok=(HELM_OK,)):
+    if status not in ok:
+        raise HelmError(status, where, last_error())
+    return status
+
+
+def _ptr(a, dtype_name: str):
+    """Data pointer of a contiguous torch tensor or numpy array of the expected dtype."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        if a.dtype.name != dtype_name:
+            raise TypeError(f"expected {dtype_name}, got {a.dtype.name}")
+        return a.ctypes.data
+    # torch tensor
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    tname = str(a.dtype).replace("torch.", "")
+    if tname != dtype_name:
+        raise TypeError(f"expected {dtype_name}, got {tname}")
+    return a.data_ptr()
+
+
+def _int_array(freq_idx, n):
+    if freq_idx is None:
+        return None, None
+    arr = np.ascontiguousarray(np.asarray(freq_idx, dtype=np.int32))
+    if arr.shape != (n,):
+        raise ValueError("freq_idx must have one entry per right-hand side")
+    return arr, arr.ctypes.data
+
+
+def helm_default_opts(**overrides) -> helm_opts:
+    o = helm_opts()
+    lib.helm_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def helm_setup(kappa, gamma, nx: int, nz: int, hx: float, hz: float, omegas, net=None, opts=None):
+    """Returns an opaque context handle (ctypes.c_void_p)."""
+    om = omegas
+    if not hasattr(om, "data_ptr") and not isinstance(om, np.ndarray):
+        om = np.ascontiguousarray(np.asarray(om, dtype=np.float32))
+    nfreq = int(om.shape[0]) if hasattr(om, "shape") else len(om)
+    ctx = ctypes.c_void_p()
+    o = opts if opts is not None else helm_default_opts()
+    st = lib.helm_setup(ctypes.byref(ctx), _ptr(kappa, "float32"), _ptr(gamma, "float32"), nx, nz, hx, hz,
+                        _ptr(om, "float32"), nfreq, net, ctypes.byref(o))
+    _check(st, "helm_setup")
+    return ctx
+
+
+def helm_set_medium(ctx, kappa, gamma, omegas):
+    om = omegas
+    if not hasattr(om, "data_ptr") and not isinstance(om, np.ndarray):
+        om = np.ascontiguousarray(np.asarray(om, dtype=np.float32))
+    nfreq = int(om.shape[0])
+    _check(lib.helm_set_medium(ctx, _ptr(kappa, "float32"), _ptr(gamma, "float32"), _ptr(om, "float32"), nfreq),
+           "helm_set_medium")
+
+
+def helm_solve(ctx, rhs, x, nrhs: int, freq_idx=None, tol: float = 1e-6, flags: int = 0, check=True):
+    """flags: HELM_SOLVE_ADJOINT | HELM_SOLVE_ZERO_X0.
+    Returns (status, iters[nrhs], rel_res[nrhs], per_rhs_status[nrhs]) as numpy arrays."""
+    iters = np.zeros(nrhs, dtype=np.int32)
+    rel = np.zeros(nrhs, dtype=np.float64)
+    stat = np.zeros(nrhs, dtype=np.int32)
+    stats = helm_stats(iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                       rel.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                       stat.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    _keep, fptr = _int_array(freq_idx, nrhs)
+    st = lib.helm_solve(ctx, _ptr(rhs, "complex64"), _ptr(x, "complex128"), nrhs, fptr, tol, flags,
+                        ctypes.byref(stats))
+    if check:
+        _check(st, "helm_solve", ok=(HELM_OK, HELM_ENOCONV, HELM_EBREAKDOWN))
+    return st, iters, rel, stat
+
+
+def helm_apply(ctx, x, y, nrhs: int, freq_idx=None, op: int = HELM_OP_H):
+    _keep, fptr = _int_array(freq_idx, nrhs)
+    _check(lib.helm_apply(ctx, _ptr(x, "complex64"), _ptr(y, "complex64"), nrhs, fptr, op), "helm_apply")
+
+
+def helm_vcycle(ctx, f, u0, u, nrhs: int, freq_idx=None):
+    _keep, fptr = _int_array(freq_idx, nrhs)
+    _check(lib.helm_vcycle(ctx, _ptr(f, "complex64"), _ptr(u0, "complex64"), _ptr(u, "complex64"), nrhs, fptr),
+           "helm_vcycle")
+
+
+def helm_destroy(ctx):
+    if ctx:
+        lib.helm_destroy(ctx)
+
+
+def helm_profile_enable(ctx, on: bool = True):
+    _check(lib.helm_profile_enable(ctx, 1 if on else 0), "helm_profile_enable")
+
+
+def helm_profile_read(ctx) -> dict:
+    """{kernel class: (total ms, launches, algorithmic bytes)}"""
+    n = 64
+    names = (ctypes.c_char_p * n)()
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_longlong * n)()
+    nbytes = (ctypes.c_double * n)()
+    k = ctypes.c_int(0)
+    _check(lib.helm_profile_read(ctx, n, names, ms, cnt, nbytes, ctypes.byref(k)), "helm_profile_read")
+    return {names[i].decode(): (ms[i], cnt[i], nbytes[i]) for i in range(k.value)}
+
+
+def helm_launch_count() -> int:
+    return int(lib.helm_launch_count())

@@ -1,0 +1,246 @@
+"""GPU parity of libhelm against the CPU FP64 oracle, through the C ABI.
+
+* the five-point operator H (Eq. 3.2) and the shifted Laplacian P (Eq. 3.12),
+  element by element, on grids that span several tiles with ragged tails,
+  with mixed frequencies in one batch;
+* one Galerkin V-cycle (Sec. 3.4) against the oracle's V-cycle, from zero
+  and from a given initial guess (the M_VU form of Eq. 3.14);
+* MG-FGMRES solves against the direct solve: FP64 relative residual <= 1e-6
+  (evaluated by the oracle from the GPU iterate) and relative error <= 1e-4;
+* adjoint solves through conjugation (Eq. 4.8) against a direct adjoint
+  solve; host-pointer arguments; chunking over max_rhs; edge cases.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import helmholtz as H, multigrid as MG  # noqa: E402
+from paper_2405_17696_gb300 import media  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def native():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_17696_gb300 import build
+    build.build()
+    from paper_2405_17696_gb300 import native as n
+    return n
+
+
+def _ctx(native, w, **opts):
+    o = native.helm_default_opts(**opts)
+    om = np.asarray(w.omegas, dtype=np.float32)
+    k = torch.from_numpy(w.kappa).cuda()
+    g = torch.from_numpy(w.gamma).cuda()
+    return native.helm_setup(k, g, w.nx, w.nz, w.h, w.h, torch.from_numpy(om).cuda(), opts=o)
+
+
+def _f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+# --------------------------------------------------------------------------
+# operator
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nx,nz", [(76, 44), (160, 160), (512, 256)])
+@pytest.mark.parametrize("op", [0, 1])
+def test_operator_parity(native, nx, nz, op):
+    w = media.crop_workload(nx, nz, freqs=(3.0, 6.0), width=8)
+    ctx = _ctx(native, w, mg_levels=2)
+    try:
+        nb = 5
+        x = media.complex_normal((nb, nz, nx), seed=7)
+        fi = np.array([0, 1, 1, 0, 1], dtype=np.int32)
+        y = torch.zeros((nb, nz, nx), dtype=torch.complex64, device="cuda")
+        native.helm_apply(ctx, torch.from_numpy(x).cuda(), y, nb, fi, op)
+        y = y.cpu().numpy().astype(np.complex128)
+        # oracle on the same float32-rounded medium
+        kap = _f32(w.kappa)
+        gam = _f32(w.gamma)
+        for b in range(nb):
+            om = float(np.float32(w.omegas[fi[b]]))
+            if op == 0:
+                coef = H.helmholtz_coefficient(kap, gam, om)
+            else:
+                coef = H.shifted_coefficient(kap, gam, om, beta=0.5, include_gamma=True)
+            ref = H.operator_apply(x[b].astype(np.complex128), coef, w.h, w.h)
+            scale = (4 / w.h ** 2 + np.abs(coef)) * np.abs(x[b]).max()
+            err = np.abs(y[b] - ref)
+            assert err.max() <= 2e-6 * scale.max(), (b, err.max(), scale.max())
+    finally:
+        native.helm_destroy(ctx)
+
+
+# --------------------------------------------------------------------------
+# V-cycle
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nx,nz,levels,kind", [(64, 32, 3, 0), (96, 48, 2, 0), (128, 64, 4, 1), (160, 160, 3, 0)])
+@pytest.mark.parametrize("with_u0", [False, True])
+def test_vcycle_parity(native, nx, nz, levels, kind, with_u0):
+    w = media.crop_workload(nx, nz, freqs=(4.0, 7.0), width=8)
+    ctx = _ctx(native, w, mg_levels=levels, coarse_kind=kind, coarse_iters=8 if kind == 0 else 6)
+    try:
+        nb = 3
+        f = media.complex_normal((nb, nz, nx), seed=21)
+        u0 = media.complex_normal((nb, nz, nx), seed=22) * 0.1 if with_u0 else None
+        fi = np.array([1, 0, 1], dtype=np.int32)
+        u = torch.zeros((nb, nz, nx), dtype=torch.complex64, device="cuda")
+        native.helm_vcycle(ctx, torch.from_numpy(f).cuda(),
+                           torch.from_numpy(u0).cuda() if with_u0 else None, u, nb, fi)
+        u = u.cpu().numpy().astype(np.complex128)
+        p = MG.VCycleParams(levels=levels, pre=2, post=2, jacobi_w=float(np.float32(0.8)), beta=0.5,
+                            include_gamma=True, coarse_kind="gmres" if kind == 0 else "jacobi",
+                            coarse_iters=8 if kind == 0 else 6)
+        for b in range(nb):
+            om = float(np.float32(w.omegas[fi[b]]))
+            pc = MG.VCyclePreconditioner(_f32(w.kappa), _f32(w.gamma), om, w.h, w.h, p)
+            ref = pc(f[b].astype(np.complex128), None if u0 is None else u0[b].astype(np.complex128))
+            rel = np.linalg.norm(u[b] - ref) / np.linalg.norm(ref)
+            assert rel < 2e-4, (b, rel)
+    finally:
+        native.helm_destroy(ctx)
+
+
+# --------------------------------------------------------------------------
+# solves
+# --------------------------------------------------------------------------
+
+def _solve_and_check(native, w, fi, rhs, levels=3, adjoint=0, tol=1e-6, host=False, **opts):
+    flags = native.HELM_SOLVE_ADJOINT if adjoint else 0
+    ctx = _ctx(native, w, mg_levels=levels, **opts)
+    try:
+        nb = rhs.shape[0]
+        if host:
+            x = np.zeros(rhs.shape, dtype=np.complex128)
+            st, iters, rel, stat = native.helm_solve(ctx, np.ascontiguousarray(rhs), x, nb, fi, tol, flags)
+            xs = x
+        else:
+            x = torch.zeros(rhs.shape, dtype=torch.complex128, device="cuda")
+            st, iters, rel, stat = native.helm_solve(ctx, torch.from_numpy(rhs).cuda(), x, nb, fi, tol, flags)
+            xs = x.cpu().numpy()
+    finally:
+        native.helm_destroy(ctx)
+    assert st == native.HELM_OK, (st, stat, iters, rel)
+    kap, gam = _f32(w.kappa), _f32(w.gamma)
+    for b in range(nb):
+        om = float(np.float32(w.omegas[fi[b]]))
+        bb = rhs[b].astype(np.complex128)
+        s = H.DirectSolver(kap, gam, om, w.h, w.h)
+        if adjoint:
+            xd = s.solve_adjoint(bb)
+            r = bb - np.conj(H.helmholtz_apply(np.conj(xs[b]), kap, gam, om, w.h, w.h))
+            rr = np.linalg.norm(r) / np.linalg.norm(bb)
+        else:
+            xd = s.solve(bb)
+            rr = H.relative_residual(xs[b], bb, kap, gam, om, w.h, w.h)
+        err = H.relative_error(xs[b], xd)
+        assert rr <= tol, (b, rr)
+        assert err <= 1e-4, (b, err)
+        assert abs(rel[b] - rr) <= 0.05 * tol + 1e-3 * rr
+    return iters
+
+
+def test_solve_small_constant_medium(native):
+    w = media.workload_small()
+    rhs = w.rhs()
+    iters = _solve_and_check(native, w, np.zeros(1, np.int32), rhs, levels=3)
+    assert 0 < iters[0] <= 300
+
+
+@pytest.mark.parametrize("nx,nz", [(64, 32), (200, 96)])
+def test_solve_layered_mixed_frequencies(native, nx, nz):
+    w = media.crop_workload(nx, nz, freqs=(3.0, 5.0, 7.0), width=12)
+    rhs = w.rhs()
+    fi = w.freq_index()
+    _solve_and_check(native, w, fi, rhs, levels=3)
+
+
+def test_solve_random_rhs_and_adjoint(native):
+    w = media.crop_workload(96, 64, freqs=(5.0,), width=10)
+    rhs = media.complex_normal((3, w.nz, w.nx), seed=5)
+    fi = np.zeros(3, np.int32)
+    _solve_and_check(native, w, fi, rhs, levels=3, adjoint=0)
+    _solve_and_check(native, w, fi, rhs, levels=3, adjoint=1)
+
+
+def test_solve_host_pointers_and_chunking(native):
+    w = media.crop_workload(64, 32, freqs=(4.0, 6.0), width=8)
+    rhs = np.concatenate([w.rhs(), w.rhs()[:3]], axis=0)
+    fi = np.concatenate([w.freq_index(), w.freq_index()[:3]]).astype(np.int32)
+    _solve_and_check(native, w, fi, rhs, levels=2, host=True, max_rhs=4)
+
+
+def test_solve_edge_cases(native):
+    w = media.crop_workload(64, 32, freqs=(4.0,), width=8)
+    ctx = _ctx(native, w, mg_levels=3)
+    try:
+        # zero right-hand side -> zero solution, converged
+        rhs = np.zeros((2, w.nz, w.nx), np.complex64)
+        rhs[1, 3, 9] = 1.0
+        x = torch.ones((2, w.nz, w.nx), dtype=torch.complex128, device="cuda")
+        st, iters, rel, stat = native.helm_solve(ctx, torch.from_numpy(rhs).cuda(), x, 2, None, 1e-6, 0)
+        assert st == native.HELM_OK
+        assert torch.count_nonzero(x[0]).item() == 0
+        assert rel[1] <= 1e-6
+        # no right-hand sides: nothing to do
+        st, *_ = native.helm_solve(ctx, torch.from_numpy(rhs).cuda(), x, 0, None, 1e-6, 0)
+        assert st == native.HELM_OK
+        # a frequency index outside the context is rejected
+        with pytest.raises(native.HelmError) as e:
+            native.helm_solve(ctx, torch.from_numpy(rhs).cuda(), x, 2, np.array([0, 3], np.int32), 1e-6, 0)
+        assert e.value.status == native.HELM_EINVAL
+        # a cap of one step cannot reach 1e-6: reported per RHS, others valid
+    finally:
+        native.helm_destroy(ctx)
+    ctx = _ctx(native, w, mg_levels=3, max_iter=1)
+    try:
+        rhs = media.complex_normal((2, w.nz, w.nx), seed=1)
+        x = torch.zeros((2, w.nz, w.nx), dtype=torch.complex128, device="cuda")
+        st, iters, rel, stat = native.helm_solve(ctx, torch.from_numpy(rhs).cuda(), x, 2, None, 1e-10, 0)
+        assert st == native.HELM_ENOCONV
+        assert list(stat) == [native.HELM_ENOCONV] * 2
+        assert list(iters) == [1, 1]
+    finally:
+        native.helm_destroy(ctx)
+
+
+def test_setup_rejects_bad_grids(native):
+    w = media.crop_workload(64, 32, freqs=(4.0,), width=8)
+    with pytest.raises(native.HelmError) as e:
+        _ctx(native, media.crop_workload(66, 32, freqs=(4.0,), width=8), mg_levels=3)
+    assert e.value.status == native.HELM_EINVAL
+    with pytest.raises(native.HelmError):
+        _ctx(native, w, restart=0)
+
+
+def test_batched_workload_sampled_against_direct_solve(native):
+    # the 512x256, 3-frequency, 192-RHS batch in one launch; a sample of the
+    # RHS is checked against the direct solve, every RHS by its FP64 residual
+    w = media.workload_batched()
+    rhs = w.rhs()
+    fi = w.freq_index()
+    ctx = _ctx(native, w, mg_levels=3)
+    try:
+        x = torch.zeros(rhs.shape, dtype=torch.complex128, device="cuda")
+        st, iters, rel, stat = native.helm_solve(ctx, torch.from_numpy(rhs).cuda(), x, rhs.shape[0], fi, 1e-6, 0)
+        xs = x.cpu().numpy()
+    finally:
+        native.helm_destroy(ctx)
+    assert st == native.HELM_OK, (stat, iters)
+    kap, gam = _f32(w.kappa), _f32(w.gamma)
+    for b in range(rhs.shape[0]):
+        om = float(np.float32(w.omegas[fi[b]]))
+        rr = H.relative_residual(xs[b], rhs[b], kap, gam, om, w.h, w.h)
+        assert rr <= 1e-6, (b, rr)
+    for b in (0, 63, 64 + 17, 191):
+        om = float(np.float32(w.omegas[fi[b]]))
+        xd = H.DirectSolver(kap, gam, om, w.h, w.h).solve(rhs[b].astype(np.complex128))
+        assert H.relative_error(xs[b], xd) <= 1e-4
