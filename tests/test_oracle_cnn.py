@@ -1,0 +1,115 @@
+"""Pins of the oracle's encoder-solver network pieces (no GPU).
+
+* the 'same' 3x3 convolution equals scipy's 2-D cross-correlation with zero
+  padding, channel by channel (a library routine, called);
+* 'down' equals 'same' sampled at the odd nodes (2Y+1, 2X+1); 'up' equals
+  'same' applied to the nearest-neighbour upsampled input;
+* gather/scatter are adjoint (<conv(x), y> = <x, conv^T(y)> without bias);
+* the backward pass of the whole encoder-solver network matches central finite
+  differences of a scalar loss, for the parameters and for the input;
+* one Adam step from zero moments moves every parameter by lr in the
+  direction opposite to its gradient sign (Kingma & Ba's bias correction).
+"""
+import numpy as np
+import pytest
+from scipy.signal import correlate2d
+
+from oracle import cnn
+
+
+def _rng(s):
+    return np.random.default_rng(s)
+
+
+def test_same_conv_is_cross_correlation():
+    g = _rng(0)
+    x = g.normal(size=(2, 7, 9, 3))
+    w = g.normal(size=(4, 9, 3))
+    b = g.normal(size=4)
+    y = cnn.conv_forward(x, w, b, "same")
+    for n in range(2):
+        for co in range(4):
+            ref = b[co] + sum(correlate2d(x[n, :, :, ci], w[co, :, ci].reshape(3, 3), mode="same", boundary="fill")
+                              for ci in range(3))
+            assert np.allclose(y[n, :, :, co], ref, atol=1e-12)
+
+
+def test_down_and_up_modes():
+    g = _rng(1)
+    x = g.normal(size=(1, 8, 10, 2))
+    w = g.normal(size=(3, 9, 2))
+    b = g.normal(size=3)
+    same = cnn.conv_forward(x, w, b, "same")
+    down = cnn.conv_forward(x, w, b, "down")
+    assert np.allclose(down, same[:, 1::2, 1::2], atol=1e-12)
+    up = cnn.conv_forward(x, w, b, "up")
+    xu = np.repeat(np.repeat(x, 2, axis=1), 2, axis=2)
+    assert np.allclose(up, cnn.conv_forward(xu, w, b, "same"), atol=1e-12)
+
+
+@pytest.mark.parametrize("mode", ["same", "down", "up"])
+def test_conv_adjoint_identity(mode):
+    g = _rng(2)
+    x = g.normal(size=(2, 6, 8, 3))
+    w = g.normal(size=(5, 9, 3))
+    y0 = cnn.conv_forward(x, w, np.zeros(5), mode)
+    gy = g.normal(size=y0.shape)
+    dx, dw, db = cnn.conv_backward(x, w, gy, mode)
+    assert abs(np.sum(y0 * gy) - np.sum(x * dx)) < 1e-10 * abs(np.sum(y0 * gy))
+    assert abs(np.sum(y0 * gy) - np.sum(w * dw)) < 1e-10 * abs(np.sum(y0 * gy))
+
+
+def _tiny():
+    specs = cnn.layer_specs(widths=(2, 4), in_enc=3, in_sol=3, out_ch=2)
+    theta = cnn.he_init(specs, seed=5) + 0.05 * _rng(6).normal(size=cnn.n_params(specs))
+    g = _rng(7)
+    enc_in = g.normal(size=(1, 8, 8, 3))
+    sol_in = g.normal(size=(2, 8, 8, 3))
+    target = g.normal(size=(2, 8, 8, 2))
+    return specs, theta, enc_in, sol_in, target
+
+
+def _loss(specs, theta, enc_in, sol_in, target):
+    out, tape = cnn.network_forward(cnn.unflatten(theta, specs), specs, enc_in, sol_in)
+    val, gout = cnn.mse(out, target)
+    return val, gout, tape
+
+
+def test_network_backward_matches_finite_differences():
+    specs, theta, enc_in, sol_in, target = _tiny()
+    P = cnn.unflatten(theta, specs)
+    val, gout, tape = _loss(specs, theta, enc_in, sol_in, target)
+    grads, _ = cnn.backward(P, specs, tape, gout)
+    gflat = cnn.flatten_grads(grads, specs)
+    # the loss is piecewise smooth (ReLU kinks lie close to the evaluation
+    # point in such a narrow net), so the step must be small
+    d = _rng(8).normal(size=theta.size)
+    eps = 1e-8
+    fp = _loss(specs, theta + eps * d, enc_in, sol_in, target)[0]
+    fm = _loss(specs, theta - eps * d, enc_in, sol_in, target)[0]
+    fd = (fp - fm) / (2 * eps)
+    assert abs(fd - gflat @ d) <= 1e-5 * abs(fd)
+    # every layer receives gradient (encoder included, through the context features)
+    assert all(np.any(grads[name][0] != 0) for name, *_ in specs)
+
+
+def test_network_input_gradient():
+    specs, theta, enc_in, sol_in, target = _tiny()
+    P = cnn.unflatten(theta, specs)
+    out, tape = cnn.network_forward(P, specs, enc_in, sol_in)
+    val, gout = cnn.mse(out, target)
+    _, gx = cnn.backward(P, specs, tape, gout, wrt=sol_in)
+    d = _rng(9).normal(size=sol_in.shape)
+    eps = 1e-8
+    fp = cnn.mse(cnn.network_forward(P, specs, enc_in, sol_in + eps * d)[0], target)[0]
+    fm = cnn.mse(cnn.network_forward(P, specs, enc_in, sol_in - eps * d)[0], target)[0]
+    assert abs((fp - fm) / (2 * eps) - np.sum(gx * d)) <= 1e-5 * abs((fp - fm) / (2 * eps))
+
+
+def test_adam_first_step():
+    g = _rng(10)
+    theta = g.normal(size=20)
+    grad = g.normal(size=20)
+    t1, m, v = cnn.adam_step(theta, grad, np.zeros(20), np.zeros(20), 1, lr=1e-3, eps=0.0)
+    assert np.allclose(t1 - theta, -1e-3 * np.sign(grad), atol=1e-15)
+    assert np.allclose(m, 0.1 * grad) and np.allclose(v, 0.001 * grad * grad)
