@@ -124,6 +124,12 @@ int helm_set_medium(helm_ctx* ctx, const float* kappa, const float* gamma,
 int helm_solve(helm_ctx* ctx, const helm_c64* rhs, helm_c128* x, int nrhs,
                const int* freq_idx, double tol, int flags, helm_stats* stats);
 
+/* r = rhs - H(m, w_f) x evaluated in FP64 from the complex128 x (the check that
+ * decides convergence in helm_solve), stored as complex64, and the per-RHS relative
+ * residual ||r||_2 / ||rhs||_2 (FP64) into the host array rel_res (may be NULL). */
+int helm_residual(helm_ctx* ctx, const helm_c64* rhs, const helm_c128* x, helm_c64* r, int nrhs,
+                  const int* freq_idx, double* rel_res);
+
 /* y = A x for A = H(m, w_f) (op = HELM_OP_H, Eq. 3.2) or the fine shifted Laplacian
  * P (op = HELM_OP_SL, Eq. 3.12 with the context's shift options); complex64 in/out. */
 int helm_apply(helm_ctx* ctx, const helm_c64* x, helm_c64* y, int nrhs,
@@ -133,6 +139,22 @@ int helm_apply(helm_ctx* ctx, const helm_c64* x, helm_c64* y, int nrhs,
  * from the initial guess u0 (NULL: zero), Sec. 3.4 / Eq. 3.14.  complex64. */
 int helm_vcycle(helm_ctx* ctx, const helm_c64* f, const helm_c64* u0, helm_c64* u,
                 int nrhs, const int* freq_idx);
+
+/* FWI data misfit and its gradient with respect to the squared slowness m = kappa^2
+ * (Eq. 3.5 with Sigma = I and no regulariser; adjoint-state gradient, Sec. 4.3):
+ *     Phi = sum_{j,s} || P^T u_sj - d_sj ||^2,   u_sj = H(m, w_j)^{-1} e_{src_s} / (hx hz)
+ *     dPhi/dm = sum_{j,s} 2 w_j^2 Re((1 - i gamma) u_sj mu_sj),  mu_sj = H^{-1} P conj(P^T u_sj - d_sj)
+ * for every frequency j of the context and every source s.  The adjoint field mu is the
+ * conjugate of the solution of H^* lambda = P r (Eq. 4.8), obtained with a forward solve.
+ *   src_idx : host int32 [nsrc], flat grid index iz * nx + ix of each point source
+ *   rcv_idx : host int32 [nrcv], flat grid index of each receiver (all sources share them)
+ *   d_obs   : complex64 [nfreq][nsrc][nrcv] observed data (host or device)
+ *   tol     : relative residual of the forward and adjoint solves
+ *   misfit_out : host double;  grad_m_out : float32 [nz][nx] (host or device)
+ * Allocates its forward/adjoint wavefields per call (2 x 16 bytes per grid point and RHS
+ * of one chunk).  Returns the first failing helm_solve status, or HELM_OK. */
+int fwi_misfit_grad(helm_ctx* ctx, const int* src_idx, int nsrc, const int* rcv_idx, int nrcv,
+                    const helm_c64* d_obs, double tol, double* misfit_out, float* grad_m_out);
 
 void helm_destroy(helm_ctx* ctx);
 

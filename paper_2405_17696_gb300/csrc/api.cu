@@ -22,7 +22,8 @@ const char* kernel_name(int id) {
     static const char* names[K_COUNT] = {
         "stencil_apply", "residual64", "arnoldi_dots_fine", "arnoldi_dots_coarse", "arnoldi_update_fine",
         "arnoldi_update_coarse", "krylov_init", "lsq", "combine", "update_x64", "jacobi_fine", "jacobi_coarse",
-        "restrict_fine", "restrict_coarse", "prolong_add", "galerkin", "copy", "restart_check", "misc"};
+        "restrict_fine", "restrict_coarse", "prolong_add", "galerkin", "copy", "restart_check", "coarse_gmres",
+        "misc"};
     return (id >= 0 && id < K_COUNT) ? names[id] : "?";
 }
 
@@ -67,7 +68,7 @@ int launch_restart_check_dev(helm_ctx* c, int nb, double tol, int* n_active_dev)
 OpFine5 fine_op(const helm_ctx* c, int sl) {
     OpFine5 op;
     op.mg = c->mg;
-    op.omega2 = c->omega2;
+    op.omega = c->omega_d;
     op.rhs_freq = c->rhs_freq;
     op.nx = c->nx;
     op.nz = c->nz;
@@ -90,15 +91,14 @@ OpC9 coarse_op(const helm_ctx* c, int level) {
 
 namespace {
 
+// {kappa, gamma} interleaved so that one 8-byte load serves a grid point;
+// the frequencies are copied next to them.
 __global__ void pack_medium_kernel(const float* __restrict__ kappa, const float* __restrict__ gamma,
                                    float2* __restrict__ mg, size_t n, const float* __restrict__ omega,
-                                   float* __restrict__ omega2, int nfreq) {
+                                   float* __restrict__ omega_d, int nfreq) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i < (size_t)nfreq) omega2[i] = omega[i] * omega[i];
-    for (; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        float k = kappa[i];
-        mg[i] = make_float2(k * k, gamma[i]);
-    }
+    if (i < (size_t)nfreq) omega_d[i] = omega[i];
+    for (; i < n; i += (size_t)gridDim.x * blockDim.x) mg[i] = make_float2(kappa[i], gamma[i]);
 }
 
 __global__ void fill_int_kernel(int* p, int v, int n) {
@@ -217,20 +217,9 @@ int coarsest_solve(helm_ctx* c, int l, float2* u_out, const float2* f, int nb, c
     Level& L = c->lev[l];
     size_t Nc = (size_t)L.nx * L.nz;
     if (c->opt.coarse_kind == HELM_COARSE_GMRES) {
-        // f is stored in Vc[0]; plain GMRES(k) from zero
+        // f is stored in Vc[0]; plain GMRES(k) from zero, one thread block per RHS
         if (f != c->Vc) HELM_TRY(launch_copy_masked(c, c->Vc, f, Nc, nb, mask));
-        KState& st = c->coarse;
-        HELM_TRY(launch_kstate_init(c, st, c->Vc, L.nx, L.nz, nb, mask));
-        HELM_TRY(launch_normalize_v0(c, st, c->Vc, Nc, nb));
-        OpC9 op = coarse_op(c, l);
-        size_t vs = (size_t)c->cap * Nc;
-        for (int j = 0; j < st.k; ++j) {
-            HELM_TRY(launch_arnoldi_dots(c, op, st, c->Vc + (size_t)j * vs, c->Wc, c->Vc, vs, j, L.nx, L.nz, nb));
-            HELM_TRY(launch_arnoldi_update(c, st, c->Wc, c->Vc, vs, j, L.nx, L.nz, nb));
-        }
-        HELM_TRY(launch_lsq(c, st, nb));
-        HELM_TRY(launch_combine(c, st, u_out, c->Vc, vs, Nc, nb, mask));
-        return HELM_OK;
+        return launch_coarse_gmres(c, l, u_out, nb, mask);
     }
     // fixed number of damped-Jacobi sweeps from zero, last one into u_out
     int n = c->opt.coarse_iters;
@@ -398,7 +387,7 @@ int helm_setup(helm_ctx** out, const float* kappa, const float* gamma, int nx, i
     auto fail = [&](int s) { helm_destroy(c); return s; };
 
     if ((st = dalloc(c, &c->mg, N))) return fail(st);
-    if ((st = dalloc(c, &c->omega2, nfreq))) return fail(st);
+    if ((st = dalloc(c, &c->omega_d, nfreq))) return fail(st);
     if ((st = dalloc(c, &c->rhs_freq, c->cap))) return fail(st);
     if ((st = dalloc(c, &c->ones, c->cap))) return fail(st);
     {
@@ -408,7 +397,7 @@ int helm_setup(helm_ctx** out, const float* kappa, const float* gamma, int nx, i
         if ((st = stage_in(c, omegas, nfreq * sizeof(float), &so, true))) { stage_free(c, &sk); stage_free(c, &sg); return fail(st); }
         LaunchScope scope(c, K_MISC);
         pack_medium_kernel<<<1184, 256, 0, c->stream>>>((const float*)sk.dev, (const float*)sg.dev, c->mg, N,
-                                                         (const float*)so.dev, c->omega2, nfreq);
+                                                         (const float*)so.dev, c->omega_d, nfreq);
         cudaError_t e = cudaGetLastError();
         std::vector<float> om(nfreq);
         cudaError_t e2 = cudaMemcpyAsync(om.data(), so.dev, nfreq * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
@@ -497,7 +486,7 @@ int helm_set_medium(helm_ctx* c, const float* kappa, const float* gamma, const f
     if (!s) {
         LaunchScope scope(c, K_MISC);
         pack_medium_kernel<<<1184, 256, 0, c->stream>>>((const float*)sk.dev, (const float*)sg.dev, c->mg, N,
-                                                         (const float*)so.dev, c->omega2, nfreq);
+                                                         (const float*)so.dev, c->omega_d, nfreq);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); s = HELM_ECUDA; }
     }
@@ -514,6 +503,41 @@ int helm_set_medium(helm_ctx* c, const float* kappa, const float* gamma, const f
     stage_free(c, &so);
     if (!s && e != cudaSuccess) { set_error(cudaGetErrorString(e)); s = HELM_ECUDA; }
     return s;
+}
+
+int helm_residual(helm_ctx* c, const helm_c64* rhs, const helm_c128* x, helm_c64* r, int nrhs,
+                  const int* freq_idx, double* rel_res) {
+    g_last_error.clear();
+    if (!c || !rhs || !x || !r || nrhs < 0) { set_error("helm_residual: invalid argument"); return HELM_EINVAL; }
+    const size_t N = npts(c);
+    std::vector<double> rn2, bn2;
+    for (int b0 = 0; b0 < nrhs; b0 += c->cap) {
+        int nb = nrhs - b0 < c->cap ? nrhs - b0 : c->cap;
+        HELM_TRY(upload_freq(c, freq_idx ? freq_idx + b0 : nullptr, nb));
+        Staged sb, sx, sr;
+        int s = stage_in(c, rhs + (size_t)b0 * N, nb * N * sizeof(float2), &sb, true);
+        if (!s) s = stage_in(c, x + (size_t)b0 * N, nb * N * sizeof(double2), &sx, true);
+        if (!s) s = stage_in(c, r + (size_t)b0 * N, nb * N * sizeof(float2), &sr, false);
+        if (!s) s = launch_outer_init(c, nb);
+        if (!s) s = launch_residual64(c, (const double2*)sx.dev, (const float2*)sb.dev, (float2*)sr.dev, nb, 0, 1);
+        if (!s) s = stage_out(c, r + (size_t)b0 * N, &sr, nb * N * sizeof(float2));
+        rn2.resize(nb);
+        bn2.resize(nb);
+        if (!s && rel_res) {
+            cudaMemcpyAsync(rn2.data(), c->outer.rnorm2, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+            cudaMemcpyAsync(bn2.data(), c->outer.bnorm2, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        }
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        stage_free(c, &sb);
+        stage_free(c, &sx);
+        stage_free(c, &sr);
+        if (s) return s;
+        if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return HELM_ECUDA; }
+        if (rel_res)
+            for (int i = 0; i < nb; ++i)
+                rel_res[b0 + i] = bn2[i] > 0 ? std::sqrt(rn2[i] / bn2[i]) : std::sqrt(rn2[i]);
+    }
+    return HELM_OK;
 }
 
 int helm_apply(helm_ctx* c, const helm_c64* x, helm_c64* y, int nrhs, const int* freq_idx, int op) {

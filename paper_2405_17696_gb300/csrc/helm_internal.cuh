@@ -64,8 +64,8 @@ __host__ __device__ __forceinline__ double dabs2(double2 a) { return a.x * a.x +
 
 // Fine level: -Lap_h - w^2 m (1 - i sigma), sigma = gamma (H) or beta + incg*gamma (P).
 struct OpFine5 {
-    const float2* mg;        // [nz][nx] {m = kappa^2, gamma}
-    const float* omega2;     // [nfreq] w^2
+    const float2* mg;        // [nz][nx] {kappa, gamma}; m = kappa^2
+    const float* omega;      // [nfreq] w (rad/s)
     const int* rhs_freq;     // [cap] frequency index per RHS slot
     int nx, nz;
     float ax, az;            // 1/hx^2, 1/hz^2
@@ -75,7 +75,8 @@ struct OpFine5 {
 
     __device__ __forceinline__ float2 coef(int b, int idx) const {
         float2 p = __ldg(mg + idx);
-        float s = __ldg(omega2 + __ldg(rhs_freq + b)) * p.x;
+        float w = __ldg(omega + __ldg(rhs_freq + b));
+        float s = (w * w) * (p.x * p.x);
         float sig = sl ? (beta + (incg ? p.y : 0.0f)) : p.y;
         return make_float2(s, -s * sig);          // s (1 - i sig)
     }
@@ -102,7 +103,8 @@ struct OpFine5 {
         int dz = k / 3 - 1, dx = k % 3 - 1;
         if (dz == 0 && dx == 0) {
             float2 p = mg[iz * nx + ix];
-            double s = (double)omega2[f] * (double)p.x;
+            double w = omega[f], k = p.x;
+            double s = (w * w) * (k * k);
             double sig = sl ? ((double)beta + (incg ? (double)p.y : 0.0)) : (double)p.y;
             return make_double2(2.0 * ((double)ax + (double)az) - s, s * sig);
         }
@@ -186,7 +188,7 @@ struct OuterState {
 enum KernelId {
     K_APPLY = 0, K_RESIDUAL64, K_DOTS_FINE, K_DOTS_COARSE, K_UPDATE_FINE, K_UPDATE_COARSE, K_KINIT, K_LSQ,
     K_COMBINE, K_UPDATE_X, K_JACOBI_FINE, K_JACOBI_COARSE, K_RESTRICT_FINE, K_RESTRICT_COARSE, K_PROLONG,
-    K_GALERKIN, K_COPY, K_RESTART, K_MISC, K_COUNT
+    K_GALERKIN, K_COPY, K_RESTART, K_COARSE_GMRES, K_MISC, K_COUNT
 };
 const char* kernel_name(int id);
 
@@ -198,8 +200,9 @@ struct Tally {
     unsigned long long base = 0;
     unsigned long long per_step = 0;
 };
-__device__ __forceinline__ void tally_once(const Tally& t, int steps = 0) {
-    if (t.ctr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+// `first` marks the first block of the RHS being processed.
+__device__ __forceinline__ void tally_once(const Tally& t, bool first, int steps = 0) {
+    if (t.ctr && first && threadIdx.x == 0 && threadIdx.y == 0)
         atomicAdd(t.ctr, t.base + t.per_step * (unsigned long long)steps);
 }
 
@@ -229,8 +232,8 @@ struct helm_ctx {
     helm_opts opt{};
     cudaStream_t stream = nullptr;
     std::vector<float> omega;       // host copy (rad/s)
-    float2* mg = nullptr;           // [nz][nx] {m, gamma}
-    float* omega2 = nullptr;        // [nfreq]
+    float2* mg = nullptr;           // [nz][nx] {kappa, gamma}
+    float* omega_d = nullptr;       // [nfreq] angular frequencies
     int cap = 0;                    // RHS slots in the workspace
     int* rhs_freq = nullptr;        // [cap]
     int* ones = nullptr;            // [cap] all ones (mask for unmasked launches)
@@ -305,6 +308,7 @@ int launch_arnoldi_update_ex(const helm_ctx* c, KState& st, const float2* w, flo
                              int nx, int nz, int nb, const int* iters_base, int max_iter, int* status);
 int launch_lsq(const helm_ctx* c, KState& st, int nb);
 int launch_normalize_v0(const helm_ctx* c, KState& st, float2* v0, size_t n, int nb);
+int launch_coarse_gmres(const helm_ctx* c, int level, float2* u_out, int nb, const int* mask);
 int launch_combine(const helm_ctx* c, const KState& st, float2* out, const float2* Zb, size_t zstride,
                    size_t n, int nb, const int* mask);
 int launch_update_x64(const helm_ctx* c, const KState& st, double2* x, const float2* Zb, size_t zstride,

@@ -77,59 +77,60 @@ __device__ void givens_step(const KState& st, int b, int j, double hnext, double
     if (!finite || tiny || est <= st.tol_abs[b] || cap || j + 1 >= st.k) st.active[b] = 0;
 }
 
-// w = A z for RHS b and the inner products h_{i,j} = s_i <v~_i, w>, i <= j.
-template <class Op>
-__global__ void __launch_bounds__(NTHREADS) arnoldi_dots_kernel(Op op, KState st, const float2* __restrict__ z,
-                                                                float2* __restrict__ w,
-                                                                const float2* __restrict__ V, size_t vstride,
-                                                                int j, int nx, int nz, Tally tl) {
+// w = A z for RHS b and the inner products h_{i,j} = s_i <v~_i, w>, i <= j,
+// plus ||w||^2 for the scaled store of the next basis vector.  J = j is a
+// template parameter so that only the j+2 accumulators that are live occupy
+// registers.
+template <class Op, int J>
+__global__ void __launch_bounds__(NTHREADS, 3) arnoldi_dots_kernel(Op op, KState st, const float2* __restrict__ z,
+                                                                   float2* __restrict__ w,
+                                                                   const float2* __restrict__ V, size_t vstride,
+                                                                   int nx, int nz, Tally tl) {
     const int b = blockIdx.z;
     if (!st.active[b]) return;
-    tally_once(tl);
+    tally_once(tl, blockIdx.x == 0 && blockIdx.y == 0);
     const size_t N = (size_t)nx * nz;
     const float2* zb = z + (size_t)b * N;
     float2* wb = w + (size_t)b * N;
     const float2* Vb = V + (size_t)b * N;
     const int ix = blockIdx.x * TILE_X + threadIdx.x;
     const int iz0 = (blockIdx.y * TILE_Y + threadIdx.y) * ROWS;
-    float2 acc[KMAX + 2];   // acc[i] = <v~_i, w> for i <= j, acc[j+1] = ||w||^2
+    float2 acc[J + 2];   // acc[i] = <v~_i, w> for i <= J, acc[J+1] = ||w||^2
 #pragma unroll
-    for (int i = 0; i <= KMAX + 1; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < J + 2; ++i) acc[i] = make_float2(0.f, 0.f);
     if (ix < nx) {
+#pragma unroll 2
         for (int r = 0; r < ROWS; ++r) {
             int iz = iz0 + r;
             if (iz >= nz) break;
-            float2 y = op.apply(zb, b, ix, iz);
             size_t p = (size_t)iz * nx + ix;
+            float2 v[J + 1];
+#pragma unroll
+            for (int i = 0; i <= J; ++i) v[i] = Vb[(size_t)i * vstride + p];
+            float2 y = op.apply(zb, b, ix, iz);
             wb[p] = y;
 #pragma unroll
-            for (int i = 0; i <= KMAX; ++i) {
-                if (i <= j) {
-                    float2 v = Vb[(size_t)i * vstride + p];
-                    acc[i].x += v.x * y.x + v.y * y.y;   // conj(v) y
-                    acc[i].y += v.x * y.y - v.y * y.x;
-                }
+            for (int i = 0; i <= J; ++i) {
+                acc[i].x += v[i].x * y.x + v[i].y * y.y;   // conj(v) y
+                acc[i].y += v[i].x * y.y - v[i].y * y.x;
             }
-#pragma unroll
-            for (int i = 1; i <= KMAX + 1; ++i)
-                if (i == j + 1) acc[i].x += y.x * y.x + y.y * y.y;
+            acc[J + 1].x += y.x * y.x + y.y * y.y;
         }
     }
-    __shared__ double2 sm[NWARPS * (KMAX + 2)];
-    __shared__ double hsq[KMAX + 2];
+    __shared__ double2 sm[NWARPS * (J + 2)];
+    __shared__ double hsq[J + 2];
     const int ntiles = gridDim.x * gridDim.y;
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
     double2* part = st.partials + ((size_t)b * st.max_tiles) * (KMAX + 2);
-    bool last = reduce_block_last<KMAX + 2>(acc, j + 2, part + (size_t)tile * (KMAX + 2), st.counters + b,
-                                            ntiles, sm);
+    bool last = reduce_block_last<J + 2>(acc, J + 2, part + (size_t)tile * (KMAX + 2), st.counters + b, ntiles, sm);
     if (last) {
         const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-        if (tid <= j + 1) {
+        if (tid <= J + 1) {
             double2 h = sum_partials(part, ntiles, KMAX + 2, tid);
-            if (tid <= j) {
+            if (tid <= J) {
                 double sc = st.s[(size_t)b * (st.k + 1) + tid];
                 h = make_double2(h.x * sc, h.y * sc);
-                kcol(st, b, j)[tid] = h;
+                kcol(st, b, J)[tid] = h;
                 hsq[tid] = dabs2(h);
             } else {
                 hsq[tid] = h.x;   // ||w||^2
@@ -137,8 +138,8 @@ __global__ void __launch_bounds__(NTHREADS) arnoldi_dots_kernel(Op op, KState st
         }
         __syncthreads();
         if (tid == 0) {
-            double w2 = hsq[j + 1], proj = 0.0;
-            for (int i = 0; i <= j; ++i) proj += hsq[i];
+            double w2 = hsq[J + 1], proj = 0.0;
+            for (int i = 0; i <= J; ++i) proj += hsq[i];
             double est2 = w2 - proj;
             // a cancelled estimate only changes the scale the vector is stored at
             if (!(est2 > 1e-12 * w2)) est2 = 1e-12 * w2;
@@ -148,20 +149,21 @@ __global__ void __launch_bounds__(NTHREADS) arnoldi_dots_kernel(Op op, KState st
     }
 }
 
-// v~_{j+1} = w - sum_i h_{i,j} s_i v~_i, its norm, then the Givens step.
-__global__ void __launch_bounds__(NTHREADS) arnoldi_update_kernel(KState st, const float2* __restrict__ w,
-                                                                  float2* __restrict__ V, size_t vstride, int j,
-                                                                  int nx, int nz, const int* iters_base,
-                                                                  int max_iter, int* status, Tally tl) {
+// v~_{j+1} = (w - sum_i h_{i,j} s_i v~_i) / est, its norm, then the Givens step.
+template <int J>
+__global__ void __launch_bounds__(NTHREADS, 3) arnoldi_update_kernel(KState st, const float2* __restrict__ w,
+                                                                     float2* __restrict__ V, size_t vstride,
+                                                                     int nx, int nz, const int* iters_base,
+                                                                     int max_iter, int* status, Tally tl) {
     const int b = blockIdx.z;
     if (!st.active[b]) return;
-    tally_once(tl);
+    tally_once(tl, blockIdx.x == 0 && blockIdx.y == 0);
     const size_t N = (size_t)nx * nz;
-    __shared__ float2 coef[KMAX + 1];
+    __shared__ float2 coef[J + 1];
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const double inv = st.inv_est[b];
-    if (tid <= j) {
-        double2 h = kcol(st, b, j)[tid];
+    if (tid <= J) {
+        double2 h = kcol(st, b, J)[tid];
         double sc = st.s[(size_t)b * (st.k + 1) + tid] * inv;
         coef[tid] = make_float2((float)(h.x * sc), (float)(h.y * sc));
     }
@@ -169,26 +171,27 @@ __global__ void __launch_bounds__(NTHREADS) arnoldi_update_kernel(KState st, con
     const float finv = (float)inv;
     const float2* wb = w + (size_t)b * N;
     float2* Vb = V + (size_t)b * N;
-    float2* vout = Vb + (size_t)(j + 1) * vstride;
+    float2* vout = Vb + (size_t)(J + 1) * vstride;
     const int ix = blockIdx.x * TILE_X + threadIdx.x;
     const int iz0 = (blockIdx.y * TILE_Y + threadIdx.y) * ROWS;
     float acc = 0.f;
     if (ix < nx) {
+#pragma unroll 2
         for (int r = 0; r < ROWS; ++r) {
             int iz = iz0 + r;
             if (iz >= nz) break;
             size_t p = (size_t)iz * nx + ix;
+            float2 v[J + 1];
+#pragma unroll
+            for (int i = 0; i <= J; ++i) v[i] = Vb[(size_t)i * vstride + p];
             float2 y = wb[p];
             y.x *= finv;
             y.y *= finv;
 #pragma unroll
-            for (int i = 0; i <= KMAX; ++i) {
-                if (i <= j) {
-                    float2 v = Vb[(size_t)i * vstride + p];
-                    float2 c = coef[i];
-                    y.x -= c.x * v.x - c.y * v.y;
-                    y.y -= c.x * v.y + c.y * v.x;
-                }
+            for (int i = 0; i <= J; ++i) {
+                const float2 c = coef[i];
+                y.x -= c.x * v[i].x - c.y * v[i].y;
+                y.y -= c.x * v[i].y + c.y * v[i].x;
             }
             vout[p] = y;
             acc += y.x * y.x + y.y * y.y;
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(NTHREADS) arnoldi_update_kernel(KState st, con
     if (last && tid == 0) {
         double nrm = sqrt(sum_partials(part, ntiles, KMAX + 2, 0).x);   // ||v~_{j+1}||
         double hnext = nrm / inv;                                       // ||w'|| = est ||v~_{j+1}||
-        givens_step(st, b, j, hnext, nrm > 0.0 ? 1.0 / nrm : 0.0, iters_base, max_iter, status);
+        givens_step(st, b, J, hnext, nrm > 0.0 ? 1.0 / nrm : 0.0, iters_base, max_iter, status);
     }
 }
 
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(NTHREADS) kstate_init_kernel(KState st, const 
         }
         return;
     }
-    tally_once(tl);
+    tally_once(tl, blockIdx.x == 0 && blockIdx.y == 0);
     const size_t N = (size_t)nx * nz;
     const float2* vb = v0 + (size_t)b * N;
     const int ix = blockIdx.x * TILE_X + threadIdx.x;
@@ -286,7 +289,7 @@ __global__ void combine_kernel(KState st, float2* __restrict__ out, const float2
     const int b = blockIdx.y;
     if (!mask[b]) return;
     int ns = st.steps[b];
-    tally_once(tl, ns);
+    tally_once(tl, blockIdx.x == 0, ns);
     __shared__ float2 yc[KMAX];
     if (threadIdx.x < KMAX) {
         double2 v = threadIdx.x < ns ? st.y[(size_t)b * st.k + threadIdx.x] : make_double2(0.0, 0.0);
@@ -304,26 +307,31 @@ __global__ void combine_kernel(KState st, float2* __restrict__ out, const float2
     }
 }
 
-// x += sum_{i < steps} y_i Z_i with x in complex128.
+// x += sum_{i < steps} y_i Z_i with x in complex128.  The correction is a
+// combination of complex64 directions and is summed in FP32; only the
+// accumulation into the iterate is FP64 (its rounding is removed by the FP64
+// restart residual).
 __global__ void update_x64_kernel(KState st, double2* __restrict__ x, const float2* __restrict__ Zb, size_t zstride,
                                   size_t n, Tally tl) {
     const int b = blockIdx.y;
     int ns = st.steps[b];
     if (ns == 0) return;
-    tally_once(tl, ns);
-    __shared__ double2 yc[KMAX];
-    if (threadIdx.x < KMAX) yc[threadIdx.x] = threadIdx.x < ns ? st.y[(size_t)b * st.k + threadIdx.x]
-                                                                 : make_double2(0.0, 0.0);
+    tally_once(tl, blockIdx.x == 0, ns);
+    __shared__ float2 yc[KMAX];
+    if (threadIdx.x < KMAX) {
+        double2 v = threadIdx.x < ns ? st.y[(size_t)b * st.k + threadIdx.x] : make_double2(0.0, 0.0);
+        yc[threadIdx.x] = make_float2((float)v.x, (float)v.y);
+    }
     __syncthreads();
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
-        double2 xv = x[(size_t)b * n + p];
-        double ax = 0.0, ay = 0.0;
+        float ax = 0.f, ay = 0.f;
         for (int i = 0; i < ns; ++i) {
             float2 zv = Zb[(size_t)i * zstride + (size_t)b * n + p];
-            ax += yc[i].x * (double)zv.x - yc[i].y * (double)zv.y;
-            ay += yc[i].x * (double)zv.y + yc[i].y * (double)zv.x;
+            ax += yc[i].x * zv.x - yc[i].y * zv.y;
+            ay += yc[i].x * zv.y + yc[i].y * zv.x;
         }
-        x[(size_t)b * n + p] = make_double2(xv.x + ax, xv.y + ay);
+        double2 xv = x[(size_t)b * n + p];
+        x[(size_t)b * n + p] = make_double2(xv.x + (double)ax, xv.y + (double)ay);
     }
 }
 
@@ -337,13 +345,27 @@ static dim3 tiled_grid(int nx, int nz, int nb) {
     return dim3((nx + TILE_X - 1) / TILE_X, (nz + TILE_Y * ROWS - 1) / (TILE_Y * ROWS), nb);
 }
 
+#define HELM_J_CASES(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15)
+
 template <class Op>
 int launch_arnoldi_dots(const helm_ctx* c, const Op& op, KState& st, const float2* z, float2* w,
                         const float2* V, size_t vstride, int j, int nx, int nz, int nb) {
-    LaunchScope scope(c, (std::is_same<Op, OpFine5>::value ? K_DOTS_FINE : K_DOTS_COARSE));
-    arnoldi_dots_kernel<Op><<<tiled_grid(nx, nz, nb), dim3(TILE_X, TILE_Y), 0, c->stream>>>(
-        op, st, z, w, V, vstride, j, nx, nz,
-        tally(c, std::is_same<Op, OpFine5>::value ? K_DOTS_FINE : K_DOTS_COARSE, 8ull * nx * nz * (j + 3)));
+    static_assert(KMAX == 16, "dispatch covers j < 16");
+    LaunchScope scope(c, std::is_same<Op, OpFine5>::value ? K_DOTS_FINE : K_DOTS_COARSE);
+    const Tally tl = tally(c, std::is_same<Op, OpFine5>::value ? K_DOTS_FINE : K_DOTS_COARSE,
+                           8ull * nx * nz * (j + 3));
+    const dim3 grid = tiled_grid(nx, nz, nb), block(TILE_X, TILE_Y);
+    switch (j) {
+#define HELM_DOTS_CASE(J)                                                                                     \
+    case J:                                                                                                   \
+        arnoldi_dots_kernel<Op, J><<<grid, block, 0, c->stream>>>(op, st, z, w, V, vstride, nx, nz, tl);   \
+        break;
+        HELM_J_CASES(HELM_DOTS_CASE)
+#undef HELM_DOTS_CASE
+        default:
+            set_error("Arnoldi step beyond KMAX");
+            return HELM_EINVAL;
+    }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -354,10 +376,22 @@ template int launch_arnoldi_dots<OpC9>(const helm_ctx*, const OpC9&, KState&, co
 
 int launch_arnoldi_update_ex(const helm_ctx* c, KState& st, const float2* w, float2* V, size_t vstride, int j,
                              int nx, int nz, int nb, const int* iters_base, int max_iter, int* status) {
-    LaunchScope scope(c, st.H == c->fine.H ? K_UPDATE_FINE : K_UPDATE_COARSE);
-    arnoldi_update_kernel<<<tiled_grid(nx, nz, nb), dim3(TILE_X, TILE_Y), 0, c->stream>>>(
-        st, w, V, vstride, j, nx, nz, iters_base, max_iter, status,
-        tally(c, st.H == c->fine.H ? K_UPDATE_FINE : K_UPDATE_COARSE, 8ull * nx * nz * (j + 3)));
+    const int kid = st.H == c->fine.H ? K_UPDATE_FINE : K_UPDATE_COARSE;
+    LaunchScope scope(c, kid);
+    const Tally tl = tally(c, kid, 8ull * nx * nz * (j + 3));
+    const dim3 grid = tiled_grid(nx, nz, nb), block(TILE_X, TILE_Y);
+    switch (j) {
+#define HELM_UPD_CASE(J)                                                                                        \
+    case J:                                                                                                     \
+        arnoldi_update_kernel<J><<<grid, block, 0, c->stream>>>(st, w, V, vstride, nx, nz, iters_base, max_iter, \
+                                                                 status, tl);                                  \
+        break;
+        HELM_J_CASES(HELM_UPD_CASE)
+#undef HELM_UPD_CASE
+        default:
+            set_error("Arnoldi step beyond KMAX");
+            return HELM_EINVAL;
+    }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }

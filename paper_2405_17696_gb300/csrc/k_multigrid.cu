@@ -18,7 +18,7 @@ __global__ void jacobi_kernel(Op op, float2* __restrict__ u_out, const float2* _
                               const float2* __restrict__ f, float w, int nx, int nz, const int* mask, Tally tl) {
     const int b = blockIdx.z;
     if (!mask[b]) return;
-    tally_once(tl);
+    tally_once(tl, blockIdx.x == 0 && blockIdx.y == 0);
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iz = blockIdx.y * blockDim.y + threadIdx.y;
     if (ix >= nx || iz >= nz) return;
@@ -43,7 +43,7 @@ __global__ void restrict_residual_kernel(Op op, float2* __restrict__ rc, const f
                                          Tally tl) {
     const int b = blockIdx.z;
     if (!mask[b]) return;
-    tally_once(tl);
+    tally_once(tl, blockIdx.x == 0 && blockIdx.y == 0);
     const int nxc = nx / 2, nzc = nz / 2;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
@@ -76,7 +76,7 @@ __global__ void prolong_add_kernel(float2* __restrict__ u, const float2* __restr
                                    const int* mask, Tally tl) {
     const int b = blockIdx.z;
     if (!mask[b]) return;
-    tally_once(tl);
+    tally_once(tl, blockIdx.x == 0 && blockIdx.y == 0);
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iz = blockIdx.y * blockDim.y + threadIdx.y;
     if (ix >= nx || iz >= nz) return;
@@ -110,7 +110,7 @@ __global__ void copy_masked_kernel(float2* __restrict__ dst, const float2* __res
                                    const int* mask, Tally tl) {
     const int b = blockIdx.y;
     if (!mask[b]) return;
-    tally_once(tl);
+    tally_once(tl, blockIdx.x == 0);
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
         dst[(size_t)b * n + p] = src[(size_t)b * n + p];
 }

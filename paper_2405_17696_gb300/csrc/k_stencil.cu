@@ -17,7 +17,7 @@ __global__ void apply_fine_kernel(OpFine5 op, const float2* __restrict__ x, floa
                                   const int* mask, Tally tl) {
     const int b = blockIdx.z;
     if (!mask[b]) return;
-    tally_once(tl);
+    tally_once(tl, blockIdx.x == 0 && blockIdx.y == 0);
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iz = blockIdx.y * blockDim.y + threadIdx.y;
     if (ix >= op.nx || iz >= op.nz) return;
@@ -32,10 +32,10 @@ __global__ void apply_fine_kernel(OpFine5 op, const float2* __restrict__ x, floa
 __global__ void __launch_bounds__(NTHREADS) residual64_kernel(OpFine5 op, const double2* __restrict__ x,
                                                               const float2* __restrict__ bvec,
                                                               float2* __restrict__ r, int conj_b, int first,
-                                                              OuterState os, Tally tl) {
+                                                              double ax, double az, OuterState os, Tally tl) {
     const int b = blockIdx.z;
     if (!os.outer_active[b]) return;
-    tally_once(tl);
+    tally_once(tl, blockIdx.x == 0 && blockIdx.y == 0);
     const int nx = op.nx, nz = op.nz;
     const size_t N = (size_t)nx * nz;
     const double2* xb = x + (size_t)b * N;
@@ -43,8 +43,8 @@ __global__ void __launch_bounds__(NTHREADS) residual64_kernel(OpFine5 op, const 
     float2* rb = r + (size_t)b * N;
     const int ix = blockIdx.x * TILE_X + threadIdx.x;
     const int iz0 = (blockIdx.y * TILE_Y + threadIdx.y) * ROWS;
-    const double ax = op.ax, az = op.az;
-    const double w2 = op.omega2[op.rhs_freq[b]];
+    const double wf = op.omega[op.rhs_freq[b]];
+    const double w2 = wf * wf;
     double acc_r = 0.0, acc_b = 0.0;
     if (ix < nx) {
         for (int rr = 0; rr < ROWS; ++rr) {
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(NTHREADS) residual64_kernel(OpFine5 op, const 
             double2 xn = iz > 0 ? xb[p - nx] : z0;
             double2 xs = iz < nz - 1 ? xb[p + nx] : z0;
             float2 mg = op.mg[p];
-            double s = w2 * (double)mg.x;
+            double s = w2 * ((double)mg.x * (double)mg.x);
             double ci = -s * (double)mg.y;                 // c = s (1 - i gamma)
             double hx_ = ax * (2.0 * xc.x - xw.x - xe.x) + az * (2.0 * xc.x - xn.x - xs.x) - (s * xc.x - ci * xc.y);
             double hy_ = ax * (2.0 * xc.y - xw.y - xe.y) + az * (2.0 * xc.y - xn.y - xs.y) - (s * xc.y + ci * xc.x);
@@ -155,7 +155,9 @@ int launch_residual64(helm_ctx* c, const double2* x, const float2* b, float2* r,
     OpFine5 op = fine_op(c, 0);
     dim3 grid((c->nx + TILE_X - 1) / TILE_X, (c->nz + TILE_Y * ROWS - 1) / (TILE_Y * ROWS), nb);
     LaunchScope scope(c, K_RESIDUAL64);
-    residual64_kernel<<<grid, dim3(TILE_X, TILE_Y), 0, c->stream>>>(op, x, b, r, conj_b, first, c->outer,
+    residual64_kernel<<<grid, dim3(TILE_X, TILE_Y), 0, c->stream>>>(op, x, b, r, conj_b, first,
+                                                                    1.0 / ((double)c->hx * c->hx),
+                                                                    1.0 / ((double)c->hz * c->hz), c->outer,
                                                                     tally(c, K_RESIDUAL64, 32ull * c->nx * c->nz));
     HELM_CK(cudaGetLastError());
     return HELM_OK;

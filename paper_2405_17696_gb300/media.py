@@ -245,7 +245,7 @@ def workload_batched(n_src: int = 64) -> Workload:
     right and bottom, 64 sources on row 2, f in {3, 4.5, 6} Hz -> 192 RHS."""
     nx, nz = 512, 256
     c = layered_velocity(nx, nz, seed=SEED_MODEL)
-    return Workload("helmholtz_512x256_192rhs", nx, nz, 20.0, [3.0, 4.5, 6.0],
+    return Workload(f"helmholtz_512x256_{3 * n_src}rhs", nx, nz, 20.0, [3.0, 4.5, 6.0],
                     kappa_of(c), abl_gamma(nx, nz, 32), top_row_positions(nx, n_src))
 
 

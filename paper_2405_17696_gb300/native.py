@@ -59,10 +59,14 @@ def _load():
     lib.helm_set_medium.restype = ip
     lib.helm_solve.argtypes = [vp, vp, vp, ip, vp, ctypes.c_double, ip, ctypes.POINTER(helm_stats)]
     lib.helm_solve.restype = ip
+    lib.helm_residual.argtypes = [vp, vp, vp, vp, ip, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.helm_residual.restype = ip
     lib.helm_apply.argtypes = [vp, vp, vp, ip, vp, ip]
     lib.helm_apply.restype = ip
     lib.helm_vcycle.argtypes = [vp, vp, vp, vp, ip, vp]
     lib.helm_vcycle.restype = ip
+    lib.fwi_misfit_grad.argtypes = [vp, vp, ip, vp, ip, vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double), vp]
+    lib.fwi_misfit_grad.restype = ip
     lib.helm_destroy.argtypes = [vp]
     lib.helm_destroy.restype = None
     lib.helm_last_error.argtypes = []
@@ -169,6 +173,15 @@ def helm_solve(ctx, rhs, x, nrhs: int, freq_idx=None, tol: float = 1e-6, flags: 
     return st, iters, rel, stat
 
 
+def helm_residual(ctx, rhs, x, r, nrhs: int, freq_idx=None):
+    """r = rhs - H x (FP64 evaluation, stored complex64); returns the relative residuals."""
+    rel = np.zeros(nrhs, dtype=np.float64)
+    _keep, fptr = _int_array(freq_idx, nrhs)
+    _check(lib.helm_residual(ctx, _ptr(rhs, "complex64"), _ptr(x, "complex128"), _ptr(r, "complex64"), nrhs, fptr,
+                             rel.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "helm_residual")
+    return rel
+
+
 def helm_apply(ctx, x, y, nrhs: int, freq_idx=None, op: int = HELM_OP_H):
     _keep, fptr = _int_array(freq_idx, nrhs)
     _check(lib.helm_apply(ctx, _ptr(x, "complex64"), _ptr(y, "complex64"), nrhs, fptr, op), "helm_apply")
@@ -178,6 +191,16 @@ def helm_vcycle(ctx, f, u0, u, nrhs: int, freq_idx=None):
     _keep, fptr = _int_array(freq_idx, nrhs)
     _check(lib.helm_vcycle(ctx, _ptr(f, "complex64"), _ptr(u0, "complex64"), _ptr(u, "complex64"), nrhs, fptr),
            "helm_vcycle")
+
+
+def fwi_misfit_grad(ctx, src_idx, rcv_idx, d_obs, grad_m, tol: float = 1e-8) -> float:
+    """Returns the misfit; writes dPhi/dm into ``grad_m`` (float32 [nz][nx])."""
+    src = np.ascontiguousarray(np.asarray(src_idx, dtype=np.int32))
+    rcv = np.ascontiguousarray(np.asarray(rcv_idx, dtype=np.int32))
+    phi = ctypes.c_double(0.0)
+    _check(lib.fwi_misfit_grad(ctx, src.ctypes.data, src.size, rcv.ctypes.data, rcv.size, _ptr(d_obs, "complex64"),
+                               tol, ctypes.byref(phi), _ptr(grad_m, "float32")), "fwi_misfit_grad")
+    return phi.value
 
 
 def helm_destroy(ctx):

