@@ -130,6 +130,30 @@ int helm_solve(helm_ctx* ctx, const helm_c64* rhs, helm_c128* x, int nrhs,
 int helm_residual(helm_ctx* ctx, const helm_c64* rhs, const helm_c128* x, helm_c64* r, int nrhs,
                   const int* freq_idx, double* rel_res);
 
+/* helm_residual_noalloc: the same FP64 residual and relative norms as helm_residual,
+ * for callers that cannot allocate device memory - a process whose device memory is
+ * reserved by another allocator (a framework's caching pool that owns the budget), or a
+ * latency-critical loop where an allocation, and the synchronisation it can imply, is not
+ * acceptable.  The paper has no counterpart; this is a deployment convenience.
+ * It allocates nothing and needs no context: every array is a caller-owned DEVICE
+ * pointer (a host pointer is rejected with HELM_EINVAL), the work is issued on `stream`
+ * (a cudaStream_t, NULL = legacy default stream) and the call returns without waiting.
+ *   kappa, gamma : float32 [nz][nx];  omega_rhs : float32 [nrhs], w of each RHS (rad/s)
+ *   rhs : complex64 [nrhs][nz][nx];  x : complex128 [nrhs][nz][nx]
+ *   r (out) : complex64 [nrhs][nz][nx] = rhs - H x;  rel_res (out) : double [nrhs] on device
+ * Scratch: a fixed 1 MiB + 16 KiB file-scope device array that every GPU loading the
+ * library holds until exit; a call needs nrhs <= 4096 and nrhs * ceil(nx/32) *
+ * ceil(nz/64) <= 65536 (1024 right-hand sides of 512 x 256), larger sizes return
+ * HELM_EINVAL with the limits in helm_last_error().  Every call shares that array and
+ * clears its counters on `stream` first, so calls that overlap on the GPU (different
+ * streams, or different host threads) race and must be serialised by the caller.
+ * The first call on each device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture. */
+int helm_residual_noalloc(const float* kappa, const float* gamma, int nx, int nz, float hx, float hz,
+                          const float* omega_rhs, const helm_c64* rhs, const helm_c128* x, helm_c64* r,
+                          double* rel_res, int nrhs, void* stream);
+
 /* y = A x for A = H(m, w_f) (op = HELM_OP_H, Eq. 3.2) or the fine shifted Laplacian
  * P (op = HELM_OP_SL, Eq. 3.12 with the context's shift options); complex64 in/out. */
 int helm_apply(helm_ctx* ctx, const helm_c64* x, helm_c64* y, int nrhs,

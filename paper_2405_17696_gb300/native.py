@@ -61,6 +61,8 @@ def _load():
     lib.helm_solve.restype = ip
     lib.helm_residual.argtypes = [vp, vp, vp, vp, ip, vp, ctypes.POINTER(ctypes.c_double)]
     lib.helm_residual.restype = ip
+    lib.helm_residual_noalloc.argtypes = [vp, vp, ip, ip, fp, fp, vp, vp, vp, vp, vp, ip, vp]
+    lib.helm_residual_noalloc.restype = ip
     lib.helm_apply.argtypes = [vp, vp, vp, ip, vp, ip]
     lib.helm_apply.restype = ip
     lib.helm_vcycle.argtypes = [vp, vp, vp, vp, ip, vp]
@@ -180,6 +182,15 @@ def helm_residual(ctx, rhs, x, r, nrhs: int, freq_idx=None):
     _check(lib.helm_residual(ctx, _ptr(rhs, "complex64"), _ptr(x, "complex128"), _ptr(r, "complex64"), nrhs, fptr,
                              rel.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "helm_residual")
     return rel
+
+
+def helm_residual_noalloc(kappa, gamma, nx: int, nz: int, hx: float, hz: float, omega_rhs, rhs, x, r, rel_res,
+                          nrhs: int, stream=None):
+    """Allocation-free FP64 residual: every array a device tensor; returns without waiting."""
+    _check(lib.helm_residual_noalloc(_ptr(kappa, "float32"), _ptr(gamma, "float32"), nx, nz, hx, hz,
+                                     _ptr(omega_rhs, "float32"), _ptr(rhs, "complex64"), _ptr(x, "complex128"),
+                                     _ptr(r, "complex64"), _ptr(rel_res, "float64"), nrhs, stream),
+           "helm_residual_noalloc")
 
 
 def helm_apply(ctx, x, y, nrhs: int, freq_idx=None, op: int = HELM_OP_H):
