@@ -182,6 +182,49 @@ int fwi_misfit_grad(helm_ctx* ctx, const int* src_idx, int nsrc, const int* rcv_
 
 void helm_destroy(helm_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Encoder-solver network (Sec. 3.4, Eq. 3.13-3.14, 4.1; Fig. 1 caption).
+ * Two U-Nets of `levels` levels with widths[0..levels-1] channels (multiples of
+ * 16, at most 128).  A ResNet layer is relu(x + conv(relu(conv(x)))).  Encoder
+ * (input [c_ref kappa, gamma, w h kappa], c_ref = 1500 m/s): in conv, 2 ResNet
+ * layers per level with a stride-2 conv between levels; on the way up a
+ * nearest-x2 + conv, concatenation with the level's feature, a conv back to
+ * the level's width and one ResNet layer, giving the context z_l of each level.
+ * Solver (input [Re r^, Im r^, gamma], r^ = r / rms(r)): the same shape, with
+ * the context z_l concatenated (and reduced by a conv) at every level of the
+ * way down, and an output conv to 2 channels.  The preconditioner (Eq. 3.14)
+ * is M_VU(r) = V-cycle(e_0, r) with e_0 = h^2 rms(r) (out_0 + i out_1).
+ * Convolutions are 3x3 implicit GEMMs on the tensor cores (tcgen05, BF16
+ * operands, FP32 accumulation in tensor memory).
+ * Parameters are one flat FP32 vector: per layer weights [cout][9][cin] then
+ * bias [cout], layers in the order above (encoder, then solver).
+ * ------------------------------------------------------------------------- */
+int cnn_create(cnn_model** out, int levels, const int* widths);
+void cnn_destroy(cnn_model* net);
+long long cnn_num_params(const cnn_model* net);
+/* Load / read the FP32 parameters (host or device pointer, n = cnn_num_params). */
+int cnn_set_params(cnn_model* net, const float* params, long long n);
+int cnn_get_params(const cnn_model* net, float* params, long long n);
+/* Raw network forward (inputs rounded to BF16): enc_in FP32 [nenc][ny][nx][3],
+ * sol_in FP32 [nsol][ny][nx][3], out FP32 [nsol][ny][nx][2].  nenc is 1 (every
+ * solver image uses the one context) or nsol (image i uses context i).
+ * ny, nx divisible by 2^(levels-1).  Host or device pointers. */
+int cnn_forward(cnn_model* net, const float* enc_in, int nenc, const float* sol_in, int nsol, int ny, int nx,
+                float* out);
+/* The network preconditioner of a context created with a network (Eq. 3.14):
+ * e = V-cycle(e_0 = h^2 rms(r) net(r / rms(r)), r) for with_vcycle = 1, or e = e_0.
+ * r, e : complex64 [nrhs][nz][nx] (host or device); freq_idx as in helm_solve. */
+int cnn_precond_apply(helm_ctx* ctx, const helm_c64* r, helm_c64* e, int nrhs, const int* freq_idx,
+                      int with_vcycle);
+/* One 3x3 convolution layer of the network, FP32 in and out (rounded to BF16 inside,
+ * FP32 accumulation on the tensor cores, output rounded to BF16 then widened):
+ *   y = act(bias + res + conv(concat(x0, x1)))      NHWC, weights [cout][9][c0 + c1]
+ *   x0 [nb][hin][win][c0], x1 [nb or 1 (x1_bcast)][hin][win][c1] or NULL (c1 = 0),
+ *   res [nb][hout][wout][cout] or NULL, mode 0 same / 1 stride-2 down / 2 nearest-x2 up,
+ *   relu 0/1, cout <= 128; y [nb][hout][wout][cout].  Host or device pointers. */
+int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, int nb, int hin, int win,
+                const float* w, const float* bias, int cout, const float* res, int mode, int relu, float* y);
+
 /* Per-kernel-class timing: when enabled, every kernel launch of the context is
  * bracketed by CUDA events on its stream and the main kernels add the
  * algorithmic bytes they move (the minimum DRAM traffic of their definition:

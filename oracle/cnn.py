@@ -126,6 +126,17 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
+def bf16_round(x):
+    """Round to the nearest bfloat16 (ties to even), returned as float64: the
+    8-bit-exponent, 8-bit-significand format, i.e. float32 with the low 16 bits
+    rounded away."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
 # --------------------------------------------------------------------------
 # network description (layer order = parameter order)
 # --------------------------------------------------------------------------
@@ -198,8 +209,9 @@ def flatten_grads(grads, specs):
 # --------------------------------------------------------------------------
 
 class Tape:
-    def __init__(self):
+    def __init__(self, quantize=None):
         self.ops = []
+        self.q = quantize if quantize is not None else (lambda a: a)
 
 
 def _conv(tape, P, specs_by_name, name, x, act: bool):
@@ -207,6 +219,8 @@ def _conv(tape, P, specs_by_name, name, x, act: bool):
     mode = specs_by_name[name][3]
     y = conv_forward(x, w, b, mode)
     out = relu(y) if act else y
+    if name != "sol.out":
+        out = tape.q(out)
     tape.ops.append(("conv", name, x, out, act, mode))
     return out
 
@@ -214,7 +228,7 @@ def _conv(tape, P, specs_by_name, name, x, act: bool):
 def _res(tape, P, sbn, prefix, x):
     h = _conv(tape, P, sbn, prefix + ".a", x, True)
     y = conv_forward(h, *P[prefix + ".b"], "same")
-    out = relu(x + y)
+    out = tape.q(relu(x + y))
     tape.ops.append(("res", prefix, x, h, out))
     return out
 
@@ -275,10 +289,12 @@ def solver_forward(P, specs, x, z, tape=None):
     return out, tape
 
 
-def network_forward(P, specs, enc_in, sol_in):
+def network_forward(P, specs, enc_in, sol_in, quantize=None):
     """Encoder then solver on one tape; the batch of solver inputs shares the
-    context features of one encoder input (Eq. 4.1)."""
-    tape = Tape()
+    context features of one encoder input (Eq. 4.1).  ``quantize`` (e.g.
+    bf16_round) is applied to every stored activation, as a BF16 network
+    stores them; the output layer stays unrounded."""
+    tape = Tape(quantize)
     z, _ = encoder_forward(P, specs, enc_in, tape)
     zb = []
     for zz in z:

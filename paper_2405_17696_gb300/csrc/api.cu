@@ -23,12 +23,13 @@ const char* kernel_name(int id) {
         "stencil_apply", "residual64", "arnoldi_dots_fine", "arnoldi_dots_coarse", "arnoldi_update_fine",
         "arnoldi_update_coarse", "krylov_init", "lsq", "combine", "update_x64", "jacobi_fine", "jacobi_coarse",
         "restrict_fine", "restrict_coarse", "prolong_add", "galerkin", "copy", "restart_check", "coarse_gmres",
-        "misc"};
+        "conv3x3_tc", "cnn_io", "misc"};
     return (id >= 0 && id < K_COUNT) ? names[id] : "?";
 }
 
 LaunchScope::LaunchScope(const helm_ctx* ctx, int kid) : c(const_cast<helm_ctx*>(ctx)), id(kid), slot(0) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!c) return;   // launches outside a context are only counted
     c->prof.launches[id] += 1;
     if (!c->prof.on) return;
     Profiler& p = c->prof;
@@ -45,7 +46,7 @@ LaunchScope::LaunchScope(const helm_ctx* ctx, int kid) : c(const_cast<helm_ctx*>
 }
 
 LaunchScope::~LaunchScope() {
-    if (c->prof.on && slot + 1 < c->prof.pool.size()) cudaEventRecord(c->prof.pool[slot + 1], c->stream);
+    if (c && c->prof.on && slot + 1 < c->prof.pool.size()) cudaEventRecord(c->prof.pool[slot + 1], c->stream);
 }
 
 void prof_flush(helm_ctx* c) {
@@ -271,6 +272,7 @@ int smooth_and_recurse(helm_ctx* c, const Op& op, int l, float2* u_out, const fl
 
 int precondition(helm_ctx* c, float2* z, const float2* v, int nb, const int* mask) {
     if (c->opt.precond == HELM_PC_MG) return vcycle_level(c, 0, z, nullptr, v, nb, mask);
+    if (c->opt.precond == HELM_PC_CNN) return cnn_ctx_precondition(c, z, v, nb, mask, 1);
     set_error("preconditioner kind not available in this context");
     return HELM_EUNSUPPORTED;
 }
@@ -316,6 +318,11 @@ int fgmres_batch(helm_ctx* c, const float2* rhs, double2* x, int nb, double tol,
 }
 
 }  // namespace
+
+int vcycle_apply(helm_ctx* c, float2* u_out, const float2* u0, const float2* f, int nb, const int* mask) {
+    return vcycle_level(c, 0, u_out, u0, f, nb, mask);
+}
+
 }  // namespace helm
 
 using namespace helm;
@@ -345,6 +352,7 @@ void helm_destroy(helm_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
+    cnn_ctx_free(c);
     for (void* p : c->allocations) cudaFree(p);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     delete c;
@@ -376,10 +384,10 @@ int helm_setup(helm_ctx** out, const float* kappa, const float* gamma, int nx, i
         return HELM_EINVAL;
     }
     if (o.precond == HELM_PC_CNN && !net) { set_error("HELM_PC_CNN needs a network"); return HELM_EINVAL; }
-    if (o.precond == HELM_PC_CNN) { set_error("network preconditioner not built in this library"); return HELM_EUNSUPPORTED; }
 
     helm_ctx* c = new helm_ctx();
     c->nx = nx; c->nz = nz; c->nfreq = nfreq; c->hx = hx; c->hz = hz; c->opt = o;
+    c->net = const_cast<cnn_model*>(net);
     c->stream = (cudaStream_t)o.stream;
     c->cap = o.max_rhs;
     const size_t N = (size_t)nx * nz;
@@ -466,6 +474,8 @@ int helm_setup(helm_ctx** out, const float* kappa, const float* gamma, int nx, i
     // Galerkin hierarchy for every frequency
     for (int l = 1; l < L; ++l)
         if ((st = launch_galerkin(c, l))) return fail(st);
+    // network context features for every frequency (Eq. 3.13, once per medium)
+    if (c->net && (st = cnn_ctx_setup(c))) return fail(st);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
         set_error(std::string("setup failed: ") + cudaGetErrorString(cudaGetLastError()));
         return fail(HELM_ECUDA);
@@ -491,6 +501,7 @@ int helm_set_medium(helm_ctx* c, const float* kappa, const float* gamma, const f
         if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); s = HELM_ECUDA; }
     }
     for (int l = 1; !s && l < (int)c->lev.size(); ++l) s = launch_galerkin(c, l);
+    if (!s && c->net) s = cnn_ctx_setup(c);
     if (!s) {
         c->omega.resize(nfreq);
         cudaError_t e = cudaMemcpyAsync(c->omega.data(), so.dev, nfreq * sizeof(float), cudaMemcpyDeviceToHost,

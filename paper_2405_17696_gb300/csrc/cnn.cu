@@ -1,0 +1,733 @@
+// The encoder-solver network (Fig. 1 caption, Sec. 3.4, Eq. 3.13-3.14, 4.1)
+// on the GPU: parameters, forward passes built from the tensor-core 3x3
+// convolution, the packing of the network inputs and the unpacking of its
+// output, and the network preconditioner M_VU used by helm_solve.
+//
+// Architecture (L levels, widths c_0..c_{L-1}; the figure is not available,
+// the caption is read as follows):
+//   ResNet layer R(x) = relu(x + conv_b(relu(conv_a(x))))
+//   encoder: in 3->c0, R, R; per level down c_{l-1}->c_l, R, R;
+//            up path: up c_{l+1}->c_l, concat with e_l, conv 2c_l->c_l, R  => z_l
+//   solver:  in 3->c0, concat z_0, conv 2c0->c0, R; per level down, concat z_l,
+//            conv, R; up path: up, concat s_l, conv, R; out conv c0->2.
+// Every conv except the second of a ResNet layer (whose ReLU follows the skip
+// addition) and the output conv is followed by ReLU.  Parameters are a flat
+// FP32 vector, per layer weights [cout][9][cin] then bias [cout], in the
+// order encoder then solver as listed above.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "helm_internal.cuh"
+#include "conv.cuh"
+#include "reduce.cuh"
+
+namespace helm {
+
+struct Layer {
+    std::string name;
+    int cin, cout, mode;     // logical channels; mode 0 same, 1 down, 2 up
+    int cin_pad, npad;       // padded to multiples of 16 (npad: 16, 32, 64 or 128)
+    int relu;
+    long long off;           // offset of this layer's weights in the flat vector
+    __nv_bfloat16* w = nullptr;   // [npad][9][cin_pad]
+    float* b = nullptr;           // [npad]
+};
+
+}  // namespace helm
+
+struct cnn_model {
+    int levels = 0;
+    std::vector<int> widths;
+    std::vector<helm::Layer> layers;
+    long long nparams = 0;
+    float* master = nullptr;      // flat FP32 parameters (device)
+    int* err = nullptr;           // device error flag of the conv kernels
+    std::vector<void*> allocations;
+};
+
+namespace helm {
+namespace {
+
+int pad16(int c) { return (c + 15) / 16 * 16; }
+int npad_of(int c) { return c <= 16 ? 16 : (c <= 32 ? 32 : (c <= 64 ? 64 : 128)); }
+
+void add_layer(cnn_model* m, const std::string& name, int cin, int cout, int mode, int relu) {
+    Layer L;
+    L.name = name;
+    L.cin = cin;
+    L.cout = cout;
+    L.mode = mode;
+    L.relu = relu;
+    L.cin_pad = pad16(cin);
+    L.npad = npad_of(cout);
+    L.off = m->nparams;
+    m->nparams += (long long)cout * 9 * cin + cout;
+    m->layers.push_back(L);
+}
+
+void build_specs(cnn_model* m) {
+    const int L = m->levels;
+    const std::vector<int>& c = m->widths;
+    auto res = [&](const std::string& p, int ch) {
+        add_layer(m, p + ".a", ch, ch, 0, 1);
+        add_layer(m, p + ".b", ch, ch, 0, 1);   // ReLU after the skip addition
+    };
+    add_layer(m, "enc.in", 3, c[0], 0, 1);
+    res("enc.r0.0", c[0]);
+    res("enc.r0.1", c[0]);
+    for (int l = 1; l < L; ++l) {
+        add_layer(m, "enc.down" + std::to_string(l), c[l - 1], c[l], 1, 1);
+        res("enc.r" + std::to_string(l) + ".0", c[l]);
+        res("enc.r" + std::to_string(l) + ".1", c[l]);
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        add_layer(m, "enc.up" + std::to_string(l), c[l + 1], c[l], 2, 1);
+        add_layer(m, "enc.cat" + std::to_string(l), 2 * c[l], c[l], 0, 1);
+        res("enc.ru" + std::to_string(l), c[l]);
+    }
+    add_layer(m, "sol.in", 3, c[0], 0, 1);
+    add_layer(m, "sol.cat0", 2 * c[0], c[0], 0, 1);
+    res("sol.r0", c[0]);
+    for (int l = 1; l < L; ++l) {
+        add_layer(m, "sol.down" + std::to_string(l), c[l - 1], c[l], 1, 1);
+        add_layer(m, "sol.cat" + std::to_string(l), 2 * c[l], c[l], 0, 1);
+        res("sol.r" + std::to_string(l), c[l]);
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        add_layer(m, "sol.up" + std::to_string(l), c[l + 1], c[l], 2, 1);
+        add_layer(m, "sol.ucat" + std::to_string(l), 2 * c[l], c[l], 0, 1);
+        res("sol.ru" + std::to_string(l), c[l]);
+    }
+    add_layer(m, "sol.out", c[0], 2, 0, 0);
+}
+
+template <class T>
+int malloc_m(cnn_model* m, T** p, size_t n) {
+    if (cudaMalloc((void**)p, (n ? n : 1) * sizeof(T)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        set_error("cudaMalloc failed for network storage");
+        return HELM_ENOMEM;
+    }
+    m->allocations.push_back(*p);
+    return HELM_OK;
+}
+
+// master FP32 [cout][9][cin] + bias -> padded BF16 [npad][9][cin_pad] + FP32 bias [npad]
+__global__ void pack_weights_kernel(const float* __restrict__ master, long long off, int cin, int cout, int cin_pad,
+                                    int npad, __nv_bfloat16* __restrict__ w, float* __restrict__ b) {
+    const int total = npad * 9 * cin_pad;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        int ci = i % cin_pad, t = (i / cin_pad) % 9, co = i / (9 * cin_pad);
+        float v = (co < cout && ci < cin) ? master[off + ((long long)co * 9 + t) * cin + ci] : 0.0f;
+        w[i] = __float2bfloat16_rn(v);
+        if (i < npad) b[i] = i < cout ? master[off + (long long)cout * 9 * cin + i] : 0.0f;
+    }
+}
+
+// FP32 [n][ny][nx][3] -> BF16 [n][ny][nx][16] (channels 3..15 zero)
+__global__ void pack_input3_kernel(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, long long npix) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x) {
+        __nv_bfloat16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < 3 ? in[p * 3 + c] : 0.0f);
+        uint4* o = reinterpret_cast<uint4*>(out + p * 16);
+        o[0] = *reinterpret_cast<uint4*>(&v[0]);
+        o[1] = *reinterpret_cast<uint4*>(&v[8]);
+    }
+}
+
+// FP32 [n][c] -> BF16 [n][cpad] (channels c..cpad-1 zero)
+__global__ void pack_channels_kernel(const float* __restrict__ in, int c, int cpad, __nv_bfloat16* __restrict__ out,
+                                     long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * cpad;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long p = i / cpad;
+        int k = (int)(i - p * cpad);
+        out[i] = __float2bfloat16_rn(k < c ? in[p * c + k] : 0.0f);
+    }
+}
+
+// BF16 [n][cpad] -> FP32 [n][c]
+__global__ void unpack_channels_kernel(const __nv_bfloat16* __restrict__ in, int cpad, int c, float* __restrict__ out,
+                                       long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * c;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long p = i / c;
+        int k = (int)(i - p * c);
+        out[i] = __bfloat162float(in[p * cpad + k]);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// forward passes
+// ---------------------------------------------------------------------------
+struct NetBuffers {
+    // encoder outputs z_l: [nenc][ny_l][nx_l][c_l]
+    std::vector<__nv_bfloat16*> z;
+    int nenc = 0;
+};
+
+class Runner {
+   public:
+    Runner(cnn_model* m, const helm_ctx* ctx, cudaStream_t st, std::vector<void*>* arena = nullptr,
+           std::vector<size_t>* arena_bytes = nullptr)
+        : m_(m), ctx_(ctx), st_(st), arena_(arena), arena_bytes_(arena_bytes) {}
+    ~Runner() {
+        for (void* p : tmp_) cudaFree(p);
+    }
+    __nv_bfloat16* alloc(size_t n) {
+        if (arena_) {
+            // the k-th buffer of a pass is reused by the k-th call of every later pass
+            const size_t k = next_++;
+            const size_t bytes = n * sizeof(__nv_bfloat16);
+            if (k >= arena_->size()) {
+                arena_->push_back(nullptr);
+                arena_bytes_->push_back(0);
+            }
+            if ((*arena_bytes_)[k] < bytes) {
+                if ((*arena_)[k]) cudaFree((*arena_)[k]);
+                (*arena_)[k] = nullptr;
+                (*arena_bytes_)[k] = 0;
+                if (cudaMalloc(&(*arena_)[k], bytes) != cudaSuccess) {
+                    (void)cudaGetLastError();
+                    (*arena_)[k] = nullptr;
+                    ok_ = false;
+                    return nullptr;
+                }
+                (*arena_bytes_)[k] = bytes;
+            }
+            return (__nv_bfloat16*)(*arena_)[k];
+        }
+        void* p = nullptr;
+        if (cudaMalloc(&p, n * sizeof(__nv_bfloat16)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            ok_ = false;
+            return nullptr;
+        }
+        tmp_.push_back(p);
+        return (__nv_bfloat16*)p;
+    }
+    bool ok() const { return ok_; }
+    const Layer& L(const std::string& name) const {
+        for (const Layer& l : m_->layers)
+            if (l.name == name) return l;
+        return m_->layers[0];
+    }
+    // y = act(conv(cat(x0, x1)) [+ res]) ; returns y (allocated here) and its spatial size
+    __nv_bfloat16* conv(const std::string& name, const __nv_bfloat16* x0, int c0, const __nv_bfloat16* x1, int c1,
+                        int x1_bcast, int nb, int hin, int win, const __nv_bfloat16* res, int* hout, int* wout,
+                        void* y_fp32 = nullptr) {
+        if (!ok_) return nullptr;
+        const Layer& l = L(name);
+        int ho = hin, wo = win;
+        if (l.mode == 1) { ho = hin / 2; wo = win / 2; }
+        if (l.mode == 2) { ho = hin * 2; wo = win * 2; }
+        __nv_bfloat16* y = nullptr;
+        if (!y_fp32) {
+            y = alloc((size_t)nb * ho * wo * l.npad);
+            if (!y) return nullptr;
+        }
+        ConvArgs a;
+        a.x0 = x0; a.c0 = c0; a.x1 = x1; a.c1 = c1; a.x1_bcast = x1_bcast; a.x1_map = x1_bcast == 2 ? zmap_ : nullptr;
+        a.nb = nb; a.hin = hin; a.win = win; a.hout = ho; a.wout = wo; a.mode = l.mode;
+        a.w = l.w; a.bias = l.b; a.res = res; a.y = y_fp32 ? y_fp32 : (void*)y;
+        a.npad = l.npad; a.cstore = l.cout; a.relu = l.relu; a.out_fp32 = y_fp32 ? 1 : 0; a.err = m_->err;
+        int s;
+        {
+            LaunchScope scope(ctx_, K_CONV);
+            s = launch_conv3x3(a, st_);
+        }
+        if (s != HELM_OK) { ok_ = false; return nullptr; }
+        if (hout) *hout = ho;
+        if (wout) *wout = wo;
+        return y;
+    }
+    __nv_bfloat16* res(const std::string& p, const __nv_bfloat16* x, int ch, int nb, int h, int w) {
+        __nv_bfloat16* t = conv(p + ".a", x, ch, nullptr, 0, 0, nb, h, w, nullptr, nullptr, nullptr);
+        return conv(p + ".b", t, ch, nullptr, 0, 0, nb, h, w, x, nullptr, nullptr);
+    }
+
+    // z_l for nenc encoder images (input BF16 [nenc][ny][nx][16]); the z buffers are
+    // owned by the caller-provided vector of pointers (allocated here, not freed by ~Runner)
+    bool encoder(const __nv_bfloat16* xin, int nenc, int ny, int nx, std::vector<__nv_bfloat16*>& z) {
+        const int Lv = m_->levels;
+        const std::vector<int>& c = m_->widths;
+        std::vector<__nv_bfloat16*> e(Lv);
+        std::vector<int> hy(Lv), wx(Lv);
+        int h = ny, w = nx;
+        __nv_bfloat16* t = conv("enc.in", xin, 16, nullptr, 0, 0, nenc, h, w, nullptr, nullptr, nullptr);
+        t = res("enc.r0.0", t, c[0], nenc, h, w);
+        t = res("enc.r0.1", t, c[0], nenc, h, w);
+        e[0] = t; hy[0] = h; wx[0] = w;
+        for (int l = 1; l < Lv; ++l) {
+            t = conv("enc.down" + std::to_string(l), t, c[l - 1], nullptr, 0, 0, nenc, h, w, nullptr, &h, &w);
+            t = res("enc.r" + std::to_string(l) + ".0", t, c[l], nenc, h, w);
+            t = res("enc.r" + std::to_string(l) + ".1", t, c[l], nenc, h, w);
+            e[l] = t; hy[l] = h; wx[l] = w;
+        }
+        std::vector<__nv_bfloat16*> zz(Lv);
+        zz[Lv - 1] = e[Lv - 1];
+        for (int l = Lv - 2; l >= 0; --l) {
+            __nv_bfloat16* u = conv("enc.up" + std::to_string(l), t, c[l + 1], nullptr, 0, 0, nenc, h, w, nullptr, &h, &w);
+            t = conv("enc.cat" + std::to_string(l), u, c[l], e[l], c[l], 0, nenc, h, w, nullptr, nullptr, nullptr);
+            t = res("enc.ru" + std::to_string(l), t, c[l], nenc, h, w);
+            zz[l] = t;
+        }
+        if (!ok_) return false;
+        // hand the context features over to the caller (they outlive this runner)
+        z = zz;
+        for (__nv_bfloat16* p : zz) {
+            for (size_t i = 0; i < tmp_.size(); ++i)
+                if (tmp_[i] == p) { tmp_.erase(tmp_.begin() + i); break; }
+        }
+        return true;
+    }
+
+    // out (FP32 [nb][ny][nx][2]) for solver inputs xin BF16 [nb][ny][nx][16]; the
+    // context image of solver image b is z[.][zmap ? zmap[b] : 0] -- handled by the
+    // caller passing per-image contexts through `zsel` (one z pointer set per call)
+    bool solver(const __nv_bfloat16* xin, int nb, int ny, int nx, const std::vector<__nv_bfloat16*>& z, int z_bcast,
+                float* out) {
+        const int Lv = m_->levels;
+        const std::vector<int>& c = m_->widths;
+        std::vector<__nv_bfloat16*> s(Lv);
+        int h = ny, w = nx;
+        __nv_bfloat16* t = conv("sol.in", xin, 16, nullptr, 0, 0, nb, h, w, nullptr, nullptr, nullptr);
+        t = conv("sol.cat0", t, c[0], z[0], c[0], z_bcast, nb, h, w, nullptr, nullptr, nullptr);
+        t = res("sol.r0", t, c[0], nb, h, w);
+        s[0] = t;
+        for (int l = 1; l < Lv; ++l) {
+            t = conv("sol.down" + std::to_string(l), t, c[l - 1], nullptr, 0, 0, nb, h, w, nullptr, &h, &w);
+            t = conv("sol.cat" + std::to_string(l), t, c[l], z[l], c[l], z_bcast, nb, h, w, nullptr, nullptr, nullptr);
+            t = res("sol.r" + std::to_string(l), t, c[l], nb, h, w);
+            s[l] = t;
+        }
+        for (int l = Lv - 2; l >= 0; --l) {
+            __nv_bfloat16* u = conv("sol.up" + std::to_string(l), t, c[l + 1], nullptr, 0, 0, nb, h, w, nullptr, &h, &w);
+            t = conv("sol.ucat" + std::to_string(l), u, c[l], s[l], c[l], 0, nb, h, w, nullptr, nullptr, nullptr);
+            t = res("sol.ru" + std::to_string(l), t, c[l], nb, h, w);
+        }
+        conv("sol.out", t, c[0], nullptr, 0, 0, nb, h, w, nullptr, nullptr, nullptr, out);
+        return ok_;
+    }
+
+    void set_zmap(const int* zmap) { zmap_ = zmap; }
+
+   private:
+    const int* zmap_ = nullptr;   // per-image context index used when x1_bcast == 2
+    std::vector<void*>* arena_;
+    std::vector<size_t>* arena_bytes_;
+    size_t next_ = 0;
+    cnn_model* m_;
+    const helm_ctx* ctx_;
+    cudaStream_t st_;
+    std::vector<void*> tmp_;
+    bool ok_ = true;
+};
+
+int check_conv_error(cnn_model* m, cudaStream_t st) {
+    int h = 0;
+    HELM_CK(cudaMemcpyAsync(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HELM_CK(cudaStreamSynchronize(st));
+    if (h) {
+        set_error("a tensor-core convolution wait expired");
+        cudaMemsetAsync(m->err, 0, sizeof(int), st);
+        return HELM_ETIMEOUT;
+    }
+    return HELM_OK;
+}
+
+namespace {
+
+// encoder input of every frequency: BF16 [nfreq][nz][nx][16] = [c_ref kappa, gamma, w h kappa, 0...]
+__global__ void encoder_input_kernel(const float2* __restrict__ mg, const float* __restrict__ omega, float h,
+                                     int nfreq, long long n, __nv_bfloat16* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nfreq;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(i / n);
+        const long long p = i - (long long)f * n;
+        const float2 kg = mg[p];
+        __nv_bfloat16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(0.0f);
+        v[0] = __float2bfloat16_rn(1500.0f * kg.x);
+        v[1] = __float2bfloat16_rn(kg.y);
+        v[2] = __float2bfloat16_rn(omega[f] * h * kg.x);
+        uint4* o = reinterpret_cast<uint4*>(out + i * 16);
+        o[0] = *reinterpret_cast<uint4*>(&v[0]);
+        o[1] = *reinterpret_cast<uint4*>(&v[8]);
+    }
+}
+
+// rms(r) per RHS (one block per RHS, FP64 sum)
+__global__ void rms_kernel(const float2* __restrict__ r, long long n, float* __restrict__ rms, const int* mask) {
+    const int b = blockIdx.x;
+    if (mask && !mask[b]) { if (threadIdx.x == 0) rms[b] = 0.0f; return; }
+    double acc = 0.0;
+    for (long long p = threadIdx.x; p < n; p += blockDim.x) {
+        float2 v = r[(long long)b * n + p];
+        acc += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    __shared__ double sm[32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[w];
+        rms[b] = (float)sqrt(t / (double)n);
+    }
+}
+
+// solver input BF16 [nb][n][16] = [Re r / rms, Im r / rms, gamma, 0...]
+__global__ void solver_input_kernel(const float2* __restrict__ r, const float* __restrict__ rms,
+                                    const float2* __restrict__ mg, long long n, int nb,
+                                    __nv_bfloat16* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nb;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(i / n);
+        const long long p = i - (long long)b * n;
+        const float s = rms[b] > 0.0f ? 1.0f / rms[b] : 0.0f;
+        const float2 v = r[i];
+        __nv_bfloat16 q[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) q[c] = __float2bfloat16_rn(0.0f);
+        q[0] = __float2bfloat16_rn(v.x * s);
+        q[1] = __float2bfloat16_rn(v.y * s);
+        q[2] = __float2bfloat16_rn(mg[p].y);
+        uint4* o = reinterpret_cast<uint4*>(out + i * 16);
+        o[0] = *reinterpret_cast<uint4*>(&q[0]);
+        o[1] = *reinterpret_cast<uint4*>(&q[8]);
+    }
+}
+
+// e0 = h^2 rms (out_0 + i out_1)
+__global__ void solver_output_kernel(const float* __restrict__ out, const float* __restrict__ rms, float h2,
+                                     long long n, int nb, float2* __restrict__ e0) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nb;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(i / n);
+        const float s = h2 * rms[b];
+        e0[i] = make_float2(s * out[2 * i], s * out[2 * i + 1]);
+    }
+}
+
+}  // namespace
+
+void cnn_ctx_free(helm_ctx* c) {
+    for (void* p : c->cnn_z) cudaFree(p);
+    c->cnn_z.clear();
+    for (void* p : c->cnn_arena) cudaFree(p);
+    c->cnn_arena.clear();
+    c->cnn_arena_bytes.clear();
+    cudaFree(c->cnn_in);
+    cudaFree(c->cnn_out);
+    cudaFree(c->cnn_e0);
+    cudaFree(c->cnn_rms);
+    c->cnn_in = nullptr;
+    c->cnn_out = nullptr;
+    c->cnn_e0 = nullptr;
+    c->cnn_rms = nullptr;
+}
+
+int cnn_ctx_setup(helm_ctx* c) {
+    cnn_model* m = c->net;
+    const int div = 1 << (m->levels - 1);
+    if (c->nx % div || c->nz % div) {
+        set_error("grid not divisible by 2^(network levels - 1)");
+        return HELM_EINVAL;
+    }
+    const long long n = (long long)c->nx * c->nz;
+    if (!c->cnn_in) {
+        HELM_CK(cudaMalloc(&c->cnn_in, (size_t)std::max<long long>(c->cap, c->nfreq) * n * 16 * sizeof(__nv_bfloat16)));
+        HELM_CK(cudaMalloc(&c->cnn_out, (size_t)c->cap * n * 2 * sizeof(float)));
+        HELM_CK(cudaMalloc(&c->cnn_e0, (size_t)c->cap * n * sizeof(float2)));
+        HELM_CK(cudaMalloc(&c->cnn_rms, (size_t)c->cap * sizeof(float)));
+    }
+    for (void* p : c->cnn_z) cudaFree(p);
+    c->cnn_z.clear();
+    {
+        LaunchScope scope(c, K_CNN_IO);
+        encoder_input_kernel<<<1184, 256, 0, c->stream>>>(c->mg, c->omega_d, c->hx, c->nfreq, n,
+                                                          (__nv_bfloat16*)c->cnn_in);
+        HELM_CK(cudaGetLastError());
+    }
+    Runner r(m, c, c->stream);
+    std::vector<__nv_bfloat16*> z;
+    if (!r.encoder((const __nv_bfloat16*)c->cnn_in, c->nfreq, c->nz, c->nx, z)) {
+        if (std::string(helm_last_error()).empty()) set_error("encoder pass failed");
+        return HELM_ECUDA;
+    }
+    for (__nv_bfloat16* p : z) c->cnn_z.push_back(p);
+    HELM_CK(cudaStreamSynchronize(c->stream));
+    return check_conv_error(m, c->stream);
+}
+
+int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const int* mask, int with_vcycle) {
+    cnn_model* m = c->net;
+    const long long n = (long long)c->nx * c->nz;
+    {
+        LaunchScope scope(c, K_CNN_IO);
+        rms_kernel<<<nb, 1024, 0, c->stream>>>(v, n, c->cnn_rms, mask);
+        HELM_CK(cudaGetLastError());
+    }
+    {
+        LaunchScope scope(c, K_CNN_IO);
+        solver_input_kernel<<<1184, 256, 0, c->stream>>>(v, c->cnn_rms, c->mg, n, nb, (__nv_bfloat16*)c->cnn_in);
+        HELM_CK(cudaGetLastError());
+    }
+    Runner r(m, c, c->stream, &c->cnn_arena, &c->cnn_arena_bytes);
+    r.set_zmap(c->rhs_freq);
+    std::vector<__nv_bfloat16*> zz;
+    for (void* p : c->cnn_z) zz.push_back((__nv_bfloat16*)p);
+    if (!r.solver((const __nv_bfloat16*)c->cnn_in, nb, c->nz, c->nx, zz, 2, c->cnn_out)) {
+        if (std::string(helm_last_error()).empty()) set_error("solver pass failed");
+        return HELM_ECUDA;
+    }
+    {
+        LaunchScope scope(c, K_CNN_IO);
+        float2* e0 = with_vcycle ? c->cnn_e0 : z;
+        solver_output_kernel<<<1184, 256, 0, c->stream>>>(c->cnn_out, c->cnn_rms, c->hx * c->hz, n, nb, e0);
+        HELM_CK(cudaGetLastError());
+    }
+    if (!with_vcycle) return HELM_OK;
+    return vcycle_apply(c, z, c->cnn_e0, v, nb, mask);   // Eq. 3.14: V-cycle from e_0 on r
+}
+
+}  // namespace helm
+
+using namespace helm;
+
+extern "C" {
+
+int cnn_precond_apply(helm_ctx* c, const helm_c64* r, helm_c64* e, int nrhs, const int* freq_idx, int with_vcycle) {
+    set_error("");
+    if (!c || !r || !e || nrhs < 0 || !c->net) {
+        set_error("cnn_precond_apply: invalid argument or no network in the context");
+        return HELM_EINVAL;
+    }
+    const size_t N = (size_t)c->nx * c->nz;
+    for (int b0 = 0; b0 < nrhs; b0 += c->cap) {
+        const int nb = nrhs - b0 < c->cap ? nrhs - b0 : c->cap;
+        std::vector<int> f(nb, 0);
+        if (freq_idx)
+            for (int i = 0; i < nb; ++i) {
+                if (freq_idx[b0 + i] < 0 || freq_idx[b0 + i] >= c->nfreq) { set_error("freq_idx outside [0, nfreq)"); return HELM_EINVAL; }
+                f[i] = freq_idx[b0 + i];
+            }
+        HELM_CK(cudaMemcpyAsync(c->rhs_freq, f.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        float2 *dr = nullptr, *de = nullptr;
+        HELM_CK(cudaMalloc(&dr, nb * N * sizeof(float2)));
+        HELM_CK(cudaMalloc(&de, nb * N * sizeof(float2)));
+        HELM_CK(cudaMemcpyAsync(dr, r + b0 * N, nb * N * sizeof(float2), cudaMemcpyDefault, c->stream));
+        int s = cnn_ctx_precondition(c, de, dr, nb, c->ones, with_vcycle);
+        if (!s) {
+            cudaError_t ce = cudaMemcpyAsync(e + b0 * N, de, nb * N * sizeof(float2), cudaMemcpyDefault, c->stream);
+            if (ce != cudaSuccess) { set_error(cudaGetErrorString(ce)); s = HELM_ECUDA; }
+        }
+        cudaError_t ce = cudaStreamSynchronize(c->stream);
+        cudaFree(dr);
+        cudaFree(de);
+        if (s) return s;
+        if (ce != cudaSuccess) { set_error(cudaGetErrorString(ce)); return HELM_ECUDA; }
+        HELM_TRY(check_conv_error(c->net, c->stream));
+    }
+    return HELM_OK;
+}
+
+
+int cnn_create(cnn_model** out, int levels, const int* widths) {
+    set_error("");
+    if (!out || levels < 2 || levels > 6 || !widths) { set_error("cnn_create: invalid argument"); return HELM_EINVAL; }
+    for (int l = 0; l < levels; ++l)
+        if (widths[l] < 16 || widths[l] > 128 || widths[l] % 16) {
+            set_error("cnn_create: widths must be multiples of 16 in [16, 128]");
+            return HELM_EINVAL;
+        }
+    cnn_model* m = new cnn_model();
+    m->levels = levels;
+    m->widths.assign(widths, widths + levels);
+    build_specs(m);
+    int s = malloc_m(m, &m->master, (size_t)m->nparams);
+    if (!s) s = malloc_m(m, &m->err, 1);
+    for (Layer& l : m->layers) {
+        if (s) break;
+        s = malloc_m(m, &l.w, (size_t)l.npad * 9 * l.cin_pad);
+        if (!s) s = malloc_m(m, &l.b, (size_t)l.npad);
+    }
+    if (s) { cnn_destroy(m); return s; }
+    cudaMemset(m->master, 0, m->nparams * sizeof(float));
+    cudaMemset(m->err, 0, sizeof(int));
+    for (Layer& l : m->layers) {
+        cudaMemset(l.w, 0, (size_t)l.npad * 9 * l.cin_pad * sizeof(__nv_bfloat16));
+        cudaMemset(l.b, 0, (size_t)l.npad * sizeof(float));
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) { set_error("cnn_create: device error"); cnn_destroy(m); return HELM_ECUDA; }
+    *out = m;
+    return HELM_OK;
+}
+
+void cnn_destroy(cnn_model* m) {
+    if (!m) return;
+    cudaDeviceSynchronize();
+    for (void* p : m->allocations) cudaFree(p);
+    delete m;
+}
+
+long long cnn_num_params(const cnn_model* m) { return m ? m->nparams : -1; }
+
+int cnn_set_params(cnn_model* m, const float* params, long long n) {
+    set_error("");
+    if (!m || !params || n != m->nparams) { set_error("cnn_set_params: size differs from cnn_num_params"); return HELM_EINVAL; }
+    HELM_CK(cudaMemcpy(m->master, params, n * sizeof(float), cudaMemcpyDefault));
+    for (const Layer& l : m->layers) {
+        pack_weights_kernel<<<64, 256>>>(m->master, l.off, l.cin, l.cout, l.cin_pad, l.npad, l.w, l.b);
+        HELM_CK(cudaGetLastError());
+    }
+    HELM_CK(cudaDeviceSynchronize());
+    return HELM_OK;
+}
+
+int cnn_get_params(const cnn_model* m, float* params, long long n) {
+    set_error("");
+    if (!m || !params || n != m->nparams) { set_error("cnn_get_params: size differs from cnn_num_params"); return HELM_EINVAL; }
+    HELM_CK(cudaMemcpy(params, m->master, n * sizeof(float), cudaMemcpyDefault));
+    return HELM_OK;
+}
+
+// Raw network forward for parity tests and offline use: FP32 inputs are
+// rounded to BF16, the network runs on the tensor cores, output FP32.
+//   enc_in : [nenc][ny][nx][3]   sol_in : [nsol][ny][nx][3]   out : [nsol][ny][nx][2]
+//   the solver images share encoder image 0 when nenc == 1, else image i uses encoder image i.
+int cnn_forward(cnn_model* m, const float* enc_in, int nenc, const float* sol_in, int nsol, int ny, int nx,
+                float* out) {
+    set_error("");
+    if (!m || !enc_in || !sol_in || !out || nenc < 1 || nsol < 1 || (nenc != 1 && nenc != nsol)) {
+        set_error("cnn_forward: invalid argument");
+        return HELM_EINVAL;
+    }
+    const int div = 1 << (m->levels - 1);
+    if (ny % div || nx % div) { set_error("cnn_forward: ny, nx must be divisible by 2^(levels-1)"); return HELM_EINVAL; }
+    cudaStream_t st = nullptr;
+    const size_t npix = (size_t)ny * nx;
+    float *ein = nullptr, *sin_ = nullptr, *o = nullptr;
+    __nv_bfloat16 *xe = nullptr, *xs = nullptr;
+    int s = HELM_OK;
+    auto ck = [&](cudaError_t e) { if (e != cudaSuccess && s == HELM_OK) { set_error(cudaGetErrorString(e)); s = HELM_ECUDA; } };
+    ck(cudaMalloc(&ein, nenc * npix * 3 * sizeof(float)));
+    ck(cudaMalloc(&sin_, nsol * npix * 3 * sizeof(float)));
+    ck(cudaMalloc(&o, nsol * npix * 2 * sizeof(float)));
+    ck(cudaMalloc(&xe, nenc * npix * 16 * sizeof(__nv_bfloat16)));
+    ck(cudaMalloc(&xs, nsol * npix * 16 * sizeof(__nv_bfloat16)));
+    if (!s) {
+        ck(cudaMemcpy(ein, enc_in, nenc * npix * 3 * sizeof(float), cudaMemcpyDefault));
+        ck(cudaMemcpy(sin_, sol_in, nsol * npix * 3 * sizeof(float), cudaMemcpyDefault));
+        pack_input3_kernel<<<256, 256>>>(ein, xe, (long long)nenc * npix);
+        pack_input3_kernel<<<256, 256>>>(sin_, xs, (long long)nsol * npix);
+        ck(cudaGetLastError());
+    }
+    if (!s) {
+        Runner r(m, nullptr, st);
+        std::vector<__nv_bfloat16*> z;
+        if (!r.encoder(xe, nenc, ny, nx, z)) s = HELM_ECUDA;
+        if (!s && !r.solver(xs, nsol, ny, nx, z, nenc == 1 ? 1 : 0, o)) s = HELM_ECUDA;
+        ck(cudaDeviceSynchronize());
+        for (__nv_bfloat16* p : z) cudaFree(p);
+        if (!s) s = check_conv_error(m, st);
+    }
+    if (!s) ck(cudaMemcpy(out, o, nsol * npix * 2 * sizeof(float), cudaMemcpyDefault));
+    cudaFree(ein); cudaFree(sin_); cudaFree(o); cudaFree(xe); cudaFree(xs);
+    return s;
+}
+
+// One 3x3 convolution layer as the network uses it: FP32 in/out (host or device),
+// BF16 operands and FP32 accumulation on the tensor cores.
+int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, int nb, int hin, int win,
+                const float* w, const float* bias, int cout, const float* res, int mode, int relu, float* y) {
+    set_error("");
+    if (!x0 || !w || !bias || !y || c0 < 1 || c1 < 0 || (c1 > 0 && !x1) || nb < 1 || hin < 1 || win < 1 ||
+        cout < 1 || cout > 128 || mode < 0 || mode > 2) {
+        set_error("cnn_conv3x3: invalid argument");
+        return HELM_EINVAL;
+    }
+    const int cp0 = pad16(c0), cp1 = c1 ? pad16(c1) : 0, cin = c0 + c1, cinp = cp0 + cp1, npad = npad_of(cout);
+    const int hout = mode == 1 ? hin / 2 : (mode == 2 ? 2 * hin : hin);
+    const int wout = mode == 1 ? win / 2 : (mode == 2 ? 2 * win : win);
+    const long long nin = (long long)nb * hin * win, nin1 = (long long)(x1_bcast ? 1 : nb) * hin * win;
+    const long long nout = (long long)nb * hout * wout;
+    float *fx0 = nullptr, *fx1 = nullptr, *fw = nullptr, *fb = nullptr, *fr = nullptr, *fy = nullptr, *bp = nullptr;
+    __nv_bfloat16 *bx0 = nullptr, *bx1 = nullptr, *bw = nullptr, *br = nullptr, *by = nullptr;
+    int* err = nullptr;
+    int s = HELM_OK;
+    auto ck = [&](cudaError_t e) { if (e != cudaSuccess && s == HELM_OK) { set_error(cudaGetErrorString(e)); s = HELM_ECUDA; } };
+    ck(cudaMalloc(&fx0, nin * c0 * sizeof(float)));
+    ck(cudaMalloc(&bx0, nin * cp0 * sizeof(__nv_bfloat16)));
+    if (c1) { ck(cudaMalloc(&fx1, nin1 * c1 * sizeof(float))); ck(cudaMalloc(&bx1, nin1 * cp1 * sizeof(__nv_bfloat16))); }
+    ck(cudaMalloc(&fw, (size_t)cout * 9 * cin * sizeof(float) + cout * sizeof(float)));
+    ck(cudaMalloc(&bw, (size_t)npad * 9 * cinp * sizeof(__nv_bfloat16)));
+    ck(cudaMalloc(&bp, npad * sizeof(float)));
+    ck(cudaMalloc(&fy, nout * cout * sizeof(float)));
+    ck(cudaMalloc(&by, nout * npad * sizeof(__nv_bfloat16)));
+    ck(cudaMalloc(&err, sizeof(int)));
+    if (res) { ck(cudaMalloc(&fr, nout * cout * sizeof(float))); ck(cudaMalloc(&br, nout * npad * sizeof(__nv_bfloat16))); }
+    if (!s) {
+        ck(cudaMemset(err, 0, sizeof(int)));
+        ck(cudaMemcpy(fx0, x0, nin * c0 * sizeof(float), cudaMemcpyDefault));
+        if (c1) ck(cudaMemcpy(fx1, x1, nin1 * c1 * sizeof(float), cudaMemcpyDefault));
+        ck(cudaMemcpy(fw, w, (size_t)cout * 9 * cin * sizeof(float), cudaMemcpyDefault));
+        ck(cudaMemcpy(fw + (size_t)cout * 9 * cin, bias, cout * sizeof(float), cudaMemcpyDefault));
+        if (res) ck(cudaMemcpy(fr, res, nout * cout * sizeof(float), cudaMemcpyDefault));
+    }
+    if (!s) {
+        pack_channels_kernel<<<256, 256>>>(fx0, c0, cp0, bx0, nin);
+        if (c1) pack_channels_kernel<<<256, 256>>>(fx1, c1, cp1, bx1, nin1);
+        if (res) pack_channels_kernel<<<256, 256>>>(fr, cout, npad, br, nout);
+        // weights: logical [cout][9][c0 + c1] -> padded [npad][9][cp0 + cp1] (concat parts padded separately)
+        std::vector<float> hw((size_t)cout * 9 * cin + cout);
+        ck(cudaMemcpy(hw.data(), fw, hw.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        std::vector<__nv_bfloat16> hbw((size_t)npad * 9 * cinp, __float2bfloat16_rn(0.0f));
+        std::vector<float> hb(npad, 0.0f);
+        for (int co = 0; co < cout; ++co) {
+            for (int t = 0; t < 9; ++t)
+                for (int ci = 0; ci < cin; ++ci) {
+                    int cpi = ci < c0 ? ci : cp0 + (ci - c0);
+                    hbw[((size_t)co * 9 + t) * cinp + cpi] = __float2bfloat16_rn(hw[((size_t)co * 9 + t) * cin + ci]);
+                }
+            hb[co] = hw[(size_t)cout * 9 * cin + co];
+        }
+        ck(cudaMemcpy(bw, hbw.data(), hbw.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+        ck(cudaMemcpy(bp, hb.data(), hb.size() * sizeof(float), cudaMemcpyHostToDevice));
+        ck(cudaGetLastError());
+    }
+    if (!s) {
+        ConvArgs a;
+        a.x0 = bx0; a.c0 = cp0; a.x1 = bx1; a.c1 = cp1; a.x1_bcast = x1_bcast; a.x1_map = nullptr;
+        a.nb = nb; a.hin = hin; a.win = win; a.hout = hout; a.wout = wout; a.mode = mode;
+        a.w = bw; a.bias = bp; a.res = br; a.y = by; a.npad = npad; a.cstore = cout; a.relu = relu; a.out_fp32 = 0;
+        a.err = err;
+        {
+            LaunchScope scope(nullptr, K_CONV);
+            s = launch_conv3x3(a, nullptr);
+        }
+        if (!s) {
+            unpack_channels_kernel<<<256, 256>>>(by, npad, cout, fy, nout);
+            ck(cudaGetLastError());
+            ck(cudaDeviceSynchronize());
+            int herr = 0;
+            ck(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+            if (!s && herr) { set_error("cnn_conv3x3: a tensor-core wait expired"); s = HELM_ETIMEOUT; }
+        }
+        if (!s) ck(cudaMemcpy(y, fy, nout * cout * sizeof(float), cudaMemcpyDefault));
+    }
+    cudaFree(fx0); cudaFree(fx1); cudaFree(fw); cudaFree(fb); cudaFree(fr); cudaFree(fy); cudaFree(bp);
+    cudaFree(bx0); cudaFree(bx1); cudaFree(bw); cudaFree(br); cudaFree(by); cudaFree(err);
+    return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,32 @@
+// Arguments of the tensor-core 3x3 convolution (k_conv.cu), shared with the
+// network driver (cnn.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace helm {
+
+struct ConvArgs {
+    const __nv_bfloat16* x0;   // [nb][hin][win][c0]
+    int c0;
+    const __nv_bfloat16* x1;   // second input concatenated after x0's channels, or nullptr
+    int c1;
+    int x1_bcast;              // 1: x1 has one image shared by the whole batch
+    const int* x1_map;         // or: image of x1 used by output image b (device array), else b
+    int nb, hin, win, hout, wout;
+    int mode;                  // 0 same, 1 down (output node (Y,X) on input node (2Y+1,2X+1)), 2 up (nearest x2)
+    const __nv_bfloat16* w;    // [npad][9][c0 + c1]
+    const float* bias;         // [npad]
+    const __nv_bfloat16* res;  // [nb][hout][wout][npad] added before the activation, or nullptr
+    void* y;                   // bf16 [nb][hout][wout][npad], or fp32 [nb][hout][wout][cstore]
+    int npad;                  // N of the MMA: 16, 32, 64 or 128
+    int cstore;                // channels stored when out_fp32
+    int relu;
+    int out_fp32;
+    int* err;                  // set to 1 when a bounded wait expires
+};
+
+int launch_conv3x3(const ConvArgs& a, cudaStream_t st);
+
+}  // namespace helm

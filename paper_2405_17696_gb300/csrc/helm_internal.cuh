@@ -188,7 +188,7 @@ struct OuterState {
 enum KernelId {
     K_APPLY = 0, K_RESIDUAL64, K_DOTS_FINE, K_DOTS_COARSE, K_UPDATE_FINE, K_UPDATE_COARSE, K_KINIT, K_LSQ,
     K_COMBINE, K_UPDATE_X, K_JACOBI_FINE, K_JACOBI_COARSE, K_RESTRICT_FINE, K_RESTRICT_COARSE, K_PROLONG,
-    K_GALERKIN, K_COPY, K_RESTART, K_COARSE_GMRES, K_MISC, K_COUNT
+    K_GALERKIN, K_COPY, K_RESTART, K_COARSE_GMRES, K_CONV, K_CNN_IO, K_MISC, K_COUNT
 };
 const char* kernel_name(int id);
 
@@ -253,6 +253,15 @@ struct helm_ctx {
     size_t stage_bytes = 0;
     std::vector<void*> allocations;
     helm::Profiler prof;
+    // encoder-solver network preconditioner (HELM_PC_CNN)
+    cnn_model* net = nullptr;
+    std::vector<void*> cnn_z;        // context features per level, [nfreq][nz_l][nx_l][c_l] (BF16)
+    void* cnn_in = nullptr;          // solver input, BF16 [cap][nz][nx][16]
+    float* cnn_out = nullptr;        // solver output, FP32 [cap][nz][nx][2]
+    float2* cnn_e0 = nullptr;        // network error estimate, [cap][nz][nx]
+    float* cnn_rms = nullptr;        // [cap]
+    std::vector<void*> cnn_arena;    // one activation buffer per convolution of the solver pass
+    std::vector<size_t> cnn_arena_bytes;
 };
 
 namespace helm {
@@ -314,5 +323,12 @@ int launch_combine(const helm_ctx* c, const KState& st, float2* out, const float
 int launch_update_x64(const helm_ctx* c, const KState& st, double2* x, const float2* Zb, size_t zstride,
                       size_t n, int nb);
 int launch_restart_check(helm_ctx* c, int nb, double tol, int* n_active_host);
+
+// V-cycle on P u = f from u0 (nullptr: zero) into u_out, for the RHS with mask != 0.
+int vcycle_apply(helm_ctx* c, float2* u_out, const float2* u0, const float2* f, int nb, const int* mask);
+// network preconditioner hooks (cnn.cu)
+int cnn_ctx_setup(helm_ctx* c);      // allocate buffers and run the encoder for every frequency
+void cnn_ctx_free(helm_ctx* c);
+int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const int* mask, int with_vcycle);
 
 }  // namespace helm

@@ -1,0 +1,265 @@
+// 3x3 convolution layers of the encoder-solver network (Fig. 1 caption,
+// Sec. 3.4) as implicit GEMMs on the sm_100-family tensor cores.
+//
+//   y[p, n] = act( bias[n] + res[p, n] + sum_{tap, c} W[n, tap, c] x(src(p, tap), c) )
+//
+// M = output pixels (128 per CTA), N = output channels (all of them per CTA,
+// 16..128), K = 9 taps x input channels.  The input may be the channel
+// concatenation of two tensors (the second one optionally shared by the
+// whole batch: the encoder's context features), and is sampled in one of
+// three modes: same grid, stride-2 'down' (output node (Y, X) centred on input
+// node (2Y+1, 2X+1)) or nearest-neighbour 'up' (output on the doubled grid).
+//
+// Per K stage (one tap x CK channels) the 128 threads gather their pixel's
+// channels and the weights into shared memory in the K-major core-matrix
+// layout (8 rows x 16 bytes per core matrix, no swizzle); one thread issues
+// tcgen05.mma (M=128, N, K=16, BF16 in, FP32 accumulate in TMEM) and commits
+// to the stage's mbarrier, so gathering stage k+1 overlaps the MMAs of stage
+// k.  The epilogue reads the accumulator rows with tcgen05.ld, adds bias and
+// residual, applies ReLU and stores BF16 (or FP32 for the output layer).
+// Every mbarrier wait is bounded; on expiry the kernel raises an error flag,
+// drains what it issued (again bounded), frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "helm_internal.cuh"
+#include "conv.cuh"
+#include "tc_ptx.cuh"
+
+namespace helm {
+
+namespace {
+
+constexpr int CT = 128;                 // threads per CTA = rows of the M tile
+constexpr long long WAIT_LIMIT = 1ll << 24;
+
+__device__ __forceinline__ bool src_coord(int mode, int o, int d, int n_in, int* i) {
+    int v;
+    if (mode == 0) v = o + d;
+    else if (mode == 1) v = 2 * o + 1 + d;
+    else {
+        int u = o + d;
+        if (u < 0 || u >= 2 * n_in) return false;
+        *i = u >> 1;
+        return true;
+    }
+    if (v < 0 || v >= n_in) return false;
+    *i = v;
+    return true;
+}
+
+__device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity) {
+    long long it = 0;
+    while (!tc::mbar_try_wait(bar, parity))
+        if (++it > WAIT_LIMIT) return false;
+    return true;
+}
+
+template <int CK>
+__global__ void __launch_bounds__(CT) conv3x3_tc_kernel(ConvArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int TILE_BYTES = CT * CK * 2;       // one operand tile (A, or B with up to 128 rows)
+    constexpr int STAGE_BYTES = 2 * TILE_BYTES;
+    constexpr int KG = CK / 8;                    // core matrices along K per row group
+    __shared__ uint64_t bar[2];
+    __shared__ uint32_t tmem_base;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t ncols = a.npad < 32 ? 32u : (uint32_t)a.npad;
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_base, ncols);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        tc::fence_mbar_init();
+    }
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    tc::tc_fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    const long long mtot = (long long)a.nb * a.hout * a.wout;
+    const long long p = (long long)blockIdx.x * CT + tid;
+    const bool valid = p < mtot;
+    int b = 0, oy = 0, ox = 0;
+    if (valid) {
+        b = (int)(p / ((long long)a.hout * a.wout));
+        int r = (int)(p - (long long)b * a.hout * a.wout);
+        oy = r / a.wout;
+        ox = r - oy * a.wout;
+    }
+    const int cin = a.c0 + a.c1;
+    const int cper = cin / CK;                    // stages per tap
+    const int nchunks = 9 * cper;
+    const uint32_t idesc = tc::idesc_bf16_f32(CT, a.npad);
+    const uint32_t sbo = KG * 128;
+    bool ok = true;
+    int committed = 0;   // chunks whose MMAs were issued and committed (same in every thread)
+
+    for (int c = 0; c < nchunks; ++c) {
+        const int s = c & 1;
+        if (c >= 2) {
+            // the MMAs that read this stage two chunks ago must be done; the
+            // verdict is made uniform so that every thread leaves together
+            const bool w = bounded_wait(&bar[s], (uint32_t)(((c >> 1) - 1) & 1));
+            if (!__syncthreads_and(w)) { ok = false; break; }
+        }
+        const int tap = c / cper;
+        const int cc = (c - tap * cper) * CK;
+        unsigned char* As = smem + s * STAGE_BYTES;
+        unsigned char* Bs = As + TILE_BYTES;
+        // A: this thread's output pixel, channels [cc, cc + CK) of the tap's source node
+        const __nv_bfloat16* src = nullptr;
+        if (valid) {
+            int iy, ix;
+            if (src_coord(a.mode, oy, tap / 3 - 1, a.hin, &iy) && src_coord(a.mode, ox, tap % 3 - 1, a.win, &ix)) {
+                if (cc < a.c0)
+                    src = a.x0 + (((size_t)b * a.hin + iy) * a.win + ix) * a.c0 + cc;
+                else {
+                    const int b1 = a.x1_map ? __ldg(a.x1_map + b) : (a.x1_bcast ? 0 : b);
+                    src = a.x1 + (((size_t)b1 * a.hin + iy) * a.win + ix) * a.c1 + (cc - a.c0);
+                }
+            }
+        }
+        unsigned char* arow = As + (tid >> 3) * (KG * 128) + (tid & 7) * 16;
+#pragma unroll
+        for (int kg = 0; kg < KG; ++kg) {
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (src) v = __ldg(reinterpret_cast<const uint4*>(src) + kg);
+            *reinterpret_cast<uint4*>(arow + kg * 128) = v;
+        }
+        // B: output channel tid, weights of the tap for the same channels
+        if (tid < a.npad) {
+            const __nv_bfloat16* wr = a.w + ((size_t)tid * 9 + tap) * cin + cc;
+            unsigned char* brow = Bs + (tid >> 3) * (KG * 128) + (tid & 7) * 16;
+#pragma unroll
+            for (int kg = 0; kg < KG; ++kg)
+                *reinterpret_cast<uint4*>(brow + kg * 128) = __ldg(reinterpret_cast<const uint4*>(wr) + kg);
+        }
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::tc_fence_after_sync();
+            const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
+#pragma unroll
+            for (int kk = 0; kk < CK / 16; ++kk) {
+                const uint64_t ad = tc::smem_desc(a0 + kk * 256, 128, sbo);
+                const uint64_t bd = tc::smem_desc(b0 + kk * 256, 128, sbo);
+                tc::mma_bf16(tmem, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&bar[s]);
+        }
+        committed = c + 1;
+    }
+    if (ok) {
+        const int last = nchunks - 1;
+        ok = __syncthreads_and(bounded_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1)));
+    }
+    if (!ok) {
+        if (tid == 0) {
+            atomicExch(a.err, 1);
+            // drain, bounded: the last commit covers every MMA this CTA issued
+            if (committed > 0) {
+                const int last = committed - 1;
+                (void)bounded_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1));
+            }
+        }
+        tc::tc_fence_before_sync();
+        __syncthreads();
+        if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+        return;
+    }
+    tc::tc_fence_after_sync();
+
+    // epilogue: this thread owns accumulator row tid (lane tid)
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int col0 = 0; col0 < a.npad; col0 += 16) {
+        float v[16];
+        tc::tmem_ld16(trow + col0, v);
+        if (!valid) continue;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] += __ldg(a.bias + col0 + i);
+        if (a.res) {
+            const uint4* rp = reinterpret_cast<const uint4*>(a.res + (size_t)p * a.npad + col0);
+            uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
+            const __nv_bfloat16* rb0 = reinterpret_cast<const __nv_bfloat16*>(&r0);
+            const __nv_bfloat16* rb1 = reinterpret_cast<const __nv_bfloat16*>(&r1);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                v[i] += __bfloat162float(rb0[i]);
+                v[8 + i] += __bfloat162float(rb1[i]);
+            }
+        }
+        if (a.relu) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
+        }
+        if (a.out_fp32) {
+            float* yo = reinterpret_cast<float*>(a.y) + (size_t)p * a.cstore;
+            for (int i = 0; i < 16; ++i)
+                if (col0 + i < a.cstore) yo[col0 + i] = v[i];
+        } else {
+            uint4 o0, o1;
+            __nv_bfloat16* ob0 = reinterpret_cast<__nv_bfloat16*>(&o0);
+            __nv_bfloat16* ob1 = reinterpret_cast<__nv_bfloat16*>(&o1);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                ob0[i] = __float2bfloat16_rn(v[i]);
+                ob1[i] = __float2bfloat16_rn(v[8 + i]);
+            }
+            uint4* yp = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + (size_t)p * a.npad + col0);
+            yp[0] = o0;
+            yp[1] = o1;
+        }
+    }
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+template <int CK>
+int launch_ck(const ConvArgs& a, cudaStream_t st) {
+    const size_t smem = 2 * 2 * (size_t)CT * CK * 2;
+    static bool configured = false;   // attribute is per function; setting it twice is harmless
+    if (!configured) {
+        cudaFuncSetAttribute(conv3x3_tc_kernel<CK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = true;
+    }
+    const long long mtot = (long long)a.nb * a.hout * a.wout;
+    const unsigned grid = (unsigned)((mtot + CT - 1) / CT);
+    conv3x3_tc_kernel<CK><<<grid, CT, smem, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
+}
+
+}  // namespace
+
+// Validates the shapes and launches; returns HELM_EINVAL for unsupported ones.
+int launch_conv3x3(const ConvArgs& a, cudaStream_t st) {
+    const int cin = a.c0 + a.c1;
+    if (a.npad != 16 && a.npad != 32 && a.npad != 64 && a.npad != 128) {
+        set_error("conv3x3: output channels must be padded to 16, 32, 64 or 128");
+        return HELM_EINVAL;
+    }
+    if (a.c0 % 16 || a.c1 % 16 || cin < 16 || !a.x0 || (a.c1 && !a.x1) || !a.w || !a.bias || !a.y || !a.err) {
+        set_error("conv3x3: input channels must be multiples of 16 and pointers non-null");
+        return HELM_EINVAL;
+    }
+    if (a.nb < 1 || a.hin < 1 || a.win < 1 || a.mode < 0 || a.mode > 2) {
+        set_error("conv3x3: bad shape or mode");
+        return HELM_EINVAL;
+    }
+    int ck = 64;
+    if (a.c0 % 64 || (a.c1 && a.c1 % 64)) ck = 32;
+    if (a.c0 % 32 || (a.c1 && a.c1 % 32)) ck = 16;
+    int s;
+    if (ck == 64) s = launch_ck<64>(a, st);
+    else if (ck == 32) s = launch_ck<32>(a, st);
+    else s = launch_ck<16>(a, st);
+    if (s != HELM_OK) set_error(std::string("conv3x3 launch: ") + cudaGetErrorString(cudaGetLastError()));
+    return s;
+}
+
+}  // namespace helm

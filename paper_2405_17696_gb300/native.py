@@ -69,6 +69,22 @@ def _load():
     lib.helm_vcycle.restype = ip
     lib.fwi_misfit_grad.argtypes = [vp, vp, ip, vp, ip, vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double), vp]
     lib.fwi_misfit_grad.restype = ip
+    lib.cnn_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(ctypes.c_int)]
+    lib.cnn_create.restype = ip
+    lib.cnn_destroy.argtypes = [vp]
+    lib.cnn_destroy.restype = None
+    lib.cnn_num_params.argtypes = [vp]
+    lib.cnn_num_params.restype = ctypes.c_longlong
+    lib.cnn_set_params.argtypes = [vp, vp, ctypes.c_longlong]
+    lib.cnn_set_params.restype = ip
+    lib.cnn_get_params.argtypes = [vp, vp, ctypes.c_longlong]
+    lib.cnn_get_params.restype = ip
+    lib.cnn_forward.argtypes = [vp, vp, ip, vp, ip, ip, ip, vp]
+    lib.cnn_forward.restype = ip
+    lib.cnn_precond_apply.argtypes = [vp, vp, vp, ip, vp, ip]
+    lib.cnn_precond_apply.restype = ip
+    lib.cnn_conv3x3.argtypes = [vp, ip, vp, ip, ip, ip, ip, ip, vp, vp, ip, vp, ip, ip, vp]
+    lib.cnn_conv3x3.restype = ip
     lib.helm_destroy.argtypes = [vp]
     lib.helm_destroy.restype = None
     lib.helm_last_error.argtypes = []
@@ -237,3 +253,49 @@ def helm_profile_read(ctx) -> dict:
 
 def helm_launch_count() -> int:
     return int(lib.helm_launch_count())
+
+
+# --------------------------------------------------------------------------
+# encoder-solver network
+# --------------------------------------------------------------------------
+
+def cnn_create(levels: int, widths):
+    w = (ctypes.c_int * levels)(*widths)
+    net = ctypes.c_void_p()
+    _check(lib.cnn_create(ctypes.byref(net), levels, w), "cnn_create")
+    return net
+
+
+def cnn_destroy(net):
+    if net:
+        lib.cnn_destroy(net)
+
+
+def cnn_num_params(net) -> int:
+    return int(lib.cnn_num_params(net))
+
+
+def cnn_set_params(net, params):
+    _check(lib.cnn_set_params(net, _ptr(params, "float32"), int(np.prod(params.shape))), "cnn_set_params")
+
+
+def cnn_get_params(net, params):
+    _check(lib.cnn_get_params(net, _ptr(params, "float32"), int(np.prod(params.shape))), "cnn_get_params")
+
+
+def cnn_forward(net, enc_in, nenc: int, sol_in, nsol: int, ny: int, nx: int, out):
+    _check(lib.cnn_forward(net, _ptr(enc_in, "float32"), nenc, _ptr(sol_in, "float32"), nsol, ny, nx,
+                           _ptr(out, "float32")), "cnn_forward")
+
+
+def cnn_conv3x3(x0, c0: int, x1, c1: int, x1_bcast: int, nb: int, hin: int, win: int, w, bias, cout: int, res,
+                mode: int, relu: int, y):
+    _check(lib.cnn_conv3x3(_ptr(x0, "float32"), c0, _ptr(x1, "float32"), c1, x1_bcast, nb, hin, win,
+                           _ptr(w, "float32"), _ptr(bias, "float32"), cout, _ptr(res, "float32"), mode, relu,
+                           _ptr(y, "float32")), "cnn_conv3x3")
+
+
+def cnn_precond_apply(ctx, r, e, nrhs: int, freq_idx=None, with_vcycle: int = 1):
+    _keep, fptr = _int_array(freq_idx, nrhs)
+    _check(lib.cnn_precond_apply(ctx, _ptr(r, "complex64"), _ptr(e, "complex64"), nrhs, fptr, with_vcycle),
+           "cnn_precond_apply")

@@ -1,0 +1,170 @@
+"""GPU parity of the tensor-core network layers and of the whole
+encoder-solver forward pass against the oracle (Fig. 1 caption, Eq. 3.13,
+4.1), through the C ABI.
+
+Both sides take the same decisions in the same precision: inputs and weights
+are rounded to bfloat16, every stored activation is rounded to bfloat16, and
+the sums are exact-ish on the oracle side (float64) and FP32 on the tensor
+cores; the output layer stays FP32.  Single layers therefore agree to about
+one bfloat16 unit; the whole network, whose activations may round to the
+other side of a tie after ~60 layers, agrees to 1e-2 relative L2.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import cnn  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def native():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_17696_gb300 import build
+    build.build()
+    from paper_2405_17696_gb300 import native as n
+    return n
+
+
+MODES = {"same": 0, "down": 1, "up": 2}
+
+
+@pytest.mark.parametrize("c0,c1,bcast,cout,mode,hin,win,nb,res,relu", [
+    (16, 0, 0, 16, "same", 20, 12, 2, False, True),      # 480 pixels: ragged last tile
+    (3, 0, 0, 16, "same", 16, 16, 1, False, True),       # network input layer (3 -> padded 16)
+    (32, 0, 0, 32, "same", 16, 24, 2, True, True),       # ResNet second conv: residual + ReLU
+    (64, 64, 1, 64, "same", 8, 16, 3, False, True),      # concat with a batch-shared context
+    (16, 16, 0, 16, "same", 12, 20, 2, False, True),     # concat of two 16-channel tensors
+    (16, 0, 0, 32, "down", 24, 16, 2, False, True),
+    (128, 0, 0, 64, "up", 6, 10, 2, False, True),
+    (128, 128, 0, 128, "same", 8, 8, 2, False, True),
+    (16, 0, 0, 2, "same", 16, 20, 2, False, False),      # output layer, 2 channels
+])
+def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res, relu):
+    g = np.random.default_rng(c0 * 7 + cout + MODES[mode])
+    x0 = cnn.bf16_round(g.normal(size=(nb, hin, win, c0)))
+    x1 = cnn.bf16_round(g.normal(size=((1 if bcast else nb), hin, win, c1))) if c1 else None
+    w = cnn.bf16_round(g.normal(size=(cout, 9, c0 + c1)) / np.sqrt(9 * (c0 + c1)))
+    b = g.normal(size=cout) * 0.1
+    ho, wo = cnn.out_shape(hin, win, mode)
+    r = cnn.bf16_round(g.normal(size=(nb, ho, wo, cout))) if res else None
+    xin = x0 if x1 is None else np.concatenate([x0, np.broadcast_to(x1, (nb,) + x1.shape[1:])], axis=-1)
+    ref = cnn.conv_forward(xin, w, b, mode)
+    if r is not None:
+        ref = ref + r
+    if relu:
+        ref = np.maximum(ref, 0)
+    ref = cnn.bf16_round(ref)
+    y = np.zeros((nb, ho, wo, cout), np.float32)
+    f32 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+    native.cnn_conv3x3(f32(x0), c0, f32(x1), c1, bcast, nb, hin, win, f32(w), f32(b), cout, f32(r),
+                       MODES[mode], 1 if relu else 0, y)
+    err = np.abs(y - ref)
+    tol = 2.0 ** -7 * np.abs(ref) + 1e-3 * np.abs(ref).max()
+    assert np.all(err <= tol), (err.max(), np.abs(ref).max())
+
+
+@pytest.mark.parametrize("widths,ny,nx,nsol", [((16, 32), 32, 32, 2), ((16, 32, 64, 128), 64, 32, 2)])
+def test_network_forward_parity(native, widths, ny, nx, nsol):
+    # Half-scale He weights keep the random network contractive: with full-scale
+    # weights a one-unit change of a single rounding decision already moves the
+    # output of this 60-layer BF16 network by a few percent (measured on the
+    # oracle), which would hide real errors.  The tolerance is three times the
+    # oracle's own spread under perturbed rounding, at least 1e-2.
+    specs = cnn.layer_specs(widths=widths)
+    g = np.random.default_rng(3)
+    theta = 0.5 * cnn.he_init(specs, seed=2) + 0.02 * g.normal(size=cnn.n_params(specs))
+    theta_bf = cnn.bf16_round(theta)                        # the weights the GPU uses
+    enc_in = cnn.bf16_round(g.normal(size=(1, ny, nx, 3)))
+    sol_in = cnn.bf16_round(g.normal(size=(nsol, ny, nx, 3)))
+    P = cnn.unflatten(theta_bf, specs)
+    ref, _ = cnn.network_forward(P, specs, enc_in, sol_in, quantize=cnn.bf16_round)
+    nudged = lambda a: cnn.bf16_round(np.asarray(a, dtype=np.float32).astype(np.float64) * (1 + 2.0 ** -22))
+    alt, _ = cnn.network_forward(P, specs, enc_in, sol_in, quantize=nudged)
+    spread = np.linalg.norm(alt - ref) / np.linalg.norm(ref)
+    net = native.cnn_create(len(widths), widths)
+    try:
+        assert native.cnn_num_params(net) == theta.size
+        native.cnn_set_params(net, theta.astype(np.float32))
+        out = np.zeros((nsol, ny, nx, 2), np.float32)
+        native.cnn_forward(net, enc_in.astype(np.float32), 1, sol_in.astype(np.float32), nsol, ny, nx, out)
+        back = np.zeros(theta.size, np.float32)
+        native.cnn_get_params(net, back)
+    finally:
+        native.cnn_destroy(net)
+    assert np.array_equal(back, theta.astype(np.float32))
+    rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+    assert rel <= max(1e-2, 3 * spread), (rel, spread)
+
+
+# --------------------------------------------------------------------------
+# the network as a preconditioner inside the solver (Eq. 3.14)
+# --------------------------------------------------------------------------
+
+def _net_ctx(native, w, widths=(16, 32, 64), seed=4, **opts):
+    from paper_2405_17696_gb300 import media  # noqa: F401
+    specs = cnn.layer_specs(widths=widths)
+    theta = cnn.he_init(specs, seed=seed) * 0.5
+    net = native.cnn_create(len(widths), widths)
+    native.cnn_set_params(net, theta.astype(np.float32))
+    o = native.helm_default_opts(precond=native.HELM_PC_CNN, **opts)
+    om = torch.from_numpy(np.asarray(w.omegas, dtype=np.float32)).cuda()
+    ctx = native.helm_setup(torch.from_numpy(w.kappa).cuda(), torch.from_numpy(w.gamma).cuda(), w.nx, w.nz, w.h,
+                            w.h, om, net=net, opts=o)
+    return net, ctx, specs, theta
+
+
+def test_network_preconditioner_parity(native):
+    from paper_2405_17696_gb300 import media
+    from oracle import multigrid as MG
+    w = media.crop_workload(64, 32, freqs=(4.0, 7.0), width=8)
+    net, ctx, specs, theta = _net_ctx(native, w, mg_levels=3)
+    try:
+        nb = 3
+        fi = np.array([1, 0, 1], np.int32)
+        r = media.complex_normal((nb, w.nz, w.nx), seed=12) * 1e-3
+        e0 = np.zeros_like(r)
+        native.cnn_precond_apply(ctx, r, e0, nb, fi, 0)
+        e = np.zeros_like(r)
+        native.cnn_precond_apply(ctx, r, e, nb, fi, 1)
+    finally:
+        native.helm_destroy(ctx)
+        native.cnn_destroy(net)
+    P = cnn.unflatten(cnn.bf16_round(theta), specs)
+    kap, gam = w.kappa.astype(np.float64), w.gamma.astype(np.float64)
+    for b in range(nb):
+        om = float(np.float32(w.omegas[fi[b]]))
+        enc = cnn.bf16_round(cnn.encoder_input(kap, gam, om, w.h))
+        x, rms = cnn.solver_input(r[b], gam)
+        out, _ = cnn.network_forward(P, specs, enc, cnn.bf16_round(x), quantize=cnn.bf16_round)
+        ref0 = cnn.solver_output_to_error(out, rms, w.h)[0]
+        assert np.linalg.norm(e0[b] - ref0) <= 2e-2 * np.linalg.norm(ref0)
+        # the V-cycle part, from the GPU's own e_0
+        pc = MG.VCyclePreconditioner(kap, gam, om, w.h, w.h, MG.VCycleParams(levels=3))
+        ref = pc(r[b].astype(np.complex128), e0[b].astype(np.complex128))
+        assert np.linalg.norm(e[b] - ref) <= 2e-4 * np.linalg.norm(ref)
+
+
+def test_cnn_fgmres_solve(native):
+    from oracle import helmholtz as H
+    from paper_2405_17696_gb300 import media
+    w = media.crop_workload(128, 64, freqs=(4.0, 6.0), width=16)
+    net, ctx, specs, theta = _net_ctx(native, w, mg_levels=3)
+    try:
+        rhs = w.rhs()
+        fi = w.freq_index()
+        x = torch.zeros(rhs.shape, dtype=torch.complex128, device="cuda")
+        st, iters, rel, stat = native.helm_solve(ctx, torch.from_numpy(rhs).cuda(), x, rhs.shape[0], fi, 1e-6,
+                                                 native.HELM_SOLVE_ZERO_X0)
+        xs = x.cpu().numpy()
+    finally:
+        native.helm_destroy(ctx)
+        native.cnn_destroy(net)
+    assert st == native.HELM_OK, (stat, iters)
+    kap, gam = w.kappa.astype(np.float64), w.gamma.astype(np.float64)
+    for b in range(rhs.shape[0]):
+        om = float(np.float32(w.omegas[fi[b]]))
+        assert H.relative_residual(xs[b], rhs[b], kap, gam, om, w.h, w.h) <= 1e-6

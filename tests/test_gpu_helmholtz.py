@@ -113,8 +113,11 @@ def test_vcycle_parity(native, nx, nz, levels, kind, with_u0):
 # solves
 # --------------------------------------------------------------------------
 
-def _solve_and_check(native, w, fi, rhs, levels=3, adjoint=0, tol=1e-6, host=False, **opts):
+def _solve_and_check(native, w, fi, rhs, levels=3, adjoint=0, tol=1e-8, host=False, **opts):
+    # solved to 1e-8: a relative residual of 1e-6 bounds the error only through the
+    # conditioning (up to a few 1e-4 at 3 Hz), the 1e-4 error target needs more
     flags = native.HELM_SOLVE_ADJOINT if adjoint else 0
+    opts.setdefault("max_iter", 800)
     ctx = _ctx(native, w, mg_levels=levels, **opts)
     try:
         nb = rhs.shape[0]
@@ -144,7 +147,7 @@ def _solve_and_check(native, w, fi, rhs, levels=3, adjoint=0, tol=1e-6, host=Fal
         err = H.relative_error(xs[b], xd)
         assert rr <= tol, (b, rr)
         assert err <= 1e-4, (b, err)
-        assert abs(rel[b] - rr) <= 0.05 * tol + 1e-3 * rr
+        assert abs(rel[b] - rr) <= 1e-3 * rr + 1e-14
     return iters
 
 
@@ -162,7 +165,7 @@ def test_solve_layered_mixed_frequencies(native, nx, nz):
     w = media.crop_workload(nx, nz, freqs=(3.0, 5.0, 7.0), width=min(24, nz // 4))
     rhs = w.rhs()
     fi = w.freq_index()
-    _solve_and_check(native, w, fi, rhs, levels=3, max_iter=600)
+    _solve_and_check(native, w, fi, rhs, levels=3)
 
 
 def test_solve_random_rhs_and_adjoint(native):
@@ -246,7 +249,7 @@ def test_batched_workload_sampled_against_direct_solve(native):
     # (up to ~4e-4 at 3 Hz here); the 1e-4 error target is checked on a
     # sample solved to 1e-8 in the same batched launch configuration
     sample = np.array([0, 63, 64 + 17, 191])
-    ctx = _ctx(native, w, mg_levels=3)
+    ctx = _ctx(native, w, mg_levels=3, max_iter=800)
     try:
         x = torch.zeros((len(sample),) + rhs.shape[1:], dtype=torch.complex128, device="cuda")
         st, *_ = native.helm_solve(ctx, torch.from_numpy(rhs[sample]).cuda(), x, len(sample), fi[sample], 1e-8, 0)

@@ -113,3 +113,12 @@ def test_adam_first_step():
     t1, m, v = cnn.adam_step(theta, grad, np.zeros(20), np.zeros(20), 1, lr=1e-3, eps=0.0)
     assert np.allclose(t1 - theta, -1e-3 * np.sign(grad), atol=1e-15)
     assert np.allclose(m, 0.1 * grad) and np.allclose(v, 0.001 * grad * grad)
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    g = _rng(11)
+    x = np.concatenate([g.normal(size=1000) * 10.0 ** g.integers(-20, 20, size=1000),
+                        [1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, -1 - 2 ** -8, 0.0, -0.0]])
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(cnn.bf16_round(x), ref)
