@@ -216,6 +216,32 @@ int cnn_forward(cnn_model* net, const float* enc_in, int nenc, const float* sol_
  * r, e : complex64 [nrhs][nz][nx] (host or device); freq_idx as in helm_solve. */
 int cnn_precond_apply(helm_ctx* ctx, const helm_c64* r, helm_c64* e, int nrhs, const int* freq_idx,
                       int with_vcycle);
+/* ---- training (Sec. 4.1-4.2, Eq. 4.2-4.3, Alg. 2) ---------------------------------
+ * Data of Eq. 4.3 for the context's medium: b = H x, x~ = FGMRES(H, M = V-cycle, b, 0)
+ * after exactly iters[i] steps (1 <= iters[i] <= restart), r = b - H x~, e = x - x~.
+ *   x : complex64 [nb][nz][nx], the caller's draws of x ~ CN(0, 1); iters : host int32 [nb]
+ *   r_out, e_out : complex64 [nb][nz][nx]; nb <= max_rhs.  Host or device pointers. */
+int cnn_make_samples(helm_ctx* ctx, const helm_c64* x, const int* freq_idx, const int* iters, int nb,
+                     helm_c64* r_out, helm_c64* e_out);
+/* One data step of Alg. 2 for every pair (r, e): e_net = network(r) (the error estimate,
+ * without V-cycle), e~ = FGMRES(H, V-cycle, r, x0 = e_net) after one step, and the new pair
+ * (r - H e~, e - e~) (literal = 0, the residual-correction reading) or (H e~, e~) (literal = 1,
+ * Alg. 2 as printed).  Needs a context created with a network. */
+int cnn_refine_samples(helm_ctx* ctx, const helm_c64* r, const helm_c64* e, const int* freq_idx, int nb,
+                       int literal, helm_c64* r_out, helm_c64* e_out);
+/* MSE loss of Eq. 4.2 on a batch, (1/nb) sum ||e_net(r_i) - e_i||^2 with
+ * e_net = h^2 rms(r) net(r / rms(r)) (network output only, no V-cycle), and its gradient
+ * with respect to every parameter (flat, FP32, written to grad_out if not NULL; host or
+ * device).  The context supplies the medium and frequencies (freq_idx per pair). */
+int cnn_loss_grad(cnn_model* net, helm_ctx* ctx, const helm_c64* r, const helm_c64* e, const int* freq_idx,
+                  int nb, double* loss, float* grad_out);
+/* One Adam step (Kingma & Ba; beta = (0.9, 0.999), eps = 1e-8, learning rate lr) on the loss
+ * of cnn_loss_grad; returns the loss before the step.  If the context was created with
+ * this network its context features are recomputed with the new weights. */
+int cnn_train_step(cnn_model* net, helm_ctx* ctx, const helm_c64* r, const helm_c64* e, const int* freq_idx,
+                   int nb, float lr, double* loss);
+int cnn_adam_reset(cnn_model* net);
+
 /* One 3x3 convolution layer of the network, FP32 in and out (rounded to BF16 inside,
  * FP32 accumulation on the tensor cores, output rounded to BF16 then widened):
  *   y = act(bias + res + conv(concat(x0, x1)))      NHWC, weights [cout][9][c0 + c1]

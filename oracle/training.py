@@ -1,0 +1,72 @@
+"""Training data and loss of the encoder-solver network (CPU, float64).
+
+TEST INFRASTRUCTURE: see the package header for who may import this.
+
+* Eq. 4.3: for a draw x, b = H x, x~ = GMRES(H, M = V-cycle, b, x0 = 0) after
+  `iters` steps, r = b - H x~, e = x - x~ (the flexible variant, since the
+  V-cycle with a GMRES coarsest solve is not a linear operator).
+* Alg. 2 data step: e_net = network(r); e~ = GMRES(H, V-cycle, r, x0 = e_net)
+  after one step; new pair (r - H e~, e - e~) in the residual-correction
+  reading, or (H e~, e~) as printed.
+* Eq. 4.2: loss = (1/m) sum_i ||e_net(r_i) - e_i||^2, e_net = h^2 rms(r) out.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import cnn
+from . import helmholtz as H
+from . import multigrid as MG
+from .krylov import fgmres_cycle
+
+
+def make_samples(kappa, gamma, omega, h, x, iters, params=None):
+    p = params if params is not None else MG.VCycleParams()
+    pc = MG.VCyclePreconditioner(kappa, gamma, omega, h, h, p)
+    A = lambda u: H.helmholtz_apply(u, kappa, gamma, omega, h, h)
+    rs, es = [], []
+    for xi, k in zip(np.asarray(x, dtype=np.complex128), iters):
+        b = A(xi)
+        xt, _, _ = fgmres_cycle(A, pc, b, np.zeros_like(b), int(k), tol_abs=0.0)
+        rs.append(b - A(xt))
+        es.append(xi - xt)
+    return np.stack(rs), np.stack(es)
+
+
+def network_error(P, specs, kappa, gamma, omega, h, r, quantize=None):
+    """e_net = h^2 rms(r) (out_re + i out_im) for residuals r [B][nz][nx]."""
+    enc = cnn.encoder_input(kappa, gamma, omega, h)
+    x, rms = cnn.solver_input(r, gamma)
+    if quantize is not None:
+        enc, x = quantize(enc), quantize(x)
+    out, tape = cnn.network_forward(P, specs, enc, x, quantize=quantize)
+    return cnn.solver_output_to_error(out, rms, h), out, tape, rms
+
+
+def refine_samples(P, specs, kappa, gamma, omega, h, r, e, literal=False, params=None, quantize=None):
+    p = params if params is not None else MG.VCycleParams()
+    pc = MG.VCyclePreconditioner(kappa, gamma, omega, h, h, p)
+    A = lambda u: H.helmholtz_apply(u, kappa, gamma, omega, h, h)
+    e_net, _, _, _ = network_error(P, specs, kappa, gamma, omega, h, r, quantize)
+    r2, e2 = [], []
+    for ri, ei, x0 in zip(np.asarray(r, dtype=np.complex128), np.asarray(e, dtype=np.complex128), e_net):
+        et, _, _ = fgmres_cycle(A, pc, ri, x0, 1, tol_abs=0.0)
+        if literal:
+            r2.append(A(et))
+            e2.append(et)
+        else:
+            r2.append(ri - A(et))
+            e2.append(ei - et)
+    return np.stack(r2), np.stack(e2)
+
+
+def loss_and_grad(P, specs, kappa, gamma, omega, h, r, e, quantize=None):
+    """(loss, {name: (dw, db)}) of Eq. 4.2 for one batch of one medium/frequency."""
+    e_net, out, tape, rms = network_error(P, specs, kappa, gamma, omega, h, r, quantize)
+    m = r.shape[0]
+    d = e_net - np.asarray(e, dtype=np.complex128)
+    loss = float(np.sum(np.abs(d) ** 2) / m)
+    s = (h * h) * rms[:, None, None]
+    g_out = np.stack([2.0 * d.real * s / m, 2.0 * d.imag * s / m], axis=-1)
+    grads, _ = cnn.backward(P, specs, tape, g_out)
+    return loss, grads

@@ -23,7 +23,7 @@ const char* kernel_name(int id) {
         "stencil_apply", "residual64", "arnoldi_dots_fine", "arnoldi_dots_coarse", "arnoldi_update_fine",
         "arnoldi_update_coarse", "krylov_init", "lsq", "combine", "update_x64", "jacobi_fine", "jacobi_coarse",
         "restrict_fine", "restrict_coarse", "prolong_add", "galerkin", "copy", "restart_check", "coarse_gmres",
-        "conv3x3_tc", "cnn_io", "misc"};
+        "conv3x3_tc", "cnn_io", "wgrad", "misc"};
     return (id >= 0 && id < K_COUNT) ? names[id] : "?";
 }
 
@@ -281,12 +281,20 @@ int precondition(helm_ctx* c, float2* z, const float2* v, int nb, const int* mas
 // restarted FGMRES for one batch of nb <= cap right-hand sides (device data)
 // ---------------------------------------------------------------------------
 int fgmres_batch(helm_ctx* c, const float2* rhs, double2* x, int nb, double tol, int adjoint, helm_stats* stats,
-                 int* n_active_dev, int* n_active_host) {
+                 int* n_active_dev, int* n_active_host, const int* steps_cap = nullptr) {
     const size_t N = npts(c);
     const size_t vs = (size_t)c->cap * N;
     const int k = c->fine.k;
     const bool pc = c->opt.precond != HELM_PC_NONE;
     HELM_TRY(launch_outer_init(c, nb));
+    if (steps_cap) {
+        // fixed number of steps per RHS (no convergence test): start the step
+        // counter at max_iter - cap so that the cap ends the RHS
+        std::vector<int> it0(nb);
+        for (int i = 0; i < nb; ++i) it0[i] = c->opt.max_iter - steps_cap[i];
+        HELM_CK(cudaMemcpyAsync(c->outer.iters, it0.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        HELM_CK(cudaStreamSynchronize(c->stream));
+    }
     if (adjoint) HELM_TRY(launch_conj64(c, x, nb));
     HELM_TRY(launch_residual64(c, x, rhs, c->V, nb, adjoint, 1));
     HELM_CK(cudaMemsetAsync(n_active_dev, 0, sizeof(int), c->stream));
@@ -315,6 +323,41 @@ int fgmres_batch(helm_ctx* c, const float2* rhs, double2* x, int nb, double tol,
     }
     if (adjoint) HELM_TRY(launch_conj64(c, x, nb));
     return HELM_OK;
+}
+
+__global__ void widen_kernel(const float2* __restrict__ a, double2* __restrict__ b, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        b[i] = make_double2(a[i].x, a[i].y);
+}
+
+// out = a - b (complex64 minus complex128, computed in FP64, stored complex64)
+__global__ void diff_kernel(const float2* __restrict__ a, const double2* __restrict__ b, float2* __restrict__ out,
+                            size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double2 v = b[i];
+        out[i] = make_float2((float)((double)a[i].x - v.x), (float)((double)a[i].y - v.y));
+    }
+}
+
+__global__ void negate_kernel(const float2* __restrict__ a, float2* __restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = make_float2(-a[i].x, -a[i].y);
+}
+
+// Fixed-step FGMRES(H, M = V-cycle, b, x0) for the data of Eq. 4.3 and Alg. 2:
+// x (complex128, device) holds x0 on entry and the iterate after steps[i] steps.
+int fixed_step_solve(helm_ctx* c, const float2* b, double2* x, int nb, const int* steps) {
+    int* n_active_dev = nullptr;
+    int* n_active_host = nullptr;
+    HELM_CK(cudaMalloc(&n_active_dev, sizeof(int)));
+    if (cudaMallocHost(&n_active_host, sizeof(int)) != cudaSuccess) { cudaFree(n_active_dev); return HELM_ENOMEM; }
+    const int pc = c->opt.precond;
+    c->opt.precond = HELM_PC_MG;      // the data of Eq. 4.3 comes from the plain V-cycle
+    int s = fgmres_batch(c, b, x, nb, 1e-300, 0, nullptr, n_active_dev, n_active_host, steps);
+    c->opt.precond = pc;
+    cudaFree(n_active_dev);
+    cudaFreeHost(n_active_host);
+    return s;
 }
 
 }  // namespace
@@ -707,5 +750,109 @@ int helm_profile_read(helm_ctx* c, int max, const char** names, double* ms, long
 }
 
 long long helm_launch_count(void) { return g_launches.load(); }
+
+int cnn_make_samples(helm_ctx* c, const helm_c64* x, const int* freq_idx, const int* iters, int nb, helm_c64* r_out,
+                     helm_c64* e_out) {
+    g_last_error.clear();
+    if (!c || !x || !iters || !r_out || !e_out || nb < 1 || nb > c->cap) {
+        set_error("cnn_make_samples: invalid argument (nb must be in [1, max_rhs])");
+        return HELM_EINVAL;
+    }
+    for (int i = 0; i < nb; ++i)
+        if (iters[i] < 1 || iters[i] > c->opt.restart) { set_error("cnn_make_samples: iters must be in [1, restart]"); return HELM_EINVAL; }
+    const size_t N = npts(c);
+    HELM_TRY(upload_freq(c, freq_idx, nb));
+    float2 *dx = nullptr, *db = nullptr, *dr = nullptr, *de = nullptr;
+    double2* xt = nullptr;
+    int s = HELM_OK;
+    auto ck = [&](cudaError_t e) { if (e != cudaSuccess && s == HELM_OK) { set_error(cudaGetErrorString(e)); s = HELM_ECUDA; } };
+    ck(cudaMalloc(&dx, nb * N * sizeof(float2)));
+    ck(cudaMalloc(&db, nb * N * sizeof(float2)));
+    ck(cudaMalloc(&dr, nb * N * sizeof(float2)));
+    ck(cudaMalloc(&de, nb * N * sizeof(float2)));
+    ck(cudaMalloc(&xt, nb * N * sizeof(double2)));
+    if (!s) ck(cudaMemcpyAsync(dx, x, nb * N * sizeof(float2), cudaMemcpyDefault, c->stream));
+    if (!s) ck(cudaMemsetAsync(xt, 0, nb * N * sizeof(double2), c->stream));
+    if (!s) s = launch_apply_fine(c, fine_op(c, 0), dx, db, nb, c->ones);          // b = H x
+    if (!s) s = fixed_step_solve(c, db, xt, nb, iters);                            // x~ (Eq. 4.3)
+    if (!s) s = launch_outer_init(c, nb);
+    if (!s) s = launch_residual64(c, xt, db, dr, nb, 0, 1);                        // r = b - H x~
+    if (!s) {
+        LaunchScope scope(c, K_MISC);
+        diff_kernel<<<1184, 256, 0, c->stream>>>(dx, xt, de, nb * N);              // e = x - x~
+        ck(cudaGetLastError());
+    }
+    if (!s) ck(cudaMemcpyAsync(r_out, dr, nb * N * sizeof(float2), cudaMemcpyDefault, c->stream));
+    if (!s) ck(cudaMemcpyAsync(e_out, de, nb * N * sizeof(float2), cudaMemcpyDefault, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+    cudaFree(dx); cudaFree(db); cudaFree(dr); cudaFree(de); cudaFree(xt);
+    return s;
+}
+
+int cnn_refine_samples(helm_ctx* c, const helm_c64* r, const helm_c64* e, const int* freq_idx, int nb, int literal,
+                       helm_c64* r_out, helm_c64* e_out) {
+    g_last_error.clear();
+    if (!c || !c->net || !r || !e || !r_out || !e_out || nb < 1 || nb > c->cap) {
+        set_error("cnn_refine_samples: invalid argument or no network in the context");
+        return HELM_EINVAL;
+    }
+    const size_t N = npts(c);
+    HELM_TRY(upload_freq(c, freq_idx, nb));
+    float2 *dr = nullptr, *de = nullptr, *en = nullptr, *ro = nullptr, *eo = nullptr;
+    double2* xt = nullptr;
+    int s = HELM_OK;
+    auto ck = [&](cudaError_t er) { if (er != cudaSuccess && s == HELM_OK) { set_error(cudaGetErrorString(er)); s = HELM_ECUDA; } };
+    ck(cudaMalloc(&dr, nb * N * sizeof(float2)));
+    ck(cudaMalloc(&de, nb * N * sizeof(float2)));
+    ck(cudaMalloc(&en, nb * N * sizeof(float2)));
+    ck(cudaMalloc(&ro, nb * N * sizeof(float2)));
+    ck(cudaMalloc(&eo, nb * N * sizeof(float2)));
+    ck(cudaMalloc(&xt, nb * N * sizeof(double2)));
+    if (!s) ck(cudaMemcpyAsync(dr, r, nb * N * sizeof(float2), cudaMemcpyDefault, c->stream));
+    if (!s) ck(cudaMemcpyAsync(de, e, nb * N * sizeof(float2), cudaMemcpyDefault, c->stream));
+    if (!s) s = cnn_ctx_precondition(c, en, dr, nb, c->ones, 0);                   // e_net = network(r)
+    if (!s) {
+        LaunchScope scope(c, K_MISC);
+        widen_kernel<<<1184, 256, 0, c->stream>>>(en, xt, nb * N);
+        ck(cudaGetLastError());
+    }
+    std::vector<int> one(nb, 1);
+    if (!s) s = fixed_step_solve(c, dr, xt, nb, one.data());                       // e~ = GMRES(H, V, r, e_net, 1)
+    if (!s && literal) {
+        // the pair (H e~, e~) of Alg. 2 as printed
+        ck(cudaMemsetAsync(en, 0, nb * N * sizeof(float2), c->stream));
+        if (!s) s = launch_outer_init(c, nb);
+        if (!s) s = launch_residual64(c, xt, en, eo, nb, 0, 1);                    // eo = 0 - H e~
+        if (!s) {
+            LaunchScope scope(c, K_MISC);
+            negate_kernel<<<1184, 256, 0, c->stream>>>(eo, ro, nb * N);           // r' = H e~
+            ck(cudaGetLastError());
+        }
+        if (!s) {
+            LaunchScope scope(c, K_MISC);
+            diff_kernel<<<1184, 256, 0, c->stream>>>(en, xt, eo, nb * N);          // 0 - e~
+            ck(cudaGetLastError());
+        }
+        if (!s) {
+            LaunchScope scope(c, K_MISC);
+            negate_kernel<<<1184, 256, 0, c->stream>>>(eo, eo, nb * N);           // e' = e~
+            ck(cudaGetLastError());
+        }
+    }
+    if (!s && !literal) {
+        if (!s) s = launch_outer_init(c, nb);
+        if (!s) s = launch_residual64(c, xt, dr, ro, nb, 0, 1);                    // r' = r - H e~
+        if (!s) {
+            LaunchScope scope(c, K_MISC);
+            diff_kernel<<<1184, 256, 0, c->stream>>>(de, xt, eo, nb * N);          // e' = e - e~
+            ck(cudaGetLastError());
+        }
+    }
+    if (!s) ck(cudaMemcpyAsync(r_out, ro, nb * N * sizeof(float2), cudaMemcpyDefault, c->stream));
+    if (!s) ck(cudaMemcpyAsync(e_out, eo, nb * N * sizeof(float2), cudaMemcpyDefault, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+    cudaFree(dr); cudaFree(de); cudaFree(en); cudaFree(ro); cudaFree(eo); cudaFree(xt);
+    return s;
+}
 
 }  // extern "C"

@@ -1,0 +1,512 @@
+// Training of the encoder-solver network (Sec. 4.1, Eq. 4.2; Alg. 2):
+// the MSE loss between the network's error estimate and the true error, the
+// backward pass through the recorded forward tape, and Adam (Kingma & Ba).
+//
+// Backward of one convolution y = act(W * x + b [+ res]) with upstream
+// gradient G_y (FP32):
+//   g      = G_y . [y > 0]  (BF16 operand; FP32 copy added to G_res for a ResNet skip)
+//   dW, db += sum over pixels of g (x) x_tap    (FP32, CUDA cores)
+//   G_x   += W^T * g   on the tensor cores with the same kernel as the forward:
+//            'same'  -> same-grid convolution with transposed, tap-flipped weights,
+//            'down'  -> the transpose-of-down gather mode with transposed weights,
+//            'up'    -> same-grid convolution on the fine grid, then a 2x2 sum.
+// The context features of the solver's concatenations (one image per
+// frequency, shared by every sample of that frequency) collect their
+// gradient summed over the samples that use them, and flow into the encoder.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <string>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "cnn_internal.cuh"
+#include "reduce.cuh"
+
+namespace helm {
+namespace {
+
+// out = bf16(G . [y > 0]) over cg gradient channels into cpad channels; when
+// res_grad is given, res_grad += the FP32 masked gradient (same layout as G).
+__global__ void mask_to_bf16_kernel(const float* __restrict__ G, int cg, const __nv_bfloat16* __restrict__ y,
+                                    int cy, int cpad, long long n, __nv_bfloat16* __restrict__ out,
+                                    float* __restrict__ res_grad) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * cpad;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / cpad;
+        const int c = (int)(i - p * cpad);
+        float v = 0.0f;
+        if (c < cg) {
+            v = G[p * cg + c];
+            if (y && !(__bfloat162float(y[p * cy + c]) > 0.0f)) v = 0.0f;
+            if (res_grad) res_grad[p * cg + c] += v;
+        }
+        out[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// Wt[ci][t][co] = W[co][flip ? 8 - t : t][off + ci]   (dgrad weights of one input part)
+__global__ void transpose_weights_kernel(const __nv_bfloat16* __restrict__ W, int npad, int cin_pad, int off,
+                                         int cpart, int flip, __nv_bfloat16* __restrict__ Wt) {
+    const int total = cpart * 9 * npad;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int co = i % npad, t = (i / npad) % 9, ci = i / (9 * npad);
+        Wt[i] = W[((size_t)co * 9 + (flip ? 8 - t : t)) * cin_pad + off + ci];
+    }
+}
+
+// coarse[b][i][j][c] += sum of the 2x2 block of fine[b][2i..2i+1][2j..2j+1][c]
+__global__ void sumpool_accum_kernel(const float* __restrict__ fine, int nb, int h, int w, int c,
+                                     float* __restrict__ coarse) {
+    const long long total = (long long)nb * h * w * c;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(i % c);
+        long long r = i / c;
+        const int x = (int)(r % w);
+        r /= w;
+        const int y = (int)(r % h);
+        const int b = (int)(r / h);
+        const size_t W2 = 2 * (size_t)w;
+        const size_t base = (((size_t)b * 2 * h + 2 * y) * W2 + 2 * x) * c + ch;
+        coarse[i] += fine[base] + fine[base + c] + fine[base + W2 * c] + fine[base + W2 * c + c];
+    }
+}
+
+// G_ctx[map(b)] += tmp[b]   (context images shared by several samples)
+__global__ void reduce_to_context_kernel(const float* __restrict__ tmp, long long per_image, int nb,
+                                         const int* __restrict__ map, int bcast, float* __restrict__ gctx) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per_image * nb;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(i / per_image);
+        const long long q = i - (long long)b * per_image;
+        const int f = bcast == 1 ? 0 : map[b];
+        atomicAdd(gctx + (long long)f * per_image + q, tmp[i]);
+    }
+}
+
+struct WgArgs {
+    const __nv_bfloat16* x0;
+    int c0;
+    const __nv_bfloat16* x1;
+    int c1;
+    int x1_bcast;
+    const int* x1_map;
+    int nb, hin, win, hout, wout, mode;
+    const __nv_bfloat16* g;   // [nb][hout][wout][npad]
+    int npad, cout, cin;      // cin: logical input channels (weights layout [cout][9][cin])
+    float* dW;
+    float* db;
+    long long ppb;            // pixels per block
+};
+
+__device__ __forceinline__ bool fwd_src(int mode, int o, int d, int n_in, int* i) {
+    int v;
+    if (mode == 0) v = o + d;
+    else if (mode == 1) v = 2 * o + 1 + d;
+    else {
+        const int u = o + d;
+        if (u < 0 || u >= 2 * n_in) return false;
+        *i = u >> 1;
+        return true;
+    }
+    if (v < 0 || v >= n_in) return false;
+    *i = v;
+    return true;
+}
+
+// dW[co][t][ci] += sum_p g[p][co] x_t[p][ci], db[co] += sum_p g[p][co]  (tile 16 co x 16 ci x 9 taps)
+__global__ void __launch_bounds__(256) wgrad_kernel(WgArgs a) {
+    constexpr int PP = 32;
+    __shared__ float gs[PP][16];
+    __shared__ float xs[PP][9][17];
+    const int tid = threadIdx.x;
+    const int co_l = tid >> 4, ci_l = tid & 15;
+    const int co0 = blockIdx.y * 16, ci0 = blockIdx.x * 16;
+    const long long ntot = (long long)a.nb * a.hout * a.wout;
+    const long long pb = (long long)blockIdx.z * a.ppb;
+    const long long pe = pb + a.ppb < ntot ? pb + a.ppb : ntot;
+    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float accb = 0.f;
+    const int ctot = a.c0 + a.c1;
+    for (long long p0 = pb; p0 < pe; p0 += PP) {
+        for (int i = tid; i < PP * 16; i += 256) {
+            const int pp = i >> 4, cc = i & 15;
+            const long long p = p0 + pp;
+            gs[pp][cc] = (p < pe && co0 + cc < a.npad) ? __bfloat162float(a.g[p * a.npad + co0 + cc]) : 0.0f;
+        }
+        for (int i = tid; i < PP * 144; i += 256) {
+            const int pp = i / 144, rem = i - pp * 144, t = rem >> 4, cc = rem & 15;
+            const long long p = p0 + pp;
+            const int ci = ci0 + cc;
+            float v = 0.0f;
+            if (p < pe && ci < ctot) {
+                const int b = (int)(p / ((long long)a.hout * a.wout));
+                const int r = (int)(p - (long long)b * a.hout * a.wout);
+                const int oy = r / a.wout, ox = r - oy * a.wout;
+                int iy, ix;
+                if (fwd_src(a.mode, oy, t / 3 - 1, a.hin, &iy) && fwd_src(a.mode, ox, t % 3 - 1, a.win, &ix)) {
+                    if (ci < a.c0) {
+                        v = __bfloat162float(a.x0[(((size_t)b * a.hin + iy) * a.win + ix) * a.c0 + ci]);
+                    } else {
+                        const int b1 = a.x1_map ? a.x1_map[b] : (a.x1_bcast ? 0 : b);
+                        v = __bfloat162float(a.x1[(((size_t)b1 * a.hin + iy) * a.win + ix) * a.c1 + (ci - a.c0)]);
+                    }
+                }
+            }
+            xs[pp][t][cc] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int pp = 0; pp < PP; ++pp) {
+            const float gv = gs[pp][co_l];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) acc[t] += gv * xs[pp][t][ci_l];
+            accb += gv;
+        }
+        __syncthreads();
+    }
+    const int co = co0 + co_l, ci = ci0 + ci_l;
+    if (co < a.cout && ci < a.cin) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) atomicAdd(a.dW + ((size_t)co * 9 + t) * a.cin + ci, acc[t]);
+    }
+    if (ci0 == 0 && ci_l == 0 && co < a.cout) atomicAdd(a.db + co, accb);
+}
+
+// loss = (1/m) sum ||e_net - e_true||^2 with e_net = h^2 rms (o_0 + i o_1); gout = dloss/do
+__global__ void mse_grad_kernel(const float* __restrict__ out, const float2* __restrict__ et,
+                                const float* __restrict__ rms, float h2, long long n, int nb, float inv_m,
+                                float* __restrict__ gout, double* __restrict__ loss) {
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nb;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(i / n);
+        const float s = h2 * rms[b];
+        const float dr = s * out[2 * i] - et[i].x, di = s * out[2 * i + 1] - et[i].y;
+        acc += (double)dr * dr + (double)di * di;
+        gout[2 * i] = 2.0f * inv_m * dr * s;
+        gout[2 * i + 1] = 2.0f * inv_m * di * s;
+    }
+    __shared__ double sm[32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[w];
+        atomicAdd(loss, t * (double)inv_m);
+    }
+}
+
+// Adam (Kingma & Ba, Alg. 1) on the flat FP32 parameters; clears the gradient
+__global__ void adam_kernel(float* __restrict__ th, float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float bc1,
+                            float bc2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        th[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        g[i] = 0.0f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the backward pass over a tape
+// ---------------------------------------------------------------------------
+class Backward {
+   public:
+    Backward(cnn_model* m, const helm_ctx* c, cudaStream_t st) : m_(m), c_(c), st_(st) {}
+    ~Backward() {
+        for (void* p : owned_) cudaFree(p);
+    }
+    bool ok() const { return ok_; }
+
+    // gradient buffer of an activation (allocated and zeroed on first use)
+    float* grad_of(const void* act, size_t n) {
+        auto it = G_.find(act);
+        if (it != G_.end()) return it->second;
+        float* p = (float*)alloc(n * sizeof(float));
+        if (!p) return nullptr;
+        if (cudaMemsetAsync(p, 0, n * sizeof(float), st_) != cudaSuccess) ok_ = false;
+        G_[act] = p;
+        return p;
+    }
+    void seed(const void* act, float* g) { G_[act] = g; }
+
+    int run(const std::vector<TapeOp>& tape, int nctx) {
+        std::unordered_set<const void*> produced;
+        for (const TapeOp& op : tape) produced.insert(op.y);
+        for (int k = (int)tape.size() - 1; k >= 0 && ok_; --k) {
+            const TapeOp& op = tape[k];
+            auto it = G_.find(op.y);
+            if (it == G_.end()) continue;
+            const float* Gy = it->second;
+            const Layer& L = m_->layers[op.layer];
+            const bool is_out = L.cout < 16;   // the 2-channel output layer (FP32 output, no activation)
+            const long long nout = (long long)op.nb * op.hout * op.wout;
+            const int cg = is_out ? L.cout : L.npad;
+            __nv_bfloat16* g = (__nv_bfloat16*)alloc((size_t)nout * L.npad * sizeof(__nv_bfloat16));
+            float* rg = op.res ? grad_of(op.res, (size_t)nout * L.npad) : nullptr;
+            if (!ok_) break;
+            {
+                LaunchScope scope(c_, K_CNN_IO);
+                mask_to_bf16_kernel<<<1184, 256, 0, st_>>>(Gy, cg, L.relu ? (const __nv_bfloat16*)op.y : nullptr,
+                                                          L.npad, L.npad, nout, g, rg);
+            }
+            // weight and bias gradient
+            {
+                WgArgs a;
+                a.x0 = op.x0; a.c0 = op.c0; a.x1 = op.x1; a.c1 = op.c1; a.x1_bcast = op.x1_bcast; a.x1_map = op.zmap;
+                a.nb = op.nb; a.hin = op.hin; a.win = op.win; a.hout = op.hout; a.wout = op.wout; a.mode = L.mode;
+                a.g = g; a.npad = L.npad; a.cout = L.cout; a.cin = L.cin;
+                a.dW = m_->grad + L.off;
+                a.db = m_->grad + L.off + (long long)L.cout * 9 * L.cin;
+                a.ppb = 2048;
+                dim3 grid((op.c0 + op.c1 + 15) / 16, (L.npad + 15) / 16, (unsigned)((nout + a.ppb - 1) / a.ppb));
+                LaunchScope scope(c_, K_WGRAD);
+                wgrad_kernel<<<grid, 256, 0, st_>>>(a);
+            }
+            if (cudaGetLastError() != cudaSuccess) { ok_ = false; break; }
+            // input gradients
+            for (int part = 0; part < 2 && ok_; ++part) {
+                const __nv_bfloat16* x = part ? op.x1 : op.x0;
+                const int cp = part ? op.c1 : op.c0;
+                if (!x || cp == 0 || !produced.count(x)) continue;
+                const int shared = part == 1 && op.x1_bcast != 0;
+                const long long nin = (long long)op.nb * op.hin * op.win;
+                __nv_bfloat16* Wt = (__nv_bfloat16*)alloc((size_t)cp * 9 * L.npad * sizeof(__nv_bfloat16));
+                if (!ok_) break;
+                {
+                    LaunchScope scope(c_, K_CNN_IO);
+                    transpose_weights_kernel<<<256, 256, 0, st_>>>(L.w, L.npad, L.cin_pad, part ? op.c0 : 0, cp,
+                                                                   L.mode == 1 ? 0 : 1, Wt);
+                }
+                float* target;
+                if (shared) {
+                    target = (float*)alloc((size_t)nin * cp * sizeof(float));
+                    if (target) cudaMemsetAsync(target, 0, (size_t)nin * cp * sizeof(float), st_);
+                } else {
+                    target = grad_of(x, (size_t)nin * cp);
+                }
+                if (!ok_ || !target) { ok_ = false; break; }
+                ConvArgs ca;
+                ca.x0 = g; ca.c0 = L.npad; ca.x1 = nullptr; ca.c1 = 0; ca.x1_bcast = 0; ca.x1_map = nullptr;
+                ca.nb = op.nb; ca.w = Wt; ca.bias = nullptr; ca.res = nullptr; ca.npad = cp; ca.cstore = cp;
+                ca.relu = 0; ca.out_fp32 = 1; ca.accum = 1; ca.err = m_->err;
+                int s = HELM_OK;
+                if (L.mode == 0) {
+                    ca.hin = op.hout; ca.win = op.wout; ca.hout = op.hin; ca.wout = op.win; ca.mode = 0; ca.y = target;
+                    LaunchScope scope(c_, K_CONV);
+                    s = launch_conv3x3(ca, st_);
+                } else if (L.mode == 1) {
+                    ca.hin = op.hout; ca.win = op.wout; ca.hout = op.hin; ca.wout = op.win; ca.mode = 3; ca.y = target;
+                    LaunchScope scope(c_, K_CONV);
+                    s = launch_conv3x3(ca, st_);
+                } else {
+                    float* fine = (float*)alloc((size_t)nout * cp * sizeof(float));
+                    if (!fine) { ok_ = false; break; }
+                    cudaMemsetAsync(fine, 0, (size_t)nout * cp * sizeof(float), st_);
+                    ca.hin = op.hout; ca.win = op.wout; ca.hout = op.hout; ca.wout = op.wout; ca.mode = 0; ca.y = fine;
+                    {
+                        LaunchScope scope(c_, K_CONV);
+                        s = launch_conv3x3(ca, st_);
+                    }
+                    LaunchScope scope(c_, K_CNN_IO);
+                    sumpool_accum_kernel<<<1184, 256, 0, st_>>>(fine, op.nb, op.hin, op.win, cp, target);
+                }
+                if (s != HELM_OK) { ok_ = false; break; }
+                if (shared) {
+                    const long long per = (long long)op.hin * op.win * cp;
+                    float* gctx = grad_of(x, (size_t)(op.x1_bcast == 1 ? 1 : nctx) * per);
+                    if (!gctx) { ok_ = false; break; }
+                    LaunchScope scope(c_, K_CNN_IO);
+                    reduce_to_context_kernel<<<1184, 256, 0, st_>>>(target, per, op.nb, op.zmap, op.x1_bcast, gctx);
+                }
+            }
+        }
+        if (cudaGetLastError() != cudaSuccess) ok_ = false;
+        return ok_ ? HELM_OK : HELM_ECUDA;
+    }
+
+   private:
+    void* alloc(size_t bytes) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+            (void)cudaGetLastError();
+            ok_ = false;
+            set_error("out of device memory in the backward pass");
+            return nullptr;
+        }
+        owned_.push_back(p);
+        return p;
+    }
+    cnn_model* m_;
+    const helm_ctx* c_;
+    cudaStream_t st_;
+    std::unordered_map<const void*, float*> G_;
+    std::vector<void*> owned_;
+    bool ok_ = true;
+};
+
+int ensure_train_state(cnn_model* m) {
+    if (m->grad) return HELM_OK;
+    const size_t n = (size_t)m->nparams;
+    HELM_CK(cudaMalloc(&m->grad, n * sizeof(float)));
+    HELM_CK(cudaMalloc(&m->adam_m, n * sizeof(float)));
+    HELM_CK(cudaMalloc(&m->adam_v, n * sizeof(float)));
+    m->allocations.push_back(m->grad);
+    m->allocations.push_back(m->adam_m);
+    m->allocations.push_back(m->adam_v);
+    HELM_CK(cudaMemset(m->grad, 0, n * sizeof(float)));
+    HELM_CK(cudaMemset(m->adam_m, 0, n * sizeof(float)));
+    HELM_CK(cudaMemset(m->adam_v, 0, n * sizeof(float)));
+    m->adam_t = 0;
+    return HELM_OK;
+}
+
+}  // namespace
+
+int cnn_refresh_weights(cnn_model* m, cudaStream_t st);   // cnn.cu
+int cnn_encoder_input(const helm_ctx* c, void* out);       // cnn.cu
+int cnn_solver_input(const helm_ctx* c, const float2* r, int nb, void* out, float* rms);   // cnn.cu
+
+// Loss (Eq. 4.2) and gradient (accumulated into net->grad) for a batch of
+// (residual, error) pairs of the context's medium.
+int cnn_loss_grad_impl(cnn_model* m, helm_ctx* c, const float2* r, const float2* e, int nb, double* loss) {
+    HELM_TRY(ensure_train_state(m));
+    cudaStream_t st = c->stream;
+    const long long n = (long long)c->nx * c->nz;
+    const int nfreq = c->nfreq;
+    __nv_bfloat16 *xe = nullptr, *xs = nullptr;
+    float *out = nullptr, *gout = nullptr, *rms = nullptr;
+    double* dloss = nullptr;
+    int s = HELM_OK;
+    auto ck = [&](cudaError_t e2) { if (e2 != cudaSuccess && s == HELM_OK) { set_error(cudaGetErrorString(e2)); s = HELM_ECUDA; } };
+    ck(cudaMalloc(&xe, (size_t)nfreq * n * 16 * sizeof(__nv_bfloat16)));
+    ck(cudaMalloc(&xs, (size_t)nb * n * 16 * sizeof(__nv_bfloat16)));
+    ck(cudaMalloc(&out, (size_t)nb * n * 2 * sizeof(float)));
+    ck(cudaMalloc(&gout, (size_t)nb * n * 2 * sizeof(float)));
+    ck(cudaMalloc(&rms, (size_t)nb * sizeof(float)));
+    ck(cudaMalloc(&dloss, sizeof(double)));
+    if (!s) ck(cudaMemsetAsync(dloss, 0, sizeof(double), st));
+    if (!s) s = cnn_encoder_input(c, xe);
+    if (!s) s = cnn_solver_input(c, r, nb, xs, rms);
+    std::vector<TapeOp> tape;
+    if (!s) {
+        Runner run(m, c, st);   // activations live until the backward pass is done
+        run.set_tape(&tape);
+        run.set_zmap(c->rhs_freq);
+        std::vector<__nv_bfloat16*> z;
+        if (!run.encoder(xe, nfreq, c->nz, c->nx, z)) s = HELM_ECUDA;
+        if (!s && !run.solver(xs, nb, c->nz, c->nx, z, 2, out)) s = HELM_ECUDA;
+        if (!s) {
+            LaunchScope scope(c, K_CNN_IO);
+            mse_grad_kernel<<<1184, 256, 0, st>>>(out, e, rms, c->hx * c->hz, n, nb, 1.0f / (float)nb, gout, dloss);
+            ck(cudaGetLastError());
+        }
+        if (!s) {
+            Backward bw(m, c, st);
+            bw.seed(out, gout);
+            s = bw.run(tape, nfreq);
+            ck(cudaStreamSynchronize(st));
+        }
+        // the encoder's context features were handed over to us
+        for (__nv_bfloat16* p : z) cudaFree(p);
+    }
+    if (!s) s = check_conv_error(m, st);
+    if (!s && loss) ck(cudaMemcpy(loss, dloss, sizeof(double), cudaMemcpyDeviceToHost));
+    cudaFree(xe); cudaFree(xs); cudaFree(out); cudaFree(gout); cudaFree(rms); cudaFree(dloss);
+    return s;
+}
+
+int cnn_adam_impl(cnn_model* m, float lr, cudaStream_t st) {
+    HELM_TRY(ensure_train_state(m));
+    m->adam_t += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const float bc1 = (float)(1.0 - std::pow(b1, (double)m->adam_t));
+    const float bc2 = (float)(1.0 - std::pow(b2, (double)m->adam_t));
+    adam_kernel<<<1184, 256, 0, st>>>(m->master, m->grad, m->adam_m, m->adam_v, m->nparams, lr, (float)b1, (float)b2,
+                                      1e-8f, bc1, bc2);
+    HELM_CK(cudaGetLastError());
+    return cnn_refresh_weights(m, st);
+}
+
+}  // namespace helm
+
+using namespace helm;
+
+namespace {
+
+int upload_freqs(helm_ctx* c, const int* freq_idx, int nb) {
+    if (nb > c->cap) { set_error("batch larger than the context's max_rhs"); return HELM_EINVAL; }
+    std::vector<int> f(nb, 0);
+    if (freq_idx)
+        for (int i = 0; i < nb; ++i) {
+            if (freq_idx[i] < 0 || freq_idx[i] >= c->nfreq) { set_error("freq_idx outside [0, nfreq)"); return HELM_EINVAL; }
+            f[i] = freq_idx[i];
+        }
+    HELM_CK(cudaMemcpyAsync(c->rhs_freq, f.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    HELM_CK(cudaStreamSynchronize(c->stream));
+    return HELM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cnn_loss_grad(cnn_model* net, helm_ctx* c, const helm_c64* r, const helm_c64* e, const int* freq_idx, int nb,
+                  double* loss, float* grad_out) {
+    set_error("");
+    if (!net || !c || !r || !e || nb < 1) { set_error("cnn_loss_grad: invalid argument"); return HELM_EINVAL; }
+    HELM_TRY(upload_freqs(c, freq_idx, nb));
+    HELM_TRY(ensure_train_state(net));
+    const size_t n = (size_t)c->nx * c->nz;
+    float2 *dr = nullptr, *de = nullptr;
+    HELM_CK(cudaMalloc(&dr, nb * n * sizeof(float2)));
+    if (cudaMalloc(&de, nb * n * sizeof(float2)) != cudaSuccess) { cudaFree(dr); set_error("cudaMalloc"); return HELM_ENOMEM; }
+    int s = HELM_OK;
+    if (cudaMemcpy(dr, r, nb * n * sizeof(float2), cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(de, e, nb * n * sizeof(float2), cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemsetAsync(net->grad, 0, net->nparams * sizeof(float), c->stream) != cudaSuccess) {
+        set_error("cnn_loss_grad: copy failed");
+        s = HELM_ECUDA;
+    }
+    if (!s) s = cnn_loss_grad_impl(net, c, dr, de, nb, loss);
+    if (!s && grad_out && cudaMemcpy(grad_out, net->grad, net->nparams * sizeof(float), cudaMemcpyDefault) != cudaSuccess) {
+        set_error("cnn_loss_grad: gradient copy failed");
+        s = HELM_ECUDA;
+    }
+    cudaFree(dr);
+    cudaFree(de);
+    return s;
+}
+
+int cnn_train_step(cnn_model* net, helm_ctx* c, const helm_c64* r, const helm_c64* e, const int* freq_idx, int nb,
+                   float lr, double* loss) {
+    int s = cnn_loss_grad(net, c, r, e, freq_idx, nb, loss, nullptr);
+    if (s) return s;
+    HELM_TRY(cnn_adam_impl(net, lr, c->stream));
+    HELM_CK(cudaStreamSynchronize(c->stream));
+    // the context's preconditioner sees the updated network
+    if (c->net == net) HELM_TRY(cnn_ctx_setup(c));
+    return HELM_OK;
+}
+
+int cnn_adam_reset(cnn_model* net) {
+    set_error("");
+    if (!net) { set_error("cnn_adam_reset: null network"); return HELM_EINVAL; }
+    HELM_TRY(ensure_train_state(net));
+    HELM_CK(cudaMemset(net->adam_m, 0, net->nparams * sizeof(float)));
+    HELM_CK(cudaMemset(net->adam_v, 0, net->nparams * sizeof(float)));
+    HELM_CK(cudaMemset(net->grad, 0, net->nparams * sizeof(float)));
+    net->adam_t = 0;
+    return HELM_OK;
+}
+
+}  // extern "C"

@@ -15,7 +15,9 @@ struct ConvArgs {
     int x1_bcast;              // 1: x1 has one image shared by the whole batch
     const int* x1_map;         // or: image of x1 used by output image b (device array), else b
     int nb, hin, win, hout, wout;
-    int mode;                  // 0 same, 1 down (output node (Y,X) on input node (2Y+1,2X+1)), 2 up (nearest x2)
+    int mode;                  // 0 same, 1 down (output node (Y,X) on input node (2Y+1,2X+1)), 2 up (nearest x2),
+                               // 3 transpose of down: output on the fine grid, tap d of output node f reads
+                               //   input node (f - 1 - d) / 2 when that is an integer inside the input
     const __nv_bfloat16* w;    // [npad][9][c0 + c1]
     const float* bias;         // [npad]
     const __nv_bfloat16* res;  // [nb][hout][wout][npad] added before the activation, or nullptr
@@ -24,6 +26,7 @@ struct ConvArgs {
     int cstore;                // channels stored when out_fp32
     int relu;
     int out_fp32;
+    int accum;                 // with out_fp32: y += result (no bias, no activation)
     int* err;                  // set to 1 when a bounded wait expires
 };
 

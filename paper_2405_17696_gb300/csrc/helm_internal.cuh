@@ -188,7 +188,7 @@ struct OuterState {
 enum KernelId {
     K_APPLY = 0, K_RESIDUAL64, K_DOTS_FINE, K_DOTS_COARSE, K_UPDATE_FINE, K_UPDATE_COARSE, K_KINIT, K_LSQ,
     K_COMBINE, K_UPDATE_X, K_JACOBI_FINE, K_JACOBI_COARSE, K_RESTRICT_FINE, K_RESTRICT_COARSE, K_PROLONG,
-    K_GALERKIN, K_COPY, K_RESTART, K_COARSE_GMRES, K_CONV, K_CNN_IO, K_MISC, K_COUNT
+    K_GALERKIN, K_COPY, K_RESTART, K_COARSE_GMRES, K_CONV, K_CNN_IO, K_WGRAD, K_MISC, K_COUNT
 };
 const char* kernel_name(int id);
 

@@ -38,7 +38,11 @@ __device__ __forceinline__ bool src_coord(int mode, int o, int d, int n_in, int*
     int v;
     if (mode == 0) v = o + d;
     else if (mode == 1) v = 2 * o + 1 + d;
-    else {
+    else if (mode == 3) {
+        const int u = o - 1 - d;
+        if (u < 0 || (u & 1)) return false;
+        v = u >> 1;
+    } else {
         int u = o + d;
         if (u < 0 || u >= 2 * n_in) return false;
         *i = u >> 1;
@@ -180,8 +184,10 @@ __global__ void __launch_bounds__(CT) conv3x3_tc_kernel(ConvArgs a) {
         float v[16];
         tc::tmem_ld16(trow + col0, v);
         if (!valid) continue;
+        if (!a.accum) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] += __ldg(a.bias + col0 + i);
+            for (int i = 0; i < 16; ++i) v[i] += __ldg(a.bias + col0 + i);
+        }
         if (a.res) {
             const uint4* rp = reinterpret_cast<const uint4*>(a.res + (size_t)p * a.npad + col0);
             uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
@@ -199,8 +205,13 @@ __global__ void __launch_bounds__(CT) conv3x3_tc_kernel(ConvArgs a) {
         }
         if (a.out_fp32) {
             float* yo = reinterpret_cast<float*>(a.y) + (size_t)p * a.cstore;
-            for (int i = 0; i < 16; ++i)
-                if (col0 + i < a.cstore) yo[col0 + i] = v[i];
+            if (a.accum) {
+                for (int i = 0; i < 16; ++i)
+                    if (col0 + i < a.cstore) yo[col0 + i] += v[i];
+            } else {
+                for (int i = 0; i < 16; ++i)
+                    if (col0 + i < a.cstore) yo[col0 + i] = v[i];
+            }
         } else {
             uint4 o0, o1;
             __nv_bfloat16* ob0 = reinterpret_cast<__nv_bfloat16*>(&o0);
@@ -243,11 +254,12 @@ int launch_conv3x3(const ConvArgs& a, cudaStream_t st) {
         set_error("conv3x3: output channels must be padded to 16, 32, 64 or 128");
         return HELM_EINVAL;
     }
-    if (a.c0 % 16 || a.c1 % 16 || cin < 16 || !a.x0 || (a.c1 && !a.x1) || !a.w || !a.bias || !a.y || !a.err) {
+    if (a.c0 % 16 || a.c1 % 16 || cin < 16 || !a.x0 || (a.c1 && !a.x1) || !a.w || !a.y || !a.err) {
         set_error("conv3x3: input channels must be multiples of 16 and pointers non-null");
         return HELM_EINVAL;
     }
-    if (a.nb < 1 || a.hin < 1 || a.win < 1 || a.mode < 0 || a.mode > 2) {
+    if (a.nb < 1 || a.hin < 1 || a.win < 1 || a.mode < 0 || a.mode > 3 || (a.accum && !a.out_fp32) ||
+        (!a.accum && !a.bias)) {
         set_error("conv3x3: bad shape or mode");
         return HELM_EINVAL;
     }

@@ -81,6 +81,16 @@ def _load():
     lib.cnn_get_params.restype = ip
     lib.cnn_forward.argtypes = [vp, vp, ip, vp, ip, ip, ip, vp]
     lib.cnn_forward.restype = ip
+    lib.cnn_make_samples.argtypes = [vp, vp, vp, vp, ip, vp, vp]
+    lib.cnn_make_samples.restype = ip
+    lib.cnn_refine_samples.argtypes = [vp, vp, vp, vp, ip, ip, vp, vp]
+    lib.cnn_refine_samples.restype = ip
+    lib.cnn_loss_grad.argtypes = [vp, vp, vp, vp, vp, ip, ctypes.POINTER(ctypes.c_double), vp]
+    lib.cnn_loss_grad.restype = ip
+    lib.cnn_train_step.argtypes = [vp, vp, vp, vp, vp, ip, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+    lib.cnn_train_step.restype = ip
+    lib.cnn_adam_reset.argtypes = [vp]
+    lib.cnn_adam_reset.restype = ip
     lib.cnn_precond_apply.argtypes = [vp, vp, vp, ip, vp, ip]
     lib.cnn_precond_apply.restype = ip
     lib.cnn_conv3x3.argtypes = [vp, ip, vp, ip, ip, ip, ip, ip, vp, vp, ip, vp, ip, ip, vp]
@@ -299,3 +309,36 @@ def cnn_precond_apply(ctx, r, e, nrhs: int, freq_idx=None, with_vcycle: int = 1)
     _keep, fptr = _int_array(freq_idx, nrhs)
     _check(lib.cnn_precond_apply(ctx, _ptr(r, "complex64"), _ptr(e, "complex64"), nrhs, fptr, with_vcycle),
            "cnn_precond_apply")
+
+
+def cnn_make_samples(ctx, x, iters, r_out, e_out, nb: int, freq_idx=None):
+    _keep, fptr = _int_array(freq_idx, nb)
+    it = np.ascontiguousarray(np.asarray(iters, dtype=np.int32))
+    _check(lib.cnn_make_samples(ctx, _ptr(x, "complex64"), fptr, it.ctypes.data, nb, _ptr(r_out, "complex64"),
+                                _ptr(e_out, "complex64")), "cnn_make_samples")
+
+
+def cnn_refine_samples(ctx, r, e, r_out, e_out, nb: int, freq_idx=None, literal: int = 0):
+    _keep, fptr = _int_array(freq_idx, nb)
+    _check(lib.cnn_refine_samples(ctx, _ptr(r, "complex64"), _ptr(e, "complex64"), fptr, nb, literal,
+                                  _ptr(r_out, "complex64"), _ptr(e_out, "complex64")), "cnn_refine_samples")
+
+
+def cnn_loss_grad(net, ctx, r, e, nb: int, freq_idx=None, grad_out=None) -> float:
+    _keep, fptr = _int_array(freq_idx, nb)
+    loss = ctypes.c_double(0.0)
+    _check(lib.cnn_loss_grad(net, ctx, _ptr(r, "complex64"), _ptr(e, "complex64"), fptr, nb, ctypes.byref(loss),
+                             _ptr(grad_out, "float32")), "cnn_loss_grad")
+    return loss.value
+
+
+def cnn_train_step(net, ctx, r, e, nb: int, lr: float, freq_idx=None) -> float:
+    _keep, fptr = _int_array(freq_idx, nb)
+    loss = ctypes.c_double(0.0)
+    _check(lib.cnn_train_step(net, ctx, _ptr(r, "complex64"), _ptr(e, "complex64"), fptr, nb, lr,
+                              ctypes.byref(loss)), "cnn_train_step")
+    return loss.value
+
+
+def cnn_adam_reset(net):
+    _check(lib.cnn_adam_reset(net), "cnn_adam_reset")

@@ -1,0 +1,152 @@
+"""GPU parity of the training path (Sec. 4.1-4.2, Eq. 4.2-4.3, Alg. 2) against
+the oracle, through the C ABI.
+
+* Eq. 4.3 data: r and e from fixed-step V-cycle-preconditioned FGMRES equal the
+  oracle's, and H e = r holds for every generated pair;
+* Alg. 2 data step in both readings keeps H e = r;
+* the loss of Eq. 4.2 and its gradient (hand-written BF16 backward on the
+  tensor cores, FP32 weight gradients) agree with the oracle's float64
+  backward through the same BF16-rounded forward;
+* Adam steps on the GPU lower the loss.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import cnn, helmholtz as H, training as T  # noqa: E402
+from paper_2405_17696_gb300 import media  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def native():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_17696_gb300 import build
+    build.build()
+    from paper_2405_17696_gb300 import native as n
+    return n
+
+
+def _setup(native, w, widths=None, theta=None, **opts):
+    net = None
+    if widths is not None:
+        net = native.cnn_create(len(widths), widths)
+        native.cnn_set_params(net, theta.astype(np.float32))
+        opts.setdefault("precond", native.HELM_PC_CNN)
+    o = native.helm_default_opts(**opts)
+    om = torch.from_numpy(np.asarray(w.omegas, dtype=np.float32)).cuda()
+    ctx = native.helm_setup(torch.from_numpy(w.kappa).cuda(), torch.from_numpy(w.gamma).cuda(), w.nx, w.nz, w.h,
+                            w.h, om, net=net, opts=o)
+    return net, ctx
+
+
+def _f64(a):
+    return np.asarray(a, dtype=np.float64)
+
+
+def _pair_defect_ok(e, r, kap, gam, om, h):
+    """H e = r up to the complex64 storage of e: |H e - r| <= 1e-6 || (|H| |e|) ||
+    (unit roundoff 6e-8 with a margin; e is O(1) while r may be 1e-4 of H e's terms)."""
+    e64 = e.astype(np.complex128)
+    he = H.helmholtz_apply(e64, kap, gam, om, h, h)
+    coef = np.abs(H.helmholtz_coefficient(kap, gam, om))
+    scale = np.linalg.norm((8.0 / h ** 2 + coef) * np.abs(e64))
+    return np.linalg.norm(he - r) <= 1e-6 * scale
+
+
+def test_make_samples_parity(native):
+    w = media.crop_workload(64, 32, freqs=(5.0,), width=8)
+    x = media.complex_normal((4, w.nz, w.nx), seed=media.SEED_DATAGEN)
+    iters = [1, 3, 5, 10]
+    _, ctx = _setup(native, w, mg_levels=3)
+    try:
+        r = np.zeros_like(x)
+        e = np.zeros_like(x)
+        native.cnn_make_samples(ctx, x, iters, r, e, 4)
+    finally:
+        native.helm_destroy(ctx)
+    om = float(np.float32(w.omegas[0]))
+    kap, gam = _f64(w.kappa), _f64(w.gamma)
+    r_ref, e_ref = T.make_samples(kap, gam, om, w.h, x, iters)
+    for i in range(4):
+        # e is the small remainder x - x~: compare the iterate x~ (relative 1e-5)
+        assert np.linalg.norm(e[i] - e_ref[i]) <= 1e-5 * np.linalg.norm(x[i] - e_ref[i]), i
+        assert np.linalg.norm(r[i] - r_ref[i]) <= 2e-3 * np.linalg.norm(r_ref[i]), i
+        assert _pair_defect_ok(e[i], r[i], kap, gam, om, w.h), i
+
+
+@pytest.mark.parametrize("literal", [0, 1])
+def test_refine_samples_keep_pairs_consistent(native, literal):
+    w = media.crop_workload(64, 32, freqs=(5.0,), width=8)
+    specs = cnn.layer_specs(widths=(16, 32))
+    theta = 0.5 * cnn.he_init(specs, seed=1)
+    net, ctx = _setup(native, w, widths=(16, 32), theta=theta, mg_levels=3)
+    try:
+        x = media.complex_normal((3, w.nz, w.nx), seed=7)
+        r = np.zeros_like(x)
+        e = np.zeros_like(x)
+        native.cnn_make_samples(ctx, x, [2, 2, 2], r, e, 3)
+        r2 = np.zeros_like(x)
+        e2 = np.zeros_like(x)
+        native.cnn_refine_samples(ctx, r, e, r2, e2, 3, literal=literal)
+    finally:
+        native.helm_destroy(ctx)
+        native.cnn_destroy(net)
+    om = float(np.float32(w.omegas[0]))
+    kap, gam = _f64(w.kappa), _f64(w.gamma)
+    for i in range(3):
+        assert _pair_defect_ok(e2[i], r2[i], kap, gam, om, w.h), i
+        assert np.linalg.norm(r2[i]) > 0
+
+
+def test_loss_and_gradient_parity(native):
+    w = media.crop_workload(32, 32, freqs=(5.0,), width=6)
+    widths = (16, 32)
+    specs = cnn.layer_specs(widths=widths)
+    g = np.random.default_rng(5)
+    theta = 0.5 * cnn.he_init(specs, seed=3) + 0.01 * g.normal(size=cnn.n_params(specs))
+    r = media.complex_normal((2, w.nz, w.nx), seed=8)
+    e = media.complex_normal((2, w.nz, w.nx), seed=9) * 20.0
+    net, ctx = _setup(native, w, widths=widths, theta=theta, mg_levels=2)
+    try:
+        grad = np.zeros(theta.size, np.float32)
+        loss = native.cnn_loss_grad(net, ctx, r, e, 2, grad_out=grad)
+    finally:
+        native.helm_destroy(ctx)
+        native.cnn_destroy(net)
+    om = float(np.float32(w.omegas[0]))
+    P = cnn.unflatten(cnn.bf16_round(theta), specs)
+    loss_ref, grads = T.loss_and_grad(P, specs, _f64(w.kappa), _f64(w.gamma), om, w.h, r, e,
+                                      quantize=cnn.bf16_round)
+    gref = cnn.flatten_grads(grads, specs)
+    assert abs(loss - loss_ref) <= 1e-2 * loss_ref, (loss, loss_ref)
+    rel = np.linalg.norm(grad - gref) / np.linalg.norm(gref)
+    cos = float(grad @ gref / (np.linalg.norm(grad) * np.linalg.norm(gref)))
+    assert rel <= 5e-2 and cos >= 0.998, (rel, cos)
+    # every layer, encoder included, receives gradient
+    o = 0
+    for name, ci, co, _ in specs:
+        n = co * 9 * ci
+        assert np.any(grad[o:o + n] != 0), name
+        o += n + co
+
+
+def test_adam_steps_lower_the_loss(native):
+    w = media.crop_workload(64, 32, freqs=(5.0,), width=8)
+    widths = (16, 32, 64)
+    specs = cnn.layer_specs(widths=widths)
+    theta = 0.5 * cnn.he_init(specs, seed=media.SEED_CNN)
+    net, ctx = _setup(native, w, widths=widths, theta=theta, mg_levels=3)
+    try:
+        x = media.complex_normal((8, w.nz, w.nx), seed=media.SEED_DATAGEN)
+        r = torch.zeros((8, w.nz, w.nx), dtype=torch.complex64, device="cuda")
+        e = torch.zeros_like(r)
+        native.cnn_make_samples(ctx, torch.from_numpy(x).cuda(), [3] * 8, r, e, 8)
+        losses = [native.cnn_train_step(net, ctx, r, e, 8, 1e-3) for _ in range(30)]
+    finally:
+        native.helm_destroy(ctx)
+        native.cnn_destroy(net)
+    assert np.mean(losses[-5:]) < 0.9 * losses[0], losses

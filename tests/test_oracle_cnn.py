@@ -122,3 +122,26 @@ def test_bf16_rounding_matches_torch():
                         [1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, -1 - 2 ** -8, 0.0, -0.0]])
     ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(cnn.bf16_round(x), ref)
+
+
+def test_training_data_and_loss_gradient():
+    # Eq. 4.3 pairs satisfy H e = r exactly; the Eq. 4.2 loss gradient (through
+    # the rms scaling of the network input and output) matches finite differences
+    from oracle import helmholtz as H, training as T
+    from paper_2405_17696_gb300 import media
+    w = media.crop_workload(16, 16, freqs=(5.0,), width=4)
+    kap, gam, om = w.kappa.astype(float), w.gamma.astype(float), w.omegas[0]
+    x = media.complex_normal((2, w.nz, w.nx), seed=3)
+    r, e = T.make_samples(kap, gam, om, w.h, x, [1, 3], params=None)
+    for i in range(2):
+        assert np.linalg.norm(H.helmholtz_apply(e[i], kap, gam, om, w.h, w.h) - r[i]) <= 1e-10 * np.linalg.norm(r[i])
+    specs = cnn.layer_specs(widths=(2, 4))
+    theta = 0.5 * cnn.he_init(specs, seed=4) + 0.02 * _rng(5).normal(size=cnn.n_params(specs))
+    loss, grads = T.loss_and_grad(cnn.unflatten(theta, specs), specs, kap, gam, om, w.h, r, e)
+    gflat = cnn.flatten_grads(grads, specs)
+    d = _rng(6).normal(size=theta.size)
+    eps = 1e-8
+    lp = T.loss_and_grad(cnn.unflatten(theta + eps * d, specs), specs, kap, gam, om, w.h, r, e)[0]
+    lm = T.loss_and_grad(cnn.unflatten(theta - eps * d, specs), specs, kap, gam, om, w.h, r, e)[0]
+    fd = (lp - lm) / (2 * eps)
+    assert abs(fd - gflat @ d) <= 1e-5 * abs(fd)
