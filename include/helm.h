@@ -77,6 +77,8 @@ typedef struct {
     int   coarse_iters;     /* steps of the coarsest-level solve            (10)  */
     int   precond;          /* HELM_PC_MG, HELM_PC_CNN or HELM_PC_NONE          */
     int   max_rhs;          /* RHS per device batch; larger calls are chunked (256) */
+    int   cnn_vcycle;       /* M_VU composition (Eq. 3.14): 0 = e_0 + V(r - H e_0), 1 = V-cycle
+                               on P u = r from u_0 = e_0                                  (0) */
     void* stream;           /* cudaStream_t for all work of the context   (NULL) */
 } helm_opts;
 
@@ -193,7 +195,9 @@ void helm_destroy(helm_ctx* ctx);
  * Solver (input [Re r^, Im r^, gamma], r^ = r / rms(r)): the same shape, with
  * the context z_l concatenated (and reduced by a conv) at every level of the
  * way down, and an output conv to 2 channels.  The preconditioner (Eq. 3.14)
- * is M_VU(r) = V-cycle(e_0, r) with e_0 = h^2 rms(r) (out_0 + i out_1).
+ * is M_VU(r) = V-cycle(e_0, r) with e_0 = h^2 rms(r) (out_0 + i out_1), composed as
+ * e_0 + V(r - H e_0) by default (opts.cnn_vcycle = 0: exact when e_0 = H^-1 r, plain
+ * multigrid when e_0 = 0) or as a V-cycle on P from the initial guess e_0 (cnn_vcycle = 1).
  * Convolutions are 3x3 implicit GEMMs on the tensor cores (tcgen05, BF16
  * operands, FP32 accumulation in tensor memory).
  * Parameters are one flat FP32 vector: per layer weights [cout][9][cin] then
@@ -212,7 +216,8 @@ int cnn_get_params(const cnn_model* net, float* params, long long n);
 int cnn_forward(cnn_model* net, const float* enc_in, int nenc, const float* sol_in, int nsol, int ny, int nx,
                 float* out);
 /* The network preconditioner of a context created with a network (Eq. 3.14):
- * e = V-cycle(e_0 = h^2 rms(r) net(r / rms(r)), r) for with_vcycle = 1, or e = e_0.
+ * e = M_VU(r) (composed as opts.cnn_vcycle selects) for with_vcycle = 1, or
+ * e = e_0 = h^2 rms(r) net(r / rms(r)) for with_vcycle = 0.
  * r, e : complex64 [nrhs][nz][nx] (host or device); freq_idx as in helm_solve. */
 int cnn_precond_apply(helm_ctx* ctx, const helm_c64* r, helm_c64* e, int nrhs, const int* freq_idx,
                       int with_vcycle);

@@ -33,7 +33,8 @@ Solver (input: 3 channels [Re r^, Im r^, gamma], r^ = r / rms(r)):
            up conv + relu, concat [., s_l], conv 2c_l->c_l + relu, ResNet -> t_l
   out conv c0->2 (no activation): [Re, Im] of the error estimate
 Preconditioner (Eq. 3.14 with the scaling that makes it 1-homogeneous):
-  e_0 = h^2 rms(r) (out_re + i out_im)(r / rms(r)),  M_VU(r) = V-cycle(e_0, r).
+  e_0 = h^2 rms(r) (out_re + i out_im)(r / rms(r)); the composition with the
+  V-cycle is `training.mvu_compose`.
 """
 from __future__ import annotations
 

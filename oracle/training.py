@@ -9,6 +9,8 @@ TEST INFRASTRUCTURE: see the package header for who may import this.
   after one step; new pair (r - H e~, e - e~) in the residual-correction
   reading, or (H e~, e~) as printed.
 * Eq. 4.2: loss = (1/m) sum_i ||e_net(r_i) - e_i||^2, e_net = h^2 rms(r) out.
+* Eq. 3.14: M_VU(r) = e_0 + V(r - H e_0) (the V-cycle corrects the residual the
+  network leaves), or a V-cycle on P started from u_0 = e_0.
 """
 from __future__ import annotations
 
@@ -31,6 +33,18 @@ def make_samples(kappa, gamma, omega, h, x, iters, params=None):
         rs.append(b - A(xt))
         es.append(xi - xt)
     return np.stack(rs), np.stack(es)
+
+
+def mvu_compose(e0, r, A, pc, composition: str = "residual"):
+    """M_VU of Eq. 3.14 for one residual, given the network's estimate e0.
+
+    ``residual``: e0 + V(r - H e0, 0): exact when e0 = H^-1 r, the plain V-cycle
+    when e0 = 0.  ``initial_guess``: V(r, u_0 = e0) on the shifted operator."""
+    if composition == "residual":
+        return e0 + pc(r - A(e0))
+    if composition == "initial_guess":
+        return pc(r, e0)
+    raise ValueError(composition)
 
 
 def network_error(P, specs, kappa, gamma, omega, h, r, quantize=None):

@@ -339,7 +339,18 @@ __global__ void diff_kernel(const float2* __restrict__ a, const double2* __restr
     }
 }
 
-__global__ void negate_kernel(const float2* __restrict__ a, float2* __restrict__ out, size_t n) {
+// d = a - b in FP64 (complex64 minus complex128): b <- d, out <- complex64(d)
+__global__ void diff64_kernel(const float2* __restrict__ a, double2* __restrict__ b, float2* __restrict__ out,
+                              size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double2 v = b[i];
+        double2 d = make_double2((double)a[i].x - v.x, (double)a[i].y - v.y);
+        b[i] = d;
+        out[i] = make_float2((float)d.x, (float)d.y);
+    }
+}
+
+__global__ void negate_kernel(const float2* a, float2* out, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         out[i] = make_float2(-a[i].x, -a[i].y);
 }
@@ -388,6 +399,7 @@ void helm_default_opts(helm_opts* o) {
     o->coarse_iters = 10;
     o->precond = HELM_PC_MG;
     o->max_rhs = 256;
+    o->cnn_vcycle = 0;
     o->stream = nullptr;
 }
 
@@ -775,11 +787,20 @@ int cnn_make_samples(helm_ctx* c, const helm_c64* x, const int* freq_idx, const 
     if (!s) ck(cudaMemsetAsync(xt, 0, nb * N * sizeof(double2), c->stream));
     if (!s) s = launch_apply_fine(c, fine_op(c, 0), dx, db, nb, c->ones);          // b = H x
     if (!s) s = fixed_step_solve(c, db, xt, nb, iters);                            // x~ (Eq. 4.3)
-    if (!s) s = launch_outer_init(c, nb);
-    if (!s) s = launch_residual64(c, xt, db, dr, nb, 0, 1);                        // r = b - H x~
+    // r = b - H x~ = H e: formed as H e in FP64 from e = x - x~, so that the stored
+    // pair satisfies H e = r up to its own complex64 rounding (b in complex64
+    // carries a rounding of |H| |x| u, far above r once GMRES has converged)
     if (!s) {
         LaunchScope scope(c, K_MISC);
-        diff_kernel<<<1184, 256, 0, c->stream>>>(dx, xt, de, nb * N);              // e = x - x~
+        diff64_kernel<<<1184, 256, 0, c->stream>>>(dx, xt, de, nb * N);            // e = x - x~
+        ck(cudaGetLastError());
+    }
+    if (!s) ck(cudaMemsetAsync(db, 0, nb * N * sizeof(float2), c->stream));
+    if (!s) s = launch_outer_init(c, nb);
+    if (!s) s = launch_residual64(c, xt, db, dr, nb, 0, 1);                        // -H e
+    if (!s) {
+        LaunchScope scope(c, K_MISC);
+        negate_kernel<<<1184, 256, 0, c->stream>>>(dr, dr, nb * N);                // r = H e
         ck(cudaGetLastError());
     }
     if (!s) ck(cudaMemcpyAsync(r_out, dr, nb * N * sizeof(float2), cudaMemcpyDefault, c->stream));

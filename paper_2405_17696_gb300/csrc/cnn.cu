@@ -205,6 +205,26 @@ __global__ void solver_input_kernel(const float2* __restrict__ r, const float* _
     }
 }
 
+// r' = r - H e0 (FP32, complex64): the residual the network leaves
+__global__ void net_residual_kernel(OpFine5 op, const float2* __restrict__ r, const float2* __restrict__ e0,
+                                    float2* __restrict__ out, int nb) {
+    const long long n = (long long)op.nx * op.nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nb;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(i / n);
+        const int p = (int)(i - (long long)b * n);
+        const int iz = p / op.nx, ix = p - iz * op.nx;
+        const float2 he = op.apply(e0 + (long long)b * n, b, ix, iz);
+        out[i] = make_float2(r[i].x - he.x, r[i].y - he.y);
+    }
+}
+
+// z += e0
+__global__ void add_kernel(float2* __restrict__ z, const float2* __restrict__ e0, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        z[i] = make_float2(z[i].x + e0[i].x, z[i].y + e0[i].y);
+}
+
 // e0 = h^2 rms (out_0 + i out_1)
 __global__ void solver_output_kernel(const float* __restrict__ out, const float* __restrict__ rms, float h2,
                                      long long n, int nb, float2* __restrict__ e0) {
@@ -259,7 +279,9 @@ void cnn_ctx_free(helm_ctx* c) {
     cudaFree(c->cnn_in);
     cudaFree(c->cnn_out);
     cudaFree(c->cnn_e0);
+    cudaFree(c->cnn_rres);
     cudaFree(c->cnn_rms);
+    c->cnn_rres = nullptr;
     c->cnn_in = nullptr;
     c->cnn_out = nullptr;
     c->cnn_e0 = nullptr;
@@ -278,6 +300,7 @@ int cnn_ctx_setup(helm_ctx* c) {
         HELM_CK(cudaMalloc(&c->cnn_in, (size_t)std::max<long long>(c->cap, c->nfreq) * n * 16 * sizeof(__nv_bfloat16)));
         HELM_CK(cudaMalloc(&c->cnn_out, (size_t)c->cap * n * 2 * sizeof(float)));
         HELM_CK(cudaMalloc(&c->cnn_e0, (size_t)c->cap * n * sizeof(float2)));
+        HELM_CK(cudaMalloc(&c->cnn_rres, (size_t)c->cap * n * sizeof(float2)));
         HELM_CK(cudaMalloc(&c->cnn_rms, (size_t)c->cap * sizeof(float)));
     }
     for (void* p : c->cnn_z) cudaFree(p);
@@ -327,7 +350,20 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
         HELM_CK(cudaGetLastError());
     }
     if (!with_vcycle) return HELM_OK;
-    return vcycle_apply(c, z, c->cnn_e0, v, nb, mask);   // Eq. 3.14: V-cycle from e_0 on r
+    if (c->opt.cnn_vcycle == 1)
+        return vcycle_apply(c, z, c->cnn_e0, v, nb, mask);   // V-cycle on P u = r from u0 = e_0
+    // e_0 + V(r - H e_0): the V-cycle corrects what the network leaves of H e = r
+    float2* rr = c->cnn_rres;
+    {
+        LaunchScope scope(c, K_CNN_IO);
+        net_residual_kernel<<<1184, 256, 0, c->stream>>>(fine_op(c, 0), v, c->cnn_e0, rr, nb);
+        HELM_CK(cudaGetLastError());
+    }
+    HELM_TRY(vcycle_apply(c, z, nullptr, rr, nb, mask));
+    LaunchScope scope(c, K_CNN_IO);
+    add_kernel<<<1184, 256, 0, c->stream>>>(z, c->cnn_e0, n * nb);
+    HELM_CK(cudaGetLastError());
+    return HELM_OK;
 }
 
 }  // namespace helm

@@ -32,7 +32,7 @@ namespace helm {
 namespace {
 
 constexpr int CT = 128;                 // threads per CTA = rows of the M tile
-constexpr long long WAIT_LIMIT = 1ll << 24;
+constexpr long long WAIT_LIMIT = 1ll << 20;   // about a second of try_wait polls
 
 __device__ __forceinline__ bool src_coord(int mode, int o, int d, int n_in, int* i) {
     int v;
@@ -60,14 +60,23 @@ __device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity) {
     return true;
 }
 
+// Warp-specialised pipeline: warps 0-3 gather stages into a ring of NS
+// shared-memory buffers and arrive on full[s]; warp 4 (one elected lane)
+// waits for full[s], issues the MMAs of the stage and commits them to
+// empty[s], which frees the buffer for the producers; the last commit also
+// arrives on `done`, after which warps 0-3 run the epilogue from TMEM.
+constexpr int NS = 4;                   // pipeline stages
+constexpr int NT = CT + 32;             // 4 producer/epilogue warps + 1 MMA warp
+
 template <int CK>
-__global__ void __launch_bounds__(CT) conv3x3_tc_kernel(ConvArgs a) {
+__global__ void __launch_bounds__(NT) conv3x3_tc_kernel(ConvArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int TILE_BYTES = CT * CK * 2;       // one operand tile (A, or B with up to 128 rows)
     constexpr int STAGE_BYTES = 2 * TILE_BYTES;
     constexpr int KG = CK / 8;                    // core matrices along K per row group
-    __shared__ uint64_t bar[2];
+    __shared__ uint64_t full[NS], empty[NS], done;
     __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t ncols = a.npad < 32 ? 32u : (uint32_t)a.npad;
@@ -76,9 +85,13 @@ __global__ void __launch_bounds__(CT) conv3x3_tc_kernel(ConvArgs a) {
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(&bar[0], 1);
-        tc::mbar_init(&bar[1], 1);
+        for (int s = 0; s < NS; ++s) {
+            tc::mbar_init(&full[s], CT);     // every producer thread arrives once per stage
+            tc::mbar_init(&empty[s], 1);     // one tcgen05.commit per stage
+        }
+        tc::mbar_init(&done, 1);
         tc::fence_mbar_init();
+        abort_flag = 0;
     }
     tc::tc_fence_before_sync();
     __syncthreads();
@@ -86,144 +99,144 @@ __global__ void __launch_bounds__(CT) conv3x3_tc_kernel(ConvArgs a) {
     const uint32_t tmem = tmem_base;
 
     const long long mtot = (long long)a.nb * a.hout * a.wout;
-    const long long p = (long long)blockIdx.x * CT + tid;
-    const bool valid = p < mtot;
-    int b = 0, oy = 0, ox = 0;
-    if (valid) {
-        b = (int)(p / ((long long)a.hout * a.wout));
-        int r = (int)(p - (long long)b * a.hout * a.wout);
-        oy = r / a.wout;
-        ox = r - oy * a.wout;
-    }
     const int cin = a.c0 + a.c1;
     const int cper = cin / CK;                    // stages per tap
     const int nchunks = 9 * cper;
-    const uint32_t idesc = tc::idesc_bf16_f32(CT, a.npad);
-    const uint32_t sbo = KG * 128;
-    bool ok = true;
-    int committed = 0;   // chunks whose MMAs were issued and committed (same in every thread)
+    volatile int* abort_v = &abort_flag;
 
-    for (int c = 0; c < nchunks; ++c) {
-        const int s = c & 1;
-        if (c >= 2) {
-            // the MMAs that read this stage two chunks ago must be done; the
-            // verdict is made uniform so that every thread leaves together
-            const bool w = bounded_wait(&bar[s], (uint32_t)(((c >> 1) - 1) & 1));
-            if (!__syncthreads_and(w)) { ok = false; break; }
-        }
-        const int tap = c / cper;
-        const int cc = (c - tap * cper) * CK;
-        unsigned char* As = smem + s * STAGE_BYTES;
-        unsigned char* Bs = As + TILE_BYTES;
-        // A: this thread's output pixel, channels [cc, cc + CK) of the tap's source node
-        const __nv_bfloat16* src = nullptr;
+    if (warp < 4) {
+        // ---------------- producers: one output pixel (A row) per thread ----------------
+        const long long p = (long long)blockIdx.x * CT + tid;
+        const bool valid = p < mtot;
+        int b = 0, oy = 0, ox = 0;
         if (valid) {
-            int iy, ix;
-            if (src_coord(a.mode, oy, tap / 3 - 1, a.hin, &iy) && src_coord(a.mode, ox, tap % 3 - 1, a.win, &ix)) {
-                if (cc < a.c0)
-                    src = a.x0 + (((size_t)b * a.hin + iy) * a.win + ix) * a.c0 + cc;
-                else {
-                    const int b1 = a.x1_map ? __ldg(a.x1_map + b) : (a.x1_bcast ? 0 : b);
-                    src = a.x1 + (((size_t)b1 * a.hin + iy) * a.win + ix) * a.c1 + (cc - a.c0);
+            b = (int)(p / ((long long)a.hout * a.wout));
+            const int r = (int)(p - (long long)b * a.hout * a.wout);
+            oy = r / a.wout;
+            ox = r - oy * a.wout;
+        }
+        const int b1 = (a.c1 && valid) ? (a.x1_map ? __ldg(a.x1_map + b) : (a.x1_bcast ? 0 : b)) : 0;
+        for (int c = 0; c < nchunks; ++c) {
+            const int s = c % NS;
+            if (c >= NS) {
+                // the MMAs that read this buffer NS chunks ago must be done
+                if (!bounded_wait(&empty[s], (uint32_t)(((c / NS) - 1) & 1))) { *abort_v = 1; }
+            }
+            if (*abort_v) break;
+            const int tap = c / cper;
+            const int cc = (c - tap * cper) * CK;
+            unsigned char* As = smem + s * STAGE_BYTES;
+            unsigned char* Bs = As + TILE_BYTES;
+            const __nv_bfloat16* src = nullptr;
+            if (valid) {
+                int iy, ix;
+                if (src_coord(a.mode, oy, tap / 3 - 1, a.hin, &iy) && src_coord(a.mode, ox, tap % 3 - 1, a.win, &ix)) {
+                    if (cc < a.c0)
+                        src = a.x0 + (((size_t)b * a.hin + iy) * a.win + ix) * a.c0 + cc;
+                    else
+                        src = a.x1 + (((size_t)b1 * a.hin + iy) * a.win + ix) * a.c1 + (cc - a.c0);
                 }
             }
-        }
-        unsigned char* arow = As + (tid >> 3) * (KG * 128) + (tid & 7) * 16;
-#pragma unroll
-        for (int kg = 0; kg < KG; ++kg) {
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (src) v = __ldg(reinterpret_cast<const uint4*>(src) + kg);
-            *reinterpret_cast<uint4*>(arow + kg * 128) = v;
-        }
-        // B: output channel tid, weights of the tap for the same channels
-        if (tid < a.npad) {
-            const __nv_bfloat16* wr = a.w + ((size_t)tid * 9 + tap) * cin + cc;
-            unsigned char* brow = Bs + (tid >> 3) * (KG * 128) + (tid & 7) * 16;
+            unsigned char* arow = As + (tid >> 3) * (KG * 128) + (tid & 7) * 16;
+            uint4 va[KG];
 #pragma unroll
             for (int kg = 0; kg < KG; ++kg)
-                *reinterpret_cast<uint4*>(brow + kg * 128) = __ldg(reinterpret_cast<const uint4*>(wr) + kg);
+                va[kg] = src ? __ldg(reinterpret_cast<const uint4*>(src) + kg) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int kg = 0; kg < KG; ++kg) *reinterpret_cast<uint4*>(arow + kg * 128) = va[kg];
+            if (tid < a.npad) {
+                const __nv_bfloat16* wr = a.w + ((size_t)tid * 9 + tap) * cin + cc;
+                unsigned char* brow = Bs + (tid >> 3) * (KG * 128) + (tid & 7) * 16;
+#pragma unroll
+                for (int kg = 0; kg < KG; ++kg)
+                    *reinterpret_cast<uint4*>(brow + kg * 128) = __ldg(reinterpret_cast<const uint4*>(wr) + kg);
+            }
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&full[s]);
         }
-        tc::fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
+    } else if (tid == CT) {
+        // ---------------- MMA issuer: one thread of warp 4 ----------------
+        const uint32_t idesc = tc::idesc_bf16_f32(CT, a.npad);
+        const uint32_t sbo = KG * 128;
+        int c = 0;
+        for (; c < nchunks; ++c) {
+            const int s = c % NS;
+            if (!bounded_wait(&full[s], (uint32_t)((c / NS) & 1)) || *abort_v) { *abort_v = 1; break; }
             tc::tc_fence_after_sync();
-            const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
+            const uint32_t a0 = tc::smem_u32(smem + s * STAGE_BYTES), b0 = a0 + TILE_BYTES;
 #pragma unroll
             for (int kk = 0; kk < CK / 16; ++kk) {
                 const uint64_t ad = tc::smem_desc(a0 + kk * 256, 128, sbo);
                 const uint64_t bd = tc::smem_desc(b0 + kk * 256, 128, sbo);
                 tc::mma_bf16(tmem, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
             }
-            tc::mma_commit(&bar[s]);
+            tc::mma_commit(&empty[s]);
         }
-        committed = c + 1;
+        // every MMA issued so far completes before `done` (also on the abort path)
+        tc::mma_commit(&done);
     }
-    if (ok) {
-        const int last = nchunks - 1;
-        ok = __syncthreads_and(bounded_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1)));
-    }
-    if (!ok) {
-        if (tid == 0) {
-            atomicExch(a.err, 1);
-            // drain, bounded: the last commit covers every MMA this CTA issued
-            if (committed > 0) {
-                const int last = committed - 1;
-                (void)bounded_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1));
-            }
-        }
+    // ---------------- epilogue (warps 0-3) ----------------
+    bool ok = true;
+    if (warp < 4) ok = bounded_wait(&done, 0u);
+    if (!ok) *abort_v = 1;
+    tc::tc_fence_after_sync();
+    __syncthreads();
+    if (*abort_v) {
+        if (tid == 0) atomicExch(a.err, 1);
         tc::tc_fence_before_sync();
         __syncthreads();
         if (warp == 0) tc::tmem_dealloc(tmem, ncols);
         return;
     }
-    tc::tc_fence_after_sync();
-
-    // epilogue: this thread owns accumulator row tid (lane tid)
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int col0 = 0; col0 < a.npad; col0 += 16) {
-        float v[16];
-        tc::tmem_ld16(trow + col0, v);
-        if (!valid) continue;
-        if (!a.accum) {
+    if (warp < 4) {
+        const long long p = (long long)blockIdx.x * CT + tid;
+        const bool valid = p < mtot;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int col0 = 0; col0 < a.npad; col0 += 16) {
+            float v[16];
+            tc::tmem_ld16(trow + col0, v);
+            if (!valid) continue;
+            if (!a.accum) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] += __ldg(a.bias + col0 + i);
-        }
-        if (a.res) {
-            const uint4* rp = reinterpret_cast<const uint4*>(a.res + (size_t)p * a.npad + col0);
-            uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
-            const __nv_bfloat16* rb0 = reinterpret_cast<const __nv_bfloat16*>(&r0);
-            const __nv_bfloat16* rb1 = reinterpret_cast<const __nv_bfloat16*>(&r1);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                v[i] += __bfloat162float(rb0[i]);
-                v[8 + i] += __bfloat162float(rb1[i]);
+                for (int i = 0; i < 16; ++i) v[i] += __ldg(a.bias + col0 + i);
             }
-        }
-        if (a.relu) {
+            if (a.res) {
+                const uint4* rp = reinterpret_cast<const uint4*>(a.res + (size_t)p * a.npad + col0);
+                uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
+                const __nv_bfloat16* rb0 = reinterpret_cast<const __nv_bfloat16*>(&r0);
+                const __nv_bfloat16* rb1 = reinterpret_cast<const __nv_bfloat16*>(&r1);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
-        }
-        if (a.out_fp32) {
-            float* yo = reinterpret_cast<float*>(a.y) + (size_t)p * a.cstore;
-            if (a.accum) {
-                for (int i = 0; i < 16; ++i)
-                    if (col0 + i < a.cstore) yo[col0 + i] += v[i];
+                for (int i = 0; i < 8; ++i) {
+                    v[i] += __bfloat162float(rb0[i]);
+                    v[8 + i] += __bfloat162float(rb1[i]);
+                }
+            }
+            if (a.relu) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
+            }
+            if (a.out_fp32) {
+                float* yo = reinterpret_cast<float*>(a.y) + (size_t)p * a.cstore;
+                if (a.accum) {
+                    for (int i = 0; i < 16; ++i)
+                        if (col0 + i < a.cstore) yo[col0 + i] += v[i];
+                } else {
+                    for (int i = 0; i < 16; ++i)
+                        if (col0 + i < a.cstore) yo[col0 + i] = v[i];
+                }
             } else {
-                for (int i = 0; i < 16; ++i)
-                    if (col0 + i < a.cstore) yo[col0 + i] = v[i];
-            }
-        } else {
-            uint4 o0, o1;
-            __nv_bfloat16* ob0 = reinterpret_cast<__nv_bfloat16*>(&o0);
-            __nv_bfloat16* ob1 = reinterpret_cast<__nv_bfloat16*>(&o1);
+                uint4 o0, o1;
+                __nv_bfloat16* ob0 = reinterpret_cast<__nv_bfloat16*>(&o0);
+                __nv_bfloat16* ob1 = reinterpret_cast<__nv_bfloat16*>(&o1);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                ob0[i] = __float2bfloat16_rn(v[i]);
-                ob1[i] = __float2bfloat16_rn(v[8 + i]);
+                for (int i = 0; i < 8; ++i) {
+                    ob0[i] = __float2bfloat16_rn(v[i]);
+                    ob1[i] = __float2bfloat16_rn(v[8 + i]);
+                }
+                uint4* yp = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + (size_t)p * a.npad + col0);
+                yp[0] = o0;
+                yp[1] = o1;
             }
-            uint4* yp = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + (size_t)p * a.npad + col0);
-            yp[0] = o0;
-            yp[1] = o1;
         }
     }
     tc::tc_fence_before_sync();
@@ -233,7 +246,7 @@ __global__ void __launch_bounds__(CT) conv3x3_tc_kernel(ConvArgs a) {
 
 template <int CK>
 int launch_ck(const ConvArgs& a, cudaStream_t st) {
-    const size_t smem = 2 * 2 * (size_t)CT * CK * 2;
+    const size_t smem = (size_t)NS * 2 * CT * CK * 2;
     static bool configured = false;   // attribute is per function; setting it twice is harmless
     if (!configured) {
         cudaFuncSetAttribute(conv3x3_tc_kernel<CK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -241,7 +254,7 @@ int launch_ck(const ConvArgs& a, cudaStream_t st) {
     }
     const long long mtot = (long long)a.nb * a.hout * a.wout;
     const unsigned grid = (unsigned)((mtot + CT - 1) / CT);
-    conv3x3_tc_kernel<CK><<<grid, CT, smem, st>>>(a);
+    conv3x3_tc_kernel<CK><<<grid, NT, smem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
 }
 

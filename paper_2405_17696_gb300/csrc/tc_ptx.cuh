@@ -69,6 +69,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile(
+        "{\n"
+        ".reg .b64 st;\n"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n"
+        "}\n" ::"r"(smem_u32(bar))
+        : "memory");
+}
+
 // Make this thread's ordinary shared-memory stores visible to the async proxy
 // (the tensor core) before it reads them.
 __device__ __forceinline__ void fence_proxy_async_smem() {

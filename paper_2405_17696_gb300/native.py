@@ -38,7 +38,7 @@ class helm_opts(ctypes.Structure):
                 ("pre", ctypes.c_int), ("post", ctypes.c_int), ("jacobi_w", ctypes.c_float),
                 ("sl_beta", ctypes.c_float), ("sl_include_gamma", ctypes.c_int), ("coarse_kind", ctypes.c_int),
                 ("coarse_iters", ctypes.c_int), ("precond", ctypes.c_int), ("max_rhs", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("cnn_vcycle", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class helm_stats(ctypes.Structure):

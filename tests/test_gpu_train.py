@@ -74,7 +74,12 @@ def test_make_samples_parity(native):
     for i in range(4):
         # e is the small remainder x - x~: compare the iterate x~ (relative 1e-5)
         assert np.linalg.norm(e[i] - e_ref[i]) <= 1e-5 * np.linalg.norm(x[i] - e_ref[i]), i
-        assert np.linalg.norm(r[i] - r_ref[i]) <= 2e-3 * np.linalg.norm(r_ref[i]), i
+        # r = b - H x~ cancels two O(||b||) terms once GMRES has converged, so the
+        # complex64 rounding of x~ (unit roundoff 6e-8) enters r as |H| |x~| u
+        xt = (x[i] - e_ref[i]).astype(np.complex128)
+        coef = np.abs(H.helmholtz_coefficient(kap, gam, om))
+        r_floor = 2.5e-7 * np.linalg.norm((8.0 / w.h ** 2 + coef) * np.abs(xt))
+        assert np.linalg.norm(r[i] - r_ref[i]) <= 2e-3 * np.linalg.norm(r_ref[i]) + r_floor, i
         assert _pair_defect_ok(e[i], r[i], kap, gam, om, w.h), i
 
 

@@ -145,3 +145,31 @@ def test_training_data_and_loss_gradient():
     lm = T.loss_and_grad(cnn.unflatten(theta - eps * d, specs), specs, kap, gam, om, w.h, r, e)[0]
     fd = (lp - lm) / (2 * eps)
     assert abs(fd - gflat @ d) <= 1e-5 * abs(fd)
+
+
+def test_mvu_composition_special_cases():
+    """Eq. 3.14 composition: an exact network estimate is returned unchanged
+    (V(0) = 0), a zero estimate gives the plain V-cycle, and the V-cycle
+    started from e0 is the other reading."""
+    from oracle import helmholtz as H, multigrid as MG, training as T
+    from paper_2405_17696_gb300 import media
+    w = media.crop_workload(32, 32, freqs=(5.0,), width=6)
+    kap, gam = np.float64(w.kappa), np.float64(w.gamma)
+    om = float(w.omegas[0])
+    A = lambda u: H.helmholtz_apply(u, kap, gam, om, w.h, w.h)
+    pc = MG.VCyclePreconditioner(kap, gam, om, w.h, w.h, MG.VCycleParams(levels=2))
+    r = media.complex_normal((w.nz, w.nx), seed=11).astype(np.complex128)
+    exact = H.DirectSolver(kap, gam, om, w.h, w.h).solve(r)
+    out = T.mvu_compose(exact, r, A, pc)
+    assert np.linalg.norm(out - exact) <= 1e-10 * np.linalg.norm(exact)
+    zero = np.zeros_like(r)
+    assert np.allclose(T.mvu_compose(zero, r, A, pc), pc(r), rtol=0, atol=1e-14)
+    # with a linear V-cycle (Jacobi coarsest solve) the correction is affine in
+    # e0: M(e0) - M(0) = e0 - V(H e0); a sign slip in r - H e0 breaks it
+    lin = MG.VCyclePreconditioner(kap, gam, om, w.h, w.h, MG.VCycleParams(levels=2, coarse_kind="jacobi"))
+    e0 = media.complex_normal((w.nz, w.nx), seed=12).astype(np.complex128) * 1e-3
+    m0 = T.mvu_compose(zero, r, A, lin)
+    d = T.mvu_compose(e0, r, A, lin) - m0
+    assert np.linalg.norm(d - (e0 - lin(A(e0)))) <= 1e-12 * np.linalg.norm(m0)
+    assert np.linalg.norm(d) > 1e-3 * np.linalg.norm(e0)
+    assert np.allclose(T.mvu_compose(e0, r, A, pc, "initial_guess"), pc(r, e0), rtol=0, atol=1e-14)
