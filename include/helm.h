@@ -256,6 +256,16 @@ int cnn_adam_reset(cnn_model* net);
 int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, int nb, int hin, int win,
                 const float* w, const float* bias, int cout, const float* res, int mode, int relu, float* y);
 
+/* Which kernel runs the same-grid layers (mode 0).  path 0 (default): the
+ * TMA halo-tile kernel (the input tile of a CTA staged once, the nine taps read
+ * as shifted shared-memory views), falling back to the gather kernel for a layer
+ * it cannot take; path 1: the gather kernel for every layer.  Process-wide; for
+ * tests and measurements.  Returns HELM_EINVAL for any other value. */
+int cnn_set_conv_path(int path);
+/* Launches of each convolution kernel since the library was loaded (either
+ * pointer may be NULL). */
+void cnn_conv_launch_counts(long long* tma, long long* gather);
+
 /* Per-kernel-class timing: when enabled, every kernel launch of the context is
  * bracketed by CUDA events on its stream and the main kernels add the
  * algorithmic bytes they move (the minimum DRAM traffic of their definition:

@@ -336,7 +336,7 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
         HELM_CK(cudaGetLastError());
     }
     Runner r(m, c, c->stream, &c->cnn_arena, &c->cnn_arena_bytes);
-    r.set_zmap(c->rhs_freq);
+    r.set_zmap(c->rhs_freq, c->nfreq);
     std::vector<__nv_bfloat16*> zz;
     for (void* p : c->cnn_z) zz.push_back((__nv_bfloat16*)p);
     if (!r.solver((const __nv_bfloat16*)c->cnn_in, nb, c->nz, c->nx, zz, 2, c->cnn_out)) {

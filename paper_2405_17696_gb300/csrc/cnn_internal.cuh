@@ -128,6 +128,7 @@ class Runner {
         }
         ConvArgs a;
         a.x0 = x0; a.c0 = c0; a.x1 = x1; a.c1 = c1; a.x1_bcast = x1_bcast; a.x1_map = x1_bcast == 2 ? zmap_ : nullptr;
+        a.nb1 = x1_bcast == 1 ? 1 : (x1_bcast == 2 ? nctx_ : nb);
         a.nb = nb; a.hin = hin; a.win = win; a.hout = ho; a.wout = wo; a.mode = l.mode;
         a.w = l.w; a.bias = l.b; a.res = res; a.y = y_fp32 ? y_fp32 : (void*)y;
         a.npad = l.npad; a.cstore = l.cout; a.relu = l.relu; a.out_fp32 = y_fp32 ? 1 : 0; a.accum = 0;
@@ -221,11 +222,13 @@ class Runner {
         return ok_;
     }
 
-    void set_zmap(const int* zmap) { zmap_ = zmap; }
+    // per-image context index (device array) into nctx context images
+    void set_zmap(const int* zmap, int nctx) { zmap_ = zmap; nctx_ = nctx; }
     void set_tape(std::vector<TapeOp>* t) { tape_ = t; }
 
    private:
     const int* zmap_ = nullptr;   // per-image context index used when x1_bcast == 2
+    int nctx_ = 1;                // context images zmap_ indexes
     std::vector<TapeOp>* tape_ = nullptr;
     std::vector<void*>* arena_;
     std::vector<size_t>* arena_bytes_;

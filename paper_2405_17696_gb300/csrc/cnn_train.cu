@@ -401,7 +401,7 @@ int cnn_loss_grad_impl(cnn_model* m, helm_ctx* c, const float2* r, const float2*
     if (!s) {
         Runner run(m, c, st);   // activations live until the backward pass is done
         run.set_tape(&tape);
-        run.set_zmap(c->rhs_freq);
+        run.set_zmap(c->rhs_freq, c->nfreq);
         std::vector<__nv_bfloat16*> z;
         if (!run.encoder(xe, nfreq, c->nz, c->nx, z)) s = HELM_ECUDA;
         if (!s && !run.solver(xs, nb, c->nz, c->nx, z, 2, out)) s = HELM_ECUDA;

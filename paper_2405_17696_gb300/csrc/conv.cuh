@@ -14,6 +14,7 @@ struct ConvArgs {
     int c1;
     int x1_bcast;              // 1: x1 has one image shared by the whole batch
     const int* x1_map;         // or: image of x1 used by output image b (device array), else b
+    int nb1 = 0;               // images in x1 (0: 1 when x1_bcast, else nb)
     int nb, hin, win, hout, wout;
     int mode;                  // 0 same, 1 down (output node (Y,X) on input node (2Y+1,2X+1)), 2 up (nearest x2),
                                // 3 transpose of down: output on the fine grid, tap d of output node f reads
@@ -31,5 +32,7 @@ struct ConvArgs {
 };
 
 int launch_conv3x3(const ConvArgs& a, cudaStream_t st);
+// same-grid layers through TMA-staged halo tiles (k_conv_tma.cu); HELM_EINVAL = not launched
+int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st);
 
 }  // namespace helm

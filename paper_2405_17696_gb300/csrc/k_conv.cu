@@ -21,7 +21,9 @@
 // drains what it issued (again bounded), frees its TMEM and returns.
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstdint>
+#include <string>
 
 #include "helm_internal.cuh"
 #include "conv.cuh"
@@ -65,12 +67,14 @@ __device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity) {
 // waits for full[s], issues the MMAs of the stage and commits them to
 // empty[s], which frees the buffer for the producers; the last commit also
 // arrives on `done`, after which warps 0-3 run the epilogue from TMEM.
-constexpr int NS = 4;                   // pipeline stages
+// pipeline stages: 64 KB of ring at most, so that three CTAs fit on an SM
+constexpr int ns_of(int ck) { return ck == 64 ? 2 : 4; }
 constexpr int NT = CT + 32;             // 4 producer/epilogue warps + 1 MMA warp
 
 template <int CK>
 __global__ void __launch_bounds__(NT) conv3x3_tc_kernel(ConvArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int NS = ns_of(CK);
     constexpr int TILE_BYTES = CT * CK * 2;       // one operand tile (A, or B with up to 128 rows)
     constexpr int STAGE_BYTES = 2 * TILE_BYTES;
     constexpr int KG = CK / 8;                    // core matrices along K per row group
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(NT) conv3x3_tc_kernel(ConvArgs a) {
 
 template <int CK>
 int launch_ck(const ConvArgs& a, cudaStream_t st) {
-    const size_t smem = (size_t)NS * 2 * CT * CK * 2;
+    const size_t smem = (size_t)ns_of(CK) * 2 * CT * CK * 2;
     static bool configured = false;   // attribute is per function; setting it twice is harmless
     if (!configured) {
         cudaFuncSetAttribute(conv3x3_tc_kernel<CK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -260,7 +264,14 @@ int launch_ck(const ConvArgs& a, cudaStream_t st) {
 
 }  // namespace
 
+namespace {
+std::atomic<int> g_conv_path{0};
+std::atomic<long long> g_launch_tma{0}, g_launch_gather{0};
+}  // namespace
+
 // Validates the shapes and launches; returns HELM_EINVAL for unsupported ones.
+// Same-grid layers go through the TMA halo-tile kernel unless the gather
+// kernel is forced (cnn_set_conv_path) or the layer does not fit it.
 int launch_conv3x3(const ConvArgs& a, cudaStream_t st) {
     const int cin = a.c0 + a.c1;
     if (a.npad != 16 && a.npad != 32 && a.npad != 64 && a.npad != 128) {
@@ -276,6 +287,18 @@ int launch_conv3x3(const ConvArgs& a, cudaStream_t st) {
         set_error("conv3x3: bad shape or mode");
         return HELM_EINVAL;
     }
+    if (a.mode == 0 && g_conv_path.load() == 0) {
+        const int t = launch_conv3x3_tma(a, st);
+        if (t == HELM_OK) {
+            ++g_launch_tma;
+            return HELM_OK;
+        }
+        if (t != HELM_EINVAL) {
+            set_error(std::string("conv3x3 (TMA) launch: ") + cudaGetErrorString(cudaGetLastError()));
+            return t;
+        }
+    }
+    ++g_launch_gather;
     int ck = 64;
     if (a.c0 % 64 || (a.c1 && a.c1 % 64)) ck = 32;
     if (a.c0 % 32 || (a.c1 && a.c1 % 32)) ck = 16;
@@ -288,3 +311,17 @@ int launch_conv3x3(const ConvArgs& a, cudaStream_t st) {
 }
 
 }  // namespace helm
+
+extern "C" int cnn_set_conv_path(int path) {
+    if (path != 0 && path != 1) {
+        helm::set_error("cnn_set_conv_path: path must be 0 (automatic) or 1 (gather kernel only)");
+        return HELM_EINVAL;
+    }
+    helm::g_conv_path.store(path);
+    return HELM_OK;
+}
+
+extern "C" void cnn_conv_launch_counts(long long* tma, long long* gather) {
+    if (tma) *tma = helm::g_launch_tma.load();
+    if (gather) *gather = helm::g_launch_gather.load();
+}

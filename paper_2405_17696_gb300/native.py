@@ -95,6 +95,10 @@ def _load():
     lib.cnn_precond_apply.restype = ip
     lib.cnn_conv3x3.argtypes = [vp, ip, vp, ip, ip, ip, ip, ip, vp, vp, ip, vp, ip, ip, vp]
     lib.cnn_conv3x3.restype = ip
+    lib.cnn_set_conv_path.argtypes = [ip]
+    lib.cnn_set_conv_path.restype = ip
+    lib.cnn_conv_launch_counts.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.cnn_conv_launch_counts.restype = None
     lib.helm_destroy.argtypes = [vp]
     lib.helm_destroy.restype = None
     lib.helm_last_error.argtypes = []
@@ -303,6 +307,18 @@ def cnn_conv3x3(x0, c0: int, x1, c1: int, x1_bcast: int, nb: int, hin: int, win:
     _check(lib.cnn_conv3x3(_ptr(x0, "float32"), c0, _ptr(x1, "float32"), c1, x1_bcast, nb, hin, win,
                            _ptr(w, "float32"), _ptr(bias, "float32"), cout, _ptr(res, "float32"), mode, relu,
                            _ptr(y, "float32")), "cnn_conv3x3")
+
+
+def cnn_set_conv_path(path: int):
+    """0: TMA halo-tile kernel for same-grid layers (default); 1: gather kernel for all."""
+    _check(lib.cnn_set_conv_path(int(path)), "cnn_set_conv_path")
+
+
+def cnn_conv_launch_counts():
+    """(TMA-kernel launches, gather-kernel launches) since the library was loaded."""
+    t, g = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    lib.cnn_conv_launch_counts(ctypes.byref(t), ctypes.byref(g))
+    return t.value, g.value
 
 
 def cnn_precond_apply(ctx, r, e, nrhs: int, freq_idx=None, with_vcycle: int = 1):

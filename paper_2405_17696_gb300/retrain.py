@@ -8,7 +8,8 @@ dataset tensors.
 Alg. 2 (with the paper's budget, Sec. 4.2): build an initial dataset of
 ``initial_size`` pairs by Eq. 4.3 (x ~ CN(0, 1), a random number of
 V-cycle-preconditioned GMRES steps in {1..10}); then for every epoch train
-once over the dataset in batches, and during the first ``data_epochs`` epochs
+once over the dataset in batches (Adam, learning rate decayed geometrically
+per epoch from ``lr`` to ``lr_final``), and during the first ``data_epochs`` epochs
 append one refined pair per existing pair (the network's estimate followed by
 one preconditioned GMRES step, `cnn_refine_samples`).  128 pairs and 3 data
 epochs give the final 1024 pairs; 30 epochs in total.
@@ -29,6 +30,7 @@ class RetrainConfig:
     epochs: int = 30
     batch: int = 16
     lr: float = 1e-4
+    lr_final: float | None = None  # learning rate of the last epoch (geometric decay per epoch); None = constant
     max_gmres_steps: int = 10
     literal: bool = False          # Alg. 2 as printed instead of the residual-correction pair
     seed: int = media.SEED_DATAGEN
@@ -77,7 +79,9 @@ def retrain(native, net, ctx, nx: int, nz: int, freq_of_sample=None, cfg: Retrai
                                 F[s0:s0 + nb])
     size = cfg.initial_size
     hist = RetrainHistory()
+    decay = 1.0 if cfg.lr_final is None or cfg.epochs < 2 else (cfg.lr_final / cfg.lr) ** (1.0 / (cfg.epochs - 1))
     for epoch in range(1, cfg.epochs + 1):
+        lr = cfg.lr * decay ** (epoch - 1)
         order = g.permutation(size)
         losses = []
         for b0 in range(0, size, cfg.batch):
@@ -85,7 +89,7 @@ def retrain(native, net, ctx, nx: int, nz: int, freq_of_sample=None, cfg: Retrai
             ti = torch.from_numpy(idx).to(device)
             r = R.index_select(0, ti).contiguous()
             e = E.index_select(0, ti).contiguous()
-            losses.append(native.cnn_train_step(net, ctx, r, e, len(idx), cfg.lr, F[idx]))
+            losses.append(native.cnn_train_step(net, ctx, r, e, len(idx), lr, F[idx]))
             hist.steps += 1
             if cfg.max_steps is not None and hist.steps >= cfg.max_steps:
                 break

@@ -42,8 +42,17 @@ MODES = {"same": 0, "down": 1, "up": 2}
     (128, 0, 0, 64, "up", 6, 10, 2, False, True),
     (128, 128, 0, 128, "same", 8, 8, 2, False, True),
     (16, 0, 0, 2, "same", 16, 20, 2, False, False),      # output layer, 2 channels
+    (32, 16, 0, 16, "same", 6, 200, 2, True, True),      # 3 channel groups, wide rows: 2 column tiles
+    (16, 0, 0, 128, "same", 5, 127, 1, False, True),     # 127 wide: one M block per row
+    (64, 0, 0, 64, "same", 37, 40, 1, True, True),       # narrow rows packed into M blocks, ragged rows
+    (32, 32, 1, 32, "down", 18, 22, 2, False, True),     # concat in the stride-2 gather path
 ])
-def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res, relu):
+@pytest.mark.parametrize("path", [0, 1])
+def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res, relu, path):
+    """path 0: same-grid layers through the TMA halo-tile kernel; path 1: every
+    layer through the gather kernel."""
+    if path == 1 and mode != "same":
+        pytest.skip("only same-grid layers have two kernels")
     g = np.random.default_rng(c0 * 7 + cout + MODES[mode])
     x0 = cnn.bf16_round(g.normal(size=(nb, hin, win, c0)))
     x1 = cnn.bf16_round(g.normal(size=((1 if bcast else nb), hin, win, c1))) if c1 else None
@@ -60,8 +69,16 @@ def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res,
     ref = cnn.bf16_round(ref)
     y = np.zeros((nb, ho, wo, cout), np.float32)
     f32 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32)
-    native.cnn_conv3x3(f32(x0), c0, f32(x1), c1, bcast, nb, hin, win, f32(w), f32(b), cout, f32(r),
-                       MODES[mode], 1 if relu else 0, y)
+    t0, g0 = native.cnn_conv_launch_counts()
+    native.cnn_set_conv_path(path)
+    try:
+        native.cnn_conv3x3(f32(x0), c0, f32(x1), c1, bcast, nb, hin, win, f32(w), f32(b), cout, f32(r),
+                           MODES[mode], 1 if relu else 0, y)
+    finally:
+        native.cnn_set_conv_path(0)
+    t1, g1 = native.cnn_conv_launch_counts()
+    used_tma = mode == "same" and path == 0
+    assert (t1 - t0, g1 - g0) == ((1, 0) if used_tma else (0, 1))
     err = np.abs(y - ref)
     tol = 2.0 ** -7 * np.abs(ref) + 1e-3 * np.abs(ref).max()
     assert np.all(err <= tol), (err.max(), np.abs(ref).max())
