@@ -262,6 +262,10 @@ int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, 
  * it cannot take; path 1: the gather kernel for every layer.  Process-wide; for
  * tests and measurements.  Returns HELM_EINVAL for any other value. */
 int cnn_set_conv_path(int path);
+/* Tile height limit of the TMA halo-tile kernel: at most max_rows output rows per
+ * tile (0 = automatic: as many as two 128-column TMEM accumulator buffers and a
+ * 56 KB stage allow).  Process-wide; for tuning.  HELM_EINVAL outside [0, 254]. */
+int cnn_set_conv_tiling(int max_rows);
 /* Launches of each convolution kernel since the library was loaded (either
  * pointer may be NULL). */
 void cnn_conv_launch_counts(long long* tma, long long* gather);

@@ -97,6 +97,8 @@ def _load():
     lib.cnn_conv3x3.restype = ip
     lib.cnn_set_conv_path.argtypes = [ip]
     lib.cnn_set_conv_path.restype = ip
+    lib.cnn_set_conv_tiling.argtypes = [ip]
+    lib.cnn_set_conv_tiling.restype = ip
     lib.cnn_conv_launch_counts.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.cnn_conv_launch_counts.restype = None
     lib.helm_destroy.argtypes = [vp]
@@ -312,6 +314,11 @@ def cnn_conv3x3(x0, c0: int, x1, c1: int, x1_bcast: int, nb: int, hin: int, win:
 def cnn_set_conv_path(path: int):
     """0: TMA halo-tile kernel for same-grid layers (default); 1: gather kernel for all."""
     _check(lib.cnn_set_conv_path(int(path)), "cnn_set_conv_path")
+
+
+def cnn_set_conv_tiling(max_rows: int):
+    """Tile-height limit of the TMA conv kernel (0 = automatic)."""
+    _check(lib.cnn_set_conv_tiling(int(max_rows)), "cnn_set_conv_tiling")
 
 
 def cnn_conv_launch_counts():
