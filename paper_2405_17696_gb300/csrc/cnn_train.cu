@@ -5,7 +5,7 @@
 // Backward of one convolution y = act(W * x + b [+ res]) with upstream
 // gradient G_y (FP32):
 //   g      = G_y . [y > 0]  (BF16 operand; FP32 copy added to G_res for a ResNet skip)
-//   dW, db += sum over pixels of g (x) x_tap    (FP32, CUDA cores)
+//   dW, db += sum over pixels of g (x) x_tap    (FP32, CUDA cores, tiled in shared memory)
 //   G_x   += W^T * g   on the tensor cores with the same kernel as the forward:
 //            'same'  -> same-grid convolution with transposed, tap-flipped weights,
 //            'down'  -> the transpose-of-down gather mode with transposed weights,
@@ -15,6 +15,7 @@
 // gradient summed over the samples that use them, and flow into the encoder.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <unordered_map>
@@ -98,7 +99,6 @@ struct WgArgs {
     int npad, cout, cin;      // cin: logical input channels (weights layout [cout][9][cin])
     float* dW;
     float* db;
-    long long ppb;            // pixels per block
 };
 
 __device__ __forceinline__ bool fwd_src(int mode, int o, int d, int n_in, int* i) {
@@ -116,63 +116,146 @@ __device__ __forceinline__ bool fwd_src(int mode, int o, int d, int n_in, int* i
     return true;
 }
 
-// dW[co][t][ci] += sum_p g[p][co] x_t[p][ci], db[co] += sum_p g[p][co]  (tile 16 co x 16 ci x 9 taps)
-__global__ void __launch_bounds__(256) wgrad_kernel(WgArgs a) {
-    constexpr int PP = 32;
-    __shared__ float gs[PP][16];
-    __shared__ float xs[PP][9][17];
-    const int tid = threadIdx.x;
-    const int co_l = tid >> 4, ci_l = tid & 15;
-    const int co0 = blockIdx.y * 16, ci0 = blockIdx.x * 16;
-    const long long ntot = (long long)a.nb * a.hout * a.wout;
-    const long long pb = (long long)blockIdx.z * a.ppb;
-    const long long pe = pb + a.ppb < ntot ? pb + a.ppb : ntot;
-    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float accb = 0.f;
+// Weight gradient on the CUDA cores (FP32):
+//   dW[co][t][ci] += sum_p g[p][co] x(src(p, t))[ci],   db[co] += sum_p g[p][co].
+// A CTA owns a block of 16 output x 16 input channels and loops over tiles of
+// th x tw output pixels.  Per tile it stages g (16 channels), the input
+// rectangle the tile's taps read (16 channels, zero outside the image) and a
+// table pixel x tap -> staged input pixel (a zero row for taps outside), all
+// in shared memory.  Thread (lane l, warp w): output channels 4 (l / 8) .. +3,
+// input channels 2 (l % 8) .. +1, all nine taps (72 FP32 accumulators), over
+// the pixels p = w, w + 8, ...; the eight warps' sums are combined in shared
+// memory and added to dW once per CTA.
+struct Wg2 {
+    int th, tw;                 // output pixel tile
+    int tiles_x, tiles_y;       // tiles per image
+    int sh, sw;                 // staged input rectangle (rows x columns)
+};
+
+__device__ __forceinline__ void wg_rect(int mode, int oy0, int ox0, int* r0, int* s0) {
+    if (mode == 0) { *r0 = oy0 - 1; *s0 = ox0 - 1; }
+    else if (mode == 1) { *r0 = 2 * oy0; *s0 = 2 * ox0; }
+    else { *r0 = (oy0 >> 1) - 1; *s0 = (ox0 >> 1) - 1; }
+}
+
+__global__ void __launch_bounds__(256) wgrad_kernel(WgArgs a, Wg2 w) {
+    extern __shared__ float wsm[];
+    const int np = w.th * w.tw;
+    const int nst = w.sh * w.sw;                     // staged pixels; row nst is all zero
+    float* xs = wsm;                                 // [nst + 1][16]
+    float* gs = xs + (size_t)(nst + 1) * 16;         // [np][16]
+    int* tab = reinterpret_cast<int*>(gs + (size_t)np * 16);   // [np][9]
+    const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 5;
+    const int n_l = (lane >> 3) * 4, c_l = (lane & 7) * 2;
+    const int cb = blockIdx.y * 16, nbk = blockIdx.z * 16;
     const int ctot = a.c0 + a.c1;
-    for (long long p0 = pb; p0 < pe; p0 += PP) {
-        for (int i = tid; i < PP * 16; i += 256) {
-            const int pp = i >> 4, cc = i & 15;
-            const long long p = p0 + pp;
-            gs[pp][cc] = (p < pe && co0 + cc < a.npad) ? __bfloat162float(a.g[p * a.npad + co0 + cc]) : 0.0f;
-        }
-        for (int i = tid; i < PP * 144; i += 256) {
-            const int pp = i / 144, rem = i - pp * 144, t = rem >> 4, cc = rem & 15;
-            const long long p = p0 + pp;
-            const int ci = ci0 + cc;
+    const long long tiles = (long long)a.nb * w.tiles_y * w.tiles_x;
+    float acc[9][4][2];
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[t][i][0] = acc[t][i][1] = 0.0f;
+    float accb[4] = {0.f, 0.f, 0.f, 0.f};
+    if (tid < 16) xs[(size_t)nst * 16 + tid] = 0.0f;
+
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int tx = (int)(tile % w.tiles_x);
+        const long long r = tile / w.tiles_x;
+        const int ty = (int)(r % w.tiles_y);
+        const int b = (int)(r / w.tiles_y);
+        const int oy0 = ty * w.th, ox0 = tx * w.tw;
+        int r0, s0;
+        wg_rect(a.mode, oy0, ox0, &r0, &s0);
+        __syncthreads();   // the previous tile's reads are done
+        // g: 16 channels of the output gradient
+        for (int i = tid; i < np * 16; i += 256) {
+            const int pp = i >> 4, k = i & 15;
+            const int oy = oy0 + pp / w.tw, ox = ox0 + pp % w.tw;
             float v = 0.0f;
-            if (p < pe && ci < ctot) {
-                const int b = (int)(p / ((long long)a.hout * a.wout));
-                const int r = (int)(p - (long long)b * a.hout * a.wout);
-                const int oy = r / a.wout, ox = r - oy * a.wout;
-                int iy, ix;
-                if (fwd_src(a.mode, oy, t / 3 - 1, a.hin, &iy) && fwd_src(a.mode, ox, t % 3 - 1, a.win, &ix)) {
-                    if (ci < a.c0) {
-                        v = __bfloat162float(a.x0[(((size_t)b * a.hin + iy) * a.win + ix) * a.c0 + ci]);
-                    } else {
-                        const int b1 = a.x1_map ? a.x1_map[b] : (a.x1_bcast ? 0 : b);
-                        v = __bfloat162float(a.x1[(((size_t)b1 * a.hin + iy) * a.win + ix) * a.c1 + (ci - a.c0)]);
-                    }
+            if (oy < a.hout && ox < a.wout)
+                v = __bfloat162float(a.g[(((size_t)b * a.hout + oy) * a.wout + ox) * a.npad + nbk + k]);
+            gs[i] = v;
+        }
+        // input rectangle: 16 channels of x0 or x1
+        const bool second = cb >= a.c0;
+        const __nv_bfloat16* xsrc = second ? a.x1 : a.x0;
+        const int cstride = second ? a.c1 : a.c0;
+        const int coff = second ? cb - a.c0 : cb;
+        const int bx = second ? (a.x1_map ? __ldg(a.x1_map + b) : (a.x1_bcast ? 0 : b)) : b;
+        for (int i = tid; i < nst * 16; i += 256) {
+            const int q = i >> 4, k = i & 15;
+            const int iy = r0 + q / w.sw, ix = s0 + q % w.sw;
+            float v = 0.0f;
+            if (iy >= 0 && iy < a.hin && ix >= 0 && ix < a.win && cb + k < ctot)
+                v = __bfloat162float(xsrc[(((size_t)bx * a.hin + iy) * a.win + ix) * cstride + coff + k]);
+            xs[i] = v;
+        }
+        // pixel x tap -> staged input pixel (nst: outside the input)
+        for (int i = tid; i < np * 9; i += 256) {
+            const int pp = i / 9, t = i - pp * 9;
+            const int oy = oy0 + pp / w.tw, ox = ox0 + pp % w.tw;
+            int iy, ix, idx = nst;
+            if (fwd_src(a.mode, oy, t / 3 - 1, a.hin, &iy) && fwd_src(a.mode, ox, t % 3 - 1, a.win, &ix))
+                idx = (iy - r0) * w.sw + (ix - s0);
+            tab[i] = idx;
+        }
+        __syncthreads();
+        for (int pp = grp; pp < np; pp += 8) {
+            const float4 g4 = *reinterpret_cast<const float4*>(gs + pp * 16 + n_l);
+            const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) accb[i] += gv[i];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const float2 x2 = *reinterpret_cast<const float2*>(xs + (size_t)tab[pp * 9 + t] * 16 + c_l);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    acc[t][i][0] = fmaf(gv[i], x2.x, acc[t][i][0]);
+                    acc[t][i][1] = fmaf(gv[i], x2.y, acc[t][i][1]);
                 }
             }
-            xs[pp][t][cc] = v;
+        }
+    }
+    // combine the eight pixel groups (warps) through shared memory, then one atomic per weight
+    __syncthreads();
+    float* red = wsm;   // [32 lanes][76]
+    for (int src = 1; src < 8; ++src) {
+        if (grp == src) {
+            float* o = red + lane * 76;
+#pragma unroll
+            for (int t = 0; t < 9; ++t)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { o[t * 8 + i * 2] = acc[t][i][0]; o[t * 8 + i * 2 + 1] = acc[t][i][1]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) o[72 + i] = accb[i];
         }
         __syncthreads();
-#pragma unroll 4
-        for (int pp = 0; pp < PP; ++pp) {
-            const float gv = gs[pp][co_l];
+        if (grp == 0) {
+            const float* o = red + lane * 76;
 #pragma unroll
-            for (int t = 0; t < 9; ++t) acc[t] += gv * xs[pp][t][ci_l];
-            accb += gv;
+            for (int t = 0; t < 9; ++t)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { acc[t][i][0] += o[t * 8 + i * 2]; acc[t][i][1] += o[t * 8 + i * 2 + 1]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) accb[i] += o[72 + i];
         }
         __syncthreads();
     }
-    const int co = co0 + co_l, ci = ci0 + ci_l;
-    if (co < a.cout && ci < a.cin) {
+    if (grp == 0) {
 #pragma unroll
-        for (int t = 0; t < 9; ++t) atomicAdd(a.dW + ((size_t)co * 9 + t) * a.cin + ci, acc[t]);
+        for (int i = 0; i < 4; ++i) {
+            const int co = nbk + n_l + i;
+            if (co >= a.cout) continue;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int ci = cb + c_l + j;
+                if (ci >= a.cin) continue;
+#pragma unroll
+                for (int t = 0; t < 9; ++t) atomicAdd(a.dW + ((size_t)co * 9 + t) * a.cin + ci, acc[t][i][j]);
+            }
+            if (blockIdx.y == 0 && c_l == 0) atomicAdd(a.db + co, accb[i]);
+        }
     }
-    if (ci0 == 0 && ci_l == 0 && co < a.cout) atomicAdd(a.db + co, accb);
 }
 
 // loss = (1/m) sum ||e_net - e_true||^2 with e_net = h^2 rms (o_0 + i o_1); gout = dloss/do
@@ -267,10 +350,26 @@ class Backward {
                 a.g = g; a.npad = L.npad; a.cout = L.cout; a.cin = L.cin;
                 a.dW = m_->grad + L.off;
                 a.db = m_->grad + L.off + (long long)L.cout * 9 * L.cin;
-                a.ppb = 2048;
-                dim3 grid((op.c0 + op.c1 + 15) / 16, (L.npad + 15) / 16, (unsigned)((nout + a.ppb - 1) / a.ppb));
+                Wg2 w;
+                if (L.mode == 1) { w.th = 4; w.tw = 32; } else { w.th = 8; w.tw = 32; }
+                w.tiles_x = (op.wout + w.tw - 1) / w.tw;
+                w.tiles_y = (op.hout + w.th - 1) / w.th;
+                if (L.mode == 0) { w.sh = w.th + 2; w.sw = w.tw + 2; }
+                else if (L.mode == 1) { w.sh = 2 * w.th + 1; w.sw = 2 * w.tw + 1; }
+                else { w.sh = w.th / 2 + 2; w.sw = w.tw / 2 + 2; }
+                const size_t np = (size_t)w.th * w.tw;
+                const size_t smem = std::max<size_t>(((size_t)(w.sh * w.sw + 1) * 16 + np * 16) * sizeof(float) +
+                                                         np * 9 * sizeof(int), 32 * 76 * sizeof(float));
+                const unsigned gy = (unsigned)((op.c0 + op.c1 + 15) / 16), gz = (unsigned)(L.npad / 16);
+                const long long tiles = (long long)op.nb * w.tiles_x * w.tiles_y;
+                const long long gx = std::max<long long>(1, std::min<long long>(tiles, 1216 / (gy * gz)));
+                static bool attr = false;
+                if (!attr) {
+                    cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+                    attr = true;
+                }
                 LaunchScope scope(c_, K_WGRAD);
-                wgrad_kernel<<<grid, 256, 0, st_>>>(a);
+                wgrad_kernel<<<dim3((unsigned)gx, gy, gz), 256, smem, st_>>>(a, w);
             }
             if (cudaGetLastError() != cudaSuccess) { ok_ = false; break; }
             // input gradients

@@ -270,8 +270,8 @@ std::atomic<long long> g_launch_tma{0}, g_launch_gather{0};
 }  // namespace
 
 // Validates the shapes and launches; returns HELM_EINVAL for unsupported ones.
-// Same-grid layers go through the TMA halo-tile kernel unless the gather
-// kernel is forced (cnn_set_conv_path) or the layer does not fit it.
+// Layers go through the TMA halo-tile kernel unless the gather kernel is
+// forced (cnn_set_conv_path) or the layer does not fit it.
 int launch_conv3x3(const ConvArgs& a, cudaStream_t st) {
     const int cin = a.c0 + a.c1;
     if (a.npad != 16 && a.npad != 32 && a.npad != 64 && a.npad != 128) {
@@ -287,7 +287,7 @@ int launch_conv3x3(const ConvArgs& a, cudaStream_t st) {
         set_error("conv3x3: bad shape or mode");
         return HELM_EINVAL;
     }
-    if (a.mode == 0 && g_conv_path.load() == 0) {
+    if (g_conv_path.load() == 0) {
         const int t = launch_conv3x3_tma(a, st);
         if (t == HELM_OK) {
             ++g_launch_tma;

@@ -1,29 +1,38 @@
-// Same-grid 3x3 convolution (the ResNet, concatenation, input and output
-// layers of the encoder-solver network, Fig. 1 caption) as an implicit GEMM on
-// the tensor cores, with the input staged once per tile by TMA.
+// 3x3 convolution layers of the encoder-solver network (Fig. 1 caption,
+// Sec. 3.4) as implicit GEMMs on the tensor cores, with the input staged once
+// per tile by TMA and the nine taps read as shifted shared-memory views.
 //
-// A CTA owns `rows` output rows x `tw` output columns of one image.  For every
-// group of 16 input channels, TMA copies the (rows + 2) x (tw + 2) halo tile of
-// the NHWC input into shared memory as two 8-channel planes, each stored
-// pixel-major with 16 bytes per pixel: exactly the K-major, no-swizzle
-// core-matrix layout (8 pixels x 16 bytes per core matrix) that tcgen05.mma
-// reads.  The A operand of tap (dy, dx) for a block of 128 output pixels is then
-// the same planes seen from a start address shifted by (dy * pitch + dx) pixels
-// -- the nine taps need no gather at all.  Out-of-image halo pixels are
-// zero-filled by TMA.  The weights of the group (9 taps x 16 channels x N) are
-// copied by TMA into the same layout.
+// Staging.  For every group of 16 input channels TMA copies the tile's input
+// into shared memory as 8-channel planes stored pixel-major, 16 bytes per
+// pixel: exactly the K-major, no-swizzle core-matrix layout (8 pixels x 16
+// bytes per core matrix) that tcgen05.mma reads.  The A operand of a tap for a
+// block of 128 output pixels is then a plane seen from a start address shifted
+// by the tap's offset in pixels; no gather.  Pixels outside the image are
+// zero-filled by TMA.  The weights of the group (9 taps x 16 channels x N)
+// arrive by TMA in the same layout.
 //
-// When the image is narrower than 128 pixels the tile holds whole rows and an
-// M block runs across row ends: the two halo columns between rows produce
-// accumulator rows that the epilogue discards (each accumulator row depends
-// only on its own A row).
+// Sampling modes (output node -> input nodes of its taps):
+//  0 same grid   (y, x)           -> (y + dy, x + dx); one (rows+2) x (tw+2) halo plane per 8 channels.
+//  1 stride-2    (Y, X)           -> (2Y + 1 + dy, 2X + 1 + dx); the input is staged as four
+//                                    parity sub-planes (even/odd rows x even/odd columns, TMA
+//                                    element strides of 2), so that every tap is again a shift.
+//  2 nearest x2  (2Y+py, 2X+px)   -> coarse ((2Y+py+dy) >> 1, (2X+px+dx) >> 1); the coarse halo
+//                                    tile is staged as in mode 0 and each of the four output
+//                                    parities (py, px) is its own set of M blocks.
+//  3 transpose of mode 1 (the input gradient of a stride-2 layer): fine (2Y+py, 2X+px) takes
+//                                    tap (dy, dx) from coarse (Y + (py-1-dy)/2, X + (px-1-dx)/2)
+//                                    when both are integers; staged as mode 2.
+// When the tile is narrower than 127 pixels, whole rows are packed into an M
+// block and the accumulator rows of the halo columns between rows are
+// discarded (each accumulator row depends only on its own A row).
 //
-// Warp 4 lane 0 issues the TMA copies and the MMAs (FP32 accumulators in TMEM,
-// one 128 x N block per 128 output pixels); warps 0-3 run the epilogue (bias,
-// residual, ReLU, BF16 or FP32 store).  Stages are released through mbarriers
-// that tcgen05.commit arrives on.  Every wait is bounded; on expiry the kernel
-// raises the error flag, waits (bounded) for the copies it issued, frees its
-// TMEM and returns.
+// Persistent warp-specialised CTAs (two per SM, or one when a tile needs more
+// than 128 TMEM columns): warp 8 lane 0 streams (tile, channel group) stages
+// through a ring by TMA; warp 9 lane 0 issues tcgen05.mma into one of two TMEM
+// accumulator buffers; warps 0-7 drain the other buffer (bias, residual, ReLU,
+// BF16 or FP32 store, or FP32 accumulation).  Every wait is bounded and gives
+// up when another role aborts; on expiry the kernel raises the error flag,
+// waits (bounded) for its copies and MMAs in flight, frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -41,26 +50,29 @@ namespace helm {
 
 namespace {
 
-constexpr int EPI = 128;                        // epilogue threads = TMEM lanes = rows of an M block
+constexpr int EPI_WARPS = 8;                    // two warpgroups drain TMEM (alternate 32-column chunks)
+constexpr int EPI = 32 * EPI_WARPS;             // epilogue threads
 constexpr int NT = EPI + 64;                    // + a TMA-producer warp and an MMA-issuer warp
 constexpr int MAX_NS = 4;                       // stages (one 16-channel group of one tile each)
 constexpr long long WAIT_LIMIT = 1ll << 22;     // polls of try_wait before a wait gives up
-constexpr int SLACK_PX = 144;                   // plane padding read by the last M block of a narrow tile
+constexpr int SLACK_PX = 144;                   // plane padding read by the last M block of a packed tile
 constexpr size_t STAGE_BUDGET = 56 * 1024;      // bytes of one stage at most (fewer rows otherwise)
-constexpr size_t RING_BUDGET = 112 * 1024;      // bytes of the stage ring: two CTAs per SM
+constexpr size_t RING_BUDGET = 112 * 1024;      // bytes of the stage ring
 
 struct Geometry {
-    int tw, rows, pw;        // output tile width/height; staged row pitch = tw + 2
-    int mb;                  // 128-pixel M blocks per tile
-    int rowaligned;          // 1: M block m is output row m (tw >= 127)
+    int tw, rows, pw;        // tile on the staged grid (output grid in mode 1); staged row pitch
+    int mb;                  // 128-pixel M blocks per output parity
+    int rowaligned;          // 1: M block m is tile row m
+    int nph;                 // output parities per tile: 1 (modes 0, 1) or 4 (modes 2, 3)
     int tiles_x, tiles_y, tiles;
-    int plane;               // bytes of one staged 8-channel plane (with slack)
-    int wbytes;              // bytes of one group's weights (9 taps x 2 planes x npad rows x 16 B)
+    int plane;               // bytes of one staged plane (with slack)
+    int nplanes;             // planes per 8-channel chunk: 1, or 4 parity sub-planes in mode 1
+    int wbytes;              // bytes of one group's weights (9 taps x 2 chunks x npad rows x 16 B)
     int stage;               // bytes of one stage
     int groups, groups0;     // 16-channel groups in total / taken from x0
     int ns;                  // stages in the ring
     uint32_t tx;             // bytes TMA delivers per stage
-    uint32_t acc_cols;       // TMEM columns of one accumulator buffer (mb * npad)
+    uint32_t acc_cols;       // TMEM columns of one accumulator buffer (nph * mb * npad)
     uint32_t tmem_cols;      // allocated: two accumulator buffers, power of two
 };
 
@@ -75,10 +87,35 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
     return true;
 }
 
-// Persistent: CTA k processes tiles k, k + gridDim.x, ...  Warp 4 (lane 0)
-// streams the 16-channel groups of its tiles through a ring of `ns` stages;
-// warp 5 (lane 0) issues the MMAs of a tile into one of two TMEM accumulator
-// buffers; warps 0-3 drain the other buffer (the previous tile) meanwhile.
+// Tap t = (dy + 1) * 3 + (dx + 1) of output parity (py, px): whether it
+// contributes, and its A operand as (plane, offset in pixels from the tile's
+// staged pixel q).
+template <int MODE>
+__device__ __forceinline__ bool tap_source(int t, int py, int px, int pw, int* plane, int* off) {
+    const int dy = t / 3 - 1, dx = t % 3 - 1;
+    if (MODE == 0) {
+        *plane = 0;
+        *off = (dy + 1) * pw + (dx + 1);
+        return true;
+    } else if (MODE == 1) {
+        // row 2Y+1+dy: odd sub-plane row Y (dy = 0), even rows Y (dy = -1) or Y + 1 (dy = +1)
+        *plane = (dy == 0 ? 2 : 0) + (dx == 0 ? 1 : 0);
+        *off = (dy == 1 ? pw : 0) + (dx == 1 ? 1 : 0);
+        return true;
+    } else if (MODE == 2) {
+        *plane = 0;
+        *off = (((py + dy) >> 1) + 1) * pw + (((px + dx) >> 1) + 1);
+        return true;
+    } else {
+        const int uy = py - 1 - dy, ux = px - 1 - dx;
+        if ((uy & 1) || (ux & 1)) return false;
+        *plane = 0;
+        *off = ((uy >> 1) + 1) * pw + ((ux >> 1) + 1);
+        return true;
+    }
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__ CUtensorMap tm_x0,
                                                          const __grid_constant__ CUtensorMap tm_x1,
                                                          const __grid_constant__ CUtensorMap tm_w, ConvArgs a,
@@ -87,8 +124,10 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
     __shared__ uint64_t full[MAX_NS], empty[MAX_NS], tfull[2], tempty[2], done;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
+    __shared__ float bias_s[128];
 
     const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid < a.npad) bias_s[tid] = a.accum ? 0.0f : __ldg(a.bias + tid);
     if (warp == 0) {
         tc::tmem_alloc(&tmem_base, g.tmem_cols);
         tc::tmem_relinquish();
@@ -114,6 +153,7 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
     const int cin = a.c0 + a.c1;
     const int G = g.groups;
     const int ntiles = g.tiles > (int)blockIdx.x ? (g.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int chunk_bytes = g.nplanes * g.plane;   // K-adjacent core matrices (LBO)
 
     auto tile_coords = [&](int k, int& b, int& xs, int& ys) {
         int t = (int)blockIdx.x + k * (int)gridDim.x;
@@ -142,12 +182,22 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                 tc::mbar_arrive_expect_tx(&full[s], g.tx);
                 for (int h = 0; h < 2; ++h) {
                     const int c = gi * 16 + h * 8;
-                    if (gi < g.groups0)
-                        tc::tma_load_4d(st + h * g.plane, &tm_x0, c, xs - 1, ys - 1, b, &full[s]);
-                    else
-                        tc::tma_load_4d(st + h * g.plane, &tm_x1, c - a.c0, xs - 1, ys - 1, b1, &full[s]);
+                    const bool second = gi >= g.groups0;
+                    const CUtensorMap* tm = second ? &tm_x1 : &tm_x0;
+                    const int cc = second ? c - a.c0 : c;
+                    const int bb = second ? b1 : b;
+                    unsigned char* dst = st + h * chunk_bytes;
+                    if (MODE == 1) {
+                        // parity sub-planes: rows 2ys + rp + 2i, columns 2xs + cp + 2j
+                        for (int rp = 0; rp < 2; ++rp)
+                            for (int cp = 0; cp < 2; ++cp)
+                                tc::tma_load_4d(dst + (rp * 2 + cp) * g.plane, tm, cc, 2 * xs + cp, 2 * ys + rp, bb,
+                                                &full[s]);
+                    } else {
+                        tc::tma_load_4d(dst, tm, cc, xs - 1, ys - 1, bb, &full[s]);
+                    }
                 }
-                unsigned char* ws = st + 2 * g.plane;
+                unsigned char* ws = st + 2 * chunk_bytes;
                 for (int tap = 0; tap < 9; ++tap)
                     for (int h = 0; h < 2; ++h)
                         tc::tma_load_2d(ws + (tap * 2 + h) * wplane, &tm_w, tap * cin + gi * 16 + h * 8, 0, &full[s]);
@@ -179,17 +229,23 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                 if (!wait_bar(&full[s], (uint32_t)((j / g.ns) & 1), abort_v)) { ok = false; break; }
                 tc::tc_fence_after_sync();
                 const uint32_t a0 = tc::smem_u32(smem + (size_t)s * g.stage);
-                const uint32_t w0 = a0 + 2 * g.plane;
-                for (int m = 0; m < g.mb; ++m) {
-                    const int q0 = g.rowaligned ? m * g.pw : m * 128;
-                    const uint32_t d = dbase + (uint32_t)(m * a.npad);
+                const uint32_t w0 = a0 + 2 * chunk_bytes;
+                for (int ph = 0; ph < g.nph; ++ph) {
+                    const int py = ph >> 1, px = ph & 1;
+                    for (int m = 0; m < g.mb; ++m) {
+                        const int q0 = g.rowaligned ? m * g.pw : m * 128;
+                        const uint32_t d = dbase + (uint32_t)((ph * g.mb + m) * a.npad);
+                        bool first = gi == 0;
 #pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const int dy = tap / 3, dx = tap % 3;   // tap offset + 1
-                        const uint64_t ad =
-                            tc::smem_desc(a0 + (uint32_t)(q0 + dy * g.pw + dx) * 16u, (uint32_t)g.plane, 128);
-                        const uint64_t bd = tc::smem_desc(w0 + (uint32_t)tap * 2u * wplane, wplane, 128);
-                        tc::mma_bf16(d, ad, bd, idesc, (gi > 0 || tap > 0) ? 1u : 0u);
+                        for (int tap = 0; tap < 9; ++tap) {
+                            int pl, off;
+                            if (!tap_source<MODE>(tap, py, px, g.pw, &pl, &off)) continue;
+                            const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(pl * g.plane + (q0 + off) * 16),
+                                                              (uint32_t)chunk_bytes, 128);
+                            const uint64_t bd = tc::smem_desc(w0 + (uint32_t)tap * 2u * wplane, wplane, 128);
+                            tc::mma_bf16(d, ad, bd, idesc, first ? 0u : 1u);
+                            first = false;
+                        }
                     }
                 }
                 tc::mma_commit(&empty[s]);
@@ -201,9 +257,14 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
         long long it = 0;
         while (!tc::mbar_try_wait(&done, 0u) && ++it < WAIT_LIMIT) {
         }
-    } else if (warp < 4) {
+    } else if (warp < EPI_WARPS) {
         // ---------------- epilogue ----------------
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 (accumulator row = M-block row);
+        // warpgroup w / 4 drains every other 32-column chunk of the buffer
+        const int row = (warp & 3) * 32 + (tid & 31);
+        const int wg = warp >> 2;
+        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        const int acols = (int)g.acc_cols;
         for (int k = 0; k < ntiles; ++k) {
             const int acc = k & 1;
             if (!wait_bar(&tfull[acc], (uint32_t)((k >> 1) & 1), abort_v)) { *abort_v = 1; break; }
@@ -211,43 +272,60 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
             int b, xs, ys;
             tile_coords(k, b, xs, ys);
             const uint32_t dbase = lane_base + (uint32_t)acc * g.acc_cols;
-            for (int m = 0; m < g.mb; ++m) {
-                const int q = (g.rowaligned ? m * g.pw : m * 128) + tid;
-                const int yy = q / g.pw, xx = q - yy * g.pw;
-                const int oy = ys + yy, ox = xs + xx;
-                const bool valid = xx < g.tw && yy < g.rows && oy < a.hout && ox < a.wout;
-                const long long p = ((long long)b * a.hout + oy) * a.wout + ox;
-                for (int col0 = 0; col0 < a.npad; col0 += 16) {
-                    float v[16];
-                    tc::tmem_ld16(dbase + (uint32_t)(m * a.npad + col0), v);
-                    if (!valid) continue;
-                    if (!a.accum) {
+            for (int c0 = wg * 32; c0 < acols; c0 += 64) {
+                float v[32];
+                int nseg;
+                if (c0 + 32 <= acols) {
+                    tc::tmem_ld32(dbase + (uint32_t)c0, v);
+                    nseg = 2;
+                } else {
+                    float h[16];
+                    tc::tmem_ld16(dbase + (uint32_t)c0, h);
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] += __ldg(a.bias + col0 + i);
+                    for (int i = 0; i < 16; ++i) v[i] = h[i];
+                    nseg = 1;
+                }
+#pragma unroll
+                for (int sgi = 0; sgi < 2; ++sgi) {
+                    if (sgi >= nseg) break;
+                    float* vv = v + 16 * sgi;
+                    const int colg = c0 + 16 * sgi;
+                    const int bm = colg / a.npad, n0 = colg - bm * a.npad;
+                    const int ph = bm / g.mb, m = bm - ph * g.mb;
+                    const int q = (g.rowaligned ? m * g.pw : m * 128) + row;
+                    const int yy = q / g.pw, xx = q - yy * g.pw;
+                    int oy = ys + yy, ox = xs + xx;
+                    if (MODE >= 2) {
+                        oy = 2 * oy + (ph >> 1);
+                        ox = 2 * ox + (ph & 1);
                     }
+                    if (!(xx < g.tw && yy < g.rows && oy < a.hout && ox < a.wout)) continue;
+                    const long long p = ((long long)b * a.hout + oy) * a.wout + ox;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) vv[i] += bias_s[n0 + i];
                     if (a.res) {
-                        const uint4* rp = reinterpret_cast<const uint4*>(a.res + (size_t)p * a.npad + col0);
+                        const uint4* rp = reinterpret_cast<const uint4*>(a.res + (size_t)p * a.npad + n0);
                         uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
                         const __nv_bfloat16* rb0 = reinterpret_cast<const __nv_bfloat16*>(&r0);
                         const __nv_bfloat16* rb1 = reinterpret_cast<const __nv_bfloat16*>(&r1);
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            v[i] += __bfloat162float(rb0[i]);
-                            v[8 + i] += __bfloat162float(rb1[i]);
+                            vv[i] += __bfloat162float(rb0[i]);
+                            vv[8 + i] += __bfloat162float(rb1[i]);
                         }
                     }
                     if (a.relu) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
+                        for (int i = 0; i < 16; ++i) vv[i] = fmaxf(vv[i], 0.0f);
                     }
                     if (a.out_fp32) {
                         float* yo = reinterpret_cast<float*>(a.y) + (size_t)p * a.cstore;
                         if (a.accum) {
                             for (int i = 0; i < 16; ++i)
-                                if (col0 + i < a.cstore) yo[col0 + i] += v[i];
+                                if (n0 + i < a.cstore) yo[n0 + i] += vv[i];
                         } else {
                             for (int i = 0; i < 16; ++i)
-                                if (col0 + i < a.cstore) yo[col0 + i] = v[i];
+                                if (n0 + i < a.cstore) yo[n0 + i] = vv[i];
                         }
                     } else {
                         uint4 o0, o1;
@@ -255,11 +333,11 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                         __nv_bfloat16* ob1 = reinterpret_cast<__nv_bfloat16*>(&o1);
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            ob0[i] = __float2bfloat16_rn(v[i]);
-                            ob1[i] = __float2bfloat16_rn(v[8 + i]);
+                            ob0[i] = __float2bfloat16_rn(vv[i]);
+                            ob1[i] = __float2bfloat16_rn(vv[8 + i]);
                         }
                         uint4* yp = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) +
-                                                             (size_t)p * a.npad + col0);
+                                                             (size_t)p * a.npad + n0);
                         yp[0] = o0;
                         yp[1] = o1;
                     }
@@ -294,12 +372,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // NHWC BF16 activation [n][h][w][c] viewed as a 4-D tensor (c, w, h, n); box =
-// 8 channels x (tw + 2) x (rows + 2) x 1 image.
-bool encode_act(CUtensorMap* m, const void* base, int c, int w, int h, int n, int box_w, int box_h) {
+// 8 channels x box_w x box_h x 1 image, traversed with element stride `es` in
+// w and h (box_w / es x box_h / es pixels land in shared memory).
+bool encode_act(CUtensorMap* m, const void* base, int c, int w, int h, int n, int box_w, int box_h, int es) {
     const cuuint64_t dims[4] = {(cuuint64_t)c, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
     const cuuint64_t strides[3] = {(cuuint64_t)c * 2, (cuuint64_t)c * 2 * w, (cuuint64_t)c * 2 * w * h};
     const cuuint32_t box[4] = {8u, (cuuint32_t)box_w, (cuuint32_t)box_h, 1u};
-    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    const cuuint32_t estr[4] = {1u, (cuuint32_t)es, (cuuint32_t)es, 1u};
     return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -318,41 +397,61 @@ bool encode_w(CUtensorMap* m, const void* base, int cin, int npad) {
 
 std::atomic<int> g_rows_cap{0};   // tile-height limit set by cnn_set_conv_tiling (0 = automatic)
 
+// Tile plan; .tiles = 0 when the layer does not fit this kernel.
 Geometry plan(const ConvArgs& a) {
     Geometry g{};
-    const int H = a.hout, W = a.wout;
+    const int mode = a.mode;
+    // the grid the tile lives on: output grid for modes 0 and 1, coarse input grid for 2 and 3
+    const int H = mode >= 2 ? a.hin : a.hout, W = mode >= 2 ? a.win : a.wout;
     g.groups = (a.c0 + a.c1) / 16;
     g.groups0 = a.c0 / 16;
-    g.tw = W >= 128 ? 128 : W;
-    g.pw = g.tw + 2;
-    g.rowaligned = g.tw >= 127;          // a row (plus its halo) no longer fits one M block
-    const int maxmb = 128 / a.npad;      // two accumulator buffers of at most 128 TMEM columns
+    g.nph = mode >= 2 ? 4 : 1;
+    g.nplanes = mode == 1 ? 4 : 1;
+    if (mode == 1) {
+        g.tw = W >= 127 ? 127 : W;   // 2 (tw + 1) traversed columns fit a 256-element box
+        g.pw = g.tw + 1;
+        g.rowaligned = 0;
+    } else {
+        g.tw = W >= 128 ? 128 : W;
+        g.pw = g.tw + 2;
+        g.rowaligned = g.tw >= 127;  // a row (plus its halo) no longer fits one M block
+    }
+    const int halo = mode == 1 ? 1 : 2;        // extra staged rows
     g.wbytes = 9 * 2 * a.npad * 16;
+    // TMEM per accumulator buffer: 128 columns (two CTAs per SM), or 256 when one
+    // block per parity already needs more (one CTA per SM)
+    int acc_max = 128;
+    if (g.nph * a.npad > acc_max) acc_max = 256;
+    const int maxmb = acc_max / (g.nph * a.npad);
     auto fill = [&](int rows) {
         g.rows = rows;
         g.mb = g.rowaligned ? rows : (rows * g.pw + 127) / 128;
-        g.plane = (((rows + 2) * g.pw + SLACK_PX) * 16 + 127) / 128 * 128;
-        g.stage = 2 * g.plane + g.wbytes;
+        g.plane = (((rows + halo) * g.pw + SLACK_PX) * 16 + 127) / 128 * 128;
+        g.stage = 2 * g.nplanes * g.plane + g.wbytes;
     };
     int rmax = g.rowaligned ? maxmb : (maxmb * 128) / g.pw;
     const int cap = g_rows_cap.load();
     if (cap > 0 && rmax > cap) rmax = cap;
-    if (rmax < 1) rmax = 1;
     if (rmax > H) rmax = H;
-    if (rmax > 254) rmax = 254;
+    const int box_rows_max = mode == 1 ? 127 : 254;   // staged rows fit a 256-element box
+    if (rmax > box_rows_max) rmax = box_rows_max;
+    if (rmax < 1) return Geometry{};   // tiles = 0: not this kernel
     int rows = rmax;
     fill(rows);
     while (rows > 1 && (size_t)g.stage > STAGE_BUDGET) fill(--rows);
+    if (g.mb < 1 || g.mb > maxmb) return Geometry{};
     g.ns = (int)(RING_BUDGET / (size_t)g.stage);
     if (g.ns > MAX_NS) g.ns = MAX_NS;
     if (g.ns < 2) g.ns = 2;
     g.tiles_x = (W + g.tw - 1) / g.tw;
     g.tiles_y = (H + g.rows - 1) / g.rows;
-    g.tx = (uint32_t)(2 * (g.rows + 2) * g.pw * 16 + g.wbytes);
-    g.acc_cols = (uint32_t)(g.mb * a.npad);
+    const int staged_px = mode == 1 ? (g.rows + 1) * g.pw : (g.rows + 2) * g.pw;
+    g.tx = (uint32_t)(2 * g.nplanes * staged_px * 16 + g.wbytes);
+    g.acc_cols = (uint32_t)(g.nph * g.mb * a.npad);
     uint32_t cols = 32;
     while (cols < 2 * g.acc_cols) cols <<= 1;
     g.tmem_cols = cols;
+    g.tiles = g.tiles_x * g.tiles_y * a.nb;
     return g;
 }
 
@@ -369,43 +468,67 @@ int sm_count() {
     return n > 0 ? n : 148;
 }
 
+template <int MODE>
+int launch_mode(const CUtensorMap& tm0, const CUtensorMap& tm1, const CUtensorMap& tmw, const ConvArgs& a,
+                const Geometry& g, cudaStream_t st) {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(conv3x3_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+    const size_t smem = (size_t)g.ns * g.stage;
+    // two CTAs per SM when two fit the 512 TMEM columns, else one; a shared-memory
+    // request above a third (half) of the SM keeps further CTAs off
+    int per_sm = g.tmem_cols <= 256 ? 2 : 1;
+    const size_t smem_req = std::max<size_t>(smem, per_sm == 2 ? 80 * 1024 : 120 * 1024);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3x3_tma_kernel<MODE>, NT, smem_req) != cudaSuccess) {
+        (void)cudaGetLastError();
+        occ = 1;
+    }
+    per_sm = std::max(1, std::min(per_sm, occ));
+    const long long grid = std::min<long long>(g.tiles, (long long)per_sm * sm_count());
+    conv3x3_tma_kernel<MODE><<<(unsigned)grid, NT, smem_req, st>>>(tm0, tm1, tmw, a, g);
+    return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
+}
+
 }  // namespace
 
-// Same-grid layers through TMA-staged halo tiles; returns HELM_EINVAL (nothing
-// launched) when the layer does not fit this path, so that the caller can use
-// the gather kernel instead.
+// Launches the TMA halo-tile kernel; returns HELM_EINVAL (nothing launched) when
+// the layer does not fit it, so that the caller can use the gather kernel.
 int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st) {
-    if (a.mode != 0 || a.hin != a.hout || a.win != a.wout || !encode_fn()) return HELM_EINVAL;
+    if (!encode_fn()) return HELM_EINVAL;
+    if (a.mode < 0 || a.mode > 3) return HELM_EINVAL;
+    if (a.mode == 0 && (a.hin != a.hout || a.win != a.wout)) return HELM_EINVAL;
+    if (a.mode == 1 && (a.hin != 2 * a.hout || a.win != 2 * a.wout)) return HELM_EINVAL;
+    if (a.mode >= 2 && (a.hout != 2 * a.hin || a.wout != 2 * a.win)) return HELM_EINVAL;
     if ((reinterpret_cast<uintptr_t>(a.x0) & 15) || (a.c1 && (reinterpret_cast<uintptr_t>(a.x1) & 15)) ||
         (reinterpret_cast<uintptr_t>(a.w) & 15))
         return HELM_EINVAL;
+    if ((long long)a.nb * (a.mode >= 2 ? (long long)a.hin * a.win : (long long)a.hout * a.wout) > 0x7fffffffLL)
+        return HELM_EINVAL;
     const Geometry g = plan(a);
-    if (g.pw > 256 || g.rows + 2 > 256) return HELM_EINVAL;
-    const size_t smem = (size_t)g.ns * g.stage;
-    if (smem > 200 * 1024 || g.tmem_cols > 256) return HELM_EINVAL;
+    if (g.tiles <= 0) return HELM_EINVAL;
+    if ((size_t)g.ns * g.stage > 200 * 1024 || g.tmem_cols > 512) return HELM_EINVAL;
+    // box extents: modes 0/2/3 (tw + 2) x (rows + 2); mode 1 traverses 2 (tw + 1) x 2 (rows + 1) with stride 2
+    const int es = a.mode == 1 ? 2 : 1;
+    const int bw = a.mode == 1 ? 2 * g.pw : g.pw;
+    const int bh = a.mode == 1 ? 2 * (g.rows + 1) : g.rows + 2;
+    if (bw > 256 || bh > 256) return HELM_EINVAL;
     alignas(64) CUtensorMap tm0, tm1, tmw;
-    if (!encode_act(&tm0, a.x0, a.c0, a.win, a.hin, a.nb, g.pw, g.rows + 2)) return HELM_EINVAL;
+    if (!encode_act(&tm0, a.x0, a.c0, a.win, a.hin, a.nb, bw, bh, es)) return HELM_EINVAL;
     if (a.c1) {
         const int n1 = a.nb1 > 0 ? a.nb1 : (a.x1_bcast ? 1 : a.nb);
-        if (!encode_act(&tm1, a.x1, a.c1, a.win, a.hin, n1, g.pw, g.rows + 2)) return HELM_EINVAL;
+        if (!encode_act(&tm1, a.x1, a.c1, a.win, a.hin, n1, bw, bh, es)) return HELM_EINVAL;
     } else {
         tm1 = tm0;
     }
     if (!encode_w(&tmw, a.w, a.c0 + a.c1, a.npad)) return HELM_EINVAL;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(conv3x3_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    });
-    const long long tiles = (long long)g.tiles_x * g.tiles_y * a.nb;
-    if (tiles > 0x7fffffffLL) return HELM_EINVAL;
-    Geometry gg = g;
-    gg.tiles = (int)tiles;
-    // two CTAs per SM (ring and TMEM budgets), persistent over the tiles
-    const long long grid = std::min<long long>(tiles, 2LL * sm_count());
-    // at least 80 KB of shared memory per CTA keeps a third CTA (and its TMEM) off an SM
-    const size_t smem_req = std::max<size_t>(smem, 80 * 1024);
-    conv3x3_tma_kernel<<<(unsigned)grid, NT, smem_req, st>>>(tm0, tm1, tmw, a, gg);
-    return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
+    switch (a.mode) {
+        case 0: return launch_mode<0>(tm0, tm1, tmw, a, g, st);
+        case 1: return launch_mode<1>(tm0, tm1, tmw, a, g, st);
+        case 2: return launch_mode<2>(tm0, tm1, tmw, a, g, st);
+        default: return launch_mode<3>(tm0, tm1, tmw, a, g, st);
+    }
 }
 
 }  // namespace helm

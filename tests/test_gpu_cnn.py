@@ -49,10 +49,7 @@ MODES = {"same": 0, "down": 1, "up": 2}
 ])
 @pytest.mark.parametrize("path", [0, 1])
 def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res, relu, path):
-    """path 0: same-grid layers through the TMA halo-tile kernel; path 1: every
-    layer through the gather kernel."""
-    if path == 1 and mode != "same":
-        pytest.skip("only same-grid layers have two kernels")
+    """path 0: the TMA halo-tile kernel; path 1: the gather kernel."""
     g = np.random.default_rng(c0 * 7 + cout + MODES[mode])
     x0 = cnn.bf16_round(g.normal(size=(nb, hin, win, c0)))
     x1 = cnn.bf16_round(g.normal(size=((1 if bcast else nb), hin, win, c1))) if c1 else None
@@ -77,7 +74,7 @@ def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res,
     finally:
         native.cnn_set_conv_path(0)
     t1, g1 = native.cnn_conv_launch_counts()
-    used_tma = mode == "same" and path == 0
+    used_tma = path == 0
     assert (t1 - t0, g1 - g0) == ((1, 0) if used_tma else (0, 1))
     err = np.abs(y - ref)
     tol = 2.0 ** -7 * np.abs(ref) + 1e-3 * np.abs(ref).max()
