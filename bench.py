@@ -1,15 +1,24 @@
 #!/usr/bin/env python3
-"""Helmholtz right-hand sides solved per second to 1e-6 relative residual.
+"""Helmholtz right-hand sides solved per second to 1e-6 relative residual:
+CNN-FGMRES against MG-FGMRES on one GPU.
 
-Workload (one step): the batched multi-source, multi-frequency solve of
-Sec. 3.1-3.4 on a 512x256 seeded layered medium (h = 20 m, 32-cell absorbing
-layer on the left, right and bottom), 64 point sources on row 2 and three
-frequencies (3, 4.5, 6 Hz) = 192 right-hand sides in one batched launch
-sequence: the per-medium set-up (medium upload + Galerkin multigrid hierarchy
-for every frequency) followed by MG-FGMRES(10) with the shifted-Laplacian
-V-cycle until every right-hand side reaches ||b - H x|| <= 1e-6 ||b|| in FP64.
+Default workload (``--workload cnn``): the encoder-solver preconditioned solve
+of Sec. 3.4 (Eq. 3.14) on a 1024x512 seeded layered medium (h = 12.5 m,
+32-cell absorbing layer on the left, right and bottom), 128 point sources on
+row 2 at 8 Hz.  Set-up, not timed: the network (widths 16/32/64/128, seeded
+He initialisation) is trained on this medium by Alg. 2 (Eq. 4.3 data from
+Gaussian x, Adam on Eq. 4.2) for ``--train-steps`` steps.  One step: the
+per-medium set-up (medium upload, Galerkin multigrid hierarchy, encoder
+context features) followed by FGMRES(10) until every right-hand side reaches
+||b - H x|| <= 1e-6 ||b|| in FP64.  ``value`` is CNN-FGMRES; the MG-FGMRES
+arm (shifted-Laplacian V-cycle alone) runs on the same batch in the same
+process and is reported beside it.
+
+``--workload mg``: the batched MG-FGMRES solve on a 512x256 medium with 64
+sources at 3, 4.5 and 6 Hz (192 right-hand sides).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload cnn|mg] [--train-steps T]
 
 Prints one JSON line.  Under torchrun (N > 1) every rank solves its own copy
 of the batch (independent problems, no collective on the data path: weak
@@ -40,16 +49,18 @@ METRIC = "Helmholtz RHS solved/sec to 1e-6 rel. residual: CNN-FGMRES vs MG-FGMRE
 UNIT = "RHS/s"
 TOL = 1e-6
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
 
 
 def peaks():
+    """(HBM GB/s, BF16 TFLOP/s burst, source) from the measured peaks file, else the fallback."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), float(d.get("bf16_tflops", FALLBACK_BF16_TFLOPS)), "measured"
     except Exception:
-        return FALLBACK_HBM_GBS, "fallback"
+        return FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS, "fallback"
 
 
 # --------------------------------------------------------------------------
@@ -112,13 +123,13 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # CPU oracle (the reference arm and the cpu_baseline field)
 # --------------------------------------------------------------------------
-def oracle_sample(w):
-    """One bounded sample of the workload on the host: the direct solve of one
-    frequency's share (one sparse LU factorisation + 64 back-solves), which is
-    one third of the 192-RHS batch.  Returns (RHS solved, seconds)."""
+def oracle_sample(w, n_rhs):
+    """One bounded sample of the workload on the host: the direct solve of the
+    last frequency (one sparse LU factorisation) and ``n_rhs`` of its
+    back-solves.  Returns (RHS solved, seconds)."""
     from oracle import helmholtz as H
     j = len(w.freqs_hz) - 1
-    rhs = w.rhs()[w.freq_index() == j]
+    rhs = w.rhs()[w.freq_index() == j][:n_rhs]
     t0 = time.perf_counter()
     solver = H.DirectSolver(w.kappa.astype(np.float64), w.gamma.astype(np.float64),
                             float(np.float32(w.omegas[j])), w.h, w.h)
@@ -126,19 +137,26 @@ def oracle_sample(w):
     return rhs.shape[0], time.perf_counter() - t0
 
 
-SAMPLE_DESC = ("direct sparse LU (SuperLU, FP64) of the 6 Hz operator plus its 64 back-solves: one third "
-               "of the 512x256, 192-RHS batch")
+def oracle_plan(workload):
+    """(workload, RHS per sample, description) of the bounded CPU sample."""
+    if workload == "cnn":
+        w = media.workload_cnn()
+        return w, 32, ("direct sparse LU (SuperLU, FP64) of the 8 Hz 1024x512 operator plus 32 back-solves: "
+                       "a quarter of the 128-RHS batch")
+    w = media.workload_batched()
+    return w, 64, ("direct sparse LU (SuperLU, FP64) of the 6 Hz 512x256 operator plus its 64 back-solves: "
+                   "one third of the 192-RHS batch")
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    w = media.workload_batched()
+    w, n_rhs, desc = oracle_plan(args.workload)
     for _ in range(args.warmup):
-        oracle_sample(w)
+        oracle_sample(w, n_rhs)
     n_tot, t_tot = 0, 0.0
     for _ in range(args.steps):
-        n, t = oracle_sample(w)
+        n, t = oracle_sample(w, n_rhs)
         n_tot += n
         t_tot += t
     value = n_tot / t_tot
@@ -146,154 +164,251 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_of(w),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": SAMPLE_DESC},
+        "config": config_of(w, args.workload),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def config_of(w):
-    return {"workload": w.name, "nx": w.nx, "nz": w.nz, "h_m": w.h, "freqs_hz": w.freqs_hz,
-            "n_sources": len(w.positions), "n_rhs": len(w.positions) * len(w.freqs_hz),
-            "medium": "seeded 12-layer model, 1.5-4.5 km/s, smoothed N(0, 0.1) km/s noise",
-            "precond": "shifted-Laplacian V-cycle (Galerkin, 3 levels, 2+2 damped Jacobi, coarse GMRES(10))",
-            "krylov": "FGMRES(10), complex64 vectors, FP64 Hessenberg/Givens/residual, complex128 iterate",
-            "tol": TOL, "l2": "inputs larger than L2 (201 MB RHS batch, 4.6 GB Krylov workspace)",
-            "parallelism": "independent replicas per GPU"}
+def config_of(w, workload):
+    cfg = {"workload": w.name, "nx": w.nx, "nz": w.nz, "h_m": w.h, "freqs_hz": w.freqs_hz,
+           "n_sources": len(w.positions), "n_rhs": len(w.positions) * len(w.freqs_hz),
+           "medium": "seeded 12-layer model, 1.5-4.5 km/s, smoothed N(0, 0.1) km/s noise, 32-cell absorbing layer",
+           "multigrid": "shifted-Laplacian V-cycle (Galerkin, 3 levels, 2+2 damped Jacobi, coarse GMRES(10))",
+           "krylov": "FGMRES(10), complex64 vectors, FP64 Hessenberg/Givens/residual, complex128 iterate",
+           "tol": TOL, "parallelism": "independent replicas per GPU"}
+    if workload == "cnn":
+        cfg["precond"] = "CNN-FGMRES: M_VU(r) = e0 + V(r - H e0), e0 = encoder-solver U-Net (16/32/64/128, BF16)"
+        cfg["l2"] = "inputs larger than L2 (537 MB RHS batch, 6 GB Krylov workspace)"
+    else:
+        cfg["precond"] = "MG-FGMRES"
+        cfg["l2"] = "inputs larger than L2 (201 MB RHS batch, 4.6 GB Krylov workspace)"
+    return cfg
 
 
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
-def run_ours(args, rank, world):
+class Problem:
+    """Device copies of one workload's inputs and the solve step through the C ABI."""
+
+    def __init__(self, native, w, dev):
+        import torch
+        self.native, self.w = native, w
+        self.nb = len(w.positions) * len(w.freqs_hz)
+        self.kappa = torch.from_numpy(w.kappa).to(dev)
+        self.gamma = torch.from_numpy(w.gamma).to(dev)
+        self.omegas = torch.from_numpy(np.asarray(w.omegas, dtype=np.float32)).to(dev)
+        self.rhs_host = w.rhs()
+        self.rhs = torch.from_numpy(self.rhs_host).to(dev)
+        self.fi = w.freq_index()
+        self.x = torch.empty((self.nb, w.nz, w.nx), dtype=torch.complex128, device=dev)
+        self.iters = []
+
+    def step(self, ctx, rhs=None, x=None, kappa=None, gamma=None, om=None):
+        n = self.native
+        n.helm_set_medium(ctx, self.kappa if kappa is None else kappa, self.gamma if gamma is None else gamma,
+                          self.omegas if om is None else om)
+        st, iters, rel, stat = n.helm_solve(ctx, self.rhs if rhs is None else rhs, self.x if x is None else x,
+                                            self.nb, self.fi, TOL, n.HELM_SOLVE_ZERO_X0)
+        if st != n.HELM_OK:
+            raise RuntimeError(f"solve did not converge: status {st}, per-RHS {np.unique(stat)}, "
+                               f"iterations {iters.min()}-{iters.max()}, max rel. residual {rel.max():.3e}")
+        self.iters.append(iters.copy())
+        return rel
+
+
+def timed(prob, ctx, steps, warmup, dev, world, stream, sampler=None):
+    """Device time (ms, max over ranks) of `steps` solve steps after `warmup`, with
+    a barrier and a synchronize on both sides; per-RHS iterations and residuals."""
     import torch
     import torch.distributed as dist
     from paper_2405_17696_gb300 import native
-
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-
-    w = media.workload_batched(args.sources)
-    nb = len(w.positions) * len(w.freqs_hz)
-    kappa = torch.from_numpy(w.kappa).to(dev)
-    gamma = torch.from_numpy(w.gamma).to(dev)
-    omegas = torch.from_numpy(np.asarray(w.omegas, dtype=np.float32)).to(dev)
-    rhs_host = w.rhs()
-    rhs = torch.from_numpy(rhs_host).to(dev)
-    fi = w.freq_index()
-    x = torch.empty((nb, w.nz, w.nx), dtype=torch.complex128, device=dev)
-    opts = native.helm_default_opts(mg_levels=3, max_rhs=nb, stream=stream.cuda_stream)
-    ctx = native.helm_setup(kappa, gamma, w.nx, w.nz, w.h, w.h, omegas, opts=opts)
-
-    iters_all = []
-
-    def step(rhs_arg, x_arg, kappa_arg, gamma_arg, om_arg):
-        native.helm_set_medium(ctx, kappa_arg, gamma_arg, om_arg)
-        st, iters, rel, stat = native.helm_solve(ctx, rhs_arg, x_arg, nb, fi, TOL, native.HELM_SOLVE_ZERO_X0)
-        if st != native.HELM_OK:
-            raise RuntimeError(f"solve did not converge: status {st}, per-RHS {np.unique(stat)}, "
-                               f"iterations {iters.min()}-{iters.max()}, max rel. residual {rel.max():.3e}")
-        iters_all.append(iters.copy())
-        return rel
-
-    for _ in range(max(args.warmup, 0)):
-        step(rhs, x, kappa, gamma, omegas)
+    for _ in range(max(warmup, 0)):
+        prob.step(ctx)
     torch.cuda.synchronize(dev)
-
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
     launches0 = native.helm_launch_count()
+    prob.iters.clear()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    iters_all.clear()
     ev0.record(stream)
-    rels = []
-    for _ in range(args.steps):
-        rels.append(step(rhs, x, kappa, gamma, omegas))
+    rels = [prob.step(ctx) for _ in range(steps)]
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     launches = native.helm_launch_count() - launches0
-    clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    clocks = sampler.stop() if sampler else None
+    t = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * nb * args.steps / (ms_max / 1e3)
-    its = np.concatenate(iters_all)
+    its = np.concatenate(prob.iters)
+    return float(t.item()), its, float(max(np.max(r) for r in rels)), launches, clocks
 
-    if args.no_extras:
-        native.helm_destroy(ctx)
-        if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                              "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-                              "config": config_of(w), "note": "timing only (--no-extras)"}), flush=True)
-        return
 
-    # one profiled step (per-kernel-class CUDA events + algorithmic bytes)
-    native.helm_profile_enable(ctx, True)
-    step(rhs, x, kappa, gamma, omegas)
-    prof = native.helm_profile_read(ctx)
-    native.helm_profile_enable(ctx, False)
-
-    # end to end through the C ABI with host buffers (pinned), copies inside
-    rhs_pin = torch.from_numpy(rhs_host).pin_memory()
-    x_pin = torch.empty((nb, w.nz, w.nx), dtype=torch.complex128).pin_memory()
+def e2e_of(prob, ctx, steps, dev):
+    """The same solve through the C ABI from pinned host buffers (copies inside)."""
+    import torch
+    w = prob.w
+    rhs_pin = torch.from_numpy(prob.rhs_host).pin_memory()
+    x_pin = torch.empty((prob.nb, w.nz, w.nx), dtype=torch.complex128).pin_memory()
     k_pin = torch.from_numpy(w.kappa).pin_memory()
     g_pin = torch.from_numpy(w.gamma).pin_memory()
     o_pin = torch.from_numpy(np.asarray(w.omegas, dtype=np.float32)).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
-    step(rhs_pin, x_pin, k_pin, g_pin, o_pin)          # warm the staging path
+    args = dict(rhs=rhs_pin, x=x_pin, kappa=k_pin, gamma=g_pin, om=o_pin)
+    prob.step(ctx, **args)   # warm the staging path
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        step(rhs_pin, x_pin, k_pin, g_pin, o_pin)
+    for _ in range(steps):
+        prob.step(ctx, **args)
     torch.cuda.synchronize(dev)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    h2d = rhs_pin.numel() * 8 + (k_pin.numel() + g_pin.numel() + o_pin.numel()) * 4 + nb * 4
+    sec = (time.perf_counter() - t0) / steps
+    h2d = rhs_pin.numel() * 8 + (k_pin.numel() + g_pin.numel() + o_pin.numel()) * 4 + prob.nb * 4
     d2h = x_pin.numel() * 16
-    native.helm_destroy(ctx)
+    return {"value": prob.nb / sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    if rank != 0:
+
+def profile_step(native, prob, ctx):
+    native.helm_profile_enable(ctx, True)
+    prob.step(ctx)
+    prof = native.helm_profile_read(ctx)
+    flops = native.helm_profile_flops(ctx)
+    native.helm_profile_enable(ctx, False)
+    return prof, flops
+
+
+def kernel_table(prof, flops):
+    total = sum(v[0] for v in prof.values())
+    out = {}
+    for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0]):
+        if v[1] <= 0:
+            continue
+        e = {"ms": round(v[0], 3), "share": round(v[0] / total, 4) if total else 0.0, "launches": v[1],
+             "GBps": round(v[2] / (v[0] / 1e3) / 1e9, 1) if v[0] > 0 and v[2] > 0 else None}
+        if flops.get(k, 0.0) > 0 and v[0] > 0:
+            e["TFLOPs"] = round(flops[k] / (v[0] / 1e3) / 1e12, 2)
+        out[k] = e
+    return out
+
+
+def roofline_of(prof, flops):
+    """Roofline of the dominant kernel class: algorithmic bytes (or flops) per
+    launch over the class's average CUDA-event launch time."""
+    hbm, bf16, kind = peaks()
+    name, (kms, kl, kbytes) = max(prof.items(), key=lambda kv: kv[1][0])
+    secs = kms / 1e3
+    r = {"bound": "hbm", "kernel": name, "achieved": kbytes / secs / 1e9 if secs > 0 else 0.0, "peak": hbm,
+         "unit": "GB/s", "peak_source": f"hbm_gbs of {kind}", "launches": kl,
+         "avg_launch_us": 1e3 * kms / max(kl, 1), "algorithmic_bytes_per_launch": kbytes / max(kl, 1),
+         "traffic": traffic_from_profiles(name)}
+    r["frac"] = r["achieved"] / r["peak"]
+    fl = flops.get(name, 0.0)
+    if fl > 0 and secs > 0:
+        r["tensor"] = {"achieved": fl / secs / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                       "frac": fl / secs / 1e12 / bf16, "peak_source": f"bf16_tflops of {kind}",
+                       "algorithmic_flops_per_launch": fl / max(kl, 1)}
+    return r
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2405_17696_gb300 import native, retrain as RT
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sampler = ClockSampler(local)
+
+    if args.workload == "mg":
+        w = media.workload_batched(args.sources)
+        prob = Problem(native, w, dev)
+        ctx = native.helm_setup(prob.kappa, prob.gamma, w.nx, w.nz, w.h, w.h, prob.omegas,
+                                opts=native.helm_default_opts(mg_levels=3, max_rhs=prob.nb,
+                                                              stream=stream.cuda_stream))
+        ms, its, relmax, launches, clocks = timed(prob, ctx, args.steps, args.warmup, dev, world, stream, sampler)
+        value = world * prob.nb * args.steps / (ms / 1e3)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64/f64", "data": "synthetic",
+                "config": config_of(w, "mg"), "impl": "ours", "precond": "mg",
+                "iterations": {"mean": float(its.mean()), "max": int(its.max()), "min": int(its.min())},
+                "max_rel_residual": relmax, "gpu_launches": int(launches), "clocks": clocks}
+        if not args.no_extras:
+            prof, flops = profile_step(native, prob, ctx)
+            line["roofline"] = roofline_of(prof, flops)
+            line["kernels"] = kernel_table(prof, flops)
+            line["e2e"] = e2e_of(prob, ctx, max(1, min(args.steps, 3)), dev)
+            if world == 1:
+                wo, n_rhs, desc = oracle_plan("mg")
+                n, tcpu = oracle_sample(wo, n_rhs)
+                line["cpu_baseline"] = {"value": n / tcpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                        "sample": desc}
+        native.helm_destroy(ctx)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
         return
-    peak, peak_kind = peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    name, (kms, kl, kbytes) = dom
-    achieved = kbytes / (kms / 1e3) / 1e9 if kms > 0 else 0.0
-    traffic = traffic_from_profiles(name)
-    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
-                "traffic": traffic, "launches": kl, "avg_launch_us": 1e3 * kms / max(kl, 1),
-                "algorithmic_bytes_per_launch": kbytes / max(kl, 1)}
-    cpu = None
-    if world == 1:
-        n, tcpu = oracle_sample(w)
-        cpu = {"value": n / tcpu, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": SAMPLE_DESC}
-    total_ms = sum(v[0] for v in prof.values())
-    kernels = {k: {"ms": round(v[0], 3), "share": round(v[0] / total_ms, 4) if total_ms else 0.0,
-                   "launches": v[1], "GBps": round(v[2] / (v[0] / 1e3) / 1e9, 1) if v[0] > 0 and v[2] > 0 else None}
-               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0]) if v[1] > 0}
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c64/f64", "data": "synthetic", "config": config_of(w),
-        "impl": "ours", "precond": "mg",
-        "iterations": {"mean": float(its.mean()), "max": int(its.max()), "min": int(its.min())},
-        "max_rel_residual": float(max(np.max(r) for r in rels)),
-        "roofline": roofline, "cpu_baseline": cpu,
-        "e2e": {"value": nb / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": int(launches), "clocks": clocks, "kernels": kernels,
-    }
-    print(json.dumps(line), flush=True)
+
+    # ---- CNN-FGMRES vs MG-FGMRES, 1024x512, 8 Hz, 128 RHS ----
+    w = media.workload_cnn()
+    prob = Problem(native, w, dev)
+    widths = (16, 32, 64, 128)
+    net = native.cnn_create(len(widths), widths)
+    native.cnn_init_params(net, media.SEED_CNN, 0.5)
+    opts = dict(mg_levels=3, max_rhs=prob.nb, max_iter=600, stream=stream.cuda_stream)
+    ctx_cnn = native.helm_setup(prob.kappa, prob.gamma, w.nx, w.nz, w.h, w.h, prob.omegas, net=net,
+                                opts=native.helm_default_opts(precond=native.HELM_PC_CNN, **opts))
+    ctx_mg = native.helm_setup(prob.kappa, prob.gamma, w.nx, w.nz, w.h, w.h, prob.omegas,
+                               opts=native.helm_default_opts(**opts))
+    # set-up: Alg. 2 training on this medium (not timed)
+    steps_data = sum(128 * 2 ** i // 16 for i in range(3))
+    epochs = 3 + max(1, -(-(args.train_steps - steps_data) // 64))
+    cfg = RT.RetrainConfig(initial_size=128, data_epochs=3, epochs=epochs, batch=16, lr=1e-3, lr_final=1e-4,
+                           max_steps=args.train_steps, seed=media.SEED_DATAGEN + rank)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    hist = RT.retrain(native, net, ctx_cnn, w.nx, w.nz, cfg=cfg)
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+
+    ms, its, relmax, launches, clocks = timed(prob, ctx_cnn, args.steps, args.warmup, dev, world, stream, sampler)
+    mg_ms, mg_its, mg_rel, _, _ = timed(prob, ctx_mg, args.steps, min(args.warmup, 1), dev, world, stream)
+    value = world * prob.nb * args.steps / (ms / 1e3)
+    mg_value = world * prob.nb * args.steps / (mg_ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64/f64 solve, bf16 network (fp32 accumulate)", "data": "synthetic",
+            "config": config_of(w, "cnn"), "impl": "ours", "precond": "cnn",
+            "iterations": {"mean": float(its.mean()), "max": int(its.max()), "min": int(its.min())},
+            "max_rel_residual": relmax,
+            "mg_fgmres": {"value": mg_value, "unit": UNIT, "ms_per_step": mg_ms / args.steps,
+                          "iterations": {"mean": float(mg_its.mean()), "max": int(mg_its.max()),
+                                         "min": int(mg_its.min())}, "max_rel_residual": mg_rel},
+            "training": {"steps": hist.steps, "seconds": train_s, "batch": 16, "lr": [1e-3, 1e-4],
+                         "loss_first_epoch": hist.epoch_loss[0] if hist.epoch_loss else None,
+                         "loss_last_epoch": hist.epoch_loss[-1] if hist.epoch_loss else None},
+            "gpu_launches": int(launches), "clocks": clocks}
+    if not args.no_extras:
+        prof, flops = profile_step(native, prob, ctx_cnn)
+        line["roofline"] = roofline_of(prof, flops)
+        line["kernels"] = kernel_table(prof, flops)
+        line["e2e"] = e2e_of(prob, ctx_cnn, max(1, min(args.steps, 2)), dev)
+        if world == 1:
+            wo, n_rhs, desc = oracle_plan("cnn")
+            n, tcpu = oracle_sample(wo, n_rhs)
+            line["cpu_baseline"] = {"value": n / tcpu, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    native.helm_destroy(ctx_cnn)
+    native.helm_destroy(ctx_mg)
+    native.cnn_destroy(net)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def traffic_from_profiles(kernel: str):
@@ -319,8 +434,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["cnn", "mg"], default="cnn",
+                    help="cnn: CNN-FGMRES vs MG-FGMRES at 1024x512 (default); mg: MG-FGMRES at 512x256")
+    ap.add_argument("--train-steps", type=int, default=800,
+                    help="Adam steps of the set-up training (Alg. 2) before the CNN-FGMRES timing")
     ap.add_argument("--sources", type=int, default=64,
-                    help="sources per frequency (64 = the benchmark workload; fewer only for profiling runs)")
+                    help="mg workload: sources per frequency (64 = the benchmark workload)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the solve only: no profiled step, end-to-end leg or CPU baseline (profiling runs)")
     args = ap.parse_args()

@@ -208,6 +208,9 @@ void cnn_destroy(cnn_model* net);
 long long cnn_num_params(const cnn_model* net);
 /* Load / read the FP32 parameters (host or device pointer, n = cnn_num_params). */
 int cnn_set_params(cnn_model* net, const float* params, long long n);
+/* Seeded He-normal initial weights, std = gain * sqrt(2 / (9 C_in)) per layer,
+ * zero biases (normal draws by Box-Muller from splitmix64 started at seed). */
+int cnn_init_params(cnn_model* net, unsigned long long seed, float gain);
 int cnn_get_params(const cnn_model* net, float* params, long long n);
 /* Raw network forward (inputs rounded to BF16): enc_in FP32 [nenc][ny][nx][3],
  * sol_in FP32 [nsol][ny][nx][3], out FP32 [nsol][ny][nx][2].  nenc is 1 (every
@@ -266,6 +269,11 @@ int cnn_set_conv_path(int path);
  * tile (0 = automatic: as many as two 128-column TMEM accumulator buffers and a
  * 56 KB stage allow).  Process-wide; for tuning.  HELM_EINVAL outside [0, 254]. */
 int cnn_set_conv_tiling(int max_rows);
+/* Launch shape of the last TMA convolution, for diagnostics: out6 = {grid,
+ * CTAs per SM, occupancy reported by the runtime (negative: its error code),
+ * dynamic shared memory per CTA in bytes, registers per thread, static shared
+ * memory in bytes}. */
+void cnn_conv_last_launch(int* out6);
 /* Launches of each convolution kernel since the library was loaded (either
  * pointer may be NULL). */
 void cnn_conv_launch_counts(long long* tma, long long* gather);
@@ -281,6 +289,10 @@ void cnn_conv_launch_counts(long long* tma, long long* gather);
 int helm_profile_enable(helm_ctx* ctx, int on);
 int helm_profile_read(helm_ctx* ctx, int max, const char** names, double* ms, long long* launches,
                       double* bytes, int* count);
+/* Algorithmic flops per class since profiling was enabled, in the order of
+ * helm_profile_read (nonzero for the tensor-core convolutions: 2 x 9 x C_in x
+ * C_out per output pixel of every layer of the network's forward pass). */
+int helm_profile_flops(helm_ctx* ctx, int max, double* flops, int* count);
 
 /* Number of kernels the library has launched in this process (all contexts). */
 long long helm_launch_count(void);

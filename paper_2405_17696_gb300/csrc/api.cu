@@ -49,6 +49,13 @@ LaunchScope::~LaunchScope() {
     if (c && c->prof.on && slot + 1 < c->prof.pool.size()) cudaEventRecord(c->prof.pool[slot + 1], c->stream);
 }
 
+void prof_add(const helm_ctx* c, int id, double bytes, double flops) {
+    if (!c || !c->prof.on || id < 0 || id >= K_COUNT) return;
+    helm_ctx* m = const_cast<helm_ctx*>(c);
+    m->prof.host_bytes[id] += bytes;
+    m->prof.flops[id] += flops;
+}
+
 void prof_flush(helm_ctx* c) {
     Profiler& p = c->prof;
     if (p.used == 0) return;
@@ -733,7 +740,12 @@ int helm_solve(helm_ctx* c, const helm_c64* rhs, helm_c128* x, int nrhs, const i
 int helm_profile_enable(helm_ctx* c, int on) {
     if (!c) { set_error("null context"); return HELM_EINVAL; }
     prof_flush(c);
-    for (int i = 0; i < K_COUNT; ++i) { c->prof.ms[i] = 0.0; c->prof.launches[i] = 0; }
+    for (int i = 0; i < K_COUNT; ++i) {
+        c->prof.ms[i] = 0.0;
+        c->prof.launches[i] = 0;
+        c->prof.host_bytes[i] = 0.0;
+        c->prof.flops[i] = 0.0;
+    }
     if (on && !c->prof.d_bytes) HELM_TRY(dalloc(c, &c->prof.d_bytes, K_COUNT));
     if (c->prof.d_bytes)
         HELM_CK(cudaMemsetAsync(c->prof.d_bytes, 0, K_COUNT * sizeof(unsigned long long), c->stream));
@@ -755,8 +767,17 @@ int helm_profile_read(helm_ctx* c, int max, const char** names, double* ms, long
         if (names) names[n] = kernel_name(i);
         if (ms) ms[n] = c->prof.ms[i];
         if (launches) launches[n] = c->prof.launches[i];
-        if (bytes) bytes[n] = (double)hb[i];
+        if (bytes) bytes[n] = (double)hb[i] + c->prof.host_bytes[i];
     }
+    if (count) *count = n;
+    return HELM_OK;
+}
+
+int helm_profile_flops(helm_ctx* c, int max, double* flops, int* count) {
+    if (!c) { set_error("null context"); return HELM_EINVAL; }
+    int n = 0;
+    for (int i = 0; i < K_COUNT && n < max; ++i, ++n)
+        if (flops) flops[n] = c->prof.flops[i];
     if (count) *count = n;
     return HELM_OK;
 }

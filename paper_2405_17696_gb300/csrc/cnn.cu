@@ -457,6 +457,37 @@ int cnn_set_params(cnn_model* m, const float* params, long long n) {
     return HELM_OK;
 }
 
+// He-normal initial weights (std = gain * sqrt(2 / (9 C_in))), zero biases.
+// Normal draws: Box-Muller on two uniforms from splitmix64 (Steele, Lea and
+// Flood 2014) started at `seed`; the same values on every platform.
+int cnn_init_params(cnn_model* m, unsigned long long seed, float gain) {
+    set_error("");
+    if (!m || !(gain > 0.0f)) { set_error("cnn_init_params: null model or gain <= 0"); return HELM_EINVAL; }
+    unsigned long long state = seed;
+    auto next = [&state]() {
+        unsigned long long z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto uniform = [&]() { return ((double)(next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); };   // (0, 1)
+    std::vector<float> h((size_t)m->nparams, 0.0f);
+    for (const Layer& l : m->layers) {
+        const double sd = gain * std::sqrt(2.0 / (9.0 * l.cin));
+        const long long nw = (long long)l.cout * 9 * l.cin;
+        for (long long i = 0; i < nw; i += 2) {
+            const double u1 = uniform(), u2 = uniform();
+            const double r = std::sqrt(-2.0 * std::log(u1)), t = 6.283185307179586 * u2;
+            h[(size_t)(l.off + i)] = (float)(sd * r * std::cos(t));
+            if (i + 1 < nw) h[(size_t)(l.off + i + 1)] = (float)(sd * r * std::sin(t));
+        }
+    }
+    HELM_CK(cudaMemcpy(m->master, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+    HELM_TRY(cnn_refresh_weights(m, nullptr));
+    HELM_CK(cudaDeviceSynchronize());
+    return HELM_OK;
+}
+
 int cnn_get_params(const cnn_model* m, float* params, long long n) {
     set_error("");
     if (!m || !params || n != m->nparams) { set_error("cnn_get_params: size differs from cnn_num_params"); return HELM_EINVAL; }

@@ -138,6 +138,15 @@ class Runner {
             LaunchScope scope(ctx_, K_CONV);
             s = launch_conv3x3(a, st_);
         }
+        if (ctx_ && ctx_->prof.on) {
+            // algorithmic traffic: every input, residual and output element once, the weights once
+            const double pin = (double)hin * win, pout = (double)nb * ho * wo;
+            const int n1 = x1 ? (x1_bcast == 1 ? 1 : (x1_bcast == 2 ? nctx_ : nb)) : 0;
+            double bytes = 2.0 * pin * ((double)nb * c0 + (double)n1 * c1) + 2.0 * 9.0 * l.npad * (c0 + c1);
+            if (res) bytes += 2.0 * pout * l.npad;
+            bytes += y_fp32 ? 4.0 * pout * l.cout : 2.0 * pout * l.npad;
+            prof_add(ctx_, K_CONV, bytes, 2.0 * 9.0 * l.cin * l.cout * pout);
+        }
         if (s != HELM_OK) { ok_ = false; return nullptr; }
         if (tape_) {
             TapeOp op;

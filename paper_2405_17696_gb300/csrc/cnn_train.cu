@@ -366,6 +366,7 @@ class Backward {
                 static bool attr = false;
                 if (!attr) {
                     cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+                    cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
                     attr = true;
                 }
                 LaunchScope scope(c_, K_WGRAD);

@@ -214,6 +214,8 @@ struct Profiler {
     size_t used = 0;                     // events used in the current window
     double ms[K_COUNT] = {0};
     long long launches[K_COUNT] = {0};
+    double host_bytes[K_COUNT] = {0};   // algorithmic bytes of launches whose size the host knows
+    double flops[K_COUNT] = {0};        // algorithmic flops (tensor-core kernels)
 };
 
 struct Level {
@@ -279,6 +281,8 @@ struct LaunchScope {
     ~LaunchScope();
 };
 void prof_flush(helm_ctx* c);       // accumulate recorded pairs (synchronises the stream)
+// add algorithmic bytes / flops of one launch to its class (no-op unless profiling)
+void prof_add(const helm_ctx* c, int id, double bytes, double flops);
 inline Tally tally(const helm_ctx* c, int id, unsigned long long base, unsigned long long per_step = 0) {
     Tally t;
     t.ctr = c->prof.on && c->prof.d_bytes ? c->prof.d_bytes + id : nullptr;

@@ -55,9 +55,12 @@ constexpr int EPI = 32 * EPI_WARPS;             // epilogue threads
 constexpr int NT = EPI + 64;                    // + a TMA-producer warp and an MMA-issuer warp
 constexpr int MAX_NS = 4;                       // stages (one 16-channel group of one tile each)
 constexpr long long WAIT_LIMIT = 1ll << 22;     // polls of try_wait before a wait gives up
-constexpr int SLACK_PX = 144;                   // plane padding read by the last M block of a packed tile
-constexpr size_t STAGE_BUDGET = 56 * 1024;      // bytes of one stage at most (fewer rows otherwise)
-constexpr size_t RING_BUDGET = 112 * 1024;      // bytes of the stage ring
+// No padding after a plane: the last M block of a packed tile may read up to
+// 2 pitches + 130 pixels past its plane's staged pixels, which lands in the next
+// plane or in the stage's weights (>= 288 pixels' worth), inside the stage.
+constexpr int SLACK_PX = 0;
+constexpr size_t STAGE_BUDGET = 47 * 1024;      // bytes of one stage at most (fewer rows otherwise)
+constexpr size_t RING_BUDGET = 96 * 1024;       // bytes of the stage ring (two CTAs fit an SM)
 
 struct Geometry {
     int tw, rows, pw;        // tile on the staged grid (output grid in mode 1); staged row pitch
@@ -396,6 +399,8 @@ bool encode_w(CUtensorMap* m, const void* base, int cin, int npad) {
 }
 
 std::atomic<int> g_rows_cap{0};   // tile-height limit set by cnn_set_conv_tiling (0 = automatic)
+int g_last_launch[6] = {0, 0, 0, 0, 0, 0};   // grid, CTAs per SM, occupancy (or -error), shared memory,
+                                             // registers per thread, static shared memory
 
 // Tile plan; .tiles = 0 when the layer does not fit this kernel.
 Geometry plan(const ConvArgs& a) {
@@ -474,6 +479,8 @@ int launch_mode(const CUtensorMap& tm0, const CUtensorMap& tm1, const CUtensorMa
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(conv3x3_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        // all of the unified L1/shared storage as shared memory: two CTAs of ~100 KB per SM
+        cudaFuncSetAttribute(conv3x3_tma_kernel<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     });
     const size_t smem = (size_t)g.ns * g.stage;
     // two CTAs per SM when two fit the 512 TMEM columns, else one; a shared-memory
@@ -481,12 +488,25 @@ int launch_mode(const CUtensorMap& tm0, const CUtensorMap& tm1, const CUtensorMa
     int per_sm = g.tmem_cols <= 256 ? 2 : 1;
     const size_t smem_req = std::max<size_t>(smem, per_sm == 2 ? 80 * 1024 : 120 * 1024);
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3x3_tma_kernel<MODE>, NT, smem_req) != cudaSuccess) {
+    const cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3x3_tma_kernel<MODE>, NT, smem_req);
+    if (oe != cudaSuccess) {
         (void)cudaGetLastError();
-        occ = 1;
+        occ = -(int)oe;
+    } else {
+        per_sm = std::max(1, std::min(per_sm, occ));
     }
-    per_sm = std::max(1, std::min(per_sm, occ));
     const long long grid = std::min<long long>(g.tiles, (long long)per_sm * sm_count());
+    g_last_launch[0] = (int)grid;
+    g_last_launch[1] = per_sm;
+    g_last_launch[2] = occ;
+    g_last_launch[3] = (int)smem_req;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, conv3x3_tma_kernel<MODE>) == cudaSuccess) {
+        g_last_launch[4] = fa.numRegs;
+        g_last_launch[5] = (int)fa.sharedSizeBytes;
+    } else {
+        (void)cudaGetLastError();
+    }
     conv3x3_tma_kernel<MODE><<<(unsigned)grid, NT, smem_req, st>>>(tm0, tm1, tmw, a, g);
     return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
 }
@@ -540,4 +560,12 @@ extern "C" int cnn_set_conv_tiling(int max_rows) {
     }
     helm::g_rows_cap.store(max_rows);
     return HELM_OK;
+}
+
+// Launch shape of the last TMA convolution (diagnostics): grid, CTAs per SM,
+// the occupancy the runtime reported (negative: its error code), dynamic
+// shared memory per CTA, registers per thread, static shared memory.
+extern "C" void cnn_conv_last_launch(int* out6) {
+    if (!out6) return;
+    for (int i = 0; i < 6; ++i) out6[i] = helm::g_last_launch[i];
 }

@@ -95,10 +95,14 @@ def _load():
     lib.cnn_precond_apply.restype = ip
     lib.cnn_conv3x3.argtypes = [vp, ip, vp, ip, ip, ip, ip, ip, vp, vp, ip, vp, ip, ip, vp]
     lib.cnn_conv3x3.restype = ip
+    lib.cnn_init_params.argtypes = [vp, ctypes.c_ulonglong, fp]
+    lib.cnn_init_params.restype = ip
     lib.cnn_set_conv_path.argtypes = [ip]
     lib.cnn_set_conv_path.restype = ip
     lib.cnn_set_conv_tiling.argtypes = [ip]
     lib.cnn_set_conv_tiling.restype = ip
+    lib.cnn_conv_last_launch.argtypes = [ctypes.POINTER(ctypes.c_int)]
+    lib.cnn_conv_last_launch.restype = None
     lib.cnn_conv_launch_counts.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.cnn_conv_launch_counts.restype = None
     lib.helm_destroy.argtypes = [vp]
@@ -111,6 +115,8 @@ def _load():
                                       ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int)]
     lib.helm_profile_read.restype = ip
+    lib.helm_profile_flops.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+    lib.helm_profile_flops.restype = ip
     lib.helm_launch_count.argtypes = []
     lib.helm_launch_count.restype = ctypes.c_longlong
     return lib
@@ -267,6 +273,17 @@ def helm_profile_read(ctx) -> dict:
     return {names[i].decode(): (ms[i], cnt[i], nbytes[i]) for i in range(k.value)}
 
 
+def helm_profile_flops(ctx) -> dict:
+    """{kernel class: algorithmic flops} since profiling was enabled"""
+    n = 64
+    names = (ctypes.c_char_p * n)()
+    k = ctypes.c_int(0)
+    _check(lib.helm_profile_read(ctx, n, names, None, None, None, ctypes.byref(k)), "helm_profile_read")
+    fl = (ctypes.c_double * n)()
+    _check(lib.helm_profile_flops(ctx, n, fl, ctypes.byref(k)), "helm_profile_flops")
+    return {names[i].decode(): fl[i] for i in range(k.value)}
+
+
 def helm_launch_count() -> int:
     return int(lib.helm_launch_count())
 
@@ -311,6 +328,11 @@ def cnn_conv3x3(x0, c0: int, x1, c1: int, x1_bcast: int, nb: int, hin: int, win:
                            _ptr(y, "float32")), "cnn_conv3x3")
 
 
+def cnn_init_params(net, seed: int, gain: float = 1.0):
+    """Seeded He-normal weights (scaled by gain), zero biases."""
+    _check(lib.cnn_init_params(net, int(seed), float(gain)), "cnn_init_params")
+
+
 def cnn_set_conv_path(path: int):
     """0: TMA halo-tile kernel for same-grid layers (default); 1: gather kernel for all."""
     _check(lib.cnn_set_conv_path(int(path)), "cnn_set_conv_path")
@@ -319,6 +341,14 @@ def cnn_set_conv_path(path: int):
 def cnn_set_conv_tiling(max_rows: int):
     """Tile-height limit of the TMA conv kernel (0 = automatic)."""
     _check(lib.cnn_set_conv_tiling(int(max_rows)), "cnn_set_conv_tiling")
+
+
+def cnn_conv_last_launch():
+    """(grid, CTAs per SM, runtime occupancy or -error, shared memory bytes, registers, static smem)
+    of the last TMA conv."""
+    out = (ctypes.c_int * 6)()
+    lib.cnn_conv_last_launch(out)
+    return tuple(out)
 
 
 def cnn_conv_launch_counts():

@@ -183,3 +183,33 @@ def test_cnn_fgmres_solve(native):
     for b in range(rhs.shape[0]):
         om = float(np.float32(w.omegas[fi[b]]))
         assert H.relative_residual(xs[b], rhs[b], kap, gam, om, w.h, w.h) <= 1e-6
+
+
+def test_init_params_he_normal(native):
+    """cnn_init_params: zero biases, per-layer He-normal spread, reproducible by seed."""
+    widths = (16, 32, 64, 128)
+    specs = cnn.layer_specs(widths=widths)
+    net = native.cnn_create(len(widths), widths)
+    try:
+        native.cnn_init_params(net, 7, 0.5)
+        a = np.zeros(cnn.n_params(specs), np.float32)
+        native.cnn_get_params(net, a)
+        native.cnn_init_params(net, 7, 0.5)
+        b = np.zeros_like(a)
+        native.cnn_get_params(net, b)
+        native.cnn_init_params(net, 8, 0.5)
+        c = np.zeros_like(a)
+        native.cnn_get_params(net, c)
+    finally:
+        native.cnn_destroy(net)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    o = 0
+    for name, ci, co, _ in specs:
+        nw = co * 9 * ci
+        wts, bias = a[o:o + nw], a[o + nw:o + nw + co]
+        o += nw + co
+        assert np.all(bias == 0), name
+        sd = 0.5 * np.sqrt(2.0 / (9 * ci))
+        # sample std within 5 standard errors of the target
+        assert abs(wts.std() / sd - 1) < 5 / np.sqrt(2 * nw) + 1e-3, (name, wts.std(), sd)
+        assert abs(wts.mean()) < 5 * sd / np.sqrt(nw), name
