@@ -267,10 +267,10 @@ int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, 
 int cnn_set_conv_path(int path);
 /* Tile height limit of the TMA halo-tile kernel: at most max_rows output rows per
  * tile (0 = automatic: as many as two 128-column TMEM accumulator buffers and a
- * 56 KB stage allow).  Process-wide; for tuning.  HELM_EINVAL outside [0, 254]. */
+ * 47 KB stage allow).  Process-wide; for tuning.  HELM_EINVAL outside [0, 254]. */
 int cnn_set_conv_tiling(int max_rows);
 /* Launch shape of the last TMA convolution, for diagnostics: out6 = {grid,
- * CTAs per SM, occupancy reported by the runtime (negative: its error code),
+ * CTAs per SM, CTAs per SM that registers and shared memory allow,
  * dynamic shared memory per CTA in bytes, registers per thread, static shared
  * memory in bytes}. */
 void cnn_conv_last_launch(int* out6);

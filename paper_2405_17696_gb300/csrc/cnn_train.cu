@@ -308,7 +308,6 @@ class Backward {
     ~Backward() {
         for (void* p : owned_) cudaFree(p);
     }
-    bool ok() const { return ok_; }
 
     // gradient buffer of an activation (allocated and zeroed on first use)
     float* grad_of(const void* act, size_t n) {

@@ -399,7 +399,7 @@ bool encode_w(CUtensorMap* m, const void* base, int cin, int npad) {
 }
 
 std::atomic<int> g_rows_cap{0};   // tile-height limit set by cnn_set_conv_tiling (0 = automatic)
-int g_last_launch[6] = {0, 0, 0, 0, 0, 0};   // grid, CTAs per SM, occupancy (or -error), shared memory,
+int g_last_launch[6] = {0, 0, 0, 0, 0, 0};   // grid, CTAs per SM, CTAs registers/smem allow, shared memory,
                                              // registers per thread, static shared memory
 
 // Tile plan; .tiles = 0 when the layer does not fit this kernel.
@@ -460,6 +460,19 @@ Geometry plan(const ConvArgs& a) {
     return g;
 }
 
+int smem_per_sm() {
+    static int n = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+            n = 0;
+        (void)cudaGetLastError();
+    });
+    return n > 0 ? n : 228 * 1024;
+}
+
 int sm_count() {
     static int n = 0;
     static std::once_flag once;
@@ -487,26 +500,31 @@ int launch_mode(const CUtensorMap& tm0, const CUtensorMap& tm1, const CUtensorMa
     // request above a third (half) of the SM keeps further CTAs off
     int per_sm = g.tmem_cols <= 256 ? 2 : 1;
     const size_t smem_req = std::max<size_t>(smem, per_sm == 2 ? 80 * 1024 : 120 * 1024);
-    int occ = 0;
-    const cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3x3_tma_kernel<MODE>, NT, smem_req);
-    if (oe != cudaSuccess) {
-        (void)cudaGetLastError();
-        occ = -(int)oe;
-    } else {
-        per_sm = std::max(1, std::min(per_sm, occ));
-    }
+    // resident CTAs per SM from this kernel's registers and shared memory (the
+    // runtime's occupancy query assumes a smaller shared-memory carveout here)
+    static int regs = 0, static_smem = 0;
+    static std::once_flag attrs;
+    std::call_once(attrs, [] {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, conv3x3_tma_kernel<MODE>) == cudaSuccess) {
+            regs = fa.numRegs;
+            static_smem = (int)fa.sharedSizeBytes;
+        } else {
+            (void)cudaGetLastError();
+        }
+    });
+    const size_t per_cta_smem = smem_req + (size_t)static_smem + 1024;   // + the driver's reservation
+    const int by_smem = (int)((size_t)smem_per_sm() / per_cta_smem);
+    const int by_regs = regs > 0 ? 65536 / (((regs * 32 + 255) / 256) * 256 * (NT / 32)) : 1;
+    const int occ = std::min(by_smem, by_regs);
+    per_sm = std::max(1, std::min(per_sm, occ));
     const long long grid = std::min<long long>(g.tiles, (long long)per_sm * sm_count());
     g_last_launch[0] = (int)grid;
     g_last_launch[1] = per_sm;
     g_last_launch[2] = occ;
     g_last_launch[3] = (int)smem_req;
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, conv3x3_tma_kernel<MODE>) == cudaSuccess) {
-        g_last_launch[4] = fa.numRegs;
-        g_last_launch[5] = (int)fa.sharedSizeBytes;
-    } else {
-        (void)cudaGetLastError();
-    }
+    g_last_launch[4] = regs;
+    g_last_launch[5] = static_smem;
     conv3x3_tma_kernel<MODE><<<(unsigned)grid, NT, smem_req, st>>>(tm0, tm1, tmw, a, g);
     return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
 }
@@ -563,7 +581,7 @@ extern "C" int cnn_set_conv_tiling(int max_rows) {
 }
 
 // Launch shape of the last TMA convolution (diagnostics): grid, CTAs per SM,
-// the occupancy the runtime reported (negative: its error code), dynamic
+// the CTAs per SM that registers and shared memory allow, dynamic
 // shared memory per CTA, registers per thread, static shared memory.
 extern "C" void cnn_conv_last_launch(int* out6) {
     if (!out6) return;

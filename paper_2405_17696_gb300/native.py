@@ -344,7 +344,7 @@ def cnn_set_conv_tiling(max_rows: int):
 
 
 def cnn_conv_last_launch():
-    """(grid, CTAs per SM, runtime occupancy or -error, shared memory bytes, registers, static smem)
+    """(grid, CTAs per SM, CTAs per SM allowed by registers and smem, shared memory bytes, registers, static smem)
     of the last TMA conv."""
     out = (ctypes.c_int * 6)()
     lib.cnn_conv_last_launch(out)

@@ -155,3 +155,54 @@ def test_adam_steps_lower_the_loss(native):
         native.helm_destroy(ctx)
         native.cnn_destroy(net)
     assert np.mean(losses[-5:]) < 0.9 * losses[0], losses
+
+
+def test_trained_network_reduces_iterations(native):
+    """What the trained network gains (Sec. 4.1-4.2): on a 128x64 layered medium at
+    6 Hz, Alg. 2 training from seeded He weights (2500 Adam steps, batch 16, Eq. 4.3
+    data) makes CNN-FGMRES reach 1e-6 in well under the iterations of MG-FGMRES
+    (measured about 25 against 66).  The loss first stalls near the error energy
+    the network cannot yet reach (about 16 from 27) and drops once it learns the
+    smooth error components; the step at which that happens varies between runs
+    (atomic summation order in the weight gradient), hence the budget."""
+    from paper_2405_17696_gb300 import retrain as RT
+    nx, nz, h = 128, 64, 20.0
+    c = media.layered_velocity(nx, nz, seed=0)
+    w = media.Workload("gain", nx, nz, h, [6.0], media.kappa_of(c), media.abl_gamma(nx, nz, 16),
+                       media.top_row_positions(nx, 8))
+    kap = torch.from_numpy(w.kappa).cuda()
+    gam = torch.from_numpy(w.gamma).cuda()
+    om = torch.from_numpy(np.asarray(w.omegas, np.float32)).cuda()
+    rhs = torch.from_numpy(w.rhs()).cuda()
+    nb = rhs.shape[0]
+
+    def solve(ctx):
+        x = torch.zeros(rhs.shape, dtype=torch.complex128, device="cuda")
+        st, it, rel, _ = native.helm_solve(ctx, rhs, x, nb, None, 1e-6, native.HELM_SOLVE_ZERO_X0)
+        assert st == native.HELM_OK and rel.max() <= 1e-6
+        return float(it.mean())
+
+    ctx = native.helm_setup(kap, gam, nx, nz, h, h, om, opts=native.helm_default_opts(mg_levels=3, max_iter=600))
+    try:
+        mg = solve(ctx)
+    finally:
+        native.helm_destroy(ctx)
+    widths = (16, 32, 64, 128)
+    net = native.cnn_create(len(widths), widths)
+    ctx = None
+    try:
+        native.cnn_init_params(net, media.SEED_CNN, 0.5)
+        ctx = native.helm_setup(kap, gam, nx, nz, h, h, om, net=net, opts=native.helm_default_opts(
+            mg_levels=3, max_iter=600, precond=native.HELM_PC_CNN, max_rhs=32))
+        untrained = solve(ctx)
+        steps = 2500
+        cfg = RT.RetrainConfig(initial_size=128, data_epochs=3, epochs=3 + -(-(steps - 56) // 64), batch=16,
+                               lr=1e-3, lr_final=1e-4, max_steps=steps)
+        hist = RT.retrain(native, net, ctx, nx, nz, cfg=cfg)
+        trained = solve(ctx)
+    finally:
+        if ctx is not None:
+            native.helm_destroy(ctx)
+        native.cnn_destroy(net)
+    assert hist.epoch_loss[-1] < 0.5 * hist.epoch_loss[0], hist.epoch_loss
+    assert trained <= 0.6 * mg, (trained, mg, untrained)
