@@ -357,7 +357,7 @@ def run_ours(args, rank, world):
         return
 
     # ---- CNN-FGMRES vs MG-FGMRES, 1024x512, 8 Hz, 128 RHS ----
-    w = media.workload_cnn()
+    w = media.workload_cnn(args.sources_cnn)
     prob = Problem(native, w, dev)
     widths = (16, 32, 64, 128)
     net = native.cnn_create(len(widths), widths)
@@ -399,7 +399,7 @@ def run_ours(args, rank, world):
         prof, flops = profile_step(native, prob, ctx_cnn)
         line["roofline"] = roofline_of(prof, flops)
         line["kernels"] = kernel_table(prof, flops)
-        line["e2e"] = e2e_of(prob, ctx_cnn, max(1, min(args.steps, 2)), dev)
+        line["e2e"] = e2e_of(prob, ctx_cnn, 1, dev)
         if world == 1:
             wo, n_rhs, desc = oracle_plan("cnn")
             n, tcpu = oracle_sample(wo, n_rhs)
@@ -436,10 +436,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["cnn", "mg"], default="cnn",
                     help="cnn: CNN-FGMRES vs MG-FGMRES at 1024x512 (default); mg: MG-FGMRES at 512x256")
-    ap.add_argument("--train-steps", type=int, default=800,
+    ap.add_argument("--train-steps", type=int, default=400,
                     help="Adam steps of the set-up training (Alg. 2) before the CNN-FGMRES timing")
     ap.add_argument("--sources", type=int, default=64,
                     help="mg workload: sources per frequency (64 = the benchmark workload)")
+    ap.add_argument("--sources-cnn", type=int, default=128,
+                    help="cnn workload: sources (128 = the benchmark workload; fewer only for profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the solve only: no profiled step, end-to-end leg or CPU baseline (profiling runs)")
     args = ap.parse_args()

@@ -98,6 +98,30 @@ struct OpFine5 {
         y.y = ax * (2.f * uc.y - uw.y - ue.y) + az * (2.f * uc.y - un.y - us.y) - (c.x * uc.y + c.y * uc.x);
         return y;
     }
+    // (H u) at the node pair (ix, ix + 1), ix even and nx even: 16-byte loads
+    __device__ __forceinline__ void apply2(const float2* __restrict__ u, int b, int ix, int iz, float2& y0,
+                                           float2& y1) const {
+        const int idx = iz * nx + ix;
+        const float4 c = *reinterpret_cast<const float4*>(u + idx);
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 n = iz > 0 ? *reinterpret_cast<const float4*>(u + idx - nx) : zero;
+        const float4 s = iz < nz - 1 ? *reinterpret_cast<const float4*>(u + idx + nx) : zero;
+        const float2 w0 = ix > 0 ? u[idx - 1] : make_float2(0.f, 0.f);
+        const float2 e1 = ix + 2 < nx ? u[idx + 2] : make_float2(0.f, 0.f);
+        const float4 mm = __ldg(reinterpret_cast<const float4*>(mg + idx));
+        const float wf = __ldg(omega + __ldg(rhs_freq + b));
+        const float w2 = wf * wf;
+        const float s0 = w2 * (mm.x * mm.x), s1 = w2 * (mm.z * mm.z);
+        const float g0 = sl ? (beta + (incg ? mm.y : 0.0f)) : mm.y;
+        const float g1 = sl ? (beta + (incg ? mm.w : 0.0f)) : mm.w;
+        const float2 k0 = make_float2(s0, -s0 * g0), k1 = make_float2(s1, -s1 * g1);
+        // node 0: west w0, east = node 1
+        y0.x = ax * (2.f * c.x - w0.x - c.z) + az * (2.f * c.x - n.x - s.x) - (k0.x * c.x - k0.y * c.y);
+        y0.y = ax * (2.f * c.y - w0.y - c.w) + az * (2.f * c.y - n.y - s.y) - (k0.x * c.y + k0.y * c.x);
+        // node 1: west = node 0, east e1
+        y1.x = ax * (2.f * c.z - c.x - e1.x) + az * (2.f * c.z - n.z - s.z) - (k1.x * c.z - k1.y * c.w);
+        y1.y = ax * (2.f * c.w - c.y - e1.y) + az * (2.f * c.w - n.w - s.w) - (k1.x * c.w + k1.y * c.z);
+    }
     __device__ __forceinline__ double2 entry(int f, int iz, int ix, int k) const {
         // fine stencil entries in double for the Galerkin product (frequency f)
         int dz = k / 3 - 1, dx = k % 3 - 1;

@@ -14,12 +14,14 @@
 namespace helm {
 namespace {
 
-constexpr int CB = 512;                 // threads per block (one block per RHS)
-constexpr int CW = CB / 32;
+// Threads per block (one block per RHS): 512 when every RHS has an SM of its
+// own, 256 (two blocks per SM) when the batch is larger than the SM count, so
+// that the whole batch runs in one wave.
 
 // Sum nv complex values held per thread over the block (FP64), result in out[0..nv).
-template <int NV>
+template <int CB, int NV>
 __device__ void block_sum(const float2 (&v)[NV], int nv, double2* red /*[CW][NV]*/, double2* out) {
+    constexpr int CW = CB / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
@@ -38,7 +40,8 @@ __device__ void block_sum(const float2 (&v)[NV], int nv, double2* red /*[CW][NV]
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(CB, 1)
+template <int CB>
+__global__ void __launch_bounds__(CB, 512 / CB)
 coarse_gmres_kernel(OpC9 op, float2* __restrict__ V, size_t vstride, float2* __restrict__ W, float2* __restrict__ u,
                     int kmax, const int* mask, Tally tl) {
     const int b = blockIdx.x;
@@ -48,6 +51,7 @@ coarse_gmres_kernel(OpC9 op, float2* __restrict__ V, size_t vstride, float2* __r
     const int n = nx * nz;
     float2* Vb = V + (size_t)b * n;       // vector i at Vb + i * vstride
     float2* Wb = W + (size_t)b * n;
+    constexpr int CW = CB / 32;
     __shared__ double2 red[CW * (KMAX + 1)];
     __shared__ double2 sums[KMAX + 1];
     __shared__ double2 H[KMAX][KMAX + 1];  // H[j][i] = h_{i,j}
@@ -62,11 +66,11 @@ coarse_gmres_kernel(OpC9 op, float2* __restrict__ V, size_t vstride, float2* __r
     // beta = ||f||, f stored as v_0
     {
         float2 a[1] = {make_float2(0.f, 0.f)};
-        for (int p = threadIdx.x; p < n; p += CB) {
-            float2 f = Vb[p];
-            a[0].x += f.x * f.x + f.y * f.y;
+        for (int p = 2 * threadIdx.x; p < n; p += 2 * CB) {
+            const float4 f = *reinterpret_cast<const float4*>(Vb + p);
+            a[0].x += f.x * f.x + f.y * f.y + f.z * f.z + f.w * f.w;
         }
-        block_sum<1>(a, 1, red, sums);
+        block_sum<CB, 1>(a, 1, red, sums);
     }
     const double beta = sqrt(sums[0].x);
     if (!(beta > 0.0) || !isfinite(beta)) {
@@ -87,22 +91,25 @@ coarse_gmres_kernel(OpC9 op, float2* __restrict__ V, size_t vstride, float2* __r
 #pragma unroll
         for (int i = 0; i <= KMAX; ++i) acc[i] = make_float2(0.f, 0.f);
         const float2* vj = Vb + (size_t)j * vstride;
-        for (int p = threadIdx.x; p < n; p += CB) {
+        // two nodes per thread (n even, vectors 16-byte aligned): 16-byte loads
+        for (int p = 2 * threadIdx.x; p < n; p += 2 * CB) {
             const int iz = p / nx, ix = p - iz * nx;
-            float2 y = op.apply(vj, b, ix, iz);
-            y.x *= sj;
-            y.y *= sj;
-            Wb[p] = y;
+            float2 y0 = op.apply(vj, b, ix, iz), y1 = op.apply(vj, b, ix + 1, iz);
+            y0.x *= sj;
+            y0.y *= sj;
+            y1.x *= sj;
+            y1.y *= sj;
+            *reinterpret_cast<float4*>(Wb + p) = make_float4(y0.x, y0.y, y1.x, y1.y);
 #pragma unroll
             for (int i = 0; i <= KMAX; ++i) {
                 if (i <= j) {
-                    float2 v = Vb[(size_t)i * vstride + p];
-                    acc[i].x += v.x * y.x + v.y * y.y;
-                    acc[i].y += v.x * y.y - v.y * y.x;
+                    const float4 v = *reinterpret_cast<const float4*>(Vb + (size_t)i * vstride + p);
+                    acc[i].x += v.x * y0.x + v.y * y0.y + v.z * y1.x + v.w * y1.y;
+                    acc[i].y += v.x * y0.y - v.y * y0.x + v.z * y1.y - v.w * y1.x;
                 }
             }
         }
-        block_sum<KMAX + 1>(acc, j + 1, red, sums);
+        block_sum<CB, KMAX + 1>(acc, j + 1, red, sums);
         if (threadIdx.x <= j) {
             double s = sc[threadIdx.x];
             double2 h = make_double2(sums[threadIdx.x].x * s, sums[threadIdx.x].y * s);
@@ -113,21 +120,23 @@ coarse_gmres_kernel(OpC9 op, float2* __restrict__ V, size_t vstride, float2* __r
         // pass B: w' = w - sum_i h_ij s_i v_i stored as v_{j+1}; ||w'||
         float2 nacc[1] = {make_float2(0.f, 0.f)};
         float2* vn = Vb + (size_t)(j + 1) * vstride;
-        for (int p = threadIdx.x; p < n; p += CB) {
-            float2 y = Wb[p];
+        for (int p = 2 * threadIdx.x; p < n; p += 2 * CB) {
+            float4 y = *reinterpret_cast<const float4*>(Wb + p);
 #pragma unroll
             for (int i = 0; i <= KMAX; ++i) {
                 if (i <= j) {
-                    float2 v = Vb[(size_t)i * vstride + p];
+                    const float4 v = *reinterpret_cast<const float4*>(Vb + (size_t)i * vstride + p);
                     const float2 cf = cfs[i];
                     y.x -= cf.x * v.x - cf.y * v.y;
                     y.y -= cf.x * v.y + cf.y * v.x;
+                    y.z -= cf.x * v.z - cf.y * v.w;
+                    y.w -= cf.x * v.w + cf.y * v.z;
                 }
             }
-            vn[p] = y;
-            nacc[0].x += y.x * y.x + y.y * y.y;
+            *reinterpret_cast<float4*>(vn + p) = y;
+            nacc[0].x += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
         }
-        block_sum<1>(nacc, 1, red, sums);
+        block_sum<CB, 1>(nacc, 1, red, sums);
         if (threadIdx.x == 0) {
             const double hb = sqrt(sums[0].x);
             double2* hc = H[j];
@@ -184,18 +193,20 @@ coarse_gmres_kernel(OpC9 op, float2* __restrict__ V, size_t vstride, float2* __r
         cfs[threadIdx.x] = make_float2((float)(v.x * s), (float)(v.y * s));
     }
     __syncthreads();
-    for (int p = threadIdx.x; p < n; p += CB) {
-        float2 acc = make_float2(0.f, 0.f);
+    for (int p = 2 * threadIdx.x; p < n; p += 2 * CB) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < KMAX; ++i) {
             if (i < m) {
-                float2 v = Vb[(size_t)i * vstride + p];
+                const float4 v = *reinterpret_cast<const float4*>(Vb + (size_t)i * vstride + p);
                 const float2 yc = cfs[i];
                 acc.x += yc.x * v.x - yc.y * v.y;
                 acc.y += yc.x * v.y + yc.y * v.x;
+                acc.z += yc.x * v.z - yc.y * v.w;
+                acc.w += yc.x * v.w + yc.y * v.z;
             }
         }
-        u[(size_t)b * n + p] = acc;
+        *reinterpret_cast<float4*>(u + (size_t)b * n + p) = acc;
     }
 }
 
@@ -205,12 +216,26 @@ int launch_coarse_gmres(const helm_ctx* c, int level, float2* u_out, int nb, con
     const Level& L = c->lev[level];
     const size_t Nc = (size_t)L.nx * L.nz;
     const int k = c->opt.coarse_iters;
+    if (Nc % 2) {
+        set_error("coarsest multigrid level needs an even number of nodes (two per thread)");
+        return HELM_EINVAL;
+    }
     // per RHS: ||f|| (1 vector), step j: 2(j + 1) basis reads + v_j + w write/read + v_{j+1} write,
     // final combination k reads + 1 write: 8 Nc (k^2 + 5k + 2) bytes
     LaunchScope scope(c, K_COARSE_GMRES);
     const unsigned long long kk = (unsigned long long)k;
-    coarse_gmres_kernel<<<nb, CB, 0, c->stream>>>(coarse_op(c, level), c->Vc, (size_t)c->cap * Nc, c->Wc, u_out, k,
-                                                  mask, tally(c, K_COARSE_GMRES, 8ull * Nc * (kk * kk + 5 * kk + 2)));
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        sms = 0;
+    }
+    const Tally tl = tally(c, K_COARSE_GMRES, 8ull * Nc * (kk * kk + 5 * kk + 2));
+    if (sms > 0 && nb > sms)
+        coarse_gmres_kernel<256><<<nb, 256, 0, c->stream>>>(coarse_op(c, level), c->Vc, (size_t)c->cap * Nc, c->Wc,
+                                                            u_out, k, mask, tl);
+    else
+        coarse_gmres_kernel<512><<<nb, 512, 0, c->stream>>>(coarse_op(c, level), c->Vc, (size_t)c->cap * Nc, c->Wc,
+                                                            u_out, k, mask, tl);
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }

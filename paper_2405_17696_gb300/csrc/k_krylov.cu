@@ -341,6 +341,78 @@ __global__ void update_x64_kernel(KState st, double2* __restrict__ x, const floa
 // launchers
 // --------------------------------------------------------------------------
 
+// The fine-grid Arnoldi dots with two nodes per thread (16-byte loads of every
+// basis vector and of z), otherwise as arnoldi_dots_kernel: w = H z and the
+// inner products <v~_i, w>, ||w||^2 with the last-block reduction.
+template <int J>
+__global__ void __launch_bounds__(NTHREADS, 3) arnoldi_dots_fine2_kernel(OpFine5 op, KState st,
+                                                                        const float2* __restrict__ z,
+                                                                        float2* __restrict__ w,
+                                                                        const float2* __restrict__ V,
+                                                                        size_t vstride, int nx, int nz, Tally tl) {
+    const int b = blockIdx.z;
+    if (!st.active[b]) return;
+    tally_once(tl, blockIdx.x == 0 && blockIdx.y == 0);
+    const size_t N = (size_t)nx * nz;
+    const float2* zb = z + (size_t)b * N;
+    float2* wb = w + (size_t)b * N;
+    const float2* Vb = V + (size_t)b * N;
+    const int ix = 2 * (blockIdx.x * TILE_X + threadIdx.x);
+    const int iz0 = (blockIdx.y * TILE_Y + threadIdx.y) * ROWS;
+    float2 acc[J + 2];
+#pragma unroll
+    for (int i = 0; i < J + 2; ++i) acc[i] = make_float2(0.f, 0.f);
+    if (ix < nx) {
+#pragma unroll 2
+        for (int r = 0; r < ROWS; ++r) {
+            const int iz = iz0 + r;
+            if (iz >= nz) break;
+            const size_t p = (size_t)iz * nx + ix;
+            float4 v[J + 1];
+#pragma unroll
+            for (int i = 0; i <= J; ++i) v[i] = *reinterpret_cast<const float4*>(Vb + (size_t)i * vstride + p);
+            float2 y0, y1;
+            op.apply2(zb, b, ix, iz, y0, y1);
+            *reinterpret_cast<float4*>(wb + p) = make_float4(y0.x, y0.y, y1.x, y1.y);
+#pragma unroll
+            for (int i = 0; i <= J; ++i) {
+                acc[i].x += v[i].x * y0.x + v[i].y * y0.y + v[i].z * y1.x + v[i].w * y1.y;
+                acc[i].y += v[i].x * y0.y - v[i].y * y0.x + v[i].z * y1.y - v[i].w * y1.x;
+            }
+            acc[J + 1].x += y0.x * y0.x + y0.y * y0.y + y1.x * y1.x + y1.y * y1.y;
+        }
+    }
+    __shared__ double2 sm[NWARPS * (J + 2)];
+    __shared__ double hsq[J + 2];
+    const int ntiles = gridDim.x * gridDim.y;
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    double2* part = st.partials + ((size_t)b * st.max_tiles) * (KMAX + 2);
+    bool last = reduce_block_last<J + 2>(acc, J + 2, part + (size_t)tile * (KMAX + 2), st.counters + b, ntiles, sm);
+    if (last) {
+        const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+        if (tid <= J + 1) {
+            double2 h = sum_partials(part, ntiles, KMAX + 2, tid);
+            if (tid <= J) {
+                double sc = st.s[(size_t)b * (st.k + 1) + tid];
+                h = make_double2(h.x * sc, h.y * sc);
+                kcol(st, b, J)[tid] = h;
+                hsq[tid] = dabs2(h);
+            } else {
+                hsq[tid] = h.x;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double w2 = hsq[J + 1], proj = 0.0;
+            for (int i = 0; i <= J; ++i) proj += hsq[i];
+            double est2 = w2 - proj;
+            if (!(est2 > 1e-12 * w2)) est2 = 1e-12 * w2;
+            double est = sqrt(est2);
+            st.inv_est[b] = (est > 0.0 && isfinite(est)) ? 1.0 / est : 1.0;
+        }
+    }
+}
+
 static dim3 tiled_grid(int nx, int nz, int nb) {
     return dim3((nx + TILE_X - 1) / TILE_X, (nz + TILE_Y * ROWS - 1) / (TILE_Y * ROWS), nb);
 }
@@ -354,6 +426,25 @@ int launch_arnoldi_dots(const helm_ctx* c, const Op& op, KState& st, const float
     LaunchScope scope(c, std::is_same<Op, OpFine5>::value ? K_DOTS_FINE : K_DOTS_COARSE);
     const Tally tl = tally(c, std::is_same<Op, OpFine5>::value ? K_DOTS_FINE : K_DOTS_COARSE,
                            8ull * nx * nz * (j + 3));
+    if constexpr (std::is_same<Op, OpFine5>::value) {
+        if (nx % 2 == 0) {
+            const dim3 grid2((nx / 2 + TILE_X - 1) / TILE_X, (nz + TILE_Y * ROWS - 1) / (TILE_Y * ROWS), nb),
+                block2(TILE_X, TILE_Y);
+            switch (j) {
+#define HELM_DOTS2_CASE(J)                                                                                  \
+    case J:                                                                                                 \
+        arnoldi_dots_fine2_kernel<J><<<grid2, block2, 0, c->stream>>>(op, st, z, w, V, vstride, nx, nz, tl); \
+        break;
+                HELM_J_CASES(HELM_DOTS2_CASE)
+#undef HELM_DOTS2_CASE
+                default:
+                    set_error("Arnoldi step beyond KMAX");
+                    return HELM_EINVAL;
+            }
+            HELM_CK(cudaGetLastError());
+            return HELM_OK;
+        }
+    }
     const dim3 grid = tiled_grid(nx, nz, nb), block(TILE_X, TILE_Y);
     switch (j) {
 #define HELM_DOTS_CASE(J)                                                                                     \

@@ -13,6 +13,30 @@ namespace helm {
 namespace {
 
 // u_out = u_in + w D^-1 (f - A u_in)    (u_in == nullptr: u_in = 0)
+// One damped Jacobi sweep on the fine grid with two nodes per thread (16-byte
+// loads); nx even.
+__global__ void jacobi_fine2_kernel(OpFine5 op, float2* __restrict__ u_out, const float2* __restrict__ u_in,
+                                    const float2* __restrict__ f, float w, int nx, int nz, const int* mask,
+                                    Tally tl) {
+    const int b = blockIdx.z;
+    if (!mask[b]) return;
+    tally_once(tl, blockIdx.x == 0 && blockIdx.y == 0);
+    const int ix = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int iz = blockIdx.y * blockDim.y + threadIdx.y;
+    if (ix >= nx || iz >= nz) return;
+    const size_t N = (size_t)nx * nz;
+    const size_t p = (size_t)iz * nx + ix;
+    const float2* ub = u_in + (size_t)b * N;
+    const float4 fv = *reinterpret_cast<const float4*>(f + (size_t)b * N + p);
+    const float4 uv = *reinterpret_cast<const float4*>(ub + p);
+    float2 y0, y1;
+    op.apply2(ub, b, ix, iz, y0, y1);
+    const float2 q0 = cdiv(make_float2(fv.x - y0.x, fv.y - y0.y), op.diag(b, (int)p));
+    const float2 q1 = cdiv(make_float2(fv.z - y1.x, fv.w - y1.y), op.diag(b, (int)p + 1));
+    *reinterpret_cast<float4*>(u_out + (size_t)b * N + p) =
+        make_float4(uv.x + w * q0.x, uv.y + w * q0.y, uv.z + w * q1.x, uv.w + w * q1.y);
+}
+
 template <class Op>
 __global__ void jacobi_kernel(Op op, float2* __restrict__ u_out, const float2* __restrict__ u_in,
                               const float2* __restrict__ f, float w, int nx, int nz, const int* mask, Tally tl) {
@@ -177,6 +201,15 @@ template <class Op>
 int launch_jacobi(const helm_ctx* c, const Op& op, float2* u_out, const float2* u_in, const float2* f, int nx,
                   int nz, int nb, const int* mask) {
     LaunchScope scope(c, (std::is_same<Op, OpFine5>::value ? K_JACOBI_FINE : K_JACOBI_COARSE));
+    if constexpr (std::is_same<Op, OpFine5>::value) {
+        if (u_in && nx % 2 == 0) {
+            const dim3 g((nx / 2 + 31) / 32, (nz + 7) / 8, nb);
+            jacobi_fine2_kernel<<<g, dim3(32, 8), 0, c->stream>>>(op, u_out, u_in, f, c->opt.jacobi_w, nx, nz, mask,
+                                                                  tally(c, K_JACOBI_FINE, 24ull * nx * nz));
+            HELM_CK(cudaGetLastError());
+            return HELM_OK;
+        }
+    }
     jacobi_kernel<Op><<<grid2(nx, nz, nb), dim3(32, 8), 0, c->stream>>>(
         op, u_out, u_in, f, c->opt.jacobi_w, nx, nz, mask,
         tally(c, std::is_same<Op, OpFine5>::value ? K_JACOBI_FINE : K_JACOBI_COARSE,

@@ -250,10 +250,10 @@ def workload_batched(n_src: int = 64) -> Workload:
 
 
 def workload_cnn(n_src: int = 128) -> Workload:
-    """1024x512 layered medium, h = 12.5 m, f = 8 Hz, 128 sources on row 2."""
+    """1024x512 layered medium, h = 12.5 m, f = 8 Hz, n_src (128) sources on row 2."""
     nx, nz = 1024, 512
     c = layered_velocity(nx, nz, seed=SEED_MODEL)
-    return Workload("helmholtz_1024x512_128rhs", nx, nz, 12.5, [8.0],
+    return Workload(f"helmholtz_1024x512_{n_src}rhs", nx, nz, 12.5, [8.0],
                     kappa_of(c), abl_gamma(nx, nz, 32), top_row_positions(nx, n_src))
 
 
