@@ -179,7 +179,8 @@ def config_of(w, workload):
            "krylov": "FGMRES(10), complex64 vectors, FP64 Hessenberg/Givens/residual, complex128 iterate",
            "tol": TOL, "parallelism": "independent replicas per GPU"}
     if workload == "cnn":
-        cfg["precond"] = "CNN-FGMRES: M_VU(r) = e0 + V(r - H e0), e0 = encoder-solver U-Net (16/32/64/128, BF16)"
+        cfg["precond"] = ("CNN-FGMRES: M_VU(r) = a e0 + V(r - a H e0), a minimising ||r - a H e0||, "
+                          "e0 = encoder-solver U-Net (16/32/64/128, BF16)")
         cfg["l2"] = "inputs larger than L2 (537 MB RHS batch, 6 GB Krylov workspace)"
     else:
         cfg["precond"] = "MG-FGMRES"
@@ -371,7 +372,7 @@ def run_ours(args, rank, world):
     steps_data = sum(128 * 2 ** i // 16 for i in range(3))
     epochs = 3 + max(1, -(-(args.train_steps - steps_data) // 64))
     cfg = RT.RetrainConfig(initial_size=128, data_epochs=3, epochs=epochs, batch=16, lr=1e-3, lr_final=1e-4,
-                           max_steps=args.train_steps, seed=media.SEED_DATAGEN + rank)
+                           max_steps=args.train_steps, seed=media.SEED_DATAGEN + rank, relative_loss=True)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     hist = RT.retrain(native, net, ctx_cnn, w.nx, w.nz, cfg=cfg)
@@ -392,6 +393,7 @@ def run_ours(args, rank, world):
                           "iterations": {"mean": float(mg_its.mean()), "max": int(mg_its.max()),
                                          "min": int(mg_its.min())}, "max_rel_residual": mg_rel},
             "training": {"steps": hist.steps, "seconds": train_s, "batch": 16, "lr": [1e-3, 1e-4],
+                         "loss": "Eq. 4.2 with each pair weighted by 1 / ||e||^2",
                          "loss_first_epoch": hist.epoch_loss[0] if hist.epoch_loss else None,
                          "loss_last_epoch": hist.epoch_loss[-1] if hist.epoch_loss else None},
             "gpu_launches": int(launches), "clocks": clocks}

@@ -9,8 +9,9 @@ TEST INFRASTRUCTURE: see the package header for who may import this.
   after one step; new pair (r - H e~, e - e~) in the residual-correction
   reading, or (H e~, e~) as printed.
 * Eq. 4.2: loss = (1/m) sum_i ||e_net(r_i) - e_i||^2, e_net = h^2 rms(r) out.
-* Eq. 3.14: M_VU(r) = e_0 + V(r - H e_0) (the V-cycle corrects the residual the
-  network leaves), or a V-cycle on P started from u_0 = e_0.
+* Eq. 3.14: M_VU(r) = a e_0 + V(r - a H e_0) (the V-cycle corrects the residual the
+  network leaves; a minimises that residual), without the scaling, or a V-cycle on P
+  started from u_0 = e_0.
 """
 from __future__ import annotations
 
@@ -35,11 +36,18 @@ def make_samples(kappa, gamma, omega, h, x, iters, params=None):
     return np.stack(rs), np.stack(es)
 
 
-def mvu_compose(e0, r, A, pc, composition: str = "residual"):
+def mvu_compose(e0, r, A, pc, composition: str = "scaled"):
     """M_VU of Eq. 3.14 for one residual, given the network's estimate e0.
 
-    ``residual``: e0 + V(r - H e0, 0): exact when e0 = H^-1 r, the plain V-cycle
-    when e0 = 0.  ``initial_guess``: V(r, u_0 = e0) on the shifted operator."""
+    ``scaled``: a e0 + V(r - a H e0, 0) with the complex a = <H e0, r> / <H e0, H e0>
+    that minimises ||r - a H e0|| (a = 0 when H e0 = 0).  ``residual``: e0 + V(r - H e0, 0):
+    exact when e0 = H^-1 r, the plain V-cycle when e0 = 0.  ``initial_guess``: V(r, u_0 = e0)
+    on the shifted operator."""
+    if composition == "scaled":
+        t = A(e0)
+        tt = np.vdot(t, t).real
+        a = np.vdot(t, r) / tt if tt > 0 else 0.0
+        return a * e0 + pc(r - a * t)
     if composition == "residual":
         return e0 + pc(r - A(e0))
     if composition == "initial_guess":
@@ -74,13 +82,16 @@ def refine_samples(P, specs, kappa, gamma, omega, h, r, e, literal=False, params
     return np.stack(r2), np.stack(e2)
 
 
-def loss_and_grad(P, specs, kappa, gamma, omega, h, r, e, quantize=None):
-    """(loss, {name: (dw, db)}) of Eq. 4.2 for one batch of one medium/frequency."""
+def loss_and_grad(P, specs, kappa, gamma, omega, h, r, e, quantize=None, relative=False):
+    """(loss, {name: (dw, db)}) of Eq. 4.2 for one batch of one medium/frequency;
+    relative=True weighs sample i by 1 / ||e_i||^2."""
     e_net, out, tape, rms = network_error(P, specs, kappa, gamma, omega, h, r, quantize)
     m = r.shape[0]
-    d = e_net - np.asarray(e, dtype=np.complex128)
-    loss = float(np.sum(np.abs(d) ** 2) / m)
-    s = (h * h) * rms[:, None, None]
+    e = np.asarray(e, dtype=np.complex128)
+    d = e_net - e
+    wt = 1.0 / np.sum(np.abs(e) ** 2, axis=(1, 2)) if relative else np.ones(m)
+    loss = float(np.sum(wt * np.sum(np.abs(d) ** 2, axis=(1, 2))) / m)
+    s = (h * h) * rms[:, None, None] * wt[:, None, None]
     g_out = np.stack([2.0 * d.real * s / m, 2.0 * d.imag * s / m], axis=-1)
     grads, _ = cnn.backward(P, specs, tape, g_out)
     return loss, grads

@@ -406,7 +406,7 @@ void helm_default_opts(helm_opts* o) {
     o->coarse_iters = 10;
     o->precond = HELM_PC_MG;
     o->max_rhs = 256;
-    o->cnn_vcycle = 0;
+    o->cnn_vcycle = 2;
     o->stream = nullptr;
 }
 
@@ -446,6 +446,7 @@ int helm_setup(helm_ctx** out, const float* kappa, const float* gamma, int nx, i
         return HELM_EINVAL;
     }
     if (o.precond == HELM_PC_CNN && !net) { set_error("HELM_PC_CNN needs a network"); return HELM_EINVAL; }
+    if (o.cnn_vcycle < 0 || o.cnn_vcycle > 2) { set_error("cnn_vcycle must be 0, 1 or 2"); return HELM_EINVAL; }
 
     helm_ctx* c = new helm_ctx();
     c->nx = nx; c->nz = nz; c->nfreq = nfreq; c->hx = hx; c->hz = hz; c->opt = o;

@@ -23,6 +23,7 @@
 
 #include "helm_internal.cuh"
 #include "cnn_internal.cuh"
+#include "conv.cuh"
 #include "reduce.cuh"
 
 namespace helm {
@@ -105,37 +106,40 @@ __global__ void pack_weights_kernel(const float* __restrict__ master, long long 
     }
 }
 
-// FP32 [n][ny][nx][3] -> BF16 [n][ny][nx][16] (channels 3..15 zero)
-__global__ void pack_input3_kernel(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, long long npix) {
+// FP32 [n][ny][nx][3] -> BF16 chunked [n][2][ny][nx][8] (channels 3..15 zero); hw = ny nx
+__global__ void pack_input3_kernel(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, long long npix,
+                                   long long hw) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x) {
-        __nv_bfloat16 v[16];
+        __nv_bfloat16 v[8];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < 3 ? in[p * 3 + c] : 0.0f);
-        uint4* o = reinterpret_cast<uint4*>(out + p * 16);
-        o[0] = *reinterpret_cast<uint4*>(&v[0]);
-        o[1] = *reinterpret_cast<uint4*>(&v[8]);
+        for (int c = 0; c < 8; ++c) v[c] = __float2bfloat16_rn(c < 3 ? in[p * 3 + c] : 0.0f);
+        const long long b = p / hw, pix = p - b * hw;
+        *reinterpret_cast<uint4*>(out + nc8(b, 0, pix, 16, hw)) = *reinterpret_cast<uint4*>(&v[0]);
+        *reinterpret_cast<uint4*>(out + nc8(b, 8, pix, 16, hw)) = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
-// FP32 [n][c] -> BF16 [n][cpad] (channels c..cpad-1 zero)
+// FP32 [n][c] (n pixels, hw per image) -> BF16 chunked [n/hw][cpad/8][hw][8] (channels c..cpad-1 zero)
 __global__ void pack_channels_kernel(const float* __restrict__ in, int c, int cpad, __nv_bfloat16* __restrict__ out,
-                                     long long n) {
+                                     long long n, long long hw) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * cpad;
          i += (long long)gridDim.x * blockDim.x) {
-        long long p = i / cpad;
-        int k = (int)(i - p * cpad);
-        out[i] = __float2bfloat16_rn(k < c ? in[p * c + k] : 0.0f);
+        const long long p = i / cpad;
+        const int k = (int)(i - p * cpad);
+        const long long b = p / hw, pix = p - b * hw;
+        out[nc8(b, k, pix, cpad, hw)] = __float2bfloat16_rn(k < c ? in[p * c + k] : 0.0f);
     }
 }
 
-// BF16 [n][cpad] -> FP32 [n][c]
+// BF16 chunked (cpad channels) -> FP32 [n][c]
 __global__ void unpack_channels_kernel(const __nv_bfloat16* __restrict__ in, int cpad, int c, float* __restrict__ out,
-                                       long long n) {
+                                       long long n, long long hw) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * c;
          i += (long long)gridDim.x * blockDim.x) {
-        long long p = i / c;
-        int k = (int)(i - p * c);
-        out[i] = __bfloat162float(in[p * cpad + k]);
+        const long long p = i / c;
+        const int k = (int)(i - p * c);
+        const long long b = p / hw, pix = p - b * hw;
+        out[i] = __bfloat162float(in[nc8(b, k, pix, cpad, hw)]);
     }
 }
 
@@ -143,7 +147,7 @@ __global__ void unpack_channels_kernel(const __nv_bfloat16* __restrict__ in, int
 
 namespace {
 
-// encoder input of every frequency: BF16 [nfreq][nz][nx][16] = [c_ref kappa, gamma, w h kappa, 0...]
+// encoder input of every frequency: BF16 chunked [nfreq][2][nz][nx][8] = [c_ref kappa, gamma, w h kappa, 0...]
 __global__ void encoder_input_kernel(const float2* __restrict__ mg, const float* __restrict__ omega, float h,
                                      int nfreq, long long n, __nv_bfloat16* __restrict__ out) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nfreq;
@@ -157,9 +161,8 @@ __global__ void encoder_input_kernel(const float2* __restrict__ mg, const float*
         v[0] = __float2bfloat16_rn(1500.0f * kg.x);
         v[1] = __float2bfloat16_rn(kg.y);
         v[2] = __float2bfloat16_rn(omega[f] * h * kg.x);
-        uint4* o = reinterpret_cast<uint4*>(out + i * 16);
-        o[0] = *reinterpret_cast<uint4*>(&v[0]);
-        o[1] = *reinterpret_cast<uint4*>(&v[8]);
+        *reinterpret_cast<uint4*>(out + nc8(f, 0, p, 16, n)) = *reinterpret_cast<uint4*>(&v[0]);
+        *reinterpret_cast<uint4*>(out + nc8(f, 8, p, 16, n)) = *reinterpret_cast<uint4*>(&v[8]);
     }
 }
 
@@ -183,7 +186,7 @@ __global__ void rms_kernel(const float2* __restrict__ r, long long n, float* __r
     }
 }
 
-// solver input BF16 [nb][n][16] = [Re r / rms, Im r / rms, gamma, 0...]
+// solver input BF16 chunked [nb][2][n][8] = [Re r / rms, Im r / rms, gamma, 0...]
 __global__ void solver_input_kernel(const float2* __restrict__ r, const float* __restrict__ rms,
                                     const float2* __restrict__ mg, long long n, int nb,
                                     __nv_bfloat16* __restrict__ out) {
@@ -199,9 +202,8 @@ __global__ void solver_input_kernel(const float2* __restrict__ r, const float* _
         q[0] = __float2bfloat16_rn(v.x * s);
         q[1] = __float2bfloat16_rn(v.y * s);
         q[2] = __float2bfloat16_rn(mg[p].y);
-        uint4* o = reinterpret_cast<uint4*>(out + i * 16);
-        o[0] = *reinterpret_cast<uint4*>(&q[0]);
-        o[1] = *reinterpret_cast<uint4*>(&q[8]);
+        *reinterpret_cast<uint4*>(out + nc8(b, 0, p, 16, n)) = *reinterpret_cast<uint4*>(&q[0]);
+        *reinterpret_cast<uint4*>(out + nc8(b, 8, p, 16, n)) = *reinterpret_cast<uint4*>(&q[8]);
     }
 }
 
@@ -220,6 +222,69 @@ __global__ void net_residual_kernel(OpFine5 op, const float2* __restrict__ r, co
 }
 
 // z += e0
+// Scaled composition: per RHS, t = H e0 and acc[b] = {Re <t, r>, Im <t, r>, <t, t>}
+// (FP64, blocks of a RHS add their partial sums atomically; acc zeroed before).
+__global__ void net_scale_dots_kernel(OpFine5 op, const float2* __restrict__ r, const float2* __restrict__ e0,
+                                      const int* mask, double* __restrict__ acc) {
+    const int b = blockIdx.y;
+    if (mask && !mask[b]) return;
+    const long long n = (long long)op.nx * op.nz;
+    const float2* eb = e0 + (long long)b * n;
+    const float2* rb = r + (long long)b * n;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const int iz = (int)(p / op.nx), ix = (int)(p - (long long)iz * op.nx);
+        const float2 t = op.apply(eb, b, ix, iz);
+        const float2 v = rb[p];
+        a0 += (double)t.x * v.x + (double)t.y * v.y;
+        a1 += (double)t.x * v.y - (double)t.y * v.x;
+        a2 += (double)t.x * t.x + (double)t.y * t.y;
+    }
+    __shared__ double sm[3][32];
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { sm[0][w] = a0; sm[1][w] = a1; sm[2][w] = a2; }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sm[threadIdx.x][k];
+        atomicAdd(acc + 3 * b + threadIdx.x, t);
+    }
+}
+
+__device__ __forceinline__ float2 net_alpha(const double* acc, int b) {
+    const double tt = acc[3 * b + 2];
+    return tt > 0.0 ? make_float2((float)(acc[3 * b] / tt), (float)(acc[3 * b + 1] / tt)) : make_float2(0.f, 0.f);
+}
+
+// out = r - alpha_b H e0, alpha_b = <t, r> / <t, t> minimising ||r - alpha t||
+__global__ void net_scaled_residual_kernel(OpFine5 op, const float2* __restrict__ r, const float2* __restrict__ e0,
+                                           float2* __restrict__ out, int nb, const double* __restrict__ acc) {
+    const long long n = (long long)op.nx * op.nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nb;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(i / n);
+        const int p = (int)(i - (long long)b * n);
+        const int iz = p / op.nx, ix = p - iz * op.nx;
+        const float2 he = op.apply(e0 + (long long)b * n, b, ix, iz);
+        const float2 al = net_alpha(acc, b);
+        out[i] = make_float2(r[i].x - (al.x * he.x - al.y * he.y), r[i].y - (al.x * he.y + al.y * he.x));
+    }
+}
+
+// z += alpha_b e0
+__global__ void add_scaled_kernel(float2* __restrict__ z, const float2* __restrict__ e0, long long n, int nb,
+                                  const double* __restrict__ acc) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nb;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 al = net_alpha(acc, (int)(i / n));
+        const float2 e = e0[i];
+        z[i] = make_float2(z[i].x + al.x * e.x - al.y * e.y, z[i].y + al.x * e.y + al.y * e.x);
+    }
+}
+
 __global__ void add_kernel(float2* __restrict__ z, const float2* __restrict__ e0, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         z[i] = make_float2(z[i].x + e0[i].x, z[i].y + e0[i].y);
@@ -281,6 +346,8 @@ void cnn_ctx_free(helm_ctx* c) {
     cudaFree(c->cnn_e0);
     cudaFree(c->cnn_rres);
     cudaFree(c->cnn_rms);
+    cudaFree(c->cnn_alpha);
+    c->cnn_alpha = nullptr;
     c->cnn_rres = nullptr;
     c->cnn_in = nullptr;
     c->cnn_out = nullptr;
@@ -302,6 +369,7 @@ int cnn_ctx_setup(helm_ctx* c) {
         HELM_CK(cudaMalloc(&c->cnn_e0, (size_t)c->cap * n * sizeof(float2)));
         HELM_CK(cudaMalloc(&c->cnn_rres, (size_t)c->cap * n * sizeof(float2)));
         HELM_CK(cudaMalloc(&c->cnn_rms, (size_t)c->cap * sizeof(float)));
+        HELM_CK(cudaMalloc(&c->cnn_alpha, (size_t)c->cap * 3 * sizeof(double)));
     }
     for (void* p : c->cnn_z) cudaFree(p);
     c->cnn_z.clear();
@@ -352,16 +420,28 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
     if (!with_vcycle) return HELM_OK;
     if (c->opt.cnn_vcycle == 1)
         return vcycle_apply(c, z, c->cnn_e0, v, nb, mask);   // V-cycle on P u = r from u0 = e_0
-    // e_0 + V(r - H e_0): the V-cycle corrects what the network leaves of H e = r
     float2* rr = c->cnn_rres;
-    {
+    if (c->opt.cnn_vcycle == 2) {
+        // alpha e_0 + V(r - alpha H e_0), alpha minimising ||r - alpha H e_0|| per RHS:
+        // the network's step never increases the residual the V-cycle sees
+        double* acc = c->cnn_alpha;
+        LaunchScope scope(c, K_CNN_IO);
+        HELM_CK(cudaMemsetAsync(acc, 0, (size_t)3 * nb * sizeof(double), c->stream));
+        net_scale_dots_kernel<<<dim3(16, nb), 256, 0, c->stream>>>(fine_op(c, 0), v, c->cnn_e0, mask, acc);
+        net_scaled_residual_kernel<<<1184, 256, 0, c->stream>>>(fine_op(c, 0), v, c->cnn_e0, rr, nb, acc);
+        HELM_CK(cudaGetLastError());
+    } else {
+        // e_0 + V(r - H e_0): the V-cycle corrects what the network leaves of H e = r
         LaunchScope scope(c, K_CNN_IO);
         net_residual_kernel<<<1184, 256, 0, c->stream>>>(fine_op(c, 0), v, c->cnn_e0, rr, nb);
         HELM_CK(cudaGetLastError());
     }
     HELM_TRY(vcycle_apply(c, z, nullptr, rr, nb, mask));
     LaunchScope scope(c, K_CNN_IO);
-    add_kernel<<<1184, 256, 0, c->stream>>>(z, c->cnn_e0, n * nb);
+    if (c->opt.cnn_vcycle == 2)
+        add_scaled_kernel<<<1184, 256, 0, c->stream>>>(z, c->cnn_e0, n, nb, c->cnn_alpha);
+    else
+        add_kernel<<<1184, 256, 0, c->stream>>>(z, c->cnn_e0, n * nb);
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -522,8 +602,8 @@ int cnn_forward(cnn_model* m, const float* enc_in, int nenc, const float* sol_in
     if (!s) {
         ck(cudaMemcpy(ein, enc_in, nenc * npix * 3 * sizeof(float), cudaMemcpyDefault));
         ck(cudaMemcpy(sin_, sol_in, nsol * npix * 3 * sizeof(float), cudaMemcpyDefault));
-        pack_input3_kernel<<<256, 256>>>(ein, xe, (long long)nenc * npix);
-        pack_input3_kernel<<<256, 256>>>(sin_, xs, (long long)nsol * npix);
+        pack_input3_kernel<<<256, 256>>>(ein, xe, (long long)nenc * npix, (long long)npix);
+        pack_input3_kernel<<<256, 256>>>(sin_, xs, (long long)nsol * npix, (long long)npix);
         ck(cudaGetLastError());
     }
     if (!s) {
@@ -579,9 +659,10 @@ int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, 
         if (res) ck(cudaMemcpy(fr, res, nout * cout * sizeof(float), cudaMemcpyDefault));
     }
     if (!s) {
-        pack_channels_kernel<<<256, 256>>>(fx0, c0, cp0, bx0, nin);
-        if (c1) pack_channels_kernel<<<256, 256>>>(fx1, c1, cp1, bx1, nin1);
-        if (res) pack_channels_kernel<<<256, 256>>>(fr, cout, npad, br, nout);
+        const long long hwi = (long long)hin * win, hwo = (long long)hout * wout;
+        pack_channels_kernel<<<256, 256>>>(fx0, c0, cp0, bx0, nin, hwi);
+        if (c1) pack_channels_kernel<<<256, 256>>>(fx1, c1, cp1, bx1, nin1, hwi);
+        if (res) pack_channels_kernel<<<256, 256>>>(fr, cout, npad, br, nout, hwo);
         // weights: logical [cout][9][c0 + c1] -> padded [npad][9][cp0 + cp1] (concat parts padded separately)
         std::vector<float> hw((size_t)cout * 9 * cin + cout);
         ck(cudaMemcpy(hw.data(), fw, hw.size() * sizeof(float), cudaMemcpyDeviceToHost));
@@ -611,7 +692,7 @@ int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, 
             s = launch_conv3x3(a, nullptr);
         }
         if (!s) {
-            unpack_channels_kernel<<<256, 256>>>(by, npad, cout, fy, nout);
+            unpack_channels_kernel<<<256, 256>>>(by, npad, cout, fy, nout, (long long)hout * wout);
             ck(cudaGetLastError());
             ck(cudaDeviceSynchronize());
             int herr = 0;

@@ -33,6 +33,7 @@ struct cnn_model {
     float* adam_m = nullptr;
     float* adam_v = nullptr;
     long long adam_t = 0;
+    int loss_kind = 0;            // 0: Eq. 4.2 (mean squared error); 1: each sample's error relative to ||e||^2
     std::vector<int> widths;
     std::vector<helm::Layer> layers;
     long long nparams = 0;

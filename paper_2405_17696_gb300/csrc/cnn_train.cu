@@ -28,22 +28,24 @@
 namespace helm {
 namespace {
 
-// out = bf16(G . [y > 0]) over cg gradient channels into cpad channels; when
+// out = bf16(G . [y > 0]) over cg gradient channels into cpad channels (out and
+// the activation y, cy channels, in the chunked layout; G is FP32 [n][cg]); when
 // res_grad is given, res_grad += the FP32 masked gradient (same layout as G).
 __global__ void mask_to_bf16_kernel(const float* __restrict__ G, int cg, const __nv_bfloat16* __restrict__ y,
-                                    int cy, int cpad, long long n, __nv_bfloat16* __restrict__ out,
+                                    int cy, int cpad, long long n, long long hw, __nv_bfloat16* __restrict__ out,
                                     float* __restrict__ res_grad) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * cpad;
          i += (long long)gridDim.x * blockDim.x) {
         const long long p = i / cpad;
         const int c = (int)(i - p * cpad);
+        const long long b = p / hw, pix = p - b * hw;
         float v = 0.0f;
         if (c < cg) {
             v = G[p * cg + c];
-            if (y && !(__bfloat162float(y[p * cy + c]) > 0.0f)) v = 0.0f;
+            if (y && !(__bfloat162float(y[nc8(b, c, pix, cy, hw)]) > 0.0f)) v = 0.0f;
             if (res_grad) res_grad[p * cg + c] += v;
         }
-        out[i] = __float2bfloat16_rn(v);
+        out[nc8(b, c, pix, cpad, hw)] = __float2bfloat16_rn(v);
     }
 }
 
@@ -95,7 +97,7 @@ struct WgArgs {
     int x1_bcast;
     const int* x1_map;
     int nb, hin, win, hout, wout, mode;
-    const __nv_bfloat16* g;   // [nb][hout][wout][npad]
+    const __nv_bfloat16* g;   // [nb][npad/8][hout][wout][8] (chunked layout)
     int npad, cout, cin;      // cin: logical input channels (weights layout [cout][9][cin])
     float* dW;
     float* db;
@@ -173,7 +175,8 @@ __global__ void __launch_bounds__(256) wgrad_kernel(WgArgs a, Wg2 w) {
             const int oy = oy0 + pp / w.tw, ox = ox0 + pp % w.tw;
             float v = 0.0f;
             if (oy < a.hout && ox < a.wout)
-                v = __bfloat162float(a.g[(((size_t)b * a.hout + oy) * a.wout + ox) * a.npad + nbk + k]);
+                v = __bfloat162float(a.g[nc8(b, nbk + k, (long long)oy * a.wout + ox, a.npad,
+                                             (long long)a.hout * a.wout)]);
             gs[i] = v;
         }
         // input rectangle: 16 channels of x0 or x1
@@ -187,7 +190,8 @@ __global__ void __launch_bounds__(256) wgrad_kernel(WgArgs a, Wg2 w) {
             const int iy = r0 + q / w.sw, ix = s0 + q % w.sw;
             float v = 0.0f;
             if (iy >= 0 && iy < a.hin && ix >= 0 && ix < a.win && cb + k < ctot)
-                v = __bfloat162float(xsrc[(((size_t)bx * a.hin + iy) * a.win + ix) * cstride + coff + k]);
+                v = __bfloat162float(xsrc[nc8(bx, coff + k, (long long)iy * a.win + ix, cstride,
+                                              (long long)a.hin * a.win)]);
             xs[i] = v;
         }
         // pixel x tap -> staged input pixel (nst: outside the input)
@@ -258,19 +262,40 @@ __global__ void __launch_bounds__(256) wgrad_kernel(WgArgs a, Wg2 w) {
     }
 }
 
-// loss = (1/m) sum ||e_net - e_true||^2 with e_net = h^2 rms (o_0 + i o_1); gout = dloss/do
+// wt[b] = 1 / ||e_b||^2 (one block per sample, FP64 sum); 0 for a zero sample
+__global__ void inv_energy_kernel(const float2* __restrict__ e, long long n, float* __restrict__ wt) {
+    const int b = blockIdx.x;
+    double acc = 0.0;
+    for (long long p = threadIdx.x; p < n; p += blockDim.x) {
+        const float2 v = e[(long long)b * n + p];
+        acc += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    __shared__ double sm[32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[w];
+        wt[b] = t > 0.0 ? (float)(1.0 / t) : 0.0f;
+    }
+}
+
+// loss = (1/m) sum_b wt_b ||e_net - e_true||^2 with e_net = h^2 rms (o_0 + i o_1)
+// (wt = 1: Eq. 4.2; wt_b = 1 / ||e_b||^2: relative error); gout = dloss/do
 __global__ void mse_grad_kernel(const float* __restrict__ out, const float2* __restrict__ et,
-                                const float* __restrict__ rms, float h2, long long n, int nb, float inv_m,
-                                float* __restrict__ gout, double* __restrict__ loss) {
+                                const float* __restrict__ rms, const float* __restrict__ wt, float h2, long long n,
+                                int nb, float inv_m, float* __restrict__ gout, double* __restrict__ loss) {
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nb;
          i += (long long)gridDim.x * blockDim.x) {
         const int b = (int)(i / n);
         const float s = h2 * rms[b];
+        const float w = wt ? wt[b] : 1.0f;
         const float dr = s * out[2 * i] - et[i].x, di = s * out[2 * i + 1] - et[i].y;
-        acc += (double)dr * dr + (double)di * di;
-        gout[2 * i] = 2.0f * inv_m * dr * s;
-        gout[2 * i + 1] = 2.0f * inv_m * di * s;
+        acc += w * ((double)dr * dr + (double)di * di);
+        gout[2 * i] = 2.0f * inv_m * w * dr * s;
+        gout[2 * i + 1] = 2.0f * inv_m * w * di * s;
     }
     __shared__ double sm[32];
     acc = warp_sum(acc);
@@ -339,7 +364,7 @@ class Backward {
             {
                 LaunchScope scope(c_, K_CNN_IO);
                 mask_to_bf16_kernel<<<1184, 256, 0, st_>>>(Gy, cg, L.relu ? (const __nv_bfloat16*)op.y : nullptr,
-                                                          L.npad, L.npad, nout, g, rg);
+                                                          L.npad, L.npad, nout, (long long)op.hout * op.wout, g, rg);
             }
             // weight and bias gradient
             {
@@ -483,7 +508,7 @@ int cnn_loss_grad_impl(cnn_model* m, helm_ctx* c, const float2* r, const float2*
     const long long n = (long long)c->nx * c->nz;
     const int nfreq = c->nfreq;
     __nv_bfloat16 *xe = nullptr, *xs = nullptr;
-    float *out = nullptr, *gout = nullptr, *rms = nullptr;
+    float *out = nullptr, *gout = nullptr, *rms = nullptr, *wt = nullptr;
     double* dloss = nullptr;
     int s = HELM_OK;
     auto ck = [&](cudaError_t e2) { if (e2 != cudaSuccess && s == HELM_OK) { set_error(cudaGetErrorString(e2)); s = HELM_ECUDA; } };
@@ -492,6 +517,7 @@ int cnn_loss_grad_impl(cnn_model* m, helm_ctx* c, const float2* r, const float2*
     ck(cudaMalloc(&out, (size_t)nb * n * 2 * sizeof(float)));
     ck(cudaMalloc(&gout, (size_t)nb * n * 2 * sizeof(float)));
     ck(cudaMalloc(&rms, (size_t)nb * sizeof(float)));
+    if (m->loss_kind == 1) ck(cudaMalloc(&wt, (size_t)nb * sizeof(float)));
     ck(cudaMalloc(&dloss, sizeof(double)));
     if (!s) ck(cudaMemsetAsync(dloss, 0, sizeof(double), st));
     if (!s) s = cnn_encoder_input(c, xe);
@@ -506,7 +532,9 @@ int cnn_loss_grad_impl(cnn_model* m, helm_ctx* c, const float2* r, const float2*
         if (!s && !run.solver(xs, nb, c->nz, c->nx, z, 2, out)) s = HELM_ECUDA;
         if (!s) {
             LaunchScope scope(c, K_CNN_IO);
-            mse_grad_kernel<<<1184, 256, 0, st>>>(out, e, rms, c->hx * c->hz, n, nb, 1.0f / (float)nb, gout, dloss);
+            if (wt) inv_energy_kernel<<<nb, 256, 0, st>>>(e, n, wt);
+            mse_grad_kernel<<<1184, 256, 0, st>>>(out, e, rms, wt, c->hx * c->hz, n, nb, 1.0f / (float)nb, gout,
+                                                  dloss);
             ck(cudaGetLastError());
         }
         if (!s) {
@@ -520,7 +548,7 @@ int cnn_loss_grad_impl(cnn_model* m, helm_ctx* c, const float2* r, const float2*
     }
     if (!s) s = check_conv_error(m, st);
     if (!s && loss) ck(cudaMemcpy(loss, dloss, sizeof(double), cudaMemcpyDeviceToHost));
-    cudaFree(xe); cudaFree(xs); cudaFree(out); cudaFree(gout); cudaFree(rms); cudaFree(dloss);
+    cudaFree(xe); cudaFree(xs); cudaFree(out); cudaFree(gout); cudaFree(rms); cudaFree(wt); cudaFree(dloss);
     return s;
 }
 
@@ -609,3 +637,12 @@ int cnn_adam_reset(cnn_model* net) {
 }
 
 }  // extern "C"
+
+extern "C" int cnn_set_loss(cnn_model* net, int kind) {
+    if (!net || (kind != 0 && kind != 1)) {
+        helm::set_error("cnn_set_loss: kind must be 0 (Eq. 4.2) or 1 (relative)");
+        return HELM_EINVAL;
+    }
+    net->loss_kind = kind;
+    return HELM_OK;
+}

@@ -7,8 +7,16 @@
 
 namespace helm {
 
+// Activations of the network are BF16 in the chunked layout [n][C/8][H][W][8]:
+// per image, one plane per 8 channels with 16 bytes per pixel (C a multiple of
+// 8).  A plane row is contiguous, so a TMA box of one plane is long rows, and
+// the plane is exactly the K-major core-matrix layout of the tensor cores.
+__host__ __device__ __forceinline__ size_t nc8(long long b, int c, long long pix, int C, long long hw) {
+    return (((size_t)b * (size_t)(C >> 3) + (size_t)(c >> 3)) * (size_t)hw + (size_t)pix) * 8 + (size_t)(c & 7);
+}
+
 struct ConvArgs {
-    const __nv_bfloat16* x0;   // [nb][hin][win][c0]
+    const __nv_bfloat16* x0;   // [nb][c0/8][hin][win][8] (chunked layout, see nc8)
     int c0;
     const __nv_bfloat16* x1;   // second input concatenated after x0's channels, or nullptr
     int c1;
@@ -21,8 +29,8 @@ struct ConvArgs {
                                //   input node (f - 1 - d) / 2 when that is an integer inside the input
     const __nv_bfloat16* w;    // [npad][9][c0 + c1]
     const float* bias;         // [npad]
-    const __nv_bfloat16* res;  // [nb][hout][wout][npad] added before the activation, or nullptr
-    void* y;                   // bf16 [nb][hout][wout][npad], or fp32 [nb][hout][wout][cstore]
+    const __nv_bfloat16* res;  // [nb][npad/8][hout][wout][8] added before the activation, or nullptr
+    void* y;                   // bf16 [nb][npad/8][hout][wout][8], or fp32 [nb][hout][wout][cstore]
     int npad;                  // N of the MMA: 16, 32, 64 or 128
     int cstore;                // channels stored when out_fp32
     int relu;

@@ -286,6 +286,7 @@ struct helm_ctx {
     float* cnn_out = nullptr;        // solver output, FP32 [cap][nz][nx][2]
     float2* cnn_e0 = nullptr;        // network error estimate, [cap][nz][nx]
     float2* cnn_rres = nullptr;      // residual left by the network, [cap][nz][nx]
+    double* cnn_alpha = nullptr;     // [cap][3] sums of the scaled composition (<t, r>, <t, t>)
     float* cnn_rms = nullptr;        // [cap]
     std::vector<void*> cnn_arena;    // one activation buffer per convolution of the solver pass
     std::vector<size_t> cnn_arena_bytes;

@@ -132,20 +132,23 @@ __global__ void __launch_bounds__(NT) conv3x3_tc_kernel(ConvArgs a) {
             unsigned char* As = smem + s * STAGE_BYTES;
             unsigned char* Bs = As + TILE_BYTES;
             const __nv_bfloat16* src = nullptr;
+            const size_t hw_in = (size_t)a.hin * a.win;
             if (valid) {
                 int iy, ix;
                 if (src_coord(a.mode, oy, tap / 3 - 1, a.hin, &iy) && src_coord(a.mode, ox, tap % 3 - 1, a.win, &ix)) {
+                    const long long pix = (long long)iy * a.win + ix;
                     if (cc < a.c0)
-                        src = a.x0 + (((size_t)b * a.hin + iy) * a.win + ix) * a.c0 + cc;
+                        src = a.x0 + nc8(b, cc, pix, a.c0, (long long)hw_in);
                     else
-                        src = a.x1 + (((size_t)b1 * a.hin + iy) * a.win + ix) * a.c1 + (cc - a.c0);
+                        src = a.x1 + nc8(b1, cc - a.c0, pix, a.c1, (long long)hw_in);
                 }
             }
             unsigned char* arow = As + (tid >> 3) * (KG * 128) + (tid & 7) * 16;
             uint4 va[KG];
 #pragma unroll
-            for (int kg = 0; kg < KG; ++kg)
-                va[kg] = src ? __ldg(reinterpret_cast<const uint4*>(src) + kg) : make_uint4(0u, 0u, 0u, 0u);
+            for (int kg = 0; kg < KG; ++kg)   // consecutive 8-channel chunks are planes hw_in pixels apart
+                va[kg] = src ? __ldg(reinterpret_cast<const uint4*>(src + (size_t)kg * hw_in * 8))
+                             : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
             for (int kg = 0; kg < KG; ++kg) *reinterpret_cast<uint4*>(arow + kg * 128) = va[kg];
             if (tid < a.npad) {
@@ -195,6 +198,8 @@ __global__ void __launch_bounds__(NT) conv3x3_tc_kernel(ConvArgs a) {
     if (warp < 4) {
         const long long p = (long long)blockIdx.x * CT + tid;
         const bool valid = p < mtot;
+        const long long hw_out = (long long)a.hout * a.wout;
+        const long long pb = valid ? p / hw_out : 0, ppix = valid ? p - pb * hw_out : 0;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         for (int col0 = 0; col0 < a.npad; col0 += 16) {
             float v[16];
@@ -205,8 +210,9 @@ __global__ void __launch_bounds__(NT) conv3x3_tc_kernel(ConvArgs a) {
                 for (int i = 0; i < 16; ++i) v[i] += __ldg(a.bias + col0 + i);
             }
             if (a.res) {
-                const uint4* rp = reinterpret_cast<const uint4*>(a.res + (size_t)p * a.npad + col0);
-                uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
+                const __nv_bfloat16* rq = a.res + nc8(pb, col0, ppix, a.npad, hw_out);
+                uint4 r0 = __ldg(reinterpret_cast<const uint4*>(rq));
+                uint4 r1 = __ldg(reinterpret_cast<const uint4*>(rq + (size_t)hw_out * 8));
                 const __nv_bfloat16* rb0 = reinterpret_cast<const __nv_bfloat16*>(&r0);
                 const __nv_bfloat16* rb1 = reinterpret_cast<const __nv_bfloat16*>(&r1);
 #pragma unroll
@@ -237,9 +243,9 @@ __global__ void __launch_bounds__(NT) conv3x3_tc_kernel(ConvArgs a) {
                     ob0[i] = __float2bfloat16_rn(v[i]);
                     ob1[i] = __float2bfloat16_rn(v[8 + i]);
                 }
-                uint4* yp = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) + (size_t)p * a.npad + col0);
-                yp[0] = o0;
-                yp[1] = o1;
+                __nv_bfloat16* yq = reinterpret_cast<__nv_bfloat16*>(a.y) + nc8(pb, col0, ppix, a.npad, hw_out);
+                *reinterpret_cast<uint4*>(yq) = o0;
+                *reinterpret_cast<uint4*>(yq + (size_t)hw_out * 8) = o1;
             }
         }
     }

@@ -22,9 +22,11 @@
 //  3 transpose of mode 1 (the input gradient of a stride-2 layer): fine (2Y+py, 2X+px) takes
 //                                    tap (dy, dx) from coarse (Y + (py-1-dy)/2, X + (px-1-dx)/2)
 //                                    when both are integers; staged as mode 2.
-// When the tile is narrower than 127 pixels, whole rows are packed into an M
-// block and the accumulator rows of the halo columns between rows are
-// discarded (each accumulator row depends only on its own A row).
+// Staged rows (tile + halo) are packed end to end into M blocks of 128 pixels;
+// the accumulator rows of the halo columns between rows are discarded (each
+// accumulator row depends only on its own A row).  Activations are in the
+// chunked layout [n][C/8][H][W][8] (nc8), so every staged row is one
+// contiguous TMA box row.
 //
 // Persistent warp-specialised CTAs (two per SM, or one when a tile needs more
 // than 128 TMEM columns): warp 8 lane 0 streams (tile, channel group) stages
@@ -65,7 +67,6 @@ constexpr size_t RING_BUDGET = 96 * 1024;       // bytes of the stage ring (two 
 struct Geometry {
     int tw, rows, pw;        // tile on the staged grid (output grid in mode 1); staged row pitch
     int mb;                  // 128-pixel M blocks per output parity
-    int rowaligned;          // 1: M block m is tile row m
     int nph;                 // output parities per tile: 1 (modes 0, 1) or 4 (modes 2, 3)
     int tiles_x, tiles_y, tiles;
     int plane;               // bytes of one staged plane (with slack)
@@ -194,10 +195,11 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                         // parity sub-planes: rows 2ys + rp + 2i, columns 2xs + cp + 2j
                         for (int rp = 0; rp < 2; ++rp)
                             for (int cp = 0; cp < 2; ++cp)
-                                tc::tma_load_4d(dst + (rp * 2 + cp) * g.plane, tm, cc, 2 * xs + cp, 2 * ys + rp, bb,
-                                                &full[s]);
+                                tc::tma_load_5d(dst + (rp * 2 + cp) * g.plane, tm, 0, 2 * xs + cp, 2 * ys + rp,
+                                                cc >> 3, bb, &full[s]);
                     } else {
-                        tc::tma_load_4d(dst, tm, cc, xs - 1, ys - 1, bb, &full[s]);
+                        // one plane: 8-byte elements, two per pixel, the row (with halo) contiguous
+                        tc::tma_load_4d(dst, tm, 2 * (xs - 1), ys - 1, cc >> 3, bb, &full[s]);
                     }
                 }
                 unsigned char* ws = st + 2 * chunk_bytes;
@@ -219,6 +221,9 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = tc::idesc_bf16_f32(128, a.npad);
         const uint32_t wplane = (uint32_t)a.npad * 16;
+        // descriptors with a zero start address: the start (bits 0-13, 16-byte units) is added per MMA
+        const uint64_t adesc0 = tc::smem_desc(0u, (uint32_t)chunk_bytes, 128);
+        const uint64_t bdesc0 = tc::smem_desc(0u, wplane, 128);
         long long j = 0;
         bool ok = true;
         for (int k = 0; k < ntiles && ok; ++k) {
@@ -231,21 +236,20 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                 const int s = (int)(j % g.ns);
                 if (!wait_bar(&full[s], (uint32_t)((j / g.ns) & 1), abort_v)) { ok = false; break; }
                 tc::tc_fence_after_sync();
-                const uint32_t a0 = tc::smem_u32(smem + (size_t)s * g.stage);
-                const uint32_t w0 = a0 + 2 * chunk_bytes;
+                const uint32_t a16 = (tc::smem_u32(smem + (size_t)s * g.stage) & 0x3FFFFu) >> 4;
+                const uint32_t w16 = a16 + ((2u * (uint32_t)chunk_bytes) >> 4);
                 for (int ph = 0; ph < g.nph; ++ph) {
-                    const int py = ph >> 1, px = ph & 1;
                     for (int m = 0; m < g.mb; ++m) {
-                        const int q0 = g.rowaligned ? m * g.pw : m * 128;
+                        const uint32_t q16 = a16 + (uint32_t)(m * 128);   // 128 pixels of 16 bytes
                         const uint32_t d = dbase + (uint32_t)((ph * g.mb + m) * a.npad);
                         bool first = gi == 0;
 #pragma unroll
                         for (int tap = 0; tap < 9; ++tap) {
-                            int pl, off;
-                            if (!tap_source<MODE>(tap, py, px, g.pw, &pl, &off)) continue;
-                            const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(pl * g.plane + (q0 + off) * 16),
-                                                              (uint32_t)chunk_bytes, 128);
-                            const uint64_t bd = tc::smem_desc(w0 + (uint32_t)tap * 2u * wplane, wplane, 128);
+                            int pl, off;   // A offset in 16-byte units from the stage
+                            if (!tap_source<MODE>(tap, ph >> 1, ph & 1, g.pw, &pl, &off)) continue;
+                            const int o = pl * (g.plane >> 4) + off;
+                            const uint64_t ad = adesc0 + (uint64_t)(q16 + (uint32_t)o);
+                            const uint64_t bd = bdesc0 + (uint64_t)(w16 + (uint32_t)tap * ((2u * wplane) >> 4));
                             tc::mma_bf16(d, ad, bd, idesc, first ? 0u : 1u);
                             first = false;
                         }
@@ -263,11 +267,13 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
     } else if (warp < EPI_WARPS) {
         // ---------------- epilogue ----------------
         // warp w reads TMEM lanes 32 (w % 4) .. + 31 (accumulator row = M-block row);
-        // warpgroup w / 4 drains every other 32-column chunk of the buffer
+        // warpgroup w / 4 drains every other M block (all npad columns of it)
         const int row = (warp & 3) * 32 + (tid & 31);
         const int wg = warp >> 2;
         const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        const int acols = (int)g.acc_cols;
+        const long long hw_out = (long long)a.hout * a.wout;
+        const size_t plane_out = (size_t)hw_out * 8;   // elements between 8-channel planes
+        const int nblk = g.nph * g.mb;
         for (int k = 0; k < ntiles; ++k) {
             const int acc = k & 1;
             if (!wait_bar(&tfull[acc], (uint32_t)((k >> 1) & 1), abort_v)) { *abort_v = 1; break; }
@@ -275,74 +281,85 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
             int b, xs, ys;
             tile_coords(k, b, xs, ys);
             const uint32_t dbase = lane_base + (uint32_t)acc * g.acc_cols;
-            for (int c0 = wg * 32; c0 < acols; c0 += 64) {
-                float v[32];
-                int nseg;
-                if (c0 + 32 <= acols) {
-                    tc::tmem_ld32(dbase + (uint32_t)c0, v);
-                    nseg = 2;
-                } else {
-                    float h[16];
-                    tc::tmem_ld16(dbase + (uint32_t)c0, h);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = h[i];
-                    nseg = 1;
+            for (int bi = wg; bi < nblk; bi += 2) {
+                const int ph = bi / g.mb, m = bi - ph * g.mb;
+                const int q = m * 128 + row;
+                const int yy = q / g.pw, xx = q - yy * g.pw;
+                int oy = ys + yy, ox = xs + xx;
+                if (MODE >= 2) {
+                    oy = 2 * oy + (ph >> 1);
+                    ox = 2 * ox + (ph & 1);
                 }
-#pragma unroll
-                for (int sgi = 0; sgi < 2; ++sgi) {
-                    if (sgi >= nseg) break;
-                    float* vv = v + 16 * sgi;
-                    const int colg = c0 + 16 * sgi;
-                    const int bm = colg / a.npad, n0 = colg - bm * a.npad;
-                    const int ph = bm / g.mb, m = bm - ph * g.mb;
-                    const int q = (g.rowaligned ? m * g.pw : m * 128) + row;
-                    const int yy = q / g.pw, xx = q - yy * g.pw;
-                    int oy = ys + yy, ox = xs + xx;
-                    if (MODE >= 2) {
-                        oy = 2 * oy + (ph >> 1);
-                        ox = 2 * ox + (ph & 1);
-                    }
-                    if (!(xx < g.tw && yy < g.rows && oy < a.hout && ox < a.wout)) continue;
-                    const long long p = ((long long)b * a.hout + oy) * a.wout + ox;
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) vv[i] += bias_s[n0 + i];
-                    if (a.res) {
-                        const uint4* rp = reinterpret_cast<const uint4*>(a.res + (size_t)p * a.npad + n0);
-                        uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
-                        const __nv_bfloat16* rb0 = reinterpret_cast<const __nv_bfloat16*>(&r0);
-                        const __nv_bfloat16* rb1 = reinterpret_cast<const __nv_bfloat16*>(&r1);
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            vv[i] += __bfloat162float(rb0[i]);
-                            vv[8 + i] += __bfloat162float(rb1[i]);
-                        }
-                    }
-                    if (a.relu) {
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) vv[i] = fmaxf(vv[i], 0.0f);
-                    }
-                    if (a.out_fp32) {
-                        float* yo = reinterpret_cast<float*>(a.y) + (size_t)p * a.cstore;
-                        if (a.accum) {
-                            for (int i = 0; i < 16; ++i)
-                                if (n0 + i < a.cstore) yo[n0 + i] += vv[i];
-                        } else {
-                            for (int i = 0; i < 16; ++i)
-                                if (n0 + i < a.cstore) yo[n0 + i] = vv[i];
-                        }
+                const bool valid = xx < g.tw && yy < g.rows && oy < a.hout && ox < a.wout;
+                const long long pix = (long long)oy * a.wout + ox;
+                const size_t ob = valid ? nc8(b, 0, pix, a.npad, hw_out) : 0;   // channel 0 of this pixel
+                const long long p = (long long)b * hw_out + pix;
+                const uint32_t tcol = dbase + (uint32_t)(bi * a.npad);
+                for (int c0 = 0; c0 < a.npad; c0 += 32) {
+                    float v[32];
+                    int nseg;
+                    if (c0 + 32 <= a.npad) {
+                        tc::tmem_ld32(tcol + (uint32_t)c0, v);
+                        nseg = 2;
                     } else {
-                        uint4 o0, o1;
-                        __nv_bfloat16* ob0 = reinterpret_cast<__nv_bfloat16*>(&o0);
-                        __nv_bfloat16* ob1 = reinterpret_cast<__nv_bfloat16*>(&o1);
+                        float h[16];
+                        tc::tmem_ld16(tcol + (uint32_t)c0, h);
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            ob0[i] = __float2bfloat16_rn(vv[i]);
-                            ob1[i] = __float2bfloat16_rn(vv[8 + i]);
+                        for (int i = 0; i < 16; ++i) v[i] = h[i];
+                        nseg = 1;
+                    }
+                    if (!valid) continue;
+#pragma unroll
+                    for (int sgi = 0; sgi < 2; ++sgi) {
+                        if (sgi >= nseg) break;
+                        float* vv = v + 16 * sgi;
+                        const int n0 = c0 + 16 * sgi;
+#pragma unroll
+                        for (int i = 0; i < 16; i += 4) {
+                            const float4 bb = *reinterpret_cast<const float4*>(bias_s + n0 + i);
+                            vv[i] += bb.x;
+                            vv[i + 1] += bb.y;
+                            vv[i + 2] += bb.z;
+                            vv[i + 3] += bb.w;
                         }
-                        uint4* yp = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.y) +
-                                                             (size_t)p * a.npad + n0);
-                        yp[0] = o0;
-                        yp[1] = o1;
+                        const size_t o0 = ob + (size_t)(n0 >> 3) * plane_out;   // planes n0/8 and n0/8 + 1
+                        if (a.res) {
+                            uint4 r0 = __ldg(reinterpret_cast<const uint4*>(a.res + o0));
+                            uint4 r1 = __ldg(reinterpret_cast<const uint4*>(a.res + o0 + plane_out));
+                            const __nv_bfloat16* rb0 = reinterpret_cast<const __nv_bfloat16*>(&r0);
+                            const __nv_bfloat16* rb1 = reinterpret_cast<const __nv_bfloat16*>(&r1);
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                vv[i] += __bfloat162float(rb0[i]);
+                                vv[8 + i] += __bfloat162float(rb1[i]);
+                            }
+                        }
+                        if (a.relu) {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) vv[i] = fmaxf(vv[i], 0.0f);
+                        }
+                        if (a.out_fp32) {
+                            float* yo = reinterpret_cast<float*>(a.y) + (size_t)p * a.cstore;
+                            if (a.accum) {
+                                for (int i = 0; i < 16; ++i)
+                                    if (n0 + i < a.cstore) yo[n0 + i] += vv[i];
+                            } else {
+                                for (int i = 0; i < 16; ++i)
+                                    if (n0 + i < a.cstore) yo[n0 + i] = vv[i];
+                            }
+                        } else {
+                            uint4 w0, w1;
+                            __nv_bfloat16* ob0 = reinterpret_cast<__nv_bfloat16*>(&w0);
+                            __nv_bfloat16* ob1 = reinterpret_cast<__nv_bfloat16*>(&w1);
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                ob0[i] = __float2bfloat16_rn(vv[i]);
+                                ob1[i] = __float2bfloat16_rn(vv[8 + i]);
+                            }
+                            __nv_bfloat16* yq = reinterpret_cast<__nv_bfloat16*>(a.y) + o0;
+                            *reinterpret_cast<uint4*>(yq) = w0;
+                            *reinterpret_cast<uint4*>(yq + plane_out) = w1;
+                        }
                     }
                 }
             }
@@ -374,15 +391,27 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// NHWC BF16 activation [n][h][w][c] viewed as a 4-D tensor (c, w, h, n); box =
-// 8 channels x box_w x box_h x 1 image, traversed with element stride `es` in
-// w and h (box_w / es x box_h / es pixels land in shared memory).
+// Chunked BF16 activation [n][c/8][h][w][8] (see nc8).  Modes 0, 2, 3: viewed
+// as 8-byte elements, a 4-D tensor (2w, h, c/8, n); box = 2 box_w elements (box_w
+// pixels of one row, contiguous) x box_h rows x one 8-channel plane x one image.
+// Mode 1: a 5-D tensor (2, w, h, c/8, n) traversed with element stride 2 in w and
+// h (box_w / 2 x box_h / 2 pixels land in shared memory).
 bool encode_act(CUtensorMap* m, const void* base, int c, int w, int h, int n, int box_w, int box_h, int es) {
-    const cuuint64_t dims[4] = {(cuuint64_t)c, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
-    const cuuint64_t strides[3] = {(cuuint64_t)c * 2, (cuuint64_t)c * 2 * w, (cuuint64_t)c * 2 * w * h};
-    const cuuint32_t box[4] = {8u, (cuuint32_t)box_w, (cuuint32_t)box_h, 1u};
-    const cuuint32_t estr[4] = {1u, (cuuint32_t)es, (cuuint32_t)es, 1u};
-    return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
+    const cuuint64_t plane = (cuuint64_t)w * h * 16;
+    if (es == 1) {
+        const cuuint64_t dims[4] = {(cuuint64_t)2 * w, (cuuint64_t)h, (cuuint64_t)(c / 8), (cuuint64_t)n};
+        const cuuint64_t strides[3] = {(cuuint64_t)w * 16, plane, plane * (cuuint64_t)(c / 8)};
+        const cuuint32_t box[4] = {(cuuint32_t)(2 * box_w), (cuuint32_t)box_h, 1u, 1u};
+        const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+        return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    const cuuint64_t dims[5] = {2u, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)(c / 8), (cuuint64_t)n};
+    const cuuint64_t strides[4] = {16u, (cuuint64_t)w * 16, plane, plane * (cuuint64_t)(c / 8)};
+    const cuuint32_t box[5] = {2u, (cuuint32_t)box_w, (cuuint32_t)box_h, 1u, 1u};
+    const cuuint32_t estr[5] = {1u, (cuuint32_t)es, (cuuint32_t)es, 1u, 1u};
+    return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<void*>(base), dims, strides, box, estr,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -415,26 +444,28 @@ Geometry plan(const ConvArgs& a) {
     if (mode == 1) {
         g.tw = W >= 127 ? 127 : W;   // 2 (tw + 1) traversed columns fit a 256-element box
         g.pw = g.tw + 1;
-        g.rowaligned = 0;
     } else {
-        g.tw = W >= 128 ? 128 : W;
+        // a staged row (tile + halo) is one TMA box row of at most 256 8-byte
+        // elements: tw <= 126; wide images are cut into equal tiles
+        const int ntx = (W + 125) / 126;
+        g.tw = (W + ntx - 1) / ntx;
         g.pw = g.tw + 2;
-        g.rowaligned = g.tw >= 127;  // a row (plus its halo) no longer fits one M block
     }
     const int halo = mode == 1 ? 1 : 2;        // extra staged rows
     g.wbytes = 9 * 2 * a.npad * 16;
     // TMEM per accumulator buffer: 128 columns (two CTAs per SM), or 256 when one
     // block per parity already needs more (one CTA per SM)
+    // (wide layers: 256, so that packed rows fill the 128-pixel M blocks)
     int acc_max = 128;
-    if (g.nph * a.npad > acc_max) acc_max = 256;
+    if (g.nph * a.npad > acc_max || a.npad >= 64) acc_max = 256;
     const int maxmb = acc_max / (g.nph * a.npad);
     auto fill = [&](int rows) {
         g.rows = rows;
-        g.mb = g.rowaligned ? rows : (rows * g.pw + 127) / 128;
+        g.mb = (rows * g.pw + 127) / 128;
         g.plane = (((rows + halo) * g.pw + SLACK_PX) * 16 + 127) / 128 * 128;
         g.stage = 2 * g.nplanes * g.plane + g.wbytes;
     };
-    int rmax = g.rowaligned ? maxmb : (maxmb * 128) / g.pw;
+    int rmax = (maxmb * 128) / g.pw;
     const int cap = g_rows_cap.load();
     if (cap > 0 && rmax > cap) rmax = cap;
     if (rmax > H) rmax = H;
@@ -547,11 +578,13 @@ int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st) {
     const Geometry g = plan(a);
     if (g.tiles <= 0) return HELM_EINVAL;
     if ((size_t)g.ns * g.stage > 200 * 1024 || g.tmem_cols > 512) return HELM_EINVAL;
-    // box extents: modes 0/2/3 (tw + 2) x (rows + 2); mode 1 traverses 2 (tw + 1) x 2 (rows + 1) with stride 2
+    // box extents: modes 0/2/3 (tw + 2) pixels = 2 (tw + 2) elements x (rows + 2); mode 1
+    // traverses 2 (tw + 1) x 2 (rows + 1) pixels with stride 2
     const int es = a.mode == 1 ? 2 : 1;
     const int bw = a.mode == 1 ? 2 * g.pw : g.pw;
     const int bh = a.mode == 1 ? 2 * (g.rows + 1) : g.rows + 2;
-    if (bw > 256 || bh > 256) return HELM_EINVAL;
+    if ((a.mode == 1 ? bw : 2 * bw) > 256 || bh > 256) return HELM_EINVAL;
+    if (a.c0 % 8 || a.c1 % 8) return HELM_EINVAL;
     alignas(64) CUtensorMap tm0, tm1, tmw;
     if (!encode_act(&tm0, a.x0, a.c0, a.win, a.hin, a.nb, bw, bh, es)) return HELM_EINVAL;
     if (a.c1) {

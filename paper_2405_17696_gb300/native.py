@@ -95,6 +95,8 @@ def _load():
     lib.cnn_precond_apply.restype = ip
     lib.cnn_conv3x3.argtypes = [vp, ip, vp, ip, ip, ip, ip, ip, vp, vp, ip, vp, ip, ip, vp]
     lib.cnn_conv3x3.restype = ip
+    lib.cnn_set_loss.argtypes = [vp, ip]
+    lib.cnn_set_loss.restype = ip
     lib.cnn_init_params.argtypes = [vp, ctypes.c_ulonglong, fp]
     lib.cnn_init_params.restype = ip
     lib.cnn_set_conv_path.argtypes = [ip]
@@ -331,6 +333,11 @@ def cnn_conv3x3(x0, c0: int, x1, c1: int, x1_bcast: int, nb: int, hin: int, win:
 def cnn_init_params(net, seed: int, gain: float = 1.0):
     """Seeded He-normal weights (scaled by gain), zero biases."""
     _check(lib.cnn_init_params(net, int(seed), float(gain)), "cnn_init_params")
+
+
+def cnn_set_loss(net, kind: int):
+    """0: Eq. 4.2 mean squared error (default); 1: per-sample error relative to ||e||^2."""
+    _check(lib.cnn_set_loss(net, int(kind)), "cnn_set_loss")
 
 
 def cnn_set_conv_path(path: int):

@@ -35,6 +35,7 @@ class RetrainConfig:
     literal: bool = False          # Alg. 2 as printed instead of the residual-correction pair
     seed: int = media.SEED_DATAGEN
     max_steps: int | None = None   # optional cap on the number of Adam steps (short sessions)
+    relative_loss: bool = False    # weigh each pair by 1 / ||e||^2 instead of Eq. 4.2's plain sum
 
 
 @dataclass
@@ -64,6 +65,7 @@ def retrain(native, net, ctx, nx: int, nz: int, freq_of_sample=None, cfg: Retrai
     import torch
 
     cfg = cfg or RetrainConfig()
+    native.cnn_set_loss(net, 1 if cfg.relative_loss else 0)
     g = media.rng(cfg.seed)
     fsel = freq_of_sample or (lambda i: 0)
     cap = cfg.initial_size * 2 ** cfg.data_epochs

@@ -131,11 +131,12 @@ def _net_ctx(native, w, widths=(16, 32, 64), seed=4, **opts):
     return net, ctx, specs, theta
 
 
-def test_network_preconditioner_parity(native):
+@pytest.mark.parametrize("comp", [2, 0])
+def test_network_preconditioner_parity(native, comp):
     from paper_2405_17696_gb300 import media
     from oracle import helmholtz as H, multigrid as MG, training as T
     w = media.crop_workload(64, 32, freqs=(4.0, 7.0), width=8)
-    net, ctx, specs, theta = _net_ctx(native, w, mg_levels=3)
+    net, ctx, specs, theta = _net_ctx(native, w, mg_levels=3, cnn_vcycle=comp)
     try:
         nb = 3
         fi = np.array([1, 0, 1], np.int32)
@@ -156,10 +157,11 @@ def test_network_preconditioner_parity(native):
         out, _ = cnn.network_forward(P, specs, enc, cnn.bf16_round(x), quantize=cnn.bf16_round)
         ref0 = cnn.solver_output_to_error(out, rms, w.h)[0]
         assert np.linalg.norm(e0[b] - ref0) <= 2e-2 * np.linalg.norm(ref0)
-        # the multigrid part, from the GPU's own e_0: e_0 + V(r - H e_0)
+        # the multigrid part, from the GPU's own e_0: (a) e_0 + V(r - (a) H e_0)
         pc = MG.VCyclePreconditioner(kap, gam, om, w.h, w.h, MG.VCycleParams(levels=3))
         A = lambda u: H.helmholtz_apply(u, kap, gam, om, w.h, w.h)
-        ref = T.mvu_compose(e0[b].astype(np.complex128), r[b].astype(np.complex128), A, pc)
+        ref = T.mvu_compose(e0[b].astype(np.complex128), r[b].astype(np.complex128), A, pc,
+                            "scaled" if comp == 2 else "residual")
         assert np.linalg.norm(e[b] - ref) <= 2e-4 * np.linalg.norm(ref)
 
 

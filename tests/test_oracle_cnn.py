@@ -160,16 +160,58 @@ def test_mvu_composition_special_cases():
     pc = MG.VCyclePreconditioner(kap, gam, om, w.h, w.h, MG.VCycleParams(levels=2))
     r = media.complex_normal((w.nz, w.nx), seed=11).astype(np.complex128)
     exact = H.DirectSolver(kap, gam, om, w.h, w.h).solve(r)
-    out = T.mvu_compose(exact, r, A, pc)
-    assert np.linalg.norm(out - exact) <= 1e-10 * np.linalg.norm(exact)
+    for comp in ("residual", "scaled"):
+        out = T.mvu_compose(exact, r, A, pc, comp)
+        assert np.linalg.norm(out - exact) <= 1e-10 * np.linalg.norm(exact), comp
     zero = np.zeros_like(r)
-    assert np.allclose(T.mvu_compose(zero, r, A, pc), pc(r), rtol=0, atol=1e-14)
+    assert np.allclose(T.mvu_compose(zero, r, A, pc, "residual"), pc(r), rtol=0, atol=1e-14)
+    assert np.allclose(T.mvu_compose(zero, r, A, pc, "scaled"), pc(r), rtol=0, atol=1e-14)
+    # the scaled composition does not depend on the estimate's complex scale, and
+    # the residual it hands the V-cycle is never larger than r
+    e_any = media.complex_normal((w.nz, w.nx), seed=13).astype(np.complex128)
+    m1 = T.mvu_compose(e_any, r, A, pc, "scaled")
+    m2 = T.mvu_compose((2.5 - 1.5j) * e_any, r, A, pc, "scaled")
+    assert np.linalg.norm(m1 - m2) <= 1e-10 * np.linalg.norm(m1)
+    t = A(e_any)
+    a = np.vdot(t, r) / np.vdot(t, t)
+    assert np.linalg.norm(r - a * t) <= np.linalg.norm(r)
+    assert np.linalg.norm(r - a * t) <= np.linalg.norm(r - 1.01 * a * t)
     # with a linear V-cycle (Jacobi coarsest solve) the correction is affine in
     # e0: M(e0) - M(0) = e0 - V(H e0); a sign slip in r - H e0 breaks it
     lin = MG.VCyclePreconditioner(kap, gam, om, w.h, w.h, MG.VCycleParams(levels=2, coarse_kind="jacobi"))
     e0 = media.complex_normal((w.nz, w.nx), seed=12).astype(np.complex128) * 1e-3
-    m0 = T.mvu_compose(zero, r, A, lin)
-    d = T.mvu_compose(e0, r, A, lin) - m0
+    m0 = T.mvu_compose(zero, r, A, lin, "residual")
+    d = T.mvu_compose(e0, r, A, lin, "residual") - m0
     assert np.linalg.norm(d - (e0 - lin(A(e0)))) <= 1e-12 * np.linalg.norm(m0)
     assert np.linalg.norm(d) > 1e-3 * np.linalg.norm(e0)
     assert np.allclose(T.mvu_compose(e0, r, A, pc, "initial_guess"), pc(r, e0), rtol=0, atol=1e-14)
+
+
+def test_relative_loss_gradient_matches_finite_differences():
+    """The relative-error weighting of the training loss (each pair divided by
+    ||e_i||^2): the oracle's gradient against central differences."""
+    from oracle import training as T
+    from paper_2405_17696_gb300 import media
+    w = media.crop_workload(16, 16, freqs=(5.0,), width=4)
+    specs = cnn.layer_specs(widths=(16,))
+    theta = 0.5 * cnn.he_init(specs, seed=3)
+    r = media.complex_normal((2, 16, 16), seed=4)
+    e = media.complex_normal((2, 16, 16), seed=5) * np.array([1.0, 10.0])[:, None, None]
+    kap, gam = np.float64(w.kappa), np.float64(w.gamma)
+    om = float(w.omegas[0])
+    loss, grads = T.loss_and_grad(cnn.unflatten(theta, specs), specs, kap, gam, om, w.h, r, e, relative=True)
+    g = cnn.flatten_grads(grads, specs)
+    k = np.argsort(-np.abs(g))[:6]
+    for i in k:
+        t1, t2 = theta.copy(), theta.copy()
+        t1[i] += 1e-6
+        t2[i] -= 1e-6
+        l1, _ = T.loss_and_grad(cnn.unflatten(t1, specs), specs, kap, gam, om, w.h, r, e, relative=True)
+        l2, _ = T.loss_and_grad(cnn.unflatten(t2, specs), specs, kap, gam, om, w.h, r, e, relative=True)
+        fd = (l1 - l2) / 2e-6
+        assert abs(fd - g[i]) <= 1e-4 * abs(g[i]) + 1e-9, (i, fd, g[i])
+    # equal weights reduce to Eq. 4.2 scaled by 1 / ||e||^2
+    e1 = e[:1]
+    l_rel, _ = T.loss_and_grad(cnn.unflatten(theta, specs), specs, kap, gam, om, w.h, r[:1], e1, relative=True)
+    l_mse, _ = T.loss_and_grad(cnn.unflatten(theta, specs), specs, kap, gam, om, w.h, r[:1], e1)
+    assert abs(l_rel - l_mse / np.sum(np.abs(e1) ** 2)) <= 1e-12 * l_rel

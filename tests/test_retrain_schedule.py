@@ -27,6 +27,9 @@ class FakeNative:
         e2.copy_(e)
         self.refined += nb
 
+    def cnn_set_loss(self, net, kind):
+        self.loss_kind = kind
+
     def cnn_train_step(self, net, ctx, r, e, nb, lr, fidx):
         assert torch.all(r == 1.0) and torch.all(e == 2.0)
         self.steps.append(nb)
