@@ -10,8 +10,8 @@ TEST INFRASTRUCTURE: see the package header for who may import this.
   reading, or (H e~, e~) as printed.
 * Eq. 4.2: loss = (1/m) sum_i ||e_net(r_i) - e_i||^2, e_net = h^2 rms(r) out.
 * Eq. 3.14: M_VU(r) = a e_0 + V(r - a H e_0) (the V-cycle corrects the residual the
-  network leaves; a minimises that residual), without the scaling, or a V-cycle on P
-  started from u_0 = e_0.
+  network leaves; a = 1 unless the network's step raises it, then a minimises it),
+  without a, or a V-cycle on P started from u_0 = e_0.
 """
 from __future__ import annotations
 
@@ -39,14 +39,18 @@ def make_samples(kappa, gamma, omega, h, x, iters, params=None):
 def mvu_compose(e0, r, A, pc, composition: str = "scaled"):
     """M_VU of Eq. 3.14 for one residual, given the network's estimate e0.
 
-    ``scaled``: a e0 + V(r - a H e0, 0) with the complex a = <H e0, r> / <H e0, H e0>
-    that minimises ||r - a H e0|| (a = 0 when H e0 = 0).  ``residual``: e0 + V(r - H e0, 0):
+    ``scaled``: a e0 + V(r - a H e0, 0) with a = 1 while ||r - H e0|| <= ||r||, else
+    the complex a = <H e0, r> / <H e0, H e0> that minimises ||r - a H e0||.  ``residual``: e0 + V(r - H e0, 0):
     exact when e0 = H^-1 r, the plain V-cycle when e0 = 0.  ``initial_guess``: V(r, u_0 = e0)
     on the shifted operator."""
     if composition == "scaled":
         t = A(e0)
         tt = np.vdot(t, t).real
-        a = np.vdot(t, r) / tt if tt > 0 else 0.0
+        tr = np.vdot(t, r)
+        if tt <= 2.0 * tr.real:          # the network's step does not raise the residual
+            a = 1.0
+        else:
+            a = tr / tt
         return a * e0 + pc(r - a * t)
     if composition == "residual":
         return e0 + pc(r - A(e0))

@@ -166,6 +166,33 @@ __global__ void encoder_input_kernel(const float2* __restrict__ mg, const float*
     }
 }
 
+// acc[b] += sum over a slice of RHS b of |r|^2 (grid (slices, nb); FP64; acc zeroed before)
+__global__ void sumsq_kernel(const float2* __restrict__ r, long long n, const int* mask, double* __restrict__ acc) {
+    const int b = blockIdx.y;
+    if (mask && !mask[b]) return;
+    const float4* rb = reinterpret_cast<const float4*>(r + (long long)b * n);   // n even: two nodes per load
+    double a = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n / 2; q += (long long)gridDim.x * blockDim.x) {
+        const float4 v = rb[q];
+        a += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+    }
+    __shared__ double sm[32];
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[w];
+        atomicAdd(acc + b, t);
+    }
+}
+
+__global__ void rms_finalize_kernel(const double* __restrict__ acc, long long n, int nb, const int* mask,
+                                    float* __restrict__ rms) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) rms[b] = (mask && !mask[b]) ? 0.0f : (float)sqrt(acc[b] / (double)n);
+}
+
 // rms(r) per RHS (one block per RHS, FP64 sum)
 __global__ void rms_kernel(const float2* __restrict__ r, long long n, float* __restrict__ rms, const int* mask) {
     const int b = blockIdx.x;
@@ -186,24 +213,25 @@ __global__ void rms_kernel(const float2* __restrict__ r, long long n, float* __r
     }
 }
 
-// solver input BF16 chunked [nb][2][n][8] = [Re r / rms, Im r / rms, gamma, 0...]
+// solver input BF16 chunked [nb][2][n][8] = [Re r / rms, Im r / rms, gamma, 0...]; grid
+// (slices, nb).  The second plane (channels 8-15) is zero and written only when
+// zero_plane1 is set (a buffer that already holds zeros there keeps them).
 __global__ void solver_input_kernel(const float2* __restrict__ r, const float* __restrict__ rms,
-                                    const float2* __restrict__ mg, long long n, int nb,
+                                    const float2* __restrict__ mg, long long n, int zero_plane1,
                                     __nv_bfloat16* __restrict__ out) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nb;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(i / n);
-        const long long p = i - (long long)b * n;
-        const float s = rms[b] > 0.0f ? 1.0f / rms[b] : 0.0f;
-        const float2 v = r[i];
-        __nv_bfloat16 q[16];
+    const int b = blockIdx.y;
+    const float s = rms[b] > 0.0f ? 1.0f / rms[b] : 0.0f;
+    const float2* rb = r + (long long)b * n;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const float2 v = rb[p];
+        __nv_bfloat16 q[8];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) q[c] = __float2bfloat16_rn(0.0f);
+        for (int c = 0; c < 8; ++c) q[c] = __float2bfloat16_rn(0.0f);
         q[0] = __float2bfloat16_rn(v.x * s);
         q[1] = __float2bfloat16_rn(v.y * s);
         q[2] = __float2bfloat16_rn(mg[p].y);
         *reinterpret_cast<uint4*>(out + nc8(b, 0, p, 16, n)) = *reinterpret_cast<uint4*>(&q[0]);
-        *reinterpret_cast<uint4*>(out + nc8(b, 8, p, 16, n)) = *reinterpret_cast<uint4*>(&q[8]);
+        if (zero_plane1) *reinterpret_cast<uint4*>(out + nc8(b, 8, p, 16, n)) = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -222,7 +250,7 @@ __global__ void net_residual_kernel(OpFine5 op, const float2* __restrict__ r, co
 }
 
 // z += e0
-// Scaled composition: per RHS, t = H e0 and acc[b] = {Re <t, r>, Im <t, r>, <t, t>}
+// Guarded composition: per RHS, t = H e0 and acc[b] = {Re <t, r>, Im <t, r>, <t, t>}
 // (FP64, blocks of a RHS add their partial sums atomically; acc zeroed before).
 __global__ void net_scale_dots_kernel(OpFine5 op, const float2* __restrict__ r, const float2* __restrict__ e0,
                                       const int* mask, double* __restrict__ acc) {
@@ -254,34 +282,39 @@ __global__ void net_scale_dots_kernel(OpFine5 op, const float2* __restrict__ r, 
     }
 }
 
+// a = 1 when the network's step does not raise the residual (||r - t|| <= ||r||, i.e.
+// <t, t> <= 2 Re <t, r>), else the a = <t, r> / <t, t> that minimises ||r - a t||
 __device__ __forceinline__ float2 net_alpha(const double* acc, int b) {
-    const double tt = acc[3 * b + 2];
-    return tt > 0.0 ? make_float2((float)(acc[3 * b] / tt), (float)(acc[3 * b + 1] / tt)) : make_float2(0.f, 0.f);
+    const double tr = acc[3 * b], tt = acc[3 * b + 2];
+    if (tt <= 2.0 * tr) return make_float2(1.f, 0.f);
+    return tt > 0.0 ? make_float2((float)(tr / tt), (float)(acc[3 * b + 1] / tt)) : make_float2(0.f, 0.f);
 }
 
-// out = r - alpha_b H e0, alpha_b = <t, r> / <t, t> minimising ||r - alpha t||
+// out = r - a_b H e0
+// grid (x tiles of 32, z rows / 8, nb), block (32, 8)
 __global__ void net_scaled_residual_kernel(OpFine5 op, const float2* __restrict__ r, const float2* __restrict__ e0,
-                                           float2* __restrict__ out, int nb, const double* __restrict__ acc) {
+                                           float2* __restrict__ out, const double* __restrict__ acc) {
+    const int b = blockIdx.z;
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x, iz = blockIdx.y * blockDim.y + threadIdx.y;
+    if (ix >= op.nx || iz >= op.nz) return;
     const long long n = (long long)op.nx * op.nz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nb;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(i / n);
-        const int p = (int)(i - (long long)b * n);
-        const int iz = p / op.nx, ix = p - iz * op.nx;
-        const float2 he = op.apply(e0 + (long long)b * n, b, ix, iz);
-        const float2 al = net_alpha(acc, b);
-        out[i] = make_float2(r[i].x - (al.x * he.x - al.y * he.y), r[i].y - (al.x * he.y + al.y * he.x));
-    }
+    const long long i = (long long)b * n + (long long)iz * op.nx + ix;
+    const float2 he = op.apply(e0 + (long long)b * n, b, ix, iz);
+    const float2 al = net_alpha(acc, b);
+    out[i] = make_float2(r[i].x - (al.x * he.x - al.y * he.y), r[i].y - (al.x * he.y + al.y * he.x));
 }
 
-// z += alpha_b e0
-__global__ void add_scaled_kernel(float2* __restrict__ z, const float2* __restrict__ e0, long long n, int nb,
+// z += a_b e0; grid (slices, nb)
+__global__ void add_scaled_kernel(float2* __restrict__ z, const float2* __restrict__ e0, long long n,
                                   const double* __restrict__ acc) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nb;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float2 al = net_alpha(acc, (int)(i / n));
-        const float2 e = e0[i];
-        z[i] = make_float2(z[i].x + al.x * e.x - al.y * e.y, z[i].y + al.x * e.y + al.y * e.x);
+    const int b = blockIdx.y;
+    const float2 al = net_alpha(acc, b);
+    float2* zb = z + (long long)b * n;
+    const float2* eb = e0 + (long long)b * n;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const float2 e = eb[p];
+        const float2 v = zb[p];
+        zb[p] = make_float2(v.x + al.x * e.x - al.y * e.y, v.y + al.x * e.y + al.y * e.x);
     }
 }
 
@@ -291,13 +324,16 @@ __global__ void add_kernel(float2* __restrict__ z, const float2* __restrict__ e0
 }
 
 // e0 = h^2 rms (out_0 + i out_1)
+// e0 = h^2 rms (o_0 + i o_1); grid (slices, nb)
 __global__ void solver_output_kernel(const float* __restrict__ out, const float* __restrict__ rms, float h2,
-                                     long long n, int nb, float2* __restrict__ e0) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nb;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(i / n);
-        const float s = h2 * rms[b];
-        e0[i] = make_float2(s * out[2 * i], s * out[2 * i + 1]);
+                                     long long n, float2* __restrict__ e0) {
+    const int b = blockIdx.y;
+    const float s = h2 * rms[b];
+    const float2* ob = reinterpret_cast<const float2*>(out) + (long long)b * n;
+    float2* eb = e0 + (long long)b * n;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const float2 o = ob[p];
+        eb[p] = make_float2(s * o.x, s * o.y);
     }
 }
 
@@ -330,7 +366,8 @@ int cnn_solver_input(const helm_ctx* c, const float2* r, int nb, void* out, floa
         HELM_CK(cudaGetLastError());
     }
     LaunchScope scope(c, K_CNN_IO);
-    solver_input_kernel<<<1184, 256, 0, c->stream>>>(r, rms, c->mg, n, nb, (__nv_bfloat16*)out);
+    solver_input_kernel<<<dim3((unsigned)std::min<long long>((n + 255) / 256, 512), nb), 256, 0, c->stream>>>(
+        r, rms, c->mg, n, 1, (__nv_bfloat16*)out);
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -365,6 +402,8 @@ int cnn_ctx_setup(helm_ctx* c) {
     const long long n = (long long)c->nx * c->nz;
     if (!c->cnn_in) {
         HELM_CK(cudaMalloc(&c->cnn_in, (size_t)std::max<long long>(c->cap, c->nfreq) * n * 16 * sizeof(__nv_bfloat16)));
+        // the solver input writes only its first 8-channel plane; the second stays zero
+        HELM_CK(cudaMemset(c->cnn_in, 0, (size_t)std::max<long long>(c->cap, c->nfreq) * n * 16 * sizeof(__nv_bfloat16)));
         HELM_CK(cudaMalloc(&c->cnn_out, (size_t)c->cap * n * 2 * sizeof(float)));
         HELM_CK(cudaMalloc(&c->cnn_e0, (size_t)c->cap * n * sizeof(float2)));
         HELM_CK(cudaMalloc(&c->cnn_rres, (size_t)c->cap * n * sizeof(float2)));
@@ -395,12 +434,16 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
     const long long n = (long long)c->nx * c->nz;
     {
         LaunchScope scope(c, K_CNN_IO);
-        rms_kernel<<<nb, 1024, 0, c->stream>>>(v, n, c->cnn_rms, mask);
+        // sum of |r|^2 per RHS into the scaled composition's sums (reset before they are used)
+        HELM_CK(cudaMemsetAsync(c->cnn_alpha, 0, (size_t)nb * sizeof(double), c->stream));
+        sumsq_kernel<<<dim3(32, nb), 256, 0, c->stream>>>(v, n, mask, c->cnn_alpha);
+        rms_finalize_kernel<<<(nb + 127) / 128, 128, 0, c->stream>>>(c->cnn_alpha, n, nb, mask, c->cnn_rms);
         HELM_CK(cudaGetLastError());
     }
+    const dim3 g2((unsigned)std::min<long long>((n + 255) / 256, 512), nb);
     {
         LaunchScope scope(c, K_CNN_IO);
-        solver_input_kernel<<<1184, 256, 0, c->stream>>>(v, c->cnn_rms, c->mg, n, nb, (__nv_bfloat16*)c->cnn_in);
+        solver_input_kernel<<<g2, 256, 0, c->stream>>>(v, c->cnn_rms, c->mg, n, 0, (__nv_bfloat16*)c->cnn_in);
         HELM_CK(cudaGetLastError());
     }
     Runner r(m, c, c->stream, &c->cnn_arena, &c->cnn_arena_bytes);
@@ -414,7 +457,7 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
     {
         LaunchScope scope(c, K_CNN_IO);
         float2* e0 = with_vcycle ? c->cnn_e0 : z;
-        solver_output_kernel<<<1184, 256, 0, c->stream>>>(c->cnn_out, c->cnn_rms, c->hx * c->hz, n, nb, e0);
+        solver_output_kernel<<<g2, 256, 0, c->stream>>>(c->cnn_out, c->cnn_rms, c->hx * c->hz, n, e0);
         HELM_CK(cudaGetLastError());
     }
     if (!with_vcycle) return HELM_OK;
@@ -422,13 +465,14 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
         return vcycle_apply(c, z, c->cnn_e0, v, nb, mask);   // V-cycle on P u = r from u0 = e_0
     float2* rr = c->cnn_rres;
     if (c->opt.cnn_vcycle == 2) {
-        // alpha e_0 + V(r - alpha H e_0), alpha minimising ||r - alpha H e_0|| per RHS:
-        // the network's step never increases the residual the V-cycle sees
+        // a e_0 + V(r - a H e_0): a = 1 unless the network's step would raise the
+        // residual the V-cycle sees, then the a that minimises it (per RHS)
         double* acc = c->cnn_alpha;
         LaunchScope scope(c, K_CNN_IO);
         HELM_CK(cudaMemsetAsync(acc, 0, (size_t)3 * nb * sizeof(double), c->stream));
         net_scale_dots_kernel<<<dim3(16, nb), 256, 0, c->stream>>>(fine_op(c, 0), v, c->cnn_e0, mask, acc);
-        net_scaled_residual_kernel<<<1184, 256, 0, c->stream>>>(fine_op(c, 0), v, c->cnn_e0, rr, nb, acc);
+        net_scaled_residual_kernel<<<dim3((c->nx + 31) / 32, (c->nz + 7) / 8, nb), dim3(32, 8), 0, c->stream>>>(
+            fine_op(c, 0), v, c->cnn_e0, rr, acc);
         HELM_CK(cudaGetLastError());
     } else {
         // e_0 + V(r - H e_0): the V-cycle corrects what the network leaves of H e = r
@@ -439,7 +483,7 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
     HELM_TRY(vcycle_apply(c, z, nullptr, rr, nb, mask));
     LaunchScope scope(c, K_CNN_IO);
     if (c->opt.cnn_vcycle == 2)
-        add_scaled_kernel<<<1184, 256, 0, c->stream>>>(z, c->cnn_e0, n, nb, c->cnn_alpha);
+        add_scaled_kernel<<<g2, 256, 0, c->stream>>>(z, c->cnn_e0, n, c->cnn_alpha);
     else
         add_kernel<<<1184, 256, 0, c->stream>>>(z, c->cnn_e0, n * nb);
     HELM_CK(cudaGetLastError());

@@ -81,12 +81,17 @@ struct Geometry {
 };
 
 // Bounded wait that also gives up once another role has raised the abort flag.
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_v) {
+// A thread that polls without useful work in between backs off for sleep_ns per
+// failed poll, so that its instructions do not take issue slots from the warps
+// that work (at most WAIT_LIMIT polls: under a second at 128 ns).
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_v,
+                                         unsigned sleep_ns = 0) {
     long long it = 0;
     while (!tc::mbar_try_wait(bar, parity)) {
         ++it;
         if (it > WAIT_LIMIT) return false;
         if ((it & 255) == 0 && *abort_v) return false;
+        if (sleep_ns) __nanosleep(sleep_ns);
     }
     return true;
 }
@@ -181,7 +186,7 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
             for (int gi = 0; gi < G; ++gi, ++j) {
                 const int s = (int)(j % g.ns);
                 const long long use = j / g.ns;
-                if (use > 0 && !wait_bar(&empty[s], (uint32_t)((use - 1) & 1), abort_v)) { ok = false; break; }
+                if (use > 0 && !wait_bar(&empty[s], (uint32_t)((use - 1) & 1), abort_v, 32)) { ok = false; break; }
                 unsigned char* st = smem + (size_t)s * g.stage;
                 tc::mbar_arrive_expect_tx(&full[s], g.tx);
                 for (int h = 0; h < 2; ++h) {
@@ -229,12 +234,12 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
         for (int k = 0; k < ntiles && ok; ++k) {
             const int acc = k & 1;
             const int ause = k >> 1;
-            if (ause > 0 && !wait_bar(&tempty[acc], (uint32_t)((ause - 1) & 1), abort_v)) { ok = false; break; }
+            if (ause > 0 && !wait_bar(&tempty[acc], (uint32_t)((ause - 1) & 1), abort_v, 32)) { ok = false; break; }
             tc::tc_fence_after_sync();
             const uint32_t dbase = tmem + (uint32_t)acc * g.acc_cols;
             for (int gi = 0; gi < G; ++gi, ++j) {
                 const int s = (int)(j % g.ns);
-                if (!wait_bar(&full[s], (uint32_t)((j / g.ns) & 1), abort_v)) { ok = false; break; }
+                if (!wait_bar(&full[s], (uint32_t)((j / g.ns) & 1), abort_v, 32)) { ok = false; break; }
                 tc::tc_fence_after_sync();
                 const uint32_t a16 = (tc::smem_u32(smem + (size_t)s * g.stage) & 0x3FFFFu) >> 4;
                 const uint32_t w16 = a16 + ((2u * (uint32_t)chunk_bytes) >> 4);
@@ -276,7 +281,7 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
         const int nblk = g.nph * g.mb;
         for (int k = 0; k < ntiles; ++k) {
             const int acc = k & 1;
-            if (!wait_bar(&tfull[acc], (uint32_t)((k >> 1) & 1), abort_v)) { *abort_v = 1; break; }
+            if (!wait_bar(&tfull[acc], (uint32_t)((k >> 1) & 1), abort_v, 128)) { *abort_v = 1; break; }
             tc::tc_fence_after_sync();
             int b, xs, ys;
             tile_coords(k, b, xs, ys);

@@ -166,13 +166,21 @@ def test_mvu_composition_special_cases():
     zero = np.zeros_like(r)
     assert np.allclose(T.mvu_compose(zero, r, A, pc, "residual"), pc(r), rtol=0, atol=1e-14)
     assert np.allclose(T.mvu_compose(zero, r, A, pc, "scaled"), pc(r), rtol=0, atol=1e-14)
-    # the scaled composition does not depend on the estimate's complex scale, and
-    # the residual it hands the V-cycle is never larger than r
-    e_any = media.complex_normal((w.nz, w.nx), seed=13).astype(np.complex128)
-    m1 = T.mvu_compose(e_any, r, A, pc, "scaled")
-    m2 = T.mvu_compose((2.5 - 1.5j) * e_any, r, A, pc, "scaled")
+    # a good estimate (its step lowers the residual) is used as it is: the guarded
+    # composition equals the plain one
+    good = exact + 1e-3 * np.linalg.norm(exact) / np.sqrt(exact.size) * media.complex_normal(
+        (w.nz, w.nx), seed=14).astype(np.complex128)
+    assert np.linalg.norm(r - A(good)) < np.linalg.norm(r)
+    assert np.allclose(T.mvu_compose(good, r, A, pc, "scaled"), T.mvu_compose(good, r, A, pc, "residual"),
+                       rtol=0, atol=1e-12 * np.linalg.norm(exact))
+    # a harmful estimate (its step raises the residual) is scaled: the result does not
+    # depend on the estimate's complex scale, and the residual handed on is at most ||r||
+    e_bad = media.complex_normal((w.nz, w.nx), seed=13).astype(np.complex128)
+    assert np.linalg.norm(r - A(e_bad)) > np.linalg.norm(r)
+    m1 = T.mvu_compose(e_bad, r, A, pc, "scaled")
+    m2 = T.mvu_compose((2.5 - 1.5j) * e_bad, r, A, pc, "scaled")
     assert np.linalg.norm(m1 - m2) <= 1e-10 * np.linalg.norm(m1)
-    t = A(e_any)
+    t = A(e_bad)
     a = np.vdot(t, r) / np.vdot(t, t)
     assert np.linalg.norm(r - a * t) <= np.linalg.norm(r)
     assert np.linalg.norm(r - a * t) <= np.linalg.norm(r - 1.01 * a * t)
