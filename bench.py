@@ -139,7 +139,7 @@ def oracle_sample(w, n_rhs):
 
 def oracle_plan(workload):
     """(workload, RHS per sample, description) of the bounded CPU sample."""
-    if workload == "cnn":
+    if workload in ("cnn", "net"):
         w = media.workload_cnn()
         return w, 32, ("direct sparse LU (SuperLU, FP64) of the 8 Hz 1024x512 operator plus 32 back-solves: "
                        "a quarter of the 128-RHS batch")
@@ -178,7 +178,7 @@ def config_of(w, workload):
            "multigrid": "shifted-Laplacian V-cycle (Galerkin, 3 levels, 2+2 damped Jacobi, coarse GMRES(10))",
            "krylov": "FGMRES(10), complex64 vectors, FP64 Hessenberg/Givens/residual, complex128 iterate",
            "tol": TOL, "parallelism": "independent replicas per GPU"}
-    if workload == "cnn":
+    if workload in ("cnn", "net"):
         cfg["precond"] = ("CNN-FGMRES: M_VU(r) = a e0 + V(r - a H e0), a minimising ||r - a H e0||, "
                           "e0 = encoder-solver U-Net (16/32/64/128, BF16)")
         cfg["l2"] = "inputs larger than L2 (537 MB RHS batch, 6 GB Krylov workspace)"
@@ -328,6 +328,48 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     sampler = ClockSampler(local)
 
+    if args.workload == "net":
+        # the encoder-solver network alone: one forward pass (solver U-Net, contexts
+        # cached) of every RHS per step, with He-initialised weights
+        w = media.workload_cnn(args.sources_cnn)
+        prob = Problem(native, w, dev)
+        widths = (16, 32, 64, 128)
+        net = native.cnn_create(len(widths), widths)
+        native.cnn_init_params(net, media.SEED_CNN, 0.5)
+        ctx = native.helm_setup(prob.kappa, prob.gamma, w.nx, w.nz, w.h, w.h, prob.omegas, net=net,
+                                opts=native.helm_default_opts(mg_levels=3, max_rhs=prob.nb,
+                                                              precond=native.HELM_PC_CNN, stream=stream.cuda_stream))
+        r = prob.rhs.to(torch.complex64) if prob.rhs.dtype != torch.complex64 else prob.rhs
+        e = torch.empty_like(r)
+        for _ in range(max(args.warmup, 0)):
+            native.cnn_precond_apply(ctx, r, e, prob.nb, prob.fi, 0)
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            native.cnn_precond_apply(ctx, r, e, prob.nb, prob.fi, 0)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1)
+        line = {"metric": "encoder-solver network forward passes per second (RHS/s)", "value":
+                world * prob.nb * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+                "config": {"workload": f"network_forward_{w.nx}x{w.nz}_{prob.nb}rhs", "widths": list(widths)}}
+        if not args.no_extras:
+            native.helm_profile_enable(ctx, True)
+            native.cnn_precond_apply(ctx, r, e, prob.nb, prob.fi, 0)
+            prof = native.helm_profile_read(ctx)
+            flops = native.helm_profile_flops(ctx)
+            native.helm_profile_enable(ctx, False)
+            line["roofline"] = roofline_of(prof, flops)
+            line["kernels"] = kernel_table(prof, flops)
+        native.helm_destroy(ctx)
+        native.cnn_destroy(net)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+
     if args.workload == "mg":
         w = media.workload_batched(args.sources)
         prob = Problem(native, w, dev)
@@ -436,8 +478,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["cnn", "mg"], default="cnn",
-                    help="cnn: CNN-FGMRES vs MG-FGMRES at 1024x512 (default); mg: MG-FGMRES at 512x256")
+    ap.add_argument("--workload", choices=["cnn", "mg", "net"], default="cnn",
+                    help="cnn: CNN-FGMRES vs MG-FGMRES at 1024x512 (default); mg: MG-FGMRES at 512x256; "
+                         "net: the network's forward pass alone at 1024x512")
     ap.add_argument("--train-steps", type=int, default=400,
                     help="Adam steps of the set-up training (Alg. 2) before the CNN-FGMRES timing")
     ap.add_argument("--sources", type=int, default=64,

@@ -77,9 +77,11 @@ typedef struct {
     int   coarse_iters;     /* steps of the coarsest-level solve            (10)  */
     int   precond;          /* HELM_PC_MG, HELM_PC_CNN or HELM_PC_NONE          */
     int   max_rhs;          /* RHS per device batch; larger calls are chunked (256) */
-    int   cnn_vcycle;       /* M_VU composition (Eq. 3.14): 2 = a e_0 + V(r - a H e_0) with a = 1 unless
-                               ||r - H e_0|| > ||r||, then the complex a minimising ||r - a H e_0|| (per
-                               RHS), 0 = e_0 + V(r - H e_0), 1 = V-cycle on P u = r from u_0 = e_0  (2) */
+    int   cnn_vcycle;       /* M_VU composition (Eq. 3.14): 0 = e_0 + V(r - H e_0); 3 = a e_0 + V(r - a H e_0)
+                               with a = 1 unless ||r - H e_0|| > ||r||, then the complex a minimising
+                               ||r - a H e_0||; 2 = 0 for every RHS until one of its restart cycles
+                               lowers the residual by less than 10 %, then 3 for that RHS; 1 = V-cycle
+                               on P u = r from u_0 = e_0                                      (2) */
     void* stream;           /* cudaStream_t for all work of the context   (NULL) */
 } helm_opts;
 
@@ -197,9 +199,10 @@ void helm_destroy(helm_ctx* ctx);
  * the context z_l concatenated (and reduced by a conv) at every level of the
  * way down, and an output conv to 2 channels.  The preconditioner (Eq. 3.14)
  * is M_VU(r) = V-cycle(e_0, r) with e_0 = h^2 rms(r) (out_0 + i out_1), composed as
- * a e_0 + V(r - a H e_0) by default (opts.cnn_vcycle = 2: a = 1 while the network's step does
- * not raise the residual, else a = <H e_0, r> / <H e_0, H e_0> per RHS; exact when e_0 = H^-1 r),
- * e_0 + V(r - H e_0) (cnn_vcycle = 0) or a V-cycle on P from e_0 (cnn_vcycle = 1).
+ * e_0 + V(r - H e_0) (exact when e_0 = H^-1 r), and for a RHS whose restart cycles stall
+ * a e_0 + V(r - a H e_0) with a = <H e_0, r> / <H e_0, H e_0> when the network's step would
+ * raise the residual (opts.cnn_vcycle = 2, default; 0, 1 and 3 select one composition).
+ * Outside a solve, composition 2 is the plain one.
  * Convolutions are 3x3 implicit GEMMs on the tensor cores (tcgen05, BF16
  * operands, FP32 accumulation in tensor memory).
  * Parameters are one flat FP32 vector: per layer weights [cout][9][cin] then

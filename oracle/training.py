@@ -36,14 +36,14 @@ def make_samples(kappa, gamma, omega, h, x, iters, params=None):
     return np.stack(rs), np.stack(es)
 
 
-def mvu_compose(e0, r, A, pc, composition: str = "scaled"):
+def mvu_compose(e0, r, A, pc, composition: str = "residual"):
     """M_VU of Eq. 3.14 for one residual, given the network's estimate e0.
 
-    ``scaled``: a e0 + V(r - a H e0, 0) with a = 1 while ||r - H e0|| <= ||r||, else
+    ``guarded``: a e0 + V(r - a H e0, 0) with a = 1 while ||r - H e0|| <= ||r||, else
     the complex a = <H e0, r> / <H e0, H e0> that minimises ||r - a H e0||.  ``residual``: e0 + V(r - H e0, 0):
     exact when e0 = H^-1 r, the plain V-cycle when e0 = 0.  ``initial_guess``: V(r, u_0 = e0)
     on the shifted operator."""
-    if composition == "scaled":
+    if composition == "guarded":
         t = A(e0)
         tt = np.vdot(t, t).real
         tr = np.vdot(t, r)

@@ -446,7 +446,7 @@ int helm_setup(helm_ctx** out, const float* kappa, const float* gamma, int nx, i
         return HELM_EINVAL;
     }
     if (o.precond == HELM_PC_CNN && !net) { set_error("HELM_PC_CNN needs a network"); return HELM_EINVAL; }
-    if (o.cnn_vcycle < 0 || o.cnn_vcycle > 2) { set_error("cnn_vcycle must be 0, 1 or 2"); return HELM_EINVAL; }
+    if (o.cnn_vcycle < 0 || o.cnn_vcycle > 3) { set_error("cnn_vcycle must be 0, 1, 2 or 3"); return HELM_EINVAL; }
 
     helm_ctx* c = new helm_ctx();
     c->nx = nx; c->nz = nz; c->nfreq = nfreq; c->hx = hx; c->hz = hz; c->opt = o;
@@ -518,9 +518,12 @@ int helm_setup(helm_ctx** out, const float* kappa, const float* gamma, int nx, i
         if ((st = dalloc(c, &os.bnorm2, cap)) || (st = dalloc(c, &os.rnorm2, cap)) ||
             (st = dalloc(c, &os.iters, cap)) || (st = dalloc(c, &os.status, cap)) ||
             (st = dalloc(c, &os.outer_active, cap)) || (st = dalloc(c, &os.partials, cap * os.max_tiles)) ||
-            (st = dalloc(c, &os.counters, cap)))
+            (st = dalloc(c, &os.counters, cap)) || (st = dalloc(c, &os.rprev, cap)) ||
+            (st = dalloc(c, &os.guard, cap)))
             return fail(st);
-        if (cudaMemsetAsync(os.counters, 0, cap * sizeof(unsigned), c->stream) != cudaSuccess) return fail(HELM_ECUDA);
+        if (cudaMemsetAsync(os.counters, 0, cap * sizeof(unsigned), c->stream) != cudaSuccess ||
+            cudaMemsetAsync(os.guard, 0, cap * sizeof(int), c->stream) != cudaSuccess)
+            return fail(HELM_ECUDA);
     }
     // coarsest GMRES workspace
     {

@@ -282,9 +282,11 @@ __global__ void net_scale_dots_kernel(OpFine5 op, const float2* __restrict__ r, 
     }
 }
 
-// a = 1 when the network's step does not raise the residual (||r - t|| <= ||r||, i.e.
-// <t, t> <= 2 Re <t, r>), else the a = <t, r> / <t, t> that minimises ||r - a t||
-__device__ __forceinline__ float2 net_alpha(const double* acc, int b) {
+// a = 1 unless the RHS is guarded (guard == nullptr: always) and the network's step
+// raises the residual (||r - t|| > ||r||, i.e. <t, t> > 2 Re <t, r>); then the
+// a = <t, r> / <t, t> that minimises ||r - a t||
+__device__ __forceinline__ float2 net_alpha(const double* acc, const int* guard, int b) {
+    if (guard && !guard[b]) return make_float2(1.f, 0.f);
     const double tr = acc[3 * b], tt = acc[3 * b + 2];
     if (tt <= 2.0 * tr) return make_float2(1.f, 0.f);
     return tt > 0.0 ? make_float2((float)(tr / tt), (float)(acc[3 * b + 1] / tt)) : make_float2(0.f, 0.f);
@@ -293,22 +295,23 @@ __device__ __forceinline__ float2 net_alpha(const double* acc, int b) {
 // out = r - a_b H e0
 // grid (x tiles of 32, z rows / 8, nb), block (32, 8)
 __global__ void net_scaled_residual_kernel(OpFine5 op, const float2* __restrict__ r, const float2* __restrict__ e0,
-                                           float2* __restrict__ out, const double* __restrict__ acc) {
+                                           float2* __restrict__ out, const double* __restrict__ acc,
+                                           const int* guard) {
     const int b = blockIdx.z;
     const int ix = blockIdx.x * blockDim.x + threadIdx.x, iz = blockIdx.y * blockDim.y + threadIdx.y;
     if (ix >= op.nx || iz >= op.nz) return;
     const long long n = (long long)op.nx * op.nz;
     const long long i = (long long)b * n + (long long)iz * op.nx + ix;
     const float2 he = op.apply(e0 + (long long)b * n, b, ix, iz);
-    const float2 al = net_alpha(acc, b);
+    const float2 al = net_alpha(acc, guard, b);
     out[i] = make_float2(r[i].x - (al.x * he.x - al.y * he.y), r[i].y - (al.x * he.y + al.y * he.x));
 }
 
 // z += a_b e0; grid (slices, nb)
 __global__ void add_scaled_kernel(float2* __restrict__ z, const float2* __restrict__ e0, long long n,
-                                  const double* __restrict__ acc) {
+                                  const double* __restrict__ acc, const int* guard) {
     const int b = blockIdx.y;
-    const float2 al = net_alpha(acc, b);
+    const float2 al = net_alpha(acc, guard, b);
     float2* zb = z + (long long)b * n;
     const float2* eb = e0 + (long long)b * n;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
@@ -464,7 +467,10 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
     if (c->opt.cnn_vcycle == 1)
         return vcycle_apply(c, z, c->cnn_e0, v, nb, mask);   // V-cycle on P u = r from u0 = e_0
     float2* rr = c->cnn_rres;
-    if (c->opt.cnn_vcycle == 2) {
+    const bool scaled = c->opt.cnn_vcycle >= 2;
+    // composition 2: guarded only for RHS whose restart cycles stall; 3: always guarded
+    const int* guard = c->opt.cnn_vcycle == 2 ? c->outer.guard : nullptr;
+    if (scaled) {
         // a e_0 + V(r - a H e_0): a = 1 unless the network's step would raise the
         // residual the V-cycle sees, then the a that minimises it (per RHS)
         double* acc = c->cnn_alpha;
@@ -472,7 +478,7 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
         HELM_CK(cudaMemsetAsync(acc, 0, (size_t)3 * nb * sizeof(double), c->stream));
         net_scale_dots_kernel<<<dim3(16, nb), 256, 0, c->stream>>>(fine_op(c, 0), v, c->cnn_e0, mask, acc);
         net_scaled_residual_kernel<<<dim3((c->nx + 31) / 32, (c->nz + 7) / 8, nb), dim3(32, 8), 0, c->stream>>>(
-            fine_op(c, 0), v, c->cnn_e0, rr, acc);
+            fine_op(c, 0), v, c->cnn_e0, rr, acc, guard);
         HELM_CK(cudaGetLastError());
     } else {
         // e_0 + V(r - H e_0): the V-cycle corrects what the network leaves of H e = r
@@ -482,8 +488,8 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
     }
     HELM_TRY(vcycle_apply(c, z, nullptr, rr, nb, mask));
     LaunchScope scope(c, K_CNN_IO);
-    if (c->opt.cnn_vcycle == 2)
-        add_scaled_kernel<<<g2, 256, 0, c->stream>>>(z, c->cnn_e0, n, c->cnn_alpha);
+    if (scaled)
+        add_scaled_kernel<<<g2, 256, 0, c->stream>>>(z, c->cnn_e0, n, c->cnn_alpha, guard);
     else
         add_kernel<<<1184, 256, 0, c->stream>>>(z, c->cnn_e0, n * nb);
     HELM_CK(cudaGetLastError());
@@ -516,6 +522,8 @@ int cnn_precond_apply(helm_ctx* c, const helm_c64* r, helm_c64* e, int nrhs, con
         HELM_CK(cudaMalloc(&dr, nb * N * sizeof(float2)));
         HELM_CK(cudaMalloc(&de, nb * N * sizeof(float2)));
         HELM_CK(cudaMemcpyAsync(dr, r + b0 * N, nb * N * sizeof(float2), cudaMemcpyDefault, c->stream));
+        // outside a solve no restart cycle has stalled: composition 2 is the plain one
+        HELM_CK(cudaMemsetAsync(c->outer.guard, 0, nb * sizeof(int), c->stream));
         int s = cnn_ctx_precondition(c, de, dr, nb, c->ones, with_vcycle);
         if (!s) {
             cudaError_t ce = cudaMemcpyAsync(e + b0 * N, de, nb * N * sizeof(float2), cudaMemcpyDefault, c->stream);

@@ -203,6 +203,8 @@ struct OuterState {
     int* iters;            // total FGMRES steps
     int* status;           // HELM_OK / HELM_ENOCONV / HELM_EBREAKDOWN / -1 (running)
     int* outer_active;     // 1 while not finished
+    double* rprev;         // ||b - A x|| at the previous restart (0 before the first)
+    int* guard;            // 1 once a restart cycle barely lowered the residual (network composition guarded)
     double2* partials;     // [cap][max_tiles][2]
     unsigned* counters;
     int max_tiles;

@@ -109,6 +109,10 @@ __global__ void restart_check_kernel(OuterState os, KState st, int nb, double to
             os.status[b] = HELM_ENOCONV;
             act = 0;
         } else {
+            // a restart cycle that lowered the residual by less than 10 % marks the RHS:
+            // its network composition is guarded from now on
+            if (os.rprev[b] > 0.0 && rn > 0.9 * os.rprev[b]) os.guard[b] = 1;
+            os.rprev[b] = rn;
             st.g[(size_t)b * (st.k + 1)] = make_double2(rn, 0.0);
             st.s[(size_t)b * (st.k + 1)] = 1.0 / rn;
             st.inv_est[b] = 1.0 / rn;
@@ -129,6 +133,8 @@ __global__ void outer_init_kernel(OuterState os, KState st, int nb) {
     os.outer_active[b] = 1;
     os.rnorm2[b] = 0.0;
     os.bnorm2[b] = 0.0;
+    os.rprev[b] = 0.0;
+    os.guard[b] = 0;
     st.steps[b] = 0;
     st.active[b] = 0;
 }

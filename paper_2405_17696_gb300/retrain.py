@@ -36,6 +36,7 @@ class RetrainConfig:
     seed: int = media.SEED_DATAGEN
     max_steps: int | None = None   # optional cap on the number of Adam steps (short sessions)
     relative_loss: bool = False    # weigh each pair by 1 / ||e||^2 instead of Eq. 4.2's plain sum
+    warmup_steps: int = 100        # linear learning-rate ramp over the first Adam steps
 
 
 @dataclass
@@ -91,7 +92,8 @@ def retrain(native, net, ctx, nx: int, nz: int, freq_of_sample=None, cfg: Retrai
             ti = torch.from_numpy(idx).to(device)
             r = R.index_select(0, ti).contiguous()
             e = E.index_select(0, ti).contiguous()
-            losses.append(native.cnn_train_step(net, ctx, r, e, len(idx), lr, F[idx]))
+            ramp = min(1.0, (hist.steps + 1) / cfg.warmup_steps) if cfg.warmup_steps > 0 else 1.0
+            losses.append(native.cnn_train_step(net, ctx, r, e, len(idx), lr * ramp, F[idx]))
             hist.steps += 1
             if cfg.max_steps is not None and hist.steps >= cfg.max_steps:
                 break

@@ -131,7 +131,7 @@ def _net_ctx(native, w, widths=(16, 32, 64), seed=4, **opts):
     return net, ctx, specs, theta
 
 
-@pytest.mark.parametrize("comp", [2, 0])
+@pytest.mark.parametrize("comp", [3, 2, 0])
 def test_network_preconditioner_parity(native, comp):
     from paper_2405_17696_gb300 import media
     from oracle import helmholtz as H, multigrid as MG, training as T
@@ -161,7 +161,7 @@ def test_network_preconditioner_parity(native, comp):
         pc = MG.VCyclePreconditioner(kap, gam, om, w.h, w.h, MG.VCycleParams(levels=3))
         A = lambda u: H.helmholtz_apply(u, kap, gam, om, w.h, w.h)
         ref = T.mvu_compose(e0[b].astype(np.complex128), r[b].astype(np.complex128), A, pc,
-                            "scaled" if comp == 2 else "residual")
+                            "guarded" if comp == 3 else "residual")
         assert np.linalg.norm(e[b] - ref) <= 2e-4 * np.linalg.norm(ref)
 
 

@@ -160,25 +160,25 @@ def test_mvu_composition_special_cases():
     pc = MG.VCyclePreconditioner(kap, gam, om, w.h, w.h, MG.VCycleParams(levels=2))
     r = media.complex_normal((w.nz, w.nx), seed=11).astype(np.complex128)
     exact = H.DirectSolver(kap, gam, om, w.h, w.h).solve(r)
-    for comp in ("residual", "scaled"):
+    for comp in ("residual", "guarded"):
         out = T.mvu_compose(exact, r, A, pc, comp)
         assert np.linalg.norm(out - exact) <= 1e-10 * np.linalg.norm(exact), comp
     zero = np.zeros_like(r)
     assert np.allclose(T.mvu_compose(zero, r, A, pc, "residual"), pc(r), rtol=0, atol=1e-14)
-    assert np.allclose(T.mvu_compose(zero, r, A, pc, "scaled"), pc(r), rtol=0, atol=1e-14)
+    assert np.allclose(T.mvu_compose(zero, r, A, pc, "guarded"), pc(r), rtol=0, atol=1e-14)
     # a good estimate (its step lowers the residual) is used as it is: the guarded
     # composition equals the plain one
     good = exact + 1e-3 * np.linalg.norm(exact) / np.sqrt(exact.size) * media.complex_normal(
         (w.nz, w.nx), seed=14).astype(np.complex128)
     assert np.linalg.norm(r - A(good)) < np.linalg.norm(r)
-    assert np.allclose(T.mvu_compose(good, r, A, pc, "scaled"), T.mvu_compose(good, r, A, pc, "residual"),
+    assert np.allclose(T.mvu_compose(good, r, A, pc, "guarded"), T.mvu_compose(good, r, A, pc, "residual"),
                        rtol=0, atol=1e-12 * np.linalg.norm(exact))
     # a harmful estimate (its step raises the residual) is scaled: the result does not
     # depend on the estimate's complex scale, and the residual handed on is at most ||r||
     e_bad = media.complex_normal((w.nz, w.nx), seed=13).astype(np.complex128)
     assert np.linalg.norm(r - A(e_bad)) > np.linalg.norm(r)
-    m1 = T.mvu_compose(e_bad, r, A, pc, "scaled")
-    m2 = T.mvu_compose((2.5 - 1.5j) * e_bad, r, A, pc, "scaled")
+    m1 = T.mvu_compose(e_bad, r, A, pc, "guarded")
+    m2 = T.mvu_compose((2.5 - 1.5j) * e_bad, r, A, pc, "guarded")
     assert np.linalg.norm(m1 - m2) <= 1e-10 * np.linalg.norm(m1)
     t = A(e_bad)
     a = np.vdot(t, r) / np.vdot(t, t)
