@@ -280,6 +280,13 @@ int cnn_set_conv_path(int path);
  * tile (0 = automatic: as many as two 128-column TMEM accumulator buffers and a
  * 47 KB stage allow).  Process-wide; for tuning.  HELM_EINVAL outside [0, 254]. */
 int cnn_set_conv_tiling(int max_rows);
+/* Shared-memory budgets of the TMA halo-tile kernel: at most stage_kb KB per
+ * stage (one tile's 16-channel group plus its weights; taller tiles are cut
+ * until a stage fits) and ring_kb KB for the ring of stages (2 to 6 stages; a
+ * ring above about 110 KB leaves one CTA per SM).  0 keeps the default (47 and
+ * 96 KB; 100 and 200 KB for stride-2 layers).  Process-wide; for tuning.  HELM_EINVAL for stage_kb outside
+ * [0, 128], ring_kb outside [0, 200], or a ring smaller than a stage. */
+int cnn_set_conv_ring(int stage_kb, int ring_kb);
 /* Launch shape of the last TMA convolution, for diagnostics: out6 = {grid,
  * CTAs per SM, CTAs per SM that registers and shared memory allow,
  * dynamic shared memory per CTA in bytes, registers per thread, static shared

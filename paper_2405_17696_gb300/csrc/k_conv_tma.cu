@@ -30,8 +30,9 @@
 //
 // Persistent warp-specialised CTAs (two per SM, or one when a tile needs more
 // than 128 TMEM columns): warp 8 lane 0 streams (tile, channel group) stages
-// through a ring by TMA; warp 9 lane 0 issues tcgen05.mma into one of two TMEM
-// accumulator buffers; warps 0-7 drain the other buffer (bias, residual, ReLU,
+// through a ring by TMA; warp 9 walks the MMA loop together (warp-uniform
+// descriptor arithmetic, a 32-bit add per MMA) and its lane 0 issues
+// tcgen05.mma into one of two TMEM accumulator buffers; warps 0-7 drain the other buffer (bias, residual, ReLU,
 // BF16 or FP32 store, or FP32 accumulation).  Every wait is bounded and gives
 // up when another role aborts; on expiry the kernel raises the error flag,
 // waits (bounded) for its copies and MMAs in flight, frees its TMEM and returns.
@@ -55,23 +56,30 @@ namespace {
 constexpr int EPI_WARPS = 8;                    // two warpgroups drain TMEM (alternate 32-column chunks)
 constexpr int EPI = 32 * EPI_WARPS;             // epilogue threads
 constexpr int NT = EPI + 64;                    // + a TMA-producer warp and an MMA-issuer warp
-constexpr int MAX_NS = 4;                       // stages (one 16-channel group of one tile each)
+constexpr int MAX_NS = 6;                       // stages (one 16-channel group of one tile each)
 constexpr long long WAIT_LIMIT = 1ll << 22;     // polls of try_wait before a wait gives up
 // No padding after a plane: the last M block of a packed tile may read up to
 // 2 pitches + 130 pixels past its plane's staged pixels, which lands in the next
 // plane or in the stage's weights (>= 288 pixels' worth), inside the stage.
 constexpr int SLACK_PX = 0;
-constexpr size_t STAGE_BUDGET = 47 * 1024;      // bytes of one stage at most (fewer rows otherwise)
-constexpr size_t RING_BUDGET = 96 * 1024;       // bytes of the stage ring (two CTAs fit an SM)
+constexpr size_t STAGE_BUDGET = 47 * 1024;      // default bytes of one stage at most (fewer rows otherwise)
+constexpr size_t RING_BUDGET = 96 * 1024;       // default bytes of the stage ring (two CTAs fit an SM)
+// Stride-2 layers stage four parity sub-planes per channel chunk; within 47 KB a
+// tile would hold a single output row (twice the input rows it needs, and the
+// weights once per row), so they take one CTA per SM with larger stages.
+constexpr size_t STAGE_BUDGET_S2 = 100 * 1024;
+constexpr size_t RING_BUDGET_S2 = 200 * 1024;
 
 struct Geometry {
     int tw, rows, pw;        // tile on the staged grid (output grid in mode 1); staged row pitch
     int mb;                  // 128-pixel M blocks per output parity
     int nph;                 // output parities per tile: 1 (modes 0, 1) or 4 (modes 2, 3)
     int tiles_x, tiles_y, tiles;
-    int plane;               // bytes of one staged plane (with slack)
-    int nplanes;             // planes per 8-channel chunk: 1, or 4 parity sub-planes in mode 1
+    int plane;               // bytes of one staged 8-channel plane (its two halves are this far apart)
+    int pstride;             // bytes between parity sub-planes (two planes, rounded up to 128 B)
+    int nplanes;             // parity sub-planes: 1, or 4 in mode 1
     int wbytes;              // bytes of one group's weights (9 taps x 2 chunks x npad rows x 16 B)
+    int w4;                  // weights by one 4-D TMA box (1) or 18 2-D boxes (0)
     int stage;               // bytes of one stage
     int groups, groups0;     // 16-channel groups in total / taken from x0
     int ns;                  // stages in the ring
@@ -162,7 +170,8 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
     const int cin = a.c0 + a.c1;
     const int G = g.groups;
     const int ntiles = g.tiles > (int)blockIdx.x ? (g.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int chunk_bytes = g.nplanes * g.plane;   // K-adjacent core matrices (LBO)
+    const int chunk_bytes = g.plane;                 // K-adjacent core matrices (LBO)
+    const int wofs = g.nplanes * g.pstride;          // the group's weights within a stage
 
     auto tile_coords = [&](int k, int& b, int& xs, int& ys) {
         int t = (int)blockIdx.x + k * (int)gridDim.x;
@@ -189,28 +198,33 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                 if (use > 0 && !wait_bar(&empty[s], (uint32_t)((use - 1) & 1), abort_v, 32)) { ok = false; break; }
                 unsigned char* st = smem + (size_t)s * g.stage;
                 tc::mbar_arrive_expect_tx(&full[s], g.tx);
-                for (int h = 0; h < 2; ++h) {
-                    const int c = gi * 16 + h * 8;
+                {
+                    // both 8-channel halves of the group in one box (a group never straddles x0 and x1)
+                    const int c = gi * 16;
                     const bool second = gi >= g.groups0;
                     const CUtensorMap* tm = second ? &tm_x1 : &tm_x0;
                     const int cc = second ? c - a.c0 : c;
                     const int bb = second ? b1 : b;
-                    unsigned char* dst = st + h * chunk_bytes;
                     if (MODE == 1) {
                         // parity sub-planes: rows 2ys + rp + 2i, columns 2xs + cp + 2j
                         for (int rp = 0; rp < 2; ++rp)
                             for (int cp = 0; cp < 2; ++cp)
-                                tc::tma_load_5d(dst + (rp * 2 + cp) * g.plane, tm, 0, 2 * xs + cp, 2 * ys + rp,
+                                tc::tma_load_5d(st + (rp * 2 + cp) * g.pstride, tm, 0, 2 * xs + cp, 2 * ys + rp,
                                                 cc >> 3, bb, &full[s]);
                     } else {
-                        // one plane: 8-byte elements, two per pixel, the row (with halo) contiguous
-                        tc::tma_load_4d(dst, tm, 2 * (xs - 1), ys - 1, cc >> 3, bb, &full[s]);
+                        // 8-byte elements, two per pixel, the row (with halo) contiguous
+                        tc::tma_load_4d(st, tm, 2 * (xs - 1), ys - 1, cc >> 3, bb, &full[s]);
                     }
                 }
-                unsigned char* ws = st + 2 * chunk_bytes;
-                for (int tap = 0; tap < 9; ++tap)
-                    for (int h = 0; h < 2; ++h)
-                        tc::tma_load_2d(ws + (tap * 2 + h) * wplane, &tm_w, tap * cin + gi * 16 + h * 8, 0, &full[s]);
+                unsigned char* ws = st + wofs;
+                if (g.w4) {
+                    tc::tma_load_4d(ws, &tm_w, 0, 0, 2 * gi, 0, &full[s]);
+                } else {
+                    for (int tap = 0; tap < 9; ++tap)
+                        for (int h = 0; h < 2; ++h)
+                            tc::tma_load_2d(ws + (tap * 2 + h) * wplane, &tm_w, tap * cin + gi * 16 + h * 8, 0,
+                                            &full[s]);
+                }
             }
         }
         if (!ok) {
@@ -222,53 +236,77 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                 }
             }
         }
-    } else if (tid == EPI + 32) {
+    } else if (warp == EPI_WARPS + 1) {
         // ---------------- MMA issuer ----------------
+        // The whole warp walks the loop, so that the descriptor arithmetic is warp-uniform,
+        // and lane 0 issues: one tcgen05.mma per (parity, M block, tap) with a 32-bit add
+        // for its A start address; the B descriptors of the nine taps are set per stage.
+        const bool leader = (tid & 31) == 0;
         const uint32_t idesc = tc::idesc_bf16_f32(128, a.npad);
         const uint32_t wplane = (uint32_t)a.npad * 16;
         // descriptors with a zero start address: the start (bits 0-13, 16-byte units) is added per MMA
         const uint64_t adesc0 = tc::smem_desc(0u, (uint32_t)chunk_bytes, 128);
         const uint64_t bdesc0 = tc::smem_desc(0u, wplane, 128);
+        const uint32_t a_lo0 = (uint32_t)adesc0, a_hi = (uint32_t)(adesc0 >> 32);
+        const uint32_t b_lo0 = (uint32_t)bdesc0, b_hi = (uint32_t)(bdesc0 >> 32);
+        const uint32_t tap_b16 = (2u * wplane) >> 4;   // B planes of one tap, 16-byte units
         long long j = 0;
         bool ok = true;
         for (int k = 0; k < ntiles && ok; ++k) {
             const int acc = k & 1;
             const int ause = k >> 1;
-            if (ause > 0 && !wait_bar(&tempty[acc], (uint32_t)((ause - 1) & 1), abort_v, 32)) { ok = false; break; }
+            // (the lanes agree on every wait's outcome, so that they leave the loop together)
+            const bool t_ok = ause == 0 || wait_bar(&tempty[acc], (uint32_t)((ause - 1) & 1), abort_v, 32);
+            if (!__all_sync(0xffffffffu, t_ok)) { ok = false; break; }
             tc::tc_fence_after_sync();
             const uint32_t dbase = tmem + (uint32_t)acc * g.acc_cols;
             for (int gi = 0; gi < G; ++gi, ++j) {
                 const int s = (int)(j % g.ns);
-                if (!wait_bar(&full[s], (uint32_t)((j / g.ns) & 1), abort_v, 32)) { ok = false; break; }
+                const bool f_ok = wait_bar(&full[s], (uint32_t)((j / g.ns) & 1), abort_v, 32);
+                if (!__all_sync(0xffffffffu, f_ok)) { ok = false; break; }
                 tc::tc_fence_after_sync();
                 const uint32_t a16 = (tc::smem_u32(smem + (size_t)s * g.stage) & 0x3FFFFu) >> 4;
-                const uint32_t w16 = a16 + ((2u * (uint32_t)chunk_bytes) >> 4);
+                const uint32_t bw_lo = b_lo0 + a16 + ((uint32_t)wofs >> 4);
                 for (int ph = 0; ph < g.nph; ++ph) {
-                    for (int m = 0; m < g.mb; ++m) {
-                        const uint32_t q16 = a16 + (uint32_t)(m * 128);   // 128 pixels of 16 bytes
-                        const uint32_t d = dbase + (uint32_t)((ph * g.mb + m) * a.npad);
-                        bool first = gi == 0;
+                    uint32_t ao[9];   // A start of each tap for M block 0, descriptor low word
+                    bool use[9];
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap) {
+                        int pl, off;   // A offset in 16-byte units from the stage
+                        use[tap] = tap_source<MODE>(tap, ph >> 1, ph & 1, g.pw, &pl, &off);
+                        ao[tap] = a_lo0 + a16 + (uint32_t)(pl * (g.pstride >> 4) + off);
+                    }
+                    uint32_t d = dbase + (uint32_t)(ph * g.mb * a.npad);
+                    for (int m = 0; m < g.mb; ++m, d += (uint32_t)a.npad) {
+                        const uint32_t mo = (uint32_t)(m * 128);   // 128 pixels of 16 bytes
+                        uint32_t accum = gi == 0 ? 0u : 1u;
 #pragma unroll
                         for (int tap = 0; tap < 9; ++tap) {
-                            int pl, off;   // A offset in 16-byte units from the stage
-                            if (!tap_source<MODE>(tap, ph >> 1, ph & 1, g.pw, &pl, &off)) continue;
-                            const int o = pl * (g.plane >> 4) + off;
-                            const uint64_t ad = adesc0 + (uint64_t)(q16 + (uint32_t)o);
-                            const uint64_t bd = bdesc0 + (uint64_t)(w16 + (uint32_t)tap * ((2u * wplane) >> 4));
-                            tc::mma_bf16(d, ad, bd, idesc, first ? 0u : 1u);
-                            first = false;
+                            if (!use[tap]) continue;
+                            if (leader) {
+                                const uint64_t ad = ((uint64_t)a_hi << 32) | (ao[tap] + mo);
+                                const uint64_t bd = ((uint64_t)b_hi << 32) | (bw_lo + (uint32_t)tap * tap_b16);
+                                tc::mma_bf16(d, ad, bd, idesc, accum);
+                            }
+                            accum = 1u;
                         }
                     }
                 }
-                tc::mma_commit(&empty[s]);
+                __syncwarp();
+                if (leader) tc::mma_commit(&empty[s]);
             }
-            if (ok) tc::mma_commit(&tfull[acc]);
+            __syncwarp();
+            if (ok && leader) tc::mma_commit(&tfull[acc]);
         }
         if (!ok) *abort_v = 1;
-        tc::mma_commit(&done);   // every MMA issued so far completes before `done`
-        long long it = 0;
-        while (!tc::mbar_try_wait(&done, 0u) && ++it < WAIT_LIMIT) {
+        __syncwarp();
+        if (leader) {
+            tc::mma_commit(&done);   // every MMA issued so far completes before `done`
+            long long it = 0;
+            while (!tc::mbar_try_wait(&done, 0u) && ++it < WAIT_LIMIT) {
+            }
         }
+        __syncwarp();
     } else if (warp < EPI_WARPS) {
         // ---------------- epilogue ----------------
         // warp w reads TMEM lanes 32 (w % 4) .. + 31 (accumulator row = M-block row);
@@ -279,6 +317,7 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
         const long long hw_out = (long long)a.hout * a.wout;
         const size_t plane_out = (size_t)hw_out * 8;   // elements between 8-channel planes
         const int nblk = g.nph * g.mb;
+        const int step_y = 256 / g.pw, step_x = 256 - step_y * g.pw;
         for (int k = 0; k < ntiles; ++k) {
             const int acc = k & 1;
             if (!wait_bar(&tfull[acc], (uint32_t)((k >> 1) & 1), abort_v, 128)) { *abort_v = 1; break; }
@@ -286,10 +325,73 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
             int b, xs, ys;
             tile_coords(k, b, xs, ys);
             const uint32_t dbase = lane_base + (uint32_t)acc * g.acc_cols;
+            const size_t img_base = (size_t)b * (size_t)(a.npad >> 3) * (size_t)hw_out * 8;
+            // one 16-channel segment of this thread's pixel: bias, residual, ReLU, store
+            auto segment = [&](float* vv, int n0, size_t ob, long long p) {
+#pragma unroll
+                for (int i = 0; i < 16; i += 4) {
+                    const float4 bb = *reinterpret_cast<const float4*>(bias_s + n0 + i);
+                    vv[i] += bb.x;
+                    vv[i + 1] += bb.y;
+                    vv[i + 2] += bb.z;
+                    vv[i + 3] += bb.w;
+                }
+                const size_t o0 = ob + (size_t)(n0 >> 3) * plane_out;   // planes n0/8 and n0/8 + 1
+                if (a.res) {
+                    uint4 r0 = __ldg(reinterpret_cast<const uint4*>(a.res + o0));
+                    uint4 r1 = __ldg(reinterpret_cast<const uint4*>(a.res + o0 + plane_out));
+                    const __nv_bfloat16* rb0 = reinterpret_cast<const __nv_bfloat16*>(&r0);
+                    const __nv_bfloat16* rb1 = reinterpret_cast<const __nv_bfloat16*>(&r1);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        vv[i] += __bfloat162float(rb0[i]);
+                        vv[8 + i] += __bfloat162float(rb1[i]);
+                    }
+                }
+                if (a.relu) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) vv[i] = fmaxf(vv[i], 0.0f);
+                }
+                if (a.out_fp32) {
+                    float* yo = reinterpret_cast<float*>(a.y) + (size_t)p * a.cstore;
+                    if (a.accum) {
+                        for (int i = 0; i < 16; ++i)
+                            if (n0 + i < a.cstore) yo[n0 + i] += vv[i];
+                    } else {
+                        for (int i = 0; i < 16; ++i)
+                            if (n0 + i < a.cstore) yo[n0 + i] = vv[i];
+                    }
+                } else {
+                    uint4 w0, w1;
+                    __nv_bfloat16* ob0 = reinterpret_cast<__nv_bfloat16*>(&w0);
+                    __nv_bfloat16* ob1 = reinterpret_cast<__nv_bfloat16*>(&w1);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        ob0[i] = __float2bfloat16_rn(vv[i]);
+                        ob1[i] = __float2bfloat16_rn(vv[8 + i]);
+                    }
+                    __nv_bfloat16* yq = reinterpret_cast<__nv_bfloat16*>(a.y) + o0;
+                    *reinterpret_cast<uint4*>(yq) = w0;
+                    *reinterpret_cast<uint4*>(yq + plane_out) = w1;
+                }
+            };
+            int m_prev = -4, yy = 0, xx = 0;
             for (int bi = wg; bi < nblk; bi += 2) {
                 const int ph = bi / g.mb, m = bi - ph * g.mb;
-                const int q = m * 128 + row;
-                const int yy = q / g.pw, xx = q - yy * g.pw;
+                if (m != m_prev + 2) {
+                    const int q = m * 128 + row;
+                    yy = q / g.pw;
+                    xx = q - yy * g.pw;
+                } else {
+                    // the warpgroup's next block of the same phase lies 256 pixels further on
+                    yy += step_y;
+                    xx += step_x;
+                    if (xx >= g.pw) {
+                        xx -= g.pw;
+                        ++yy;
+                    }
+                }
+                m_prev = m;
                 int oy = ys + yy, ox = xs + xx;
                 if (MODE >= 2) {
                     oy = 2 * oy + (ph >> 1);
@@ -297,74 +399,20 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                 }
                 const bool valid = xx < g.tw && yy < g.rows && oy < a.hout && ox < a.wout;
                 const long long pix = (long long)oy * a.wout + ox;
-                const size_t ob = valid ? nc8(b, 0, pix, a.npad, hw_out) : 0;   // channel 0 of this pixel
+                const size_t ob = img_base + (size_t)pix * 8;   // channel 0 of this pixel
                 const long long p = (long long)b * hw_out + pix;
                 const uint32_t tcol = dbase + (uint32_t)(bi * a.npad);
-                for (int c0 = 0; c0 < a.npad; c0 += 32) {
-                    float v[32];
-                    int nseg;
-                    if (c0 + 32 <= a.npad) {
+                if (a.npad == 16) {
+                    float v[16];
+                    tc::tmem_ld16(tcol, v);
+                    if (valid) segment(v, 0, ob, p);
+                } else {
+                    for (int c0 = 0; c0 < a.npad; c0 += 32) {
+                        float v[32];
                         tc::tmem_ld32(tcol + (uint32_t)c0, v);
-                        nseg = 2;
-                    } else {
-                        float h[16];
-                        tc::tmem_ld16(tcol + (uint32_t)c0, h);
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] = h[i];
-                        nseg = 1;
-                    }
-                    if (!valid) continue;
-#pragma unroll
-                    for (int sgi = 0; sgi < 2; ++sgi) {
-                        if (sgi >= nseg) break;
-                        float* vv = v + 16 * sgi;
-                        const int n0 = c0 + 16 * sgi;
-#pragma unroll
-                        for (int i = 0; i < 16; i += 4) {
-                            const float4 bb = *reinterpret_cast<const float4*>(bias_s + n0 + i);
-                            vv[i] += bb.x;
-                            vv[i + 1] += bb.y;
-                            vv[i + 2] += bb.z;
-                            vv[i + 3] += bb.w;
-                        }
-                        const size_t o0 = ob + (size_t)(n0 >> 3) * plane_out;   // planes n0/8 and n0/8 + 1
-                        if (a.res) {
-                            uint4 r0 = __ldg(reinterpret_cast<const uint4*>(a.res + o0));
-                            uint4 r1 = __ldg(reinterpret_cast<const uint4*>(a.res + o0 + plane_out));
-                            const __nv_bfloat16* rb0 = reinterpret_cast<const __nv_bfloat16*>(&r0);
-                            const __nv_bfloat16* rb1 = reinterpret_cast<const __nv_bfloat16*>(&r1);
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                vv[i] += __bfloat162float(rb0[i]);
-                                vv[8 + i] += __bfloat162float(rb1[i]);
-                            }
-                        }
-                        if (a.relu) {
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) vv[i] = fmaxf(vv[i], 0.0f);
-                        }
-                        if (a.out_fp32) {
-                            float* yo = reinterpret_cast<float*>(a.y) + (size_t)p * a.cstore;
-                            if (a.accum) {
-                                for (int i = 0; i < 16; ++i)
-                                    if (n0 + i < a.cstore) yo[n0 + i] += vv[i];
-                            } else {
-                                for (int i = 0; i < 16; ++i)
-                                    if (n0 + i < a.cstore) yo[n0 + i] = vv[i];
-                            }
-                        } else {
-                            uint4 w0, w1;
-                            __nv_bfloat16* ob0 = reinterpret_cast<__nv_bfloat16*>(&w0);
-                            __nv_bfloat16* ob1 = reinterpret_cast<__nv_bfloat16*>(&w1);
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                ob0[i] = __float2bfloat16_rn(vv[i]);
-                                ob1[i] = __float2bfloat16_rn(vv[8 + i]);
-                            }
-                            __nv_bfloat16* yq = reinterpret_cast<__nv_bfloat16*>(a.y) + o0;
-                            *reinterpret_cast<uint4*>(yq) = w0;
-                            *reinterpret_cast<uint4*>(yq + plane_out) = w1;
-                        }
+                        if (!valid) continue;
+                        segment(v, c0, ob, p);
+                        segment(v + 16, c0 + 16, ob, p);
                     }
                 }
             }
@@ -398,15 +446,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // Chunked BF16 activation [n][c/8][h][w][8] (see nc8).  Modes 0, 2, 3: viewed
 // as 8-byte elements, a 4-D tensor (2w, h, c/8, n); box = 2 box_w elements (box_w
-// pixels of one row, contiguous) x box_h rows x one 8-channel plane x one image.
+// pixels of one row, contiguous) x box_h rows x two 8-channel planes x one image.
 // Mode 1: a 5-D tensor (2, w, h, c/8, n) traversed with element stride 2 in w and
-// h (box_w / 2 x box_h / 2 pixels land in shared memory).
+// h (box_w / 2 x box_h / 2 pixels of each of the two planes land in shared memory).
 bool encode_act(CUtensorMap* m, const void* base, int c, int w, int h, int n, int box_w, int box_h, int es) {
     const cuuint64_t plane = (cuuint64_t)w * h * 16;
     if (es == 1) {
         const cuuint64_t dims[4] = {(cuuint64_t)2 * w, (cuuint64_t)h, (cuuint64_t)(c / 8), (cuuint64_t)n};
         const cuuint64_t strides[3] = {(cuuint64_t)w * 16, plane, plane * (cuuint64_t)(c / 8)};
-        const cuuint32_t box[4] = {(cuuint32_t)(2 * box_w), (cuuint32_t)box_h, 1u, 1u};
+        const cuuint32_t box[4] = {(cuuint32_t)(2 * box_w), (cuuint32_t)box_h, 2u, 1u};
         const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
         return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void*>(base), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -414,11 +462,25 @@ bool encode_act(CUtensorMap* m, const void* base, int c, int w, int h, int n, in
     }
     const cuuint64_t dims[5] = {2u, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)(c / 8), (cuuint64_t)n};
     const cuuint64_t strides[4] = {16u, (cuuint64_t)w * 16, plane, plane * (cuuint64_t)(c / 8)};
-    const cuuint32_t box[5] = {2u, (cuuint32_t)box_w, (cuuint32_t)box_h, 1u, 1u};
+    const cuuint32_t box[5] = {2u, (cuuint32_t)box_w, (cuuint32_t)box_h, 2u, 1u};
     const cuuint32_t estr[5] = {1u, (cuuint32_t)es, (cuuint32_t)es, 1u, 1u};
     return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<void*>(base), dims, strides, box, estr,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// weights [npad][9][cin] viewed as a 4-D tensor (8 channels, npad rows, cin/8
+// chunks, 9 taps); box = (8, npad, 2, 9): the 16-channel group's 18 core-matrix
+// planes (tap, half) in one copy, laid out as [tap][half][npad][8].
+bool encode_w4(CUtensorMap* m, const void* base, int cin, int npad) {
+    const cuuint64_t dims[4] = {8u, (cuuint64_t)npad, (cuuint64_t)(cin / 8), 9u};
+    const cuuint64_t strides[3] = {(cuuint64_t)9 * cin * 2, 16u, (cuuint64_t)cin * 2};
+    const cuuint32_t box[4] = {8u, (cuuint32_t)npad, 2u, 9u};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    const CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides,
+                                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 // weights [npad][9 * cin] viewed as 2-D; box = 8 input channels x npad rows.
@@ -433,6 +495,7 @@ bool encode_w(CUtensorMap* m, const void* base, int cin, int npad) {
 }
 
 std::atomic<int> g_rows_cap{0};   // tile-height limit set by cnn_set_conv_tiling (0 = automatic)
+std::atomic<int> g_stage_kb{0}, g_ring_kb{0};   // stage / ring budgets set by cnn_set_conv_ring (0 = default)
 int g_last_launch[6] = {0, 0, 0, 0, 0, 0};   // grid, CTAs per SM, CTAs registers/smem allow, shared memory,
                                              // registers per thread, static shared memory
 
@@ -467,8 +530,9 @@ Geometry plan(const ConvArgs& a) {
     auto fill = [&](int rows) {
         g.rows = rows;
         g.mb = (rows * g.pw + 127) / 128;
-        g.plane = (((rows + halo) * g.pw + SLACK_PX) * 16 + 127) / 128 * 128;
-        g.stage = 2 * g.nplanes * g.plane + g.wbytes;
+        g.plane = ((rows + halo) * g.pw + SLACK_PX) * 16;
+        g.pstride = (2 * g.plane + 127) / 128 * 128;
+        g.stage = g.nplanes * g.pstride + g.wbytes;
     };
     int rmax = (maxmb * 128) / g.pw;
     const int cap = g_rows_cap.load();
@@ -479,9 +543,13 @@ Geometry plan(const ConvArgs& a) {
     if (rmax < 1) return Geometry{};   // tiles = 0: not this kernel
     int rows = rmax;
     fill(rows);
-    while (rows > 1 && (size_t)g.stage > STAGE_BUDGET) fill(--rows);
+    const size_t stage_budget = g_stage_kb.load() > 0 ? (size_t)g_stage_kb.load() * 1024
+                                : (mode == 1 ? STAGE_BUDGET_S2 : STAGE_BUDGET);
+    const size_t ring_budget = g_ring_kb.load() > 0 ? (size_t)g_ring_kb.load() * 1024
+                               : (mode == 1 ? RING_BUDGET_S2 : RING_BUDGET);
+    while (rows > 1 && (size_t)g.stage > stage_budget) fill(--rows);
     if (g.mb < 1 || g.mb > maxmb) return Geometry{};
-    g.ns = (int)(RING_BUDGET / (size_t)g.stage);
+    g.ns = (int)(ring_budget / (size_t)g.stage);
     if (g.ns > MAX_NS) g.ns = MAX_NS;
     if (g.ns < 2) g.ns = 2;
     g.tiles_x = (W + g.tw - 1) / g.tw;
@@ -572,6 +640,7 @@ int launch_mode(const CUtensorMap& tm0, const CUtensorMap& tm1, const CUtensorMa
 int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st) {
     if (!encode_fn()) return HELM_EINVAL;
     if (a.mode < 0 || a.mode > 3) return HELM_EINVAL;
+    if (a.npad != 16 && a.npad % 32) return HELM_EINVAL;   // the epilogue reads 16 or 32k columns
     if (a.mode == 0 && (a.hin != a.hout || a.win != a.wout)) return HELM_EINVAL;
     if (a.mode == 1 && (a.hin != 2 * a.hout || a.win != 2 * a.wout)) return HELM_EINVAL;
     if (a.mode >= 2 && (a.hout != 2 * a.hin || a.wout != 2 * a.win)) return HELM_EINVAL;
@@ -580,7 +649,7 @@ int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st) {
         return HELM_EINVAL;
     if ((long long)a.nb * (a.mode >= 2 ? (long long)a.hin * a.win : (long long)a.hout * a.wout) > 0x7fffffffLL)
         return HELM_EINVAL;
-    const Geometry g = plan(a);
+    Geometry g = plan(a);
     if (g.tiles <= 0) return HELM_EINVAL;
     if ((size_t)g.ns * g.stage > 200 * 1024 || g.tmem_cols > 512) return HELM_EINVAL;
     // box extents: modes 0/2/3 (tw + 2) pixels = 2 (tw + 2) elements x (rows + 2); mode 1
@@ -598,7 +667,8 @@ int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st) {
     } else {
         tm1 = tm0;
     }
-    if (!encode_w(&tmw, a.w, a.c0 + a.c1, a.npad)) return HELM_EINVAL;
+    g.w4 = encode_w4(&tmw, a.w, a.c0 + a.c1, a.npad) ? 1 : 0;
+    if (!g.w4 && !encode_w(&tmw, a.w, a.c0 + a.c1, a.npad)) return HELM_EINVAL;
     switch (a.mode) {
         case 0: return launch_mode<0>(tm0, tm1, tmw, a, g, st);
         case 1: return launch_mode<1>(tm0, tm1, tmw, a, g, st);
@@ -615,6 +685,16 @@ extern "C" int cnn_set_conv_tiling(int max_rows) {
         return HELM_EINVAL;
     }
     helm::g_rows_cap.store(max_rows);
+    return HELM_OK;
+}
+
+extern "C" int cnn_set_conv_ring(int stage_kb, int ring_kb) {
+    if (stage_kb < 0 || stage_kb > 128 || ring_kb < 0 || ring_kb > 200 || (stage_kb && ring_kb && ring_kb < stage_kb)) {
+        helm::set_error("cnn_set_conv_ring: stage_kb in [0, 128], ring_kb in [0, 200], ring_kb >= stage_kb");
+        return HELM_EINVAL;
+    }
+    helm::g_stage_kb.store(stage_kb);
+    helm::g_ring_kb.store(ring_kb);
     return HELM_OK;
 }
 

@@ -103,6 +103,8 @@ def _load():
     lib.cnn_set_conv_path.restype = ip
     lib.cnn_set_conv_tiling.argtypes = [ip]
     lib.cnn_set_conv_tiling.restype = ip
+    lib.cnn_set_conv_ring.argtypes = [ip, ip]
+    lib.cnn_set_conv_ring.restype = ip
     lib.cnn_conv_last_launch.argtypes = [ctypes.POINTER(ctypes.c_int)]
     lib.cnn_conv_last_launch.restype = None
     lib.cnn_conv_launch_counts.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
@@ -348,6 +350,11 @@ def cnn_set_conv_path(path: int):
 def cnn_set_conv_tiling(max_rows: int):
     """Tile-height limit of the TMA conv kernel (0 = automatic)."""
     _check(lib.cnn_set_conv_tiling(int(max_rows)), "cnn_set_conv_tiling")
+
+
+def cnn_set_conv_ring(stage_kb: int, ring_kb: int):
+    """Stage and ring shared-memory budgets of the TMA conv kernel in KB (0 = default)."""
+    _check(lib.cnn_set_conv_ring(int(stage_kb), int(ring_kb)), "cnn_set_conv_ring")
 
 
 def cnn_conv_last_launch():
