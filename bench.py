@@ -206,6 +206,7 @@ class Problem:
         self.fi = w.freq_index()
         self.x = torch.empty((self.nb, w.nz, w.nx), dtype=torch.complex128, device=dev)
         self.iters = []
+        self.solved = []   # RHS per step that reached the tolerance
 
     def step(self, ctx, rhs=None, x=None, kappa=None, gamma=None, om=None):
         n = self.native
@@ -213,10 +214,12 @@ class Problem:
                           self.omegas if om is None else om)
         st, iters, rel, stat = n.helm_solve(ctx, self.rhs if rhs is None else rhs, self.x if x is None else x,
                                             self.nb, self.fi, TOL, n.HELM_SOLVE_ZERO_X0)
-        if st != n.HELM_OK:
-            raise RuntimeError(f"solve did not converge: status {st}, per-RHS {np.unique(stat)}, "
+        if st not in (n.HELM_OK, n.HELM_ENOCONV):
+            raise RuntimeError(f"solve failed: status {st}, per-RHS {np.unique(stat)}, "
                                f"iterations {iters.min()}-{iters.max()}, max rel. residual {rel.max():.3e}")
+        # an RHS that hits the iteration cap is not counted as solved
         self.iters.append(iters.copy())
+        self.solved.append(int(np.count_nonzero(np.asarray(stat) == n.HELM_OK)))
         return rel
 
 
@@ -237,6 +240,7 @@ def timed(prob, ctx, steps, warmup, dev, world, stream, sampler=None):
     torch.cuda.synchronize(dev)
     launches0 = native.helm_launch_count()
     prob.iters.clear()
+    prob.solved.clear()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -251,6 +255,11 @@ def timed(prob, ctx, steps, warmup, dev, world, stream, sampler=None):
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     its = np.concatenate(prob.iters)
+    # RHS that reached the tolerance in the timed steps, summed over ranks
+    solved = torch.tensor([float(sum(prob.solved))], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(solved, op=dist.ReduceOp.SUM)
+    timed.solved = int(solved.item())
     return float(t.item()), its, float(max(np.max(r) for r in rels)), launches, clocks
 
 
@@ -271,9 +280,10 @@ def e2e_of(prob, ctx, steps, dev):
         prob.step(ctx, **args)
     torch.cuda.synchronize(dev)
     sec = (time.perf_counter() - t0) / steps
+    solved = sum(prob.solved[-steps:]) / steps   # RHS per step that reached the tolerance
     h2d = rhs_pin.numel() * 8 + (k_pin.numel() + g_pin.numel() + o_pin.numel()) * 4 + prob.nb * 4
     d2h = x_pin.numel() * 16
-    return {"value": prob.nb / sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    return {"value": solved / sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
 
 def profile_step(native, prob, ctx):
@@ -377,13 +387,14 @@ def run_ours(args, rank, world):
                                 opts=native.helm_default_opts(mg_levels=3, max_rhs=prob.nb,
                                                               stream=stream.cuda_stream))
         ms, its, relmax, launches, clocks = timed(prob, ctx, args.steps, args.warmup, dev, world, stream, sampler)
-        value = world * prob.nb * args.steps / (ms / 1e3)
+        value = timed.solved / (ms / 1e3)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "c64/f64", "data": "synthetic",
                 "config": config_of(w, "mg"), "impl": "ours", "precond": "mg",
                 "iterations": {"mean": float(its.mean()), "max": int(its.max()), "min": int(its.min())},
-                "max_rel_residual": relmax, "gpu_launches": int(launches), "clocks": clocks}
+                "max_rel_residual": relmax, "unsolved_rhs": world * prob.nb * args.steps - timed.solved,
+                "gpu_launches": int(launches), "clocks": clocks}
         if not args.no_extras:
             prof, flops = profile_step(native, prob, ctx)
             line["roofline"] = roofline_of(prof, flops)
@@ -405,7 +416,7 @@ def run_ours(args, rank, world):
     widths = (16, 32, 64, 128)
     net = native.cnn_create(len(widths), widths)
     native.cnn_init_params(net, media.SEED_CNN, 0.5)
-    opts = dict(mg_levels=3, max_rhs=prob.nb, max_iter=600, stream=stream.cuda_stream)
+    opts = dict(mg_levels=3, max_rhs=prob.nb, max_iter=1000, stream=stream.cuda_stream)
     ctx_cnn = native.helm_setup(prob.kappa, prob.gamma, w.nx, w.nz, w.h, w.h, prob.omegas, net=net,
                                 opts=native.helm_default_opts(precond=native.HELM_PC_CNN, **opts))
     ctx_mg = native.helm_setup(prob.kappa, prob.gamma, w.nx, w.nz, w.h, w.h, prob.omegas,
@@ -422,16 +433,19 @@ def run_ours(args, rank, world):
     train_s = time.perf_counter() - t0
 
     ms, its, relmax, launches, clocks = timed(prob, ctx_cnn, args.steps, args.warmup, dev, world, stream, sampler)
+    solved = timed.solved
     mg_ms, mg_its, mg_rel, _, _ = timed(prob, ctx_mg, args.steps, min(args.warmup, 1), dev, world, stream)
-    value = world * prob.nb * args.steps / (ms / 1e3)
-    mg_value = world * prob.nb * args.steps / (mg_ms / 1e3)
+    mg_solved = timed.solved
+    value = solved / (ms / 1e3)
+    mg_value = mg_solved / (mg_ms / 1e3)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64/f64 solve, bf16 network (fp32 accumulate)", "data": "synthetic",
             "config": config_of(w, "cnn"), "impl": "ours", "precond": "cnn",
             "iterations": {"mean": float(its.mean()), "max": int(its.max()), "min": int(its.min())},
-            "max_rel_residual": relmax,
+            "max_rel_residual": relmax, "unsolved_rhs": world * prob.nb * args.steps - solved,
             "mg_fgmres": {"value": mg_value, "unit": UNIT, "ms_per_step": mg_ms / args.steps,
+                          "unsolved_rhs": world * prob.nb * args.steps - mg_solved,
                           "iterations": {"mean": float(mg_its.mean()), "max": int(mg_its.max()),
                                          "min": int(mg_its.min())}, "max_rel_residual": mg_rel},
             "training": {"steps": hist.steps, "seconds": train_s, "batch": 16, "lr": [1e-3, 1e-4],

@@ -293,6 +293,9 @@ int fgmres_batch(helm_ctx* c, const float2* rhs, double2* x, int nb, double tol,
     const size_t vs = (size_t)c->cap * N;
     const int k = c->fine.k;
     const bool pc = c->opt.precond != HELM_PC_NONE;
+    // the network pass of each cycle takes only the RHS still running at its restart
+    const bool compact = c->opt.precond == HELM_PC_CNN && c->cnn_act_host;
+    c->cnn_nact = -1;
     HELM_TRY(launch_outer_init(c, nb));
     if (steps_cap) {
         // fixed number of steps per RHS (no convergence test): start the step
@@ -326,8 +329,13 @@ int fgmres_batch(helm_ctx* c, const float2* rhs, double2* x, int nb, double tol,
         HELM_CK(cudaMemsetAsync(n_active_dev, 0, sizeof(int), c->stream));
         HELM_TRY(launch_restart_check_dev(c, nb, tol, n_active_dev));
         HELM_CK(cudaMemcpyAsync(n_active_host, n_active_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        if (compact)
+            HELM_CK(cudaMemcpyAsync(c->cnn_act_host, c->outer.outer_active, nb * sizeof(int),
+                                    cudaMemcpyDeviceToHost, c->stream));
         HELM_CK(cudaStreamSynchronize(c->stream));
+        if (compact && *n_active_host > 0) HELM_TRY(cnn_ctx_compact(c, nb));
     }
+    c->cnn_nact = -1;
     if (adjoint) HELM_TRY(launch_conj64(c, x, nb));
     return HELM_OK;
 }

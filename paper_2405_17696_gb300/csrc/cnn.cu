@@ -171,13 +171,14 @@ __global__ void sumsq_kernel(const float2* __restrict__ r, long long n, const in
     const int b = blockIdx.y;
     if (mask && !mask[b]) return;
     const float4* rb = reinterpret_cast<const float4*>(r + (long long)b * n);   // n even: two nodes per load
-    double a = 0.0;
+    // FP32 partial sums per thread (a few hundred terms), FP64 from the warp sums on
+    float af = 0.0f;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n / 2; q += (long long)gridDim.x * blockDim.x) {
         const float4 v = rb[q];
-        a += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+        af = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, af))));
     }
     __shared__ double sm[32];
-    a = warp_sum(a);
+    double a = warp_sum((double)af);
     if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = a;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -193,17 +194,17 @@ __global__ void rms_finalize_kernel(const double* __restrict__ acc, long long n,
     if (b < nb) rms[b] = (mask && !mask[b]) ? 0.0f : (float)sqrt(acc[b] / (double)n);
 }
 
-// rms(r) per RHS (one block per RHS, FP64 sum)
+// rms(r) per RHS (one block per RHS)
 __global__ void rms_kernel(const float2* __restrict__ r, long long n, float* __restrict__ rms, const int* mask) {
     const int b = blockIdx.x;
     if (mask && !mask[b]) { if (threadIdx.x == 0) rms[b] = 0.0f; return; }
-    double acc = 0.0;
+    float af = 0.0f;   // FP32 partial sum per thread, FP64 from the warp sums on
     for (long long p = threadIdx.x; p < n; p += blockDim.x) {
         float2 v = r[(long long)b * n + p];
-        acc += (double)v.x * v.x + (double)v.y * v.y;
+        af = fmaf(v.x, v.x, fmaf(v.y, v.y, af));
     }
     __shared__ double sm[32];
-    acc = warp_sum(acc);
+    double acc = warp_sum((double)af);
     if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -216,12 +217,14 @@ __global__ void rms_kernel(const float2* __restrict__ r, long long n, float* __r
 // solver input BF16 chunked [nb][2][n][8] = [Re r / rms, Im r / rms, gamma, 0...]; grid
 // (slices, nb).  The second plane (channels 8-15) is zero and written only when
 // zero_plane1 is set (a buffer that already holds zeros there keeps them).
+// Image b of the solver input from RHS idx[b] (idx == nullptr: RHS b).
 __global__ void solver_input_kernel(const float2* __restrict__ r, const float* __restrict__ rms,
                                     const float2* __restrict__ mg, long long n, int zero_plane1,
-                                    __nv_bfloat16* __restrict__ out) {
+                                    __nv_bfloat16* __restrict__ out, const int* __restrict__ idx) {
     const int b = blockIdx.y;
-    const float s = rms[b] > 0.0f ? 1.0f / rms[b] : 0.0f;
-    const float2* rb = r + (long long)b * n;
+    const int src = idx ? idx[b] : b;
+    const float s = rms[src] > 0.0f ? 1.0f / rms[src] : 0.0f;
+    const float2* rb = r + (long long)src * n;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const float2 v = rb[p];
         __nv_bfloat16 q[8];
@@ -251,27 +254,30 @@ __global__ void net_residual_kernel(OpFine5 op, const float2* __restrict__ r, co
 
 // z += e0
 // Guarded composition: per RHS, t = H e0 and acc[b] = {Re <t, r>, Im <t, r>, <t, t>}
-// (FP64, blocks of a RHS add their partial sums atomically; acc zeroed before).
+// (FP32 partial sums per thread, FP64 from the warp sums on; blocks of a RHS add
+// their sums atomically; acc zeroed before).  Block x takes grid rows x, x + gridDim.x, ...
+// A RHS that is not guarded (guard non-null and guard[b] = 0) takes a = 1 and
+// needs no sums.
 __global__ void net_scale_dots_kernel(OpFine5 op, const float2* __restrict__ r, const float2* __restrict__ e0,
-                                      const int* mask, double* __restrict__ acc) {
+                                      const int* mask, const int* guard, double* __restrict__ acc) {
     const int b = blockIdx.y;
-    if (mask && !mask[b]) return;
+    if ((mask && !mask[b]) || (guard && !guard[b])) return;
     const long long n = (long long)op.nx * op.nz;
     const float2* eb = e0 + (long long)b * n;
     const float2* rb = r + (long long)b * n;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        const int iz = (int)(p / op.nx), ix = (int)(p - (long long)iz * op.nx);
-        const float2 t = op.apply(eb, b, ix, iz);
-        const float2 v = rb[p];
-        a0 += (double)t.x * v.x + (double)t.y * v.y;
-        a1 += (double)t.x * v.y - (double)t.y * v.x;
-        a2 += (double)t.x * t.x + (double)t.y * t.y;
-    }
+    float f0 = 0.0f, f1 = 0.0f, f2 = 0.0f;
+    for (int iz = blockIdx.x; iz < op.nz; iz += gridDim.x)
+        for (int ix = threadIdx.x; ix < op.nx; ix += blockDim.x) {
+            const float2 t = op.apply(eb, b, ix, iz);
+            const float2 v = rb[(long long)iz * op.nx + ix];
+            f0 += t.x * v.x + t.y * v.y;
+            f1 += t.x * v.y - t.y * v.x;
+            f2 += t.x * t.x + t.y * t.y;
+        }
     __shared__ double sm[3][32];
-    a0 = warp_sum(a0);
-    a1 = warp_sum(a1);
-    a2 = warp_sum(a2);
+    double a0 = warp_sum((double)f0);
+    double a1 = warp_sum((double)f1);
+    double a2 = warp_sum((double)f2);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) { sm[0][w] = a0; sm[1][w] = a1; sm[2][w] = a2; }
     __syncthreads();
@@ -328,12 +334,14 @@ __global__ void add_kernel(float2* __restrict__ z, const float2* __restrict__ e0
 
 // e0 = h^2 rms (out_0 + i out_1)
 // e0 = h^2 rms (o_0 + i o_1); grid (slices, nb)
+// Image b of the solver output to RHS idx[b] (idx == nullptr: RHS b).
 __global__ void solver_output_kernel(const float* __restrict__ out, const float* __restrict__ rms, float h2,
-                                     long long n, float2* __restrict__ e0) {
+                                     long long n, float2* __restrict__ e0, const int* __restrict__ idx) {
     const int b = blockIdx.y;
-    const float s = h2 * rms[b];
+    const int dst = idx ? idx[b] : b;
+    const float s = h2 * rms[dst];
     const float2* ob = reinterpret_cast<const float2*>(out) + (long long)b * n;
-    float2* eb = e0 + (long long)b * n;
+    float2* eb = e0 + (long long)dst * n;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const float2 o = ob[p];
         eb[p] = make_float2(s * o.x, s * o.y);
@@ -370,7 +378,7 @@ int cnn_solver_input(const helm_ctx* c, const float2* r, int nb, void* out, floa
     }
     LaunchScope scope(c, K_CNN_IO);
     solver_input_kernel<<<dim3((unsigned)std::min<long long>((n + 255) / 256, 512), nb), 256, 0, c->stream>>>(
-        r, rms, c->mg, n, 1, (__nv_bfloat16*)out);
+        r, rms, c->mg, n, 1, (__nv_bfloat16*)out, nullptr);
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -387,6 +395,12 @@ void cnn_ctx_free(helm_ctx* c) {
     cudaFree(c->cnn_rres);
     cudaFree(c->cnn_rms);
     cudaFree(c->cnn_alpha);
+    cudaFree(c->cnn_idx);
+    cudaFree(c->cnn_zmapc);
+    cudaFreeHost(c->cnn_idx_host);
+    cudaFreeHost(c->cnn_act_host);
+    c->cnn_idx = c->cnn_zmapc = c->cnn_idx_host = c->cnn_act_host = nullptr;
+    c->cnn_nact = -1;
     c->cnn_alpha = nullptr;
     c->cnn_rres = nullptr;
     c->cnn_in = nullptr;
@@ -412,6 +426,10 @@ int cnn_ctx_setup(helm_ctx* c) {
         HELM_CK(cudaMalloc(&c->cnn_rres, (size_t)c->cap * n * sizeof(float2)));
         HELM_CK(cudaMalloc(&c->cnn_rms, (size_t)c->cap * sizeof(float)));
         HELM_CK(cudaMalloc(&c->cnn_alpha, (size_t)c->cap * 3 * sizeof(double)));
+        HELM_CK(cudaMalloc(&c->cnn_idx, (size_t)c->cap * sizeof(int)));
+        HELM_CK(cudaMalloc(&c->cnn_zmapc, (size_t)c->cap * sizeof(int)));
+        HELM_CK(cudaMallocHost(&c->cnn_idx_host, (size_t)c->cap * sizeof(int)));
+        HELM_CK(cudaMallocHost(&c->cnn_act_host, (size_t)c->cap * sizeof(int)));
     }
     for (void* p : c->cnn_z) cudaFree(p);
     c->cnn_z.clear();
@@ -432,6 +450,29 @@ int cnn_ctx_setup(helm_ctx* c) {
     return check_conv_error(m, c->stream);
 }
 
+__global__ void gather_int_kernel(const int* __restrict__ src, const int* __restrict__ idx, int n,
+                                  int* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[idx[i]];
+}
+
+// After a restart check: list the RHS whose outer iteration is still running
+// (flags already copied to cnn_act_host and the stream synchronised) so that the
+// next cycle's network passes take only those.
+int cnn_ctx_compact(helm_ctx* c, int nb) {
+    c->cnn_nact = -1;
+    if (!c->net || !c->cnn_idx_host || !c->cnn_act_host) return HELM_OK;
+    int n = 0;
+    for (int b = 0; b < nb; ++b)
+        if (c->cnn_act_host[b]) c->cnn_idx_host[n++] = b;
+    if (n == 0 || n == nb) return HELM_OK;
+    HELM_CK(cudaMemcpyAsync(c->cnn_idx, c->cnn_idx_host, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    gather_int_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(c->rhs_freq, c->cnn_idx, n, c->cnn_zmapc);
+    HELM_CK(cudaGetLastError());
+    c->cnn_nact = n;
+    return HELM_OK;
+}
+
 int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const int* mask, int with_vcycle) {
     cnn_model* m = c->net;
     const long long n = (long long)c->nx * c->nz;
@@ -444,23 +485,30 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
         HELM_CK(cudaGetLastError());
     }
     const dim3 g2((unsigned)std::min<long long>((n + 255) / 256, 512), nb);
+    // inside FGMRES (mask = the cycle's active flags) only the RHS still iterating at
+    // the last restart go through the network; the others keep a stale e0 that the
+    // masked kernels below never read
+    const bool compact = mask == c->fine.active && c->cnn_nact > 0 && c->cnn_nact < nb;
+    const int nnet = compact ? c->cnn_nact : nb;
+    const int* idx = compact ? c->cnn_idx : nullptr;
+    const dim3 gn(g2.x, (unsigned)nnet);
     {
         LaunchScope scope(c, K_CNN_IO);
-        solver_input_kernel<<<g2, 256, 0, c->stream>>>(v, c->cnn_rms, c->mg, n, 0, (__nv_bfloat16*)c->cnn_in);
+        solver_input_kernel<<<gn, 256, 0, c->stream>>>(v, c->cnn_rms, c->mg, n, 0, (__nv_bfloat16*)c->cnn_in, idx);
         HELM_CK(cudaGetLastError());
     }
     Runner r(m, c, c->stream, &c->cnn_arena, &c->cnn_arena_bytes);
-    r.set_zmap(c->rhs_freq, c->nfreq);
+    r.set_zmap(compact ? c->cnn_zmapc : c->rhs_freq, c->nfreq);
     std::vector<__nv_bfloat16*> zz;
     for (void* p : c->cnn_z) zz.push_back((__nv_bfloat16*)p);
-    if (!r.solver((const __nv_bfloat16*)c->cnn_in, nb, c->nz, c->nx, zz, 2, c->cnn_out)) {
+    if (!r.solver((const __nv_bfloat16*)c->cnn_in, nnet, c->nz, c->nx, zz, 2, c->cnn_out)) {
         if (std::string(helm_last_error()).empty()) set_error("solver pass failed");
         return HELM_ECUDA;
     }
     {
         LaunchScope scope(c, K_CNN_IO);
         float2* e0 = with_vcycle ? c->cnn_e0 : z;
-        solver_output_kernel<<<g2, 256, 0, c->stream>>>(c->cnn_out, c->cnn_rms, c->hx * c->hz, n, e0);
+        solver_output_kernel<<<gn, 256, 0, c->stream>>>(c->cnn_out, c->cnn_rms, c->hx * c->hz, n, e0, idx);
         HELM_CK(cudaGetLastError());
     }
     if (!with_vcycle) return HELM_OK;
@@ -476,7 +524,7 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
         double* acc = c->cnn_alpha;
         LaunchScope scope(c, K_CNN_IO);
         HELM_CK(cudaMemsetAsync(acc, 0, (size_t)3 * nb * sizeof(double), c->stream));
-        net_scale_dots_kernel<<<dim3(16, nb), 256, 0, c->stream>>>(fine_op(c, 0), v, c->cnn_e0, mask, acc);
+        net_scale_dots_kernel<<<dim3(64, nb), 256, 0, c->stream>>>(fine_op(c, 0), v, c->cnn_e0, mask, guard, acc);
         net_scaled_residual_kernel<<<dim3((c->nx + 31) / 32, (c->nz + 7) / 8, nb), dim3(32, 8), 0, c->stream>>>(
             fine_op(c, 0), v, c->cnn_e0, rr, acc, guard);
         HELM_CK(cudaGetLastError());

@@ -290,6 +290,14 @@ struct helm_ctx {
     float2* cnn_rres = nullptr;      // residual left by the network, [cap][nz][nx]
     double* cnn_alpha = nullptr;     // [cap][3] sums of the scaled composition (<t, r>, <t, t>)
     float* cnn_rms = nullptr;        // [cap]
+    // Active-RHS compaction of the network pass inside FGMRES: at each restart the
+    // RHS still iterating are listed (cnn_idx, their context indices in cnn_zmapc)
+    // and only those cnn_nact images go through the network (-1: off, all RHS).
+    int* cnn_idx = nullptr;          // [cap] device
+    int* cnn_zmapc = nullptr;        // [cap] device
+    int* cnn_idx_host = nullptr;     // [cap] pinned
+    int* cnn_act_host = nullptr;     // [cap] pinned copy of the outer active flags
+    int cnn_nact = -1;
     std::vector<void*> cnn_arena;    // one activation buffer per convolution of the solver pass
     std::vector<size_t> cnn_arena_bytes;
 };
@@ -362,5 +370,6 @@ int vcycle_apply(helm_ctx* c, float2* u_out, const float2* u0, const float2* f, 
 int cnn_ctx_setup(helm_ctx* c);      // allocate buffers and run the encoder for every frequency
 void cnn_ctx_free(helm_ctx* c);
 int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const int* mask, int with_vcycle);
+int cnn_ctx_compact(helm_ctx* c, int nb);   // list the RHS still running (flags in cnn_act_host)
 
 }  // namespace helm
