@@ -334,6 +334,7 @@ def run_ours(args, rank, world):
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    native.cnn_set_conv_path(args.conv_path)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     sampler = ClockSampler(local)
@@ -365,7 +366,8 @@ def run_ours(args, rank, world):
                 world * prob.nb * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
-                "config": {"workload": f"network_forward_{w.nx}x{w.nz}_{prob.nb}rhs", "widths": list(widths)}}
+                "config": {"workload": f"network_forward_{w.nx}x{w.nz}_{prob.nb}rhs", "widths": list(widths),
+                           "conv_path": args.conv_path}}
         if not args.no_extras:
             native.helm_profile_enable(ctx, True)
             native.cnn_precond_apply(ctx, r, e, prob.nb, prob.fi, 0)
@@ -501,6 +503,9 @@ def main():
                     help="mg workload: sources per frequency (64 = the benchmark workload)")
     ap.add_argument("--sources-cnn", type=int, default=128,
                     help="cnn workload: sources (128 = the benchmark workload; fewer only for profiling runs)")
+    ap.add_argument("--conv-path", type=int, default=0, choices=[0, 1, 2],
+                    help="convolution kernel: 0 TMA halo tiles (default), 1 gather, 2 TMA with the column "
+                         "taps in N for 16-channel layers")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the solve only: no profiled step, end-to-end leg or CPU baseline (profiling runs)")
     args = ap.parse_args()

@@ -270,12 +270,17 @@ int cnn_set_loss(cnn_model* net, int kind);
 int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, int nb, int hin, int win,
                 const float* w, const float* bias, int cout, const float* res, int mode, int relu, float* y);
 
-/* Which kernel runs the same-grid layers (mode 0).  path 0 (default): the
- * TMA halo-tile kernel (the input tile of a CTA staged once, the nine taps read
- * as shifted shared-memory views), falling back to the gather kernel for a layer
- * it cannot take; path 1: the gather kernel for every layer.  Process-wide; for
+/* Which kernel runs the convolutions.  path 0 (default): the TMA halo-tile
+ * kernel (the input tile of a CTA staged once, the nine taps read as shifted
+ * shared-memory views), falling back to the gather kernel for a layer it
+ * cannot take; path 1: the gather kernel for every layer; path 2: as path 0,
+ * but same-grid layers with 16 output channels put the three column taps into
+ * the MMA's N and add them in the epilogue (fewer shared-memory operand reads,
+ * more epilogue work; slower than path 0 on GB300 so far).  Process-wide; for
  * tests and measurements.  Returns HELM_EINVAL for any other value. */
 int cnn_set_conv_path(int path);
+/* Launches of the column-taps-in-N convolution since the library was loaded. */
+long long cnn_conv_narrow_launches(void);
 /* Tile height limit of the TMA halo-tile kernel: at most max_rows output rows per
  * tile (0 = automatic: as many as two 128-column TMEM accumulator buffers and a
  * 47 KB stage allow).  Process-wide; for tuning.  HELM_EINVAL outside [0, 254]. */

@@ -40,7 +40,8 @@ struct ConvArgs {
 };
 
 int launch_conv3x3(const ConvArgs& a, cudaStream_t st);
-// same-grid layers through TMA-staged halo tiles (k_conv_tma.cu); HELM_EINVAL = not launched
-int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st);
+// layers through TMA-staged halo tiles (k_conv_tma.cu); HELM_EINVAL = not launched.
+// narrow: 16-channel same-grid layers take the column-taps-in-N variant.
+int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st, bool narrow);
 
 }  // namespace helm

@@ -293,8 +293,9 @@ int launch_conv3x3(const ConvArgs& a, cudaStream_t st) {
         set_error("conv3x3: bad shape or mode");
         return HELM_EINVAL;
     }
-    if (g_conv_path.load() == 0) {
-        const int t = launch_conv3x3_tma(a, st);
+    const int path = g_conv_path.load();
+    if (path == 0 || path == 2) {
+        const int t = launch_conv3x3_tma(a, st, path == 2);
         if (t == HELM_OK) {
             ++g_launch_tma;
             return HELM_OK;
@@ -319,8 +320,9 @@ int launch_conv3x3(const ConvArgs& a, cudaStream_t st) {
 }  // namespace helm
 
 extern "C" int cnn_set_conv_path(int path) {
-    if (path != 0 && path != 1) {
-        helm::set_error("cnn_set_conv_path: path must be 0 (automatic) or 1 (gather kernel only)");
+    if (path < 0 || path > 2) {
+        helm::set_error("cnn_set_conv_path: path must be 0 (automatic), 1 (gather kernel only) or 2 (TMA "
+                        "kernel with the column-taps-in-N variant)");
         return HELM_EINVAL;
     }
     helm::g_conv_path.store(path);

@@ -22,6 +22,15 @@
 //  3 transpose of mode 1 (the input gradient of a stride-2 layer): fine (2Y+py, 2X+px) takes
 //                                    tap (dy, dx) from coarse (Y + (py-1-dy)/2, X + (px-1-dx)/2)
 //                                    when both are integers; staged as mode 2.
+//  4 (opt-in, cnn_set_conv_path(2)) same grid as mode 0, for 16 output channels, with the three
+//    column taps in N: one MMA per
+//    tap row dy computes D[s][(dx, o)] for N = 48, and the epilogue adds
+//    D[q][(-1, o)] + D[q + 1][(0, o)] + D[q + 2][(1, o)].  The A operand of an M block
+//    takes its 16 core-matrix groups of 8 pixels at a 6-pixel stride (SBO = 96 B), so that
+//    the two neighbours of the first six rows of a group are rows of the same group (same
+//    warp: two shuffles).  Each staged pixel is read by 3 MMAs instead of 9; the rows 6
+//    and 7 of each group are computed and dropped.  Accumulators live in a ring of
+//    per-M-block TMEM slots, so that a tile's size is not bounded by TMEM.
 // Staged rows (tile + halo) are packed end to end into M blocks of 128 pixels;
 // the accumulator rows of the halo columns between rows are discarded (each
 // accumulator row depends only on its own A row).  Activations are in the
@@ -57,6 +66,8 @@ constexpr int EPI_WARPS = 8;                    // two warpgroups drain TMEM (al
 constexpr int EPI = 32 * EPI_WARPS;             // epilogue threads
 constexpr int NT = EPI + 64;                    // + a TMA-producer warp and an MMA-issuer warp
 constexpr int MAX_NS = 6;                       // stages (one 16-channel group of one tile each)
+constexpr int MAX_SLOTS = 4;                    // TMEM accumulator slots of mode 4 (two buffers otherwise)
+constexpr int N3_PX = 96;                       // mode 4: staged pixels per M block (16 groups x 6)
 constexpr long long WAIT_LIMIT = 1ll << 22;     // polls of try_wait before a wait gives up
 // No padding after a plane: the last M block of a packed tile may read up to
 // 2 pitches + 130 pixels past its plane's staged pixels, which lands in the next
@@ -80,6 +91,7 @@ struct Geometry {
     int nplanes;             // parity sub-planes: 1, or 4 in mode 1
     int wbytes;              // bytes of one group's weights (9 taps x 2 chunks x npad rows x 16 B)
     int w4;                  // weights by one 4-D TMA box (1) or 18 2-D boxes (0)
+    int nslot, slot_cols;    // mode 4: TMEM slots (one M block each) and their columns
     int stage;               // bytes of one stage
     int groups, groups0;     // 16-channel groups in total / taken from x0
     int ns;                  // stages in the ring
@@ -138,7 +150,7 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                                                          const __grid_constant__ CUtensorMap tm_w, ConvArgs a,
                                                          Geometry g) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t full[MAX_NS], empty[MAX_NS], tfull[2], tempty[2], done;
+    __shared__ uint64_t full[MAX_NS], empty[MAX_NS], tfull[MAX_SLOTS], tempty[MAX_SLOTS], done;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ float bias_s[128];
@@ -154,9 +166,10 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
             tc::mbar_init(&full[s], 1);     // the producer's expect_tx arrival + the TMA bytes
             tc::mbar_init(&empty[s], 1);    // one tcgen05.commit per use
         }
-        for (int i = 0; i < 2; ++i) {
-            tc::mbar_init(&tfull[i], 1);    // tcgen05.commit after the last MMA of a tile
-            tc::mbar_init(&tempty[i], EPI); // every epilogue thread, after its TMEM loads
+        for (int i = 0; i < MAX_SLOTS; ++i) {
+            tc::mbar_init(&tfull[i], 1);    // tcgen05.commit after the last MMA of a tile (mode 4: M block)
+            // every epilogue thread after its TMEM loads (mode 4: the warpgroup that drains the slot)
+            tc::mbar_init(&tempty[i], MODE == 4 ? EPI / 2 : EPI);
         }
         tc::mbar_init(&done, 1);
         tc::fence_mbar_init();
@@ -217,7 +230,10 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                     }
                 }
                 unsigned char* ws = st + wofs;
-                if (g.w4) {
+                if (MODE == 4) {
+                    // [dy][half][dx][npad][8]: the B operand of tap row dy is 3 npad rows (dx, o)
+                    tc::tma_load_5d(ws, &tm_w, 0, 0, 0, 2 * gi, 0, &full[s]);
+                } else if (g.w4) {
                     tc::tma_load_4d(ws, &tm_w, 0, 0, 2 * gi, 0, &full[s]);
                 } else {
                     for (int tap = 0; tap < 9; ++tap)
@@ -252,51 +268,101 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
         const uint32_t tap_b16 = (2u * wplane) >> 4;   // B planes of one tap, 16-byte units
         long long j = 0;
         bool ok = true;
-        for (int k = 0; k < ntiles && ok; ++k) {
-            const int acc = k & 1;
-            const int ause = k >> 1;
-            // (the lanes agree on every wait's outcome, so that they leave the loop together)
-            const bool t_ok = ause == 0 || wait_bar(&tempty[acc], (uint32_t)((ause - 1) & 1), abort_v, 32);
-            if (!__all_sync(0xffffffffu, t_ok)) { ok = false; break; }
-            tc::tc_fence_after_sync();
-            const uint32_t dbase = tmem + (uint32_t)acc * g.acc_cols;
-            for (int gi = 0; gi < G; ++gi, ++j) {
-                const int s = (int)(j % g.ns);
-                const bool f_ok = wait_bar(&full[s], (uint32_t)((j / g.ns) & 1), abort_v, 32);
-                if (!__all_sync(0xffffffffu, f_ok)) { ok = false; break; }
+        if constexpr (MODE == 4) {
+            // m outer: an M block takes every group of its tile (all G stages resident) and
+            // three MMAs per group (tap rows dy), then commits its TMEM slot
+            const uint32_t idesc4 = tc::idesc_bf16_f32(128, 3 * a.npad);
+            const uint64_t adesc4 = tc::smem_desc(0u, (uint32_t)chunk_bytes, 16 * 6);   // 6-pixel group stride
+            const uint64_t bdesc4 = tc::smem_desc(0u, 3u * wplane, 128);
+            const uint32_t a4_lo = (uint32_t)adesc4, a4_hi = (uint32_t)(adesc4 >> 32);
+            const uint32_t b4_lo = (uint32_t)bdesc4, b4_hi = (uint32_t)(bdesc4 >> 32);
+            const uint32_t row_b16 = (6u * wplane) >> 4;   // B of one tap row (2 halves x 3 dx)
+            long long jb = 0;
+            for (int k = 0; k < ntiles && ok; ++k) {
+                for (int gi = 0; gi < G; ++gi) {
+                    const long long js = j + gi;
+                    const bool f_ok = wait_bar(&full[js % g.ns], (uint32_t)((js / g.ns) & 1), abort_v, 32);
+                    if (!__all_sync(0xffffffffu, f_ok)) { ok = false; break; }
+                }
+                if (!ok) break;
                 tc::tc_fence_after_sync();
-                const uint32_t a16 = (tc::smem_u32(smem + (size_t)s * g.stage) & 0x3FFFFu) >> 4;
-                const uint32_t bw_lo = b_lo0 + a16 + ((uint32_t)wofs >> 4);
-                for (int ph = 0; ph < g.nph; ++ph) {
-                    uint32_t ao[9];   // A start of each tap for M block 0, descriptor low word
-                    bool use[9];
+                for (int m = 0; m < g.mb; ++m, ++jb) {
+                    const int slot = (int)(jb % g.nslot);
+                    const long long use = jb / g.nslot;
+                    const bool t_ok = use == 0 || wait_bar(&tempty[slot], (uint32_t)((use - 1) & 1), abort_v, 32);
+                    if (!__all_sync(0xffffffffu, t_ok)) { ok = false; break; }
+                    tc::tc_fence_after_sync();
+                    const uint32_t d = tmem + (uint32_t)(slot * g.slot_cols);
+                    for (int gi = 0; gi < G; ++gi) {
+                        const int s = (int)((j + gi) % g.ns);
+                        const uint32_t a16 = (tc::smem_u32(smem + (size_t)s * g.stage) & 0x3FFFFu) >> 4;
+                        const uint32_t a_m = a4_lo + a16 + (uint32_t)(m * N3_PX);
+                        const uint32_t b_s = b4_lo + a16 + ((uint32_t)wofs >> 4);
 #pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        int pl, off;   // A offset in 16-byte units from the stage
-                        use[tap] = tap_source<MODE>(tap, ph >> 1, ph & 1, g.pw, &pl, &off);
-                        ao[tap] = a_lo0 + a16 + (uint32_t)(pl * (g.pstride >> 4) + off);
-                    }
-                    uint32_t d = dbase + (uint32_t)(ph * g.mb * a.npad);
-                    for (int m = 0; m < g.mb; ++m, d += (uint32_t)a.npad) {
-                        const uint32_t mo = (uint32_t)(m * 128);   // 128 pixels of 16 bytes
-                        uint32_t accum = gi == 0 ? 0u : 1u;
-#pragma unroll
-                        for (int tap = 0; tap < 9; ++tap) {
-                            if (!use[tap]) continue;
+                        for (int dy = 0; dy < 3; ++dy) {
                             if (leader) {
-                                const uint64_t ad = ((uint64_t)a_hi << 32) | (ao[tap] + mo);
-                                const uint64_t bd = ((uint64_t)b_hi << 32) | (bw_lo + (uint32_t)tap * tap_b16);
-                                tc::mma_bf16(d, ad, bd, idesc, accum);
+                                const uint64_t ad = ((uint64_t)a4_hi << 32) | (a_m + (uint32_t)(dy * g.pw));
+                                const uint64_t bd = ((uint64_t)b4_hi << 32) | (b_s + (uint32_t)dy * row_b16);
+                                tc::mma_bf16(d, ad, bd, idesc4, (gi | dy) ? 1u : 0u);
                             }
-                            accum = 1u;
                         }
                     }
+                    __syncwarp();
+                    if (leader) tc::mma_commit(&tfull[slot]);
+                }
+                if (!ok) break;
+                __syncwarp();
+                if (leader)
+                    for (int gi = 0; gi < G; ++gi) tc::mma_commit(&empty[(j + gi) % g.ns]);
+                j += G;
+            }
+        } else {
+            for (int k = 0; k < ntiles && ok; ++k) {
+                const int acc = k & 1;
+                const int ause = k >> 1;
+                // (the lanes agree on every wait's outcome, so that they leave the loop together)
+                const bool t_ok = ause == 0 || wait_bar(&tempty[acc], (uint32_t)((ause - 1) & 1), abort_v, 32);
+                if (!__all_sync(0xffffffffu, t_ok)) { ok = false; break; }
+                tc::tc_fence_after_sync();
+                const uint32_t dbase = tmem + (uint32_t)acc * g.acc_cols;
+                for (int gi = 0; gi < G; ++gi, ++j) {
+                    const int s = (int)(j % g.ns);
+                    const bool f_ok = wait_bar(&full[s], (uint32_t)((j / g.ns) & 1), abort_v, 32);
+                    if (!__all_sync(0xffffffffu, f_ok)) { ok = false; break; }
+                    tc::tc_fence_after_sync();
+                    const uint32_t a16 = (tc::smem_u32(smem + (size_t)s * g.stage) & 0x3FFFFu) >> 4;
+                    const uint32_t bw_lo = b_lo0 + a16 + ((uint32_t)wofs >> 4);
+                    for (int ph = 0; ph < g.nph; ++ph) {
+                        uint32_t ao[9];   // A start of each tap for M block 0, descriptor low word
+                        bool use[9];
+    #pragma unroll
+                        for (int tap = 0; tap < 9; ++tap) {
+                            int pl, off;   // A offset in 16-byte units from the stage
+                            use[tap] = tap_source<MODE>(tap, ph >> 1, ph & 1, g.pw, &pl, &off);
+                            ao[tap] = a_lo0 + a16 + (uint32_t)(pl * (g.pstride >> 4) + off);
+                        }
+                        uint32_t d = dbase + (uint32_t)(ph * g.mb * a.npad);
+                        for (int m = 0; m < g.mb; ++m, d += (uint32_t)a.npad) {
+                            const uint32_t mo = (uint32_t)(m * 128);   // 128 pixels of 16 bytes
+                            uint32_t accum = gi == 0 ? 0u : 1u;
+    #pragma unroll
+                            for (int tap = 0; tap < 9; ++tap) {
+                                if (!use[tap]) continue;
+                                if (leader) {
+                                    const uint64_t ad = ((uint64_t)a_hi << 32) | (ao[tap] + mo);
+                                    const uint64_t bd = ((uint64_t)b_hi << 32) | (bw_lo + (uint32_t)tap * tap_b16);
+                                    tc::mma_bf16(d, ad, bd, idesc, accum);
+                                }
+                                accum = 1u;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    if (leader) tc::mma_commit(&empty[s]);
                 }
                 __syncwarp();
-                if (leader) tc::mma_commit(&empty[s]);
+                if (ok && leader) tc::mma_commit(&tfull[acc]);
             }
-            __syncwarp();
-            if (ok && leader) tc::mma_commit(&tfull[acc]);
         }
         if (!ok) *abort_v = 1;
         __syncwarp();
@@ -318,107 +384,148 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
         const size_t plane_out = (size_t)hw_out * 8;   // elements between 8-channel planes
         const int nblk = g.nph * g.mb;
         const int step_y = 256 / g.pw, step_x = 256 - step_y * g.pw;
-        for (int k = 0; k < ntiles; ++k) {
-            const int acc = k & 1;
-            if (!wait_bar(&tfull[acc], (uint32_t)((k >> 1) & 1), abort_v, 128)) { *abort_v = 1; break; }
-            tc::tc_fence_after_sync();
-            int b, xs, ys;
-            tile_coords(k, b, xs, ys);
-            const uint32_t dbase = lane_base + (uint32_t)acc * g.acc_cols;
-            const size_t img_base = (size_t)b * (size_t)(a.npad >> 3) * (size_t)hw_out * 8;
-            // one 16-channel segment of this thread's pixel: bias, residual, ReLU, store
-            auto segment = [&](float* vv, int n0, size_t ob, long long p) {
+        // one 16-channel segment of this thread's pixel: bias, residual, ReLU, store
+        auto segment = [&](float* vv, int n0, size_t ob, long long p) {
 #pragma unroll
-                for (int i = 0; i < 16; i += 4) {
-                    const float4 bb = *reinterpret_cast<const float4*>(bias_s + n0 + i);
-                    vv[i] += bb.x;
-                    vv[i + 1] += bb.y;
-                    vv[i + 2] += bb.z;
-                    vv[i + 3] += bb.w;
-                }
-                const size_t o0 = ob + (size_t)(n0 >> 3) * plane_out;   // planes n0/8 and n0/8 + 1
-                if (a.res) {
-                    uint4 r0 = __ldg(reinterpret_cast<const uint4*>(a.res + o0));
-                    uint4 r1 = __ldg(reinterpret_cast<const uint4*>(a.res + o0 + plane_out));
-                    const __nv_bfloat16* rb0 = reinterpret_cast<const __nv_bfloat16*>(&r0);
-                    const __nv_bfloat16* rb1 = reinterpret_cast<const __nv_bfloat16*>(&r1);
+            for (int i = 0; i < 16; i += 4) {
+                const float4 bb = *reinterpret_cast<const float4*>(bias_s + n0 + i);
+                vv[i] += bb.x;
+                vv[i + 1] += bb.y;
+                vv[i + 2] += bb.z;
+                vv[i + 3] += bb.w;
+            }
+            const size_t o0 = ob + (size_t)(n0 >> 3) * plane_out;   // planes n0/8 and n0/8 + 1
+            if (a.res) {
+                uint4 r0 = __ldg(reinterpret_cast<const uint4*>(a.res + o0));
+                uint4 r1 = __ldg(reinterpret_cast<const uint4*>(a.res + o0 + plane_out));
+                const __nv_bfloat16* rb0 = reinterpret_cast<const __nv_bfloat16*>(&r0);
+                const __nv_bfloat16* rb1 = reinterpret_cast<const __nv_bfloat16*>(&r1);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        vv[i] += __bfloat162float(rb0[i]);
-                        vv[8 + i] += __bfloat162float(rb1[i]);
-                    }
-                }
-                if (a.relu) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) vv[i] = fmaxf(vv[i], 0.0f);
-                }
-                if (a.out_fp32) {
-                    float* yo = reinterpret_cast<float*>(a.y) + (size_t)p * a.cstore;
-                    if (a.accum) {
-                        for (int i = 0; i < 16; ++i)
-                            if (n0 + i < a.cstore) yo[n0 + i] += vv[i];
-                    } else {
-                        for (int i = 0; i < 16; ++i)
-                            if (n0 + i < a.cstore) yo[n0 + i] = vv[i];
-                    }
-                } else {
-                    uint4 w0, w1;
-                    __nv_bfloat16* ob0 = reinterpret_cast<__nv_bfloat16*>(&w0);
-                    __nv_bfloat16* ob1 = reinterpret_cast<__nv_bfloat16*>(&w1);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        ob0[i] = __float2bfloat16_rn(vv[i]);
-                        ob1[i] = __float2bfloat16_rn(vv[8 + i]);
-                    }
-                    __nv_bfloat16* yq = reinterpret_cast<__nv_bfloat16*>(a.y) + o0;
-                    *reinterpret_cast<uint4*>(yq) = w0;
-                    *reinterpret_cast<uint4*>(yq + plane_out) = w1;
-                }
-            };
-            int m_prev = -4, yy = 0, xx = 0;
-            for (int bi = wg; bi < nblk; bi += 2) {
-                const int ph = bi / g.mb, m = bi - ph * g.mb;
-                if (m != m_prev + 2) {
-                    const int q = m * 128 + row;
-                    yy = q / g.pw;
-                    xx = q - yy * g.pw;
-                } else {
-                    // the warpgroup's next block of the same phase lies 256 pixels further on
-                    yy += step_y;
-                    xx += step_x;
-                    if (xx >= g.pw) {
-                        xx -= g.pw;
-                        ++yy;
-                    }
-                }
-                m_prev = m;
-                int oy = ys + yy, ox = xs + xx;
-                if (MODE >= 2) {
-                    oy = 2 * oy + (ph >> 1);
-                    ox = 2 * ox + (ph & 1);
-                }
-                const bool valid = xx < g.tw && yy < g.rows && oy < a.hout && ox < a.wout;
-                const long long pix = (long long)oy * a.wout + ox;
-                const size_t ob = img_base + (size_t)pix * 8;   // channel 0 of this pixel
-                const long long p = (long long)b * hw_out + pix;
-                const uint32_t tcol = dbase + (uint32_t)(bi * a.npad);
-                if (a.npad == 16) {
-                    float v[16];
-                    tc::tmem_ld16(tcol, v);
-                    if (valid) segment(v, 0, ob, p);
-                } else {
-                    for (int c0 = 0; c0 < a.npad; c0 += 32) {
-                        float v[32];
-                        tc::tmem_ld32(tcol + (uint32_t)c0, v);
-                        if (!valid) continue;
-                        segment(v, c0, ob, p);
-                        segment(v + 16, c0 + 16, ob, p);
-                    }
+                for (int i = 0; i < 8; ++i) {
+                    vv[i] += __bfloat162float(rb0[i]);
+                    vv[8 + i] += __bfloat162float(rb1[i]);
                 }
             }
-            // this thread's TMEM reads of the buffer are complete (tcgen05.ld waited)
-            tc::tc_fence_before_sync();
-            tc::mbar_arrive(&tempty[acc]);
+            if (a.relu) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) vv[i] = fmaxf(vv[i], 0.0f);
+            }
+            if (a.out_fp32) {
+                float* yo = reinterpret_cast<float*>(a.y) + (size_t)p * a.cstore;
+                if (a.accum) {
+                    for (int i = 0; i < 16; ++i)
+                        if (n0 + i < a.cstore) yo[n0 + i] += vv[i];
+                } else {
+                    for (int i = 0; i < 16; ++i)
+                        if (n0 + i < a.cstore) yo[n0 + i] = vv[i];
+                }
+            } else {
+                uint4 w0, w1;
+                __nv_bfloat16* ob0 = reinterpret_cast<__nv_bfloat16*>(&w0);
+                __nv_bfloat16* ob1 = reinterpret_cast<__nv_bfloat16*>(&w1);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    ob0[i] = __float2bfloat16_rn(vv[i]);
+                    ob1[i] = __float2bfloat16_rn(vv[8 + i]);
+                }
+                __nv_bfloat16* yq = reinterpret_cast<__nv_bfloat16*>(a.y) + o0;
+                *reinterpret_cast<uint4*>(yq) = w0;
+                *reinterpret_cast<uint4*>(yq + plane_out) = w1;
+            }
+        };
+        if constexpr (MODE == 4) {
+            // warpgroup wg drains the slots of parity wg (the slot count is even); row
+            // (group gr, row i) of an M block is staged pixel 96 m + 6 gr + i
+            const int gr = row >> 3, i8 = row & 7;
+            long long jb = 0;
+            bool ok = true;
+            for (int k = 0; k < ntiles && ok; ++k) {
+                int b, xs, ys;
+                tile_coords(k, b, xs, ys);
+                const size_t img_base = (size_t)b * (size_t)(a.npad >> 3) * (size_t)hw_out * 8;
+                for (int m = 0; m < g.mb; ++m, ++jb) {
+                    const int slot = (int)(jb % g.nslot);
+                    if ((slot & 1) != wg) continue;
+                    if (!wait_bar(&tfull[slot], (uint32_t)((jb / g.nslot) & 1), abort_v, 128)) {
+                        *abort_v = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after_sync();
+                    const int q = m * N3_PX + 6 * gr + i8;
+                    const int yy = q / g.pw, xx = q - yy * g.pw;
+                    const int oy = ys + yy, ox = xs + xx;
+                    const bool valid = i8 < 6 && xx < g.tw && yy < g.rows && oy < a.hout && ox < a.wout;
+                    const long long pix = (long long)oy * a.wout + ox;
+                    const size_t ob = img_base + (size_t)pix * 8;
+                    const long long p = (long long)b * hw_out + pix;
+                    const uint32_t tcol = lane_base + (uint32_t)(slot * g.slot_cols);
+                    float v[16], vn[16], vf[16];   // dx = -1 (this row), 0 (row + 1), +1 (row + 2)
+                    tc::tmem_ld16(tcol, v);
+                    tc::tmem_ld16(tcol + 16u, vn);
+                    tc::tmem_ld16(tcol + 32u, vf);
+                    tc::tc_fence_before_sync();
+                    tc::mbar_arrive(&tempty[slot]);   // the slot's TMEM reads are done
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        v[c] += __shfl_down_sync(0xffffffffu, vn[c], 1) + __shfl_down_sync(0xffffffffu, vf[c], 2);
+                    if (valid) segment(v, 0, ob, p);
+                }
+            }
+        } else {
+            for (int k = 0; k < ntiles; ++k) {
+                const int acc = k & 1;
+                if (!wait_bar(&tfull[acc], (uint32_t)((k >> 1) & 1), abort_v, 128)) { *abort_v = 1; break; }
+                tc::tc_fence_after_sync();
+                int b, xs, ys;
+                tile_coords(k, b, xs, ys);
+                const uint32_t dbase = lane_base + (uint32_t)acc * g.acc_cols;
+                const size_t img_base = (size_t)b * (size_t)(a.npad >> 3) * (size_t)hw_out * 8;
+                int m_prev = -4, yy = 0, xx = 0;
+                for (int bi = wg; bi < nblk; bi += 2) {
+                    const int ph = bi / g.mb, m = bi - ph * g.mb;
+                    if (m != m_prev + 2) {
+                        const int q = m * 128 + row;
+                        yy = q / g.pw;
+                        xx = q - yy * g.pw;
+                    } else {
+                        // the warpgroup's next block of the same phase lies 256 pixels further on
+                        yy += step_y;
+                        xx += step_x;
+                        if (xx >= g.pw) {
+                            xx -= g.pw;
+                            ++yy;
+                        }
+                    }
+                    m_prev = m;
+                    int oy = ys + yy, ox = xs + xx;
+                    if (MODE >= 2) {
+                        oy = 2 * oy + (ph >> 1);
+                        ox = 2 * ox + (ph & 1);
+                    }
+                    const bool valid = xx < g.tw && yy < g.rows && oy < a.hout && ox < a.wout;
+                    const long long pix = (long long)oy * a.wout + ox;
+                    const size_t ob = img_base + (size_t)pix * 8;   // channel 0 of this pixel
+                    const long long p = (long long)b * hw_out + pix;
+                    const uint32_t tcol = dbase + (uint32_t)(bi * a.npad);
+                    if (a.npad == 16) {
+                        float v[16];
+                        tc::tmem_ld16(tcol, v);
+                        if (valid) segment(v, 0, ob, p);
+                    } else {
+                        for (int c0 = 0; c0 < a.npad; c0 += 32) {
+                            float v[32];
+                            tc::tmem_ld32(tcol + (uint32_t)c0, v);
+                            if (!valid) continue;
+                            segment(v, c0, ob, p);
+                            segment(v + 16, c0 + 16, ob, p);
+                        }
+                    }
+                }
+                // this thread's TMEM reads of the buffer are complete (tcgen05.ld waited)
+                tc::tc_fence_before_sync();
+                tc::mbar_arrive(&tempty[acc]);
+            }
         }
     }
 
@@ -483,6 +590,19 @@ bool encode_w4(CUtensorMap* m, const void* base, int cin, int npad) {
     return r == CUDA_SUCCESS;
 }
 
+// Mode 4: weights [npad][9][cin] viewed as a 5-D tensor (8 channels, npad rows,
+// 3 column taps, cin/8 chunks, 3 tap rows); box = (8, npad, 3, 2, 3) lands as
+// [dy][half][dx][npad][8], so that the B operand of tap row dy is 3 npad rows.
+bool encode_w5(CUtensorMap* m, const void* base, int cin, int npad) {
+    const cuuint64_t dims[5] = {8u, (cuuint64_t)npad, 3u, (cuuint64_t)(cin / 8), 3u};
+    const cuuint64_t strides[4] = {(cuuint64_t)9 * cin * 2, (cuuint64_t)cin * 2, 16u, (cuuint64_t)3 * cin * 2};
+    const cuuint32_t box[5] = {8u, (cuuint32_t)npad, 3u, 2u, 3u};
+    const cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
+    return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // weights [npad][9 * cin] viewed as 2-D; box = 8 input channels x npad rows.
 bool encode_w(CUtensorMap* m, const void* base, int cin, int npad) {
     const cuuint64_t dims[2] = {(cuuint64_t)9 * cin, (cuuint64_t)npad};
@@ -495,7 +615,8 @@ bool encode_w(CUtensorMap* m, const void* base, int cin, int npad) {
 }
 
 std::atomic<int> g_rows_cap{0};   // tile-height limit set by cnn_set_conv_tiling (0 = automatic)
-std::atomic<int> g_stage_kb{0}, g_ring_kb{0};   // stage / ring budgets set by cnn_set_conv_ring (0 = default)
+std::atomic<int> g_stage_kb{0}, g_ring_kb{0};
+std::atomic<long long> g_launch_narrow{0};   // launches of mode 4   // stage / ring budgets set by cnn_set_conv_ring (0 = default)
 int g_last_launch[6] = {0, 0, 0, 0, 0, 0};   // grid, CTAs per SM, CTAs registers/smem allow, shared memory,
                                              // registers per thread, static shared memory
 
@@ -503,6 +624,53 @@ int g_last_launch[6] = {0, 0, 0, 0, 0, 0};   // grid, CTAs per SM, CTAs register
 Geometry plan(const ConvArgs& a) {
     Geometry g{};
     const int mode = a.mode;
+    if (mode == 4) {
+        // same grid, 16 output channels, column taps in N (see the mode list above)
+        if (a.npad != 16) return Geometry{};
+        const int H = a.hout, W = a.wout;
+        g.groups = (a.c0 + a.c1) / 16;
+        g.groups0 = a.c0 / 16;
+        g.nph = 1;
+        g.nplanes = 1;
+        const int ntx = (W + 125) / 126;
+        g.tw = (W + ntx - 1) / ntx;
+        g.pw = g.tw + 2;
+        g.wbytes = 9 * 2 * a.npad * 16;
+        const size_t stage_budget = g_stage_kb.load() > 0 ? (size_t)g_stage_kb.load() * 1024 : STAGE_BUDGET;
+        const size_t ring_budget = g_ring_kb.load() > 0 ? (size_t)g_ring_kb.load() * 1024 : RING_BUDGET;
+        int rmax = std::min(H, 252);
+        const int cap = g_rows_cap.load();
+        if (cap > 0 && rmax > cap) rmax = cap;
+        // the tallest tile whose stage fits, with a ring that holds every group of a tile
+        // and one more stage (the MMA warp takes all groups of a tile at once)
+        g.rows = 0;
+        for (int rows = rmax; rows >= 1; --rows) {
+            const int plane = (rows + 2) * g.pw * 16;
+            const int pstride = (2 * plane + 127) / 128 * 128;
+            const int stage = pstride + g.wbytes;
+            if ((size_t)stage > stage_budget) continue;
+            int ns = (int)(ring_budget / (size_t)stage);
+            if (ns > MAX_NS) ns = MAX_NS;
+            if (ns < g.groups + 1) continue;
+            g.rows = rows;
+            g.plane = plane;
+            g.pstride = pstride;
+            g.stage = stage;
+            g.ns = ns;
+            break;
+        }
+        if (g.rows < 1) return Geometry{};
+        g.mb = (g.rows * g.pw + N3_PX - 1) / N3_PX;
+        g.slot_cols = 64;            // 48 columns used: (dx, o) for dx = -1, 0, 1
+        g.nslot = MAX_SLOTS;
+        g.tmem_cols = (uint32_t)(g.nslot * g.slot_cols);
+        g.acc_cols = 0;
+        g.tiles_x = (W + g.tw - 1) / g.tw;
+        g.tiles_y = (H + g.rows - 1) / g.rows;
+        g.tx = (uint32_t)(2 * (g.rows + 2) * g.pw * 16 + g.wbytes);
+        g.tiles = g.tiles_x * g.tiles_y * a.nb;
+        return g;
+    }
     // the grid the tile lives on: output grid for modes 0 and 1, coarse input grid for 2 and 3
     const int H = mode >= 2 ? a.hin : a.hout, W = mode >= 2 ? a.win : a.wout;
     g.groups = (a.c0 + a.c1) / 16;
@@ -637,8 +805,9 @@ int launch_mode(const CUtensorMap& tm0, const CUtensorMap& tm1, const CUtensorMa
 
 // Launches the TMA halo-tile kernel; returns HELM_EINVAL (nothing launched) when
 // the layer does not fit it, so that the caller can use the gather kernel.
-int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st) {
+int launch_conv3x3_tma(const ConvArgs& a_in, cudaStream_t st, bool narrow) {
     if (!encode_fn()) return HELM_EINVAL;
+    ConvArgs a = a_in;
     if (a.mode < 0 || a.mode > 3) return HELM_EINVAL;
     if (a.npad != 16 && a.npad % 32) return HELM_EINVAL;   // the epilogue reads 16 or 32k columns
     if (a.mode == 0 && (a.hin != a.hout || a.win != a.wout)) return HELM_EINVAL;
@@ -649,7 +818,16 @@ int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st) {
         return HELM_EINVAL;
     if ((long long)a.nb * (a.mode >= 2 ? (long long)a.hin * a.win : (long long)a.hout * a.wout) > 0x7fffffffLL)
         return HELM_EINVAL;
-    Geometry g = plan(a);
+    Geometry g{};
+    alignas(64) CUtensorMap tmw;
+    if (narrow && a.mode == 0 && a.npad == 16) {
+        // 16 output channels: column taps in N (mode 4) when its plan and weight map exist
+        a.mode = 4;
+        g = plan(a);
+        if (g.tiles <= 0 || (size_t)g.ns * g.stage > 200 * 1024 || !encode_w5(&tmw, a.w, a.c0 + a.c1, a.npad))
+            a.mode = 0;
+    }
+    if (a.mode != 4) g = plan(a);
     if (g.tiles <= 0) return HELM_EINVAL;
     if ((size_t)g.ns * g.stage > 200 * 1024 || g.tmem_cols > 512) return HELM_EINVAL;
     // box extents: modes 0/2/3 (tw + 2) pixels = 2 (tw + 2) elements x (rows + 2); mode 1
@@ -659,7 +837,7 @@ int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st) {
     const int bh = a.mode == 1 ? 2 * (g.rows + 1) : g.rows + 2;
     if ((a.mode == 1 ? bw : 2 * bw) > 256 || bh > 256) return HELM_EINVAL;
     if (a.c0 % 8 || a.c1 % 8) return HELM_EINVAL;
-    alignas(64) CUtensorMap tm0, tm1, tmw;
+    alignas(64) CUtensorMap tm0, tm1;
     if (!encode_act(&tm0, a.x0, a.c0, a.win, a.hin, a.nb, bw, bh, es)) return HELM_EINVAL;
     if (a.c1) {
         const int n1 = a.nb1 > 0 ? a.nb1 : (a.x1_bcast ? 1 : a.nb);
@@ -667,9 +845,12 @@ int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st) {
     } else {
         tm1 = tm0;
     }
-    g.w4 = encode_w4(&tmw, a.w, a.c0 + a.c1, a.npad) ? 1 : 0;
-    if (!g.w4 && !encode_w(&tmw, a.w, a.c0 + a.c1, a.npad)) return HELM_EINVAL;
+    if (a.mode != 4) {
+        g.w4 = encode_w4(&tmw, a.w, a.c0 + a.c1, a.npad) ? 1 : 0;
+        if (!g.w4 && !encode_w(&tmw, a.w, a.c0 + a.c1, a.npad)) return HELM_EINVAL;
+    }
     switch (a.mode) {
+        case 4: ++g_launch_narrow; return launch_mode<4>(tm0, tm1, tmw, a, g, st);
         case 0: return launch_mode<0>(tm0, tm1, tmw, a, g, st);
         case 1: return launch_mode<1>(tm0, tm1, tmw, a, g, st);
         case 2: return launch_mode<2>(tm0, tm1, tmw, a, g, st);
@@ -697,6 +878,8 @@ extern "C" int cnn_set_conv_ring(int stage_kb, int ring_kb) {
     helm::g_ring_kb.store(ring_kb);
     return HELM_OK;
 }
+
+extern "C" long long cnn_conv_narrow_launches(void) { return helm::g_launch_narrow.load(); }
 
 // Launch shape of the last TMA convolution (diagnostics): grid, CTAs per SM,
 // the CTAs per SM that registers and shared memory allow, dynamic

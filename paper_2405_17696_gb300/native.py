@@ -105,6 +105,8 @@ def _load():
     lib.cnn_set_conv_tiling.restype = ip
     lib.cnn_set_conv_ring.argtypes = [ip, ip]
     lib.cnn_set_conv_ring.restype = ip
+    lib.cnn_conv_narrow_launches.argtypes = []
+    lib.cnn_conv_narrow_launches.restype = ctypes.c_longlong
     lib.cnn_conv_last_launch.argtypes = [ctypes.POINTER(ctypes.c_int)]
     lib.cnn_conv_last_launch.restype = None
     lib.cnn_conv_launch_counts.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
@@ -343,13 +345,19 @@ def cnn_set_loss(net, kind: int):
 
 
 def cnn_set_conv_path(path: int):
-    """0: TMA halo-tile kernel for same-grid layers (default); 1: gather kernel for all."""
+    """0: TMA halo-tile kernel (default); 1: gather kernel for all layers;
+    2: TMA kernel with the column-taps-in-N variant of the 16-channel layers."""
     _check(lib.cnn_set_conv_path(int(path)), "cnn_set_conv_path")
 
 
 def cnn_set_conv_tiling(max_rows: int):
     """Tile-height limit of the TMA conv kernel (0 = automatic)."""
     _check(lib.cnn_set_conv_tiling(int(max_rows)), "cnn_set_conv_tiling")
+
+
+def cnn_conv_narrow_launches() -> int:
+    """Launches of the column-taps-in-N convolution since the library was loaded."""
+    return int(lib.cnn_conv_narrow_launches())
 
 
 def cnn_set_conv_ring(stage_kb: int, ring_kb: int):

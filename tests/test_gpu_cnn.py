@@ -47,9 +47,10 @@ MODES = {"same": 0, "down": 1, "up": 2}
     (64, 0, 0, 64, "same", 37, 40, 1, True, True),       # narrow rows packed into M blocks, ragged rows
     (32, 32, 1, 32, "down", 18, 22, 2, False, True),     # concat in the stride-2 gather path
 ])
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("path", [0, 1, 2])
 def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res, relu, path):
-    """path 0: the TMA halo-tile kernel; path 1: the gather kernel."""
+    """path 0: the TMA halo-tile kernel; path 1: the gather kernel; path 2: the TMA
+    kernel with the column taps in N for 16-channel same-grid layers."""
     g = np.random.default_rng(c0 * 7 + cout + MODES[mode])
     x0 = cnn.bf16_round(g.normal(size=(nb, hin, win, c0)))
     x1 = cnn.bf16_round(g.normal(size=((1 if bcast else nb), hin, win, c1))) if c1 else None
@@ -67,6 +68,7 @@ def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res,
     y = np.zeros((nb, ho, wo, cout), np.float32)
     f32 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32)
     t0, g0 = native.cnn_conv_launch_counts()
+    n0 = native.cnn_conv_narrow_launches()
     native.cnn_set_conv_path(path)
     try:
         native.cnn_conv3x3(f32(x0), c0, f32(x1), c1, bcast, nb, hin, win, f32(w), f32(b), cout, f32(r),
@@ -74,8 +76,10 @@ def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res,
     finally:
         native.cnn_set_conv_path(0)
     t1, g1 = native.cnn_conv_launch_counts()
-    used_tma = path == 0
+    used_tma = path != 1
     assert (t1 - t0, g1 - g0) == ((1, 0) if used_tma else (0, 1))
+    narrow = path == 2 and mode == "same" and cout <= 16
+    assert native.cnn_conv_narrow_launches() - n0 == (1 if narrow else 0)
     err = np.abs(y - ref)
     tol = 2.0 ** -7 * np.abs(ref) + 1e-3 * np.abs(ref).max()
     assert np.all(err <= tol), (err.max(), np.abs(ref).max())
