@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                     for (int ph = 0; ph < g.nph; ++ph) {
                         uint32_t ao[9];   // A start of each tap for M block 0, descriptor low word
                         bool use[9];
-    #pragma unroll
+#pragma unroll
                         for (int tap = 0; tap < 9; ++tap) {
                             int pl, off;   // A offset in 16-byte units from the stage
                             use[tap] = tap_source<MODE>(tap, ph >> 1, ph & 1, g.pw, &pl, &off);
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                         for (int m = 0; m < g.mb; ++m, d += (uint32_t)a.npad) {
                             const uint32_t mo = (uint32_t)(m * 128);   // 128 pixels of 16 bytes
                             uint32_t accum = gi == 0 ? 0u : 1u;
-    #pragma unroll
+#pragma unroll
                             for (int tap = 0; tap < 9; ++tap) {
                                 if (!use[tap]) continue;
                                 if (leader) {
