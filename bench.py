@@ -177,7 +177,8 @@ def config_of(w, workload):
            "medium": "seeded 12-layer model, 1.5-4.5 km/s, smoothed N(0, 0.1) km/s noise, 32-cell absorbing layer",
            "multigrid": "shifted-Laplacian V-cycle (Galerkin, 3 levels, 2+2 damped Jacobi, coarse GMRES(10))",
            "krylov": "FGMRES(10), complex64 vectors, FP64 Hessenberg/Givens/residual, complex128 iterate",
-           "tol": TOL, "parallelism": "independent replicas per GPU"}
+           "tol": TOL, "parallelism": "independent replicas per GPU",
+           "restart_cycles": "CUDA graph replay (MG-FGMRES)"}
     if workload in ("cnn", "net"):
         cfg["precond"] = ("CNN-FGMRES: M_VU(r) = a e0 + V(r - a H e0), a minimising ||r - a H e0||, "
                           "e0 = encoder-solver U-Net (16/32/64/128, BF16)")
@@ -388,6 +389,7 @@ def run_ours(args, rank, world):
         ctx = native.helm_setup(prob.kappa, prob.gamma, w.nx, w.nz, w.h, w.h, prob.omegas,
                                 opts=native.helm_default_opts(mg_levels=3, max_rhs=prob.nb,
                                                               stream=stream.cuda_stream))
+        native.helm_set_graphs(ctx, bool(args.graphs))
         ms, its, relmax, launches, clocks = timed(prob, ctx, args.steps, args.warmup, dev, world, stream, sampler)
         value = timed.solved / (ms / 1e3)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -423,6 +425,7 @@ def run_ours(args, rank, world):
                                 opts=native.helm_default_opts(precond=native.HELM_PC_CNN, **opts))
     ctx_mg = native.helm_setup(prob.kappa, prob.gamma, w.nx, w.nz, w.h, w.h, prob.omegas,
                                opts=native.helm_default_opts(**opts))
+    native.helm_set_graphs(ctx_mg, bool(args.graphs))
     # set-up: Alg. 2 training on this medium (not timed)
     steps_data = sum(128 * 2 ** i // 16 for i in range(3))
     epochs = 3 + max(1, -(-(args.train_steps - steps_data) // 64))
@@ -503,6 +506,8 @@ def main():
                     help="mg workload: sources per frequency (64 = the benchmark workload)")
     ap.add_argument("--sources-cnn", type=int, default=128,
                     help="cnn workload: sources (128 = the benchmark workload; fewer only for profiling runs)")
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="replay the restart cycles of MG-FGMRES from a CUDA graph (1, default) or launch them one by one")
     ap.add_argument("--conv-path", type=int, default=0, choices=[0, 1, 2],
                     help="convolution kernel: 0 TMA halo tiles (default), 1 gather, 2 TMA with the column "
                          "taps in N for 16-channel layers")

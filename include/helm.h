@@ -317,7 +317,17 @@ int helm_profile_read(helm_ctx* ctx, int max, const char** names, double* ms, lo
  * C_out per output pixel of every layer of the network's forward pass). */
 int helm_profile_flops(helm_ctx* ctx, int max, double* flops, int* count);
 
-/* Number of kernels the library has launched in this process (all contexts). */
+/* CUDA graphs for the restart cycles of helm_solve (on by default).  With the
+ * MG preconditioner or none, the second restart cycle of a solve is captured as
+ * a CUDA graph (the k Arnoldi steps with their V-cycles, the update of x, the
+ * true residual and the restart check) and every later cycle replays it with one
+ * launch.  CNN-preconditioned solves and solves under the profiler run their
+ * cycles as single launches; so does a solve whose capture fails.  Results are
+ * the same either way.  HELM_EINVAL for a null context. */
+int helm_set_graphs(helm_ctx* ctx, int on);
+
+/* Number of kernels the library has launched in this process (all contexts;
+ * a graph replay counts the kernels it runs). */
 long long helm_launch_count(void);
 
 /* Thread-local description of the last error on this thread ("" if none). */

@@ -284,6 +284,14 @@ int precondition(helm_ctx* c, float2* z, const float2* v, int nb, const int* mas
     return HELM_EUNSUPPORTED;
 }
 
+// owns the instantiated restart-cycle graph of one solve
+struct GraphGuard {
+    cudaGraphExec_t exec = nullptr;
+    ~GraphGuard() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
 // ---------------------------------------------------------------------------
 // restarted FGMRES for one batch of nb <= cap right-hand sides (device data)
 // ---------------------------------------------------------------------------
@@ -313,7 +321,9 @@ int fgmres_batch(helm_ctx* c, const float2* rhs, double2* x, int nb, double tol,
     HELM_CK(cudaMemcpyAsync(n_active_host, n_active_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     HELM_CK(cudaStreamSynchronize(c->stream));
     OpFine5 H = fine_op(c, 0);
-    while (*n_active_host > 0) {
+    // One restart cycle: k Arnoldi steps, the update of x, the true residual and the
+    // restart check, whose count lands in n_active_host once the stream is synchronised.
+    auto cycle = [&]() -> int {
         HELM_TRY(launch_normalize_v0(c, c->fine, c->V, N, nb));
         for (int j = 0; j < k; ++j) {
             float2* vj = c->V + (size_t)j * vs;
@@ -332,6 +342,63 @@ int fgmres_batch(helm_ctx* c, const float2* rhs, double2* x, int nb, double tol,
         if (compact)
             HELM_CK(cudaMemcpyAsync(c->cnn_act_host, c->outer.outer_active, nb * sizeof(int),
                                     cudaMemcpyDeviceToHost, c->stream));
+        return HELM_OK;
+    };
+    // MG or no preconditioner: the second cycle is captured as a CUDA graph (on a
+    // private stream, so that the caller's stream may be the legacy default stream)
+    // and every later cycle replays it; the network's cycles vary with the RHS still
+    // running and the profiler brackets single launches, so those run eagerly.
+    GraphGuard gg;
+    bool use_graph = c->graphs && c->opt.precond != HELM_PC_CNN && !c->prof.on;
+    long long g_delta = 0, k_delta[K_COUNT] = {};
+    for (int ncycle = 0; *n_active_host > 0; ++ncycle) {
+        if (use_graph && ncycle == 1 && !gg.exec) {
+            if (!c->capture_stream &&
+                cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+                (void)cudaGetLastError();
+                c->capture_stream = nullptr;
+            }
+            const long long g0 = g_launches.load();
+            long long k0[K_COUNT];
+            for (int i = 0; i < K_COUNT; ++i) k0[i] = c->prof.launches[i];
+            bool ok = false;
+            if (c->capture_stream) {
+                // the capture stream starts after everything queued so far on the caller's stream
+                cudaStream_t user = c->stream;
+                ok = cudaStreamSynchronize(user) == cudaSuccess &&
+                     cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (ok) {
+                    c->stream = c->capture_stream;
+                    const int st = cycle();
+                    c->stream = user;
+                    cudaGraph_t graph = nullptr;
+                    ok = cudaStreamEndCapture(c->capture_stream, &graph) == cudaSuccess && graph && st == HELM_OK;
+                    if (ok) ok = cudaGraphInstantiate(&gg.exec, graph, 0) == cudaSuccess;
+                    if (graph) cudaGraphDestroy(graph);
+                }
+            }
+            // the captured launches did not run: count them per replay instead
+            g_delta = g_launches.load() - g0;
+            g_launches.fetch_sub(g_delta);
+            for (int i = 0; i < K_COUNT; ++i) {
+                k_delta[i] = c->prof.launches[i] - k0[i];
+                c->prof.launches[i] = k0[i];
+            }
+            if (!ok) {
+                (void)cudaGetLastError();
+                if (gg.exec) cudaGraphExecDestroy(gg.exec);
+                gg.exec = nullptr;
+                use_graph = false;
+                set_error("");
+            }
+        }
+        if (gg.exec) {
+            HELM_CK(cudaGraphLaunch(gg.exec, c->stream));
+            g_launches.fetch_add(g_delta);
+            for (int i = 0; i < K_COUNT; ++i) c->prof.launches[i] += k_delta[i];
+        } else {
+            HELM_TRY(cycle());
+        }
         HELM_CK(cudaStreamSynchronize(c->stream));
         if (compact && *n_active_host > 0) HELM_TRY(cnn_ctx_compact(c, nb));
     }
@@ -423,6 +490,7 @@ void helm_destroy(helm_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     cnn_ctx_free(c);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     for (void* p : c->allocations) cudaFree(p);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     delete c;
@@ -747,6 +815,12 @@ int helm_solve(helm_ctx* c, const helm_c64* rhs, helm_c128* x, int nrhs, const i
     if (result == HELM_ENOCONV) set_error("some right-hand sides did not reach tol within max_iter");
     if (result == HELM_EBREAKDOWN) set_error("breakdown (NaN/Inf) in some right-hand sides");
     return result;
+}
+
+int helm_set_graphs(helm_ctx* c, int on) {
+    if (!c) { set_error("null context"); return HELM_EINVAL; }
+    c->graphs = on != 0;
+    return HELM_OK;
 }
 
 int helm_profile_enable(helm_ctx* c, int on) {

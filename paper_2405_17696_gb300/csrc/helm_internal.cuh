@@ -259,6 +259,10 @@ struct helm_ctx {
     float hx = 0, hz = 0;
     helm_opts opt{};
     cudaStream_t stream = nullptr;
+    // restart cycles of MG-preconditioned (or plain) FGMRES are captured once per solve
+    // as a CUDA graph on capture_stream and replayed on stream (helm_set_graphs)
+    int graphs = 1;
+    cudaStream_t capture_stream = nullptr;
     std::vector<float> omega;       // host copy (rad/s)
     float2* mg = nullptr;           // [nz][nx] {kappa, gamma}
     float* omega_d = nullptr;       // [nfreq] angular frequencies

@@ -103,6 +103,8 @@ def _load():
     lib.cnn_set_conv_path.restype = ip
     lib.cnn_set_conv_tiling.argtypes = [ip]
     lib.cnn_set_conv_tiling.restype = ip
+    lib.helm_set_graphs.argtypes = [vp, ip]
+    lib.helm_set_graphs.restype = ip
     lib.cnn_set_conv_ring.argtypes = [ip, ip]
     lib.cnn_set_conv_ring.restype = ip
     lib.cnn_conv_narrow_launches.argtypes = []
@@ -292,6 +294,11 @@ def helm_profile_flops(ctx) -> dict:
 
 def helm_launch_count() -> int:
     return int(lib.helm_launch_count())
+
+
+def helm_set_graphs(ctx, on: bool):
+    """Capture and replay the restart cycles of MG / plain FGMRES as a CUDA graph (default on)."""
+    _check(lib.helm_set_graphs(ctx, 1 if on else 0), "helm_set_graphs")
 
 
 # --------------------------------------------------------------------------

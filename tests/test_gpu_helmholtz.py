@@ -168,6 +168,34 @@ def test_solve_layered_mixed_frequencies(native, nx, nz):
     _solve_and_check(native, w, fi, rhs, levels=3)
 
 
+def test_graph_replayed_cycles_match_single_launches(native):
+    """The restart cycles replayed from a CUDA graph give the same iterates,
+    iteration counts and residuals as the same cycles launched one by one, and the
+    launch counter counts the kernels the replays run."""
+    w = media.crop_workload(128, 64, freqs=(4.0, 6.0), width=12)
+    rhs = w.rhs()
+    fi = w.freq_index()
+    nb = rhs.shape[0]
+    out = {}
+    for graphs in (False, True):
+        ctx = _ctx(native, w, mg_levels=3, max_iter=800)
+        try:
+            native.helm_set_graphs(ctx, graphs)
+            x = torch.zeros(rhs.shape, dtype=torch.complex128, device="cuda")
+            n0 = native.helm_launch_count()
+            st, iters, rel, stat = native.helm_solve(ctx, torch.from_numpy(rhs).cuda(), x, nb, fi, 1e-6, 0)
+            torch.cuda.synchronize()
+            out[graphs] = (st, iters.copy(), rel.copy(), x.cpu().numpy(), native.helm_launch_count() - n0)
+        finally:
+            native.helm_destroy(ctx)
+    (s0, i0, r0, x0, l0), (s1, i1, r1, x1, l1) = out[False], out[True]
+    assert s0 == s1 == native.HELM_OK
+    assert np.array_equal(i0, i1) and i0.max() > 20   # several restart cycles
+    assert np.array_equal(r0, r1)
+    assert np.array_equal(x0, x1)
+    assert l0 == l1
+
+
 def test_solve_random_rhs_and_adjoint(native):
     w = media.crop_workload(96, 64, freqs=(5.0,), width=10)
     rhs = media.complex_normal((3, w.nz, w.nx), seed=5)
