@@ -287,6 +287,15 @@ def e2e_of(prob, ctx, steps, dev):
     return {"value": solved / sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
 
+def autotune_of(native, ctx, nb, on):
+    """Set-up (untimed): the fastest tiling of every convolution shape, timed on the GPU."""
+    if not on:
+        return None
+    t0 = time.perf_counter()
+    n = native.cnn_autotune(ctx, nb)
+    return {"shapes": n, "seconds": round(time.perf_counter() - t0, 3)}
+
+
 def profile_step(native, prob, ctx):
     native.helm_profile_enable(ctx, True)
     prob.step(ctx)
@@ -351,6 +360,7 @@ def run_ours(args, rank, world):
         ctx = native.helm_setup(prob.kappa, prob.gamma, w.nx, w.nz, w.h, w.h, prob.omegas, net=net,
                                 opts=native.helm_default_opts(mg_levels=3, max_rhs=prob.nb,
                                                               precond=native.HELM_PC_CNN, stream=stream.cuda_stream))
+        tune = autotune_of(native, ctx, prob.nb, args.autotune)
         r = prob.rhs.to(torch.complex64) if prob.rhs.dtype != torch.complex64 else prob.rhs
         e = torch.empty_like(r)
         for _ in range(max(args.warmup, 0)):
@@ -368,7 +378,7 @@ def run_ours(args, rank, world):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
                 "config": {"workload": f"network_forward_{w.nx}x{w.nz}_{prob.nb}rhs", "widths": list(widths),
-                           "conv_path": args.conv_path}}
+                           "conv_path": args.conv_path}, "autotune": tune}
         if not args.no_extras:
             native.helm_profile_enable(ctx, True)
             native.cnn_precond_apply(ctx, r, e, prob.nb, prob.fi, 0)
@@ -426,6 +436,7 @@ def run_ours(args, rank, world):
     ctx_mg = native.helm_setup(prob.kappa, prob.gamma, w.nx, w.nz, w.h, w.h, prob.omegas,
                                opts=native.helm_default_opts(**opts))
     native.helm_set_graphs(ctx_mg, bool(args.graphs))
+    tune = autotune_of(native, ctx_cnn, prob.nb, args.autotune)
     # set-up: Alg. 2 training on this medium (not timed)
     steps_data = sum(128 * 2 ** i // 16 for i in range(3))
     epochs = 3 + max(1, -(-(args.train_steps - steps_data) // 64))
@@ -457,7 +468,7 @@ def run_ours(args, rank, world):
                          "loss": "Eq. 4.2 with each pair weighted by 1 / ||e||^2",
                          "loss_first_epoch": hist.epoch_loss[0] if hist.epoch_loss else None,
                          "loss_last_epoch": hist.epoch_loss[-1] if hist.epoch_loss else None},
-            "gpu_launches": int(launches), "clocks": clocks}
+            "autotune": tune, "gpu_launches": int(launches), "clocks": clocks}
     if not args.no_extras:
         prof, flops = profile_step(native, prob, ctx_cnn)
         line["roofline"] = roofline_of(prof, flops)
@@ -506,6 +517,8 @@ def main():
                     help="mg workload: sources per frequency (64 = the benchmark workload)")
     ap.add_argument("--sources-cnn", type=int, default=128,
                     help="cnn workload: sources (128 = the benchmark workload; fewer only for profiling runs)")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="time the candidate tilings of every convolution shape before the run (set-up, untimed)")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="replay the restart cycles of MG-FGMRES from a CUDA graph (1, default) or launch them one by one")
     ap.add_argument("--conv-path", type=int, default=0, choices=[0, 1, 2],

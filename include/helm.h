@@ -279,6 +279,20 @@ int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, 
  * more epilogue work; slower than path 0 on GB300 so far).  Process-wide; for
  * tests and measurements.  Returns HELM_EINVAL for any other value. */
 int cnn_set_conv_path(int path);
+/* Autotuning of the convolutions' tiling.  Runs the network's solver pass once
+ * on a synthetic residual batch of nrhs RHS (1 <= nrhs <= max_rhs) of the
+ * context's medium.  The first launch of every layer shape times its candidate
+ * tilings and records the fastest: the default stage and ring budgets,
+ * 36/110, 56/112, 100/200 and 47/200 KB, at most 4 rows per tile, and for
+ * 16-channel same-grid layers the column-taps-in-N variant.  Later launches of
+ * that shape, at any batch size and in any context, use it.  The table is
+ * process-wide; explicit cnn_set_conv_tiling / cnn_set_conv_ring values take
+ * precedence.  Layers that accumulate into their output (the backward pass)
+ * keep the defaults.  *n_shapes (may be NULL) receives the number of tuned
+ * shapes.  HELM_EINVAL without a network or for nrhs outside the range. */
+int cnn_autotune(helm_ctx* ctx, int nrhs, int* n_shapes);
+/* Forget every tuned tiling. */
+void cnn_autotune_reset(void);
 /* Launches of the column-taps-in-N convolution since the library was loaded. */
 long long cnn_conv_narrow_launches(void);
 /* Tile height limit of the TMA halo-tile kernel: at most max_rows output rows per

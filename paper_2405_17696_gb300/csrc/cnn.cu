@@ -546,6 +546,25 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
 
 }  // namespace helm
 
+namespace helm {
+namespace {
+
+// Timing input of the autotuner: unit-scale values from a hash of the index.
+__global__ void synth_residual_kernel(float2* __restrict__ r, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const float a = (float)(z & 0xFFFFFFu) * (1.0f / 16777216.0f) - 0.5f;
+        const float b = (float)((z >> 24) & 0xFFFFFFu) * (1.0f / 16777216.0f) - 0.5f;
+        r[i] = make_float2(a, b);
+    }
+}
+
+}  // namespace
+}  // namespace helm
+
 using namespace helm;
 
 extern "C" {
@@ -587,6 +606,39 @@ int cnn_precond_apply(helm_ctx* c, const helm_c64* r, helm_c64* e, int nrhs, con
     return HELM_OK;
 }
 
+
+int cnn_autotune(helm_ctx* c, int nrhs, int* n_shapes) {
+    set_error("");
+    if (!c || !c->net || nrhs < 1 || nrhs > c->cap) {
+        set_error("cnn_autotune: needs a context with a network and 1 <= nrhs <= max_rhs");
+        return HELM_EINVAL;
+    }
+    const long long n = (long long)npts(c) * nrhs;
+    float2 *r = nullptr, *e = nullptr;
+    HELM_CK(cudaMalloc(&r, n * sizeof(float2)));
+    if (cudaMalloc(&e, n * sizeof(float2)) != cudaSuccess) {
+        cudaFree(r);
+        set_error("cnn_autotune: out of device memory");
+        return HELM_ENOMEM;
+    }
+    synth_residual_kernel<<<1184, 256, 0, c->stream>>>(r, n);
+    int s = cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
+    if (!s) {
+        conv_tuning(true);
+        s = cnn_ctx_precondition(c, e, r, nrhs, c->ones, 0);
+        conv_tuning(false);
+    }
+    const cudaError_t ce = cudaStreamSynchronize(c->stream);
+    cudaFree(r);
+    cudaFree(e);
+    if (s) return s;
+    if (ce != cudaSuccess) { set_error(cudaGetErrorString(ce)); return HELM_ECUDA; }
+    HELM_TRY(check_conv_error(c->net, c->stream));
+    if (n_shapes) *n_shapes = conv_tuned_count();
+    return HELM_OK;
+}
+
+void cnn_autotune_reset(void) { conv_tune_reset(); }
 
 int cnn_create(cnn_model** out, int levels, const int* widths) {
     set_error("");

@@ -43,5 +43,11 @@ int launch_conv3x3(const ConvArgs& a, cudaStream_t st);
 // layers through TMA-staged halo tiles (k_conv_tma.cu); HELM_EINVAL = not launched.
 // narrow: 16-channel same-grid layers take the column-taps-in-N variant.
 int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st, bool narrow);
+// Autotuning of the TMA kernel's tiling: while on, the first launch of each layer
+// shape times the candidate tilings and records the fastest, which every later
+// launch of that shape uses (process-wide table).
+void conv_tuning(bool on);
+int conv_tuned_count();
+void conv_tune_reset();
 
 }  // namespace helm

@@ -52,7 +52,11 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdint>
+#include <cstdio>
+#include <map>
 #include <mutex>
+#include <string>
+#include <vector>
 
 #include "helm_internal.cuh"
 #include "conv.cuh"
@@ -615,13 +619,19 @@ bool encode_w(CUtensorMap* m, const void* base, int cin, int npad) {
 }
 
 std::atomic<int> g_rows_cap{0};   // tile-height limit set by cnn_set_conv_tiling (0 = automatic)
+
+// Tiling of one launch: tile-height cap, stage and ring budgets (0 = default), and
+// whether a 16-channel same-grid layer takes the column-taps-in-N variant.
+struct TileCfg {
+    int rows_cap = 0, stage_kb = 0, ring_kb = 0, narrow = 0;
+};
 std::atomic<int> g_stage_kb{0}, g_ring_kb{0};
 std::atomic<long long> g_launch_narrow{0};   // launches of mode 4   // stage / ring budgets set by cnn_set_conv_ring (0 = default)
 int g_last_launch[6] = {0, 0, 0, 0, 0, 0};   // grid, CTAs per SM, CTAs registers/smem allow, shared memory,
                                              // registers per thread, static shared memory
 
 // Tile plan; .tiles = 0 when the layer does not fit this kernel.
-Geometry plan(const ConvArgs& a) {
+Geometry plan(const ConvArgs& a, const TileCfg& t) {
     Geometry g{};
     const int mode = a.mode;
     if (mode == 4) {
@@ -636,10 +646,10 @@ Geometry plan(const ConvArgs& a) {
         g.tw = (W + ntx - 1) / ntx;
         g.pw = g.tw + 2;
         g.wbytes = 9 * 2 * a.npad * 16;
-        const size_t stage_budget = g_stage_kb.load() > 0 ? (size_t)g_stage_kb.load() * 1024 : STAGE_BUDGET;
-        const size_t ring_budget = g_ring_kb.load() > 0 ? (size_t)g_ring_kb.load() * 1024 : RING_BUDGET;
+        const size_t stage_budget = t.stage_kb > 0 ? (size_t)t.stage_kb * 1024 : STAGE_BUDGET;
+        const size_t ring_budget = t.ring_kb > 0 ? (size_t)t.ring_kb * 1024 : RING_BUDGET;
         int rmax = std::min(H, 252);
-        const int cap = g_rows_cap.load();
+        const int cap = t.rows_cap;
         if (cap > 0 && rmax > cap) rmax = cap;
         // the tallest tile whose stage fits, with a ring that holds every group of a tile
         // and one more stage (the MMA warp takes all groups of a tile at once)
@@ -703,7 +713,7 @@ Geometry plan(const ConvArgs& a) {
         g.stage = g.nplanes * g.pstride + g.wbytes;
     };
     int rmax = (maxmb * 128) / g.pw;
-    const int cap = g_rows_cap.load();
+    const int cap = t.rows_cap;
     if (cap > 0 && rmax > cap) rmax = cap;
     if (rmax > H) rmax = H;
     const int box_rows_max = mode == 1 ? 127 : 254;   // staged rows fit a 256-element box
@@ -711,9 +721,9 @@ Geometry plan(const ConvArgs& a) {
     if (rmax < 1) return Geometry{};   // tiles = 0: not this kernel
     int rows = rmax;
     fill(rows);
-    const size_t stage_budget = g_stage_kb.load() > 0 ? (size_t)g_stage_kb.load() * 1024
+    const size_t stage_budget = t.stage_kb > 0 ? (size_t)t.stage_kb * 1024
                                 : (mode == 1 ? STAGE_BUDGET_S2 : STAGE_BUDGET);
-    const size_t ring_budget = g_ring_kb.load() > 0 ? (size_t)g_ring_kb.load() * 1024
+    const size_t ring_budget = t.ring_kb > 0 ? (size_t)t.ring_kb * 1024
                                : (mode == 1 ? RING_BUDGET_S2 : RING_BUDGET);
     while (rows > 1 && (size_t)g.stage > stage_budget) fill(--rows);
     if (g.mb < 1 || g.mb > maxmb) return Geometry{};
@@ -805,10 +815,12 @@ int launch_mode(const CUtensorMap& tm0, const CUtensorMap& tm1, const CUtensorMa
 
 // Launches the TMA halo-tile kernel; returns HELM_EINVAL (nothing launched) when
 // the layer does not fit it, so that the caller can use the gather kernel.
-int launch_conv3x3_tma(const ConvArgs& a_in, cudaStream_t st, bool narrow) {
-    if (!encode_fn()) return HELM_EINVAL;
+namespace {
+
+// One launch of the TMA kernel with tiling t; HELM_EINVAL when the layer does not fit it.
+int launch_cfg(const ConvArgs& a_in, cudaStream_t st, const TileCfg& t) {
     ConvArgs a = a_in;
-    if (a.mode < 0 || a.mode > 3) return HELM_EINVAL;
+    const bool narrow = t.narrow != 0;
     if (a.npad != 16 && a.npad % 32) return HELM_EINVAL;   // the epilogue reads 16 or 32k columns
     if (a.mode == 0 && (a.hin != a.hout || a.win != a.wout)) return HELM_EINVAL;
     if (a.mode == 1 && (a.hin != 2 * a.hout || a.win != 2 * a.wout)) return HELM_EINVAL;
@@ -823,11 +835,11 @@ int launch_conv3x3_tma(const ConvArgs& a_in, cudaStream_t st, bool narrow) {
     if (narrow && a.mode == 0 && a.npad == 16) {
         // 16 output channels: column taps in N (mode 4) when its plan and weight map exist
         a.mode = 4;
-        g = plan(a);
+        g = plan(a, t);
         if (g.tiles <= 0 || (size_t)g.ns * g.stage > 200 * 1024 || !encode_w5(&tmw, a.w, a.c0 + a.c1, a.npad))
             a.mode = 0;
     }
-    if (a.mode != 4) g = plan(a);
+    if (a.mode != 4) g = plan(a, t);
     if (g.tiles <= 0) return HELM_EINVAL;
     if ((size_t)g.ns * g.stage > 200 * 1024 || g.tmem_cols > 512) return HELM_EINVAL;
     // box extents: modes 0/2/3 (tw + 2) pixels = 2 (tw + 2) elements x (rows + 2); mode 1
@@ -856,6 +868,119 @@ int launch_conv3x3_tma(const ConvArgs& a_in, cudaStream_t st, bool narrow) {
         case 2: return launch_mode<2>(tm0, tm1, tmw, a, g, st);
         default: return launch_mode<3>(tm0, tm1, tmw, a, g, st);
     }
+}
+
+// Autotuning: the tiling that ran a layer shape fastest, by shape (batch size left out,
+// so that the active-RHS batches of a solve find the entry of the full batch).
+std::mutex g_tune_mu;
+std::map<std::string, TileCfg> g_tuned;
+std::atomic<int> g_tuning{0};
+
+std::string shape_key(const ConvArgs& a) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d", a.mode, a.c0, a.c1, a.x1_bcast,
+                  a.x1_map ? 1 : 0, a.hin, a.win, a.npad, a.res ? 1 : 0, a.out_fp32, a.accum, a.relu);
+    return buf;
+}
+
+// Runs the candidate tilings of a layer twice each (the second timed with CUDA events),
+// keeps the fastest and launches it once more, so that y holds its result.  Only
+// layers whose output aliases none of their inputs and that do not accumulate are
+// re-run (the caller checks).
+int tune_and_launch(const ConvArgs& a, cudaStream_t st, const std::string& key, const TileCfg& base) {
+    std::vector<TileCfg> cands;
+    cands.push_back(base);
+    const int budgets[][2] = {{36, 110}, {56, 112}, {100, 200}, {47, 200}};
+    for (const auto& b : budgets) {
+        TileCfg c = base;
+        c.stage_kb = b[0];
+        c.ring_kb = b[1];
+        c.narrow = 0;
+        cands.push_back(c);
+    }
+    {
+        TileCfg c = base;
+        c.rows_cap = 4;
+        c.narrow = 0;
+        cands.push_back(c);
+    }
+    if (a.mode == 0 && a.npad == 16) {
+        TileCfg c = base;
+        c.narrow = !base.narrow;
+        cands.push_back(c);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        (void)cudaGetLastError();
+        return launch_cfg(a, st, base);
+    }
+    TileCfg best = base;
+    float best_ms = 1e30f;
+    int s = HELM_OK;
+    for (const TileCfg& c : cands) {
+        s = launch_cfg(a, st, c);
+        if (s == HELM_EINVAL) { s = HELM_OK; continue; }   // this tiling does not fit the layer
+        if (s != HELM_OK) break;
+        cudaEventRecord(e0, st);
+        s = launch_cfg(a, st, c);
+        cudaEventRecord(e1, st);
+        if (s != HELM_OK) break;
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            s = HELM_ECUDA;
+            break;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != HELM_OK) return s;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = best;
+    }
+    return launch_cfg(a, st, best);
+}
+
+}  // namespace
+
+int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st, bool narrow) {
+    if (!encode_fn()) return HELM_EINVAL;
+    if (a.mode < 0 || a.mode > 3) return HELM_EINVAL;
+    TileCfg t;
+    t.rows_cap = g_rows_cap.load();
+    t.stage_kb = g_stage_kb.load();
+    t.ring_kb = g_ring_kb.load();
+    t.narrow = narrow ? 1 : 0;
+    // explicit tiling knobs take precedence over the tuned table
+    if (t.rows_cap || t.stage_kb || t.ring_kb) return launch_cfg(a, st, t);
+    const std::string key = shape_key(a);
+    bool tune = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end())
+            t = it->second;
+        else   // a layer is re-run while tuning only if that leaves its result unchanged
+            tune = g_tuning.load() && !a.accum && a.y != a.x0 && a.y != a.x1 && a.y != a.res;
+    }
+    return tune ? tune_and_launch(a, st, key, t) : launch_cfg(a, st, t);
+}
+
+void conv_tuning(bool on) { g_tuning.store(on ? 1 : 0); }
+
+int conv_tuned_count() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return (int)g_tuned.size();
+}
+
+void conv_tune_reset() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
 }
 
 }  // namespace helm

@@ -103,6 +103,10 @@ def _load():
     lib.cnn_set_conv_path.restype = ip
     lib.cnn_set_conv_tiling.argtypes = [ip]
     lib.cnn_set_conv_tiling.restype = ip
+    lib.cnn_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
+    lib.cnn_autotune.restype = ip
+    lib.cnn_autotune_reset.argtypes = []
+    lib.cnn_autotune_reset.restype = None
     lib.helm_set_graphs.argtypes = [vp, ip]
     lib.helm_set_graphs.restype = ip
     lib.cnn_set_conv_ring.argtypes = [ip, ip]
@@ -360,6 +364,18 @@ def cnn_set_conv_path(path: int):
 def cnn_set_conv_tiling(max_rows: int):
     """Tile-height limit of the TMA conv kernel (0 = automatic)."""
     _check(lib.cnn_set_conv_tiling(int(max_rows)), "cnn_set_conv_tiling")
+
+
+def cnn_autotune(ctx, nrhs: int) -> int:
+    """Time the candidate tilings of every layer shape of the solver pass; returns the tuned shapes."""
+    n = ctypes.c_int(0)
+    _check(lib.cnn_autotune(ctx, int(nrhs), ctypes.byref(n)), "cnn_autotune")
+    return int(n.value)
+
+
+def cnn_autotune_reset():
+    """Forget every tuned convolution tiling."""
+    lib.cnn_autotune_reset()
 
 
 def cnn_conv_narrow_launches() -> int:

@@ -219,3 +219,37 @@ def test_init_params_he_normal(native):
         # sample std within 5 standard errors of the target
         assert abs(wts.std() / sd - 1) < 5 / np.sqrt(2 * nw) + 1e-3, (name, wts.std(), sd)
         assert abs(wts.mean()) < 5 * sd / np.sqrt(nw), name
+
+
+def test_autotune_keeps_the_network_output(native):
+    """cnn_autotune times the candidate tilings of each layer shape and keeps the
+    fastest; the network's output stays the oracle's (same tolerance as the
+    forward parity test) and agrees with the untuned pass."""
+    from paper_2405_17696_gb300 import media
+    w = media.crop_workload(128, 64, freqs=(5.0,), width=12)
+    net, ctx, specs, theta = _net_ctx(native, w, mg_levels=3)
+    native.cnn_autotune_reset()
+    try:
+        nb = 4
+        fi = np.zeros(nb, np.int32)
+        r = media.complex_normal((nb, w.nz, w.nx), seed=21) * 1e-3
+        e0 = np.zeros_like(r)
+        native.cnn_precond_apply(ctx, r, e0, nb, fi, 0)
+        n = native.cnn_autotune(ctx, nb)
+        e1 = np.zeros_like(r)
+        native.cnn_precond_apply(ctx, r, e1, nb, fi, 0)
+    finally:
+        native.cnn_autotune_reset()
+        native.helm_destroy(ctx)
+        native.cnn_destroy(net)
+    assert n >= 8   # distinct layer shapes of the solver pass
+    assert np.linalg.norm(e1 - e0) <= 2e-2 * np.linalg.norm(e0)
+    P = cnn.unflatten(cnn.bf16_round(theta), specs)
+    kap, gam = w.kappa.astype(np.float64), w.gamma.astype(np.float64)
+    om = float(np.float32(w.omegas[0]))
+    enc = cnn.bf16_round(cnn.encoder_input(kap, gam, om, w.h))
+    for b in range(nb):
+        x, rms = cnn.solver_input(r[b], gam)
+        out, _ = cnn.network_forward(P, specs, enc, cnn.bf16_round(x), quantize=cnn.bf16_round)
+        ref = cnn.solver_output_to_error(out, rms, w.h)[0]
+        assert np.linalg.norm(e1[b] - ref) <= 2e-2 * np.linalg.norm(ref)
