@@ -60,39 +60,89 @@ __global__ void jacobi_kernel(Op op, float2* __restrict__ u_out, const float2* _
     u_out[(size_t)b * N + p] = make_float2(u0.x + w * q.x, u0.y + w * q.y);
 }
 
-// rc(J, I) = sum_{a,b} w_a w_b / 16 (f - A u)(2J+1+a, 2I+1+b)   (u == nullptr: u = 0)
+// rc(J, I) = sum_{a,b} w_a w_b / 16 (f - A u)(2J+1+a, 2I+1+b)   (u == nullptr: u = 0),
+// full weighting with each fine residual computed once: a block of 32 x 8 coarse
+// nodes first writes f - A u on its 65 x 17 fine window (the nodes 2J .. 2J+2,
+// 2I .. 2I+2 of its coarse nodes; zero outside the grid) to shared memory, then
+// weights it.
 template <class Op>
-__global__ void restrict_residual_kernel(Op op, float2* __restrict__ rc, const float2* __restrict__ u,
-                                         const float2* __restrict__ f, int nx, int nz, const int* mask,
-                                         Tally tl) {
+__global__ void __launch_bounds__(256) restrict_residual_tiled_kernel(Op op, float2* __restrict__ rc,
+                                                                      const float2* __restrict__ u,
+                                                                      const float2* __restrict__ f, int nx, int nz,
+                                                                      const int* mask, Tally tl) {
+    constexpr int TX = 32, TY = 8, WX = 2 * TX + 1, WY = 2 * TY + 1;
+    __shared__ float2 rs[WY][WX + 1];
     const int b = blockIdx.z;
     if (!mask[b]) return;
     tally_once(tl, blockIdx.x == 0 && blockIdx.y == 0);
     const int nxc = nx / 2, nzc = nz / 2;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    const int J = blockIdx.y * blockDim.y + threadIdx.y;
-    if (I >= nxc || J >= nzc) return;
+    const int I0 = blockIdx.x * TX, J0 = blockIdx.y * TY;
     const size_t N = (size_t)nx * nz;
     const float2* fb = f + (size_t)b * N;
     const float2* ub = u ? u + (size_t)b * N : nullptr;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    for (int t = tid; t < WX * WY; t += TX * TY) {
+        const int lz = t / WX, lx = t - lz * WX;
+        const int iz = 2 * J0 + lz, ix = 2 * I0 + lx;
+        float2 r = make_float2(0.f, 0.f);
+        if (iz < nz && ix < nx) {
+            r = fb[(size_t)iz * nx + ix];
+            if (ub) r = csub(r, op.apply(ub, b, ix, iz));
+        }
+        rs[lz][lx] = r;
+    }
+    __syncthreads();
+    const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
+    if (I >= nxc || J >= nzc) return;
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int a = -1; a <= 1; ++a) {
-        int iz = 2 * J + 1 + a;
-        if (iz < 0 || iz >= nz) continue;
-        float wa = (a == 0) ? 2.f : 1.f;
+    for (int a = 0; a < 3; ++a) {
+        const float wa = a == 1 ? 2.f : 1.f;
 #pragma unroll
-        for (int c = -1; c <= 1; ++c) {
-            int ix = 2 * I + 1 + c;
-            if (ix < 0 || ix >= nx) continue;
-            float wt = wa * ((c == 0) ? 2.f : 1.f) * (1.0f / 16.0f);
-            float2 r = fb[(size_t)iz * nx + ix];
-            if (ub) r = csub(r, op.apply(ub, b, ix, iz));
+        for (int c = 0; c < 3; ++c) {
+            const float wt = wa * (c == 1 ? 2.f : 1.f) * (1.0f / 16.0f);
+            const float2 r = rs[2 * threadIdx.y + a][2 * threadIdx.x + c];
             acc.x += wt * r.x;
             acc.y += wt * r.y;
         }
     }
     rc[(size_t)b * nxc * nzc + (size_t)J * nxc + I] = acc;
+}
+
+// u += bilinear interpolation of ec for the fine node pair (iz, 2k), (iz, 2k+1) of each
+// thread (16-byte access to u; nx even): the odd node takes coarse column k, the even
+// node the mean of columns k-1 and k; an odd row takes coarse row (iz-1)/2, an even
+// row the mean of rows iz/2 - 1 and iz/2.
+__global__ void prolong_add2_kernel(float2* __restrict__ u, const float2* __restrict__ ec, int nx, int nz,
+                                    const int* mask, Tally tl) {
+    const int b = blockIdx.z;
+    if (!mask[b]) return;
+    tally_once(tl, blockIdx.x == 0 && blockIdx.y == 0);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iz = blockIdx.y * blockDim.y + threadIdx.y;
+    const int nxc = nx / 2, nzc = nz / 2;
+    if (2 * k >= nx || iz >= nz) return;
+    const float2* eb = ec + (size_t)b * nxc * nzc;
+    int jz0, jz1;
+    float wz0, wz1;
+    if (iz & 1) { jz0 = (iz - 1) >> 1; wz0 = 1.f; jz1 = -1; wz1 = 0.f; }
+    else { jz0 = (iz >> 1) - 1; wz0 = 0.5f; jz1 = iz >> 1; wz1 = 0.5f; }
+    float2 em = make_float2(0.f, 0.f), e0 = make_float2(0.f, 0.f);   // columns k-1 and k, rows weighted
+    auto row = [&](int jz, float wz) {
+        if (jz < 0 || jz >= nzc || wz == 0.f) return;
+        const float2* er = eb + (size_t)jz * nxc;
+        if (k < nxc) { const float2 v = er[k]; e0.x += wz * v.x; e0.y += wz * v.y; }
+        if (k >= 1) { const float2 v = er[k - 1]; em.x += wz * v.x; em.y += wz * v.y; }
+    };
+    row(jz0, wz0);
+    row(jz1, wz1);
+    float4* up = reinterpret_cast<float4*>(u + (size_t)b * nx * nz + (size_t)iz * nx + 2 * k);
+    float4 v = *up;
+    v.x += 0.5f * (em.x + e0.x);
+    v.y += 0.5f * (em.y + e0.y);
+    v.z += e0.x;
+    v.w += e0.y;
+    *up = v;
 }
 
 // u += bilinear interpolation of ec (coarse node (J, I) on fine node (2J+1, 2I+1)).
@@ -226,7 +276,7 @@ template <class Op>
 int launch_restrict_residual(const helm_ctx* c, const Op& op, float2* rc, const float2* u, const float2* f,
                              int nx, int nz, int nb, const int* mask) {
     LaunchScope scope(c, (std::is_same<Op, OpFine5>::value ? K_RESTRICT_FINE : K_RESTRICT_COARSE));
-    restrict_residual_kernel<Op><<<grid2(nx / 2, nz / 2, nb), dim3(32, 8), 0, c->stream>>>(
+    restrict_residual_tiled_kernel<Op><<<grid2(nx / 2, nz / 2, nb), dim3(32, 8), 0, c->stream>>>(
         op, rc, u, f, nx, nz, mask,
         tally(c, std::is_same<Op, OpFine5>::value ? K_RESTRICT_FINE : K_RESTRICT_COARSE,
               (u ? 16ull : 8ull) * nx * nz + 2ull * nx * nz));
@@ -240,6 +290,12 @@ template int launch_restrict_residual<OpC9>(const helm_ctx*, const OpC9&, float2
 
 int launch_prolong_add(const helm_ctx* c, float2* u, const float2* ec, int nx, int nz, int nb, const int* mask) {
     LaunchScope scope(c, K_PROLONG);
+    if (nx % 2 == 0) {
+        prolong_add2_kernel<<<grid2(nx / 2, nz, nb), dim3(32, 8), 0, c->stream>>>(
+            u, ec, nx, nz, mask, tally(c, K_PROLONG, 18ull * nx * nz));
+        HELM_CK(cudaGetLastError());
+        return HELM_OK;
+    }
     prolong_add_kernel<<<grid2(nx, nz, nb), dim3(32, 8), 0, c->stream>>>(u, ec, nx, nz, mask,
                                                                           tally(c, K_PROLONG, 18ull * nx * nz));
     HELM_CK(cudaGetLastError());
