@@ -298,12 +298,32 @@ __device__ __forceinline__ float2 net_alpha(const double* acc, const int* guard,
     return tt > 0.0 ? make_float2((float)(tr / tt), (float)(acc[3 * b + 1] / tt)) : make_float2(0.f, 0.f);
 }
 
-// out = r - a_b H e0
-// grid (x tiles of 32, z rows / 8, nb), block (32, 8)
+// out = r - a_b H e0 on node pairs (ix, ix + 1), ix even (16-byte access; nx even);
+// RHS with a zero mask entry are skipped.  grid (x tiles of 32 pairs, z rows / 8, nb), block (32, 8)
+__global__ void net_scaled_residual2_kernel(OpFine5 op, const float2* __restrict__ r, const float2* __restrict__ e0,
+                                            float2* __restrict__ out, const double* __restrict__ acc,
+                                            const int* guard, const int* mask) {
+    const int b = blockIdx.z;
+    if (mask && !mask[b]) return;
+    const int ix = 2 * (blockIdx.x * blockDim.x + threadIdx.x), iz = blockIdx.y * blockDim.y + threadIdx.y;
+    if (ix >= op.nx || iz >= op.nz) return;
+    const long long n = (long long)op.nx * op.nz;
+    const long long i = (long long)b * n + (long long)iz * op.nx + ix;
+    float2 h0, h1;
+    op.apply2(e0 + (long long)b * n, b, ix, iz, h0, h1);
+    const float2 al = net_alpha(acc, guard, b);
+    const float4 rv = *reinterpret_cast<const float4*>(r + i);
+    *reinterpret_cast<float4*>(out + i) =
+        make_float4(rv.x - (al.x * h0.x - al.y * h0.y), rv.y - (al.x * h0.y + al.y * h0.x),
+                    rv.z - (al.x * h1.x - al.y * h1.y), rv.w - (al.x * h1.y + al.y * h1.x));
+}
+
+// out = r - a_b H e0 (any nx); grid (x tiles of 32, z rows / 8, nb), block (32, 8)
 __global__ void net_scaled_residual_kernel(OpFine5 op, const float2* __restrict__ r, const float2* __restrict__ e0,
                                            float2* __restrict__ out, const double* __restrict__ acc,
-                                           const int* guard) {
+                                           const int* guard, const int* mask) {
     const int b = blockIdx.z;
+    if (mask && !mask[b]) return;
     const int ix = blockIdx.x * blockDim.x + threadIdx.x, iz = blockIdx.y * blockDim.y + threadIdx.y;
     if (ix >= op.nx || iz >= op.nz) return;
     const long long n = (long long)op.nx * op.nz;
@@ -313,17 +333,20 @@ __global__ void net_scaled_residual_kernel(OpFine5 op, const float2* __restrict_
     out[i] = make_float2(r[i].x - (al.x * he.x - al.y * he.y), r[i].y - (al.x * he.y + al.y * he.x));
 }
 
-// z += a_b e0; grid (slices, nb)
+// z += a_b e0 on node pairs (n even); RHS with a zero mask entry are skipped; grid (slices, nb)
 __global__ void add_scaled_kernel(float2* __restrict__ z, const float2* __restrict__ e0, long long n,
-                                  const double* __restrict__ acc, const int* guard) {
+                                  const double* __restrict__ acc, const int* guard, const int* mask) {
     const int b = blockIdx.y;
+    if (mask && !mask[b]) return;
     const float2 al = net_alpha(acc, guard, b);
-    float2* zb = z + (long long)b * n;
-    const float2* eb = e0 + (long long)b * n;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        const float2 e = eb[p];
-        const float2 v = zb[p];
-        zb[p] = make_float2(v.x + al.x * e.x - al.y * e.y, v.y + al.x * e.y + al.y * e.x);
+    float4* zb = reinterpret_cast<float4*>(z + (long long)b * n);
+    const float4* eb = reinterpret_cast<const float4*>(e0 + (long long)b * n);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n / 2;
+         p += (long long)gridDim.x * blockDim.x) {
+        const float4 e = eb[p];
+        const float4 v = zb[p];
+        zb[p] = make_float4(v.x + al.x * e.x - al.y * e.y, v.y + al.x * e.y + al.y * e.x,
+                            v.z + al.x * e.z - al.y * e.w, v.w + al.x * e.w + al.y * e.z);
     }
 }
 
@@ -525,8 +548,12 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
         LaunchScope scope(c, K_CNN_IO);
         HELM_CK(cudaMemsetAsync(acc, 0, (size_t)3 * nb * sizeof(double), c->stream));
         net_scale_dots_kernel<<<dim3(64, nb), 256, 0, c->stream>>>(fine_op(c, 0), v, c->cnn_e0, mask, guard, acc);
-        net_scaled_residual_kernel<<<dim3((c->nx + 31) / 32, (c->nz + 7) / 8, nb), dim3(32, 8), 0, c->stream>>>(
-            fine_op(c, 0), v, c->cnn_e0, rr, acc, guard);
+        if (c->nx % 2 == 0)
+            net_scaled_residual2_kernel<<<dim3((c->nx / 2 + 31) / 32, (c->nz + 7) / 8, nb), dim3(32, 8), 0,
+                                          c->stream>>>(fine_op(c, 0), v, c->cnn_e0, rr, acc, guard, mask);
+        else
+            net_scaled_residual_kernel<<<dim3((c->nx + 31) / 32, (c->nz + 7) / 8, nb), dim3(32, 8), 0, c->stream>>>(
+                fine_op(c, 0), v, c->cnn_e0, rr, acc, guard, mask);
         HELM_CK(cudaGetLastError());
     } else {
         // e_0 + V(r - H e_0): the V-cycle corrects what the network leaves of H e = r
@@ -537,7 +564,7 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
     HELM_TRY(vcycle_apply(c, z, nullptr, rr, nb, mask));
     LaunchScope scope(c, K_CNN_IO);
     if (scaled)
-        add_scaled_kernel<<<g2, 256, 0, c->stream>>>(z, c->cnn_e0, n, c->cnn_alpha, guard);
+        add_scaled_kernel<<<g2, 256, 0, c->stream>>>(z, c->cnn_e0, n, c->cnn_alpha, guard, mask);
     else
         add_kernel<<<1184, 256, 0, c->stream>>>(z, c->cnn_e0, n * nb);
     HELM_CK(cudaGetLastError());
