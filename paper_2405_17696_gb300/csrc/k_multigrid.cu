@@ -37,6 +37,69 @@ __global__ void jacobi_fine2_kernel(OpFine5 op, float2* __restrict__ u_out, cons
         make_float4(uv.x + w * q0.x, uv.y + w * q0.y, uv.z + w * q1.x, uv.w + w * q1.y);
 }
 
+// One damped Jacobi sweep of a coarse level for the RHS pair (2z, 2z + 1): the nine
+// Galerkin coefficients of a node are loaded once for both when the two RHS share a
+// frequency (they are read from L2 for every RHS otherwise).
+__global__ void jacobi_c9_pair_kernel(OpC9 op, float2* __restrict__ u_out, const float2* __restrict__ u_in,
+                                      const float2* __restrict__ f, float w, int nx, int nz, int nb,
+                                      const int* mask, Tally tl) {
+    const int b0 = 2 * blockIdx.z, b1 = b0 + 1;
+    const bool a0 = mask[b0] != 0, a1 = b1 < nb && mask[b1] != 0;
+    if (!a0 && !a1) return;
+    if (a0) tally_once(tl, blockIdx.x == 0 && blockIdx.y == 0);
+    if (a1) tally_once(tl, blockIdx.x == 0 && blockIdx.y == 0);
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iz = blockIdx.y * blockDim.y + threadIdx.y;
+    if (ix >= nx || iz >= nz) return;
+    const size_t N = (size_t)nx * nz;
+    const int idx = iz * nx + ix;
+    const int f0 = __ldg(op.rhs_freq + b0), f1 = a1 ? __ldg(op.rhs_freq + b1) : f0;
+    const float2* c0 = op.base(f0);
+    const float2* c1 = op.base(f1);
+    const bool same = f0 == f1;
+    const float2* u0b = u_in ? u_in + (size_t)b0 * N : nullptr;
+    const float2* u1b = u_in ? u_in + (size_t)b1 * N : nullptr;
+    float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
+    if (u_in) {
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int jz = iz + dz, jx = ix + dx;
+                if (jz < 0 || jz >= nz || jx < 0 || jx >= nx) continue;
+                const size_t off = (size_t)((dz + 1) * 3 + (dx + 1)) * N + idx;
+                const float2 k0 = __ldg(c0 + off);
+                const float2 k1 = same ? k0 : __ldg(c1 + off);
+                const int q = jz * nx + jx;
+                if (a0) {
+                    const float2 v = u0b[q];
+                    y0.x += k0.x * v.x - k0.y * v.y;
+                    y0.y += k0.x * v.y + k0.y * v.x;
+                }
+                if (a1) {
+                    const float2 v = u1b[q];
+                    y1.x += k1.x * v.x - k1.y * v.y;
+                    y1.y += k1.x * v.y + k1.y * v.x;
+                }
+            }
+        }
+    }
+    const float2 d0 = __ldg(c0 + 4 * N + idx);
+    const float2 d1 = same ? d0 : __ldg(c1 + 4 * N + idx);
+    if (a0) {
+        const size_t i = (size_t)b0 * N + idx;
+        const float2 u0 = u_in ? u_in[i] : make_float2(0.f, 0.f);
+        const float2 q = cdiv(csub(f[i], y0), d0);
+        u_out[i] = make_float2(u0.x + w * q.x, u0.y + w * q.y);
+    }
+    if (a1) {
+        const size_t i = (size_t)b1 * N + idx;
+        const float2 u0 = u_in ? u_in[i] : make_float2(0.f, 0.f);
+        const float2 q = cdiv(csub(f[i], y1), d1);
+        u_out[i] = make_float2(u0.x + w * q.x, u0.y + w * q.y);
+    }
+}
+
 template <class Op>
 __global__ void jacobi_kernel(Op op, float2* __restrict__ u_out, const float2* __restrict__ u_in,
                               const float2* __restrict__ f, float w, int nx, int nz, const int* mask, Tally tl) {
@@ -259,6 +322,13 @@ int launch_jacobi(const helm_ctx* c, const Op& op, float2* u_out, const float2* 
             HELM_CK(cudaGetLastError());
             return HELM_OK;
         }
+    }
+    if constexpr (std::is_same<Op, OpC9>::value) {
+        const dim3 g((nx + 31) / 32, (nz + 7) / 8, (nb + 1) / 2);
+        jacobi_c9_pair_kernel<<<g, dim3(32, 8), 0, c->stream>>>(op, u_out, u_in, f, c->opt.jacobi_w, nx, nz, nb, mask,
+                                                                 tally(c, K_JACOBI_COARSE, (u_in ? 24ull : 16ull) * nx * nz));
+        HELM_CK(cudaGetLastError());
+        return HELM_OK;
     }
     jacobi_kernel<Op><<<grid2(nx, nz, nb), dim3(32, 8), 0, c->stream>>>(
         op, u_out, u_in, f, c->opt.jacobi_w, nx, nz, mask,
