@@ -795,7 +795,7 @@ int launch_mode(const CUtensorMap& tm0, const CUtensorMap& tm1, const CUtensorMa
             (void)cudaGetLastError();
         }
     });
-    const size_t per_cta_smem = smem_req + (size_t)static_smem + 1024;   // + the driver's reservation
+    const size_t per_cta_smem = smem_req + (size_t)static_smem + 1024;   // + the per-block shared memory the CUDA runtime reserves
     const int by_smem = (int)((size_t)smem_per_sm() / per_cta_smem);
     const int by_regs = regs > 0 ? 65536 / (((regs * 32 + 255) / 256) * 256 * (NT / 32)) : 1;
     const int occ = std::min(by_smem, by_regs);
