@@ -1,6 +1,8 @@
 """Alg. 2 schedule of the retraining driver, checked on the CPU with a fake
 backend that records the calls (no GPU): 128 initial pairs and 3 data epochs
 end with 1024 pairs (Sec. 4.2); 30 epochs of batch 16 make 1784 Adam steps."""
+import os
+
 import numpy as np
 import pytest
 
@@ -36,12 +38,28 @@ class FakeNative:
         return 1.0 / len(self.steps)
 
 
+def _golden():
+    path = os.path.join(os.path.dirname(__file__), "golden", "alg2_schedule.txt")
+    vals = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = int(v)
+    return vals
+
+
 def test_schedule_matches_the_paper_budget():
+    gold = _golden()   # Sec. 4.2, Alg. 2
     cfg = RT.RetrainConfig()
+    assert (cfg.initial_size, cfg.data_epochs, cfg.epochs, cfg.batch) == (
+        gold["initial_pairs"], gold["data_epochs"], gold["epochs"], gold["batch"])
     sched = RT.schedule(cfg)
-    assert [s for s, _ in sched[:4]] == [128, 256, 512, 1024]
-    assert sched[-1][0] == 1024 and len(sched) == 30
-    assert sum(n for _, n in sched) == 1784
+    sizes = [gold["initial_pairs"] * 2 ** i for i in range(gold["data_epochs"] + 1)]
+    assert [s for s, _ in sched[:4]] == sizes and sizes[-1] == gold["final_pairs"]
+    assert sched[-1][0] == gold["final_pairs"] and len(sched) == gold["epochs"]
+    # Adam steps: ceil(pairs / batch) per epoch
+    assert sum(n for _, n in sched) == sum(-(-s // gold["batch"]) for s, _ in sched) == 1784
 
 
 def test_driver_follows_the_schedule():
