@@ -262,16 +262,17 @@ __global__ void __launch_bounds__(256) wgrad_kernel(WgArgs a, Wg2 w) {
     }
 }
 
-// wt[b] = 1 / ||e_b||^2 (one block per sample, FP64 sum); 0 for a zero sample
+// wt[b] = 1 / ||e_b||^2 (one block per sample; FP32 partial sums per thread, FP64
+// from the warp sums on); 0 for a zero sample
 __global__ void inv_energy_kernel(const float2* __restrict__ e, long long n, float* __restrict__ wt) {
     const int b = blockIdx.x;
-    double acc = 0.0;
+    float af = 0.0f;
     for (long long p = threadIdx.x; p < n; p += blockDim.x) {
         const float2 v = e[(long long)b * n + p];
-        acc += (double)v.x * v.x + (double)v.y * v.y;
+        af = fmaf(v.x, v.x, fmaf(v.y, v.y, af));
     }
     __shared__ double sm[32];
-    acc = warp_sum(acc);
+    double acc = warp_sum((double)af);
     if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -282,23 +283,26 @@ __global__ void inv_energy_kernel(const float2* __restrict__ e, long long n, flo
 }
 
 // loss = (1/m) sum_b wt_b ||e_net - e_true||^2 with e_net = h^2 rms (o_0 + i o_1)
-// (wt = 1: Eq. 4.2; wt_b = 1 / ||e_b||^2: relative error); gout = dloss/do
+// (wt = 1: Eq. 4.2; wt_b = 1 / ||e_b||^2: relative error); gout = dloss/do.
+// grid (slices, nb): sample b = blockIdx.y; FP32 partial sums per thread, FP64 from
+// the warp sums on.
 __global__ void mse_grad_kernel(const float* __restrict__ out, const float2* __restrict__ et,
                                 const float* __restrict__ rms, const float* __restrict__ wt, float h2, long long n,
                                 int nb, float inv_m, float* __restrict__ gout, double* __restrict__ loss) {
-    double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nb;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(i / n);
-        const float s = h2 * rms[b];
-        const float w = wt ? wt[b] : 1.0f;
-        const float dr = s * out[2 * i] - et[i].x, di = s * out[2 * i + 1] - et[i].y;
-        acc += w * ((double)dr * dr + (double)di * di);
-        gout[2 * i] = 2.0f * inv_m * w * dr * s;
-        gout[2 * i + 1] = 2.0f * inv_m * w * di * s;
+    const int b = blockIdx.y;
+    const float s = h2 * rms[b];
+    const float w = wt ? wt[b] : 1.0f;
+    float af = 0.0f;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const long long i = (long long)b * n + p;
+        const float2 o = reinterpret_cast<const float2*>(out)[i];
+        const float2 t = et[i];
+        const float dr = s * o.x - t.x, di = s * o.y - t.y;
+        af = fmaf(dr, dr, fmaf(di, di, af));
+        reinterpret_cast<float2*>(gout)[i] = make_float2(2.0f * inv_m * w * dr * s, 2.0f * inv_m * w * di * s);
     }
     __shared__ double sm[32];
-    acc = warp_sum(acc);
+    double acc = (double)w * warp_sum((double)af);
     if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -533,7 +537,8 @@ int cnn_loss_grad_impl(cnn_model* m, helm_ctx* c, const float2* r, const float2*
         if (!s) {
             LaunchScope scope(c, K_CNN_IO);
             if (wt) inv_energy_kernel<<<nb, 256, 0, st>>>(e, n, wt);
-            mse_grad_kernel<<<1184, 256, 0, st>>>(out, e, rms, wt, c->hx * c->hz, n, nb, 1.0f / (float)nb, gout,
+            mse_grad_kernel<<<dim3((unsigned)std::min<long long>((n + 255) / 256, 128), nb), 256, 0, st>>>(
+                out, e, rms, wt, c->hx * c->hz, n, nb, 1.0f / (float)nb, gout,
                                                   dloss);
             ck(cudaGetLastError());
         }
