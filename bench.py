@@ -224,6 +224,20 @@ class Problem:
         return rel
 
 
+def reduce_over_ranks(ms, solved, world, device="cpu"):
+    """Whole-job figures of a timed region: the slowest rank's milliseconds and the
+    RHS that reached the tolerance on all ranks together (all-reduce MAX and SUM over
+    the default process group when world > 1)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(solved)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
+
+
 def timed(prob, ctx, steps, warmup, dev, world, stream, sampler=None):
     """Device time (ms, max over ranks) of `steps` solve steps after `warmup`, with
     a barrier and a synchronize on both sides; per-RHS iterations and residuals."""
@@ -252,16 +266,10 @@ def timed(prob, ctx, steps, warmup, dev, world, stream, sampler=None):
         dist.barrier()
     launches = native.helm_launch_count() - launches0
     clocks = sampler.stop() if sampler else None
-    t = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
     its = np.concatenate(prob.iters)
-    # RHS that reached the tolerance in the timed steps, summed over ranks
-    solved = torch.tensor([float(sum(prob.solved))], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(solved, op=dist.ReduceOp.SUM)
-    timed.solved = int(solved.item())
-    return float(t.item()), its, float(max(np.max(r) for r in rels)), launches, clocks
+    # slowest rank's time; RHS that reached the tolerance in the timed steps, summed over ranks
+    ms, timed.solved = reduce_over_ranks(ev0.elapsed_time(ev1), sum(prob.solved), world, dev)
+    return ms, its, float(max(np.max(r) for r in rels)), launches, clocks
 
 
 def e2e_of(prob, ctx, steps, dev):
