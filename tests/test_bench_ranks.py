@@ -46,3 +46,22 @@ def test_single_rank_is_unchanged():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.reduce_over_ranks(7.5, 42, 1) == (7.5, 42)
+
+
+def test_roofline_fields_from_a_profile():
+    """roofline_of: algorithmic bytes per launch over the average launch time against
+    the measured HBM peak; the tensor companion against the sustained BF16 peak; DRAM
+    traffic per launch from the committed ncu summary of the class."""
+    sys.path.insert(0, ROOT)
+    import bench
+    hbm, bf16_s, src = bench.peaks(sustained=True)
+    prof = {"conv3x3_tc": (2000.0, 1000, 5.0e12), "cnn_io": (100.0, 10, 0.0)}
+    flops = {"conv3x3_tc": 7.0e14}
+    r = bench.roofline_of(prof, flops)
+    assert r["kernel"] == "conv3x3_tc" and r["bound"] == "hbm"
+    assert abs(r["achieved"] - 5.0e12 / 2.0 / 1e9) < 1e-6          # GB/s over 2 s
+    assert abs(r["frac"] - r["achieved"] / hbm) < 1e-12
+    assert abs(r["tensor"]["achieved"] - 7.0e14 / 2.0 / 1e12) < 1e-9
+    assert abs(r["tensor"]["frac"] - r["tensor"]["achieved"] / bf16_s) < 1e-12
+    assert r["traffic"] == bench.traffic_from_profiles("conv3x3_tc") and r["traffic"] > 0
+    assert abs(r["algorithmic_bytes_per_launch"] - 5.0e9) < 1e-3
