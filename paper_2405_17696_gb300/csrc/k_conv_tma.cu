@@ -464,15 +464,16 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                     const size_t ob = img_base + (size_t)pix * 8;
                     const long long p = (long long)b * hw_out + pix;
                     const uint32_t tcol = lane_base + (uint32_t)(slot * g.slot_cols);
-                    float v[16], vn[16], vf[16];   // dx = -1 (this row), 0 (row + 1), +1 (row + 2)
-                    tc::tmem_ld16(tcol, v);
-                    tc::tmem_ld16(tcol + 16u, vn);
-                    tc::tmem_ld16(tcol + 32u, vf);
+                    // columns 0-15: dx = -1 (this row); 16-31: dx = 0 (row + 1); 32-47: dx = +1 (row + 2)
+                    float d[48];
+                    tc::tmem_ld48(tcol, d);
                     tc::tc_fence_before_sync();
                     tc::mbar_arrive(&tempty[slot]);   // the slot's TMEM reads are done
+                    float v[16];
 #pragma unroll
                     for (int c = 0; c < 16; ++c)
-                        v[c] += __shfl_down_sync(0xffffffffu, vn[c], 1) + __shfl_down_sync(0xffffffffu, vf[c], 2);
+                        v[c] = d[c] + __shfl_down_sync(0xffffffffu, d[16 + c], 1) +
+                               __shfl_down_sync(0xffffffffu, d[32 + c], 2);
                     if (valid) segment(v, 0, ob, p);
                 }
             }
