@@ -293,6 +293,20 @@ int cnn_set_conv_path(int path);
 int cnn_autotune(helm_ctx* ctx, int nrhs, int* n_shapes);
 /* Forget every tuned tiling. */
 void cnn_autotune_reset(void);
+/* Tile plan of the TMA convolution for a layer shape, computed on the host (no
+ * GPU needed), for checking its bounds: mode 0 same grid, 1 stride-2 down, 2
+ * nearest x2 up, 3 transpose of stride 2; c0, c1 input channels (multiples of
+ * 16), npad output channels (16 or a multiple of 32, at most 128), hin x win
+ * input grid, nb images; stage_kb / ring_kb / rows_cap as for
+ * cnn_set_conv_ring / cnn_set_conv_tiling (0 = default); narrow selects the
+ * column-taps-in-N variant for 16-channel same-grid layers.  out16 = {tiles,
+ * tile width, tile rows, staged row pitch, M blocks per parity, parities,
+ * parity sub-planes, plane bytes, parity stride bytes, weight bytes, stage
+ * bytes, stages, TMEM columns, TMEM slots, slot columns, mode used (4 = the
+ * variant)}.  HELM_EINVAL for an invalid shape or one the kernel does not take
+ * (out16 is filled either way for a valid shape). */
+int cnn_conv_plan(int mode, int c0, int c1, int npad, int hin, int win, int nb, int stage_kb, int ring_kb,
+                  int rows_cap, int narrow, int* out16);
 /* Launches of the column-taps-in-N convolution since the library was loaded. */
 long long cnn_conv_narrow_launches(void);
 /* Tile height limit of the TMA halo-tile kernel: at most max_rows output rows per

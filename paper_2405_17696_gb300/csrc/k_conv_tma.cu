@@ -1007,6 +1007,42 @@ extern "C" int cnn_set_conv_ring(int stage_kb, int ring_kb) {
 
 extern "C" long long cnn_conv_narrow_launches(void) { return helm::g_launch_narrow.load(); }
 
+// Tile plan of the TMA kernel for a layer shape (host only, no GPU needed): out16 =
+// {tiles, tw, rows, pw, mb, nph, nplanes, plane, pstride, wbytes, stage, ns, tmem_cols,
+// nslot, slot_cols, mode}.  For checking the plan's bounds on the CPU.
+extern "C" int cnn_conv_plan(int mode, int c0, int c1, int npad, int hin, int win, int nb, int stage_kb,
+                             int ring_kb, int rows_cap, int narrow, int* out16) {
+    if (!out16 || mode < 0 || mode > 3 || c0 < 16 || c0 % 16 || c1 < 0 || c1 % 16 || nb < 1 || hin < 1 ||
+        win < 1 || (npad != 16 && npad % 32) || npad > 128) {
+        helm::set_error("cnn_conv_plan: invalid layer shape");
+        return HELM_EINVAL;
+    }
+    helm::ConvArgs a{};
+    a.c0 = c0;
+    a.c1 = c1;
+    a.nb = nb;
+    a.hin = hin;
+    a.win = win;
+    a.hout = mode == 1 ? hin / 2 : (mode >= 2 ? 2 * hin : hin);
+    a.wout = mode == 1 ? win / 2 : (mode >= 2 ? 2 * win : win);
+    a.npad = npad;
+    a.mode = (narrow && mode == 0 && npad == 16) ? 4 : mode;
+    helm::TileCfg t;
+    t.rows_cap = rows_cap;
+    t.stage_kb = stage_kb;
+    t.ring_kb = ring_kb;
+    t.narrow = narrow;
+    const helm::Geometry g = helm::plan(a, t);
+    const int v[16] = {g.tiles, g.tw, g.rows, g.pw, g.mb, g.nph, g.nplanes, g.plane, g.pstride, g.wbytes,
+                       g.stage, g.ns, (int)g.tmem_cols, g.nslot, g.slot_cols, a.mode};
+    for (int i = 0; i < 16; ++i) out16[i] = v[i];
+    if (g.tiles <= 0) {
+        helm::set_error("cnn_conv_plan: the layer does not fit the TMA kernel");
+        return HELM_EINVAL;
+    }
+    return HELM_OK;
+}
+
 // Launch shape of the last TMA convolution (diagnostics): grid, CTAs per SM,
 // the CTAs per SM that registers and shared memory allow, dynamic
 // shared memory per CTA, registers per thread, static shared memory.

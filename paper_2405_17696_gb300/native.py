@@ -103,6 +103,8 @@ def _load():
     lib.cnn_set_conv_path.restype = ip
     lib.cnn_set_conv_tiling.argtypes = [ip]
     lib.cnn_set_conv_tiling.restype = ip
+    lib.cnn_conv_plan.argtypes = [ip] * 11 + [ctypes.POINTER(ctypes.c_int)]
+    lib.cnn_conv_plan.restype = ip
     lib.cnn_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
     lib.cnn_autotune.restype = ip
     lib.cnn_autotune_reset.argtypes = []
@@ -364,6 +366,21 @@ def cnn_set_conv_path(path: int):
 def cnn_set_conv_tiling(max_rows: int):
     """Tile-height limit of the TMA conv kernel (0 = automatic)."""
     _check(lib.cnn_set_conv_tiling(int(max_rows)), "cnn_set_conv_tiling")
+
+
+CONV_PLAN_FIELDS = ("tiles", "tw", "rows", "pw", "mb", "nph", "nplanes", "plane", "pstride", "wbytes", "stage",
+                    "ns", "tmem_cols", "nslot", "slot_cols", "mode")
+
+
+def cnn_conv_plan(mode: int, c0: int, c1: int, npad: int, hin: int, win: int, nb: int = 1, stage_kb: int = 0,
+                  ring_kb: int = 0, rows_cap: int = 0, narrow: bool = False):
+    """Host-side tile plan of the TMA convolution (dict of CONV_PLAN_FIELDS), or None when
+    the kernel does not take the layer."""
+    out = (ctypes.c_int * 16)()
+    st = lib.cnn_conv_plan(mode, c0, c1, npad, hin, win, nb, stage_kb, ring_kb, rows_cap, 1 if narrow else 0, out)
+    if st != HELM_OK:
+        return None
+    return dict(zip(CONV_PLAN_FIELDS, list(out)))
 
 
 def cnn_autotune(ctx, nrhs: int) -> int:

@@ -15,7 +15,7 @@ def _declared():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?(?:int|void|char|double|float|size_t)\s*\*?\s*(\w+)\s*\(",
+        for m in re.finditer(r"^\s*(?:const\s+)?(?:long\s+long|int|void|char|double|float|size_t)\s*\*?\s*(\w+)\s*\(",
                              text, flags=re.M):
             names.add(m.group(1))
     return names
