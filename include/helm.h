@@ -141,7 +141,8 @@ int helm_residual(helm_ctx* ctx, const helm_c64* rhs, const helm_c128* x, helm_c
  * latency-critical loop where an allocation, and the synchronisation it can imply, is not
  * acceptable.  The paper has no counterpart; this is a deployment convenience.
  * It allocates nothing and needs no context: every array is a caller-owned DEVICE
- * pointer (a host pointer is rejected with HELM_EINVAL), the work is issued on `stream`
+ * pointer of the current device (a host pointer, or memory of another GPU, is rejected
+ * with HELM_EINVAL; managed memory is accepted), the work is issued on `stream`
  * (a cudaStream_t, NULL = legacy default stream) and the call returns without waiting.
  *   kappa, gamma : float32 [nz][nx];  omega_rhs : float32 [nrhs], w of each RHS (rad/s)
  *   rhs : complex64 [nrhs][nz][nx];  x : complex128 [nrhs][nz][nx]

@@ -21,6 +21,10 @@ paper defines, in float64/complex128, citing the passage it follows:
 * ``green``      - the 2D free-space Green's function used as a pin.
 * ``cnn``        - nested-loop reference of the encoder-solver U-Net layers
   (Fig. 1 caption, Eq. 3.13, 4.1), MSE (Eq. 4.2) and Adam.
-* ``philox``     - Philox-4x32-10 counter-based generator (Salmon et al.,
-  SC'11), implemented from its published definition.
+* ``training``   - training pairs of Eq. 4.3, the data step of Alg. 2, the
+  loss of Eq. 4.2 and the M_VU compositions of Eq. 3.14.
+
+Random draws (the x ~ CN(0, 1) of Eq. 4.3, the GMRES step counts) are made by
+the seeded input generators of ``paper_2405_17696_gb300.media`` and passed in
+as inputs to both sides.
 """

@@ -69,13 +69,19 @@ def network_error(P, specs, kappa, gamma, omega, h, r, quantize=None):
     return cnn.solver_output_to_error(out, rms, h), out, tape, rms
 
 
-def refine_samples(P, specs, kappa, gamma, omega, h, r, e, literal=False, params=None, quantize=None):
+def refine_from_estimate(kappa, gamma, omega, h, r, e, e_net, literal=False, params=None):
+    """The data step of Alg. 2 (Sec. 4.2) given the network's error estimates.
+
+    For each pair (r, e) with H e = r: e~ = x after one V-cycle-preconditioned
+    (F)GMRES step on H x = r started from x0 = e_net, and the new pair is
+    (r - H e~, e - e~) in the residual-correction reading (the error that is still
+    left after the step, with its residual), or (H e~, e~) as Alg. 2 prints it."""
     p = params if params is not None else MG.VCycleParams()
     pc = MG.VCyclePreconditioner(kappa, gamma, omega, h, h, p)
     A = lambda u: H.helmholtz_apply(u, kappa, gamma, omega, h, h)
-    e_net, _, _, _ = network_error(P, specs, kappa, gamma, omega, h, r, quantize)
     r2, e2 = [], []
-    for ri, ei, x0 in zip(np.asarray(r, dtype=np.complex128), np.asarray(e, dtype=np.complex128), e_net):
+    for ri, ei, x0 in zip(np.asarray(r, dtype=np.complex128), np.asarray(e, dtype=np.complex128),
+                          np.asarray(e_net, dtype=np.complex128)):
         et, _, _ = fgmres_cycle(A, pc, ri, x0, 1, tol_abs=0.0)
         if literal:
             r2.append(A(et))
@@ -84,6 +90,13 @@ def refine_samples(P, specs, kappa, gamma, omega, h, r, e, literal=False, params
             r2.append(ri - A(et))
             e2.append(ei - et)
     return np.stack(r2), np.stack(e2)
+
+
+def refine_samples(P, specs, kappa, gamma, omega, h, r, e, literal=False, params=None, quantize=None):
+    """Alg. 2 data step with the network of parameters P as the estimator
+    (network output alone, no V-cycle)."""
+    e_net, _, _, _ = network_error(P, specs, kappa, gamma, omega, h, r, quantize)
+    return refine_from_estimate(kappa, gamma, omega, h, r, e, e_net, literal, params)
 
 
 def loss_and_grad(P, specs, kappa, gamma, omega, h, r, e, quantize=None, relative=False):

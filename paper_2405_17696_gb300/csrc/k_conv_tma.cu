@@ -818,38 +818,62 @@ int launch_mode(const CUtensorMap& tm0, const CUtensorMap& tm1, const CUtensorMa
 // the layer does not fit it, so that the caller can use the gather kernel.
 namespace {
 
-// One launch of the TMA kernel with tiling t; HELM_EINVAL when the layer does not fit it.
-int launch_cfg(const ConvArgs& a_in, cudaStream_t st, const TileCfg& t) {
-    ConvArgs a = a_in;
-    const bool narrow = t.narrow != 0;
+// The launch decision of one layer, host code shared by the launcher and
+// cnn_conv_plan: the shape checks of the kernel, the tile plan, and for a
+// 16-channel same-grid layer with `narrow` the column-taps-in-N variant (mode 4),
+// which falls back to mode 0 when its plan does not fit (or when the caller says
+// that its weight map could not be encoded: no_mode4).  *mode_out = the mode that
+// runs.  HELM_EINVAL when the kernel does not take the layer (nothing launched);
+// *g_out is the plan either way.
+int plan_launch(const ConvArgs& a, const TileCfg& t, bool no_mode4, int* mode_out, Geometry* g_out) {
+    *g_out = Geometry{};
+    *mode_out = a.mode;
+    if (a.mode < 0 || a.mode > 3) return HELM_EINVAL;
     if (a.npad != 16 && a.npad % 32) return HELM_EINVAL;   // the epilogue reads 16 or 32k columns
+    if (a.npad > 128 || a.c0 % 8 || a.c1 % 8) return HELM_EINVAL;
     if (a.mode == 0 && (a.hin != a.hout || a.win != a.wout)) return HELM_EINVAL;
     if (a.mode == 1 && (a.hin != 2 * a.hout || a.win != 2 * a.wout)) return HELM_EINVAL;
     if (a.mode >= 2 && (a.hout != 2 * a.hin || a.wout != 2 * a.win)) return HELM_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(a.x0) & 15) || (a.c1 && (reinterpret_cast<uintptr_t>(a.x1) & 15)) ||
-        (reinterpret_cast<uintptr_t>(a.w) & 15))
-        return HELM_EINVAL;
     if ((long long)a.nb * (a.mode >= 2 ? (long long)a.hin * a.win : (long long)a.hout * a.wout) > 0x7fffffffLL)
         return HELM_EINVAL;
+    ConvArgs b = a;
     Geometry g{};
-    alignas(64) CUtensorMap tmw;
-    if (narrow && a.mode == 0 && a.npad == 16) {
-        // 16 output channels: column taps in N (mode 4) when its plan and weight map exist
-        a.mode = 4;
-        g = plan(a, t);
-        if (g.tiles <= 0 || (size_t)g.ns * g.stage > 200 * 1024 || !encode_w5(&tmw, a.w, a.c0 + a.c1, a.npad))
-            a.mode = 0;
+    if (t.narrow && !no_mode4 && a.mode == 0 && a.npad == 16) {
+        b.mode = 4;
+        g = plan(b, t);
+        if (g.tiles <= 0 || (size_t)g.ns * g.stage > 200 * 1024) b.mode = 0;
     }
-    if (a.mode != 4) g = plan(a, t);
+    if (b.mode != 4) g = plan(b, t);
+    *g_out = g;
+    *mode_out = b.mode;
     if (g.tiles <= 0) return HELM_EINVAL;
     if ((size_t)g.ns * g.stage > 200 * 1024 || g.tmem_cols > 512) return HELM_EINVAL;
     // box extents: modes 0/2/3 (tw + 2) pixels = 2 (tw + 2) elements x (rows + 2); mode 1
     // traverses 2 (tw + 1) x 2 (rows + 1) pixels with stride 2
+    const int bw = b.mode == 1 ? 2 * g.pw : g.pw;
+    const int bh = b.mode == 1 ? 2 * (g.rows + 1) : g.rows + 2;
+    if ((b.mode == 1 ? bw : 2 * bw) > 256 || bh > 256) return HELM_EINVAL;
+    return HELM_OK;
+}
+
+// One launch of the TMA kernel with tiling t; HELM_EINVAL when the layer does not fit it.
+int launch_cfg(const ConvArgs& a_in, cudaStream_t st, const TileCfg& t) {
+    ConvArgs a = a_in;
+    if ((reinterpret_cast<uintptr_t>(a.x0) & 15) || (a.c1 && (reinterpret_cast<uintptr_t>(a.x1) & 15)) ||
+        (reinterpret_cast<uintptr_t>(a.w) & 15))
+        return HELM_EINVAL;
+    Geometry g{};
+    int mode = a.mode;
+    if (plan_launch(a, t, false, &mode, &g) != HELM_OK) return HELM_EINVAL;
+    alignas(64) CUtensorMap tmw;
+    if (mode == 4 && !encode_w5(&tmw, a.w, a.c0 + a.c1, a.npad)) {
+        // no weight map for the variant: the plain same-grid kernel
+        if (plan_launch(a, t, true, &mode, &g) != HELM_OK) return HELM_EINVAL;
+    }
+    a.mode = mode;
     const int es = a.mode == 1 ? 2 : 1;
     const int bw = a.mode == 1 ? 2 * g.pw : g.pw;
     const int bh = a.mode == 1 ? 2 * (g.rows + 1) : g.rows + 2;
-    if ((a.mode == 1 ? bw : 2 * bw) > 256 || bh > 256) return HELM_EINVAL;
-    if (a.c0 % 8 || a.c1 % 8) return HELM_EINVAL;
     alignas(64) CUtensorMap tm0, tm1;
     if (!encode_act(&tm0, a.x0, a.c0, a.win, a.hin, a.nb, bw, bh, es)) return HELM_EINVAL;
     if (a.c1) {
@@ -1026,17 +1050,19 @@ extern "C" int cnn_conv_plan(int mode, int c0, int c1, int npad, int hin, int wi
     a.hout = mode == 1 ? hin / 2 : (mode >= 2 ? 2 * hin : hin);
     a.wout = mode == 1 ? win / 2 : (mode >= 2 ? 2 * win : win);
     a.npad = npad;
-    a.mode = (narrow && mode == 0 && npad == 16) ? 4 : mode;
+    a.mode = mode;
     helm::TileCfg t;
     t.rows_cap = rows_cap;
     t.stage_kb = stage_kb;
     t.ring_kb = ring_kb;
     t.narrow = narrow;
-    const helm::Geometry g = helm::plan(a, t);
+    helm::Geometry g{};
+    int used = mode;
+    const int s = helm::plan_launch(a, t, false, &used, &g);
     const int v[16] = {g.tiles, g.tw, g.rows, g.pw, g.mb, g.nph, g.nplanes, g.plane, g.pstride, g.wbytes,
-                       g.stage, g.ns, (int)g.tmem_cols, g.nslot, g.slot_cols, a.mode};
+                       g.stage, g.ns, (int)g.tmem_cols, g.nslot, g.slot_cols, used};
     for (int i = 0; i < 16; ++i) out16[i] = v[i];
-    if (g.tiles <= 0) {
+    if (s != HELM_OK) {
         helm::set_error("cnn_conv_plan: the layer does not fit the TMA kernel");
         return HELM_EINVAL;
     }

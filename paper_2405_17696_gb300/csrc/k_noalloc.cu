@@ -109,13 +109,17 @@ int noalloc_scratch(void** out) {
     return HELM_OK;
 }
 
-bool on_device(const void* p) {
+// Device memory of the current device `dev` (managed memory is reachable from
+// every device); memory of another GPU is rejected, since the kernel would read
+// it through the peer path, which faults where peer access is not enabled.
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         (void)cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -141,10 +145,13 @@ extern "C" int helm_residual_noalloc(const float* kappa, const float* gamma, int
                   std::to_string(NOALLOC_MAX_RHS) + " right-hand sides");
         return HELM_EINVAL;
     }
+    int dev = 0;
+    HELM_CK(cudaGetDevice(&dev));
     const void* ptrs[] = {kappa, gamma, omega_rhs, rhs, x, r, rel_res};
     for (const void* p : ptrs)
-        if (!on_device(p)) {
-            set_error("helm_residual_noalloc: every array must be device memory (nothing is staged)");
+        if (!on_device(p, dev)) {
+            set_error("helm_residual_noalloc: every array must be device memory of the current device "
+                      "(nothing is staged)");
             return HELM_EINVAL;
         }
     void* base = nullptr;

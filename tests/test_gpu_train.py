@@ -107,6 +107,42 @@ def test_refine_samples_keep_pairs_consistent(native, literal):
         assert np.linalg.norm(r2[i]) > 0
 
 
+@pytest.mark.parametrize("literal", [0, 1])
+def test_refine_samples_parity(native, literal):
+    """Alg. 2 data step against the oracle, element by element: the GPU network's own
+    estimate e_net (cnn_precond_apply without V-cycle) is handed to the oracle's step,
+    so that both sides take one preconditioned GMRES step from the same x0."""
+    w = media.crop_workload(64, 32, freqs=(5.0,), width=8)
+    specs = cnn.layer_specs(widths=(16, 32))
+    theta = 0.5 * cnn.he_init(specs, seed=1)
+    net, ctx = _setup(native, w, widths=(16, 32), theta=theta, mg_levels=3)
+    try:
+        x = media.complex_normal((3, w.nz, w.nx), seed=17)
+        r = np.zeros_like(x)
+        e = np.zeros_like(x)
+        native.cnn_make_samples(ctx, x, [1, 2, 4], r, e, 3)
+        e_net = np.zeros_like(x)
+        native.cnn_precond_apply(ctx, r, e_net, 3, None, 0)
+        r2 = np.zeros_like(x)
+        e2 = np.zeros_like(x)
+        native.cnn_refine_samples(ctx, r, e, r2, e2, 3, literal=literal)
+    finally:
+        native.helm_destroy(ctx)
+        native.cnn_destroy(net)
+    om = float(np.float32(w.omegas[0]))
+    kap, gam = _f64(w.kappa), _f64(w.gamma)
+    r_ref, e_ref = T.refine_from_estimate(kap, gam, om, w.h, r, e, e_net, literal=bool(literal))
+    coef = np.abs(H.helmholtz_coefficient(kap, gam, om))
+    for i in range(3):
+        # the step's iterate e~ (e - e' in the residual-correction reading): relative 1e-5
+        et = e_ref[i] if literal else e[i] - e_ref[i]
+        et_gpu = e2[i] if literal else e[i] - e2[i]
+        assert np.linalg.norm(et_gpu - et) <= 1e-5 * np.linalg.norm(et), i
+        # the residual: relative 2e-3 plus the complex64 rounding of e~ through |H|
+        r_floor = 2.5e-7 * np.linalg.norm((8.0 / w.h ** 2 + coef) * np.abs(et))
+        assert np.linalg.norm(r2[i] - r_ref[i]) <= 2e-3 * np.linalg.norm(r_ref[i]) + r_floor, i
+
+
 @pytest.mark.parametrize("relative", [0, 1])
 def test_loss_and_gradient_parity(native, relative):
     w = media.crop_workload(32, 32, freqs=(5.0,), width=6)

@@ -64,3 +64,18 @@ def test_noalloc_rejects_sizes_beyond_the_scratch(native):
         native.helm_residual_noalloc(kap, kap, nx, nz, 10.0, 10.0, om, b, x, b, rel, nb)
     assert e.value.status == native.HELM_EINVAL
     assert "scratch" in str(e.value)
+
+
+def test_noalloc_rejects_host_arrays(native):
+    """Nothing is staged: an array in host memory is refused before any launch."""
+    nx, nz, nb = 64, 32, 1
+    kap = torch.zeros((nz, nx), dtype=torch.float32, device="cuda")
+    kap_host = torch.zeros((nz, nx), dtype=torch.float32)
+    om = torch.zeros((nb,), dtype=torch.float32, device="cuda")
+    b = torch.zeros((nb, nz, nx), dtype=torch.complex64, device="cuda")
+    x = torch.zeros((nb, nz, nx), dtype=torch.complex128, device="cuda")
+    rel = torch.zeros((nb,), dtype=torch.float64, device="cuda")
+    with pytest.raises(native.HelmError) as e:
+        native.helm_residual_noalloc(kap_host, kap, nx, nz, 10.0, 10.0, om, b, x, b, rel, nb)
+    assert e.value.status == native.HELM_EINVAL
+    assert "device memory" in str(e.value)
