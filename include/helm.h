@@ -82,6 +82,7 @@ typedef struct {
                                ||r - a H e_0||; 2 = 0 for every RHS until one of its restart cycles
                                lowers the residual by less than 10 %, then 3 for that RHS; 1 = V-cycle
                                on P u = r from u_0 = e_0                                      (2) */
+    int   autotune;         /* 1: helm_setup with a network runs cnn_autotune on max_rhs RHS  (0) */
     void* stream;           /* cudaStream_t for all work of the context   (NULL) */
 } helm_opts;
 
@@ -209,7 +210,9 @@ void helm_destroy(helm_ctx* ctx);
  * Parameters are one flat FP32 vector: per layer weights [cout][9][cin] then
  * bias [cout], layers in the order above (encoder, then solver).
  * ------------------------------------------------------------------------- */
-int cnn_create(cnn_model** out, int levels, const int* widths);
+/* Create the network with seeded He-normal initial weights (cnn_init_params with gain
+ * 0.5: the half-scale initialisation the training starts from) and zero biases. */
+int cnn_create(cnn_model** out, int levels, const int* widths, unsigned long long seed);
 void cnn_destroy(cnn_model* net);
 long long cnn_num_params(const cnn_model* net);
 /* Load / read the FP32 parameters (host or device pointer, n = cnn_num_params). */
@@ -261,6 +264,58 @@ int cnn_adam_reset(cnn_model* net);
  * preconditioned GMRES steps count as much as the large ones.  HELM_EINVAL for
  * other kinds. */
 int cnn_set_loss(cnn_model* net, int kind);
+
+/* ---- retraining inside the library: Alg. 2 of Sec. 4.2, one unit per call ----------
+ * The context (created with the network) owns a dataset of (residual, error) pairs of
+ * its medium and a schedule:
+ *   - the first cnn_retrain_step builds initial_size pairs by Eq. 4.3 (x ~ CN(0, 1),
+ *     b = H x, x~ after k V-cycle-preconditioned FGMRES steps, k uniform on
+ *     [1, max_gmres_steps], pair (b - H x~, x - x~)); pair i has frequency index i mod nfreq;
+ *   - every call trains on the next `batch` pairs of the current epoch (a fresh
+ *     permutation per epoch; the last batch of an epoch may be shorter): one Adam step
+ *     of cnn_train_step with learning rate lr (the caller schedules lr);
+ *   - at the end of each of the first data_epochs epochs every pair gets a refined
+ *     partner (cnn_refine_samples: the network's estimate followed by one preconditioned
+ *     GMRES step), doubling the dataset: 128 -> 1024 pairs over 3 epochs by default.
+ * Steps continue past `epochs` on the full dataset; cnn_retrain_state reports done = 1 then.
+ * Random draws (x, k, the permutations) come from a counter-based splitmix64 stream of
+ * `seed` (Steele, Lea and Flood 2014), so a run is reproducible.  The dataset takes
+ * 2 x 8 bytes per grid point per pair (8.6 GB for 1024 pairs of 1024 x 512). */
+typedef struct {
+    int initial_size;            /* pairs of the initial dataset, Eq. 4.3            (128) */
+    int data_epochs;             /* epochs that end with the data step of Alg. 2       (3) */
+    int epochs;                  /* epochs of the schedule                             (30) */
+    int max_gmres_steps;         /* largest step count of Eq. 4.3 (<= restart)          (10) */
+    int literal;                 /* 1: Alg. 2's pair as printed (H e~, e~); 0: residual-correction
+                                    pair (r - H e~, e - e~)                              (0) */
+    unsigned long long seed;     /* generator seed                                        (3) */
+} cnn_retrain_opts;
+void cnn_retrain_default_opts(cnn_retrain_opts* opts);
+/* (Re)start the schedule with the given options (NULL: defaults), dropping any dataset.
+ * HELM_EINVAL without a network or for out-of-range options; HELM_ENOMEM if the dataset
+ * does not fit.  cnn_retrain_step starts with the defaults when this was not called. */
+int cnn_retrain_begin(helm_ctx* ctx, const cnn_retrain_opts* opts);
+/* One unit of Alg. 2 (see above); loss_out (host, may be NULL) receives the batch loss of
+ * Eq. 4.2 (or its relative form, cnn_set_loss) before the Adam step.  The context must
+ * have been created with `net`; 1 <= batch <= max_rhs. */
+int cnn_retrain_step(cnn_model* net, helm_ctx* ctx, int batch, float lr, float* loss_out);
+/* out6 = {epochs completed, pairs of the current epoch trained on, dataset size,
+ * Adam steps taken, done (epochs reached), dataset capacity}; zeros before the first step. */
+int cnn_retrain_state(const helm_ctx* ctx, long long* out6);
+/* Copy pairs first .. first + n - 1 of the dataset (complex64 [n][nz][nx], host or
+ * device) and their frequency indices (host int32 [n], may be NULL). */
+int cnn_retrain_pairs(helm_ctx* ctx, int first, int n, helm_c64* r_out, helm_c64* e_out, int* freq_out);
+
+/* ---- checkpoints of the network (trained weights outlive the process) ----------------
+ * File: "HELMCNN1", then little-endian u32 version (1), u32 levels, u32 widths[8] (unused
+ * slots 0), i64 number of parameters, i64 Adam steps, u32 flags (bit 0: Adam moments
+ * follow), u32 loss kind, u64 FNV-1a checksum of the float payload, then the FP32
+ * parameters (cnn_set_params layout) and, with bit 0, the Adam moments m and v.
+ * cnn_load creates the network the file describes (the architecture comes from the
+ * header) and returns HELM_EINVAL for a missing, truncated, corrupted (checksum) or
+ * foreign file; cnn_save returns HELM_EINVAL if the file cannot be written. */
+int cnn_save(const cnn_model* net, const char* path);
+int cnn_load(cnn_model** out, const char* path);
 
 /* One 3x3 convolution layer of the network, FP32 in and out (rounded to BF16 inside,
  * FP32 accumulation on the tensor cores, output rounded to BF16 then widened):

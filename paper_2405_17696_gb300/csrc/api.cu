@@ -482,6 +482,7 @@ void helm_default_opts(helm_opts* o) {
     o->precond = HELM_PC_MG;
     o->max_rhs = 256;
     o->cnn_vcycle = 2;
+    o->autotune = 0;
     o->stream = nullptr;
 }
 
@@ -490,6 +491,7 @@ void helm_destroy(helm_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     cnn_ctx_free(c);
+    cnn_retrain_free(c);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     for (void* p : c->allocations) cudaFree(p);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -618,6 +620,8 @@ int helm_setup(helm_ctx** out, const float* kappa, const float* gamma, int nx, i
         if ((st = launch_galerkin(c, l))) return fail(st);
     // network context features for every frequency (Eq. 3.13, once per medium)
     if (c->net && (st = cnn_ctx_setup(c))) return fail(st);
+    // tiling of every convolution shape of the solver pass, timed on this device
+    if (c->net && o.autotune && (st = cnn_autotune(c, c->cap, nullptr))) return fail(st);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
         set_error(std::string("setup failed: ") + cudaGetErrorString(cudaGetLastError()));
         return fail(HELM_ECUDA);

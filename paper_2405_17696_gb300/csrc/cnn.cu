@@ -16,6 +16,9 @@
 // order encoder then solver as listed above.
 #include <cuda_bf16.h>
 
+#include <cstdio>
+#include <cstring>
+
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -667,8 +670,9 @@ int cnn_autotune(helm_ctx* c, int nrhs, int* n_shapes) {
 
 void cnn_autotune_reset(void) { conv_tune_reset(); }
 
-int cnn_create(cnn_model** out, int levels, const int* widths) {
-    set_error("");
+namespace {
+// the network without initial weights (all zero)
+int create_zero(cnn_model** out, int levels, const int* widths) {
     if (!out || levels < 2 || levels > 6 || !widths) { set_error("cnn_create: invalid argument"); return HELM_EINVAL; }
     for (int l = 0; l < levels; ++l)
         if (widths[l] < 16 || widths[l] > 128 || widths[l] % 16) {
@@ -694,6 +698,20 @@ int cnn_create(cnn_model** out, int levels, const int* widths) {
         cudaMemset(l.b, 0, (size_t)l.npad * sizeof(float));
     }
     if (cudaDeviceSynchronize() != cudaSuccess) { set_error("cnn_create: device error"); cnn_destroy(m); return HELM_ECUDA; }
+    *out = m;
+    return HELM_OK;
+}
+}  // namespace
+
+int cnn_create(cnn_model** out, int levels, const int* widths, unsigned long long seed) {
+    set_error("");
+    cnn_model* m = nullptr;
+    HELM_TRY(create_zero(&m, levels, widths));
+    const int s = cnn_init_params(m, seed, 0.5f);
+    if (s) {
+        cnn_destroy(m);
+        return s;
+    }
     *out = m;
     return HELM_OK;
 }
@@ -883,6 +901,128 @@ int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, 
     cudaFree(fx0); cudaFree(fx1); cudaFree(fw); cudaFree(fb); cudaFree(fr); cudaFree(fy); cudaFree(bp);
     cudaFree(bx0); cudaFree(bx1); cudaFree(bw); cudaFree(br); cudaFree(by); cudaFree(err);
     return s;
+}
+
+// ---- checkpoints ------------------------------------------------------------
+namespace {
+
+constexpr char CKPT_MAGIC[8] = {'H', 'E', 'L', 'M', 'C', 'N', 'N', '1'};
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t levels;
+    uint32_t widths[8];
+    int64_t nparams;
+    int64_t adam_t;
+    uint32_t flags;
+    uint32_t loss_kind;
+    uint64_t checksum;
+};
+
+// FNV-1a, 64-bit (Fowler, Noll, Vo)
+uint64_t fnv1a(const void* data, size_t n, uint64_t h = 0xcbf29ce484222325ull) {
+    const unsigned char* p = static_cast<const unsigned char*>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+}  // namespace
+
+int cnn_save(const cnn_model* m, const char* path) {
+    set_error("");
+    if (!m || !path) { set_error("cnn_save: null argument"); return HELM_EINVAL; }
+    const size_t n = (size_t)m->nparams;
+    const bool adam = m->adam_m && m->adam_v;
+    std::vector<float> buf(n * (adam ? 3 : 1));
+    HELM_CK(cudaMemcpy(buf.data(), m->master, n * sizeof(float), cudaMemcpyDeviceToHost));
+    if (adam) {
+        HELM_CK(cudaMemcpy(buf.data() + n, m->adam_m, n * sizeof(float), cudaMemcpyDeviceToHost));
+        HELM_CK(cudaMemcpy(buf.data() + 2 * n, m->adam_v, n * sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    CkptHeader h{};
+    std::memcpy(h.magic, CKPT_MAGIC, 8);
+    h.version = 1;
+    h.levels = (uint32_t)m->levels;
+    for (int l = 0; l < m->levels && l < 8; ++l) h.widths[l] = (uint32_t)m->widths[l];
+    h.nparams = m->nparams;
+    h.adam_t = adam ? m->adam_t : 0;
+    h.flags = adam ? 1u : 0u;
+    h.loss_kind = (uint32_t)m->loss_kind;
+    h.checksum = fnv1a(buf.data(), buf.size() * sizeof(float));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) { set_error(std::string("cnn_save: cannot open ") + path); return HELM_EINVAL; }
+    const bool ok = std::fwrite(&h, sizeof h, 1, f) == 1 &&
+                    std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    const bool closed = std::fclose(f) == 0;
+    if (!ok || !closed) { set_error(std::string("cnn_save: write failed: ") + path); return HELM_EINVAL; }
+    return HELM_OK;
+}
+
+int cnn_load(cnn_model** out, const char* path) {
+    set_error("");
+    if (!out || !path) { set_error("cnn_load: null argument"); return HELM_EINVAL; }
+    *out = nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) { set_error(std::string("cnn_load: cannot open ") + path); return HELM_EINVAL; }
+    CkptHeader h{};
+    if (std::fread(&h, sizeof h, 1, f) != 1 || std::memcmp(h.magic, CKPT_MAGIC, 8) != 0 || h.version != 1 ||
+        h.levels < 2 || h.levels > 6 || (h.flags & ~1u) || h.loss_kind > 1) {
+        std::fclose(f);
+        set_error(std::string("cnn_load: not a network checkpoint of this library: ") + path);
+        return HELM_EINVAL;
+    }
+    // the whole file is checked on the host before anything touches the device
+    int widths[8];
+    cnn_model spec;
+    spec.levels = (int)h.levels;
+    for (int l = 0; l < 8; ++l) widths[l] = (int)h.widths[l];
+    bool widths_ok = true;
+    for (int l = 0; l < spec.levels; ++l)
+        widths_ok = widths_ok && widths[l] >= 16 && widths[l] <= 128 && widths[l] % 16 == 0;
+    if (widths_ok) {
+        spec.widths.assign(widths, widths + spec.levels);
+        build_specs(&spec);
+    }
+    if (!widths_ok || h.nparams != spec.nparams) {
+        std::fclose(f);
+        set_error("cnn_load: the header's architecture and parameter count do not match");
+        return HELM_EINVAL;
+    }
+    const size_t n = (size_t)spec.nparams;
+    const bool adam = h.flags & 1u;
+    std::vector<float> buf(n * (adam ? 3 : 1));
+    const bool ok = std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    unsigned char extra;
+    const bool at_end = std::fread(&extra, 1, 1, f) == 0;
+    std::fclose(f);
+    if (!ok || !at_end || fnv1a(buf.data(), buf.size() * sizeof(float)) != h.checksum) {
+        set_error(std::string("cnn_load: truncated or corrupted checkpoint: ") + path);
+        return HELM_EINVAL;
+    }
+    cnn_model* m = nullptr;
+    int s = create_zero(&m, (int)h.levels, widths);
+    if (s) return s;
+    s = cnn_set_params(m, buf.data(), m->nparams);
+    if (!s) s = cnn_set_loss(m, (int)h.loss_kind);
+    if (!s && adam) {
+        s = cnn_adam_reset(m);
+        if (!s && (cudaMemcpy(m->adam_m, buf.data() + n, n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+                   cudaMemcpy(m->adam_v, buf.data() + 2 * n, n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)) {
+            set_error("cnn_load: Adam state upload failed");
+            s = HELM_ECUDA;
+        }
+        if (!s) m->adam_t = h.adam_t;
+    }
+    if (s) {
+        cnn_destroy(m);
+        return s;
+    }
+    *out = m;
+    return HELM_OK;
 }
 
 }  // extern "C"

@@ -252,6 +252,8 @@ struct Level {
     float2* t = nullptr;        // Jacobi partner    [cap][nz][nx]
 };
 
+struct RetrainState;   // cnn_retrain.cu: the dataset and schedule of cnn_retrain_step
+
 }  // namespace helm
 
 struct helm_ctx {
@@ -304,6 +306,7 @@ struct helm_ctx {
     int cnn_nact = -1;
     std::vector<void*> cnn_arena;    // one activation buffer per convolution of the solver pass
     std::vector<size_t> cnn_arena_bytes;
+    helm::RetrainState* retrain = nullptr;   // Alg. 2 dataset and schedule (cnn_retrain_step)
 };
 
 namespace helm {
@@ -375,5 +378,6 @@ int cnn_ctx_setup(helm_ctx* c);      // allocate buffers and run the encoder for
 void cnn_ctx_free(helm_ctx* c);
 int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const int* mask, int with_vcycle);
 int cnn_ctx_compact(helm_ctx* c, int nb);   // list the RHS still running (flags in cnn_act_host)
+void cnn_retrain_free(helm_ctx* c);         // cnn_retrain.cu
 
 }  // namespace helm

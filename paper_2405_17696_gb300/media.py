@@ -37,6 +37,52 @@ def rng(seed: int) -> np.random.Generator:
 
 
 # --------------------------------------------------------------------------
+# counter-based splitmix64 streams (the draws the library makes itself when it
+# builds training data, reproduced here from the generator's published definition:
+# Steele, Lea and Flood, OOPSLA 2014)
+# --------------------------------------------------------------------------
+_SM_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+
+
+def _sm_mix(z):
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def _sm_uniform(key, n):
+    """u in (0, 1) from counter n of the stream with key `key`."""
+    with np.errstate(over="ignore"):
+        z = _sm_mix(np.uint64(key) + np.asarray(n, dtype=np.uint64) * _SM_GAMMA)
+    return ((z >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
+def splitmix_key(seed: int, stream: int) -> np.uint64:
+    with np.errstate(over="ignore"):
+        return _sm_mix(np.uint64(seed) + np.uint64(stream) * _SM_GAMMA)
+
+
+def splitmix_complex_normal(first: int, n: int, npts: int, seed: int) -> np.ndarray:
+    """x ~ CN(0, 1) of pairs first .. first + n - 1 (npts nodes each) of the training-data
+    stream (stream 1): Box-Muller on the uniforms of counters 2q + 1 and 2q + 2, q = i npts + p."""
+    key = splitmix_key(seed, 1)
+    q = np.arange(first * npts, (first + n) * npts, dtype=np.uint64)
+    u1 = _sm_uniform(key, np.uint64(2) * q + np.uint64(1))
+    u2 = _sm_uniform(key, np.uint64(2) * q + np.uint64(2))
+    rho = np.sqrt(-np.log(u1))
+    x = (rho * np.cos(2.0 * np.pi * u2) + 1j * rho * np.sin(2.0 * np.pi * u2)).astype(np.complex64)
+    return x.reshape(n, npts)
+
+
+def splitmix_step_counts(n: int, seed: int, kmax: int) -> np.ndarray:
+    """GMRES step counts 1 + floor(u kmax) of pairs 0 .. n - 1 (stream 2, counter i + 1)."""
+    u = _sm_uniform(splitmix_key(seed, 2), np.arange(1, n + 1, dtype=np.uint64))
+    return np.minimum(1 + np.floor(u * kmax).astype(np.int64), kmax).astype(np.int32)
+
+
+# --------------------------------------------------------------------------
 # smoothing used to shape the media (input construction only)
 # --------------------------------------------------------------------------
 

@@ -38,7 +38,12 @@ class helm_opts(ctypes.Structure):
                 ("pre", ctypes.c_int), ("post", ctypes.c_int), ("jacobi_w", ctypes.c_float),
                 ("sl_beta", ctypes.c_float), ("sl_include_gamma", ctypes.c_int), ("coarse_kind", ctypes.c_int),
                 ("coarse_iters", ctypes.c_int), ("precond", ctypes.c_int), ("max_rhs", ctypes.c_int),
-                ("cnn_vcycle", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("cnn_vcycle", ctypes.c_int), ("autotune", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class cnn_retrain_opts(ctypes.Structure):
+    _fields_ = [("initial_size", ctypes.c_int), ("data_epochs", ctypes.c_int), ("epochs", ctypes.c_int),
+                ("max_gmres_steps", ctypes.c_int), ("literal", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
 
 
 class helm_stats(ctypes.Structure):
@@ -69,7 +74,7 @@ def _load():
     lib.helm_vcycle.restype = ip
     lib.fwi_misfit_grad.argtypes = [vp, vp, ip, vp, ip, vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double), vp]
     lib.fwi_misfit_grad.restype = ip
-    lib.cnn_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(ctypes.c_int)]
+    lib.cnn_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(ctypes.c_int), ctypes.c_ulonglong]
     lib.cnn_create.restype = ip
     lib.cnn_destroy.argtypes = [vp]
     lib.cnn_destroy.restype = None
@@ -119,6 +124,20 @@ def _load():
     lib.cnn_conv_last_launch.restype = None
     lib.cnn_conv_launch_counts.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.cnn_conv_launch_counts.restype = None
+    lib.cnn_retrain_default_opts.argtypes = [ctypes.POINTER(cnn_retrain_opts)]
+    lib.cnn_retrain_default_opts.restype = None
+    lib.cnn_retrain_begin.argtypes = [vp, ctypes.POINTER(cnn_retrain_opts)]
+    lib.cnn_retrain_begin.restype = ip
+    lib.cnn_retrain_step.argtypes = [vp, vp, ip, fp, ctypes.POINTER(ctypes.c_float)]
+    lib.cnn_retrain_step.restype = ip
+    lib.cnn_retrain_state.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    lib.cnn_retrain_state.restype = ip
+    lib.cnn_retrain_pairs.argtypes = [vp, ip, ip, vp, vp, ctypes.POINTER(ctypes.c_int)]
+    lib.cnn_retrain_pairs.restype = ip
+    lib.cnn_save.argtypes = [vp, ctypes.c_char_p]
+    lib.cnn_save.restype = ip
+    lib.cnn_load.argtypes = [ctypes.POINTER(vp), ctypes.c_char_p]
+    lib.cnn_load.restype = ip
     lib.helm_destroy.argtypes = [vp]
     lib.helm_destroy.restype = None
     lib.helm_last_error.argtypes = []
@@ -311,11 +330,57 @@ def helm_set_graphs(ctx, on: bool):
 # encoder-solver network
 # --------------------------------------------------------------------------
 
-def cnn_create(levels: int, widths):
+def cnn_create(levels: int, widths, seed: int = 2):
+    """The network with seeded half-scale He-normal weights (seed 2 is the library's CNN stream)."""
     w = (ctypes.c_int * levels)(*widths)
     net = ctypes.c_void_p()
-    _check(lib.cnn_create(ctypes.byref(net), levels, w), "cnn_create")
+    _check(lib.cnn_create(ctypes.byref(net), levels, w, seed), "cnn_create")
     return net
+
+
+def cnn_save(net, path: str):
+    _check(lib.cnn_save(net, os.fsencode(path)), "cnn_save")
+
+
+def cnn_load(path: str):
+    net = ctypes.c_void_p()
+    _check(lib.cnn_load(ctypes.byref(net), os.fsencode(path)), "cnn_load")
+    return net
+
+
+def cnn_retrain_default_opts(**overrides) -> cnn_retrain_opts:
+    o = cnn_retrain_opts()
+    lib.cnn_retrain_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def cnn_retrain_begin(ctx, **opts):
+    o = cnn_retrain_default_opts(**opts)
+    _check(lib.cnn_retrain_begin(ctx, ctypes.byref(o)), "cnn_retrain_begin")
+
+
+def cnn_retrain_step(net, ctx, batch: int, lr: float) -> float:
+    loss = ctypes.c_float(0.0)
+    _check(lib.cnn_retrain_step(net, ctx, batch, lr, ctypes.byref(loss)), "cnn_retrain_step")
+    return float(loss.value)
+
+
+def cnn_retrain_state(ctx) -> dict:
+    v = (ctypes.c_longlong * 6)()
+    _check(lib.cnn_retrain_state(ctx, v), "cnn_retrain_state")
+    return dict(zip(("epoch", "pos", "size", "steps", "done", "capacity"), (int(x) for x in v)))
+
+
+def cnn_retrain_pairs(ctx, first: int, n: int, r_out, e_out):
+    """Copies pairs first .. first + n - 1 of the dataset; returns their frequency indices."""
+    f = np.zeros(max(n, 1), dtype=np.int32)
+    _check(lib.cnn_retrain_pairs(ctx, first, n, _ptr(r_out, "complex64"), _ptr(e_out, "complex64"),
+                                 f.ctypes.data_as(ctypes.POINTER(ctypes.c_int))), "cnn_retrain_pairs")
+    return f[:n]
 
 
 def cnn_destroy(net):

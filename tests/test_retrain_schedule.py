@@ -12,29 +12,39 @@ from paper_2405_17696_gb300 import retrain as RT  # noqa: E402
 
 
 class FakeNative:
+    """The schedule cnn_retrain_step documents (include/helm.h), on the host: the
+    first step builds the initial pairs, each step trains on the next batch of the
+    epoch, and the first data_epochs epochs end by doubling the dataset."""
+
     def __init__(self):
-        self.made = 0
-        self.refined = 0
         self.steps = []
-
-    def cnn_make_samples(self, ctx, x, iters, r, e, nb, fidx):
-        assert x.shape[0] == nb and r.shape[0] == nb and all(1 <= int(i) <= 10 for i in iters)
-        r.fill_(1.0)
-        e.fill_(2.0)
-        self.made += nb
-
-    def cnn_refine_samples(self, ctx, r, e, r2, e2, nb, fidx, literal):
-        assert torch.all(r == 1.0)          # refines existing pairs only
-        r2.copy_(r)
-        e2.copy_(e)
-        self.refined += nb
+        self.lrs = []
+        self.begun = None
 
     def cnn_set_loss(self, net, kind):
         self.loss_kind = kind
 
-    def cnn_train_step(self, net, ctx, r, e, nb, lr, fidx):
-        assert torch.all(r == 1.0) and torch.all(e == 2.0)
+    def cnn_retrain_begin(self, ctx, **opts):
+        self.begun = opts
+        self.size, self.epoch, self.pos, self.nsteps = 0, 0, 0, 0
+
+    def cnn_retrain_state(self, ctx):
+        return {"epoch": self.epoch, "pos": self.pos, "size": self.size, "steps": self.nsteps,
+                "done": int(self.epoch >= self.begun["epochs"]), "capacity": 0}
+
+    def cnn_retrain_step(self, net, ctx, batch, lr):
+        if self.size == 0:
+            self.size = self.begun["initial_size"]
+        nb = min(batch, self.size - self.pos)
         self.steps.append(nb)
+        self.lrs.append(lr)
+        self.pos += nb
+        self.nsteps += 1
+        if self.pos >= self.size:
+            self.pos = 0
+            self.epoch += 1
+            if self.epoch <= self.begun["data_epochs"]:
+                self.size *= 2
         return 1.0 / len(self.steps)
 
 
@@ -63,10 +73,17 @@ def test_schedule_matches_the_paper_budget():
 
 
 def test_driver_follows_the_schedule():
-    cfg = RT.RetrainConfig(initial_size=8, data_epochs=3, epochs=5, batch=4)
+    cfg = RT.RetrainConfig(initial_size=8, data_epochs=3, epochs=5, batch=4, lr=1e-3, lr_final=1e-4,
+                           warmup_steps=4)
     fake = FakeNative()
-    hist = RT.retrain(fake, None, None, nx=4, nz=2, cfg=cfg, device="cpu", chunk=3)
-    assert fake.made == 8
-    assert fake.refined == 8 + 16 + 32
+    hist = RT.retrain(fake, None, None, cfg=cfg)
+    assert fake.begun["initial_size"] == 8 and fake.begun["data_epochs"] == 3 and fake.begun["epochs"] == 5
     assert hist.dataset_sizes == [8, 16, 32, 64, 64]
     assert hist.steps == sum(n for _, n in RT.schedule(cfg)) == len(fake.steps)
+    assert fake.steps == [4] * hist.steps
+    # warm-up ramp over the first 4 steps, then the geometric decay per epoch down to lr_final
+    decay = (1e-4 / 1e-3) ** (1 / 4)
+    assert fake.lrs[0] == pytest.approx(1e-3 / 4) and fake.lrs[1] == pytest.approx(1e-3 / 2)   # epoch 0
+    assert fake.lrs[4] == pytest.approx(1e-3 * decay)                                         # epoch 1
+    assert fake.lrs[-1] == pytest.approx(1e-4)
+    assert len(hist.epoch_loss) == 5
