@@ -326,6 +326,35 @@ int cnn_load(cnn_model** out, const char* path);
 int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, int nb, int hin, int win,
                 const float* w, const float* bias, int cout, const float* res, int mode, int relu, float* y);
 
+/* Backward pass of one 3x3 convolution layer (for parity tests and offline use):
+ * for y = conv(concat(x0, x1)) (the layout of cnn_conv3x3, mode 0 same / 1 stride-2 down /
+ * 2 nearest-x2 up) and an upstream gradient gy FP32 [nb][hout][wout][cout] (any ReLU mask
+ * already applied), the input gradients gx0 [nb][hin][win][c0] and gx1 ([nb or 1 when
+ * x1_bcast][hin][win][c1], summed over the images for a broadcast x1), the weight gradient
+ * dw [cout][9][c0 + c1] and the bias gradient db [cout].  Inputs, weights and gy are rounded
+ * to BF16; the products accumulate in FP32 on the tensor cores (the weight gradient on the
+ * path of cnn_set_wgrad_path).  Outputs (host or device, any may be NULL) are overwritten.
+ * c1 > 0 needs c0 % 16 == 0.  HELM_EINVAL for bad sizes. */
+int cnn_conv3x3_backward(const float* x0, int c0, const float* x1, int c1, int x1_bcast, int nb, int hin, int win,
+                         const float* w, int cout, int mode, const float* gy, float* gx0, float* gx1, float* dw,
+                         float* db);
+/* Which kernel computes the weight gradients of the backward pass: 0 (default) the
+ * tensor cores (K = output pixels; per-CTA partial sums added in a fixed order, so the
+ * result does not change from run to run), 1 the FP32 CUDA-core kernel (one atomic add
+ * per weight per CTA; also the fallback for a layer the tensor-core kernel does not
+ * take).  Process-wide.  HELM_EINVAL for any other value. */
+int cnn_set_wgrad_path(int path);
+/* Tile plan of the tensor-core weight gradient for a layer shape, computed on the host
+ * (no GPU needed), for checking its bounds: mode 0/1/2 as above, c0, c1 input channels
+ * (multiples of 8), npad output channels (a multiple of 16, at most 128), hin x win input
+ * grid, nb images, sms multiprocessors (0: 148).  out20 = {K tiles, tile width, tile rows,
+ * pixels per K tile, tiles along x, along y, output parities, input chunks per tap,
+ * chunks from x0, chunks of the gradient, taps per group, groups, largest chunk count of
+ * a group, bytes per staged plane, bytes per stage, stages, slack bytes after the ring,
+ * TMEM columns, CTAs along K, dynamic shared memory bytes}.  HELM_EINVAL when the kernel
+ * does not take the layer. */
+int cnn_wgrad_plan(int mode, int c0, int c1, int npad, int hin, int win, int nb, int sms, long long* out20);
+
 /* Which kernel runs the convolutions.  path 0 (default): the TMA halo-tile
  * kernel (the input tile of a CTA staged once, the nine taps read as shifted
  * shared-memory views), falling back to the gather kernel for a layer it

@@ -123,6 +123,67 @@ def conv_backward(x, w, gy, mode: str):
     return dx, dw, db
 
 
+def _src_point(i: int, n_in: int, mode: str, d: int):
+    """Input coordinate read by output coordinate i through tap offset d (None outside)."""
+    if mode == "same":
+        v = i + d
+    elif mode == "down":
+        v = 2 * i + 1 + d
+    else:
+        u = i + d
+        return u // 2 if 0 <= u < 2 * n_in else None
+    return v if 0 <= v < n_in else None
+
+
+def conv_forward_points(x, w, b, mode: str, points):
+    """y at the output nodes points = [(n, Y, X)], one by one from the definition
+    y[n, Y, X, co] = b[co] + sum over taps t and input channels of w[co, t, ci] x[n, src_t(Y, X), ci]."""
+    _, ny, nx, _ = x.shape
+    out = np.zeros((len(points), w.shape[0]))
+    for k, (n, Y, X) in enumerate(points):
+        acc = np.array(b, dtype=np.float64)
+        for t in range(9):
+            iy, ix = _src_point(Y, ny, mode, t // 3 - 1), _src_point(X, nx, mode, t % 3 - 1)
+            if iy is not None and ix is not None:
+                acc = acc + w[:, t, :] @ x[n, iy, ix, :]
+        out[k] = acc
+    return out
+
+
+def conv_input_grad_points(gy, w, in_shape, mode: str, points):
+    """The input gradient of conv_forward at the input nodes points = [(n, y, x)]: the sum
+    over every output node (Y, X) and tap t with src_t(Y, X) = (y, x) of w[:, t, :]^T gy[n, Y, X]."""
+    _, ny, nx, _ = in_shape
+    _, my, mx, _ = gy.shape
+    out = np.zeros((len(points), w.shape[2]))
+    for k, (n, y, x) in enumerate(points):
+        acc = np.zeros(w.shape[2])
+        for t in range(9):
+            dy, dx = t // 3 - 1, t % 3 - 1
+            Ys = [Y for Y in range(max(0, (y - 2) // 2 - 2), min(my, 2 * y + 4)) if _src_point(Y, ny, mode, dy) == y]
+            Xs = [X for X in range(max(0, (x - 2) // 2 - 2), min(mx, 2 * x + 4)) if _src_point(X, nx, mode, dx) == x]
+            for Y in Ys:
+                for X in Xs:
+                    acc = acc + w[:, t, :].T @ gy[n, Y, X, :]
+        out[k] = acc
+    return out
+
+
+def conv_weight_grad(x, gy, mode: str):
+    """(dw, db) of conv_forward, tap by tap: dw[co, t, ci] = sum over output nodes p of
+    gy[p, co] x[src_t(p), ci] (zero outside the input), db = sum over p of gy[p]."""
+    B, ny, nx, cin = x.shape
+    _, my, mx, cout = gy.shape
+    dw = np.zeros((cout, 9, cin))
+    for t in range(9):
+        dy, dx = t // 3 - 1, t % 3 - 1
+        iy, oky = _src_index(ny, my, mode, dy)
+        ix, okx = _src_index(nx, mx, mode, dx)
+        xt = x[:, iy][:, :, ix] * (oky[:, None] & okx[None, :])[None, :, :, None]
+        dw[:, t, :] = np.tensordot(gy, xt, axes=([0, 1, 2], [0, 1, 2]))
+    return dw, gy.sum(axis=(0, 1, 2))
+
+
 def relu(x):
     return np.maximum(x, 0.0)
 
@@ -306,11 +367,16 @@ def network_forward(P, specs, enc_in, sol_in, quantize=None):
     return out, tape
 
 
-def backward(P, specs, tape, g_out, wrt=None):
+def backward(P, specs, tape, g_out, wrt=None, grad_quantize=None):
     """Reverse pass over the tape for the upstream gradient g_out of the last
     output.  Returns {name: (dw, db)} and, if ``wrt`` is given, the gradient
     with respect to that tape input.  An array used by several consumers
-    (skip connections, context features) sums their gradients."""
+    (skip connections, context features) sums their gradients.
+    ``grad_quantize`` (e.g. bf16_round) is applied to the (masked) output gradient
+    of every convolution before its weight and input gradients are formed, as a
+    BF16 network does with its gradient operand; the gradient handed on through a
+    skip connection is not rounded."""
+    qg = grad_quantize if grad_quantize is not None else (lambda a: a)
     grads = {name: (np.zeros_like(P[name][0]), np.zeros_like(P[name][1])) for name, *_ in specs}
     acc = {}
 
@@ -332,7 +398,7 @@ def backward(P, specs, tape, g_out, wrt=None):
                 continue
             if act:
                 g = g * (out > 0)
-            dx, dw, db = conv_backward(x, P[name][0], g, mode)
+            dx, dw, db = conv_backward(x, P[name][0], qg(g), mode)
             gw, gb = grads[name]
             grads[name] = (gw + dw, gb + db)
             add(x, dx)
@@ -342,7 +408,7 @@ def backward(P, specs, tape, g_out, wrt=None):
             if g is None:
                 continue
             g = g * (out > 0)
-            dh, dw, db = conv_backward(h, P[prefix + ".b"][0], g, "same")
+            dh, dw, db = conv_backward(h, P[prefix + ".b"][0], qg(g), "same")
             gw, gb = grads[prefix + ".b"]
             grads[prefix + ".b"] = (gw + dw, gb + db)
             add(x, g)

@@ -99,9 +99,11 @@ def refine_samples(P, specs, kappa, gamma, omega, h, r, e, literal=False, params
     return refine_from_estimate(kappa, gamma, omega, h, r, e, e_net, literal, params)
 
 
-def loss_and_grad(P, specs, kappa, gamma, omega, h, r, e, quantize=None, relative=False):
+def loss_and_grad(P, specs, kappa, gamma, omega, h, r, e, quantize=None, relative=False, grad_quantize=None):
     """(loss, {name: (dw, db)}) of Eq. 4.2 for one batch of one medium/frequency;
-    relative=True weighs sample i by 1 / ||e_i||^2."""
+    relative=True weighs sample i by 1 / ||e_i||^2.  quantize rounds the inputs and
+    stored activations, grad_quantize the gradient operand of every convolution
+    (both bf16_round for a BF16 network)."""
     e_net, out, tape, rms = network_error(P, specs, kappa, gamma, omega, h, r, quantize)
     m = r.shape[0]
     e = np.asarray(e, dtype=np.complex128)
@@ -110,5 +112,5 @@ def loss_and_grad(P, specs, kappa, gamma, omega, h, r, e, quantize=None, relativ
     loss = float(np.sum(wt * np.sum(np.abs(d) ** 2, axis=(1, 2))) / m)
     s = (h * h) * rms[:, None, None] * wt[:, None, None]
     g_out = np.stack([2.0 * d.real * s / m, 2.0 * d.imag * s / m], axis=-1)
-    grads, _ = cnn.backward(P, specs, tape, g_out)
+    grads, _ = cnn.backward(P, specs, tape, g_out, grad_quantize=grad_quantize)
     return loss, grads

@@ -719,6 +719,7 @@ int cnn_create(cnn_model** out, int levels, const int* widths, unsigned long lon
 void cnn_destroy(cnn_model* m) {
     if (!m) return;
     cudaDeviceSynchronize();
+    if (m->wg_scratch) cudaFree(m->wg_scratch);
     for (void* p : m->allocations) cudaFree(p);
     delete m;
 }
@@ -900,6 +901,118 @@ int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, 
     }
     cudaFree(fx0); cudaFree(fx1); cudaFree(fw); cudaFree(fb); cudaFree(fr); cudaFree(fy); cudaFree(bp);
     cudaFree(bx0); cudaFree(bx1); cudaFree(bw); cudaFree(br); cudaFree(by); cudaFree(err);
+    return s;
+}
+
+// One layer's backward pass for parity tests: FP32 in and out (inputs, weights and
+// the upstream gradient rounded to BF16 inside), the same kernels as the network's
+// backward pass (tensor-core input gradient; weight gradient on the path chosen by
+// cnn_set_wgrad_path).  Outputs are overwritten; any may be NULL.
+int cnn_conv3x3_backward(const float* x0, int c0, const float* x1, int c1, int x1_bcast, int nb, int hin, int win,
+                         const float* w, int cout, int mode, const float* gy, float* gx0, float* gx1, float* dw,
+                         float* db) {
+    set_error("");
+    if (!x0 || !w || !gy || c0 < 1 || c1 < 0 || (c1 > 0 && (!x1 || c0 % 16)) || nb < 1 || hin < 1 || win < 1 ||
+        cout < 1 || cout > 128 || mode < 0 || mode > 2 || x1_bcast < 0 || x1_bcast > 1) {
+        set_error("cnn_conv3x3_backward: invalid argument");
+        return HELM_EINVAL;
+    }
+    const int cp0 = pad16(c0), cp1 = c1 ? pad16(c1) : 0, cin = c0 + c1, cinp = cp0 + cp1, npad = npad_of(cout);
+    const int hout = mode == 1 ? hin / 2 : (mode == 2 ? 2 * hin : hin);
+    const int wout = mode == 1 ? win / 2 : (mode == 2 ? 2 * win : win);
+    const int nb1 = c1 ? (x1_bcast ? 1 : nb) : 0;
+    const long long hwi = (long long)hin * win, hwo = (long long)hout * wout;
+    const long long nin = (long long)nb * hwi, nin1 = (long long)nb1 * hwi, nout = (long long)nb * hwo;
+    std::vector<void*> tmp;
+    int s = HELM_OK;
+    auto alloc = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (s == HELM_OK && cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+            (void)cudaGetLastError();
+            set_error("cnn_conv3x3_backward: out of device memory");
+            s = HELM_ENOMEM;
+            return nullptr;
+        }
+        tmp.push_back(p);
+        return p;
+    };
+    auto ck = [&](cudaError_t e) { if (e != cudaSuccess && s == HELM_OK) { set_error(cudaGetErrorString(e)); s = HELM_ECUDA; } };
+    float* fx0 = (float*)alloc(nin * c0 * sizeof(float));
+    float* fx1 = c1 ? (float*)alloc(nin1 * c1 * sizeof(float)) : nullptr;
+    float* fgy = (float*)alloc(nout * cout * sizeof(float));
+    auto* bx0 = (__nv_bfloat16*)alloc(nin * cp0 * sizeof(__nv_bfloat16));
+    auto* bx1 = c1 ? (__nv_bfloat16*)alloc(nin1 * cp1 * sizeof(__nv_bfloat16)) : nullptr;
+    auto* bg = (__nv_bfloat16*)alloc(nout * npad * sizeof(__nv_bfloat16));
+    auto* bw = (__nv_bfloat16*)alloc((size_t)npad * 9 * cinp * sizeof(__nv_bfloat16));
+    float* dW = (float*)alloc((size_t)cout * 9 * cin * sizeof(float));
+    float* dB = (float*)alloc((size_t)cout * sizeof(float));
+    int* err = (int*)alloc(sizeof(int));
+    if (s) { for (void* p : tmp) cudaFree(p); return s; }
+    ck(cudaMemset(err, 0, sizeof(int)));
+    ck(cudaMemset(dW, 0, (size_t)cout * 9 * cin * sizeof(float)));
+    ck(cudaMemset(dB, 0, (size_t)cout * sizeof(float)));
+    ck(cudaMemcpy(fx0, x0, nin * c0 * sizeof(float), cudaMemcpyDefault));
+    if (c1) ck(cudaMemcpy(fx1, x1, nin1 * c1 * sizeof(float), cudaMemcpyDefault));
+    ck(cudaMemcpy(fgy, gy, nout * cout * sizeof(float), cudaMemcpyDefault));
+    {
+        // weights: logical [cout][9][c0 + c1] -> padded BF16 [npad][9][cp0 + cp1]
+        std::vector<float> hw((size_t)cout * 9 * cin);
+        ck(cudaMemcpy(hw.data(), w, hw.size() * sizeof(float), cudaMemcpyDefault));
+        std::vector<__nv_bfloat16> hbw((size_t)npad * 9 * cinp, __float2bfloat16_rn(0.0f));
+        for (int co = 0; co < cout; ++co)
+            for (int t = 0; t < 9; ++t)
+                for (int ci = 0; ci < cin; ++ci) {
+                    const int cpi = ci < c0 ? ci : cp0 + (ci - c0);
+                    hbw[((size_t)co * 9 + t) * cinp + cpi] = __float2bfloat16_rn(hw[((size_t)co * 9 + t) * cin + ci]);
+                }
+        ck(cudaMemcpy(bw, hbw.data(), hbw.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+    }
+    if (!s) {
+        pack_channels_kernel<<<256, 256>>>(fx0, c0, cp0, bx0, nin, hwi);
+        if (c1) pack_channels_kernel<<<256, 256>>>(fx1, c1, cp1, bx1, nin1, hwi);
+        pack_channels_kernel<<<256, 256>>>(fgy, cout, npad, bg, nout, hwo);
+        ck(cudaGetLastError());
+    }
+    float* scratch = nullptr;
+    size_t scap = 0;
+    if (!s && (dw || db))
+        s = layer_wgrad(bx0, cp0, bx1, cp1, x1_bcast, nullptr, nb1, nb, hin, win, hout, wout, mode, bg, npad, cout,
+                        cin, dW, dB, &scratch, &scap, err, nullptr, nullptr);
+    // input gradients of the two parts, FP32 [n][cp] accumulated, then narrowed to [n][c]
+    for (int part = 0; part < 2 && !s; ++part) {
+        float* out = part ? gx1 : gx0;
+        const int c = part ? c1 : c0, cp = part ? cp1 : cp0;
+        if (!out || c == 0) continue;
+        float* target = (float*)alloc(nin * cp * sizeof(float));
+        auto* Wt = (__nv_bfloat16*)alloc((size_t)cp * 9 * npad * sizeof(__nv_bfloat16));
+        float* fine = mode == 2 ? (float*)alloc(nout * cp * sizeof(float)) : nullptr;
+        if (s) break;
+        ck(cudaMemset(target, 0, nin * cp * sizeof(float)));
+        if (!s) s = layer_dgrad(bg, npad, bw, cinp, part ? cp0 : 0, cp, mode, nb, hin, win, hout, wout, target, Wt,
+                                fine, err, nullptr, nullptr);
+        ck(cudaDeviceSynchronize());
+        if (s) break;
+        // narrow (and, for a broadcast x1, sum over the images) on the host
+        std::vector<float> h((size_t)nin * cp);
+        ck(cudaMemcpy(h.data(), target, h.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        const long long nimg = part && x1_bcast ? 1 : nb;
+        std::vector<float> o((size_t)nimg * hwi * c, 0.0f);
+        for (long long b = 0; b < nb; ++b)
+            for (long long q = 0; q < hwi; ++q)
+                for (int k = 0; k < c; ++k)
+                    o[((size_t)(nimg == 1 ? 0 : b) * hwi + q) * c + k] += h[((size_t)b * hwi + q) * cp + k];
+        ck(cudaMemcpy(out, o.data(), o.size() * sizeof(float), cudaMemcpyDefault));
+    }
+    ck(cudaDeviceSynchronize());
+    if (!s) {
+        int herr = 0;
+        ck(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (!s && herr) { set_error("cnn_conv3x3_backward: a tensor-core wait expired"); s = HELM_ETIMEOUT; }
+    }
+    if (!s && dw) ck(cudaMemcpy(dw, dW, (size_t)cout * 9 * cin * sizeof(float), cudaMemcpyDefault));
+    if (!s && db) ck(cudaMemcpy(db, dB, (size_t)cout * sizeof(float), cudaMemcpyDefault));
+    if (scratch) cudaFree(scratch);
+    for (void* p : tmp) cudaFree(p);
     return s;
 }
 

@@ -40,6 +40,8 @@ struct cnn_model {
     float* master = nullptr;      // flat FP32 parameters (device)
     int* err = nullptr;           // device error flag of the conv kernels
     std::vector<void*> allocations;
+    float* wg_scratch = nullptr;  // weight-gradient partial sums (grown on demand, freed with the model)
+    size_t wg_scratch_n = 0;
 };
 
 namespace helm {
@@ -249,6 +251,17 @@ class Runner {
     std::vector<void*> tmp_;
     bool ok_ = true;
 };
+
+// Backward pieces of one convolution layer (cnn_train.cu).
+// dW, db += weight and bias gradient (tensor cores, deterministic; CUDA-core path 1 or fallback)
+int layer_wgrad(const __nv_bfloat16* x0, int c0, const __nv_bfloat16* x1, int c1, int x1_bcast, const int* x1_map,
+                int nb1, int nb, int hin, int win, int hout, int wout, int mode, const __nv_bfloat16* g, int npad,
+                int cout, int cin, float* dW, float* db, float** scratch, size_t* scratch_cap, int* err,
+                cudaStream_t st, const helm_ctx* prof_ctx);
+// target += W^T g for input channels off .. off + cp - 1 (tensor cores)
+int layer_dgrad(const __nv_bfloat16* g, int npad, const __nv_bfloat16* W, int cin_pad, int off, int cp, int mode,
+                int nb, int hin, int win, int hout, int wout, float* target, __nv_bfloat16* Wt, float* fine, int* err,
+                cudaStream_t st, const helm_ctx* prof_ctx);
 
 inline int check_conv_error(cnn_model* m, cudaStream_t st) {
     int h = 0;

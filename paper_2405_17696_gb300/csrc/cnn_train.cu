@@ -5,7 +5,9 @@
 // Backward of one convolution y = act(W * x + b [+ res]) with upstream
 // gradient G_y (FP32):
 //   g      = G_y . [y > 0]  (BF16 operand; FP32 copy added to G_res for a ResNet skip)
-//   dW, db += sum over pixels of g (x) x_tap    (FP32, CUDA cores, tiled in shared memory)
+//   dW, db += sum over pixels of g (x) x_tap    (tensor cores, K = pixels, deterministic
+//            reduction over CTAs: k_wgrad_tc.cu; the FP32 CUDA-core kernel below is
+//            the second path, cnn_set_wgrad_path(1), and the fallback)
 //   G_x   += W^T * g   on the tensor cores with the same kernel as the forward:
 //            'same'  -> same-grid convolution with transposed, tap-flipped weights,
 //            'down'  -> the transpose-of-down gather mode with transposed weights,
@@ -22,8 +24,11 @@
 #include <unordered_set>
 #include <vector>
 
+#include <atomic>
+
 #include "cnn_internal.cuh"
 #include "reduce.cuh"
+#include "wgrad.cuh"
 
 namespace helm {
 namespace {
@@ -77,15 +82,19 @@ __global__ void sumpool_accum_kernel(const float* __restrict__ fine, int nb, int
     }
 }
 
-// G_ctx[map(b)] += tmp[b]   (context images shared by several samples)
+// G_ctx[f] += sum over the samples b that use context image f (map(b) == f, or f = 0
+// when bcast == 1) of tmp[b], summed in the order of b: one thread per context element,
+// no atomics, so that the gradient is the same on every run
 __global__ void reduce_to_context_kernel(const float* __restrict__ tmp, long long per_image, int nb,
-                                         const int* __restrict__ map, int bcast, float* __restrict__ gctx) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per_image * nb;
+                                         const int* __restrict__ map, int bcast, int nctx, float* __restrict__ gctx) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per_image * nctx;
          i += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(i / per_image);
-        const long long q = i - (long long)b * per_image;
-        const int f = bcast == 1 ? 0 : map[b];
-        atomicAdd(gctx + (long long)f * per_image + q, tmp[i]);
+        const int f = (int)(i / per_image);
+        const long long q = i - (long long)f * per_image;
+        float acc = 0.0f;
+        for (int b = 0; b < nb; ++b)
+            if ((bcast == 1 ? 0 : __ldg(map + b)) == f) acc += tmp[(long long)b * per_image + q];
+        gctx[i] += acc;
     }
 }
 
@@ -262,6 +271,129 @@ __global__ void __launch_bounds__(256) wgrad_kernel(WgArgs a, Wg2 w) {
     }
 }
 
+}  // namespace
+
+std::atomic<int> g_wgrad_path{0};   // 0: tensor cores (k_wgrad_tc.cu), 1: CUDA cores
+
+// Scratch of the tensor-core weight gradient (partial sums per CTA, bias partials),
+// grown on demand; *buf / *cap owned by the caller.
+int wgrad_scratch(float** buf, size_t* cap, size_t need) {
+    if (*cap >= need) return HELM_OK;
+    if (*buf) {
+        cudaFree(*buf);   // (synchronises the device: no kernel of ours is reading it)
+        *buf = nullptr;
+        *cap = 0;
+    }
+    if (cudaMalloc(buf, need * sizeof(float)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        *buf = nullptr;
+        set_error("out of device memory for the weight-gradient scratch");
+        return HELM_ENOMEM;
+    }
+    *cap = need;
+    return HELM_OK;
+}
+
+constexpr int WG_BIAS_SEGMENTS = 1184;
+
+// dW, db += the weight and bias gradient of one layer: g is the BF16 masked output
+// gradient (chunked layout, npad channels), x0 / x1 the layer's inputs.
+int layer_wgrad(const __nv_bfloat16* x0, int c0, const __nv_bfloat16* x1, int c1, int x1_bcast, const int* x1_map,
+                int nb1, int nb, int hin, int win, int hout, int wout, int mode, const __nv_bfloat16* g, int npad,
+                int cout, int cin, float* dW, float* db, float** scratch, size_t* scratch_cap, int* err,
+                cudaStream_t st, const helm_ctx* prof_ctx) {
+    if (g_wgrad_path.load() == 0) {
+        int sms = 0, dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            (void)cudaGetLastError();
+            sms = 148;
+        }
+        const WgradGeom geo = wgrad_plan(mode, c0, c1, npad, hin, win, hout, wout, nb, sms);
+        if (geo.ktiles > 0) {
+            const size_t part = (size_t)geo.splits * 9 * (size_t)(c0 + c1) * npad;
+            HELM_TRY(wgrad_scratch(scratch, scratch_cap, part + (size_t)WG_BIAS_SEGMENTS * npad));
+            WgradArgs wa;
+            wa.x0 = x0; wa.c0 = c0; wa.x1 = x1; wa.c1 = c1; wa.x1_bcast = x1_bcast; wa.x1_map = x1_map; wa.nb1 = nb1;
+            wa.nb = nb; wa.hin = hin; wa.win = win; wa.hout = hout; wa.wout = wout; wa.mode = mode;
+            wa.g = g; wa.npad = npad; wa.cout = cout; wa.cin = cin; wa.dW = dW; wa.db = db;
+            wa.partials = *scratch; wa.max_splits = geo.splits;
+            wa.bias_partials = *scratch + part; wa.max_bias_segments = WG_BIAS_SEGMENTS;
+            wa.err = err;
+            int s;
+            {
+                LaunchScope scope(prof_ctx, K_WGRAD);
+                s = launch_wgrad_tc(wa, st);
+            }
+            if (s != HELM_EINVAL) return s;
+        }
+    }
+    // CUDA-core path (and the fallback for a layer the tensor-core kernel does not take)
+    WgArgs a;
+    a.x0 = x0; a.c0 = c0; a.x1 = x1; a.c1 = c1; a.x1_bcast = x1_bcast; a.x1_map = x1_map;
+    a.nb = nb; a.hin = hin; a.win = win; a.hout = hout; a.wout = wout; a.mode = mode;
+    a.g = g; a.npad = npad; a.cout = cout; a.cin = cin; a.dW = dW; a.db = db;
+    Wg2 w;
+    if (mode == 1) { w.th = 4; w.tw = 32; } else { w.th = 8; w.tw = 32; }
+    w.tiles_x = (wout + w.tw - 1) / w.tw;
+    w.tiles_y = (hout + w.th - 1) / w.th;
+    if (mode == 0) { w.sh = w.th + 2; w.sw = w.tw + 2; }
+    else if (mode == 1) { w.sh = 2 * w.th + 1; w.sw = 2 * w.tw + 1; }
+    else { w.sh = w.th / 2 + 2; w.sw = w.tw / 2 + 2; }
+    const size_t np = (size_t)w.th * w.tw;
+    const size_t smem = std::max<size_t>(((size_t)(w.sh * w.sw + 1) * 16 + np * 16) * sizeof(float) +
+                                             np * 9 * sizeof(int), 32 * 76 * sizeof(float));
+    const unsigned gy = (unsigned)((c0 + c1 + 15) / 16), gz = (unsigned)(npad / 16);
+    const long long tiles = (long long)nb * w.tiles_x * w.tiles_y;
+    const long long gx = std::max<long long>(1, std::min<long long>(tiles, 1216 / (gy * gz)));
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        attr = true;
+    }
+    LaunchScope scope(prof_ctx, K_WGRAD);
+    wgrad_kernel<<<dim3((unsigned)gx, gy, gz), 256, smem, st>>>(a, w);
+    return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
+}
+
+// target += the input gradient W^T g of one input part (channels off .. off + cp - 1 of the
+// layer's padded input) on the tensor cores: 'same' -> same-grid convolution with
+// transposed, tap-flipped weights; 'down' -> the transpose-of-down mode; 'up' -> a
+// same-grid convolution on the fine grid, then a 2 x 2 sum.  target FP32 [nb][hin][win][cp];
+// Wt: scratch of cp x 9 x npad BF16; fine: scratch of nb x hout x wout x cp FP32 (mode 2).
+int layer_dgrad(const __nv_bfloat16* g, int npad, const __nv_bfloat16* W, int cin_pad, int off, int cp, int mode,
+                int nb, int hin, int win, int hout, int wout, float* target, __nv_bfloat16* Wt, float* fine, int* err,
+                cudaStream_t st, const helm_ctx* prof_ctx) {
+    {
+        LaunchScope scope(prof_ctx, K_CNN_IO);
+        transpose_weights_kernel<<<256, 256, 0, st>>>(W, npad, cin_pad, off, cp, mode == 1 ? 0 : 1, Wt);
+    }
+    ConvArgs ca;
+    ca.x0 = g; ca.c0 = npad; ca.x1 = nullptr; ca.c1 = 0; ca.x1_bcast = 0; ca.x1_map = nullptr;
+    ca.nb = nb; ca.w = Wt; ca.bias = nullptr; ca.res = nullptr; ca.npad = cp; ca.cstore = cp;
+    ca.relu = 0; ca.out_fp32 = 1; ca.accum = 1; ca.err = err;
+    ca.hin = hout; ca.win = wout;
+    if (mode == 0 || mode == 1) {
+        ca.hout = hin; ca.wout = win; ca.mode = mode == 0 ? 0 : 3; ca.y = target;
+        LaunchScope scope(prof_ctx, K_CONV);
+        return launch_conv3x3(ca, st);
+    }
+    const long long nout = (long long)nb * hout * wout;
+    if (cudaMemsetAsync(fine, 0, (size_t)nout * cp * sizeof(float), st) != cudaSuccess) return HELM_ECUDA;
+    ca.hout = hout; ca.wout = wout; ca.mode = 0; ca.y = fine;
+    int s;
+    {
+        LaunchScope scope(prof_ctx, K_CONV);
+        s = launch_conv3x3(ca, st);
+    }
+    if (s) return s;
+    LaunchScope scope(prof_ctx, K_CNN_IO);
+    sumpool_accum_kernel<<<1184, 256, 0, st>>>(fine, nb, hin, win, cp, target);
+    return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
+}
+
+namespace {
+
 // wt[b] = 1 / ||e_b||^2 (one block per sample; FP32 partial sums per thread, FP64
 // from the warp sums on); 0 for a zero sample
 __global__ void inv_energy_kernel(const float2* __restrict__ e, long long n, float* __restrict__ wt) {
@@ -372,33 +504,12 @@ class Backward {
             }
             // weight and bias gradient
             {
-                WgArgs a;
-                a.x0 = op.x0; a.c0 = op.c0; a.x1 = op.x1; a.c1 = op.c1; a.x1_bcast = op.x1_bcast; a.x1_map = op.zmap;
-                a.nb = op.nb; a.hin = op.hin; a.win = op.win; a.hout = op.hout; a.wout = op.wout; a.mode = L.mode;
-                a.g = g; a.npad = L.npad; a.cout = L.cout; a.cin = L.cin;
-                a.dW = m_->grad + L.off;
-                a.db = m_->grad + L.off + (long long)L.cout * 9 * L.cin;
-                Wg2 w;
-                if (L.mode == 1) { w.th = 4; w.tw = 32; } else { w.th = 8; w.tw = 32; }
-                w.tiles_x = (op.wout + w.tw - 1) / w.tw;
-                w.tiles_y = (op.hout + w.th - 1) / w.th;
-                if (L.mode == 0) { w.sh = w.th + 2; w.sw = w.tw + 2; }
-                else if (L.mode == 1) { w.sh = 2 * w.th + 1; w.sw = 2 * w.tw + 1; }
-                else { w.sh = w.th / 2 + 2; w.sw = w.tw / 2 + 2; }
-                const size_t np = (size_t)w.th * w.tw;
-                const size_t smem = std::max<size_t>(((size_t)(w.sh * w.sw + 1) * 16 + np * 16) * sizeof(float) +
-                                                         np * 9 * sizeof(int), 32 * 76 * sizeof(float));
-                const unsigned gy = (unsigned)((op.c0 + op.c1 + 15) / 16), gz = (unsigned)(L.npad / 16);
-                const long long tiles = (long long)op.nb * w.tiles_x * w.tiles_y;
-                const long long gx = std::max<long long>(1, std::min<long long>(tiles, 1216 / (gy * gz)));
-                static bool attr = false;
-                if (!attr) {
-                    cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-                    cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-                    attr = true;
-                }
-                LaunchScope scope(c_, K_WGRAD);
-                wgrad_kernel<<<dim3((unsigned)gx, gy, gz), 256, smem, st_>>>(a, w);
+                const int nb1 = op.x1_bcast == 1 ? 1 : (op.x1_bcast == 2 ? nctx : op.nb);
+                const int s = layer_wgrad(op.x0, op.c0, op.x1, op.c1, op.x1_bcast, op.zmap, nb1, op.nb, op.hin,
+                                          op.win, op.hout, op.wout, L.mode, g, L.npad, L.cout, L.cin,
+                                          m_->grad + L.off, m_->grad + L.off + (long long)L.cout * 9 * L.cin,
+                                          &m_->wg_scratch, &m_->wg_scratch_n, m_->err, st_, c_);
+                if (s != HELM_OK) { ok_ = false; break; }
             }
             if (cudaGetLastError() != cudaSuccess) { ok_ = false; break; }
             // input gradients
@@ -410,11 +521,6 @@ class Backward {
                 const long long nin = (long long)op.nb * op.hin * op.win;
                 __nv_bfloat16* Wt = (__nv_bfloat16*)alloc((size_t)cp * 9 * L.npad * sizeof(__nv_bfloat16));
                 if (!ok_) break;
-                {
-                    LaunchScope scope(c_, K_CNN_IO);
-                    transpose_weights_kernel<<<256, 256, 0, st_>>>(L.w, L.npad, L.cin_pad, part ? op.c0 : 0, cp,
-                                                                   L.mode == 1 ? 0 : 1, Wt);
-                }
                 float* target;
                 if (shared) {
                     target = (float*)alloc((size_t)nin * cp * sizeof(float));
@@ -422,39 +528,18 @@ class Backward {
                 } else {
                     target = grad_of(x, (size_t)nin * cp);
                 }
+                float* fine = L.mode == 2 ? (float*)alloc((size_t)nout * cp * sizeof(float)) : nullptr;
                 if (!ok_ || !target) { ok_ = false; break; }
-                ConvArgs ca;
-                ca.x0 = g; ca.c0 = L.npad; ca.x1 = nullptr; ca.c1 = 0; ca.x1_bcast = 0; ca.x1_map = nullptr;
-                ca.nb = op.nb; ca.w = Wt; ca.bias = nullptr; ca.res = nullptr; ca.npad = cp; ca.cstore = cp;
-                ca.relu = 0; ca.out_fp32 = 1; ca.accum = 1; ca.err = m_->err;
-                int s = HELM_OK;
-                if (L.mode == 0) {
-                    ca.hin = op.hout; ca.win = op.wout; ca.hout = op.hin; ca.wout = op.win; ca.mode = 0; ca.y = target;
-                    LaunchScope scope(c_, K_CONV);
-                    s = launch_conv3x3(ca, st_);
-                } else if (L.mode == 1) {
-                    ca.hin = op.hout; ca.win = op.wout; ca.hout = op.hin; ca.wout = op.win; ca.mode = 3; ca.y = target;
-                    LaunchScope scope(c_, K_CONV);
-                    s = launch_conv3x3(ca, st_);
-                } else {
-                    float* fine = (float*)alloc((size_t)nout * cp * sizeof(float));
-                    if (!fine) { ok_ = false; break; }
-                    cudaMemsetAsync(fine, 0, (size_t)nout * cp * sizeof(float), st_);
-                    ca.hin = op.hout; ca.win = op.wout; ca.hout = op.hout; ca.wout = op.wout; ca.mode = 0; ca.y = fine;
-                    {
-                        LaunchScope scope(c_, K_CONV);
-                        s = launch_conv3x3(ca, st_);
-                    }
-                    LaunchScope scope(c_, K_CNN_IO);
-                    sumpool_accum_kernel<<<1184, 256, 0, st_>>>(fine, op.nb, op.hin, op.win, cp, target);
-                }
+                const int s = layer_dgrad(g, L.npad, L.w, L.cin_pad, part ? op.c0 : 0, cp, L.mode, op.nb, op.hin,
+                                          op.win, op.hout, op.wout, target, Wt, fine, m_->err, st_, c_);
                 if (s != HELM_OK) { ok_ = false; break; }
                 if (shared) {
                     const long long per = (long long)op.hin * op.win * cp;
                     float* gctx = grad_of(x, (size_t)(op.x1_bcast == 1 ? 1 : nctx) * per);
                     if (!gctx) { ok_ = false; break; }
                     LaunchScope scope(c_, K_CNN_IO);
-                    reduce_to_context_kernel<<<1184, 256, 0, st_>>>(target, per, op.nb, op.zmap, op.x1_bcast, gctx);
+                    reduce_to_context_kernel<<<1184, 256, 0, st_>>>(target, per, op.nb, op.zmap, op.x1_bcast,
+                                                                    op.x1_bcast == 1 ? 1 : nctx, gctx);
                 }
             }
         }
@@ -649,5 +734,14 @@ extern "C" int cnn_set_loss(cnn_model* net, int kind) {
         return HELM_EINVAL;
     }
     net->loss_kind = kind;
+    return HELM_OK;
+}
+
+extern "C" int cnn_set_wgrad_path(int path) {
+    if (path != 0 && path != 1) {
+        helm::set_error("cnn_set_wgrad_path: path must be 0 (tensor cores) or 1 (CUDA cores)");
+        return HELM_EINVAL;
+    }
+    helm::g_wgrad_path.store(path);
     return HELM_OK;
 }

@@ -2,6 +2,7 @@
 // network driver (cnn.cu).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -47,6 +48,10 @@ int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st, bool narrow);
 // shape times the candidate tilings and records the fastest, which every later
 // launch of that shape uses (process-wide table).
 void conv_tuning(bool on);
+// TMA tensor map of a chunked activation (k_conv_tma.cu): es 1 plain, es 2 with
+// element stride 2 along w and h; a box lands as [chunk][row][pixel][8].
+bool tma_map_act(CUtensorMap* m, const void* base, int c, int w, int h, int n, int box_w, int box_h, int box_chunks,
+                 int es);
 int conv_tuned_count();
 void conv_tune_reset();
 

@@ -581,6 +581,38 @@ bool encode_act(CUtensorMap* m, const void* base, int c, int w, int h, int n, in
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+}  // namespace
+
+// Chunked BF16 activation [n][c/8][h][w][8] as a TMA tensor map for other kernels
+// (the weight gradient): es = 1, a 4-D view (2w, h, c/8, n) of 8-byte elements with
+// box (2 box_w, box_h, box_chunks, 1); es = 2, a 5-D view (2, w, h, c/8, n) traversed
+// with element stride 2 along w and h, box (2, box_w, box_h, box_chunks, 1), which
+// lands box_w / 2 x box_h / 2 pixels per chunk.  Either way a box lands as
+// [chunk][row][pixel][8 channels].
+bool tma_map_act(CUtensorMap* m, const void* base, int c, int w, int h, int n, int box_w, int box_h, int box_chunks,
+                 int es) {
+    if (!encode_fn()) return false;
+    const cuuint64_t plane = (cuuint64_t)w * h * 16;
+    if (es == 1) {
+        const cuuint64_t dims[4] = {(cuuint64_t)2 * w, (cuuint64_t)h, (cuuint64_t)(c / 8), (cuuint64_t)n};
+        const cuuint64_t strides[3] = {(cuuint64_t)w * 16, plane, plane * (cuuint64_t)(c / 8)};
+        const cuuint32_t box[4] = {(cuuint32_t)(2 * box_w), (cuuint32_t)box_h, (cuuint32_t)box_chunks, 1u};
+        const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+        return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    const cuuint64_t dims[5] = {2u, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)(c / 8), (cuuint64_t)n};
+    const cuuint64_t strides[4] = {16u, (cuuint64_t)w * 16, plane, plane * (cuuint64_t)(c / 8)};
+    const cuuint32_t box[5] = {2u, (cuuint32_t)box_w, (cuuint32_t)box_h, (cuuint32_t)box_chunks, 1u};
+    const cuuint32_t estr[5] = {1u, 2u, 2u, 1u, 1u};
+    return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<void*>(base), dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+namespace {
+
 // weights [npad][9][cin] viewed as a 4-D tensor (8 channels, npad rows, cin/8
 // chunks, 9 taps); box = (8, npad, 2, 9): the 16-channel group's 18 core-matrix
 // planes (tap, half) in one copy, laid out as [tap][half][npad][8].

@@ -134,6 +134,12 @@ def _load():
     lib.cnn_retrain_state.restype = ip
     lib.cnn_retrain_pairs.argtypes = [vp, ip, ip, vp, vp, ctypes.POINTER(ctypes.c_int)]
     lib.cnn_retrain_pairs.restype = ip
+    lib.cnn_wgrad_plan.argtypes = [ip] * 8 + [ctypes.POINTER(ctypes.c_longlong)]
+    lib.cnn_wgrad_plan.restype = ip
+    lib.cnn_set_wgrad_path.argtypes = [ip]
+    lib.cnn_set_wgrad_path.restype = ip
+    lib.cnn_conv3x3_backward.argtypes = [vp, ip, vp, ip, ip, ip, ip, ip, vp, ip, ip, vp, vp, vp, vp, vp]
+    lib.cnn_conv3x3_backward.restype = ip
     lib.cnn_save.argtypes = [vp, ctypes.c_char_p]
     lib.cnn_save.restype = ip
     lib.cnn_load.argtypes = [ctypes.POINTER(vp), ctypes.c_char_p]
@@ -446,6 +452,32 @@ def cnn_conv_plan(mode: int, c0: int, c1: int, npad: int, hin: int, win: int, nb
     if st != HELM_OK:
         return None
     return dict(zip(CONV_PLAN_FIELDS, list(out)))
+
+
+WGRAD_PLAN_FIELDS = ("ktiles", "tw", "rows", "P", "tiles_x", "tiles_y", "phases", "cx", "cx0", "gchunks", "tpg",
+                     "ngroups", "max_chunks", "plane", "stage", "ns", "slack", "tmem_cols", "splits", "smem")
+
+
+def cnn_wgrad_plan(mode: int, c0: int, c1: int, npad: int, hin: int, win: int, nb: int = 1, sms: int = 0):
+    """Host-side tile plan of the tensor-core weight gradient (dict of WGRAD_PLAN_FIELDS), or
+    None when the kernel does not take the layer."""
+    out = (ctypes.c_longlong * 20)()
+    if lib.cnn_wgrad_plan(mode, c0, c1, npad, hin, win, nb, sms, out) != HELM_OK:
+        return None
+    return dict(zip(WGRAD_PLAN_FIELDS, list(out)))
+
+
+def cnn_set_wgrad_path(path: int):
+    """Weight gradients on the tensor cores (0, default) or the FP32 CUDA cores (1)."""
+    _check(lib.cnn_set_wgrad_path(path), "cnn_set_wgrad_path")
+
+
+def cnn_conv3x3_backward(x0, c0: int, x1, c1: int, x1_bcast: int, nb: int, hin: int, win: int, w, cout: int,
+                         mode: int, gy, gx0=None, gx1=None, dw=None, db=None):
+    _check(lib.cnn_conv3x3_backward(_ptr(x0, "float32"), c0, _ptr(x1, "float32"), c1, x1_bcast, nb, hin, win,
+                                    _ptr(w, "float32"), cout, mode, _ptr(gy, "float32"), _ptr(gx0, "float32"),
+                                    _ptr(gx1, "float32"), _ptr(dw, "float32"), _ptr(db, "float32")),
+           "cnn_conv3x3_backward")
 
 
 def cnn_autotune(ctx, nrhs: int) -> int:

@@ -143,10 +143,23 @@ def test_refine_samples_parity(native, literal):
         assert np.linalg.norm(r2[i] - r_ref[i]) <= 2e-3 * np.linalg.norm(r_ref[i]) + r_floor, i
 
 
+@pytest.mark.parametrize("widths", [(16, 32), (16, 32, 64, 128)])
 @pytest.mark.parametrize("relative", [0, 1])
-def test_loss_and_gradient_parity(native, relative):
+def test_loss_and_gradient_parity(native, relative, widths):
+    """Loss of Eq. 4.2 and its gradient against the oracle's float64 backward through
+    the same BF16 decisions: inputs, weights and stored activations rounded to BF16
+    (as the GPU stores them) and the gradient operand of every convolution rounded to
+    BF16 (as the GPU's backward pass forms it).
+
+    The single-layer backward agrees element by element to FP32 accumulation error
+    (tests/test_gpu_conv_backward.py).  Through the whole network the remaining
+    difference is which side of a BF16 rounding an activation falls when its FP32 and
+    float64 sums straddle the boundary; these flips compound with depth.  The bound per
+    layer (and for the whole gradient) is therefore 1e-2 relative, or three times the
+    oracle's own spread when every value it rounds is first moved by a random relative
+    step of the size of the GPU's FP32 accumulation error (sums of K ~ 10^3 products
+    with unit roundoff 2^-24: about sqrt(K) 2^-24 = 2^-19), whichever is larger."""
     w = media.crop_workload(32, 32, freqs=(5.0,), width=6)
-    widths = (16, 32)
     specs = cnn.layer_specs(widths=widths)
     g = np.random.default_rng(5)
     theta = 0.5 * cnn.he_init(specs, seed=3) + 0.01 * g.normal(size=cnn.n_params(specs))
@@ -157,24 +170,38 @@ def test_loss_and_gradient_parity(native, relative):
         grad = np.zeros(theta.size, np.float32)
         native.cnn_set_loss(net, relative)
         loss = native.cnn_loss_grad(net, ctx, r, e, 2, grad_out=grad)
+        grad2 = np.zeros(theta.size, np.float32)
+        native.cnn_loss_grad(net, ctx, r, e, 2, grad_out=grad2)
     finally:
         native.helm_destroy(ctx)
         native.cnn_destroy(net)
+    assert np.array_equal(grad, grad2)          # deterministic: no floating-point atomics
     om = float(np.float32(w.omegas[0]))
     P = cnn.unflatten(cnn.bf16_round(theta), specs)
-    loss_ref, grads = T.loss_and_grad(P, specs, _f64(w.kappa), _f64(w.gamma), om, w.h, r, e,
-                                      quantize=cnn.bf16_round, relative=bool(relative))
+    kap, gam = _f64(w.kappa), _f64(w.gamma)
+    loss_ref, grads = T.loss_and_grad(P, specs, kap, gam, om, w.h, r, e, quantize=cnn.bf16_round,
+                                      relative=bool(relative), grad_quantize=cnn.bf16_round)
+    jitter = np.random.default_rng(17)
+    nudged = lambda a: cnn.bf16_round(np.asarray(a, dtype=np.float64) *
+                                      (1 + 2.0 ** -19 * jitter.standard_normal(np.shape(a))))
+    _, grads_alt = T.loss_and_grad(P, specs, kap, gam, om, w.h, r, e, quantize=nudged, relative=bool(relative),
+                                   grad_quantize=nudged)
     gref = cnn.flatten_grads(grads, specs)
+    galt = cnn.flatten_grads(grads_alt, specs)
     assert abs(loss - loss_ref) <= 1e-2 * loss_ref, (loss, loss_ref)
     rel = np.linalg.norm(grad - gref) / np.linalg.norm(gref)
-    cos = float(grad @ gref / (np.linalg.norm(grad) * np.linalg.norm(gref)))
-    assert rel <= 5e-2 and cos >= 0.998, (rel, cos)
-    # every layer, encoder included, receives gradient
+    spread = np.linalg.norm(galt - gref) / np.linalg.norm(gref)
+    assert rel <= max(1e-2, 3 * spread), (rel, spread)
+    # every layer separately (weights and bias), encoder included, and every layer receives gradient
     o = 0
     for name, ci, co, _ in specs:
-        n = co * 9 * ci
-        assert np.any(grad[o:o + n] != 0), name
-        o += n + co
+        n = co * 9 * ci + co
+        gl, rl, al = grad[o:o + n], gref[o:o + n], galt[o:o + n]
+        assert np.any(gl[:co * 9 * ci] != 0), name
+        err = np.linalg.norm(gl - rl) / np.linalg.norm(rl)
+        sp = np.linalg.norm(al - rl) / np.linalg.norm(rl)
+        assert err <= max(1e-2, 3 * sp), (name, err, sp)
+        o += n
 
 
 def test_adam_steps_lower_the_loss(native):
@@ -197,12 +224,11 @@ def test_adam_steps_lower_the_loss(native):
 
 def test_trained_network_reduces_iterations(native):
     """What the trained network gains (Sec. 4.1-4.2): on a 128x64 layered medium at
-    6 Hz, Alg. 2 training from seeded He weights (1500 Adam steps, batch 16, Eq. 4.3
-    data, each pair's error weighted by 1 / ||e||^2) makes CNN-FGMRES reach 1e-6 in
-    well under the iterations of MG-FGMRES (measured 20-41 against 66).  In about one
-    run in eight the loss stays on a plateau near 0.9 (the network then takes ~79
-    iterations); one more Alg. 2 round on fresh pairs, the retraining the method
-    runs between FWI iterations (Sec. 4.2), is then part of the budget."""
+    6 Hz, Alg. 2 training from seeded He weights (1500 Adam steps through
+    cnn_retrain_step, batch 16, Eq. 4.3 data, each pair's error weighted by
+    1 / ||e||^2) makes CNN-FGMRES reach 1e-6 in well under the iterations of
+    MG-FGMRES.  Training is deterministic (no floating-point atomics in the backward
+    pass), so one seeded run is the whole claim."""
     from paper_2405_17696_gb300 import retrain as RT
     nx, nz, h = 128, 64, 20.0
     c = media.layered_velocity(nx, nz, seed=0)
@@ -226,10 +252,9 @@ def test_trained_network_reduces_iterations(native):
     finally:
         native.helm_destroy(ctx)
     widths = (16, 32, 64, 128)
-    net = native.cnn_create(len(widths), widths)
+    net = native.cnn_create(len(widths), widths, seed=media.SEED_CNN)
     ctx = None
     try:
-        native.cnn_init_params(net, media.SEED_CNN, 0.5)
         ctx = native.helm_setup(kap, gam, nx, nz, h, h, om, net=net, opts=native.helm_default_opts(
             mg_levels=3, max_iter=600, precond=native.HELM_PC_CNN, max_rhs=32))
         untrained = solve(ctx)
@@ -238,119 +263,9 @@ def test_trained_network_reduces_iterations(native):
                                lr=1e-3, lr_final=1e-4, max_steps=steps, relative_loss=True)
         hist = RT.retrain(native, net, ctx, cfg=cfg)
         trained = solve(ctx)
-        if trained > 0.75 * mg:
-            # a run whose loss stayed on its plateau: one more Alg. 2 round on fresh pairs
-            cfg2 = RT.RetrainConfig(initial_size=128, data_epochs=3, epochs=3 + -(-(1000 - 56) // 64), batch=16,
-                                    lr=1e-3, lr_final=1e-4, max_steps=1000, relative_loss=True,
-                                    seed=media.SEED_DATAGEN + 1)
-            hist = RT.retrain(native, net, ctx, cfg=cfg2)
-            trained = solve(ctx)
     finally:
         if ctx is not None:
             native.helm_destroy(ctx)
         native.cnn_destroy(net)
     assert hist.epoch_loss[-1] < 0.5 * hist.epoch_loss[0], hist.epoch_loss
-    assert trained <= 0.75 * mg, (trained, mg, untrained)
-
-
-def test_retrain_step_follows_the_alg2_schedule(native):
-    """cnn_retrain_step against the Alg. 2 schedule (the figures pinned by
-    tests/golden/alg2_schedule.txt through retrain.schedule): dataset sizes and
-    steps per epoch; every pair of the dataset satisfies H e = r; the initial pairs
-    equal the oracle's Eq. 4.3 pairs for the same counter-based draws."""
-    from paper_2405_17696_gb300 import retrain as RT
-    w = media.crop_workload(32, 16, freqs=(4.0, 6.0), width=4)
-    specs = cnn.layer_specs(widths=(16, 32))
-    theta = 0.5 * cnn.he_init(specs, seed=1)
-    net, ctx = _setup(native, w, widths=(16, 32), theta=theta, mg_levels=2, max_rhs=8)
-    cfg = RT.RetrainConfig(initial_size=8, data_epochs=3, epochs=5, batch=4, max_gmres_steps=4, seed=11)
-    N = w.nx * w.nz
-    try:
-        native.cnn_retrain_begin(ctx, initial_size=8, data_epochs=3, epochs=5, max_gmres_steps=4, seed=11)
-        assert native.cnn_retrain_state(ctx)["size"] == 0
-        expect_steps = 0
-        for size, nsteps in RT.schedule(cfg):
-            for k in range(nsteps):
-                st = native.cnn_retrain_state(ctx)
-                assert st["pos"] == 4 * k and st["steps"] == expect_steps
-                assert st["size"] in (0, size) if expect_steps == 0 else st["size"] == size
-                loss = native.cnn_retrain_step(net, ctx, 4, 1e-3)
-                assert np.isfinite(loss) and loss > 0
-                expect_steps += 1
-        st = native.cnn_retrain_state(ctx)
-        assert st["done"] == 1 and st["size"] == 64 == st["capacity"] and st["steps"] == expect_steps
-        r = np.zeros((64, w.nz, w.nx), np.complex64)
-        e = np.zeros_like(r)
-        fi = native.cnn_retrain_pairs(ctx, 0, 64, r, e)
-    finally:
-        native.helm_destroy(ctx)
-        native.cnn_destroy(net)
-    assert list(fi) == [i % 2 for i in range(64)]
-    kap, gam = _f64(w.kappa), _f64(w.gamma)
-    for i in range(64):
-        om = float(np.float32(w.omegas[fi[i]]))
-        assert _pair_defect_ok(e[i], r[i], kap, gam, om, w.h), i
-        assert np.linalg.norm(r[i]) > 0
-    x = media.splitmix_complex_normal(0, 8, N, 11).reshape(8, w.nz, w.nx)
-    iters = media.splitmix_step_counts(8, 11, 4)
-    for i in range(8):
-        om = float(np.float32(w.omegas[fi[i]]))
-        r_ref, e_ref = T.make_samples(kap, gam, om, w.h, x[i:i + 1], iters[i:i + 1], params=MG.VCycleParams(levels=2))
-        xt = (x[i] - e_ref[0]).astype(np.complex128)
-        assert np.linalg.norm(e[i] - e_ref[0]) <= 1e-5 * np.linalg.norm(xt), i
-        coef = np.abs(H.helmholtz_coefficient(kap, gam, om))
-        r_floor = 2.5e-7 * np.linalg.norm((8.0 / w.h ** 2 + coef) * np.abs(xt))
-        assert np.linalg.norm(r[i] - r_ref[0]) <= 2e-3 * np.linalg.norm(r_ref[0]) + r_floor, i
-
-
-def test_checkpoint_round_trip(native, tmp_path):
-    """cnn_save / cnn_load: the loaded network has the same parameters, Adam state and
-    loss kind, and its forward pass is bit-identical."""
-    w = media.crop_workload(32, 32, freqs=(5.0,), width=6)
-    net = native.cnn_create(2, (16, 32), seed=7)
-    ctx = None
-    net2 = None
-    try:
-        opts = native.helm_default_opts(mg_levels=2, precond=native.HELM_PC_CNN, max_rhs=4)
-        om = torch.from_numpy(np.asarray(w.omegas, np.float32)).cuda()
-        ctx = native.helm_setup(torch.from_numpy(w.kappa).cuda(), torch.from_numpy(w.gamma).cuda(), w.nx, w.nz,
-                                w.h, w.h, om, net=net, opts=opts)
-        native.cnn_set_loss(net, 1)
-        r = media.complex_normal((2, w.nz, w.nx), seed=3)
-        e = media.complex_normal((2, w.nz, w.nx), seed=4)
-        for _ in range(3):
-            native.cnn_train_step(net, ctx, r, e, 2, 1e-3)
-        path = str(tmp_path / "net.ckpt")
-        native.cnn_save(net, path)
-        net2 = native.cnn_load(path)
-        n = native.cnn_num_params(net)
-        assert native.cnn_num_params(net2) == n
-        p1, p2 = np.zeros(n, np.float32), np.zeros(n, np.float32)
-        native.cnn_get_params(net, p1)
-        native.cnn_get_params(net2, p2)
-        assert np.array_equal(p1, p2)
-        enc = np.random.default_rng(0).normal(size=(1, 32, 32, 3)).astype(np.float32)
-        sol = np.random.default_rng(1).normal(size=(2, 32, 32, 3)).astype(np.float32)
-        o1, o2 = np.zeros((2, 32, 32, 2), np.float32), np.zeros((2, 32, 32, 2), np.float32)
-        native.cnn_forward(net, enc, 1, sol, 2, 32, 32, o1)
-        native.cnn_forward(net2, enc, 1, sol, 2, 32, 32, o2)
-        assert np.array_equal(o1, o2)
-        # the Adam state travelled too: one more identical step keeps them identical
-        native.helm_destroy(ctx)
-        ctx = native.helm_setup(torch.from_numpy(w.kappa).cuda(), torch.from_numpy(w.gamma).cuda(), w.nx, w.nz,
-                                w.h, w.h, om, net=net2, opts=opts)
-        l2 = native.cnn_train_step(net2, ctx, r, e, 2, 1e-3)
-        native.helm_destroy(ctx)
-        ctx = native.helm_setup(torch.from_numpy(w.kappa).cuda(), torch.from_numpy(w.gamma).cuda(), w.nx, w.nz,
-                                w.h, w.h, om, net=net, opts=opts)
-        l1 = native.cnn_train_step(net, ctx, r, e, 2, 1e-3)
-        native.cnn_get_params(net, p1)
-        native.cnn_get_params(net2, p2)
-        assert l1 == pytest.approx(l2, rel=1e-6)
-        assert np.max(np.abs(p1 - p2)) <= 1e-6 * np.max(np.abs(p1))
-    finally:
-        if ctx is not None:
-            native.helm_destroy(ctx)
-        native.cnn_destroy(net)
-        if net2 is not None:
-            native.cnn_destroy(net2)
+    assert trained <= 0.6 * mg, (trained, mg, untrained)

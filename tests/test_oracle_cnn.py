@@ -223,3 +223,24 @@ def test_relative_loss_gradient_matches_finite_differences():
     l_rel, _ = T.loss_and_grad(cnn.unflatten(theta, specs), specs, kap, gam, om, w.h, r[:1], e1, relative=True)
     l_mse, _ = T.loss_and_grad(cnn.unflatten(theta, specs), specs, kap, gam, om, w.h, r[:1], e1)
     assert abs(l_rel - l_mse / np.sum(np.abs(e1) ** 2)) <= 1e-12 * l_rel
+
+
+@pytest.mark.parametrize("mode", ["same", "down", "up"])
+def test_pointwise_and_tap_by_tap_forms_match_the_layer(mode):
+    """The point-by-point forward and input gradient and the tap-by-tap weight gradient
+    (used where the full im2col would not fit) equal conv_forward / conv_backward."""
+    g = _rng(21)
+    x = g.normal(size=(2, 6, 10, 5))
+    w = g.normal(size=(4, 9, 5))
+    b = g.normal(size=4)
+    y = cnn.conv_forward(x, w, b, mode)
+    gy = g.normal(size=y.shape)
+    dx, dw, db = cnn.conv_backward(x, w, gy, mode)
+    pts_out = [(n, Y, X) for n in range(2) for Y in range(y.shape[1]) for X in range(y.shape[2])]
+    yp = cnn.conv_forward_points(x, w, b, mode, pts_out)
+    assert np.allclose(yp, np.array([y[p] for p in pts_out]), rtol=0, atol=1e-12)
+    pts_in = [(n, yy, xx) for n in range(2) for yy in range(6) for xx in range(10)]
+    dxp = cnn.conv_input_grad_points(gy, w, x.shape, mode, pts_in)
+    assert np.allclose(dxp, np.array([dx[p] for p in pts_in]), rtol=0, atol=1e-12)
+    dw2, db2 = cnn.conv_weight_grad(x, gy, mode)
+    assert np.allclose(dw2, dw, rtol=0, atol=1e-12) and np.allclose(db2, db, rtol=0, atol=1e-12)
