@@ -187,6 +187,69 @@ int helm_vcycle(helm_ctx* ctx, const helm_c64* f, const helm_c64* u0, helm_c64* 
 int fwi_misfit_grad(helm_ctx* ctx, const int* src_idx, int nsrc, const int* rcv_idx, int nrcv,
                     const helm_c64* d_obs, double tol, double* misfit_out, float* grad_m_out);
 
+/* ---- Gauss-Newton FWI (Sec. 3.2-3.3, Alg. 1) ------------------------------------------
+ * A survey: point-source nodes src_idx[nsrc] and receiver nodes rcv_idx[nrcv] (flat grid
+ * indices iz * nx + ix, host int32; every source shares the receivers).  With src_w ==
+ * NULL the sources are the nsrc point sources e_s / (hx hz); otherwise there are nsim
+ * simultaneous (encoded) sources, source k = sum_s src_w[k][s] e_s / (hx hz) (host float32
+ * [nsim][nsrc], e.g. Rademacher +-1 weights, Sec. 3.2).  Data arrays are complex64
+ * [nfreq][nsources][nrcv] over the context's frequencies (host or device). */
+typedef struct {
+    const int* src_idx;
+    int nsrc;
+    const float* src_w;     /* [nsim][nsrc] or NULL */
+    int nsim;
+    const int* rcv_idx;
+    int nrcv;
+} fwi_survey;
+
+/* d = P^T H(m, w_j)^{-1} q_k for every frequency and source of the survey (the synthetic
+ * data of Eq. 3.3); *iters_out (may be NULL) receives the Helmholtz iterations used. */
+int fwi_forward_data(helm_ctx* ctx, const fwi_survey* survey, double tol, helm_c64* d_out, long long* iters_out);
+
+/* Sensitivity products (Eq. 3.10 written out from the operator of Eq. 3.1: dH/dm =
+ * -w^2 (1 - i gamma)), for real model perturbations of m = kappa^2:
+ *   fwi_jacobian:          dd = J dm,  dd_jk = P^T w_j^2 H^{-1} ((1 - i gamma) u_jk dm)
+ *   fwi_jacobian_adjoint:  dm = J^T dd = Re(J^H dd) = sum_jk w_j^2 Re((1 - i gamma) u_jk mu_jk),
+ *                          H mu_jk = P conj(dd_jk)   (conjugation identity, Sec. 4.3)
+ * dm : float32 [nz][nx]; dd : complex64 [nfreq][nsources][nrcv]; host or device.  Each call
+ * solves for the forward fields (tolerance tol) and then the sensitivity or adjoint
+ * systems (same tolerance; the paper takes 1e-4 for these). */
+int fwi_jacobian(helm_ctx* ctx, const fwi_survey* survey, const float* dm, double tol, helm_c64* dd_out);
+int fwi_jacobian_adjoint(helm_ctx* ctx, const fwi_survey* survey, const helm_c64* dd, double tol, float* dm_out);
+
+typedef struct {
+    double tol;             /* forward and adjoint solves (misfit, gradient)          (1e-6) */
+    double tol_sens;        /* sensitivity solves inside conjugate gradients           (1e-4) */
+    int    cg_iters;        /* conjugate-gradient steps on the Gauss-Newton system       (5) */
+    float  reg;             /* Tikhonov term reg I added to J^T J                        (0) */
+    float  m_min, m_max;    /* bounds of m = kappa^2 after the step              (0, 1e30) */
+    int    max_backtracks;  /* halvings of the step when the misfit does not drop      (4) */
+} fwi_gn_opts;
+typedef struct {
+    double misfit_before, misfit_after;   /* Eq. 3.5 at the model before / after the step */
+    double step;                          /* accepted step length (0: model unchanged)    */
+    int    cg_iters;                      /* CG steps taken                               */
+    long long iters_forward, iters_adjoint, iters_sensitivity, iters_line_search;
+                                          /* Helmholtz (FGMRES) iterations per phase      */
+} fwi_gn_info;
+void fwi_default_gn_opts(fwi_gn_opts* opts);
+/* kappa = sqrt(m) for n nodes (device arrays): the medium of a model m = kappa^2. */
+int fwi_model_to_kappa(const float* m, float* kappa, long long n);
+/* One Gauss-Newton iteration of Alg. 1 at the context's frequencies: sets the medium
+ * from m (clipped to [m_min, m_max]; kappa = sqrt(m), gamma kept), forward fields and the
+ * misfit of Eq. 3.5, its gradient 2 J^T r, cg_iters conjugate-gradient steps on
+ * (J^T J + reg I) dm = -J^T r from 0 with the forward fields kept (two solves per source
+ * and frequency per step), then m <- clip(m + a dm) for a = 1, 1/2, ... (at most
+ * max_backtracks halvings) as soon as the misfit drops; if none does, m is unchanged.
+ * d_obs: complex64 [nfreq][nsrc][nrcv] per POINT source (host or device); with
+ * simultaneous sources it is encoded here with the survey's weights (d_k = sum_s w_ks d_s).
+ * m: float32 [nz][nx] (host or device), updated in place; the context's medium is left
+ * at the returned m.  Memory: 16 bytes per grid point per (frequency, source) for the
+ * kept fields. */
+int fwi_gn_iteration(helm_ctx* ctx, const fwi_survey* survey, const helm_c64* d_obs, const fwi_gn_opts* opts,
+                     float* m, fwi_gn_info* info);
+
 void helm_destroy(helm_ctx* ctx);
 
 /* ---------------------------------------------------------------------------

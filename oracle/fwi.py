@@ -86,3 +86,59 @@ def misfit_at_m(m, gamma, omegas, hx, hz, sources, receivers, d_obs) -> float:
     """Phi as a function of m itself (kappa = sqrt(m)), for finite differences."""
     return misfit(np.sqrt(np.asarray(m, dtype=np.float64)), gamma, omegas, hx, hz, sources,
                   receivers, d_obs)
+
+
+def jacobian_apply(kappa, gamma, omegas, hx, hz, sources, receivers, dm):
+    """J dm: the first-order change of the data of every frequency j and source s for a
+    real change dm of m = kappa^2 (the sensitivity of Eq. 3.10, written out from the
+    operator of Eq. 3.1):  du = w^2 H^{-1} ((1 - i gamma) u dm),  dd = P_s^T du.
+    Returns complex128 ``[nf][ns][nr]``."""
+    g64 = np.asarray(gamma, dtype=np.float64)
+    dm = np.asarray(dm, dtype=np.float64)
+    out = []
+    for w in omegas:
+        solver = DirectSolver(kappa, gamma, w, hx, hz)
+        u = solver.solve(sources)
+        du = solver.solve(w ** 2 * (1.0 - 1j * g64) * u * dm)
+        out.append(sample(du, receivers))
+    return np.stack(out)
+
+
+def jacobian_adjoint(kappa, gamma, omegas, hx, hz, sources, receivers, dd):
+    """J^T dd for real model perturbations: the m-vector with <J v, dd> = v . J^T dd in the
+    real inner product Re(sum conj(dd) J v), i.e. Re(J^H dd).  Written out:
+    Re(J^H dd)_k = sum_{j,s} w^2 Re((1 - i gamma_k) u_k mu_k),  H mu = P_s conj(dd_sj)
+    (the conjugation identity of Sec. 4.3).  Returns float64 ``[nz][nx]``."""
+    g64 = np.asarray(gamma, dtype=np.float64)
+    shape = np.shape(kappa)
+    out = np.zeros(shape)
+    for j, w in enumerate(omegas):
+        solver = DirectSolver(kappa, gamma, w, hx, hz)
+        u = solver.solve(sources)
+        mu = solver.solve(scatter(np.conj(np.asarray(dd)[j]), receivers, shape))
+        out += w ** 2 * np.sum(np.real((1.0 - 1j * g64) * u * mu), axis=0)
+    return out
+
+
+def gauss_newton_direction(kappa, gamma, omegas, hx, hz, sources, receivers, d_obs, cg_iters: int,
+                           reg: float = 0.0):
+    """The Gauss-Newton step of Sec. 3.3 (Alg. 1): dm approximately solving
+    (J^T J + reg I) dm = -J^T r,  r = d(m) - d_obs  (J^T r = grad Phi / 2 for Eq. 3.5),
+    by cg_iters iterations of conjugate gradients from dm = 0 (Hestenes and Stiefel).
+    Returns (dm, Phi, grad Phi)."""
+    phi, grad = misfit_and_gradient(kappa, gamma, omegas, hx, hz, sources, receivers, d_obs)
+    b = -0.5 * grad
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = float(np.sum(r * r))
+    for _ in range(cg_iters):
+        Ap = jacobian_adjoint(kappa, gamma, omegas, hx, hz, sources, receivers,
+                              jacobian_apply(kappa, gamma, omegas, hx, hz, sources, receivers, p)) + reg * p
+        alpha = rr / float(np.sum(p * Ap))
+        x = x + alpha * p
+        r = r - alpha * Ap
+        rr_new = float(np.sum(r * r))
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x, phi, grad

@@ -1,0 +1,122 @@
+"""Frequency-domain FWI by Gauss-Newton with frequency continuation (Alg. 1,
+Sec. 3.2-3.3) and light-weight retraining of the encoder-solver network between
+iterations (Alg. 2, Sec. 4.2).
+
+A thin driver over the C ABI: every arithmetic step (the forward, adjoint and
+sensitivity solves, the conjugate-gradient iterations of a Gauss-Newton step, the
+line search, the retraining) runs in libhelm.  This module sequences the calls:
+for each frequency window (low to high) a context with the window's frequencies is
+set up on the current model, ``gn_iters`` Gauss-Newton iterations run with a fresh
+set of ``sim_sources`` Rademacher-encoded simultaneous sources each (Sec. 3.2;
+the random signs are drawn here, seeded, and passed in), and with the network
+preconditioner ``retrain_steps`` steps of Alg. 2 follow each iteration on the new
+medium.  The paper's figure of merit is the total number of Helmholtz solver
+iterations of the whole inversion, with and without retraining (Sec. 5.4).
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import media
+from . import retrain as RT
+
+
+@dataclass
+class FwiConfig:
+    windows: list                   # frequency windows in Hz, low to high (Alg. 1)
+    gn_iters: int = 3               # Gauss-Newton iterations per window
+    cg_iters: int = 5               # CG steps per Gauss-Newton iteration
+    tol: float = 1e-6               # forward / adjoint solves
+    tol_sens: float = 1e-4          # sensitivity solves
+    sim_sources: int = 16           # Rademacher-encoded sources per iteration (0: every point source)
+    retrain_steps: int = 0          # Alg. 2 steps after each iteration (0: no retraining)
+    retrain_lr: float = 1e-4
+    retrain_initial: int = 32       # pairs of the Eq. 4.3 dataset built on each new medium
+    v_min: float = 1400.0           # m/s bounds of the model (m = 1 / v^2)
+    v_max: float = 5000.0
+    mg_levels: int = 3
+    max_rhs: int = 64
+    seed: int = media.SEED_SOURCES
+
+
+@dataclass
+class FwiHistory:
+    rows: list = field(default_factory=list)   # one dict per Gauss-Newton iteration
+
+    @property
+    def total_iterations(self) -> int:
+        return int(sum(r["iters_forward"] + r["iters_adjoint"] + r["iters_sensitivity"] + r["iters_line_search"]
+                       for r in self.rows))
+
+
+def rademacher(p: int, nsrc: int, rng: np.random.Generator) -> np.ndarray:
+    """p x nsrc weights of +-1 (simultaneous sources, Sec. 3.2)."""
+    return np.where(rng.random((p, nsrc)) < 0.5, -1.0, 1.0).astype(np.float32)
+
+
+def observed_data(native, kappa_true, gamma, nx, nz, hx, hz, freqs_hz, survey, mg_levels=3, max_rhs=64, tol=1e-8):
+    """Synthetic observed data [nfreq][nsrc][nrcv] of the true model (Eq. 3.3) and the
+    Helmholtz iterations it took."""
+    import torch
+    om = torch.tensor([2 * math.pi * f for f in freqs_hz], dtype=torch.float32, device="cuda")
+    ctx = native.helm_setup(torch.as_tensor(kappa_true, dtype=torch.float32, device="cuda").contiguous(),
+                            torch.as_tensor(gamma, dtype=torch.float32, device="cuda").contiguous(), nx, nz, hx, hz,
+                            om, opts=native.helm_default_opts(mg_levels=mg_levels, max_rhs=max_rhs, max_iter=2000))
+    try:
+        d = torch.zeros((len(freqs_hz), survey.src.size, survey.rcv.size), dtype=torch.complex64, device="cuda")
+        it = native.fwi_forward_data(ctx, survey, d, tol=tol)
+    finally:
+        native.helm_destroy(ctx)
+    return d, it
+
+
+def run(native, m, gamma, nx, nz, hx, hz, src_idx, rcv_idx, d_obs, freqs_hz, cfg: FwiConfig, net=None,
+        log=None) -> FwiHistory:
+    """Alg. 1 on the model m (float32 CUDA tensor [nz][nx] of m = 1 / v^2, updated in
+    place).  d_obs: observed data [nfreq][nsrc][nrcv] (CUDA tensor) at freqs_hz, ordered as
+    the windows' frequencies are drawn from.  net: the encoder-solver network (CNN-FGMRES
+    with retraining when cfg.retrain_steps > 0), or None for MG-FGMRES."""
+    import torch
+    hist = FwiHistory()
+    rng = media.rng(cfg.seed)
+    gam = torch.as_tensor(gamma, dtype=torch.float32, device="cuda").contiguous()
+    fidx = {f: i for i, f in enumerate(freqs_hz)}
+    opts = native.fwi_default_gn_opts(tol=cfg.tol, tol_sens=cfg.tol_sens, cg_iters=cfg.cg_iters,
+                                      m_min=1.0 / cfg.v_max ** 2, m_max=1.0 / cfg.v_min ** 2)
+    for wi, window in enumerate(cfg.windows):
+        om = torch.tensor([2 * math.pi * f for f in window], dtype=torch.float32, device="cuda")
+        dw = torch.stack([d_obs[fidx[f]] for f in window]).contiguous()
+        kappa = torch.empty_like(m)
+        native.fwi_model_to_kappa(m, kappa)   # the medium the context starts from
+        pc = native.HELM_PC_CNN if net is not None else native.HELM_PC_MG
+        ctx = native.helm_setup(kappa, gam, nx, nz, hx, hz, om, net=net,
+                                opts=native.helm_default_opts(mg_levels=cfg.mg_levels, max_rhs=cfg.max_rhs,
+                                                              precond=pc, max_iter=2000))
+        try:
+            for it in range(cfg.gn_iters):
+                nsrc = len(src_idx)
+                w = rademacher(cfg.sim_sources, nsrc, rng) if cfg.sim_sources > 0 else None
+                survey = native.Survey(src_idx, rcv_idx, w)
+                t0 = time.perf_counter()
+                info = native.fwi_gn_iteration(ctx, survey, dw, m, opts)
+                row = dict(info, window=wi, freqs=list(window), iteration=it, seconds=time.perf_counter() - t0)
+                if net is not None and cfg.retrain_steps > 0:
+                    # Alg. 2 on the new medium: a fresh Eq. 4.3 dataset, then Adam steps
+                    t1 = time.perf_counter()
+                    rcfg = RT.RetrainConfig(initial_size=cfg.retrain_initial, data_epochs=3, epochs=1000,
+                                            batch=min(16, cfg.max_rhs), lr=cfg.retrain_lr,
+                                            max_steps=cfg.retrain_steps, relative_loss=True, warmup_steps=0,
+                                            seed=int(rng.integers(1 << 31)))
+                    h = RT.retrain(native, net, ctx, cfg=rcfg)
+                    row["retrain_loss"] = h.epoch_loss
+                    row["retrain_seconds"] = time.perf_counter() - t1
+                hist.rows.append(row)
+                if log:
+                    log(row)
+        finally:
+            native.helm_destroy(ctx)
+    return hist

@@ -41,6 +41,24 @@ class helm_opts(ctypes.Structure):
                 ("cnn_vcycle", ctypes.c_int), ("autotune", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
+class fwi_survey_t(ctypes.Structure):
+    _fields_ = [("src_idx", ctypes.c_void_p), ("nsrc", ctypes.c_int), ("src_w", ctypes.c_void_p),
+                ("nsim", ctypes.c_int), ("rcv_idx", ctypes.c_void_p), ("nrcv", ctypes.c_int)]
+
+
+class fwi_gn_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("tol_sens", ctypes.c_double), ("cg_iters", ctypes.c_int),
+                ("reg", ctypes.c_float), ("m_min", ctypes.c_float), ("m_max", ctypes.c_float),
+                ("max_backtracks", ctypes.c_int)]
+
+
+class fwi_gn_info(ctypes.Structure):
+    _fields_ = [("misfit_before", ctypes.c_double), ("misfit_after", ctypes.c_double), ("step", ctypes.c_double),
+                ("cg_iters", ctypes.c_int), ("iters_forward", ctypes.c_longlong),
+                ("iters_adjoint", ctypes.c_longlong), ("iters_sensitivity", ctypes.c_longlong),
+                ("iters_line_search", ctypes.c_longlong)]
+
+
 class cnn_retrain_opts(ctypes.Structure):
     _fields_ = [("initial_size", ctypes.c_int), ("data_epochs", ctypes.c_int), ("epochs", ctypes.c_int),
                 ("max_gmres_steps", ctypes.c_int), ("literal", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
@@ -134,6 +152,19 @@ def _load():
     lib.cnn_retrain_state.restype = ip
     lib.cnn_retrain_pairs.argtypes = [vp, ip, ip, vp, vp, ctypes.POINTER(ctypes.c_int)]
     lib.cnn_retrain_pairs.restype = ip
+    sp = ctypes.POINTER(fwi_survey_t)
+    lib.fwi_forward_data.argtypes = [vp, sp, ctypes.c_double, vp, ctypes.POINTER(ctypes.c_longlong)]
+    lib.fwi_forward_data.restype = ip
+    lib.fwi_jacobian.argtypes = [vp, sp, vp, ctypes.c_double, vp]
+    lib.fwi_jacobian.restype = ip
+    lib.fwi_jacobian_adjoint.argtypes = [vp, sp, vp, ctypes.c_double, vp]
+    lib.fwi_jacobian_adjoint.restype = ip
+    lib.fwi_model_to_kappa.argtypes = [vp, vp, ctypes.c_longlong]
+    lib.fwi_model_to_kappa.restype = ip
+    lib.fwi_default_gn_opts.argtypes = [ctypes.POINTER(fwi_gn_opts)]
+    lib.fwi_default_gn_opts.restype = None
+    lib.fwi_gn_iteration.argtypes = [vp, sp, vp, ctypes.POINTER(fwi_gn_opts), vp, ctypes.POINTER(fwi_gn_info)]
+    lib.fwi_gn_iteration.restype = ip
     lib.cnn_wgrad_plan.argtypes = [ip] * 8 + [ctypes.POINTER(ctypes.c_longlong)]
     lib.cnn_wgrad_plan.restype = ip
     lib.cnn_set_wgrad_path.argtypes = [ip]
@@ -289,6 +320,62 @@ def fwi_misfit_grad(ctx, src_idx, rcv_idx, d_obs, grad_m, tol: float = 1e-8) -> 
     _check(lib.fwi_misfit_grad(ctx, src.ctypes.data, src.size, rcv.ctypes.data, rcv.size, _ptr(d_obs, "complex64"),
                                tol, ctypes.byref(phi), _ptr(grad_m, "float32")), "fwi_misfit_grad")
     return phi.value
+
+
+class Survey:
+    """An FWI survey (include/helm.h fwi_survey): point-source and receiver node indices
+    (flat iz * nx + ix) and, for simultaneous sources, the weights [nsim][nsrc]."""
+
+    def __init__(self, src_idx, rcv_idx, src_w=None):
+        self.src = np.ascontiguousarray(np.asarray(src_idx, dtype=np.int32))
+        self.rcv = np.ascontiguousarray(np.asarray(rcv_idx, dtype=np.int32))
+        self.w = None if src_w is None else np.ascontiguousarray(np.asarray(src_w, dtype=np.float32))
+        self.nsim = self.src.size if self.w is None else int(self.w.shape[0])
+        self.c = fwi_survey_t(self.src.ctypes.data, self.src.size, None if self.w is None else self.w.ctypes.data,
+                              0 if self.w is None else self.nsim, self.rcv.ctypes.data, self.rcv.size)
+
+
+def fwi_forward_data(ctx, survey: Survey, d_out, tol: float = 1e-6) -> int:
+    """Synthetic data [nfreq][nsources][nrcv] into d_out; returns the Helmholtz iterations used."""
+    it = ctypes.c_longlong(0)
+    _check(lib.fwi_forward_data(ctx, ctypes.byref(survey.c), tol, _ptr(d_out, "complex64"), ctypes.byref(it)),
+           "fwi_forward_data")
+    return int(it.value)
+
+
+def fwi_jacobian(ctx, survey: Survey, dm, dd_out, tol: float = 1e-4):
+    _check(lib.fwi_jacobian(ctx, ctypes.byref(survey.c), _ptr(dm, "float32"), tol, _ptr(dd_out, "complex64")),
+           "fwi_jacobian")
+
+
+def fwi_jacobian_adjoint(ctx, survey: Survey, dd, dm_out, tol: float = 1e-4):
+    _check(lib.fwi_jacobian_adjoint(ctx, ctypes.byref(survey.c), _ptr(dd, "complex64"), tol,
+                                    _ptr(dm_out, "float32")), "fwi_jacobian_adjoint")
+
+
+def fwi_model_to_kappa(m, kappa):
+    """kappa = sqrt(m) (device tensors)."""
+    _check(lib.fwi_model_to_kappa(_ptr(m, "float32"), _ptr(kappa, "float32"), int(m.numel())),
+           "fwi_model_to_kappa")
+
+
+def fwi_default_gn_opts(**overrides) -> fwi_gn_opts:
+    o = fwi_gn_opts()
+    lib.fwi_default_gn_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def fwi_gn_iteration(ctx, survey: Survey, d_obs, m, opts=None) -> dict:
+    """One Gauss-Newton iteration; m (float32 [nz][nx]) updated in place.  Returns the info fields."""
+    o = opts if opts is not None else fwi_default_gn_opts()
+    info = fwi_gn_info()
+    _check(lib.fwi_gn_iteration(ctx, ctypes.byref(survey.c), _ptr(d_obs, "complex64"), ctypes.byref(o),
+                                _ptr(m, "float32"), ctypes.byref(info)), "fwi_gn_iteration")
+    return {k: getattr(info, k) for k, _ in fwi_gn_info._fields_}
 
 
 def helm_destroy(ctx):

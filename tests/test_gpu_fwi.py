@@ -1,0 +1,161 @@
+"""GPU parity of the Gauss-Newton FWI pieces (Sec. 3.2-3.3, Alg. 1) against the
+oracle, through the C ABI: synthetic data, the sensitivity products J v and J^T w
+(Eq. 3.10 written out from the operator of Eq. 3.1), simultaneous sources, and one
+Gauss-Newton iteration (conjugate gradients on the normal equations).
+
+Solves run to a tight tolerance (1e-8) so that the comparison is of the products
+themselves; the bounds follow the solver's accuracy (complex64 Krylov vectors,
+FP64 residual), 1e-5 for data and 1e-4 for products of two solves.  At the paper's
+sensitivity tolerance 1e-4 a solve's error is bounded by the condition number of H
+times 1e-4 (about 25 times on this problem, measured), so those products are held to 1e-2."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import fwi  # noqa: E402
+from paper_2405_17696_gb300 import media  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def native():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_17696_gb300 import build
+    build.build()
+    from paper_2405_17696_gb300 import native as n
+    return n
+
+
+def _f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def _case(hx=20.0, hz=20.0):
+    nx, nz = 64, 32
+    c_true = media.layered_velocity(nx, nz, seed=4, n_layers=6)
+    c0 = media.gaussian_smooth(c_true, 4.0)
+    gamma = media.abl_gamma(nx, nz, 8)
+    freqs = [3.0, 5.0]
+    src = [2 * nx + 4 + 8 * s for s in range(8)]
+    rcv = [2 * nx + ix for ix in range(1, nx, 2)]
+    return nx, nz, hx, hz, media.kappa_of(c_true), media.kappa_of(c0), gamma, freqs, src, rcv
+
+
+def _ctx(native, nx, nz, hx, hz, kappa, gamma, freqs, **opts):
+    om = torch.from_numpy(np.asarray([2 * math.pi * f for f in freqs], np.float32)).cuda()
+    return native.helm_setup(torch.from_numpy(np.asarray(kappa, np.float32)).cuda(),
+                             torch.from_numpy(np.asarray(gamma, np.float32)).cuda(), nx, nz, hx, hz, om,
+                             opts=native.helm_default_opts(mg_levels=3, **opts))
+
+
+def _sources(nx, nz, hx, hz, src, w=None):
+    g = np.zeros((len(src), nz * nx), np.complex128)
+    for s, k in enumerate(src):
+        g[s, k] = 1.0 / (hx * hz)
+    g = g.reshape(len(src), nz, nx)
+    return g if w is None else np.tensordot(np.asarray(w, np.float64), g, axes=1)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.mark.parametrize("sim", [False, True])
+def test_forward_data_and_sensitivities(native, sim):
+    nx, nz, hx, hz, k_true, k0, gamma, freqs, src, rcv = _case()
+    om = [float(np.float32(2 * math.pi * f)) for f in freqs]
+    w = np.where(np.random.default_rng(1).random((4, len(src))) < 0.5, -1.0, 1.0) if sim else None
+    g = _sources(nx, nz, hx, hz, src, w)
+    k64, gam = _f32(k0), _f32(gamma)
+    d_ref, _ = fwi.forward_data(k64, gam, om, hx, hz, g, np.array(rcv))
+    rng = np.random.default_rng(2)
+    dm = (rng.normal(size=(nz, nx)) * k64 ** 2 * 1e-2).astype(np.float32)
+    dd_in = (rng.normal(size=d_ref.shape) + 1j * rng.normal(size=d_ref.shape)).astype(np.complex64)
+    jv_ref = fwi.jacobian_apply(k64, gam, om, hx, hz, g, np.array(rcv), _f32(dm))
+    jt_ref = fwi.jacobian_adjoint(k64, gam, om, hx, hz, g, np.array(rcv), dd_in.astype(np.complex128))
+    sv = native.Survey(src, rcv, w)
+    ctx = _ctx(native, nx, nz, hx, hz, k0, gamma, freqs)
+    try:
+        d = np.zeros(d_ref.shape, np.complex64)
+        iters = native.fwi_forward_data(ctx, sv, d, tol=1e-8)
+        jv = np.zeros(d_ref.shape, np.complex64)
+        native.fwi_jacobian(ctx, sv, dm, jv, tol=1e-8)
+        jt = np.zeros((nz, nx), np.float32)
+        native.fwi_jacobian_adjoint(ctx, sv, dd_in, jt, tol=1e-8)
+        jv4 = np.zeros(d_ref.shape, np.complex64)
+        native.fwi_jacobian(ctx, sv, dm, jv4, tol=1e-4)
+        jt4 = np.zeros((nz, nx), np.float32)
+        native.fwi_jacobian_adjoint(ctx, sv, dd_in, jt4, tol=1e-4)
+    finally:
+        native.helm_destroy(ctx)
+    assert iters > 0
+    assert _rel(d, d_ref) <= 1e-5
+    assert _rel(jv, jv_ref) <= 1e-4
+    assert _rel(jt, jt_ref) <= 1e-4
+    assert _rel(jv4, jv_ref) <= 1e-2 and _rel(jt4, jt_ref) <= 1e-2
+    # the adjoint identity on the GPU's own products
+    lhs = float(np.real(np.vdot(dd_in.astype(np.complex128), jv.astype(np.complex128))))
+    rhs = float(np.sum(_f32(dm) * _f32(jt)))
+    assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+
+
+def test_gauss_newton_iteration_matches_the_oracle(native):
+    """One Gauss-Newton iteration (3 CG steps, full step accepted) against the oracle's
+    direction; the misfit drops and the iteration counts are reported per phase."""
+    nx, nz, hx, hz, k_true, k0, gamma, freqs, src, rcv = _case()
+    om = [float(np.float32(2 * math.pi * f)) for f in freqs]
+    g = _sources(nx, nz, hx, hz, src)
+    d_obs, _ = fwi.forward_data(_f32(k_true), _f32(gamma), om, hx, hz, g, np.array(rcv))
+    dm_ref, phi_ref, _ = fwi.gauss_newton_direction(_f32(k0), _f32(gamma), om, hx, hz, g, np.array(rcv), d_obs, 3)
+    sv = native.Survey(src, rcv)
+    m = (np.asarray(k0, np.float32) ** 2).astype(np.float32)
+    m0 = m.copy()
+    ctx = _ctx(native, nx, nz, hx, hz, k0, gamma, freqs)
+    try:
+        info = native.fwi_gn_iteration(ctx, sv, np.ascontiguousarray(d_obs, np.complex64), m,
+                                       native.fwi_default_gn_opts(tol=1e-8, tol_sens=1e-8, cg_iters=3,
+                                                                  max_backtracks=0))
+    finally:
+        native.helm_destroy(ctx)
+    assert abs(info["misfit_before"] - phi_ref) <= 1e-5 * phi_ref
+    assert info["step"] == 1.0 and info["misfit_after"] < info["misfit_before"]
+    assert info["cg_iters"] == 3
+    assert min(info["iters_forward"], info["iters_adjoint"], info["iters_sensitivity"]) > 0
+    assert _rel(_f32(m) - _f32(m0), dm_ref) <= 1e-3
+
+
+def test_frequency_continuation_lowers_the_misfit(native):
+    """Alg. 1 through the driver: two frequency windows of Gauss-Newton iterations with
+    simultaneous sources, MG-FGMRES and CNN-FGMRES with Alg. 2 retraining after each
+    iteration; the model error to the true medium drops and the Helmholtz iterations of
+    every phase are counted."""
+    from paper_2405_17696_gb300 import fwi as FWI
+    nx, nz, hx, hz, k_true, k0, gamma, _, src, rcv = _case()
+    freqs = [3.0, 4.0]
+    d_obs, _ = FWI.observed_data(native, k_true, gamma, nx, nz, hx, hz, freqs, native.Survey(src, rcv))
+    m_true = torch.from_numpy((np.asarray(k_true, np.float64) ** 2).astype(np.float32)).cuda()
+    results = {}
+    for label, retrain in (("mg", None), ("cnn", 4)):
+        m = torch.from_numpy((np.asarray(k0, np.float64) ** 2).astype(np.float32)).cuda()
+        err0 = float(torch.linalg.norm(m - m_true) / torch.linalg.norm(m_true))
+        net = native.cnn_create(3, (16, 32, 64), seed=media.SEED_CNN) if retrain else None
+        try:
+            cfg = FWI.FwiConfig(windows=[[3.0], [4.0]], gn_iters=2, cg_iters=3, sim_sources=4,
+                                retrain_steps=retrain or 0, retrain_initial=8, max_rhs=8)
+            hist = FWI.run(native, m, gamma, nx, nz, hx, hz, src, rcv, d_obs, freqs, cfg, net=net)
+        finally:
+            if net is not None:
+                native.cnn_destroy(net)
+        err1 = float(torch.linalg.norm(m - m_true) / torch.linalg.norm(m_true))
+        results[label] = (err0, err1, hist)
+        assert err1 < err0, (label, err0, err1)
+        assert len(hist.rows) == 4 and hist.total_iterations > 0
+        for r in hist.rows:
+            assert r["misfit_after"] <= r["misfit_before"]
+        if retrain:
+            assert all("retrain_loss" in r for r in hist.rows)

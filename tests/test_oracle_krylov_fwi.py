@@ -76,3 +76,56 @@ def test_misfit_zero_at_true_model():
     kappa, gamma, omegas, h, sources, receivers, _ = _fwi_problem()
     d, _ = fwi.forward_data(kappa, gamma, omegas, h, h, sources, receivers)
     assert fwi.misfit(kappa, gamma, omegas, h, h, sources, receivers, d) < 1e-20
+
+
+def test_jacobian_matches_finite_differences_of_the_data():
+    """J v (sensitivity, Eq. 3.10 from the operator of Eq. 3.1) against central differences
+    of the forward data d(m) in m = kappa^2."""
+    kappa, gamma, omegas, h, sources, receivers, _ = _fwi_problem()
+    m = kappa.astype(np.float64) ** 2
+    v = np.random.default_rng(4).normal(size=m.shape) * m * 1e-3
+    jv = fwi.jacobian_apply(kappa.astype(np.float64), gamma, omegas, h, h, sources, receivers, v)
+    eps = 1e-2
+    dp, _ = fwi.forward_data(np.sqrt(m + eps * v), gamma, omegas, h, h, sources, receivers)
+    dm_, _ = fwi.forward_data(np.sqrt(m - eps * v), gamma, omegas, h, h, sources, receivers)
+    fd = (dp - dm_) / (2 * eps)
+    assert np.linalg.norm(jv - fd) <= 1e-6 * np.linalg.norm(fd)
+
+
+def test_jacobian_adjoint_identity_and_gradient():
+    """<J v, w> = v . J^T w in the real inner product Re(sum conj(w) J v), and the misfit
+    gradient is 2 J^T r with r = d(m) - d_obs."""
+    kappa, gamma, omegas, h, sources, receivers, d_obs = _fwi_problem()
+    k64 = kappa.astype(np.float64)
+    g = np.random.default_rng(6)
+    v = g.normal(size=k64.shape)
+    wdat = g.normal(size=np.shape(d_obs)) + 1j * g.normal(size=np.shape(d_obs))
+    jv = fwi.jacobian_apply(k64, gamma, omegas, h, h, sources, receivers, v)
+    jtw = fwi.jacobian_adjoint(k64, gamma, omegas, h, h, sources, receivers, wdat)
+    lhs = float(np.real(np.vdot(wdat, jv)))
+    rhs = float(np.sum(v * jtw))
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+    d, _ = fwi.forward_data(k64, gamma, omegas, h, h, sources, receivers)
+    _, grad = fwi.misfit_and_gradient(k64, gamma, omegas, h, h, sources, receivers, d_obs)
+    jtr = fwi.jacobian_adjoint(k64, gamma, omegas, h, h, sources, receivers, d - d_obs)
+    assert np.linalg.norm(grad - 2 * jtr) <= 1e-10 * np.linalg.norm(grad)
+
+
+def test_gauss_newton_cg_reaches_the_normal_equations_solution():
+    """With as many CG iterations as unknowns, the Gauss-Newton direction equals the
+    solution of the (regularised) normal equations built from the explicit Jacobian."""
+    w = media.crop_workload(6, 4, h=50.0, freqs=(2.0,), width=1)
+    k64 = w.kappa.astype(np.float64)
+    gam = w.gamma.astype(np.float64)
+    omegas = [2 * math.pi * 2.0, 2 * math.pi * 3.0]
+    sources = media.point_source_rhs(w.nx, w.nz, [(0, 1), (0, 4)], w.h, w.h)
+    receivers = np.arange(0, w.nx)
+    d_obs, _ = fwi.forward_data(1.0 / (1.0 / k64 * 1.03), gam, omegas, w.h, w.h, sources, receivers)
+    n = k64.size
+    J = np.stack([fwi.jacobian_apply(k64, gam, omegas, w.h, w.h, sources, receivers,
+                                     np.eye(n)[i].reshape(k64.shape)).ravel() for i in range(n)], axis=1)
+    JtJ = np.real(J.conj().T @ J)
+    reg = 1e-3 * np.trace(JtJ) / n
+    dm, phi, grad = fwi.gauss_newton_direction(k64, gam, omegas, w.h, w.h, sources, receivers, d_obs, n, reg)
+    ref = np.linalg.solve(JtJ + reg * np.eye(n), -0.5 * grad.ravel())
+    assert np.linalg.norm(dm.ravel() - ref) <= 1e-6 * np.linalg.norm(ref)
