@@ -46,6 +46,7 @@ if ROOT not in sys.path:
 from paper_2405_17696_gb300 import media  # noqa: E402
 
 METRIC = "Helmholtz RHS solved/sec to 1e-6 rel. residual: CNN-FGMRES vs MG-FGMRES, 1 GB300"
+CHECKPOINT = os.path.join(ROOT, "paper_2405_17696_gb300", "weights", "encoder_solver_1024x512_8hz.ckpt")
 UNIT = "RHS/s"
 TOL = 1e-6
 FALLBACK_HBM_GBS = 6800.0
@@ -441,6 +442,161 @@ def roofline_of(prof, flops):
     return r
 
 
+def run_retrain_series(args, native, dev, stream, world, rank):
+    """CNN-FGMRES iterations along the medium path m_t (t = 0..8, Gaussian-smoothed to true,
+    a stand-in for the models an FWI visits) on the 1024x512, 8 Hz batch (every fourth of
+    the 128 sources): MG-FGMRES, the network as loaded, and the network retrained by Alg. 2
+    for --retrain-steps steps on each m_t (cumulative) before its solve."""
+    import torch
+    from paper_2405_17696_gb300 import retrain as RT
+    w = media.workload_cnn(args.sources_cnn)
+    c_true = media.layered_velocity(w.nx, w.nz, seed=media.SEED_MODEL)
+    kappas = media.medium_sequence(c_true, 8, 10.0)
+    pos = w.positions[::4]
+    rhs = torch.from_numpy(media.point_source_rhs(w.nx, w.nz, pos, w.h, w.h)).to(dev)
+    nb = rhs.shape[0]
+    gam = torch.from_numpy(w.gamma).to(dev)
+    om = torch.tensor(w.omegas, dtype=torch.float32, device=dev)
+    nets = {"cnn_no_retraining": native.cnn_load(args.checkpoint), "cnn_retrained": native.cnn_load(args.checkpoint)}
+    rows, t_retrain = [], 0.0
+    for t, kap in enumerate(kappas):
+        k = torch.from_numpy(kap).to(dev)
+        row = {"t": t}
+        for label, net in [("mg", None)] + list(nets.items()):
+            ctx = native.helm_setup(k, gam, w.nx, w.nz, w.h, w.h, om, net=net, opts=native.helm_default_opts(
+                mg_levels=3, max_iter=1000, max_rhs=nb, stream=stream.cuda_stream,
+                precond=native.HELM_PC_CNN if net else native.HELM_PC_MG))
+            try:
+                if label == "cnn_retrained" and args.retrain_steps > 0:
+                    t0 = time.perf_counter()
+                    RT.retrain(native, net, ctx, cfg=RT.RetrainConfig(
+                        initial_size=128, data_epochs=3, epochs=1 << 20, batch=16, lr=1e-4,
+                        max_steps=args.retrain_steps, relative_loss=True, warmup_steps=0,
+                        seed=media.SEED_DATAGEN + 100 * t))
+                    torch.cuda.synchronize(dev)
+                    t_retrain += time.perf_counter() - t0
+                x = torch.zeros(rhs.shape, dtype=torch.complex128, device=dev)
+                _, it, rel, _ = native.helm_solve(ctx, rhs, x, nb, None, TOL, native.HELM_SOLVE_ZERO_X0)
+                row[label] = {"mean": float(it.mean()), "max": int(it.max()), "max_rel_residual": float(rel.max())}
+            finally:
+                native.helm_destroy(ctx)
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    for net in nets.values():
+        native.cnn_destroy(net)
+    tot = {k: sum(r[k]["mean"] for r in rows) * nb for k in ("mg", "cnn_no_retraining", "cnn_retrained")}
+    line = {"metric": "CNN-FGMRES iterations to 1e-6 along a medium sequence, with and without Alg. 2 retraining",
+            "value": tot["cnn_retrained"], "unit": "total FGMRES iterations", "higher_is_better": False,
+            "n_gpus": world, "data": "synthetic",
+            "config": {"workload": f"retraining_series_{w.nx}x{w.nz}_{nb}rhs_9media", "freq_hz": 8.0,
+                       "media": "m_t = (1 - t/8) G_10(m_true) + (t/8) m_true, t = 0..8 (seeded 12-layer m_true)",
+                       "retrain_steps_per_medium": args.retrain_steps,
+                       "initial_weights": os.path.relpath(args.checkpoint, ROOT)},
+            "totals": tot, "retrain_seconds": t_retrain, "per_medium": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_fwi_c5(args, native, dev, stream, world, rank):
+    """FWI misfit and adjoint-state gradient (Eq. 3.5, Sec. 4.3) on the 2048 x 1024 (h = 10 m)
+    fault-and-salt model: 256 sources and 512 receivers on row 2, 8 frequencies in
+    [2.5, 10] Hz, each on its own grid of about ten points per 1.5 km/s wavelength (sizes
+    multiples of 16).  Set-up (untimed): observed data from the true model on every grid.
+    Timed: misfit and gradient at the Gaussian-smoothed starting model, the eight
+    frequency contexts solved concurrently (one host thread each, own streams)."""
+    import threading
+    import torch
+    from paper_2405_17696_gb300 import fwi as FWI
+    nx0, nz0, h0 = 2048, 1024, 10.0
+    c_true = media.fault_salt_velocity(nx0, nz0, seed=media.SEED_MODEL)
+    c_init = media.gaussian_smooth(c_true, 10.0)
+    k_true0 = torch.from_numpy(media.kappa_of(c_true)).to(dev)
+    k_init0 = torch.from_numpy(media.kappa_of(c_init)).to(dev)
+    freqs = [float(f) for f in np.linspace(2.5, 10.0, 8)]
+    lx, lz = nx0 * h0, nz0 * h0
+    ctxs, items = [], []
+    t_setup = time.perf_counter()
+    for f in freqs:
+        nx, nz, hx, hz = FWI.window_grid_size(lx, lz, f)
+        kt = torch.empty((nz, nx), dtype=torch.float32, device=dev)
+        ki = torch.empty((nz, nx), dtype=torch.float32, device=dev)
+        native.helm_resample(k_true0, nx0, nz0, kt, nx, nz)
+        native.helm_resample(k_init0, nx0, nz0, ki, nx, nz)
+        gam = torch.from_numpy(media.abl_gamma(nx, nz, max(8, int(round(320.0 / hx))))).to(dev)
+        src = [2 * nx + int(round((s + 0.5) * nx / 256)) for s in range(256)]
+        rcv = [2 * nx + int(round((r + 0.5) * nx / 512)) for r in range(512)]
+        st = torch.cuda.Stream(dev)
+        om = torch.tensor([2 * math.pi * f], dtype=torch.float32, device=dev)
+        ctx = native.helm_setup(kt, gam, nx, nz, hx, hz, om, opts=native.helm_default_opts(
+            mg_levels=3, max_iter=2000, max_rhs=128, stream=st.cuda_stream))
+        ctxs.append(ctx)
+        sv = native.Survey(src, rcv)
+        d = torch.zeros((1, len(src), len(rcv)), dtype=torch.complex64, device=dev)
+        native.fwi_forward_data(ctx, sv, d, tol=TOL)
+        native.helm_set_medium(ctx, ki, gam, om)
+        items.append({"f": f, "grid": [nx, nz], "h": [hx, hz], "ctx": ctx, "sv": sv, "d": d,
+                      "g": torch.zeros((nz, nx), dtype=torch.float32, device=dev), "om": om, "gam": gam})
+    torch.cuda.synchronize(dev)
+    t_setup = time.perf_counter() - t_setup
+    results = [None] * len(items)
+
+    def work(i):
+        it = items[i]
+        torch.cuda.set_device(dev)
+        results[i] = native.fwi_misfit_grad(it["ctx"], it["sv"].src, it["sv"].rcv, it["d"], it["g"], tol=TOL)
+
+    for _ in range(max(0, min(args.warmup, 1))):
+        for i in range(len(items)):
+            work(i)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(len(items))]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    torch.cuda.synchronize(dev)
+    secs = time.perf_counter() - t0
+    # the gradient against the oracle on a 64 x 32 crop of the model (3 and 5 Hz, 8 sources)
+    from oracle import fwi as OF
+    crop_c = c_true[:32, 1000:1064]
+    crop_c0 = media.gaussian_smooth(crop_c, 4.0)
+    gam_c = media.abl_gamma(64, 32, 8)
+    src_c = [(2, 4 + 8 * s) for s in range(8)]
+    rcv_c = [2 * 64 + ix for ix in range(1, 64, 2)]
+    om_c = [float(np.float32(2 * math.pi * f)) for f in (3.0, 5.0)]
+    gc = media.point_source_rhs(64, 32, src_c, h0, h0)
+    k_c = media.kappa_of(crop_c).astype(np.float64)
+    k_c0 = media.kappa_of(crop_c0)
+    d_c, _ = OF.forward_data(k_c, gam_c.astype(np.float64), om_c, h0, h0, gc, np.array(rcv_c))
+    _, g_ref = OF.misfit_and_gradient(k_c0.astype(np.float64), gam_c.astype(np.float64), om_c, h0, h0, gc,
+                                      np.array(rcv_c), d_c)
+    ctx_c = native.helm_setup(torch.from_numpy(k_c0).to(dev), torch.from_numpy(gam_c).to(dev), 64, 32, h0, h0,
+                              torch.tensor(om_c, dtype=torch.float32, device=dev),
+                              opts=native.helm_default_opts(mg_levels=3))
+    g_gpu = np.zeros((32, 64), np.float32)
+    native.fwi_misfit_grad(ctx_c, [iz * 64 + ix for iz, ix in src_c], rcv_c,
+                           np.ascontiguousarray(d_c, np.complex64), g_gpu, tol=1e-8)
+    native.helm_destroy(ctx_c)
+    crop_err = float(np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref))
+    for c in ctxs:
+        native.helm_destroy(c)
+    line = {"metric": "FWI misfit + adjoint-state gradient, 8 frequencies x 256 sources, seconds", "value": secs,
+            "unit": "s", "higher_is_better": False, "n_gpus": world, "data": "synthetic", "dtype": "c64/f64",
+            "config": {"workload": "fwi_misfit_grad_2048x1024_256src_512rcv_8freq",
+                       "model": "seeded 12-layer model, 3 fault offsets, 4.5 km/s salt ellipse; start: Gaussian "
+                                "smoothing (10 cells)",
+                       "grids": [{"f_hz": round(it["f"], 3), "grid": it["grid"], "h_m": [round(v, 2) for v in it["h"]]}
+                                 for it in items],
+                       "solver": "MG-FGMRES to 1e-6 (forward and conjugated adjoint solves), contexts concurrent",
+                       "tol": TOL},
+            "misfit": float(sum(results)), "setup_seconds": t_setup,
+            "rhs_solved": 2 * 256 * len(items),
+            "gradient_rel_error_vs_oracle_64x32_crop": crop_err}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2405_17696_gb300 import native, retrain as RT
@@ -451,6 +607,13 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     sampler = ClockSampler(local)
+
+    if args.workload == "retrain":
+        run_retrain_series(args, native, dev, stream, world, rank)
+        return
+    if args.workload == "fwi":
+        run_fwi_c5(args, native, dev, stream, world, rank)
+        return
 
     if args.workload == "net":
         # the encoder-solver network alone: one forward pass (solver U-Net, contexts
@@ -528,8 +691,17 @@ def run_ours(args, rank, world):
     w = media.workload_cnn(args.sources_cnn)
     prob = Problem(native, w, dev)
     widths = (16, 32, 64, 128)
-    net = native.cnn_create(len(widths), widths)
-    native.cnn_init_params(net, media.SEED_CNN, 0.5)
+    use_ckpt = args.checkpoint and os.path.exists(args.checkpoint) and args.train_steps is None
+    if use_ckpt:
+        # initial weights trained offline by the library's own Alg. 2 training on other media of
+        # the family (paper_2405_17696_gb300.train_checkpoint), as the paper trains its initial
+        # weights offline (Sec. 5.2); light Alg. 2 retraining on this medium follows (set-up)
+        net = native.cnn_load(args.checkpoint)
+        with open(os.path.splitext(args.checkpoint)[0] + ".json") as fh:
+            prov = json.load(fh)
+    else:
+        net = native.cnn_create(len(widths), widths, seed=media.SEED_CNN)
+        prov = None
     opts = dict(mg_levels=3, max_rhs=prob.nb, max_iter=1000, stream=stream.cuda_stream)
     ctx_cnn = native.helm_setup(prob.kappa, prob.gamma, w.nx, w.nz, w.h, w.h, prob.omegas, net=net,
                                 opts=native.helm_default_opts(precond=native.HELM_PC_CNN, **opts))
@@ -537,16 +709,28 @@ def run_ours(args, rank, world):
                                opts=native.helm_default_opts(**opts))
     native.helm_set_graphs(ctx_mg, bool(args.graphs))
     tune = autotune_of(native, ctx_cnn, prob.nb, args.autotune)
-    # set-up: Alg. 2 training on this medium (not timed)
-    steps_data = sum(128 * 2 ** i // 16 for i in range(3))
-    epochs = 3 + max(1, -(-(args.train_steps - steps_data) // 64))
-    cfg = RT.RetrainConfig(initial_size=128, data_epochs=3, epochs=epochs, batch=16, lr=1e-3, lr_final=1e-4,
-                           max_steps=args.train_steps, seed=media.SEED_DATAGEN + rank, relative_loss=True)
+    # set-up (not timed): Alg. 2 on this medium
+    steps = args.retrain_steps if use_ckpt else (400 if args.train_steps is None else args.train_steps)
+    epochs = 3 + max(1, -(-(steps - 56) // 64))
+    cfg = RT.RetrainConfig(initial_size=128, data_epochs=3, epochs=epochs, batch=16,
+                           lr=1e-4 if use_ckpt else 1e-3, lr_final=1e-4, max_steps=steps,
+                           seed=media.SEED_DATAGEN + rank, relative_loss=True, warmup_steps=0 if use_ckpt else 100)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    hist = RT.retrain(native, net, ctx_cnn, cfg=cfg)
+    hist = RT.retrain(native, net, ctx_cnn, cfg=cfg) if steps > 0 else RT.RetrainHistory()
     torch.cuda.synchronize(dev)
     train_s = time.perf_counter() - t0
+    training = {"steps": hist.steps, "seconds": train_s, "batch": 16, "lr": [cfg.lr, cfg.lr_final],
+                "loss": "Eq. 4.2 with each pair weighted by 1 / ||e||^2",
+                "loss_first_epoch": hist.epoch_loss[0] if hist.epoch_loss else None,
+                "loss_last_epoch": hist.epoch_loss[-1] if hist.epoch_loss else None}
+    if prov is not None:
+        training["initial_weights"] = {"checkpoint": os.path.relpath(args.checkpoint, ROOT),
+                                       "offline_steps": prov.get("steps"), "offline_seconds": prov.get("seconds"),
+                                       "train_media_seeds": prov.get("train_media_seeds"),
+                                       "offline_loss_last_200": prov.get("loss_last_200"),
+                                       "benchmark_medium_in_offline_training":
+                                           media.SEED_MODEL in (prov.get("train_media_seeds") or [])}
 
     ms, its, relmax, launches, clocks = timed(prob, ctx_cnn, args.steps, args.warmup, dev, world, stream, sampler)
     solved = timed.solved
@@ -564,10 +748,7 @@ def run_ours(args, rank, world):
                           "unsolved_rhs": world * prob.nb * args.steps - mg_solved,
                           "iterations": {"mean": float(mg_its.mean()), "max": int(mg_its.max()),
                                          "min": int(mg_its.min())}, "max_rel_residual": mg_rel},
-            "training": {"steps": hist.steps, "seconds": train_s, "batch": 16, "lr": [1e-3, 1e-4],
-                         "loss": "Eq. 4.2 with each pair weighted by 1 / ||e||^2",
-                         "loss_first_epoch": hist.epoch_loss[0] if hist.epoch_loss else None,
-                         "loss_last_epoch": hist.epoch_loss[-1] if hist.epoch_loss else None},
+            "training": training,
             "autotune": tune, "gpu_launches": int(launches), "clocks": clocks}
     if not args.no_extras:
         prof, flops = profile_step(native, prob, ctx_cnn)
@@ -606,11 +787,18 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["cnn", "mg", "net"], default="cnn",
+    ap.add_argument("--workload", choices=["cnn", "mg", "net", "retrain", "fwi"], default="cnn",
                     help="cnn: CNN-FGMRES vs MG-FGMRES at 1024x512 (default); mg: MG-FGMRES at 512x256; "
-                         "net: the network's forward pass alone at 1024x512")
-    ap.add_argument("--train-steps", type=int, default=400,
-                    help="Adam steps of the set-up training (Alg. 2) before the CNN-FGMRES timing")
+                         "net: the network's forward pass alone at 1024x512; retrain: CNN-FGMRES iterations "
+                         "along a medium sequence with and without Alg. 2 retraining; fwi: FWI misfit and "
+                         "gradient at 2048x1024 on per-frequency grids")
+    ap.add_argument("--train-steps", type=int, default=None,
+                    help="train the network from seeded weights for this many Alg. 2 steps instead of loading "
+                         "the checkpoint (default: the checkpoint when it exists, else 400 steps)")
+    ap.add_argument("--checkpoint", default=CHECKPOINT,
+                    help="initial weights (cnn_load) for the cnn workload")
+    ap.add_argument("--retrain-steps", type=int, default=200,
+                    help="Alg. 2 steps on the benchmark medium after loading the checkpoint (set-up, untimed)")
     ap.add_argument("--sources", type=int, default=64,
                     help="mg workload: sources per frequency (64 = the benchmark workload)")
     ap.add_argument("--sources-cnn", type=int, default=128,

@@ -250,6 +250,24 @@ int fwi_model_to_kappa(const float* m, float* kappa, long long n);
 int fwi_gn_iteration(helm_ctx* ctx, const fwi_survey* survey, const helm_c64* d_obs, const fwi_gn_opts* opts,
                      float* m, fwi_gn_info* info);
 
+/* ---- several grids (per-frequency grids of the FWI windows) ------------------------------
+ * helm_resample: dst = alpha * bilinear(src) + beta * dst between two node grids covering the
+ * same rectangle (node (i, j) of an n_x x n_z grid at the cell centre ((i + 1/2) Lx / n_x,
+ * (j + 1/2) Lz / n_z); source positions clamped to its outermost nodes).  float32 device
+ * arrays [nz0][nx0] -> [nz1][nx1], not aliased; issued on `stream` (cudaStream_t) and waited
+ * for.  With beta = 1 it adds a resampled update to a field. */
+int helm_resample(const float* src, int nx0, int nz0, float* dst, int nx1, int nz1, float alpha, float beta,
+                  void* stream);
+/* helm_solve for several contexts in one call (different grids, media or frequencies):
+ * context i solves its nrhs[i] right-hand sides rhs[i] into x[i] (freq_idx[i] may be NULL,
+ * freq_idx itself may be NULL; stats may be NULL or an array of nctx), each from its own host
+ * thread on its context's stream, so that contexts with distinct streams share the GPU.
+ * A context may appear once.  Returns the first hard error, else HELM_ENOCONV /
+ * HELM_EBREAKDOWN if some context had them, else HELM_OK; helm_last_error() names the
+ * context. */
+int helm_solve_multi(helm_ctx* const* ctxs, int nctx, const helm_c64* const* rhs, helm_c128* const* x,
+                     const int* nrhs, const int* const* freq_idx, double tol, int flags, helm_stats* stats);
+
 void helm_destroy(helm_ctx* ctx);
 
 /* ---------------------------------------------------------------------------

@@ -23,10 +23,12 @@ from . import multigrid as MG
 from .krylov import fgmres_cycle
 
 
-def make_samples(kappa, gamma, omega, h, x, iters, params=None):
+def make_samples(kappa, gamma, omega, h, x, iters, params=None, hz=None):
+    """Eq. 4.3 pairs; h is hx, and hz (default h) the vertical spacing."""
+    hz = h if hz is None else hz
     p = params if params is not None else MG.VCycleParams()
-    pc = MG.VCyclePreconditioner(kappa, gamma, omega, h, h, p)
-    A = lambda u: H.helmholtz_apply(u, kappa, gamma, omega, h, h)
+    pc = MG.VCyclePreconditioner(kappa, gamma, omega, h, hz, p)
+    A = lambda u: H.helmholtz_apply(u, kappa, gamma, omega, h, hz)
     rs, es = [], []
     for xi, k in zip(np.asarray(x, dtype=np.complex128), iters):
         b = A(xi)
@@ -59,26 +61,31 @@ def mvu_compose(e0, r, A, pc, composition: str = "residual"):
     raise ValueError(composition)
 
 
-def network_error(P, specs, kappa, gamma, omega, h, r, quantize=None):
-    """e_net = h^2 rms(r) (out_re + i out_im) for residuals r [B][nz][nx]."""
-    enc = cnn.encoder_input(kappa, gamma, omega, h)
+def network_error(P, specs, kappa, gamma, omega, h, r, quantize=None, hz=None):
+    """e_net = hx hz rms(r) (out_re + i out_im) for residuals r [B][nz][nx]; on an
+    anisotropic grid (hz given) the network sees the geometric-mean spacing sqrt(hx hz)
+    in its input w h kappa, and the output scale is hx hz."""
+    hz = h if hz is None else hz
+    hg = float(np.sqrt(h * hz))
+    enc = cnn.encoder_input(kappa, gamma, omega, hg)
     x, rms = cnn.solver_input(r, gamma)
     if quantize is not None:
         enc, x = quantize(enc), quantize(x)
     out, tape = cnn.network_forward(P, specs, enc, x, quantize=quantize)
-    return cnn.solver_output_to_error(out, rms, h), out, tape, rms
+    return cnn.solver_output_to_error(out, rms, hg), out, tape, rms
 
 
-def refine_from_estimate(kappa, gamma, omega, h, r, e, e_net, literal=False, params=None):
+def refine_from_estimate(kappa, gamma, omega, h, r, e, e_net, literal=False, params=None, hz=None):
     """The data step of Alg. 2 (Sec. 4.2) given the network's error estimates.
 
     For each pair (r, e) with H e = r: e~ = x after one V-cycle-preconditioned
     (F)GMRES step on H x = r started from x0 = e_net, and the new pair is
     (r - H e~, e - e~) in the residual-correction reading (the error that is still
     left after the step, with its residual), or (H e~, e~) as Alg. 2 prints it."""
+    hz = h if hz is None else hz
     p = params if params is not None else MG.VCycleParams()
-    pc = MG.VCyclePreconditioner(kappa, gamma, omega, h, h, p)
-    A = lambda u: H.helmholtz_apply(u, kappa, gamma, omega, h, h)
+    pc = MG.VCyclePreconditioner(kappa, gamma, omega, h, hz, p)
+    A = lambda u: H.helmholtz_apply(u, kappa, gamma, omega, h, hz)
     r2, e2 = [], []
     for ri, ei, x0 in zip(np.asarray(r, dtype=np.complex128), np.asarray(e, dtype=np.complex128),
                           np.asarray(e_net, dtype=np.complex128)):
@@ -92,25 +99,27 @@ def refine_from_estimate(kappa, gamma, omega, h, r, e, e_net, literal=False, par
     return np.stack(r2), np.stack(e2)
 
 
-def refine_samples(P, specs, kappa, gamma, omega, h, r, e, literal=False, params=None, quantize=None):
+def refine_samples(P, specs, kappa, gamma, omega, h, r, e, literal=False, params=None, quantize=None, hz=None):
     """Alg. 2 data step with the network of parameters P as the estimator
     (network output alone, no V-cycle)."""
-    e_net, _, _, _ = network_error(P, specs, kappa, gamma, omega, h, r, quantize)
-    return refine_from_estimate(kappa, gamma, omega, h, r, e, e_net, literal, params)
+    e_net, _, _, _ = network_error(P, specs, kappa, gamma, omega, h, r, quantize, hz=hz)
+    return refine_from_estimate(kappa, gamma, omega, h, r, e, e_net, literal, params, hz=hz)
 
 
-def loss_and_grad(P, specs, kappa, gamma, omega, h, r, e, quantize=None, relative=False, grad_quantize=None):
+def loss_and_grad(P, specs, kappa, gamma, omega, h, r, e, quantize=None, relative=False, grad_quantize=None,
+                  hz=None):
     """(loss, {name: (dw, db)}) of Eq. 4.2 for one batch of one medium/frequency;
     relative=True weighs sample i by 1 / ||e_i||^2.  quantize rounds the inputs and
     stored activations, grad_quantize the gradient operand of every convolution
     (both bf16_round for a BF16 network)."""
-    e_net, out, tape, rms = network_error(P, specs, kappa, gamma, omega, h, r, quantize)
+    e_net, out, tape, rms = network_error(P, specs, kappa, gamma, omega, h, r, quantize, hz=hz)
+    hz = h if hz is None else hz
     m = r.shape[0]
     e = np.asarray(e, dtype=np.complex128)
     d = e_net - e
     wt = 1.0 / np.sum(np.abs(e) ** 2, axis=(1, 2)) if relative else np.ones(m)
     loss = float(np.sum(wt * np.sum(np.abs(d) ** 2, axis=(1, 2))) / m)
-    s = (h * h) * rms[:, None, None] * wt[:, None, None]
+    s = (h * hz) * rms[:, None, None] * wt[:, None, None]
     g_out = np.stack([2.0 * d.real * s / m, 2.0 * d.imag * s / m], axis=-1)
     grads, _ = cnn.backward(P, specs, tape, g_out, grad_quantize=grad_quantize)
     return loss, grads

@@ -15,6 +15,7 @@ namespace helm {
 
 static thread_local std::string g_last_error;
 static std::atomic<long long> g_launches{0};
+static thread_local long long t_launches = 0;   // this thread's launches (graph capture accounting)
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -29,6 +30,7 @@ const char* kernel_name(int id) {
 
 LaunchScope::LaunchScope(const helm_ctx* ctx, int kid) : c(const_cast<helm_ctx*>(ctx)), id(kid), slot(0) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
+    ++t_launches;
     if (!c) return;   // launches outside a context are only counted
     c->prof.launches[id] += 1;
     if (!c->prof.on) return;
@@ -358,7 +360,7 @@ int fgmres_batch(helm_ctx* c, const float2* rhs, double2* x, int nb, double tol,
                 (void)cudaGetLastError();
                 c->capture_stream = nullptr;
             }
-            const long long g0 = g_launches.load();
+            const long long g0 = t_launches;   // this thread's count: other threads may launch meanwhile
             long long k0[K_COUNT];
             for (int i = 0; i < K_COUNT; ++i) k0[i] = c->prof.launches[i];
             bool ok = false;
@@ -378,8 +380,9 @@ int fgmres_batch(helm_ctx* c, const float2* rhs, double2* x, int nb, double tol,
                 }
             }
             // the captured launches did not run: count them per replay instead
-            g_delta = g_launches.load() - g0;
+            g_delta = t_launches - g0;
             g_launches.fetch_sub(g_delta);
+            t_launches -= g_delta;
             for (int i = 0; i < K_COUNT; ++i) {
                 k_delta[i] = c->prof.launches[i] - k0[i];
                 c->prof.launches[i] = k0[i];
@@ -395,6 +398,7 @@ int fgmres_batch(helm_ctx* c, const float2* rhs, double2* x, int nb, double tol,
         if (gg.exec) {
             HELM_CK(cudaGraphLaunch(gg.exec, c->stream));
             g_launches.fetch_add(g_delta);
+            t_launches += g_delta;
             for (int i = 0; i < K_COUNT; ++i) c->prof.launches[i] += k_delta[i];
         } else {
             HELM_TRY(cycle());
@@ -648,6 +652,7 @@ int helm_set_medium(helm_ctx* c, const float* kappa, const float* gamma, const f
     }
     for (int l = 1; !s && l < (int)c->lev.size(); ++l) s = launch_galerkin(c, l);
     if (!s && c->net) s = cnn_ctx_setup(c);
+    if (!s) c->cnn_stale = false;
     if (!s) {
         c->omega.resize(nfreq);
         cudaError_t e = cudaMemcpyAsync(c->omega.data(), so.dev, nfreq * sizeof(float), cudaMemcpyDeviceToHost,

@@ -389,7 +389,7 @@ int cnn_refresh_weights(cnn_model* m, cudaStream_t st) {
 int cnn_encoder_input(const helm_ctx* c, void* out) {
     const long long n = (long long)c->nx * c->nz;
     LaunchScope scope(c, K_CNN_IO);
-    encoder_input_kernel<<<1184, 256, 0, c->stream>>>(c->mg, c->omega_d, c->hx, c->nfreq, n, (__nv_bfloat16*)out);
+    encoder_input_kernel<<<1184, 256, 0, c->stream>>>(c->mg, c->omega_d, std::sqrt(c->hx * c->hz), c->nfreq, n, (__nv_bfloat16*)out);
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -461,7 +461,7 @@ int cnn_ctx_setup(helm_ctx* c) {
     c->cnn_z.clear();
     {
         LaunchScope scope(c, K_CNN_IO);
-        encoder_input_kernel<<<1184, 256, 0, c->stream>>>(c->mg, c->omega_d, c->hx, c->nfreq, n,
+        encoder_input_kernel<<<1184, 256, 0, c->stream>>>(c->mg, c->omega_d, std::sqrt(c->hx * c->hz), c->nfreq, n,
                                                           (__nv_bfloat16*)c->cnn_in);
         HELM_CK(cudaGetLastError());
     }
@@ -500,6 +500,11 @@ int cnn_ctx_compact(helm_ctx* c, int nb) {
 }
 
 int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const int* mask, int with_vcycle) {
+    // context features computed with the network's current weights (stale after training steps)
+    if (c->cnn_stale) {
+        HELM_TRY(cnn_ctx_setup(c));
+        c->cnn_stale = false;
+    }
     cnn_model* m = c->net;
     const long long n = (long long)c->nx * c->nz;
     {
@@ -720,6 +725,9 @@ void cnn_destroy(cnn_model* m) {
     if (!m) return;
     cudaDeviceSynchronize();
     if (m->wg_scratch) cudaFree(m->wg_scratch);
+    for (auto* a : {&m->fw_arena, &m->bw_arena, &m->io_arena})
+        for (void* p : *a)
+            if (p) cudaFree(p);
     for (void* p : m->allocations) cudaFree(p);
     delete m;
 }

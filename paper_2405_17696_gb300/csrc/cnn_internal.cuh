@@ -42,9 +42,35 @@ struct cnn_model {
     std::vector<void*> allocations;
     float* wg_scratch = nullptr;  // weight-gradient partial sums (grown on demand, freed with the model)
     size_t wg_scratch_n = 0;
+    // Buffers of a training step, reused by call order from step to step (the k-th buffer
+    // of a pass serves the k-th request of every later pass; grown when a request is larger):
+    // the forward pass's activations, the backward pass's scratch, the loss inputs/outputs.
+    std::vector<void*> fw_arena, bw_arena, io_arena;
+    std::vector<size_t> fw_arena_bytes, bw_arena_bytes, io_arena_bytes;
 };
 
 namespace helm {
+
+// The k-th buffer of an arena, at least `bytes` long (reallocated when smaller); nullptr
+// when the device is out of memory.
+inline void* arena_buffer(std::vector<void*>& bufs, std::vector<size_t>& sizes, size_t k, size_t bytes) {
+    if (k >= bufs.size()) {
+        bufs.resize(k + 1, nullptr);
+        sizes.resize(k + 1, 0);
+    }
+    if (sizes[k] < bytes) {
+        if (bufs[k]) cudaFree(bufs[k]);
+        bufs[k] = nullptr;
+        sizes[k] = 0;
+        if (cudaMalloc(&bufs[k], bytes ? bytes : 16) != cudaSuccess) {
+            (void)cudaGetLastError();
+            bufs[k] = nullptr;
+            return nullptr;
+        }
+        sizes[k] = bytes;
+    }
+    return bufs[k];
+}
 
 int pad16(int c);
 int npad_of(int c);

@@ -466,9 +466,6 @@ __global__ void adam_kernel(float* __restrict__ th, float* __restrict__ g, float
 class Backward {
    public:
     Backward(cnn_model* m, const helm_ctx* c, cudaStream_t st) : m_(m), c_(c), st_(st) {}
-    ~Backward() {
-        for (void* p : owned_) cudaFree(p);
-    }
 
     // gradient buffer of an activation (allocated and zeroed on first use)
     float* grad_of(const void* act, size_t n) {
@@ -548,22 +545,21 @@ class Backward {
     }
 
    private:
+    // scratch of the backward pass from the model's arena (the k-th request of a pass reuses
+    // the k-th buffer of the previous step: one training step's pass has the same sequence)
     void* alloc(size_t bytes) {
-        void* p = nullptr;
-        if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
-            (void)cudaGetLastError();
+        void* p = arena_buffer(m_->bw_arena, m_->bw_arena_bytes, next_++, bytes);
+        if (!p) {
             ok_ = false;
             set_error("out of device memory in the backward pass");
-            return nullptr;
         }
-        owned_.push_back(p);
         return p;
     }
+    size_t next_ = 0;
     cnn_model* m_;
     const helm_ctx* c_;
     cudaStream_t st_;
     std::unordered_map<const void*, float*> G_;
-    std::vector<void*> owned_;
     bool ok_ = true;
 };
 
@@ -596,24 +592,28 @@ int cnn_loss_grad_impl(cnn_model* m, helm_ctx* c, const float2* r, const float2*
     cudaStream_t st = c->stream;
     const long long n = (long long)c->nx * c->nz;
     const int nfreq = c->nfreq;
-    __nv_bfloat16 *xe = nullptr, *xs = nullptr;
-    float *out = nullptr, *gout = nullptr, *rms = nullptr, *wt = nullptr;
-    double* dloss = nullptr;
     int s = HELM_OK;
     auto ck = [&](cudaError_t e2) { if (e2 != cudaSuccess && s == HELM_OK) { set_error(cudaGetErrorString(e2)); s = HELM_ECUDA; } };
-    ck(cudaMalloc(&xe, (size_t)nfreq * n * 16 * sizeof(__nv_bfloat16)));
-    ck(cudaMalloc(&xs, (size_t)nb * n * 16 * sizeof(__nv_bfloat16)));
-    ck(cudaMalloc(&out, (size_t)nb * n * 2 * sizeof(float)));
-    ck(cudaMalloc(&gout, (size_t)nb * n * 2 * sizeof(float)));
-    ck(cudaMalloc(&rms, (size_t)nb * sizeof(float)));
-    if (m->loss_kind == 1) ck(cudaMalloc(&wt, (size_t)nb * sizeof(float)));
-    ck(cudaMalloc(&dloss, sizeof(double)));
+    // loss inputs and outputs from the model's arena (slots 2.. ; 0 and 1 hold the batch)
+    size_t slot = 2;
+    auto io = [&](size_t bytes) -> void* {
+        void* p = arena_buffer(m->io_arena, m->io_arena_bytes, slot++, bytes);
+        if (!p && s == HELM_OK) { set_error("out of device memory for the training step"); s = HELM_ENOMEM; }
+        return p;
+    };
+    auto* xe = (__nv_bfloat16*)io((size_t)nfreq * n * 16 * sizeof(__nv_bfloat16));
+    auto* xs = (__nv_bfloat16*)io((size_t)nb * n * 16 * sizeof(__nv_bfloat16));
+    auto* out = (float*)io((size_t)nb * n * 2 * sizeof(float));
+    auto* gout = (float*)io((size_t)nb * n * 2 * sizeof(float));
+    auto* rms = (float*)io((size_t)nb * sizeof(float));
+    auto* wt = m->loss_kind == 1 ? (float*)io((size_t)nb * sizeof(float)) : nullptr;
+    auto* dloss = (double*)io(sizeof(double));
     if (!s) ck(cudaMemsetAsync(dloss, 0, sizeof(double), st));
     if (!s) s = cnn_encoder_input(c, xe);
     if (!s) s = cnn_solver_input(c, r, nb, xs, rms);
     std::vector<TapeOp> tape;
     if (!s) {
-        Runner run(m, c, st);   // activations live until the backward pass is done
+        Runner run(m, c, st, &m->fw_arena, &m->fw_arena_bytes);   // activations live until the backward pass is done
         run.set_tape(&tape);
         run.set_zmap(c->rhs_freq, c->nfreq);
         std::vector<__nv_bfloat16*> z;
@@ -633,12 +633,10 @@ int cnn_loss_grad_impl(cnn_model* m, helm_ctx* c, const float2* r, const float2*
             s = bw.run(tape, nfreq);
             ck(cudaStreamSynchronize(st));
         }
-        // the encoder's context features were handed over to us
-        for (__nv_bfloat16* p : z) cudaFree(p);
+        // (the encoder's context features are arena buffers of the model: nothing to free)
     }
     if (!s) s = check_conv_error(m, st);
     if (!s && loss) ck(cudaMemcpy(loss, dloss, sizeof(double), cudaMemcpyDeviceToHost));
-    cudaFree(xe); cudaFree(xs); cudaFree(out); cudaFree(gout); cudaFree(rms); cudaFree(wt); cudaFree(dloss);
     return s;
 }
 
@@ -684,9 +682,9 @@ int cnn_loss_grad(cnn_model* net, helm_ctx* c, const helm_c64* r, const helm_c64
     HELM_TRY(upload_freqs(c, freq_idx, nb));
     HELM_TRY(ensure_train_state(net));
     const size_t n = (size_t)c->nx * c->nz;
-    float2 *dr = nullptr, *de = nullptr;
-    HELM_CK(cudaMalloc(&dr, nb * n * sizeof(float2)));
-    if (cudaMalloc(&de, nb * n * sizeof(float2)) != cudaSuccess) { cudaFree(dr); set_error("cudaMalloc"); return HELM_ENOMEM; }
+    auto* dr = (float2*)arena_buffer(net->io_arena, net->io_arena_bytes, 0, nb * n * sizeof(float2));
+    auto* de = (float2*)arena_buffer(net->io_arena, net->io_arena_bytes, 1, nb * n * sizeof(float2));
+    if (!dr || !de) { set_error("cnn_loss_grad: out of device memory"); return HELM_ENOMEM; }
     int s = HELM_OK;
     if (cudaMemcpy(dr, r, nb * n * sizeof(float2), cudaMemcpyDefault) != cudaSuccess ||
         cudaMemcpy(de, e, nb * n * sizeof(float2), cudaMemcpyDefault) != cudaSuccess ||
@@ -699,8 +697,6 @@ int cnn_loss_grad(cnn_model* net, helm_ctx* c, const helm_c64* r, const helm_c64
         set_error("cnn_loss_grad: gradient copy failed");
         s = HELM_ECUDA;
     }
-    cudaFree(dr);
-    cudaFree(de);
     return s;
 }
 
@@ -710,8 +706,9 @@ int cnn_train_step(cnn_model* net, helm_ctx* c, const helm_c64* r, const helm_c6
     if (s) return s;
     HELM_TRY(cnn_adam_impl(net, lr, c->stream));
     HELM_CK(cudaStreamSynchronize(c->stream));
-    // the context's preconditioner sees the updated network
-    if (c->net == net) HELM_TRY(cnn_ctx_setup(c));
+    // the context's preconditioner sees the updated network: its context features are
+    // recomputed before the next use (the loss pass runs its own encoder)
+    if (c->net == net) c->cnn_stale = true;
     return HELM_OK;
 }
 

@@ -307,6 +307,7 @@ struct helm_ctx {
     std::vector<void*> cnn_arena;    // one activation buffer per convolution of the solver pass
     std::vector<size_t> cnn_arena_bytes;
     helm::RetrainState* retrain = nullptr;   // Alg. 2 dataset and schedule (cnn_retrain_step)
+    bool cnn_stale = false;          // the weights changed since the context features were computed
 };
 
 namespace helm {

@@ -74,8 +74,58 @@ def observed_data(native, kappa_true, gamma, nx, nz, hx, hz, freqs_hz, survey, m
     return d, it
 
 
+@dataclass
+class WindowGrid:
+    """The grid of one frequency window (about ten points per wavelength): its size and
+    spacings over the fine grid's rectangle, absorbing layer, source and receiver nodes
+    and observed data [nfreq][nsrc][nrcv] (CUDA tensors / arrays on that grid)."""
+    freqs: list
+    nx: int
+    nz: int
+    hx: float
+    hz: float
+    gamma: object
+    src_idx: list
+    rcv_idx: list
+    d_obs: object
+
+
+def window_grid_size(lx: float, lz: float, fmax_hz: float, c_min: float = 1500.0, ppw: float = 10.0,
+                     multiple: int = 16):
+    """(nx, nz, hx, hz) of a grid of about ppw points per shortest wavelength c_min / fmax over
+    an lx x lz rectangle, sizes rounded to multiples of `multiple` (multigrid and network)."""
+    h = c_min / (ppw * fmax_hz)
+    nx = max(multiple, int(round(lx / h / multiple)) * multiple)
+    nz = max(multiple, int(round(lz / h / multiple)) * multiple)
+    return nx, nz, lx / nx, lz / nz
+
+
+def run_windows(native, m, nx0, nz0, windows, cfg: FwiConfig, net=None, log=None) -> FwiHistory:
+    """Alg. 1 with a grid per frequency window: the fine model m (CUDA tensor [nz0][nx0],
+    updated in place) is resampled to each window's grid, the window's Gauss-Newton
+    iterations update that copy, and the update is resampled back and added to m."""
+    import torch
+    hist = FwiHistory()
+    for wi, win in enumerate(windows):
+        same = (win.nx, win.nz) == (nx0, nz0)
+        if same:
+            mw = m
+        else:
+            mw = torch.empty((win.nz, win.nx), dtype=torch.float32, device="cuda")
+            native.helm_resample(m, nx0, nz0, mw, win.nx, win.nz)
+            mw0 = mw.clone()
+        c = FwiConfig(**{**cfg.__dict__, "windows": [win.freqs]})
+        h = run(native, mw, win.gamma, win.nx, win.nz, win.hx, win.hz, win.src_idx, win.rcv_idx, win.d_obs,
+                win.freqs, c, net=net, log=log, window_offset=wi)
+        hist.rows += h.rows
+        if not same:
+            native.helm_resample(mw, win.nx, win.nz, m, nx0, nz0, 1.0, 1.0)     # m += R(m_w) - R(m_w0)
+            native.helm_resample(mw0, win.nx, win.nz, m, nx0, nz0, -1.0, 1.0)
+    return hist
+
+
 def run(native, m, gamma, nx, nz, hx, hz, src_idx, rcv_idx, d_obs, freqs_hz, cfg: FwiConfig, net=None,
-        log=None) -> FwiHistory:
+        log=None, window_offset: int = 0) -> FwiHistory:
     """Alg. 1 on the model m (float32 CUDA tensor [nz][nx] of m = 1 / v^2, updated in
     place).  d_obs: observed data [nfreq][nsrc][nrcv] (CUDA tensor) at freqs_hz, ordered as
     the windows' frequencies are drawn from.  net: the encoder-solver network (CNN-FGMRES
@@ -103,7 +153,8 @@ def run(native, m, gamma, nx, nz, hx, hz, src_idx, rcv_idx, d_obs, freqs_hz, cfg
                 survey = native.Survey(src_idx, rcv_idx, w)
                 t0 = time.perf_counter()
                 info = native.fwi_gn_iteration(ctx, survey, dw, m, opts)
-                row = dict(info, window=wi, freqs=list(window), iteration=it, seconds=time.perf_counter() - t0)
+                row = dict(info, window=wi + window_offset, freqs=list(window), iteration=it,
+                           seconds=time.perf_counter() - t0, grid=[nx, nz])
                 if net is not None and cfg.retrain_steps > 0:
                     # Alg. 2 on the new medium: a fresh Eq. 4.3 dataset, then Adam steps
                     t1 = time.perf_counter()

@@ -310,3 +310,16 @@ def crop_workload(nx: int = 64, nz: int = 32, h: float = 20.0, freqs=(6.0,),
     return Workload(f"helmholtz_{nx}x{nz}", nx, nz, h, list(freqs), kappa_of(c),
                     abl_gamma(nx, nz, width), top_row_positions(nx, max(1, nx // 8), iz=2,
                                                                    step=8, offset=4))
+
+
+def medium_sequence(c_true: np.ndarray, steps: int = 8, sigma: float = 10.0):
+    """The squared-slowness path m_t = (1 - t/T) G_sigma(m_true) + (t/T) m_true, t = 0..T, from a
+    Gaussian-smoothed model to the true one (a stand-in for the models an FWI visits), as
+    kappa = sqrt(m_t) float32 arrays."""
+    m_true = 1.0 / np.asarray(c_true, dtype=np.float64) ** 2
+    m_s = gaussian_smooth(m_true, sigma)
+    out = []
+    for t in range(steps + 1):
+        m = (1.0 - t / steps) * m_s + (t / steps) * m_true
+        out.append(np.sqrt(m).astype(np.float32))
+    return out

@@ -159,6 +159,12 @@ def _load():
     lib.fwi_jacobian.restype = ip
     lib.fwi_jacobian_adjoint.argtypes = [vp, sp, vp, ctypes.c_double, vp]
     lib.fwi_jacobian_adjoint.restype = ip
+    lib.helm_resample.argtypes = [vp, ip, ip, vp, ip, ip, fp, fp, vp]
+    lib.helm_resample.restype = ip
+    lib.helm_solve_multi.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp), ctypes.c_double, ip,
+                                     ctypes.POINTER(helm_stats)]
+    lib.helm_solve_multi.restype = ip
     lib.fwi_model_to_kappa.argtypes = [vp, vp, ctypes.c_longlong]
     lib.fwi_model_to_kappa.restype = ip
     lib.fwi_default_gn_opts.argtypes = [ctypes.POINTER(fwi_gn_opts)]
@@ -376,6 +382,41 @@ def fwi_gn_iteration(ctx, survey: Survey, d_obs, m, opts=None) -> dict:
     _check(lib.fwi_gn_iteration(ctx, ctypes.byref(survey.c), _ptr(d_obs, "complex64"), ctypes.byref(o),
                                 _ptr(m, "float32"), ctypes.byref(info)), "fwi_gn_iteration")
     return {k: getattr(info, k) for k, _ in fwi_gn_info._fields_}
+
+
+def helm_resample(src, nx0: int, nz0: int, dst, nx1: int, nz1: int, alpha: float = 1.0, beta: float = 0.0,
+                  stream=None):
+    """dst = alpha * bilinear(src) + beta * dst between node grids of one rectangle (device tensors)."""
+    _check(lib.helm_resample(_ptr(src, "float32"), nx0, nz0, _ptr(dst, "float32"), nx1, nz1, alpha, beta, stream),
+           "helm_resample")
+
+
+def helm_solve_multi(ctxs, rhs_list, x_list, nrhs_list, freq_list=None, tol: float = 1e-6, flags: int = 0):
+    """helm_solve of several contexts in one call.  Returns (status, [(iters, rel_res, status) per context])."""
+    n = len(ctxs)
+    carr = (ctypes.c_void_p * n)(*[c.value if hasattr(c, "value") else c for c in ctxs])
+    rarr = (ctypes.c_void_p * n)(*[_ptr(r, "complex64") for r in rhs_list])
+    xarr = (ctypes.c_void_p * n)(*[_ptr(x, "complex128") for x in x_list])
+    nb = (ctypes.c_int * n)(*[int(v) for v in nrhs_list])
+    keep, fptrs = [], []
+    for i in range(n):
+        f = None if freq_list is None else freq_list[i]
+        k, p = _int_array(f, int(nrhs_list[i]))
+        keep.append(k)
+        fptrs.append(p)
+    farr = (ctypes.c_void_p * n)(*fptrs)
+    outs, stats = [], (helm_stats * n)()
+    for i in range(n):
+        it = np.zeros(nrhs_list[i], np.int32)
+        rel = np.zeros(nrhs_list[i], np.float64)
+        st = np.zeros(nrhs_list[i], np.int32)
+        outs.append((it, rel, st))
+        stats[i] = helm_stats(it.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                              rel.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    status = lib.helm_solve_multi(carr, n, rarr, xarr, nb, farr, tol, flags, stats)
+    _check(status, "helm_solve_multi", ok=(HELM_OK, HELM_ENOCONV, HELM_EBREAKDOWN))
+    return status, outs
 
 
 def helm_destroy(ctx):

@@ -105,6 +105,10 @@ def test_vcycle_parity(native, nx, nz, levels, kind, with_u0):
             ref = pc(f[b].astype(np.complex128), None if u0 is None else u0[b].astype(np.complex128))
             rel = np.linalg.norm(u[b] - ref) / np.linalg.norm(ref)
             assert rel < 2e-4, (b, rel)
+            # element by element: complex64 arithmetic through 2 x levels smoothing sweeps and
+            # the coarsest GMRES, relative to each node plus a floor of the field's maximum
+            err = np.abs(u[b] - ref)
+            assert np.all(err <= 1e-3 * np.abs(ref) + 2e-5 * np.abs(ref).max()), (b, err.max())
     finally:
         native.helm_destroy(ctx)
 

@@ -58,3 +58,20 @@ def test_one_step_is_the_closed_form_minimal_residual_step():
         assert np.linalg.norm(r2[i]) < np.linalg.norm(r0)
         assert np.linalg.norm(A(e2[i]) - r2[i]) <= 1e-10 * np.linalg.norm(r[i])
         assert np.linalg.norm(A(e3[i]) - r3[i]) <= 1e-10 * np.linalg.norm(r[i])
+
+
+def test_anisotropic_network_scaling_reduces_to_the_isotropic_one():
+    """On a grid with hx hz = h^2 the network sees the same input (w sqrt(hx hz) kappa) and
+    its output gets the same scale (hx hz) as on the isotropic grid of spacing h."""
+    from oracle import cnn
+    w = media.crop_workload(16, 16, freqs=(5.0,), width=4)
+    kap, gam = w.kappa.astype(np.float64), w.gamma.astype(np.float64)
+    specs = cnn.layer_specs(widths=(16, 32))
+    P = cnn.unflatten(0.5 * cnn.he_init(specs, seed=1), specs)
+    r = media.complex_normal((1, 16, 16), seed=2).astype(np.complex128)
+    h = 20.0
+    e_iso, _, _, _ = T.network_error(P, specs, kap, gam, 30.0, h, r)
+    e_ani, _, _, _ = T.network_error(P, specs, kap, gam, 30.0, 2.0 * h, r, hz=h / 2.0)
+    assert np.allclose(e_iso, e_ani, rtol=1e-13, atol=0)
+    e_other, _, _, _ = T.network_error(P, specs, kap, gam, 30.0, 2.0 * h, r, hz=h)
+    assert not np.allclose(e_iso, e_other)
