@@ -497,6 +497,69 @@ def run_retrain_series(args, native, dev, stream, world, rank):
         print(json.dumps(line), flush=True)
 
 
+def run_train(args, native, dev, stream, world, rank, sampler):
+    """Alg. 2 training steps per second (cnn_retrain_step: a batch of 16 Eq. 4.3 pairs through
+    the network's forward and backward pass and Adam) on the 1024x512, 8 Hz medium, after
+    the 128-pair dataset is built; the roofline of the tensor-core weight gradient beside it."""
+    import torch
+    w = media.workload_cnn(16)
+    kap = torch.from_numpy(w.kappa).to(dev)
+    gam = torch.from_numpy(w.gamma).to(dev)
+    om = torch.tensor(w.omegas, dtype=torch.float32, device=dev)
+    net = native.cnn_create(4, (16, 32, 64, 128), seed=media.SEED_CNN)
+    ctx = native.helm_setup(kap, gam, w.nx, w.nz, w.h, w.h, om, net=net, opts=native.helm_default_opts(
+        mg_levels=3, max_rhs=16, precond=native.HELM_PC_CNN, stream=stream.cuda_stream))
+    native.cnn_set_loss(net, 1)
+    # 64 steps per epoch once the dataset holds 1024 pairs: warm up into the full dataset first
+    native.cnn_retrain_begin(ctx, initial_size=128, data_epochs=3, epochs=1 << 20, seed=media.SEED_DATAGEN)
+    for _ in range(56 + max(args.warmup, 3)):
+        native.cnn_retrain_step(net, ctx, 16, 1e-4)
+    torch.cuda.synchronize(dev)
+    steps = args.steps
+    st0 = native.cnn_retrain_state(ctx)
+    sampler.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = native.helm_launch_count()
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(steps):
+        native.cnn_retrain_step(net, ctx, 16, 1e-4)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = native.helm_launch_count() - launches0
+    line = {"metric": "Alg. 2 training steps per second (batch 16, 1024x512, 8 Hz)", "value": steps / (ms / 1e3),
+            "unit": "steps/s", "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
+            "wall_ms_per_step": 1e3 * wall / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 network (fp32 accumulate, fp32 master weights)", "data": "synthetic",
+            "config": {"workload": "retrain_step_1024x512_batch16", "widths": [16, 32, 64, 128],
+                       "dataset_pairs": st0["size"], "loss": "Eq. 4.2 with each pair weighted by 1 / ||e||^2"},
+            "gpu_launches": int(launches), "clocks": clocks}
+    if not args.no_extras:
+        native.helm_profile_enable(ctx, True)
+        native.cnn_retrain_step(net, ctx, 16, 1e-4)
+        prof = native.helm_profile_read(ctx)
+        flops = native.helm_profile_flops(ctx)
+        native.helm_profile_enable(ctx, False)
+        line["kernels"] = kernel_table(prof, flops)
+        hbm, bf16, kind = peaks(sustained=True)
+        if "wgrad" in prof and prof["wgrad"][0] > 0:
+            kms, kl, kb = prof["wgrad"]
+            secs = kms / 1e3
+            line["wgrad_roofline"] = {"bound": "tensor", "achieved": flops.get("wgrad", 0.0) / secs / 1e12,
+                                      "peak": bf16, "unit": "TFLOP/s", "peak_source": kind,
+                                      "frac": flops.get("wgrad", 0.0) / secs / 1e12 / bf16,
+                                      "hbm_GBps": kb / secs / 1e9, "hbm_frac": kb / secs / 1e9 / hbm,
+                                      "launches": kl, "avg_launch_us": 1e3 * kms / max(kl, 1)}
+    native.helm_destroy(ctx)
+    native.cnn_destroy(net)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_fwi_c5(args, native, dev, stream, world, rank):
     """FWI misfit and adjoint-state gradient (Eq. 3.5, Sec. 4.3) on the 2048 x 1024 (h = 10 m)
     fault-and-salt model: 256 sources and 512 receivers on row 2, 8 frequencies in
@@ -608,6 +671,9 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     sampler = ClockSampler(local)
 
+    if args.workload == "train":
+        run_train(args, native, dev, stream, world, rank, sampler)
+        return
     if args.workload == "retrain":
         run_retrain_series(args, native, dev, stream, world, rank)
         return
@@ -787,9 +853,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["cnn", "mg", "net", "retrain", "fwi"], default="cnn",
+    ap.add_argument("--workload", choices=["cnn", "mg", "net", "train", "retrain", "fwi"], default="cnn",
                     help="cnn: CNN-FGMRES vs MG-FGMRES at 1024x512 (default); mg: MG-FGMRES at 512x256; "
-                         "net: the network's forward pass alone at 1024x512; retrain: CNN-FGMRES iterations "
+                         "net: the network's forward pass alone at 1024x512; train: Alg. 2 training steps; "
+                         "retrain: CNN-FGMRES iterations "
                          "along a medium sequence with and without Alg. 2 retraining; fwi: FWI misfit and "
                          "gradient at 2048x1024 on per-frequency grids")
     ap.add_argument("--train-steps", type=int, default=None,

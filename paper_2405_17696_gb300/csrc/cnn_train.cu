@@ -54,6 +54,40 @@ __global__ void mask_to_bf16_kernel(const float* __restrict__ G, int cg, const _
     }
 }
 
+// The same for cg == cpad, a multiple of 8: one thread per (pixel, 8-channel chunk) with
+// 16-byte loads and stores (grid.y = chunk).
+__global__ void mask_to_bf16_vec_kernel(const float* __restrict__ G, const __nv_bfloat16* __restrict__ y, int cy,
+                                        int cpad, long long n, long long hw, __nv_bfloat16* __restrict__ out,
+                                        float* __restrict__ res_grad) {
+    const int c8 = blockIdx.y;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const long long b = p / hw, pix = p - b * hw;
+        const float4* g4 = reinterpret_cast<const float4*>(G + p * cpad + 8 * c8);
+        float4 a = g4[0], c = g4[1];
+        float v[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+        if (y) {
+            const uint4 yv = *reinterpret_cast<const uint4*>(y + nc8(b, 8 * c8, pix, cy, hw));
+            const __nv_bfloat16* yh = reinterpret_cast<const __nv_bfloat16*>(&yv);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (!(__bfloat162float(yh[j]) > 0.0f)) v[j] = 0.0f;
+        }
+        if (res_grad) {
+            float4* r4 = reinterpret_cast<float4*>(res_grad + p * cpad + 8 * c8);
+            float4 r0 = r4[0], r1 = r4[1];
+            r0.x += v[0]; r0.y += v[1]; r0.z += v[2]; r0.w += v[3];
+            r1.x += v[4]; r1.y += v[5]; r1.z += v[6]; r1.w += v[7];
+            r4[0] = r0;
+            r4[1] = r1;
+        }
+        uint4 o;
+        __nv_bfloat16* oh = reinterpret_cast<__nv_bfloat16*>(&o);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) oh[j] = __float2bfloat16_rn(v[j]);
+        *reinterpret_cast<uint4*>(out + nc8(b, 8 * c8, pix, cpad, hw)) = o;
+    }
+}
+
 // Wt[ci][t][co] = W[co][flip ? 8 - t : t][off + ci]   (dgrad weights of one input part)
 __global__ void transpose_weights_kernel(const __nv_bfloat16* __restrict__ W, int npad, int cin_pad, int off,
                                          int cpart, int flip, __nv_bfloat16* __restrict__ Wt) {
@@ -324,6 +358,15 @@ int layer_wgrad(const __nv_bfloat16* x0, int c0, const __nv_bfloat16* x1, int c1
                 LaunchScope scope(prof_ctx, K_WGRAD);
                 s = launch_wgrad_tc(wa, st);
             }
+            if (s == HELM_OK && prof_ctx && prof_ctx->prof.on) {
+                // algorithmic traffic: the layer's inputs and output gradient once, the weight and bias
+                // gradients once; flops: 2 x 9 x C_in x C_out per output pixel (logical channels)
+                const int nx1 = x1_bcast == 1 ? 1 : nb1;
+                const double pin = (double)hin * win, pout = (double)nb * hout * wout;
+                const double bytes = 2.0 * pin * ((double)nb * c0 + (double)nx1 * c1) + 2.0 * pout * npad +
+                                     4.0 * ((double)cout * 9 * cin + cout);
+                prof_add(prof_ctx, K_WGRAD, bytes, 2.0 * 9.0 * cin * cout * pout);
+            }
             if (s != HELM_EINVAL) return s;
         }
     }
@@ -496,8 +539,14 @@ class Backward {
             if (!ok_) break;
             {
                 LaunchScope scope(c_, K_CNN_IO);
-                mask_to_bf16_kernel<<<1184, 256, 0, st_>>>(Gy, cg, L.relu ? (const __nv_bfloat16*)op.y : nullptr,
-                                                          L.npad, L.npad, nout, (long long)op.hout * op.wout, g, rg);
+                const __nv_bfloat16* ymask = L.relu ? (const __nv_bfloat16*)op.y : nullptr;
+                if (cg == L.npad && cg % 8 == 0)
+                    mask_to_bf16_vec_kernel<<<dim3((unsigned)std::min<long long>((nout + 255) / 256, 1184),
+                                                   (unsigned)(cg / 8)), 256, 0, st_>>>(
+                        Gy, ymask, L.npad, L.npad, nout, (long long)op.hout * op.wout, g, rg);
+                else
+                    mask_to_bf16_kernel<<<1184, 256, 0, st_>>>(Gy, cg, ymask, L.npad, L.npad, nout,
+                                                              (long long)op.hout * op.wout, g, rg);
             }
             // weight and bias gradient
             {
