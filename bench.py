@@ -457,6 +457,7 @@ def run_retrain_series(args, native, dev, stream, world, rank):
     nb = rhs.shape[0]
     gam = torch.from_numpy(w.gamma).to(dev)
     om = torch.tensor(w.omegas, dtype=torch.float32, device=dev)
+    retrain_steps = args.retrain_steps or 200
     nets = {"cnn_no_retraining": native.cnn_load(args.checkpoint), "cnn_retrained": native.cnn_load(args.checkpoint)}
     rows, t_retrain = [], 0.0
     for t, kap in enumerate(kappas):
@@ -467,11 +468,11 @@ def run_retrain_series(args, native, dev, stream, world, rank):
                 mg_levels=3, max_iter=1000, max_rhs=nb, stream=stream.cuda_stream,
                 precond=native.HELM_PC_CNN if net else native.HELM_PC_MG))
             try:
-                if label == "cnn_retrained" and args.retrain_steps > 0:
+                if label == "cnn_retrained" and retrain_steps > 0:
                     t0 = time.perf_counter()
                     RT.retrain(native, net, ctx, cfg=RT.RetrainConfig(
                         initial_size=128, data_epochs=3, epochs=1 << 20, batch=16, lr=1e-4,
-                        max_steps=args.retrain_steps, relative_loss=True, warmup_steps=0,
+                        max_steps=retrain_steps, relative_loss=True, warmup_steps=50,
                         seed=media.SEED_DATAGEN + 100 * t))
                     torch.cuda.synchronize(dev)
                     t_retrain += time.perf_counter() - t0
@@ -490,7 +491,7 @@ def run_retrain_series(args, native, dev, stream, world, rank):
             "n_gpus": world, "data": "synthetic",
             "config": {"workload": f"retraining_series_{w.nx}x{w.nz}_{nb}rhs_9media", "freq_hz": 8.0,
                        "media": "m_t = (1 - t/8) G_10(m_true) + (t/8) m_true, t = 0..8 (seeded 12-layer m_true)",
-                       "retrain_steps_per_medium": args.retrain_steps,
+                       "retrain_steps_per_medium": retrain_steps,
                        "initial_weights": os.path.relpath(args.checkpoint, ROOT)},
             "totals": tot, "retrain_seconds": t_retrain, "per_medium": rows}
     if rank == 0:
@@ -864,8 +865,9 @@ def main():
                          "the checkpoint (default: the checkpoint when it exists, else 400 steps)")
     ap.add_argument("--checkpoint", default=CHECKPOINT,
                     help="initial weights (cnn_load) for the cnn workload")
-    ap.add_argument("--retrain-steps", type=int, default=200,
-                    help="Alg. 2 steps on the benchmark medium after loading the checkpoint (set-up, untimed)")
+    ap.add_argument("--retrain-steps", type=int, default=0,
+                    help="Alg. 2 steps on the benchmark medium after loading the checkpoint (set-up, untimed); "
+                         "the retraining series (--workload retrain) uses it per medium (default there: 200)")
     ap.add_argument("--sources", type=int, default=64,
                     help="mg workload: sources per frequency (64 = the benchmark workload)")
     ap.add_argument("--sources-cnn", type=int, default=128,

@@ -82,7 +82,8 @@ typedef struct {
                                ||r - a H e_0||; 2 = 0 for every RHS until one of its restart cycles
                                lowers the residual by less than 10 %, then 3 for that RHS; 1 = V-cycle
                                on P u = r from u_0 = e_0                                      (2) */
-    int   autotune;         /* 1: helm_setup with a network runs cnn_autotune on max_rhs RHS  (0) */
+    int   autotune;         /* 1: helm_setup runs helm_autotune (sweeps, and convolutions with a network)
+                               on max_rhs RHS                                                 (0) */
     void* stream;           /* cudaStream_t for all work of the context   (NULL) */
 } helm_opts;
 
@@ -519,6 +520,17 @@ int helm_profile_flops(helm_ctx* ctx, int max, double* flops, int* count);
  * cycles as single launches; so does a solve whose capture fails.  Results are
  * the same either way.  HELM_EINVAL for a null context. */
 int helm_set_graphs(helm_ctx* ctx, int on);
+
+/* Autotuning of the multigrid sweeps' thread-block shapes (and, for a context with a
+ * network, of the convolutions' tiling, cnn_autotune): runs one V-cycle on a synthetic batch
+ * of nrhs right-hand sides (1 <= nrhs <= max_rhs).  The first Jacobi sweep on each grid times
+ * the candidate block shapes (32x8, 64x4, 32x4, 128x2, 32x16, 16x16) with CUDA events and
+ * records the fastest in a process-wide table that every later sweep on that grid uses, at
+ * any batch size and in any context.  *n_shapes (may be NULL) receives the number of tuned
+ * (sweep, grid) entries.  helm_setup runs it with max_rhs when opts.autotune is set. */
+int helm_autotune(helm_ctx* ctx, int nrhs, int* n_shapes);
+/* Forget every tuned block shape of the sweeps. */
+void helm_autotune_reset(void);
 
 /* Number of kernels the library has launched in this process (all contexts;
  * a graph replay counts the kernels it runs). */

@@ -624,8 +624,8 @@ int helm_setup(helm_ctx** out, const float* kappa, const float* gamma, int nx, i
         if ((st = launch_galerkin(c, l))) return fail(st);
     // network context features for every frequency (Eq. 3.13, once per medium)
     if (c->net && (st = cnn_ctx_setup(c))) return fail(st);
-    // tiling of every convolution shape of the solver pass, timed on this device
-    if (c->net && o.autotune && (st = cnn_autotune(c, c->cap, nullptr))) return fail(st);
+    // block shapes of the sweeps and tiling of every convolution shape, timed on this device
+    if (o.autotune && (st = helm_autotune(c, c->cap, nullptr))) return fail(st);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
         set_error(std::string("setup failed: ") + cudaGetErrorString(cudaGetLastError()));
         return fail(HELM_ECUDA);
@@ -878,6 +878,40 @@ int helm_profile_flops(helm_ctx* c, int max, double* flops, int* count) {
 }
 
 long long helm_launch_count(void) { return g_launches.load(); }
+
+int helm_autotune(helm_ctx* c, int nrhs, int* n_shapes) {
+    g_last_error.clear();
+    if (!c || nrhs < 1 || nrhs > c->cap) { set_error("helm_autotune: need 1 <= nrhs <= max_rhs"); return HELM_EINVAL; }
+    const size_t N = npts(c);
+    float2 *f = nullptr, *u = nullptr;
+    HELM_CK(cudaMalloc(&f, (size_t)nrhs * N * sizeof(float2)));
+    if (cudaMalloc(&u, (size_t)nrhs * N * sizeof(float2)) != cudaSuccess) {
+        cudaFree(f);
+        set_error("helm_autotune: out of device memory");
+        return HELM_ENOMEM;
+    }
+    int s = HELM_OK;
+    // a V-cycle on a synthetic right-hand side (frequency 0) with the sweeps' shapes tuned
+    if (cudaMemsetAsync(f, 0, (size_t)nrhs * N * sizeof(float2), c->stream) != cudaSuccess) s = HELM_ECUDA;
+    if (!s) {
+        LaunchScope scope(c, K_MISC);
+        fill_int_kernel<<<(nrhs + 127) / 128, 128, 0, c->stream>>>(c->rhs_freq, 0, nrhs);
+        if (cudaGetLastError() != cudaSuccess) s = HELM_ECUDA;
+    }
+    if (!s) {
+        stencil_tuning(true);
+        s = vcycle_apply(c, u, nullptr, f, nrhs, c->ones);
+        stencil_tuning(false);
+    }
+    if (!s && cudaStreamSynchronize(c->stream) != cudaSuccess) s = HELM_ECUDA;
+    cudaFree(f);
+    cudaFree(u);
+    if (!s && c->net) s = cnn_autotune(c, nrhs, nullptr);
+    if (n_shapes) *n_shapes = stencil_tuned_count();
+    return s;
+}
+
+void helm_autotune_reset(void) { stencil_tune_reset(); }
 
 int cnn_make_samples(helm_ctx* c, const helm_c64* x, const int* freq_idx, const int* iters, int nb, helm_c64* r_out,
                      helm_c64* e_out) {

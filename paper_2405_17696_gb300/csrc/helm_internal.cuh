@@ -380,5 +380,10 @@ void cnn_ctx_free(helm_ctx* c);
 int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const int* mask, int with_vcycle);
 int cnn_ctx_compact(helm_ctx* c, int nb);   // list the RHS still running (flags in cnn_act_host)
 void cnn_retrain_free(helm_ctx* c);         // cnn_retrain.cu
+// Block-shape autotuning of the Jacobi sweeps (k_multigrid.cu): while on, the first launch
+// on a grid times the candidate shapes and records the fastest (process-wide table).
+void stencil_tuning(bool on);
+int stencil_tuned_count();
+void stencil_tune_reset();
 
 }  // namespace helm

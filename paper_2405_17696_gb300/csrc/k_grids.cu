@@ -1,6 +1,6 @@
-// Several grids at once (per-frequency grids of the FWI windows, BASELINE's
-// full-FWI configuration after Sec. 4.2: each frequency window solved on a grid
-// of about ten points per wavelength):
+// Several grids at once (per-frequency grids of the FWI windows: each frequency
+// window solved on a grid of about ten points per wavelength over the same
+// rectangle, so that the low frequencies cost far less than the high ones):
 //   * helm_resample: a field moved between two node grids that cover the same
 //     rectangle (bilinear interpolation), to carry the model m from the fine grid
 //     to a window's grid and the window's model update back;
@@ -25,14 +25,23 @@ __global__ void resample_kernel(const float* __restrict__ src, int nx0, int nz0,
     const long long n = (long long)nx1 * nz1;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(p % nx1), j = (int)(p / nx1);
-        // position in source node units: (i + 1/2) nx0 / nx1 - 1/2
-        float x = ((float)i + 0.5f) * ((float)nx0 / (float)nx1) - 0.5f;
-        float z = ((float)j + 0.5f) * ((float)nz0 / (float)nz1) - 0.5f;
-        x = fminf(fmaxf(x, 0.0f), (float)(nx0 - 1));
-        z = fminf(fmaxf(z, 0.0f), (float)(nz0 - 1));
-        const int i0 = min((int)x, nx0 - 1), j0 = min((int)z, nz0 - 1);
+        // position in source node units, (i + 1/2) nx0 / nx1 - 1/2 = ((2i + 1) nx0 - nx1) / (2 nx1),
+        // split exactly into its integer part and fraction (clamped to the outermost nodes)
+        int i0, j0;
+        float fx, fz;
+        {
+            const long long num = (2ll * i + 1) * nx0 - nx1, den = 2ll * nx1;
+            if (num <= 0) { i0 = 0; fx = 0.0f; }
+            else if (num >= (long long)(nx0 - 1) * den) { i0 = nx0 - 1; fx = 0.0f; }
+            else { i0 = (int)(num / den); fx = (float)(num - (long long)i0 * den) / (float)den; }
+        }
+        {
+            const long long num = (2ll * j + 1) * nz0 - nz1, den = 2ll * nz1;
+            if (num <= 0) { j0 = 0; fz = 0.0f; }
+            else if (num >= (long long)(nz0 - 1) * den) { j0 = nz0 - 1; fz = 0.0f; }
+            else { j0 = (int)(num / den); fz = (float)(num - (long long)j0 * den) / (float)den; }
+        }
         const int i1 = min(i0 + 1, nx0 - 1), j1 = min(j0 + 1, nz0 - 1);
-        const float fx = x - (float)i0, fz = z - (float)j0;
         const float a = src[(size_t)j0 * nx0 + i0], b = src[(size_t)j0 * nx0 + i1];
         const float c = src[(size_t)j1 * nx0 + i0], d = src[(size_t)j1 * nx0 + i1];
         const float v = (1.0f - fz) * ((1.0f - fx) * a + fx * b) + fz * ((1.0f - fx) * c + fx * d);

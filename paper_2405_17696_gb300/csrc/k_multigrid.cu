@@ -4,6 +4,10 @@
 // of a level sits on node (2J+1, 2I+1) of the level above; values outside a
 // grid are zero.  All kernels are batched over right-hand sides (blockIdx.z)
 // and skip right-hand sides whose mask entry is zero.
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "helm_internal.cuh"
@@ -308,7 +312,75 @@ __global__ void galerkin_kernel(OpF fine, int f, float2* __restrict__ out, int n
 
 dim3 grid2(int nx, int nz, int nb) { return dim3((nx + 31) / 32, (nz + 7) / 8, nb); }
 
+// ---------------------------------------------------------------------------
+// Block shapes of the Jacobi sweeps, chosen by timing.  While tuning is on (see
+// stencil_tuning), the first launch of a sweep on a (kernel, grid) pair runs each
+// candidate shape twice, times the second run with CUDA events on the context's
+// stream, and records the fastest in a process-wide table that every later launch
+// on that grid uses (any batch size).  Re-running a sweep is harmless: its output
+// never aliases its input.
+// ---------------------------------------------------------------------------
+constexpr int N_SHAPES = 6;
+constexpr int SHAPES[N_SHAPES][2] = {{32, 8}, {64, 4}, {32, 4}, {128, 2}, {32, 16}, {16, 16}};
+std::mutex g_shape_mu;
+std::map<std::tuple<int, int, int>, int> g_shape;   // (kernel, nx, nz) -> index into SHAPES
+std::atomic<int> g_stencil_tuning{0};
+
+int shape_of(int kernel, int nx, int nz, bool* tune) {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    auto it = g_shape.find(std::make_tuple(kernel, nx, nz));
+    if (it != g_shape.end()) {
+        *tune = false;
+        return it->second;
+    }
+    *tune = g_stencil_tuning.load() != 0;
+    return 0;
+}
+
+// launch(shape index) for every candidate, timed; records and returns the fastest index
+template <class F>
+int tune_shape(const helm_ctx* c, int kernel, int nx, int nz, F launch) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        (void)cudaGetLastError();
+        return 0;
+    }
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int i = 0; i < N_SHAPES; ++i) {
+        launch(i);
+        cudaEventRecord(e0, c->stream);
+        launch(i);
+        cudaEventRecord(e1, c->stream);
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shape[std::make_tuple(kernel, nx, nz)] = best;
+    return best;
+}
+
 }  // namespace
+
+void stencil_tuning(bool on) { g_stencil_tuning.store(on ? 1 : 0); }
+int stencil_tuned_count() {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    return (int)g_shape.size();
+}
+void stencil_tune_reset() {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shape.clear();
+}
 
 template <class Op>
 int launch_jacobi(const helm_ctx* c, const Op& op, float2* u_out, const float2* u_in, const float2* f, int nx,
@@ -316,17 +388,33 @@ int launch_jacobi(const helm_ctx* c, const Op& op, float2* u_out, const float2* 
     LaunchScope scope(c, (std::is_same<Op, OpFine5>::value ? K_JACOBI_FINE : K_JACOBI_COARSE));
     if constexpr (std::is_same<Op, OpFine5>::value) {
         if (u_in && nx % 2 == 0) {
-            const dim3 g((nx / 2 + 31) / 32, (nz + 7) / 8, nb);
-            jacobi_fine2_kernel<<<g, dim3(32, 8), 0, c->stream>>>(op, u_out, u_in, f, c->opt.jacobi_w, nx, nz, mask,
-                                                                  tally(c, K_JACOBI_FINE, 24ull * nx * nz));
+            const Tally tl = tally(c, K_JACOBI_FINE, 24ull * nx * nz);
+            auto launch = [&](int i) {
+                const int bx = SHAPES[i][0], by = SHAPES[i][1];
+                const dim3 g((nx / 2 + bx - 1) / bx, (nz + by - 1) / by, nb);
+                jacobi_fine2_kernel<<<g, dim3(bx, by), 0, c->stream>>>(op, u_out, u_in, f, c->opt.jacobi_w, nx, nz,
+                                                                        mask, tl);
+            };
+            bool tune = false;
+            int i = shape_of(0, nx, nz, &tune);
+            if (tune && u_out != u_in) i = tune_shape(c, 0, nx, nz, launch);
+            launch(i);
             HELM_CK(cudaGetLastError());
             return HELM_OK;
         }
     }
     if constexpr (std::is_same<Op, OpC9>::value) {
-        const dim3 g((nx + 31) / 32, (nz + 7) / 8, (nb + 1) / 2);
-        jacobi_c9_pair_kernel<<<g, dim3(32, 8), 0, c->stream>>>(op, u_out, u_in, f, c->opt.jacobi_w, nx, nz, nb, mask,
-                                                                 tally(c, K_JACOBI_COARSE, (u_in ? 24ull : 16ull) * nx * nz));
+        const Tally tl = tally(c, K_JACOBI_COARSE, (u_in ? 24ull : 16ull) * nx * nz);
+        auto launch = [&](int i) {
+            const int bx = SHAPES[i][0], by = SHAPES[i][1];
+            const dim3 g((nx + bx - 1) / bx, (nz + by - 1) / by, (nb + 1) / 2);
+            jacobi_c9_pair_kernel<<<g, dim3(bx, by), 0, c->stream>>>(op, u_out, u_in, f, c->opt.jacobi_w, nx, nz, nb,
+                                                                      mask, tl);
+        };
+        bool tune = false;
+        int i = shape_of(1, nx, nz, &tune);
+        if (tune && u_out != u_in) i = tune_shape(c, 1, nx, nz, launch);
+        launch(i);
         HELM_CK(cudaGetLastError());
         return HELM_OK;
     }

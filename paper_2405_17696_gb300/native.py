@@ -159,6 +159,10 @@ def _load():
     lib.fwi_jacobian.restype = ip
     lib.fwi_jacobian_adjoint.argtypes = [vp, sp, vp, ctypes.c_double, vp]
     lib.fwi_jacobian_adjoint.restype = ip
+    lib.helm_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
+    lib.helm_autotune.restype = ip
+    lib.helm_autotune_reset.argtypes = []
+    lib.helm_autotune_reset.restype = None
     lib.helm_resample.argtypes = [vp, ip, ip, vp, ip, ip, fp, fp, vp]
     lib.helm_resample.restype = ip
     lib.helm_solve_multi.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -382,6 +386,18 @@ def fwi_gn_iteration(ctx, survey: Survey, d_obs, m, opts=None) -> dict:
     _check(lib.fwi_gn_iteration(ctx, ctypes.byref(survey.c), _ptr(d_obs, "complex64"), ctypes.byref(o),
                                 _ptr(m, "float32"), ctypes.byref(info)), "fwi_gn_iteration")
     return {k: getattr(info, k) for k, _ in fwi_gn_info._fields_}
+
+
+def helm_autotune(ctx, nrhs: int) -> int:
+    """Time the multigrid sweeps' block shapes (and the convolutions with a network); returns the
+    number of tuned sweep entries."""
+    n = ctypes.c_int(0)
+    _check(lib.helm_autotune(ctx, nrhs, ctypes.byref(n)), "helm_autotune")
+    return int(n.value)
+
+
+def helm_autotune_reset():
+    lib.helm_autotune_reset()
 
 
 def helm_resample(src, nx0: int, nz0: int, dst, nx1: int, nz1: int, alpha: float = 1.0, beta: float = 0.0,

@@ -348,3 +348,31 @@ def test_residual_entry_point(native):
         ref = b[k] - H.helmholtz_apply(x[k], _f32(w.kappa), _f32(w.gamma), om, w.h, w.h)
         assert np.abs(r[k] - ref).max() <= 1e-6 * np.abs(ref).max()
         assert abs(rel[k] - np.linalg.norm(ref) / np.linalg.norm(b[k].astype(np.complex128))) <= 1e-12 * rel[k]
+
+
+def test_sweep_autotune_keeps_results(native):
+    """helm_autotune times the Jacobi sweeps' block shapes; the sweeps compute every node the
+    same way whatever the shape, so a V-cycle and a solve are bit-identical after tuning."""
+    w = media.crop_workload(192, 96, freqs=(4.0, 6.0), width=8)
+    native.helm_autotune_reset()
+    ctx = _ctx(native, w, mg_levels=3)
+    try:
+        nb = 3
+        f = torch.from_numpy(media.complex_normal((nb, w.nz, w.nx), seed=41)).cuda()
+        fi = np.array([0, 1, 1], np.int32)
+        u0 = torch.zeros((nb, w.nz, w.nx), dtype=torch.complex64, device="cuda")
+        native.helm_vcycle(ctx, f, None, u0, nb, fi)
+        rhs = torch.from_numpy(w.rhs()).cuda()
+        x0 = torch.zeros(rhs.shape, dtype=torch.complex128, device="cuda")
+        _, it0, _, _ = native.helm_solve(ctx, rhs, x0, rhs.shape[0], w.freq_index(), 1e-6, native.HELM_SOLVE_ZERO_X0)
+        n = native.helm_autotune(ctx, 4)
+        assert n >= 2                     # the fine sweep and at least one coarse level
+        u1 = torch.zeros_like(u0)
+        native.helm_vcycle(ctx, f, None, u1, nb, fi)
+        x1 = torch.zeros_like(x0)
+        _, it1, _, _ = native.helm_solve(ctx, rhs, x1, rhs.shape[0], w.freq_index(), 1e-6, native.HELM_SOLVE_ZERO_X0)
+    finally:
+        native.helm_destroy(ctx)
+        native.helm_autotune_reset()
+    assert torch.equal(u0, u1)
+    assert np.array_equal(it0, it1) and torch.equal(x0, x1)
