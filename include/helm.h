@@ -183,8 +183,10 @@ int helm_vcycle(helm_ctx* ctx, const helm_c64* f, const helm_c64* u0, helm_c64* 
  *   d_obs   : complex64 [nfreq][nsrc][nrcv] observed data (host or device)
  *   tol     : relative residual of the forward and adjoint solves
  *   misfit_out : host double;  grad_m_out : float32 [nz][nx] (host or device)
- * Allocates its forward/adjoint wavefields per call (2 x 16 bytes per grid point and RHS
- * of one chunk).  Returns the first failing helm_solve status, or HELM_OK. */
+ * The nfreq x nsrc (frequency, source) pairs are solved in chunks of up to max_rhs pairs
+ * (a frequency's sources may span two chunks).  Allocates its forward/adjoint wavefields
+ * per call (2 x 16 bytes per grid point and pair of one chunk).  Returns the first failing
+ * helm_solve status, or HELM_OK. */
 int fwi_misfit_grad(helm_ctx* ctx, const int* src_idx, int nsrc, const int* rcv_idx, int nrcv,
                     const helm_c64* d_obs, double tol, double* misfit_out, float* grad_m_out);
 

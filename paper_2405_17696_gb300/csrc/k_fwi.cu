@@ -18,11 +18,12 @@
 namespace helm {
 namespace {
 
-// g_s = e_{src} / (hx hz) for every RHS slot b = j * nsrc + s
-__global__ void point_sources_kernel(float2* __restrict__ g, const int* __restrict__ src, int nsrc, size_t n,
-                                     float amp) {
+// g_s = e_{src} / (hx hz) for every RHS slot b of a chunk that starts at global slot b0,
+// global slot b0 + b = j * nsrc + s
+__global__ void point_sources_kernel(float2* __restrict__ g, const int* __restrict__ src, int nsrc, int b0,
+                                     size_t n, float amp) {
     const int b = blockIdx.y;
-    const int s = b % nsrc;
+    const int s = (b0 + b) % nsrc;
     const int k = src[s];
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
         g[(size_t)b * n + p] = make_float2(p == (size_t)k ? amp : 0.f, 0.f);
@@ -107,8 +108,9 @@ extern "C" int fwi_misfit_grad(helm_ctx* c, const int* src_idx, int nsrc, const 
         if (rcv_idx[i] < 0 || (size_t)rcv_idx[i] >= N) { set_error("fwi_misfit_grad: receiver index outside the grid"); return HELM_EINVAL; }
     const int nfreq = c->nfreq;
     const int nb_tot = nfreq * nsrc;
-    const int nbc = c->cap < nb_tot ? (c->cap / nsrc) * nsrc : nb_tot;   // whole frequencies per chunk
-    if (nbc < nsrc) { set_error("fwi_misfit_grad: max_rhs smaller than the number of sources"); return HELM_EINVAL; }
+    // chunks of up to max_rhs (frequency, source) slots, a frequency's sources possibly split
+    const int nbc = c->cap < nb_tot ? c->cap : nb_tot;
+    if (nbc < 1) { set_error("fwi_misfit_grad: context without RHS capacity"); return HELM_EINVAL; }
 
     float2 *g = nullptr, *q = nullptr, *d_dev = nullptr;
     float* grad_dev = nullptr;
@@ -159,7 +161,7 @@ extern "C" int fwi_misfit_grad(helm_ctx* c, const int* src_idx, int nsrc, const 
         for (int i = 0; i < nb; ++i) fidx[i] = (b0 + i) / nsrc;
         {
             LaunchScope scope(c, K_MISC);
-            point_sources_kernel<<<dim3(64, nb), 256, 0, c->stream>>>(g, src, nsrc, N, 1.0f / (c->hx * c->hz));
+            point_sources_kernel<<<dim3(64, nb), 256, 0, c->stream>>>(g, src, nsrc, b0, N, 1.0f / (c->hx * c->hz));
             ck(cudaGetLastError());
         }
         if (status) break;

@@ -310,7 +310,10 @@ def _fwi_case():
     return nx, nz, h, media.kappa_of(c_true), media.kappa_of(c0), gamma, freqs, src, rcv
 
 
-def test_fwi_misfit_and_gradient_parity(native):
+@pytest.mark.parametrize("max_rhs", [64, 5])
+def test_fwi_misfit_and_gradient_parity(native, max_rhs):
+    """16 (frequency, source) slots in one chunk, and in chunks of 5 that split a
+    frequency's sources across chunks."""
     from oracle import fwi
     nx, nz, h, k_true, k0, gamma, freqs, src, rcv = _fwi_case()
     om = [float(np.float32(2 * math.pi * f)) for f in freqs]
@@ -318,7 +321,7 @@ def test_fwi_misfit_and_gradient_parity(native):
     d_obs, _ = fwi.forward_data(_f32(k_true), _f32(gamma), om, h, h, g, np.array(rcv))
     phi_ref, grad_ref = fwi.misfit_and_gradient(_f32(k0), _f32(gamma), om, h, h, g, np.array(rcv), d_obs)
     w = media.Workload("fwi", nx, nz, h, freqs, k0, gamma, src)
-    ctx = _ctx(native, w, mg_levels=3)
+    ctx = _ctx(native, w, mg_levels=3, max_rhs=max_rhs)
     try:
         grad = torch.zeros((nz, nx), dtype=torch.float32, device="cuda")
         d_dev = torch.from_numpy(np.ascontiguousarray(d_obs, dtype=np.complex64)).cuda().contiguous()
