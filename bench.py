@@ -603,11 +603,15 @@ def run_fwi_c5(args, native, dev, stream, world, rank):
     torch.cuda.synchronize(dev)
     t_setup = time.perf_counter() - t_setup
     results = [None] * len(items)
+    errors = [None] * len(items)
 
     def work(i):
         it = items[i]
         torch.cuda.set_device(dev)
-        results[i] = native.fwi_misfit_grad(it["ctx"], it["sv"].src, it["sv"].rcv, it["d"], it["g"], tol=TOL)
+        try:
+            results[i] = native.fwi_misfit_grad(it["ctx"], it["sv"].src, it["sv"].rcv, it["d"], it["g"], tol=TOL)
+        except Exception as e:      # re-raised on the main thread
+            errors[i] = e
 
     for _ in range(max(0, min(args.warmup, 1))):
         for i in range(len(items)):
@@ -621,6 +625,9 @@ def run_fwi_c5(args, native, dev, stream, world, rank):
         th.join()
     torch.cuda.synchronize(dev)
     secs = time.perf_counter() - t0
+    for e in errors:
+        if e is not None:
+            raise e
     # the gradient against the oracle on a 64 x 32 crop of the model (3 and 5 Hz, 8 sources)
     from oracle import fwi as OF
     crop_c = c_true[:32, 1000:1064]
@@ -876,9 +883,10 @@ def main():
                     help="time the candidate tilings of every convolution shape before the run (set-up, untimed)")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="replay the restart cycles of MG-FGMRES from a CUDA graph (1, default) or launch them one by one")
-    ap.add_argument("--conv-path", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--conv-path", type=int, default=0, choices=[0, 1, 2, 3],
                     help="convolution kernel: 0 TMA halo tiles (default), 1 gather, 2 TMA with the column "
-                         "taps in N for 16-channel layers")
+                         "taps in N for 16-channel layers, 3 TMA with the tap rows in N for "
+                         "16- and 32-channel same-grid layers")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the solve only: no profiled step, end-to-end leg or CPU baseline (profiling runs)")
     args = ap.parse_args()

@@ -445,8 +445,13 @@ int cnn_wgrad_plan(int mode, int c0, int c1, int npad, int hin, int win, int nb,
  * cannot take; path 1: the gather kernel for every layer; path 2: as path 0,
  * but same-grid layers with 16 output channels put the three column taps into
  * the MMA's N and add them in the epilogue (fewer shared-memory operand reads,
- * more epilogue work; slower than path 0 on GB300 so far).  Process-wide; for
- * tests and measurements.  Returns HELM_EINVAL for any other value. */
+ * more epilogue work; slower than path 0 on GB300 so far); path 3: as path 0,
+ * but same-grid layers with 16 or 32 output channels put the three tap rows into
+ * the MMA's N (three MMAs of N = 48 or 96 per staged row and 16-channel group
+ * instead of nine of N = 16 or 32 per output row) and add the three rows' partial
+ * sums in the epilogue (Sec. 3.4's 3x3 convolutions; the tap sums are unchanged;
+ * also slower than path 0 on GB300 so far).  Process-wide; for tests and
+ * measurements.  Returns HELM_EINVAL for any other value. */
 int cnn_set_conv_path(int path);
 /* Autotuning of the convolutions' tiling.  Runs the network's solver pass once
  * on a synthetic residual batch of nrhs RHS (1 <= nrhs <= max_rhs) of the
@@ -467,17 +472,22 @@ void cnn_autotune_reset(void);
  * nearest x2 up, 3 transpose of stride 2; c0, c1 input channels (multiples of
  * 16), npad output channels (16 or a multiple of 32, at most 128), hin x win
  * input grid, nb images; stage_kb / ring_kb / rows_cap as for
- * cnn_set_conv_ring / cnn_set_conv_tiling (0 = default); narrow selects the
- * column-taps-in-N variant for 16-channel same-grid layers.  out16 = {tiles,
+ * cnn_set_conv_ring / cnn_set_conv_tiling (0 = default); narrow = 1 selects the
+ * column-taps-in-N variant for 16-channel same-grid layers, narrow = 2 the
+ * row-taps-in-N variant for 16- and 32-channel ones.  out18 = {tiles,
  * tile width, tile rows, staged row pitch, M blocks per parity, parities,
  * parity sub-planes, plane bytes, parity stride bytes, weight bytes, stage
- * bytes, stages, TMEM columns, TMEM slots, slot columns, mode used (4 = the
- * variant)}.  HELM_EINVAL for an invalid shape or one the kernel does not take
- * (out16 is filled either way for a valid shape). */
+ * bytes, stages, TMEM columns, TMEM slots, slot columns, mode used (4 or 6 =
+ * the variant), epilogue warpgroups and staged rows per commit of mode 6}.
+ * HELM_EINVAL for an invalid shape or one the kernel does not take (out18 is filled
+ * either way for a valid shape). */
 int cnn_conv_plan(int mode, int c0, int c1, int npad, int hin, int win, int nb, int stage_kb, int ring_kb,
-                  int rows_cap, int narrow, int* out16);
+                  int rows_cap, int narrow, int* out18);
 /* Launches of the column-taps-in-N convolution since the library was loaded. */
 long long cnn_conv_narrow_launches(void);
+/* Launches of the row-taps-in-N convolution (cnn_set_conv_path(3)) since the library
+ * was loaded. */
+long long cnn_conv_rowtaps_launches(void);
 /* Tile height limit of the TMA halo-tile kernel: at most max_rows output rows per
  * tile (0 = automatic: as many as two 128-column TMEM accumulator buffers and a
  * 47 KB stage allow).  Process-wide; for tuning.  HELM_EINVAL outside [0, 254]. */

@@ -294,8 +294,8 @@ int launch_conv3x3(const ConvArgs& a, cudaStream_t st) {
         return HELM_EINVAL;
     }
     const int path = g_conv_path.load();
-    if (path == 0 || path == 2) {
-        const int t = launch_conv3x3_tma(a, st, path == 2);
+    if (path != 1) {
+        const int t = launch_conv3x3_tma(a, st, path == 2 ? 1 : (path == 3 ? 2 : 0));
         if (t == HELM_OK) {
             ++g_launch_tma;
             return HELM_OK;
@@ -320,9 +320,9 @@ int launch_conv3x3(const ConvArgs& a, cudaStream_t st) {
 }  // namespace helm
 
 extern "C" int cnn_set_conv_path(int path) {
-    if (path < 0 || path > 2) {
-        helm::set_error("cnn_set_conv_path: path must be 0 (automatic), 1 (gather kernel only) or 2 (TMA "
-                        "kernel with the column-taps-in-N variant)");
+    if (path < 0 || path > 3) {
+        helm::set_error("cnn_set_conv_path: path must be 0 (automatic), 1 (gather kernel only), 2 (TMA "
+                        "kernel with the column-taps-in-N variant) or 3 (TMA kernel with the A operand in TMEM)");
         return HELM_EINVAL;
     }
     helm::g_conv_path.store(path);

@@ -31,6 +31,16 @@
 //    warp: two shuffles).  Each staged pixel is read by 3 MMAs instead of 9; the rows 6
 //    and 7 of each group are computed and dropped.  Accumulators live in a ring of
 //    per-M-block TMEM slots, so that a tile's size is not bounded by TMEM.
+//  6 (16 or 32 output channels, same grid as mode 0) the three tap rows in N: an M block is
+//    one staged row (pitch tw + 2 <= 128, lanes >= tw dropped) and per 16-channel group takes
+//    three MMAs, one per column shift dx, computing D[b][x][(dy, o)] for N = 3 npad.  Output
+//    row m sums D[m][x][(-1, o)] + D[m + 1][x][(0, o)] + D[m + 2][x][(1, o)]: the same TMEM
+//    lane of three consecutive staged-row slots, no shuffles.  An MMA with M = 128, K = 16
+//    costs about as much for N = 16 as for N = 64 on this GPU, so three N = 48 MMAs per
+//    staged row replace nine N = 16 ones per output row.  Staged-row accumulators live in a
+//    ring of TMEM slots (3 npad columns each); every group of a tile is resident.  Opt-in
+//    (cnn_set_conv_path(3)): on the 1024x512 network's layers it measured 2.3x slower than
+//    mode 0, which stays the default.
 // Staged rows (tile + halo) are packed end to end into M blocks of 128 pixels;
 // the accumulator rows of the halo columns between rows are discarded (each
 // accumulator row depends only on its own A row).  Activations are in the
@@ -66,12 +76,18 @@ namespace helm {
 
 namespace {
 
-constexpr int EPI_WARPS = 8;                    // two warpgroups drain TMEM (alternate 32-column chunks)
-constexpr int EPI = 32 * EPI_WARPS;             // epilogue threads
-constexpr int NT = EPI + 64;                    // + a TMA-producer warp and an MMA-issuer warp
+// Epilogue warps: two warpgroups drain TMEM (alternate M blocks); mode 6, four warpgroups
+// (alternate output rows), one CTA per SM.  + a TMA-producer warp and an MMA-issuer warp.
+__host__ __device__ constexpr int epi_warps(int mode) { return mode == 6 ? 16 : 8; }
+__host__ __device__ constexpr int threads_of(int mode) { return 32 * epi_warps(mode) + 64; }
 constexpr int MAX_NS = 6;                       // stages (one 16-channel group of one tile each)
-constexpr int MAX_SLOTS = 4;                    // TMEM accumulator slots of mode 4 (two buffers otherwise)
+constexpr int MAX_SLOTS = 10;                   // TMEM slot barriers: mode 4 uses 4, mode 6 up to 10
+constexpr int NSLOT4 = 4;                       // TMEM accumulator slots of mode 4 (two buffers otherwise)
 constexpr int N3_PX = 96;                       // mode 4: staged pixels per M block (16 groups x 6)
+constexpr size_t RING_BUDGET_RT = 200 * 1024;   // mode 6: one CTA per SM (all 512 TMEM columns)
+constexpr int ROWS_RT_MAX = 32;                 // mode 6: output rows per tile at most
+constexpr int RT_CHUNK = 4;                     // mode 6: staged rows per commit at most (a commit
+                                                // costs about as much as several MMAs)
 constexpr long long WAIT_LIMIT = 1ll << 22;     // polls of try_wait before a wait gives up
 // No padding after a plane: the last M block of a packed tile may read up to
 // 2 pitches + 130 pixels past its plane's staged pixels, which lands in the next
@@ -95,7 +111,9 @@ struct Geometry {
     int nplanes;             // parity sub-planes: 1, or 4 in mode 1
     int wbytes;              // bytes of one group's weights (9 taps x 2 chunks x npad rows x 16 B)
     int w4;                  // weights by one 4-D TMA box (1) or 18 2-D boxes (0)
-    int nslot, slot_cols;    // mode 4: TMEM slots (one M block each) and their columns
+    int nslot, slot_cols;    // modes 4 and 6: TMEM slots (an M block / a staged row each) and their columns
+    int nwg;                 // mode 6: epilogue warpgroups that take output rows
+    int chunk;               // mode 6: staged rows per commit
     int stage;               // bytes of one stage
     int groups, groups0;     // 16-channel groups in total / taken from x0
     int ns;                  // stages in the ring
@@ -149,7 +167,7 @@ __device__ __forceinline__ bool tap_source(int t, int py, int px, int pw, int* p
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__ CUtensorMap tm_x0,
+__global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __grid_constant__ CUtensorMap tm_x0,
                                                          const __grid_constant__ CUtensorMap tm_x1,
                                                          const __grid_constant__ CUtensorMap tm_w, ConvArgs a,
                                                          Geometry g) {
@@ -159,6 +177,8 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
     __shared__ int abort_flag;
     __shared__ float bias_s[128];
 
+    constexpr int EPI_WARPS = epi_warps(MODE);
+    constexpr int EPI = 32 * EPI_WARPS;             // epilogue threads
     const int tid = threadIdx.x, warp = tid >> 5;
     if (tid < a.npad) bias_s[tid] = a.accum ? 0.0f : __ldg(a.bias + tid);
     if (warp == 0) {
@@ -172,8 +192,9 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
         }
         for (int i = 0; i < MAX_SLOTS; ++i) {
             tc::mbar_init(&tfull[i], 1);    // tcgen05.commit after the last MMA of a tile (mode 4: M block)
-            // every epilogue thread after its TMEM loads (mode 4: the warpgroup that drains the slot)
-            tc::mbar_init(&tempty[i], MODE == 4 ? EPI / 2 : EPI);
+            // every epilogue thread after its TMEM loads (mode 4: the warpgroup that drains the
+            // slot; mode 6: the warpgroups of the three output rows that read the slot)
+            tc::mbar_init(&tempty[i], MODE == 4 ? EPI / 2 : (MODE == 6 ? 3 * 128 : EPI));
         }
         tc::mbar_init(&done, 1);
         tc::fence_mbar_init();
@@ -234,8 +255,9 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                     }
                 }
                 unsigned char* ws = st + wofs;
-                if (MODE == 4) {
-                    // [dy][half][dx][npad][8]: the B operand of tap row dy is 3 npad rows (dx, o)
+                if (MODE == 4 || MODE == 6) {
+                    // mode 4 [dy][half][dx][npad][8]: the B operand of tap row dy is 3 npad rows (dx, o);
+                    // mode 6 [dx][half][dy][npad][8]: the B operand of column shift dx is 3 npad rows (dy, o)
                     tc::tma_load_5d(ws, &tm_w, 0, 0, 0, 2 * gi, 0, &full[s]);
                 } else if (g.w4) {
                     tc::tma_load_4d(ws, &tm_w, 0, 0, 2 * gi, 0, &full[s]);
@@ -313,6 +335,59 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                     }
                     __syncwarp();
                     if (leader) tc::mma_commit(&tfull[slot]);
+                }
+                if (!ok) break;
+                __syncwarp();
+                if (leader)
+                    for (int gi = 0; gi < G; ++gi) tc::mma_commit(&empty[(j + gi) % g.ns]);
+                j += G;
+            }
+        } else if constexpr (MODE == 6) {
+            // staged row b of every tile (global index jb) into TMEM slot jb % nslot: for each
+            // group and column shift dx one MMA with N = 3 npad (B rows (dy, o)).  Rows are
+            // committed in chunks of g.chunk (and at the tile's last row): commit id
+            // k * ceil(mb / chunk) + b / chunk on tfull[id % MAX_SLOTS].  A slot is
+            // refilled once the epilogue released it.
+            const uint32_t ncol = 3u * (uint32_t)a.npad;
+            const uint32_t idesc6 = tc::idesc_bf16_f32(128, 3 * a.npad);
+            const uint64_t bdesc6 = tc::smem_desc(0u, 3u * wplane, 128);   // K halves 3 npad rows apart
+            const uint32_t b6_lo = (uint32_t)bdesc6, b6_hi = (uint32_t)(bdesc6 >> 32);
+            const uint32_t dx_b16 = (6u * wplane) >> 4;                    // B of one column shift
+            long long jb = 0, cid = 0;
+            for (int k = 0; k < ntiles && ok; ++k) {
+                for (int gi = 0; gi < G; ++gi) {
+                    const long long js = j + gi;
+                    const bool f_ok = wait_bar(&full[js % g.ns], (uint32_t)((js / g.ns) & 1), abort_v, 32);
+                    if (!__all_sync(0xffffffffu, f_ok)) { ok = false; break; }
+                }
+                if (!ok) break;
+                tc::tc_fence_after_sync();
+                for (int b = 0; b < g.mb; ++b, ++jb) {
+                    const int slot = (int)(jb % g.nslot);
+                    const long long use = jb / g.nslot;
+                    const bool t_ok = use == 0 || wait_bar(&tempty[slot], (uint32_t)((use - 1) & 1), abort_v, 32);
+                    if (!__all_sync(0xffffffffu, t_ok)) { ok = false; break; }
+                    tc::tc_fence_after_sync();
+                    const uint32_t d = tmem + (uint32_t)slot * ncol;
+                    for (int gi = 0; gi < G; ++gi) {
+                        const int s = (int)((j + gi) % g.ns);
+                        const uint32_t a16 = (tc::smem_u32(smem + (size_t)s * g.stage) & 0x3FFFFu) >> 4;
+                        const uint32_t a_b = a_lo0 + a16 + (uint32_t)(b * g.pw);
+                        const uint32_t b_s = b6_lo + a16 + ((uint32_t)wofs >> 4);
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            if (leader) {
+                                const uint64_t ad = ((uint64_t)a_hi << 32) | (a_b + (uint32_t)dx);
+                                const uint64_t bd = ((uint64_t)b6_hi << 32) | (b_s + (uint32_t)dx * dx_b16);
+                                tc::mma_bf16(d, ad, bd, idesc6, (gi | dx) ? 1u : 0u);
+                            }
+                        }
+                    }
+                    if ((b + 1) % g.chunk == 0 || b == g.mb - 1) {
+                        __syncwarp();
+                        if (leader) tc::mma_commit(&tfull[cid % MAX_SLOTS]);
+                        ++cid;
+                    }
                 }
                 if (!ok) break;
                 __syncwarp();
@@ -416,7 +491,19 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
             }
             if (a.out_fp32) {
                 float* yo = reinterpret_cast<float*>(a.y) + (size_t)p * a.cstore;
-                if (a.accum) {
+                if ((a.cstore & 15) == 0) {
+                    // whole 16-channel segments, 64-byte aligned: four 16-byte accesses
+                    float4* y4 = reinterpret_cast<float4*>(yo + n0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float4 t = a.accum ? y4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        t.x += vv[4 * q];
+                        t.y += vv[4 * q + 1];
+                        t.z += vv[4 * q + 2];
+                        t.w += vv[4 * q + 3];
+                        y4[q] = t;
+                    }
+                } else if (a.accum) {
                     for (int i = 0; i < 16; ++i)
                         if (n0 + i < a.cstore) yo[n0 + i] += vv[i];
                 } else {
@@ -437,7 +524,69 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                 *reinterpret_cast<uint4*>(yq + plane_out) = w1;
             }
         };
-        if constexpr (MODE == 4) {
+        if constexpr (MODE == 6) {
+            // Output row m of a tile (warpgroup m % nwg) sums three staged-row slots in this
+            // thread's lane (= column), all channels.  The commit that covers the newest of
+            // the three rows implies the older two.  Every slot takes 3 x 128 arrivals per
+            // fill: one from each output row
+            // that reads it, and for the tile's first and last two staged rows (read by fewer
+            // rows) the extra arrivals come from the tile's first and last output rows.
+            const int nwg = g.nwg;
+            const uint32_t ncol = 3u * (uint32_t)a.npad;
+            const int cpt = (g.mb + g.chunk - 1) / g.chunk;   // commits per tile
+            long long jb = 0;
+            bool ok = true;
+            for (int k = 0; k < ntiles && ok; ++k) {
+                int b, xs, ys;
+                tile_coords(k, b, xs, ys);
+                const size_t img_base = (size_t)b * (size_t)(a.npad >> 3) * (size_t)hw_out * 8;
+                const int R = g.rows;
+                for (int m = wg < nwg ? wg : R; m < R; m += nwg) {
+                    const long long newest = jb + m + 2;
+                    const long long cid = (long long)k * cpt + (m + 2) / g.chunk;
+                    if (!wait_bar(&tfull[cid % MAX_SLOTS], (uint32_t)((cid / MAX_SLOTS) & 1), abort_v, 64)) {
+                        *abort_v = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after_sync();
+                    const uint32_t s0 = (uint32_t)((jb + m) % g.nslot), s1 = (uint32_t)((jb + m + 1) % g.nslot),
+                                   s2 = (uint32_t)(newest % g.nslot);
+                    const int ox = xs + row, oy = ys + m;
+                    const bool valid = row < g.tw && ox < a.wout && oy < a.hout;
+                    const long long pix = (long long)oy * a.wout + ox;
+                    const size_t ob = img_base + (size_t)pix * 8;
+                    const long long p = (long long)b * hw_out + pix;
+                    for (int c0 = 0; c0 < a.npad; c0 += 16) {
+                        float v0[16], v1[16], v2[16];
+                        tc::tmem_ld16x3(lane_base + s0 * ncol + (uint32_t)c0,
+                                        lane_base + s1 * ncol + (uint32_t)(a.npad + c0),
+                                        lane_base + s2 * ncol + (uint32_t)(2 * a.npad + c0), v0, v1, v2);
+                        if (c0 + 16 >= a.npad) {
+                            // this thread's reads of the three slots are complete
+                            tc::tc_fence_before_sync();
+                            tc::mbar_arrive(&tempty[s0]);
+                            tc::mbar_arrive(&tempty[s1]);
+                            tc::mbar_arrive(&tempty[s2]);
+                            if (m == 0) {
+                                tc::mbar_arrive(&tempty[s0]);
+                                tc::mbar_arrive(&tempty[s0]);
+                                tc::mbar_arrive(&tempty[s1]);
+                            }
+                            if (m == R - 1) {
+                                tc::mbar_arrive(&tempty[s1]);
+                                tc::mbar_arrive(&tempty[s2]);
+                                tc::mbar_arrive(&tempty[s2]);
+                            }
+                        }
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v0[i] += v1[i] + v2[i];
+                        if (valid) segment(v0, c0, ob, p);
+                    }
+                }
+                jb += g.mb;
+            }
+        } else if constexpr (MODE == 4) {
             // warpgroup wg drains the slots of parity wg (the slot count is even); row
             // (group gr, row i) of an M block is staged pixel 96 m + 6 gr + i
             const int gr = row >> 3, i8 = row & 7;
@@ -504,7 +653,7 @@ __global__ void __launch_bounds__(NT) conv3x3_tma_kernel(const __grid_constant__
                     }
                     m_prev = m;
                     int oy = ys + yy, ox = xs + xx;
-                    if (MODE >= 2) {
+                    if (MODE == 2 || MODE == 3) {
                         oy = 2 * oy + (ph >> 1);
                         ox = 2 * ox + (ph & 1);
                     }
@@ -640,6 +789,19 @@ bool encode_w5(CUtensorMap* m, const void* base, int cin, int npad) {
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Mode 6: weights [npad][9][cin] viewed as a 5-D tensor (8 channels, npad rows, 3 tap
+// rows, cin/8 chunks, 3 column taps); box = (8, npad, 3, 2, 3) lands as [dx][half][dy][npad][8],
+// so that the B operand of column shift dx is 3 npad rows (dy, o).
+bool encode_w6(CUtensorMap* m, const void* base, int cin, int npad) {
+    const cuuint64_t dims[5] = {8u, (cuuint64_t)npad, 3u, (cuuint64_t)(cin / 8), 3u};
+    const cuuint64_t strides[4] = {(cuuint64_t)9 * cin * 2, (cuuint64_t)3 * cin * 2, 16u, (cuuint64_t)cin * 2};
+    const cuuint32_t box[5] = {8u, (cuuint32_t)npad, 3u, 2u, 3u};
+    const cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
+    return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // weights [npad][9 * cin] viewed as 2-D; box = 8 input channels x npad rows.
 bool encode_w(CUtensorMap* m, const void* base, int cin, int npad) {
     const cuuint64_t dims[2] = {(cuuint64_t)9 * cin, (cuuint64_t)npad};
@@ -654,12 +816,14 @@ bool encode_w(CUtensorMap* m, const void* base, int cin, int npad) {
 std::atomic<int> g_rows_cap{0};   // tile-height limit set by cnn_set_conv_tiling (0 = automatic)
 
 // Tiling of one launch: tile-height cap, stage and ring budgets (0 = default), and
-// whether a 16-channel same-grid layer takes the column-taps-in-N variant.
+// the variant of a narrow same-grid layer: narrow = 1, the column-taps-in-N kernel
+// (mode 4, 16 output channels); narrow = 2, the row-taps-in-N kernel (mode 6, 16 or 32).
 struct TileCfg {
     int rows_cap = 0, stage_kb = 0, ring_kb = 0, narrow = 0;
 };
 std::atomic<int> g_stage_kb{0}, g_ring_kb{0};
-std::atomic<long long> g_launch_narrow{0};   // launches of mode 4   // stage / ring budgets set by cnn_set_conv_ring (0 = default)
+std::atomic<long long> g_launch_narrow{0};   // launches of mode 4
+std::atomic<long long> g_launch_rowtaps{0};  // launches of mode 6   // stage / ring budgets set by cnn_set_conv_ring (0 = default)
 int g_last_launch[6] = {0, 0, 0, 0, 0, 0};   // grid, CTAs per SM, CTAs registers/smem allow, shared memory,
                                              // registers per thread, static shared memory
 
@@ -667,6 +831,61 @@ int g_last_launch[6] = {0, 0, 0, 0, 0, 0};   // grid, CTAs per SM, CTAs register
 Geometry plan(const ConvArgs& a, const TileCfg& t) {
     Geometry g{};
     const int mode = a.mode;
+    if (mode == 6) {
+        // same grid, 16 or 32 output channels, tap rows in N (see the mode list above): an M
+        // block is one staged row (pitch tw + 2 <= 128)
+        if (a.npad != 16 && a.npad != 32) return Geometry{};
+        const int H = a.hout, W = a.wout;
+        g.groups = (a.c0 + a.c1) / 16;
+        g.groups0 = a.c0 / 16;
+        g.nph = 1;
+        g.nplanes = 1;
+        const int ntx = (W + 125) / 126;   // staged rows of at most 128 pixels: one 4-D TMA box row
+        g.tw = (W + ntx - 1) / ntx;
+        g.pw = g.tw + 2;
+        g.wbytes = 9 * 2 * a.npad * 16;
+        g.slot_cols = 3 * a.npad;
+        g.nslot = std::min(MAX_SLOTS, 512 / g.slot_cols);
+        int rmax = std::min(H, ROWS_RT_MAX);
+        if (t.rows_cap > 0 && rmax > t.rows_cap) rmax = t.rows_cap;
+        const size_t ring_budget = t.ring_kb > 0 ? (size_t)t.ring_kb * 1024 : RING_BUDGET_RT;
+        // the tallest tile whose stages fit a ring holding every group of a tile and one more
+        g.rows = 0;
+        for (int rows = rmax; rows >= 1; --rows) {
+            const int plane = (rows + 2) * g.pw * 16;
+            const int pstride = (2 * plane + 127) / 128 * 128;
+            const int stage = pstride + g.wbytes;
+            if (t.stage_kb > 0 && (size_t)stage > (size_t)t.stage_kb * 1024) continue;
+            int ns = (int)(ring_budget / (size_t)stage);
+            if (ns > MAX_NS) ns = MAX_NS;
+            if (ns < g.groups + 1) continue;
+            g.rows = rows;
+            g.plane = plane;
+            g.pstride = pstride;
+            g.stage = stage;
+            g.ns = ns;
+            break;
+        }
+        if (g.rows < 1) return Geometry{};
+        g.mb = g.rows + 2;          // staged rows (TMEM slots) per tile
+        // Warpgroup w takes output rows w, w + nwg, ...  Its parity wait on the commit that
+        // covers its newest staged row is unambiguous when that barrier's previous commit is
+        // known complete, which its own previous wait proves: consecutive waits of a
+        // warpgroup are at most 2 nwg + 1 rows apart when every warpgroup has a row in every
+        // tile, i.e. at most (2 nwg + 1) / chunk + 2 commits, fewer than MAX_SLOTS.  A chunk
+        // of rows can complete only if its last row's slot is released by output rows that
+        // wait on earlier commits: chunk <= nslot - 2.
+        g.nwg = 4;
+        while (g.nwg > 1 && g.nwg > g.rows) g.nwg >>= 1;
+        g.chunk = std::min(RT_CHUNK, g.nslot - 2);
+        g.acc_cols = 0;
+        g.tmem_cols = 512;
+        g.tiles_x = (W + g.tw - 1) / g.tw;
+        g.tiles_y = (H + g.rows - 1) / g.rows;
+        g.tx = (uint32_t)(2 * (g.rows + 2) * g.pw * 16 + g.wbytes);
+        g.tiles = g.tiles_x * g.tiles_y * a.nb;
+        return g;
+    }
     if (mode == 4) {
         // same grid, 16 output channels, column taps in N (see the mode list above)
         if (a.npad != 16) return Geometry{};
@@ -705,7 +924,7 @@ Geometry plan(const ConvArgs& a, const TileCfg& t) {
         if (g.rows < 1) return Geometry{};
         g.mb = (g.rows * g.pw + N3_PX - 1) / N3_PX;
         g.slot_cols = 64;            // 48 columns used: (dx, o) for dx = -1, 0, 1
-        g.nslot = MAX_SLOTS;
+        g.nslot = NSLOT4;
         g.tmem_cols = (uint32_t)(g.nslot * g.slot_cols);
         g.acc_cols = 0;
         g.tiles_x = (W + g.tw - 1) / g.tw;
@@ -830,6 +1049,7 @@ int launch_mode(const CUtensorMap& tm0, const CUtensorMap& tm1, const CUtensorMa
     });
     const size_t per_cta_smem = smem_req + (size_t)static_smem + 1024;   // + the per-block shared memory the CUDA runtime reserves
     const int by_smem = (int)((size_t)smem_per_sm() / per_cta_smem);
+    constexpr int NT = threads_of(MODE);
     const int by_regs = regs > 0 ? 65536 / (((regs * 32 + 255) / 256) * 256 * (NT / 32)) : 1;
     const int occ = std::min(by_smem, by_regs);
     per_sm = std::max(1, std::min(per_sm, occ));
@@ -851,9 +1071,10 @@ int launch_mode(const CUtensorMap& tm0, const CUtensorMap& tm1, const CUtensorMa
 namespace {
 
 // The launch decision of one layer, host code shared by the launcher and
-// cnn_conv_plan: the shape checks of the kernel, the tile plan, and for a
-// 16-channel same-grid layer with `narrow` the column-taps-in-N variant (mode 4),
-// which falls back to mode 0 when its plan does not fit (or when the caller says
+// cnn_conv_plan: the shape checks of the kernel, the tile plan, and for a narrow
+// same-grid layer the variant that t.narrow asks for: 1, the column-taps-in-N kernel
+// (mode 4, 16 channels); 2, the row-taps-in-N kernel (mode 6, 16 or 32 channels).  Either
+// falls back to mode 0 when its plan does not fit (mode 4 also when the caller says
 // that its weight map could not be encoded: no_mode4).  *mode_out = the mode that
 // runs.  HELM_EINVAL when the kernel does not take the layer (nothing launched);
 // *g_out is the plan either way.
@@ -870,12 +1091,16 @@ int plan_launch(const ConvArgs& a, const TileCfg& t, bool no_mode4, int* mode_ou
         return HELM_EINVAL;
     ConvArgs b = a;
     Geometry g{};
-    if (t.narrow && !no_mode4 && a.mode == 0 && a.npad == 16) {
+    if (t.narrow == 1 && !no_mode4 && a.mode == 0 && a.npad == 16) {
         b.mode = 4;
         g = plan(b, t);
         if (g.tiles <= 0 || (size_t)g.ns * g.stage > 200 * 1024) b.mode = 0;
+    } else if (t.narrow == 2 && !no_mode4 && a.mode == 0 && (a.npad == 16 || a.npad == 32)) {
+        b.mode = 6;
+        g = plan(b, t);
+        if (g.tiles <= 0 || (size_t)g.ns * g.stage > 200 * 1024) b.mode = 0;
     }
-    if (b.mode != 4) g = plan(b, t);
+    if (b.mode != 4 && b.mode != 6) g = plan(b, t);
     *g_out = g;
     *mode_out = b.mode;
     if (g.tiles <= 0) return HELM_EINVAL;
@@ -898,7 +1123,8 @@ int launch_cfg(const ConvArgs& a_in, cudaStream_t st, const TileCfg& t) {
     int mode = a.mode;
     if (plan_launch(a, t, false, &mode, &g) != HELM_OK) return HELM_EINVAL;
     alignas(64) CUtensorMap tmw;
-    if (mode == 4 && !encode_w5(&tmw, a.w, a.c0 + a.c1, a.npad)) {
+    if ((mode == 4 && !encode_w5(&tmw, a.w, a.c0 + a.c1, a.npad)) ||
+        (mode == 6 && !encode_w6(&tmw, a.w, a.c0 + a.c1, a.npad))) {
         // no weight map for the variant: the plain same-grid kernel
         if (plan_launch(a, t, true, &mode, &g) != HELM_OK) return HELM_EINVAL;
     }
@@ -907,19 +1133,23 @@ int launch_cfg(const ConvArgs& a_in, cudaStream_t st, const TileCfg& t) {
     const int bw = a.mode == 1 ? 2 * g.pw : g.pw;
     const int bh = a.mode == 1 ? 2 * (g.rows + 1) : g.rows + 2;
     alignas(64) CUtensorMap tm0, tm1;
-    if (!encode_act(&tm0, a.x0, a.c0, a.win, a.hin, a.nb, bw, bh, es)) return HELM_EINVAL;
+    auto enc = [&](CUtensorMap* m, const void* base, int c, int n) {
+        return encode_act(m, base, c, a.win, a.hin, n, bw, bh, es);
+    };
+    if (!enc(&tm0, a.x0, a.c0, a.nb)) return HELM_EINVAL;
     if (a.c1) {
         const int n1 = a.nb1 > 0 ? a.nb1 : (a.x1_bcast ? 1 : a.nb);
-        if (!encode_act(&tm1, a.x1, a.c1, a.win, a.hin, n1, bw, bh, es)) return HELM_EINVAL;
+        if (!enc(&tm1, a.x1, a.c1, n1)) return HELM_EINVAL;
     } else {
         tm1 = tm0;
     }
-    if (a.mode != 4) {
+    if (a.mode != 4 && a.mode != 6) {
         g.w4 = encode_w4(&tmw, a.w, a.c0 + a.c1, a.npad) ? 1 : 0;
         if (!g.w4 && !encode_w(&tmw, a.w, a.c0 + a.c1, a.npad)) return HELM_EINVAL;
     }
     switch (a.mode) {
         case 4: ++g_launch_narrow; return launch_mode<4>(tm0, tm1, tmw, a, g, st);
+        case 6: ++g_launch_rowtaps; return launch_mode<6>(tm0, tm1, tmw, a, g, st);
         case 0: return launch_mode<0>(tm0, tm1, tmw, a, g, st);
         case 1: return launch_mode<1>(tm0, tm1, tmw, a, g, st);
         case 2: return launch_mode<2>(tm0, tm1, tmw, a, g, st);
@@ -961,9 +1191,14 @@ int tune_and_launch(const ConvArgs& a, cudaStream_t st, const std::string& key, 
         c.narrow = 0;
         cands.push_back(c);
     }
-    if (a.mode == 0 && a.npad == 16) {
+    if (a.mode == 0 && a.npad == 16 && base.narrow != 1) {
         TileCfg c = base;
-        c.narrow = !base.narrow;
+        c.narrow = 1;
+        cands.push_back(c);
+    }
+    if (base.narrow) {
+        TileCfg c = base;
+        c.narrow = 0;
         cands.push_back(c);
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1005,14 +1240,14 @@ int tune_and_launch(const ConvArgs& a, cudaStream_t st, const std::string& key, 
 
 }  // namespace
 
-int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st, bool narrow) {
+int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st, int narrow) {
     if (!encode_fn()) return HELM_EINVAL;
     if (a.mode < 0 || a.mode > 3) return HELM_EINVAL;
     TileCfg t;
     t.rows_cap = g_rows_cap.load();
     t.stage_kb = g_stage_kb.load();
     t.ring_kb = g_ring_kb.load();
-    t.narrow = narrow ? 1 : 0;
+    t.narrow = narrow;
     // explicit tiling knobs take precedence over the tuned table
     if (t.rows_cap || t.stage_kb || t.ring_kb) return launch_cfg(a, st, t);
     const std::string key = shape_key(a);
@@ -1062,14 +1297,15 @@ extern "C" int cnn_set_conv_ring(int stage_kb, int ring_kb) {
 }
 
 extern "C" long long cnn_conv_narrow_launches(void) { return helm::g_launch_narrow.load(); }
+extern "C" long long cnn_conv_rowtaps_launches(void) { return helm::g_launch_rowtaps.load(); }
 
-// Tile plan of the TMA kernel for a layer shape (host only, no GPU needed): out16 =
+// Tile plan of the TMA kernel for a layer shape (host only, no GPU needed): out18 =
 // {tiles, tw, rows, pw, mb, nph, nplanes, plane, pstride, wbytes, stage, ns, tmem_cols,
-// nslot, slot_cols, mode}.  For checking the plan's bounds on the CPU.
+// nslot, slot_cols, mode, nwg, chunk}.  For checking the plan's bounds on the CPU.
 extern "C" int cnn_conv_plan(int mode, int c0, int c1, int npad, int hin, int win, int nb, int stage_kb,
-                             int ring_kb, int rows_cap, int narrow, int* out16) {
-    if (!out16 || mode < 0 || mode > 3 || c0 < 16 || c0 % 16 || c1 < 0 || c1 % 16 || nb < 1 || hin < 1 ||
-        win < 1 || (npad != 16 && npad % 32) || npad > 128) {
+                             int ring_kb, int rows_cap, int narrow, int* out18) {
+    if (!out18 || mode < 0 || mode > 3 || c0 < 16 || c0 % 16 || c1 < 0 || c1 % 16 || nb < 1 || hin < 1 ||
+        win < 1 || (npad != 16 && npad % 32) || npad > 128 || narrow < 0 || narrow > 2) {
         helm::set_error("cnn_conv_plan: invalid layer shape");
         return HELM_EINVAL;
     }
@@ -1091,9 +1327,9 @@ extern "C" int cnn_conv_plan(int mode, int c0, int c1, int npad, int hin, int wi
     helm::Geometry g{};
     int used = mode;
     const int s = helm::plan_launch(a, t, false, &used, &g);
-    const int v[16] = {g.tiles, g.tw, g.rows, g.pw, g.mb, g.nph, g.nplanes, g.plane, g.pstride, g.wbytes,
-                       g.stage, g.ns, (int)g.tmem_cols, g.nslot, g.slot_cols, used};
-    for (int i = 0; i < 16; ++i) out16[i] = v[i];
+    const int v[18] = {g.tiles, g.tw, g.rows, g.pw, g.mb, g.nph, g.nplanes, g.plane, g.pstride, g.wbytes,
+                       g.stage, g.ns, (int)g.tmem_cols, g.nslot, g.slot_cols, used, g.nwg, g.chunk};
+    for (int i = 0; i < 18; ++i) out18[i] = v[i];
     if (s != HELM_OK) {
         helm::set_error("cnn_conv_plan: the layer does not fit the TMA kernel");
         return HELM_EINVAL;

@@ -138,6 +138,8 @@ def _load():
     lib.cnn_set_conv_ring.restype = ip
     lib.cnn_conv_narrow_launches.argtypes = []
     lib.cnn_conv_narrow_launches.restype = ctypes.c_longlong
+    lib.cnn_conv_rowtaps_launches.argtypes = []
+    lib.cnn_conv_rowtaps_launches.restype = ctypes.c_longlong
     lib.cnn_conv_last_launch.argtypes = [ctypes.POINTER(ctypes.c_int)]
     lib.cnn_conv_last_launch.restype = None
     lib.cnn_conv_launch_counts.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
@@ -574,7 +576,9 @@ def cnn_set_loss(net, kind: int):
 
 def cnn_set_conv_path(path: int):
     """0: TMA halo-tile kernel (default); 1: gather kernel for all layers;
-    2: TMA kernel with the column-taps-in-N variant of the 16-channel layers."""
+    2: TMA kernel with the column-taps-in-N variant of the 16-channel layers;
+    3: TMA kernel with the three tap rows in N for the 16- and 32-channel same-grid
+    layers."""
     _check(lib.cnn_set_conv_path(int(path)), "cnn_set_conv_path")
 
 
@@ -584,15 +588,16 @@ def cnn_set_conv_tiling(max_rows: int):
 
 
 CONV_PLAN_FIELDS = ("tiles", "tw", "rows", "pw", "mb", "nph", "nplanes", "plane", "pstride", "wbytes", "stage",
-                    "ns", "tmem_cols", "nslot", "slot_cols", "mode")
+                    "ns", "tmem_cols", "nslot", "slot_cols", "mode", "nwg", "chunk")
 
 
 def cnn_conv_plan(mode: int, c0: int, c1: int, npad: int, hin: int, win: int, nb: int = 1, stage_kb: int = 0,
-                  ring_kb: int = 0, rows_cap: int = 0, narrow: bool = False):
+                  ring_kb: int = 0, rows_cap: int = 0, narrow: int = 0):
     """Host-side tile plan of the TMA convolution (dict of CONV_PLAN_FIELDS), or None when
-    the kernel does not take the layer."""
-    out = (ctypes.c_int * 16)()
-    st = lib.cnn_conv_plan(mode, c0, c1, npad, hin, win, nb, stage_kb, ring_kb, rows_cap, 1 if narrow else 0, out)
+    the kernel does not take the layer.  narrow: 0 plain, 1 (or True) the column-taps-in-N
+    variant, 2 the row-taps-in-N variant."""
+    out = (ctypes.c_int * 18)()
+    st = lib.cnn_conv_plan(mode, c0, c1, npad, hin, win, nb, stage_kb, ring_kb, rows_cap, int(narrow), out)
     if st != HELM_OK:
         return None
     return dict(zip(CONV_PLAN_FIELDS, list(out)))
@@ -639,6 +644,11 @@ def cnn_autotune_reset():
 def cnn_conv_narrow_launches() -> int:
     """Launches of the column-taps-in-N convolution since the library was loaded."""
     return int(lib.cnn_conv_narrow_launches())
+
+
+def cnn_conv_rowtaps_launches() -> int:
+    """Launches of the row-taps-in-N convolution since the library was loaded."""
+    return int(lib.cnn_conv_rowtaps_launches())
 
 
 def cnn_set_conv_ring(stage_kb: int, ring_kb: int):

@@ -128,3 +128,126 @@ def test_default_plans_of_the_benchmark_network(n):
     assert (g0["rows"], g0["tw"], g0["ns"], g0["tmem_cols"]) == (8, 114, 2, 256)
     g1 = n.cnn_conv_plan(1, 16, 0, 32, 512, 1024)
     assert g1["rows"] == 4 and g1["stage"] > 47 * 1024 and g1["ns"] * g1["stage"] <= 200 * 1024
+
+
+def _rowtaps_schedule(rows, ntiles, nslot, nwg=4, chunk=4, nbar=10):
+    """The row-taps-in-N kernel's slot protocol, run as a simulation: the MMA side fills staged
+    row jb (all tiles in order, rows + 2 per tile) into slot jb % nslot once the slot's
+    previous fill took its 3 arrivals (x 128 threads), and commits after every `chunk` rows
+    of a tile and after its last row (commit id c on barrier c % nbar); warpgroup w computes
+    the output rows m = w, w + nwg, ... of every tile in order, each once the commit that
+    covers staged row m + 2 is done, and arrives once on each of its three rows (the tile's
+    first output row twice more on staged row 0 and once on row 1, its last once more on
+    row R and twice on row R + 1).  The sides advance round-robin.  Returns True when
+    everything finishes; asserts that no slot takes more than 3 arrivals per fill, that
+    outputs read committed, unreleased rows, and that every parity wait is unambiguous: the
+    barrier's previous commit is known complete to the waiting warpgroup, and its next
+    commit cannot be done before the warpgroup arrives."""
+    per = rows + 2
+    cpt = -(-per // chunk)
+    total = per * ntiles
+    committed = [False] * total
+    arrivals = [0] * total
+    commits_done = 0
+    jb = 0
+    queues = [[(k, m) for k in range(ntiles) for m in range(w, rows, nwg)] for w in range(nwg)]
+    heads = [0] * nwg
+    known = [-1] * nwg          # commit ids this warpgroup's earlier waits proved complete
+    progress = True
+    while progress:
+        progress = False
+        while jb < total and (jb < nslot or arrivals[jb - nslot] == 3):
+            jb += 1
+            b = (jb - 1) % per
+            if (b + 1) % chunk == 0 or b == per - 1:
+                k = (jb - 1) // per
+                for r in range(k * per + (b // chunk) * chunk, jb):
+                    committed[r] = True
+                commits_done += 1
+            progress = True
+        for w in range(nwg):
+            if heads[w] >= len(queues[w]):
+                continue
+            k, m = queues[w][heads[w]]
+            base = k * per
+            cid = k * cpt + (m + 2) // chunk
+            if cid >= commits_done:
+                continue
+            assert cid < nbar or cid - nbar <= known[w], (rows, nslot, nwg, k, m)
+            assert commits_done <= cid + nbar, (rows, nslot, nwg, k, m)
+            known[w] = cid
+            for d in range(3):
+                assert committed[base + m + d] and arrivals[base + m + d] < 3
+            add = [base + m, base + m + 1, base + m + 2]
+            if m == 0:
+                add += [base, base, base + 1]
+            if m == rows - 1:
+                add += [base + rows, base + rows + 1, base + rows + 1]
+            for b in add:
+                arrivals[b] += 1
+                assert arrivals[b] <= 3
+            heads[w] += 1
+            progress = True
+    return jb == total and all(h == len(q) for h, q in zip(heads, queues)) and all(a == 3 for a in arrivals)
+
+
+def test_rowtaps_plans_stay_in_bounds(n):
+    """Mode 6 (tap rows in N): the A operand of staged row b at column shift dx (128 rows of
+    16 bytes per 8-channel half) and the B operand of each shift stay inside the stage;
+    every output node is lane x < tw of its row's three slots, read once; the slot ring
+    (3 npad columns a slot) fits TMEM; every group of a tile and one more stage fit the
+    ring; the slot protocol finishes for the planned ring."""
+    checked = 0
+    for (H, W), c0, c1, npad in itertools.product(SHAPES, (16, 32), (0, 16), (16, 32)):
+        g = n.cnn_conv_plan(0, c0, c1, npad, H, W, 2, narrow=2)
+        if g is None or g["mode"] != 6:
+            continue
+        rows, tw, pw = g["rows"], g["tw"], g["pw"]
+        groups = (c0 + c1) // 16
+        assert pw == tw + 2 and 2 * pw <= 256 and rows + 2 <= 256 and rows <= 32
+        assert g["tiles"] == -(-W // tw) * -(-H // rows) * 2
+        assert g["mb"] == rows + 2 and g["nph"] == 1 and g["nplanes"] == 1
+        assert g["plane"] == (rows + 2) * pw * 16
+        assert g["pstride"] >= 2 * g["plane"] and g["pstride"] % 128 == 0
+        assert g["stage"] == g["pstride"] + g["wbytes"] and g["stage"] % 128 == 0
+        assert g["wbytes"] == 9 * 2 * npad * 16
+        assert groups + 1 <= g["ns"] <= 6 and g["ns"] * g["stage"] <= 200 * 1024
+        assert g["slot_cols"] == 3 * npad and g["nslot"] == min(10, 512 // (3 * npad)) and g["nslot"] >= 3
+        assert g["tmem_cols"] == 512 and g["nslot"] * g["slot_cols"] <= 512
+        for b in range(rows + 2):
+            for dx in range(3):
+                for h in (0, 1):
+                    lo = h * g["plane"] + (b * pw + dx) * 16
+                    assert lo + 128 * 16 <= g["stage"]
+        for dx in range(3):
+            assert g["pstride"] + (dx + 1) * 6 * npad * 16 <= g["stage"]
+        cover = set()
+        for m in range(rows):
+            for x in range(128):
+                if x < tw:
+                    assert 0 <= x + 2 < pw        # the three column shifts stay in the staged row
+                    assert (m, x) not in cover
+                    cover.add((m, x))
+        assert len(cover) == rows * tw
+        assert g["nwg"] in (1, 2, 4) and g["nwg"] <= rows
+        assert 1 <= g["chunk"] <= min(4, g["nslot"] - 2)
+        assert _rowtaps_schedule(rows, 3, g["nslot"], g["nwg"], chunk=g["chunk"])
+        checked += 1
+    assert checked > 20
+
+
+def test_rowtaps_slot_protocol_for_every_ring():
+    """The slot protocol finishes with exactly three arrivals per fill and unambiguous parity
+    waits for every tile height down to one row, every ring of at least three slots, and
+    the warpgroup count and commit chunk the planner's rule gives (the largest of 4, 2, 1
+    not above the tile height; at most 4 rows and nslot - 2); commit barriers reused too
+    soon would not be, and a larger chunk deadlocks."""
+    for nslot in range(3, 11):
+        for rows in range(1, 40):
+            nwg = 4
+            while nwg > 1 and nwg > rows:
+                nwg //= 2
+            assert _rowtaps_schedule(rows, 4, nslot, nwg, chunk=min(4, nslot - 2))
+    assert not _rowtaps_schedule(16, 3, 5, 4, chunk=4)
+    with pytest.raises(AssertionError):
+        _rowtaps_schedule(16, 4, 10, 4, chunk=1, nbar=3)

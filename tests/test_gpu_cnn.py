@@ -47,10 +47,11 @@ MODES = {"same": 0, "down": 1, "up": 2}
     (64, 0, 0, 64, "same", 37, 40, 1, True, True),       # narrow rows packed into M blocks, ragged rows
     (32, 32, 1, 32, "down", 18, 22, 2, False, True),     # concat in the stride-2 gather path
 ])
-@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("path", [0, 1, 2, 3])
 def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res, relu, path):
     """path 0: the TMA halo-tile kernel; path 1: the gather kernel; path 2: the TMA
-    kernel with the column taps in N for 16-channel same-grid layers."""
+    kernel with the column taps in N for 16-channel same-grid layers; path 3: the TMA
+    kernel with the three tap rows in N for 16- and 32-channel same-grid layers."""
     g = np.random.default_rng(c0 * 7 + cout + MODES[mode])
     x0 = cnn.bf16_round(g.normal(size=(nb, hin, win, c0)))
     x1 = cnn.bf16_round(g.normal(size=((1 if bcast else nb), hin, win, c1))) if c1 else None
@@ -69,6 +70,7 @@ def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res,
     f32 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32)
     t0, g0 = native.cnn_conv_launch_counts()
     n0 = native.cnn_conv_narrow_launches()
+    n6 = native.cnn_conv_rowtaps_launches()
     native.cnn_set_conv_path(path)
     try:
         native.cnn_conv3x3(f32(x0), c0, f32(x1), c1, bcast, nb, hin, win, f32(w), f32(b), cout, f32(r),
@@ -80,13 +82,16 @@ def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res,
     assert (t1 - t0, g1 - g0) == ((1, 0) if used_tma else (0, 1))
     narrow = path == 2 and mode == "same" and cout <= 16
     assert native.cnn_conv_narrow_launches() - n0 == (1 if narrow else 0)
+    rowtaps = path == 3 and mode == "same" and cout <= 32
+    assert native.cnn_conv_rowtaps_launches() - n6 == (1 if rowtaps else 0)
     err = np.abs(y - ref)
     tol = 2.0 ** -7 * np.abs(ref) + 1e-3 * np.abs(ref).max()
     assert np.all(err <= tol), (err.max(), np.abs(ref).max())
 
 
-@pytest.mark.parametrize("widths,ny,nx,nsol", [((16, 32), 32, 32, 2), ((16, 32, 64, 128), 64, 32, 2)])
-def test_network_forward_parity(native, widths, ny, nx, nsol):
+@pytest.mark.parametrize("widths,ny,nx,nsol,path", [((16, 32), 32, 32, 2, 0), ((16, 32, 64, 128), 64, 32, 2, 0),
+                                                    ((16, 32, 64, 128), 64, 160, 2, 3)])
+def test_network_forward_parity(native, widths, ny, nx, nsol, path):
     # Half-scale He weights keep the random network contractive: with full-scale
     # weights a one-unit change of a single rounding decision already moves the
     # output of this 60-layer BF16 network by a few percent (measured on the
@@ -108,7 +113,11 @@ def test_network_forward_parity(native, widths, ny, nx, nsol):
         assert native.cnn_num_params(net) == theta.size
         native.cnn_set_params(net, theta.astype(np.float32))
         out = np.zeros((nsol, ny, nx, 2), np.float32)
-        native.cnn_forward(net, enc_in.astype(np.float32), 1, sol_in.astype(np.float32), nsol, ny, nx, out)
+        native.cnn_set_conv_path(path)
+        try:
+            native.cnn_forward(net, enc_in.astype(np.float32), 1, sol_in.astype(np.float32), nsol, ny, nx, out)
+        finally:
+            native.cnn_set_conv_path(0)
         back = np.zeros(theta.size, np.float32)
         native.cnn_get_params(net, back)
     finally:

@@ -139,17 +139,20 @@ def test_weight_gradient_is_deterministic(native):
     assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
 
 
-@pytest.mark.parametrize("c0,c1,bcast,cout,mode,hin,win,nb", [
-    (16, 16, 0, 16, "same", 256, 256, 16),  # >= 3 tiles per CTA of the persistent forward kernel
-    (32, 0, 0, 64, "down", 256, 256, 16),
-    (128, 0, 0, 64, "up", 64, 128, 8),
-    (64, 64, 1, 64, "same", 128, 128, 16),  # batch-shared context
+@pytest.mark.parametrize("c0,c1,bcast,cout,mode,hin,win,nb,path", [
+    (16, 16, 0, 16, "same", 256, 256, 16, 0),  # >= 3 tiles per CTA of the persistent forward kernel
+    (32, 0, 0, 64, "down", 256, 256, 16, 0),
+    (128, 0, 0, 64, "up", 64, 128, 8, 0),
+    (64, 64, 1, 64, "same", 128, 128, 16, 0),  # batch-shared context
+    (16, 16, 0, 16, "same", 256, 256, 16, 3),  # tap rows in N: slot ring across tiles, two groups
+    (32, 0, 0, 32, "same", 200, 300, 16, 3),   # 32 channels, three column tiles of 100
 ])
-def test_conv_forward_multi_tile_sampled_parity(native, c0, c1, bcast, cout, mode, hin, win, nb):
+def test_conv_forward_multi_tile_sampled_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, path):
     """The persistent TMA convolution at sizes where every CTA loops over three or more
     tiles (accumulator-buffer alternation, barrier phases and ring reuse across tiles),
     checked at sampled output nodes (all of a few full rows and columns, and random ones)
-    against the oracle's point-by-point forward, to one BF16 unit."""
+    against the oracle's point-by-point forward, to one BF16 unit.  Path 3: the
+    same-grid layers with the three tap rows in N."""
     g = np.random.default_rng(c0 + cout)
     x0 = cnn.bf16_round(g.normal(size=(nb, hin, win, c0))).astype(np.float32)
     x1 = cnn.bf16_round(g.normal(size=((1 if bcast else nb), hin, win, c1))).astype(np.float32) if c1 else None
@@ -157,11 +160,19 @@ def test_conv_forward_multi_tile_sampled_parity(native, c0, c1, bcast, cout, mod
     b = g.normal(size=cout) * 0.1
     ho, wo = cnn.out_shape(hin, win, mode)
     y = torch.zeros((nb, ho, wo, cout), dtype=torch.float32, device="cuda")
-    native.cnn_conv3x3(torch.from_numpy(x0).cuda(), c0, None if x1 is None else torch.from_numpy(x1).cuda(), c1,
-                       bcast, nb, hin, win, _f32(w), _f32(b), cout, None, MODES[mode], 1, y)
+    n6 = native.cnn_conv_rowtaps_launches()
+    native.cnn_set_conv_path(path)
+    try:
+        native.cnn_conv3x3(torch.from_numpy(x0).cuda(), c0, None if x1 is None else torch.from_numpy(x1).cuda(),
+                           c1, bcast, nb, hin, win, _f32(w), _f32(b), cout, None, MODES[mode], 1, y)
+    finally:
+        native.cnn_set_conv_path(0)
     launch = native.cnn_conv_last_launch()
     npad = 16 if cout <= 16 else 32 * -(-cout // 32)
-    plan = native.cnn_conv_plan(MODES[mode], 16 * -(-c0 // 16), 16 * -(-c1 // 16) if c1 else 0, npad, hin, win, nb)
+    plan = native.cnn_conv_plan(MODES[mode], 16 * -(-c0 // 16), 16 * -(-c1 // 16) if c1 else 0, npad, hin, win, nb,
+                                narrow=2 if path == 3 else 0)
+    assert plan["mode"] == (6 if path == 3 else MODES[mode])
+    assert native.cnn_conv_rowtaps_launches() - n6 == (1 if path == 3 else 0)
     assert plan["tiles"] >= 3 * launch[0], (plan["tiles"], launch)
     y = y.cpu().numpy()
     pts = [(int(g.integers(nb)), int(g.integers(ho)), int(g.integers(wo))) for _ in range(400)]
