@@ -28,10 +28,13 @@ const char* kernel_name(int id) {
     return (id >= 0 && id < K_COUNT) ? names[id] : "?";
 }
 
-LaunchScope::LaunchScope(const helm_ctx* ctx, int kid) : c(const_cast<helm_ctx*>(ctx)), id(kid), slot(0) {
+void count_launch() {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     ++t_launches;
-    if (!c) return;   // launches outside a context are only counted
+}
+
+LaunchScope::LaunchScope(const helm_ctx* ctx, int kid) : c(const_cast<helm_ctx*>(ctx)), id(kid), slot(0) {
+    if (!c) return;
     c->prof.launches[id] += 1;
     if (!c->prof.on) return;
     Profiler& p = c->prof;
@@ -549,8 +552,8 @@ int helm_setup(helm_ctx** out, const float* kappa, const float* gamma, int nx, i
         if ((st = stage_in(c, gamma, N * sizeof(float), &sg, true))) { stage_free(c, &sk); return fail(st); }
         if ((st = stage_in(c, omegas, nfreq * sizeof(float), &so, true))) { stage_free(c, &sk); stage_free(c, &sg); return fail(st); }
         LaunchScope scope(c, K_MISC);
-        pack_medium_kernel<<<1184, 256, 0, c->stream>>>((const float*)sk.dev, (const float*)sg.dev, c->mg, N,
-                                                         (const float*)so.dev, c->omega_d, nfreq);
+        { pack_medium_kernel<<<1184, 256, 0, c->stream>>>((const float*)sk.dev, (const float*)sg.dev, c->mg, N,
+                                                         (const float*)so.dev, c->omega_d, nfreq); count_launch(); }
         cudaError_t e = cudaGetLastError();
         std::vector<float> om(nfreq);
         cudaError_t e2 = cudaMemcpyAsync(om.data(), so.dev, nfreq * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
@@ -561,11 +564,11 @@ int helm_setup(helm_ctx** out, const float* kappa, const float* gamma, int nx, i
     }
     {
         LaunchScope scope(c, K_MISC);
-        fill_int_kernel<<<(c->cap + 127) / 128, 128, 0, c->stream>>>(c->ones, 1, c->cap);
+        { fill_int_kernel<<<(c->cap + 127) / 128, 128, 0, c->stream>>>(c->ones, 1, c->cap); count_launch(); }
     }
     {
         LaunchScope scope(c, K_MISC);
-        fill_int_kernel<<<(c->cap + 127) / 128, 128, 0, c->stream>>>(c->rhs_freq, 0, c->cap);
+        { fill_int_kernel<<<(c->cap + 127) / 128, 128, 0, c->stream>>>(c->rhs_freq, 0, c->cap); count_launch(); }
     }
 
     // multigrid levels
@@ -645,8 +648,8 @@ int helm_set_medium(helm_ctx* c, const float* kappa, const float* gamma, const f
     if (!s) s = stage_in(c, omegas, nfreq * sizeof(float), &so, true);
     if (!s) {
         LaunchScope scope(c, K_MISC);
-        pack_medium_kernel<<<1184, 256, 0, c->stream>>>((const float*)sk.dev, (const float*)sg.dev, c->mg, N,
-                                                         (const float*)so.dev, c->omega_d, nfreq);
+        { pack_medium_kernel<<<1184, 256, 0, c->stream>>>((const float*)sk.dev, (const float*)sg.dev, c->mg, N,
+                                                         (const float*)so.dev, c->omega_d, nfreq); count_launch(); }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); s = HELM_ECUDA; }
     }
@@ -895,7 +898,7 @@ int helm_autotune(helm_ctx* c, int nrhs, int* n_shapes) {
     if (cudaMemsetAsync(f, 0, (size_t)nrhs * N * sizeof(float2), c->stream) != cudaSuccess) s = HELM_ECUDA;
     if (!s) {
         LaunchScope scope(c, K_MISC);
-        fill_int_kernel<<<(nrhs + 127) / 128, 128, 0, c->stream>>>(c->rhs_freq, 0, nrhs);
+        { fill_int_kernel<<<(nrhs + 127) / 128, 128, 0, c->stream>>>(c->rhs_freq, 0, nrhs); count_launch(); }
         if (cudaGetLastError() != cudaSuccess) s = HELM_ECUDA;
     }
     if (!s) {
@@ -942,7 +945,7 @@ int cnn_make_samples(helm_ctx* c, const helm_c64* x, const int* freq_idx, const 
     // carries a rounding of |H| |x| u, far above r once GMRES has converged)
     if (!s) {
         LaunchScope scope(c, K_MISC);
-        diff64_kernel<<<1184, 256, 0, c->stream>>>(dx, xt, de, nb * N);            // e = x - x~
+        { diff64_kernel<<<1184, 256, 0, c->stream>>>(dx, xt, de, nb * N); count_launch(); }            // e = x - x~
         ck(cudaGetLastError());
     }
     if (!s) ck(cudaMemsetAsync(db, 0, nb * N * sizeof(float2), c->stream));
@@ -950,7 +953,7 @@ int cnn_make_samples(helm_ctx* c, const helm_c64* x, const int* freq_idx, const 
     if (!s) s = launch_residual64(c, xt, db, dr, nb, 0, 1);                        // -H e
     if (!s) {
         LaunchScope scope(c, K_MISC);
-        negate_kernel<<<1184, 256, 0, c->stream>>>(dr, dr, nb * N);                // r = H e
+        { negate_kernel<<<1184, 256, 0, c->stream>>>(dr, dr, nb * N); count_launch(); }                // r = H e
         ck(cudaGetLastError());
     }
     if (!s) ck(cudaMemcpyAsync(r_out, dr, nb * N * sizeof(float2), cudaMemcpyDefault, c->stream));
@@ -984,7 +987,7 @@ int cnn_refine_samples(helm_ctx* c, const helm_c64* r, const helm_c64* e, const 
     if (!s) s = cnn_ctx_precondition(c, en, dr, nb, c->ones, 0);                   // e_net = network(r)
     if (!s) {
         LaunchScope scope(c, K_MISC);
-        widen_kernel<<<1184, 256, 0, c->stream>>>(en, xt, nb * N);
+        { widen_kernel<<<1184, 256, 0, c->stream>>>(en, xt, nb * N); count_launch(); }
         ck(cudaGetLastError());
     }
     std::vector<int> one(nb, 1);
@@ -996,17 +999,17 @@ int cnn_refine_samples(helm_ctx* c, const helm_c64* r, const helm_c64* e, const 
         if (!s) s = launch_residual64(c, xt, en, eo, nb, 0, 1);                    // eo = 0 - H e~
         if (!s) {
             LaunchScope scope(c, K_MISC);
-            negate_kernel<<<1184, 256, 0, c->stream>>>(eo, ro, nb * N);           // r' = H e~
+            { negate_kernel<<<1184, 256, 0, c->stream>>>(eo, ro, nb * N); count_launch(); }           // r' = H e~
             ck(cudaGetLastError());
         }
         if (!s) {
             LaunchScope scope(c, K_MISC);
-            diff_kernel<<<1184, 256, 0, c->stream>>>(en, xt, eo, nb * N);          // 0 - e~
+            { diff_kernel<<<1184, 256, 0, c->stream>>>(en, xt, eo, nb * N); count_launch(); }          // 0 - e~
             ck(cudaGetLastError());
         }
         if (!s) {
             LaunchScope scope(c, K_MISC);
-            negate_kernel<<<1184, 256, 0, c->stream>>>(eo, eo, nb * N);           // e' = e~
+            { negate_kernel<<<1184, 256, 0, c->stream>>>(eo, eo, nb * N); count_launch(); }           // e' = e~
             ck(cudaGetLastError());
         }
     }
@@ -1015,7 +1018,7 @@ int cnn_refine_samples(helm_ctx* c, const helm_c64* r, const helm_c64* e, const 
         if (!s) s = launch_residual64(c, xt, dr, ro, nb, 0, 1);                    // r' = r - H e~
         if (!s) {
             LaunchScope scope(c, K_MISC);
-            diff_kernel<<<1184, 256, 0, c->stream>>>(de, xt, eo, nb * N);          // e' = e - e~
+            { diff_kernel<<<1184, 256, 0, c->stream>>>(de, xt, eo, nb * N); count_launch(); }          // e' = e - e~
             ck(cudaGetLastError());
         }
     }

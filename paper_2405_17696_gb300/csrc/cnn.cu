@@ -379,7 +379,7 @@ __global__ void solver_output_kernel(const float* __restrict__ out, const float*
 // Rebuild the padded BF16 weights from the FP32 master parameters.
 int cnn_refresh_weights(cnn_model* m, cudaStream_t st) {
     for (const Layer& l : m->layers) {
-        pack_weights_kernel<<<64, 256, 0, st>>>(m->master, l.off, l.cin, l.cout, l.cin_pad, l.npad, l.w, l.b);
+        { pack_weights_kernel<<<64, 256, 0, st>>>(m->master, l.off, l.cin, l.cout, l.cin_pad, l.npad, l.w, l.b); count_launch(); }
         HELM_CK(cudaGetLastError());
     }
     return HELM_OK;
@@ -389,7 +389,7 @@ int cnn_refresh_weights(cnn_model* m, cudaStream_t st) {
 int cnn_encoder_input(const helm_ctx* c, void* out) {
     const long long n = (long long)c->nx * c->nz;
     LaunchScope scope(c, K_CNN_IO);
-    encoder_input_kernel<<<1184, 256, 0, c->stream>>>(c->mg, c->omega_d, std::sqrt(c->hx * c->hz), c->nfreq, n, (__nv_bfloat16*)out);
+    { encoder_input_kernel<<<1184, 256, 0, c->stream>>>(c->mg, c->omega_d, std::sqrt(c->hx * c->hz), c->nfreq, n, (__nv_bfloat16*)out); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -399,12 +399,12 @@ int cnn_solver_input(const helm_ctx* c, const float2* r, int nb, void* out, floa
     const long long n = (long long)c->nx * c->nz;
     {
         LaunchScope scope(c, K_CNN_IO);
-        rms_kernel<<<nb, 1024, 0, c->stream>>>(r, n, rms, nullptr);
+        { rms_kernel<<<nb, 1024, 0, c->stream>>>(r, n, rms, nullptr); count_launch(); }
         HELM_CK(cudaGetLastError());
     }
     LaunchScope scope(c, K_CNN_IO);
-    solver_input_kernel<<<dim3((unsigned)std::min<long long>((n + 255) / 256, 512), nb), 256, 0, c->stream>>>(
-        r, rms, c->mg, n, 1, (__nv_bfloat16*)out, nullptr);
+    { solver_input_kernel<<<dim3((unsigned)std::min<long long>((n + 255) / 256, 512), nb), 256, 0, c->stream>>>(
+        r, rms, c->mg, n, 1, (__nv_bfloat16*)out, nullptr); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -461,8 +461,8 @@ int cnn_ctx_setup(helm_ctx* c) {
     c->cnn_z.clear();
     {
         LaunchScope scope(c, K_CNN_IO);
-        encoder_input_kernel<<<1184, 256, 0, c->stream>>>(c->mg, c->omega_d, std::sqrt(c->hx * c->hz), c->nfreq, n,
-                                                          (__nv_bfloat16*)c->cnn_in);
+        { encoder_input_kernel<<<1184, 256, 0, c->stream>>>(c->mg, c->omega_d, std::sqrt(c->hx * c->hz), c->nfreq, n,
+                                                          (__nv_bfloat16*)c->cnn_in); count_launch(); }
         HELM_CK(cudaGetLastError());
     }
     Runner r(m, c, c->stream);
@@ -493,7 +493,7 @@ int cnn_ctx_compact(helm_ctx* c, int nb) {
         if (c->cnn_act_host[b]) c->cnn_idx_host[n++] = b;
     if (n == 0 || n == nb) return HELM_OK;
     HELM_CK(cudaMemcpyAsync(c->cnn_idx, c->cnn_idx_host, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    gather_int_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(c->rhs_freq, c->cnn_idx, n, c->cnn_zmapc);
+    { gather_int_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(c->rhs_freq, c->cnn_idx, n, c->cnn_zmapc); count_launch(); }
     HELM_CK(cudaGetLastError());
     c->cnn_nact = n;
     return HELM_OK;
@@ -511,8 +511,8 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
         LaunchScope scope(c, K_CNN_IO);
         // sum of |r|^2 per RHS into the scaled composition's sums (reset before they are used)
         HELM_CK(cudaMemsetAsync(c->cnn_alpha, 0, (size_t)nb * sizeof(double), c->stream));
-        sumsq_kernel<<<dim3(32, nb), 256, 0, c->stream>>>(v, n, mask, c->cnn_alpha);
-        rms_finalize_kernel<<<(nb + 127) / 128, 128, 0, c->stream>>>(c->cnn_alpha, n, nb, mask, c->cnn_rms);
+        { sumsq_kernel<<<dim3(32, nb), 256, 0, c->stream>>>(v, n, mask, c->cnn_alpha); count_launch(); }
+        { rms_finalize_kernel<<<(nb + 127) / 128, 128, 0, c->stream>>>(c->cnn_alpha, n, nb, mask, c->cnn_rms); count_launch(); }
         HELM_CK(cudaGetLastError());
     }
     const dim3 g2((unsigned)std::min<long long>((n + 255) / 256, 512), nb);
@@ -525,7 +525,7 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
     const dim3 gn(g2.x, (unsigned)nnet);
     {
         LaunchScope scope(c, K_CNN_IO);
-        solver_input_kernel<<<gn, 256, 0, c->stream>>>(v, c->cnn_rms, c->mg, n, 0, (__nv_bfloat16*)c->cnn_in, idx);
+        { solver_input_kernel<<<gn, 256, 0, c->stream>>>(v, c->cnn_rms, c->mg, n, 0, (__nv_bfloat16*)c->cnn_in, idx); count_launch(); }
         HELM_CK(cudaGetLastError());
     }
     Runner r(m, c, c->stream, &c->cnn_arena, &c->cnn_arena_bytes);
@@ -539,7 +539,7 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
     {
         LaunchScope scope(c, K_CNN_IO);
         float2* e0 = with_vcycle ? c->cnn_e0 : z;
-        solver_output_kernel<<<gn, 256, 0, c->stream>>>(c->cnn_out, c->cnn_rms, c->hx * c->hz, n, e0, idx);
+        { solver_output_kernel<<<gn, 256, 0, c->stream>>>(c->cnn_out, c->cnn_rms, c->hx * c->hz, n, e0, idx); count_launch(); }
         HELM_CK(cudaGetLastError());
     }
     if (!with_vcycle) return HELM_OK;
@@ -555,26 +555,26 @@ int cnn_ctx_precondition(helm_ctx* c, float2* z, const float2* v, int nb, const 
         double* acc = c->cnn_alpha;
         LaunchScope scope(c, K_CNN_IO);
         HELM_CK(cudaMemsetAsync(acc, 0, (size_t)3 * nb * sizeof(double), c->stream));
-        net_scale_dots_kernel<<<dim3(64, nb), 256, 0, c->stream>>>(fine_op(c, 0), v, c->cnn_e0, mask, guard, acc);
+        { net_scale_dots_kernel<<<dim3(64, nb), 256, 0, c->stream>>>(fine_op(c, 0), v, c->cnn_e0, mask, guard, acc); count_launch(); }
         if (c->nx % 2 == 0)
-            net_scaled_residual2_kernel<<<dim3((c->nx / 2 + 31) / 32, (c->nz + 7) / 8, nb), dim3(32, 8), 0,
-                                          c->stream>>>(fine_op(c, 0), v, c->cnn_e0, rr, acc, guard, mask);
+            { net_scaled_residual2_kernel<<<dim3((c->nx / 2 + 31) / 32, (c->nz + 7) / 8, nb), dim3(32, 8), 0,
+                                          c->stream>>>(fine_op(c, 0), v, c->cnn_e0, rr, acc, guard, mask); count_launch(); }
         else
-            net_scaled_residual_kernel<<<dim3((c->nx + 31) / 32, (c->nz + 7) / 8, nb), dim3(32, 8), 0, c->stream>>>(
-                fine_op(c, 0), v, c->cnn_e0, rr, acc, guard, mask);
+            { net_scaled_residual_kernel<<<dim3((c->nx + 31) / 32, (c->nz + 7) / 8, nb), dim3(32, 8), 0, c->stream>>>(
+                fine_op(c, 0), v, c->cnn_e0, rr, acc, guard, mask); count_launch(); }
         HELM_CK(cudaGetLastError());
     } else {
         // e_0 + V(r - H e_0): the V-cycle corrects what the network leaves of H e = r
         LaunchScope scope(c, K_CNN_IO);
-        net_residual_kernel<<<1184, 256, 0, c->stream>>>(fine_op(c, 0), v, c->cnn_e0, rr, nb);
+        { net_residual_kernel<<<1184, 256, 0, c->stream>>>(fine_op(c, 0), v, c->cnn_e0, rr, nb); count_launch(); }
         HELM_CK(cudaGetLastError());
     }
     HELM_TRY(vcycle_apply(c, z, nullptr, rr, nb, mask));
     LaunchScope scope(c, K_CNN_IO);
     if (scaled)
-        add_scaled_kernel<<<g2, 256, 0, c->stream>>>(z, c->cnn_e0, n, c->cnn_alpha, guard, mask);
+        { add_scaled_kernel<<<g2, 256, 0, c->stream>>>(z, c->cnn_e0, n, c->cnn_alpha, guard, mask); count_launch(); }
     else
-        add_kernel<<<1184, 256, 0, c->stream>>>(z, c->cnn_e0, n * nb);
+        { add_kernel<<<1184, 256, 0, c->stream>>>(z, c->cnn_e0, n * nb); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -656,7 +656,7 @@ int cnn_autotune(helm_ctx* c, int nrhs, int* n_shapes) {
         set_error("cnn_autotune: out of device memory");
         return HELM_ENOMEM;
     }
-    synth_residual_kernel<<<1184, 256, 0, c->stream>>>(r, n);
+    { synth_residual_kernel<<<1184, 256, 0, c->stream>>>(r, n); count_launch(); }
     int s = cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
     if (!s) {
         conv_tuning(true);
@@ -808,8 +808,8 @@ int cnn_forward(cnn_model* m, const float* enc_in, int nenc, const float* sol_in
     if (!s) {
         ck(cudaMemcpy(ein, enc_in, nenc * npix * 3 * sizeof(float), cudaMemcpyDefault));
         ck(cudaMemcpy(sin_, sol_in, nsol * npix * 3 * sizeof(float), cudaMemcpyDefault));
-        pack_input3_kernel<<<256, 256>>>(ein, xe, (long long)nenc * npix, (long long)npix);
-        pack_input3_kernel<<<256, 256>>>(sin_, xs, (long long)nsol * npix, (long long)npix);
+        { pack_input3_kernel<<<256, 256>>>(ein, xe, (long long)nenc * npix, (long long)npix); count_launch(); }
+        { pack_input3_kernel<<<256, 256>>>(sin_, xs, (long long)nsol * npix, (long long)npix); count_launch(); }
         ck(cudaGetLastError());
     }
     if (!s) {
@@ -866,9 +866,9 @@ int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, 
     }
     if (!s) {
         const long long hwi = (long long)hin * win, hwo = (long long)hout * wout;
-        pack_channels_kernel<<<256, 256>>>(fx0, c0, cp0, bx0, nin, hwi);
-        if (c1) pack_channels_kernel<<<256, 256>>>(fx1, c1, cp1, bx1, nin1, hwi);
-        if (res) pack_channels_kernel<<<256, 256>>>(fr, cout, npad, br, nout, hwo);
+        { pack_channels_kernel<<<256, 256>>>(fx0, c0, cp0, bx0, nin, hwi); count_launch(); }
+        if (c1) { pack_channels_kernel<<<256, 256>>>(fx1, c1, cp1, bx1, nin1, hwi); count_launch(); }
+        if (res) { pack_channels_kernel<<<256, 256>>>(fr, cout, npad, br, nout, hwo); count_launch(); }
         // weights: logical [cout][9][c0 + c1] -> padded [npad][9][cp0 + cp1] (concat parts padded separately)
         std::vector<float> hw((size_t)cout * 9 * cin + cout);
         ck(cudaMemcpy(hw.data(), fw, hw.size() * sizeof(float), cudaMemcpyDeviceToHost));
@@ -898,7 +898,7 @@ int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, 
             s = launch_conv3x3(a, nullptr);
         }
         if (!s) {
-            unpack_channels_kernel<<<256, 256>>>(by, npad, cout, fy, nout, (long long)hout * wout);
+            { unpack_channels_kernel<<<256, 256>>>(by, npad, cout, fy, nout, (long long)hout * wout); count_launch(); }
             ck(cudaGetLastError());
             ck(cudaDeviceSynchronize());
             int herr = 0;
@@ -976,9 +976,9 @@ int cnn_conv3x3_backward(const float* x0, int c0, const float* x1, int c1, int x
         ck(cudaMemcpy(bw, hbw.data(), hbw.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
     }
     if (!s) {
-        pack_channels_kernel<<<256, 256>>>(fx0, c0, cp0, bx0, nin, hwi);
-        if (c1) pack_channels_kernel<<<256, 256>>>(fx1, c1, cp1, bx1, nin1, hwi);
-        pack_channels_kernel<<<256, 256>>>(fgy, cout, npad, bg, nout, hwo);
+        { pack_channels_kernel<<<256, 256>>>(fx0, c0, cp0, bx0, nin, hwi); count_launch(); }
+        if (c1) { pack_channels_kernel<<<256, 256>>>(fx1, c1, cp1, bx1, nin1, hwi); count_launch(); }
+        { pack_channels_kernel<<<256, 256>>>(fgy, cout, npad, bg, nout, hwo); count_launch(); }
         ck(cudaGetLastError());
     }
     float* scratch = nullptr;

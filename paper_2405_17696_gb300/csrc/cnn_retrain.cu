@@ -135,7 +135,7 @@ int build_initial(helm_ctx* c, RetrainState* s) {
             iters[i] = std::min(k, s->opt.max_gmres_steps);
             fi[i] = s->freq[i0 + i];
         }
-        draw_cn01_kernel<<<1184, 256, 0, c->stream>>>(x, (long long)nb * (long long)N, (long long)i0 * (long long)N, kx);
+        { draw_cn01_kernel<<<1184, 256, 0, c->stream>>>(x, (long long)nb * (long long)N, (long long)i0 * (long long)N, kx); count_launch(); }
         if (cudaGetLastError() != cudaSuccess) {
             set_error("cnn_retrain: draw kernel launch failed");
             st = HELM_ECUDA;

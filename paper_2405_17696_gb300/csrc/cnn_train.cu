@@ -395,7 +395,7 @@ int layer_wgrad(const __nv_bfloat16* x0, int c0, const __nv_bfloat16* x1, int c1
         attr = true;
     }
     LaunchScope scope(prof_ctx, K_WGRAD);
-    wgrad_kernel<<<dim3((unsigned)gx, gy, gz), 256, smem, st>>>(a, w);
+    { wgrad_kernel<<<dim3((unsigned)gx, gy, gz), 256, smem, st>>>(a, w); count_launch(); }
     return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
 }
 
@@ -409,7 +409,7 @@ int layer_dgrad(const __nv_bfloat16* g, int npad, const __nv_bfloat16* W, int ci
                 cudaStream_t st, const helm_ctx* prof_ctx) {
     {
         LaunchScope scope(prof_ctx, K_CNN_IO);
-        transpose_weights_kernel<<<256, 256, 0, st>>>(W, npad, cin_pad, off, cp, mode == 1 ? 0 : 1, Wt);
+        { transpose_weights_kernel<<<256, 256, 0, st>>>(W, npad, cin_pad, off, cp, mode == 1 ? 0 : 1, Wt); count_launch(); }
     }
     ConvArgs ca;
     ca.x0 = g; ca.c0 = npad; ca.x1 = nullptr; ca.c1 = 0; ca.x1_bcast = 0; ca.x1_map = nullptr;
@@ -431,7 +431,7 @@ int layer_dgrad(const __nv_bfloat16* g, int npad, const __nv_bfloat16* W, int ci
     }
     if (s) return s;
     LaunchScope scope(prof_ctx, K_CNN_IO);
-    sumpool_accum_kernel<<<1184, 256, 0, st>>>(fine, nb, hin, win, cp, target);
+    { sumpool_accum_kernel<<<1184, 256, 0, st>>>(fine, nb, hin, win, cp, target); count_launch(); }
     return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
 }
 
@@ -541,12 +541,12 @@ class Backward {
                 LaunchScope scope(c_, K_CNN_IO);
                 const __nv_bfloat16* ymask = L.relu ? (const __nv_bfloat16*)op.y : nullptr;
                 if (cg == L.npad && cg % 8 == 0)
-                    mask_to_bf16_vec_kernel<<<dim3((unsigned)std::min<long long>((nout + 255) / 256, 1184),
+                    { mask_to_bf16_vec_kernel<<<dim3((unsigned)std::min<long long>((nout + 255) / 256, 1184),
                                                    (unsigned)(cg / 8)), 256, 0, st_>>>(
-                        Gy, ymask, L.npad, L.npad, nout, (long long)op.hout * op.wout, g, rg);
+                        Gy, ymask, L.npad, L.npad, nout, (long long)op.hout * op.wout, g, rg); count_launch(); }
                 else
-                    mask_to_bf16_kernel<<<1184, 256, 0, st_>>>(Gy, cg, ymask, L.npad, L.npad, nout,
-                                                              (long long)op.hout * op.wout, g, rg);
+                    { mask_to_bf16_kernel<<<1184, 256, 0, st_>>>(Gy, cg, ymask, L.npad, L.npad, nout,
+                                                              (long long)op.hout * op.wout, g, rg); count_launch(); }
             }
             // weight and bias gradient
             {
@@ -584,8 +584,8 @@ class Backward {
                     float* gctx = grad_of(x, (size_t)(op.x1_bcast == 1 ? 1 : nctx) * per);
                     if (!gctx) { ok_ = false; break; }
                     LaunchScope scope(c_, K_CNN_IO);
-                    reduce_to_context_kernel<<<1184, 256, 0, st_>>>(target, per, op.nb, op.zmap, op.x1_bcast,
-                                                                    op.x1_bcast == 1 ? 1 : nctx, gctx);
+                    { reduce_to_context_kernel<<<1184, 256, 0, st_>>>(target, per, op.nb, op.zmap, op.x1_bcast,
+                                                                    op.x1_bcast == 1 ? 1 : nctx, gctx); count_launch(); }
                 }
             }
         }
@@ -670,10 +670,10 @@ int cnn_loss_grad_impl(cnn_model* m, helm_ctx* c, const float2* r, const float2*
         if (!s && !run.solver(xs, nb, c->nz, c->nx, z, 2, out)) s = HELM_ECUDA;
         if (!s) {
             LaunchScope scope(c, K_CNN_IO);
-            if (wt) inv_energy_kernel<<<nb, 256, 0, st>>>(e, n, wt);
-            mse_grad_kernel<<<dim3((unsigned)std::min<long long>((n + 255) / 256, 128), nb), 256, 0, st>>>(
+            if (wt) { inv_energy_kernel<<<nb, 256, 0, st>>>(e, n, wt); count_launch(); }
+            { mse_grad_kernel<<<dim3((unsigned)std::min<long long>((n + 255) / 256, 128), nb), 256, 0, st>>>(
                 out, e, rms, wt, c->hx * c->hz, n, nb, 1.0f / (float)nb, gout,
-                                                  dloss);
+                                                  dloss); count_launch(); }
             ck(cudaGetLastError());
         }
         if (!s) {
@@ -695,8 +695,8 @@ int cnn_adam_impl(cnn_model* m, float lr, cudaStream_t st) {
     const double b1 = 0.9, b2 = 0.999;
     const float bc1 = (float)(1.0 - std::pow(b1, (double)m->adam_t));
     const float bc2 = (float)(1.0 - std::pow(b2, (double)m->adam_t));
-    adam_kernel<<<1184, 256, 0, st>>>(m->master, m->grad, m->adam_m, m->adam_v, m->nparams, lr, (float)b1, (float)b2,
-                                      1e-8f, bc1, bc2);
+    { adam_kernel<<<1184, 256, 0, st>>>(m->master, m->grad, m->adam_m, m->adam_v, m->nparams, lr, (float)b1, (float)b2,
+                                      1e-8f, bc1, bc2); count_launch(); }
     HELM_CK(cudaGetLastError());
     return cnn_refresh_weights(m, st);
 }

@@ -314,8 +314,12 @@ namespace helm {
 
 inline size_t npts(const helm_ctx* c) { return (size_t)c->nx * c->nz; }
 
-// Counts every kernel launch of the library; when profiling is on, brackets
-// the launch with a pair of CUDA events on the context's stream.
+// Counts one kernel launch of the library (helm_launch_count); every launch site
+// calls it right after its launch.
+void count_launch();
+
+// Counts the launches of a kernel class per context; when profiling is on,
+// brackets them with a pair of CUDA events on the context's stream.
 struct LaunchScope {
     helm_ctx* c;
     int id;

@@ -231,11 +231,11 @@ int launch_coarse_gmres(const helm_ctx* c, int level, float2* u_out, int nb, con
     }
     const Tally tl = tally(c, K_COARSE_GMRES, 8ull * Nc * (kk * kk + 5 * kk + 2));
     if (sms > 0 && nb > sms)
-        coarse_gmres_kernel<256><<<nb, 256, 0, c->stream>>>(coarse_op(c, level), c->Vc, (size_t)c->cap * Nc, c->Wc,
-                                                            u_out, k, mask, tl);
+        { coarse_gmres_kernel<256><<<nb, 256, 0, c->stream>>>(coarse_op(c, level), c->Vc, (size_t)c->cap * Nc, c->Wc,
+                                                            u_out, k, mask, tl); count_launch(); }
     else
-        coarse_gmres_kernel<512><<<nb, 512, 0, c->stream>>>(coarse_op(c, level), c->Vc, (size_t)c->cap * Nc, c->Wc,
-                                                            u_out, k, mask, tl);
+        { coarse_gmres_kernel<512><<<nb, 512, 0, c->stream>>>(coarse_op(c, level), c->Vc, (size_t)c->cap * Nc, c->Wc,
+                                                            u_out, k, mask, tl); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }

@@ -264,7 +264,7 @@ int launch_ck(const ConvArgs& a, cudaStream_t st) {
     }
     const long long mtot = (long long)a.nb * a.hout * a.wout;
     const unsigned grid = (unsigned)((mtot + CT - 1) / CT);
-    conv3x3_tc_kernel<CK><<<grid, NT, smem, st>>>(a);
+    { conv3x3_tc_kernel<CK><<<grid, NT, smem, st>>>(a); count_launch(); }
     return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
 }
 

@@ -1060,7 +1060,7 @@ int launch_mode(const CUtensorMap& tm0, const CUtensorMap& tm1, const CUtensorMa
     g_last_launch[3] = (int)smem_req;
     g_last_launch[4] = regs;
     g_last_launch[5] = static_smem;
-    conv3x3_tma_kernel<MODE><<<(unsigned)grid, NT, smem_req, st>>>(tm0, tm1, tmw, a, g);
+    { conv3x3_tma_kernel<MODE><<<(unsigned)grid, NT, smem_req, st>>>(tm0, tm1, tmw, a, g); count_launch(); }
     return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
 }
 

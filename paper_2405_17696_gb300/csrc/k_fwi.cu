@@ -161,7 +161,7 @@ extern "C" int fwi_misfit_grad(helm_ctx* c, const int* src_idx, int nsrc, const 
         for (int i = 0; i < nb; ++i) fidx[i] = (b0 + i) / nsrc;
         {
             LaunchScope scope(c, K_MISC);
-            point_sources_kernel<<<dim3(64, nb), 256, 0, c->stream>>>(g, src, nsrc, b0, N, 1.0f / (c->hx * c->hz));
+            { point_sources_kernel<<<dim3(64, nb), 256, 0, c->stream>>>(g, src, nsrc, b0, N, 1.0f / (c->hx * c->hz)); count_launch(); }
             ck(cudaGetLastError());
         }
         if (status) break;
@@ -169,18 +169,18 @@ extern "C" int fwi_misfit_grad(helm_ctx* c, const int* src_idx, int nsrc, const 
         if (s != HELM_OK) { status = s; break; }
         {
             LaunchScope scope(c, K_MISC);
-            receiver_residual_kernel<<<nb, 256, 0, c->stream>>>(u, dptr + (size_t)b0 * nrcv, rcv, nrcv, N, r,
-                                                                  phi + b0);
+            { receiver_residual_kernel<<<nb, 256, 0, c->stream>>>(u, dptr + (size_t)b0 * nrcv, rcv, nrcv, N, r,
+                                                                  phi + b0); count_launch(); }
             ck(cudaGetLastError());
         }
         {
             LaunchScope scope(c, K_MISC);
-            zero_c64_kernel<<<1184, 256, 0, c->stream>>>(q, (size_t)nb * N);
+            { zero_c64_kernel<<<1184, 256, 0, c->stream>>>(q, (size_t)nb * N); count_launch(); }
             ck(cudaGetLastError());
         }
         {
             LaunchScope scope(c, K_MISC);
-            scatter_adjoint_kernel<<<nb, 256, 0, c->stream>>>(r, rcv, nrcv, N, q);
+            { scatter_adjoint_kernel<<<nb, 256, 0, c->stream>>>(r, rcv, nrcv, N, q); count_launch(); }
             ck(cudaGetLastError());
         }
         if (status) break;
@@ -189,8 +189,8 @@ extern "C" int fwi_misfit_grad(helm_ctx* c, const int* src_idx, int nsrc, const 
         // helm_solve left the frequency of every slot in rhs_freq
         {
             LaunchScope scope(c, K_MISC);
-            gradient_kernel<<<1184, 256, 0, c->stream>>>(u, mu, c->mg, c->omega_d, c->rhs_freq, nb, N, gptr,
-                                                         b0 > 0 ? 1 : 0);
+            { gradient_kernel<<<1184, 256, 0, c->stream>>>(u, mu, c->mg, c->omega_d, c->rhs_freq, nb, N, gptr,
+                                                         b0 > 0 ? 1 : 0); count_launch(); }
             ck(cudaGetLastError());
         }
     }

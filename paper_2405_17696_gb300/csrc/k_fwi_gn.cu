@@ -280,11 +280,11 @@ class Fwi {
     int sources(int b0, int nb) {
         {
             LaunchScope scope(c_, K_MISC);
-            zero_f2_kernel<<<1184, 256, 0, c_->stream>>>(q_, (size_t)nb * N_);
+            { zero_f2_kernel<<<1184, 256, 0, c_->stream>>>(q_, (size_t)nb * N_); count_launch(); }
         }
         LaunchScope scope(c_, K_MISC);
-        encoded_sources_kernel<<<(nb + 127) / 128, 128, 0, c_->stream>>>(q_, src_, w_, sv_->nsrc, nsim_, b0, nb, N_,
-                                                                         1.0f / (c_->hx * c_->hz));
+        { encoded_sources_kernel<<<(nb + 127) / 128, 128, 0, c_->stream>>>(q_, src_, w_, sv_->nsrc, nsim_, b0, nb, N_,
+                                                                         1.0f / (c_->hx * c_->hz)); count_launch(); }
         HELM_CK(cudaGetLastError());
         return HELM_OK;
     }
@@ -300,13 +300,13 @@ class Fwi {
             std::vector<int> fi;
             freqs(b0, nb, fi);
             HELM_CK(cudaMemcpyAsync(c_->rhs_freq, fi.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c_->stream));
-            born_rhs_kernel<<<1184, 256, 0, c_->stream>>>(u, v, c_->mg, c_->omega_d, c_->rhs_freq, nb, N_, q_);
+            { born_rhs_kernel<<<1184, 256, 0, c_->stream>>>(u, v, c_->mg, c_->omega_d, c_->rhs_freq, nb, N_, q_); count_launch(); }
             HELM_CK(cudaGetLastError());
             HELM_CK(cudaStreamSynchronize(c_->stream));   // fi leaves scope
         }
         HELM_TRY(solve(q_, x_, b0, nb, tol));
         LaunchScope scope(c_, K_MISC);
-        sample_kernel<<<256, 256, 0, c_->stream>>>(x_, rcv_, sv_->nrcv, N_, nb, dd);
+        { sample_kernel<<<256, 256, 0, c_->stream>>>(x_, rcv_, sv_->nrcv, N_, nb, dd); count_launch(); }
         HELM_CK(cudaGetLastError());
         return HELM_OK;
     }
@@ -314,21 +314,21 @@ class Fwi {
     int jtd(const double2* u, const float2* dd, int b0, int nb, double tol, double scale, double* acc) {
         {
             LaunchScope scope(c_, K_MISC);
-            zero_f2_kernel<<<1184, 256, 0, c_->stream>>>(q_, (size_t)nb * N_);
-            scatter_conj_kernel<<<(nb + 127) / 128, 128, 0, c_->stream>>>(dd, rcv_, sv_->nrcv, N_, nb, q_);
+            { zero_f2_kernel<<<1184, 256, 0, c_->stream>>>(q_, (size_t)nb * N_); count_launch(); }
+            { scatter_conj_kernel<<<(nb + 127) / 128, 128, 0, c_->stream>>>(dd, rcv_, sv_->nrcv, N_, nb, q_); count_launch(); }
             HELM_CK(cudaGetLastError());
         }
         HELM_TRY(solve(q_, x_, b0, nb, tol));
         // helm_solve left the frequency of every slot in rhs_freq
         LaunchScope scope(c_, K_MISC);
-        adjoint_accum_kernel<<<1184, 256, 0, c_->stream>>>(u, x_, c_->mg, c_->omega_d, c_->rhs_freq, nb, N_, scale, acc);
+        { adjoint_accum_kernel<<<1184, 256, 0, c_->stream>>>(u, x_, c_->mg, c_->omega_d, c_->rhs_freq, nb, N_, scale, acc); count_launch(); }
         HELM_CK(cudaGetLastError());
         return HELM_OK;
     }
     int dot(const double* a, const double* b, double* out) {
         {
             LaunchScope scope(c_, K_MISC);
-            dot_partial_kernel<<<DOT_BLOCKS, 256, 0, c_->stream>>>(a, b, N_, part_);
+            { dot_partial_kernel<<<DOT_BLOCKS, 256, 0, c_->stream>>>(a, b, N_, part_); count_launch(); }
             HELM_CK(cudaGetLastError());
         }
         std::vector<double> h(DOT_BLOCKS);
@@ -354,8 +354,8 @@ class Fwi {
             float2* rb = R ? R + (size_t)b0 * sv_->nrcv : rtmp;
             HELM_TRY(forward(b0, nb, ub, tol));
             LaunchScope scope(c_, K_MISC);
-            data_residual_kernel<<<nb, 256, 0, c_->stream>>>(ub, d_obs + (size_t)b0 * sv_->nrcv, rcv_, sv_->nrcv, N_,
-                                                             rb, phi_dev_ + b0);
+            { data_residual_kernel<<<nb, 256, 0, c_->stream>>>(ub, d_obs + (size_t)b0 * sv_->nrcv, rcv_, sv_->nrcv, N_,
+                                                             rb, phi_dev_ + b0); count_launch(); }
             HELM_CK(cudaGetLastError());
         }
         std::vector<double> h(nb_tot_);
@@ -423,7 +423,7 @@ int set_model(helm_ctx* c, Fwi& F, const float* m0, const double* dm, double alp
     HELM_TRY(F.alloc(&gam, N));
     {
         LaunchScope scope(c, K_MISC);
-        model_step_kernel<<<1184, 256, 0, c->stream>>>(m0, dm, alpha, lo, hi, c->mg, m_out, kap, gam, N);
+        { model_step_kernel<<<1184, 256, 0, c->stream>>>(m0, dm, alpha, lo, hi, c->mg, m_out, kap, gam, N); count_launch(); }
         HELM_CK(cudaGetLastError());
     }
     const int s = helm_set_medium(c, kap, gam, c->omega_d, c->nfreq);
@@ -456,7 +456,7 @@ int fwi_model_to_kappa(const float* m, float* kappa, long long n) {
         set_error("fwi_model_to_kappa: device arrays of n >= 1 elements expected");
         return HELM_EINVAL;
     }
-    sqrt_kernel<<<1184, 256>>>(m, kappa, (size_t)n);
+    { sqrt_kernel<<<1184, 256>>>(m, kappa, (size_t)n); count_launch(); }
     HELM_CK(cudaGetLastError());
     HELM_CK(cudaDeviceSynchronize());
     return HELM_OK;
@@ -475,7 +475,7 @@ int fwi_forward_data(helm_ctx* c, const fwi_survey* sv, double tol, helm_c64* d_
         const int nb = std::min(F.nbc(), F.nb_tot() - b0);
         HELM_TRY(F.forward(b0, nb, u, tol));
         LaunchScope scope(c, K_MISC);
-        sample_kernel<<<256, 256, 0, c->stream>>>(u, F.rcv(), F.nrcv(), F.N(), nb, d + (size_t)b0 * F.nrcv());
+        { sample_kernel<<<256, 256, 0, c->stream>>>(u, F.rcv(), F.nrcv(), F.N(), nb, d + (size_t)b0 * F.nrcv()); count_launch(); }
         HELM_CK(cudaGetLastError());
     }
     if (iters_out) *iters_out = F.iterations();
@@ -498,7 +498,7 @@ int fwi_jacobian(helm_ctx* c, const fwi_survey* sv, const float* dm, double tol,
     HELM_TRY(F.alloc(&dd, (size_t)F.nb_tot() * F.nrcv()));
     {
         LaunchScope scope(c, K_MISC);
-        f64_of_f32_kernel<<<1184, 256, 0, c->stream>>>(dmd, v, 1.0, F.N());
+        { f64_of_f32_kernel<<<1184, 256, 0, c->stream>>>(dmd, v, 1.0, F.N()); count_launch(); }
         HELM_CK(cudaGetLastError());
     }
     for (int b0 = 0; b0 < F.nb_tot(); b0 += F.nbc()) {
@@ -531,7 +531,7 @@ int fwi_jacobian_adjoint(helm_ctx* c, const fwi_survey* sv, const helm_c64* dd, 
     }
     {
         LaunchScope scope(c, K_MISC);
-        f32_of_f64_kernel<<<1184, 256, 0, c->stream>>>(acc, out, F.N());
+        { f32_of_f64_kernel<<<1184, 256, 0, c->stream>>>(acc, out, F.N()); count_launch(); }
         HELM_CK(cudaGetLastError());
     }
     return copy_out(dm_out, (const float*)out, F.N(), c->stream);
@@ -565,7 +565,7 @@ int fwi_gn_iteration(helm_ctx* c, const fwi_survey* sv, const helm_c64* d_obs, c
         HELM_CK(cudaMemcpyAsync(wd, sv->src_w, (size_t)sv->nsim * sv->nsrc * sizeof(float), cudaMemcpyHostToDevice,
                                 c->stream));
         LaunchScope scope(c, K_MISC);
-        encode_data_kernel<<<256, 256, 0, c->stream>>>(dobs, wd, c->nfreq, sv->nsrc, sv->nsim, sv->nrcv, denc);
+        { encode_data_kernel<<<256, 256, 0, c->stream>>>(dobs, wd, c->nfreq, sv->nsrc, sv->nsim, sv->nrcv, denc); count_launch(); }
         HELM_CK(cudaGetLastError());
         dobs = denc;
     }
@@ -602,8 +602,8 @@ int fwi_gn_iteration(helm_ctx* c, const fwi_survey* sv, const helm_c64* d_obs, c
     HELM_CK(cudaMemsetAsync(x, 0, N * sizeof(double), c->stream));
     {
         LaunchScope scope(c, K_MISC);
-        axpby_kernel<<<1184, 256, 0, c->stream>>>(-0.5, g, 0.0, r, N);   // r = -g / 2
-        axpby_kernel<<<1184, 256, 0, c->stream>>>(1.0, r, 0.0, p, N);    // p = r
+        { axpby_kernel<<<1184, 256, 0, c->stream>>>(-0.5, g, 0.0, r, N); count_launch(); }   // r = -g / 2
+        { axpby_kernel<<<1184, 256, 0, c->stream>>>(1.0, r, 0.0, p, N); count_launch(); }    // p = r
         HELM_CK(cudaGetLastError());
     }
     double rr = 0.0;
@@ -619,7 +619,7 @@ int fwi_gn_iteration(helm_ctx* c, const fwi_survey* sv, const helm_c64* d_obs, c
         }
         if (o.reg > 0) {
             LaunchScope scope(c, K_MISC);
-            axpby_kernel<<<1184, 256, 0, c->stream>>>((double)o.reg, p, 1.0, ap, N);
+            { axpby_kernel<<<1184, 256, 0, c->stream>>>((double)o.reg, p, 1.0, ap, N); count_launch(); }
             HELM_CK(cudaGetLastError());
         }
         double pap = 0.0;
@@ -628,15 +628,15 @@ int fwi_gn_iteration(helm_ctx* c, const fwi_survey* sv, const helm_c64* d_obs, c
         const double alpha = rr / pap;
         {
             LaunchScope scope(c, K_MISC);
-            axpby_kernel<<<1184, 256, 0, c->stream>>>(alpha, p, 1.0, x, N);     // x += alpha p
-            axpby_kernel<<<1184, 256, 0, c->stream>>>(-alpha, ap, 1.0, r, N);   // r -= alpha A p
+            { axpby_kernel<<<1184, 256, 0, c->stream>>>(alpha, p, 1.0, x, N); count_launch(); }     // x += alpha p
+            { axpby_kernel<<<1184, 256, 0, c->stream>>>(-alpha, ap, 1.0, r, N); count_launch(); }   // r -= alpha A p
             HELM_CK(cudaGetLastError());
         }
         double rr_new = 0.0;
         HELM_TRY(F.dot(r, r, &rr_new));
         {
             LaunchScope scope(c, K_MISC);
-            axpby_kernel<<<1184, 256, 0, c->stream>>>(1.0, r, rr_new / rr, p, N);   // p = r + beta p
+            { axpby_kernel<<<1184, 256, 0, c->stream>>>(1.0, r, rr_new / rr, p, N); count_launch(); }   // p = r + beta p
             HELM_CK(cudaGetLastError());
         }
         rr = rr_new;

@@ -74,7 +74,7 @@ int helm_resample(const float* src, int nx0, int nz0, float* dst, int nx1, int n
     }
     if (src == dst) { set_error("helm_resample: src and dst must not alias"); return HELM_EINVAL; }
     const cudaStream_t st = (cudaStream_t)stream;
-    resample_kernel<<<1184, 256, 0, st>>>(src, nx0, nz0, dst, nx1, nz1, alpha, beta);
+    { resample_kernel<<<1184, 256, 0, st>>>(src, nx0, nz0, dst, nx1, nz1, alpha, beta); count_launch(); }
     HELM_CK(cudaGetLastError());
     HELM_CK(cudaStreamSynchronize(st));
     return HELM_OK;

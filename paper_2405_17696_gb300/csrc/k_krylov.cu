@@ -433,7 +433,7 @@ int launch_arnoldi_dots(const helm_ctx* c, const Op& op, KState& st, const float
             switch (j) {
 #define HELM_DOTS2_CASE(J)                                                                                  \
     case J:                                                                                                 \
-        arnoldi_dots_fine2_kernel<J><<<grid2, block2, 0, c->stream>>>(op, st, z, w, V, vstride, nx, nz, tl); \
+        { arnoldi_dots_fine2_kernel<J><<<grid2, block2, 0, c->stream>>>(op, st, z, w, V, vstride, nx, nz, tl); count_launch(); } \
         break;
                 HELM_J_CASES(HELM_DOTS2_CASE)
 #undef HELM_DOTS2_CASE
@@ -449,7 +449,7 @@ int launch_arnoldi_dots(const helm_ctx* c, const Op& op, KState& st, const float
     switch (j) {
 #define HELM_DOTS_CASE(J)                                                                                     \
     case J:                                                                                                   \
-        arnoldi_dots_kernel<Op, J><<<grid, block, 0, c->stream>>>(op, st, z, w, V, vstride, nx, nz, tl);   \
+        { arnoldi_dots_kernel<Op, J><<<grid, block, 0, c->stream>>>(op, st, z, w, V, vstride, nx, nz, tl); count_launch(); }   \
         break;
         HELM_J_CASES(HELM_DOTS_CASE)
 #undef HELM_DOTS_CASE
@@ -474,8 +474,8 @@ int launch_arnoldi_update_ex(const helm_ctx* c, KState& st, const float2* w, flo
     switch (j) {
 #define HELM_UPD_CASE(J)                                                                                        \
     case J:                                                                                                     \
-        arnoldi_update_kernel<J><<<grid, block, 0, c->stream>>>(st, w, V, vstride, nx, nz, iters_base, max_iter, \
-                                                                 status, tl);                                  \
+        { arnoldi_update_kernel<J><<<grid, block, 0, c->stream>>>(st, w, V, vstride, nx, nz, iters_base, max_iter, \
+                                                                 status, tl); count_launch(); }                                  \
         break;
         HELM_J_CASES(HELM_UPD_CASE)
 #undef HELM_UPD_CASE
@@ -495,8 +495,8 @@ int launch_arnoldi_update(const helm_ctx* c, KState& st, const float2* w, float2
 int launch_kstate_init(const helm_ctx* c, KState& st, const float2* v0, int nx, int nz, int nb,
                        const int* mask) {
     LaunchScope scope(c, K_KINIT);
-    kstate_init_kernel<<<tiled_grid(nx, nz, nb), dim3(TILE_X, TILE_Y), 0, c->stream>>>(st, v0, nx, nz, mask,
-                                                                                    tally(c, K_KINIT, 8ull * nx * nz));
+    { kstate_init_kernel<<<tiled_grid(nx, nz, nb), dim3(TILE_X, TILE_Y), 0, c->stream>>>(st, v0, nx, nz, mask,
+                                                                                    tally(c, K_KINIT, 8ull * nx * nz)); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -505,14 +505,14 @@ int launch_normalize_v0(const helm_ctx* c, KState& st, float2* v0, size_t n, int
     size_t blocks = (n + 255) / 256;
     if (blocks > 64) blocks = 64;
     LaunchScope scope(c, K_MISC);
-    normalize_v0_kernel<<<dim3((unsigned)blocks, nb), 256, 0, c->stream>>>(st, v0, n);
+    { normalize_v0_kernel<<<dim3((unsigned)blocks, nb), 256, 0, c->stream>>>(st, v0, n); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
 
 int launch_lsq(const helm_ctx* c, KState& st, int nb) {
     LaunchScope scope(c, K_LSQ);
-    lsq_kernel<<<(nb + 127) / 128, 128, 0, c->stream>>>(st, nb);
+    { lsq_kernel<<<(nb + 127) / 128, 128, 0, c->stream>>>(st, nb); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -525,8 +525,8 @@ static int grid_for(size_t n) {
 int launch_combine(const helm_ctx* c, const KState& st, float2* out, const float2* Zb, size_t zstride, size_t n,
                    int nb, const int* mask) {
     LaunchScope scope(c, K_COMBINE);
-    combine_kernel<<<dim3(grid_for(n) / 8 + 1, nb), 256, 0, c->stream>>>(st, out, Zb, zstride, n, mask,
-                                                                                  tally(c, K_COMBINE, 8ull * n, 8ull * n));
+    { combine_kernel<<<dim3(grid_for(n) / 8 + 1, nb), 256, 0, c->stream>>>(st, out, Zb, zstride, n, mask,
+                                                                                  tally(c, K_COMBINE, 8ull * n, 8ull * n)); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -534,8 +534,8 @@ int launch_combine(const helm_ctx* c, const KState& st, float2* out, const float
 int launch_update_x64(const helm_ctx* c, const KState& st, double2* x, const float2* Zb, size_t zstride,
                       size_t n, int nb) {
     LaunchScope scope(c, K_UPDATE_X);
-    update_x64_kernel<<<dim3(grid_for(n) / 8 + 1, nb), 256, 0, c->stream>>>(st, x, Zb, zstride, n,
-                                                                                     tally(c, K_UPDATE_X, 32ull * n, 8ull * n));
+    { update_x64_kernel<<<dim3(grid_for(n) / 8 + 1, nb), 256, 0, c->stream>>>(st, x, Zb, zstride, n,
+                                                                                     tally(c, K_UPDATE_X, 32ull * n, 8ull * n)); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }

@@ -392,8 +392,8 @@ int launch_jacobi(const helm_ctx* c, const Op& op, float2* u_out, const float2* 
             auto launch = [&](int i) {
                 const int bx = SHAPES[i][0], by = SHAPES[i][1];
                 const dim3 g((nx / 2 + bx - 1) / bx, (nz + by - 1) / by, nb);
-                jacobi_fine2_kernel<<<g, dim3(bx, by), 0, c->stream>>>(op, u_out, u_in, f, c->opt.jacobi_w, nx, nz,
-                                                                        mask, tl);
+                { jacobi_fine2_kernel<<<g, dim3(bx, by), 0, c->stream>>>(op, u_out, u_in, f, c->opt.jacobi_w, nx, nz,
+                                                                        mask, tl); count_launch(); }
             };
             bool tune = false;
             int i = shape_of(0, nx, nz, &tune);
@@ -408,8 +408,8 @@ int launch_jacobi(const helm_ctx* c, const Op& op, float2* u_out, const float2* 
         auto launch = [&](int i) {
             const int bx = SHAPES[i][0], by = SHAPES[i][1];
             const dim3 g((nx + bx - 1) / bx, (nz + by - 1) / by, (nb + 1) / 2);
-            jacobi_c9_pair_kernel<<<g, dim3(bx, by), 0, c->stream>>>(op, u_out, u_in, f, c->opt.jacobi_w, nx, nz, nb,
-                                                                      mask, tl);
+            { jacobi_c9_pair_kernel<<<g, dim3(bx, by), 0, c->stream>>>(op, u_out, u_in, f, c->opt.jacobi_w, nx, nz, nb,
+                                                                      mask, tl); count_launch(); }
         };
         bool tune = false;
         int i = shape_of(1, nx, nz, &tune);
@@ -418,10 +418,10 @@ int launch_jacobi(const helm_ctx* c, const Op& op, float2* u_out, const float2* 
         HELM_CK(cudaGetLastError());
         return HELM_OK;
     }
-    jacobi_kernel<Op><<<grid2(nx, nz, nb), dim3(32, 8), 0, c->stream>>>(
+    { jacobi_kernel<Op><<<grid2(nx, nz, nb), dim3(32, 8), 0, c->stream>>>(
         op, u_out, u_in, f, c->opt.jacobi_w, nx, nz, mask,
         tally(c, std::is_same<Op, OpFine5>::value ? K_JACOBI_FINE : K_JACOBI_COARSE,
-              (u_in ? 24ull : 16ull) * nx * nz));
+              (u_in ? 24ull : 16ull) * nx * nz)); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -434,10 +434,10 @@ template <class Op>
 int launch_restrict_residual(const helm_ctx* c, const Op& op, float2* rc, const float2* u, const float2* f,
                              int nx, int nz, int nb, const int* mask) {
     LaunchScope scope(c, (std::is_same<Op, OpFine5>::value ? K_RESTRICT_FINE : K_RESTRICT_COARSE));
-    restrict_residual_tiled_kernel<Op><<<grid2(nx / 2, nz / 2, nb), dim3(32, 8), 0, c->stream>>>(
+    { restrict_residual_tiled_kernel<Op><<<grid2(nx / 2, nz / 2, nb), dim3(32, 8), 0, c->stream>>>(
         op, rc, u, f, nx, nz, mask,
         tally(c, std::is_same<Op, OpFine5>::value ? K_RESTRICT_FINE : K_RESTRICT_COARSE,
-              (u ? 16ull : 8ull) * nx * nz + 2ull * nx * nz));
+              (u ? 16ull : 8ull) * nx * nz + 2ull * nx * nz)); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -449,13 +449,13 @@ template int launch_restrict_residual<OpC9>(const helm_ctx*, const OpC9&, float2
 int launch_prolong_add(const helm_ctx* c, float2* u, const float2* ec, int nx, int nz, int nb, const int* mask) {
     LaunchScope scope(c, K_PROLONG);
     if (nx % 2 == 0) {
-        prolong_add2_kernel<<<grid2(nx / 2, nz, nb), dim3(32, 8), 0, c->stream>>>(
-            u, ec, nx, nz, mask, tally(c, K_PROLONG, 18ull * nx * nz));
+        { prolong_add2_kernel<<<grid2(nx / 2, nz, nb), dim3(32, 8), 0, c->stream>>>(
+            u, ec, nx, nz, mask, tally(c, K_PROLONG, 18ull * nx * nz)); count_launch(); }
         HELM_CK(cudaGetLastError());
         return HELM_OK;
     }
-    prolong_add_kernel<<<grid2(nx, nz, nb), dim3(32, 8), 0, c->stream>>>(u, ec, nx, nz, mask,
-                                                                          tally(c, K_PROLONG, 18ull * nx * nz));
+    { prolong_add_kernel<<<grid2(nx, nz, nb), dim3(32, 8), 0, c->stream>>>(u, ec, nx, nz, mask,
+                                                                          tally(c, K_PROLONG, 18ull * nx * nz)); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -464,7 +464,7 @@ int launch_copy_masked(const helm_ctx* c, float2* dst, const float2* src, size_t
     size_t blocks = (n + 255) / 256;
     if (blocks > 148) blocks = 148;
     LaunchScope scope(c, K_COPY);
-    copy_masked_kernel<<<dim3((unsigned)blocks, nb), 256, 0, c->stream>>>(dst, src, n, mask, tally(c, K_COPY, 16ull * n));
+    { copy_masked_kernel<<<dim3((unsigned)blocks, nb), 256, 0, c->stream>>>(dst, src, n, mask, tally(c, K_COPY, 16ull * n)); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -476,12 +476,12 @@ int launch_galerkin(helm_ctx* c, int level) {
         dim3 grid((F.nx / 2 + 31) / 32, (F.nz / 2 + 7) / 8);
         if (level == 1) {
             LaunchScope scope(c, K_GALERKIN);
-            galerkin_kernel<OpFine5><<<grid, dim3(32, 8), 0, c->stream>>>(fine_op(c, 1), f, c->lev[level].coef9,
-                                                                         F.nx, F.nz);
+            { galerkin_kernel<OpFine5><<<grid, dim3(32, 8), 0, c->stream>>>(fine_op(c, 1), f, c->lev[level].coef9,
+                                                                         F.nx, F.nz); count_launch(); }
         } else {
             LaunchScope scope(c, K_GALERKIN);
-            galerkin_kernel<OpC9><<<grid, dim3(32, 8), 0, c->stream>>>(coarse_op(c, level - 1), f,
-                                                                      c->lev[level].coef9, F.nx, F.nz);
+            { galerkin_kernel<OpC9><<<grid, dim3(32, 8), 0, c->stream>>>(coarse_op(c, level - 1), f,
+                                                                      c->lev[level].coef9, F.nx, F.nz); count_launch(); }
         }
         HELM_CK(cudaGetLastError());
     }

@@ -162,9 +162,9 @@ extern "C" int helm_residual_noalloc(const float* kappa, const float* gamma, int
     // the counters must start at zero; the array keeps whatever the last call left
     HELM_CK(cudaMemsetAsync(counters, 0, (size_t)nrhs * sizeof(unsigned), st));
     dim3 grid((nx + TILE_X - 1) / TILE_X, (nz + TILE_Y * ROWS - 1) / (TILE_Y * ROWS), nrhs);
-    residual_noalloc_kernel<<<grid, dim3(TILE_X, TILE_Y), 0, st>>>(
+    { residual_noalloc_kernel<<<grid, dim3(TILE_X, TILE_Y), 0, st>>>(
         kappa, gamma, nx, nz, 1.0 / ((double)hx * hx), 1.0 / ((double)hz * hz), omega_rhs, (const float2*)rhs,
-        (const double2*)x, (float2*)r, rel_res, partials, counters);
+        (const double2*)x, (float2*)r, rel_res, partials, counters); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }

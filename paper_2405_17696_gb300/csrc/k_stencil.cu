@@ -151,8 +151,8 @@ __global__ void zero_x_kernel(OuterState os, double2* x, size_t n) {
 
 int launch_apply_fine(const helm_ctx* c, const OpFine5& op, const float2* x, float2* y, int nb, const int* mask) {
     LaunchScope scope(c, K_APPLY);
-    apply_fine_kernel<<<dim3((op.nx + 31) / 32, (op.nz + 7) / 8, nb), dim3(32, 8), 0, c->stream>>>(op, x, y, mask,
-                                                                                               tally(c, K_APPLY, 16ull * op.nx * op.nz));
+    { apply_fine_kernel<<<dim3((op.nx + 31) / 32, (op.nz + 7) / 8, nb), dim3(32, 8), 0, c->stream>>>(op, x, y, mask,
+                                                                                               tally(c, K_APPLY, 16ull * op.nx * op.nz)); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -161,10 +161,10 @@ int launch_residual64(helm_ctx* c, const double2* x, const float2* b, float2* r,
     OpFine5 op = fine_op(c, 0);
     dim3 grid((c->nx + TILE_X - 1) / TILE_X, (c->nz + TILE_Y * ROWS - 1) / (TILE_Y * ROWS), nb);
     LaunchScope scope(c, K_RESIDUAL64);
-    residual64_kernel<<<grid, dim3(TILE_X, TILE_Y), 0, c->stream>>>(op, x, b, r, conj_b, first,
+    { residual64_kernel<<<grid, dim3(TILE_X, TILE_Y), 0, c->stream>>>(op, x, b, r, conj_b, first,
                                                                     1.0 / ((double)c->hx * c->hx),
                                                                     1.0 / ((double)c->hz * c->hz), c->outer,
-                                                                    tally(c, K_RESIDUAL64, 32ull * c->nx * c->nz));
+                                                                    tally(c, K_RESIDUAL64, 32ull * c->nx * c->nz)); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
@@ -172,29 +172,29 @@ int launch_residual64(helm_ctx* c, const double2* x, const float2* b, float2* r,
 int launch_conj64(helm_ctx* c, double2* x, int nb) {
     size_t n = (size_t)nb * npts(c);
     LaunchScope scope(c, K_MISC);
-    conj64_kernel<<<1184, 256, 0, c->stream>>>(x, n);
+    { conj64_kernel<<<1184, 256, 0, c->stream>>>(x, n); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
 
 int launch_outer_init(helm_ctx* c, int nb) {
     LaunchScope scope(c, K_MISC);
-    outer_init_kernel<<<(nb + 127) / 128, 128, 0, c->stream>>>(c->outer, c->fine, nb);
+    { outer_init_kernel<<<(nb + 127) / 128, 128, 0, c->stream>>>(c->outer, c->fine, nb); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
 
 int launch_zero_x(helm_ctx* c, double2* x, int nb) {
     LaunchScope scope(c, K_MISC);
-    zero_x_kernel<<<dim3(64, nb), 256, 0, c->stream>>>(c->outer, x, npts(c));
+    { zero_x_kernel<<<dim3(64, nb), 256, 0, c->stream>>>(c->outer, x, npts(c)); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }
 
 int launch_restart_check_dev(helm_ctx* c, int nb, double tol, int* n_active_dev) {
     LaunchScope scope(c, K_RESTART);
-    restart_check_kernel<<<(nb + 127) / 128, 128, 0, c->stream>>>(c->outer, c->fine, nb, tol, c->opt.max_iter, 0.7,
-                                                                  n_active_dev);
+    { restart_check_kernel<<<(nb + 127) / 128, 128, 0, c->stream>>>(c->outer, c->fine, nb, tol, c->opt.max_iter, 0.7,
+                                                                  n_active_dev); count_launch(); }
     HELM_CK(cudaGetLastError());
     return HELM_OK;
 }

@@ -329,7 +329,7 @@ int launch_wg_mode(const CUtensorMap& tx0, const CUtensorMap& tx1, const CUtenso
     });
     // at least 116 KB, so that one CTA per SM holds the TMEM (up to all 512 columns)
     const size_t smem = std::max<size_t>((size_t)g.ns * g.stage + g.slack, 116 * 1024);
-    wgrad_tc_kernel<MODE><<<dim3((unsigned)g.splits, (unsigned)g.ngroups), WG_NT, smem, st>>>(tx0, tx1, tg, a, g);
+    { wgrad_tc_kernel<MODE><<<dim3((unsigned)g.splits, (unsigned)g.ngroups), WG_NT, smem, st>>>(tx0, tx1, tg, a, g); count_launch(); }
     return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
 }
 
@@ -415,16 +415,16 @@ int launch_wgrad_tc(const WgradArgs& a, cudaStream_t st) {
     }
     if (s != HELM_OK) return s;
     const long long n = 9ll * g.cx * 8 * a.npad;
-    wgrad_reduce_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(
-        a.partials, g.splits, g.cx * 8, a.npad, a.cin, a.cout, a.dW);
+    { wgrad_reduce_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(
+        a.partials, g.splits, g.cx * 8, a.npad, a.cin, a.cout, a.dW); count_launch(); }
     if (cudaGetLastError() != cudaSuccess) return HELM_ECUDA;
     // bias: per-segment sums of g, then their sum in a fixed order
     const long long hw = (long long)a.hout * a.wout, npix = (long long)a.nb * hw;
     const int nseg = (int)std::min<long long>(a.max_bias_segments, std::max<long long>(1, (npix + 4095) / 4096));
     const long long seg_len = (npix + nseg - 1) / nseg;
-    bias_partial_kernel<<<dim3((unsigned)nseg, (unsigned)(a.npad / 8)), 256, 0, st>>>(a.g, a.npad, hw, npix, seg_len,
-                                                                                     a.bias_partials);
-    bias_reduce_kernel<<<1, 128, 0, st>>>(a.bias_partials, nseg, a.npad, a.cout, a.db);
+    { bias_partial_kernel<<<dim3((unsigned)nseg, (unsigned)(a.npad / 8)), 256, 0, st>>>(a.g, a.npad, hw, npix, seg_len,
+                                                                                     a.bias_partials); count_launch(); }
+    { bias_reduce_kernel<<<1, 128, 0, st>>>(a.bias_partials, nseg, a.npad, a.cout, a.db); count_launch(); }
     return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
 }
 
