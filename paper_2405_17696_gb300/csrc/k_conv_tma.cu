@@ -76,15 +76,16 @@ namespace helm {
 
 namespace {
 
-// Epilogue warps: two warpgroups drain TMEM (alternate M blocks); mode 6, four warpgroups
-// (alternate output rows), one CTA per SM.  + a TMA-producer warp and an MMA-issuer warp.
-__host__ __device__ constexpr int epi_warps(int mode) { return mode == 6 ? 16 : 8; }
+// Epilogue warps: two warpgroups drain TMEM (alternate M blocks; mode 6, alternate output
+// rows).  + a TMA-producer warp and an MMA-issuer warp.
+__host__ __device__ constexpr int epi_warps(int) { return 8; }
 __host__ __device__ constexpr int threads_of(int mode) { return 32 * epi_warps(mode) + 64; }
 constexpr int MAX_NS = 6;                       // stages (one 16-channel group of one tile each)
 constexpr int MAX_SLOTS = 10;                   // TMEM slot barriers: mode 4 uses 4, mode 6 up to 10
 constexpr int NSLOT4 = 4;                       // TMEM accumulator slots of mode 4 (two buffers otherwise)
 constexpr int N3_PX = 96;                       // mode 4: staged pixels per M block (16 groups x 6)
-constexpr size_t RING_BUDGET_RT = 200 * 1024;   // mode 6: one CTA per SM (all 512 TMEM columns)
+constexpr size_t RING_BUDGET_RT16 = 100 * 1024;  // mode 6, 16 channels: two CTAs per SM (256 TMEM columns each)
+constexpr size_t RING_BUDGET_RT32 = 200 * 1024;  // mode 6, 32 channels: one CTA per SM (512 TMEM columns)
 constexpr int ROWS_RT_MAX = 32;                 // mode 6: output rows per tile at most
 constexpr int RT_CHUNK = 4;                     // mode 6: staged rows per commit at most (a commit
                                                 // costs about as much as several MMAs)
@@ -347,33 +348,34 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
             // group and column shift dx one MMA with N = 3 npad (B rows (dy, o)).  Rows are
             // committed in chunks of g.chunk (and at the tile's last row): commit id
             // k * ceil(mb / chunk) + b / chunk on tfull[id % MAX_SLOTS].  A slot is
-            // refilled once the epilogue released it.
-            const uint32_t ncol = 3u * (uint32_t)a.npad;
+            // refilled once the epilogue released it.  Slot, use and commit indices advance
+            // as counters: a 64-bit division per row cost more than the row's MMAs.
+            const uint32_t ncol = (uint32_t)g.slot_cols;
             const uint32_t idesc6 = tc::idesc_bf16_f32(128, 3 * a.npad);
             const uint64_t bdesc6 = tc::smem_desc(0u, 3u * wplane, 128);   // K halves 3 npad rows apart
             const uint32_t b6_lo = (uint32_t)bdesc6, b6_hi = (uint32_t)(bdesc6 >> 32);
             const uint32_t dx_b16 = (6u * wplane) >> 4;                    // B of one column shift
-            long long jb = 0, cid = 0;
+            int slot = 0, wraps = 0, cslot = 0;
+            uint32_t a16s[MAX_NS];
             for (int k = 0; k < ntiles && ok; ++k) {
                 for (int gi = 0; gi < G; ++gi) {
                     const long long js = j + gi;
-                    const bool f_ok = wait_bar(&full[js % g.ns], (uint32_t)((js / g.ns) & 1), abort_v, 32);
+                    const int s = (int)(js % g.ns);
+                    const bool f_ok = wait_bar(&full[s], (uint32_t)((js / g.ns) & 1), abort_v, 32);
                     if (!__all_sync(0xffffffffu, f_ok)) { ok = false; break; }
+                    a16s[gi] = (tc::smem_u32(smem + (size_t)s * g.stage) & 0x3FFFFu) >> 4;
                 }
                 if (!ok) break;
                 tc::tc_fence_after_sync();
-                for (int b = 0; b < g.mb; ++b, ++jb) {
-                    const int slot = (int)(jb % g.nslot);
-                    const long long use = jb / g.nslot;
-                    const bool t_ok = use == 0 || wait_bar(&tempty[slot], (uint32_t)((use - 1) & 1), abort_v, 32);
+                int cb = 0;
+                for (int b = 0; b < g.mb; ++b) {
+                    const bool t_ok = wraps == 0 || wait_bar(&tempty[slot], (uint32_t)((wraps - 1) & 1), abort_v, 32);
                     if (!__all_sync(0xffffffffu, t_ok)) { ok = false; break; }
                     tc::tc_fence_after_sync();
                     const uint32_t d = tmem + (uint32_t)slot * ncol;
                     for (int gi = 0; gi < G; ++gi) {
-                        const int s = (int)((j + gi) % g.ns);
-                        const uint32_t a16 = (tc::smem_u32(smem + (size_t)s * g.stage) & 0x3FFFFu) >> 4;
-                        const uint32_t a_b = a_lo0 + a16 + (uint32_t)(b * g.pw);
-                        const uint32_t b_s = b6_lo + a16 + ((uint32_t)wofs >> 4);
+                        const uint32_t a_b = a_lo0 + a16s[gi] + (uint32_t)(b * g.pw);
+                        const uint32_t b_s = b6_lo + a16s[gi] + ((uint32_t)wofs >> 4);
 #pragma unroll
                         for (int dx = 0; dx < 3; ++dx) {
                             if (leader) {
@@ -383,10 +385,15 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
                             }
                         }
                     }
-                    if ((b + 1) % g.chunk == 0 || b == g.mb - 1) {
+                    if (++slot == g.nslot) {
+                        slot = 0;
+                        ++wraps;
+                    }
+                    if (++cb == g.chunk || b == g.mb - 1) {
                         __syncwarp();
-                        if (leader) tc::mma_commit(&tfull[cid % MAX_SLOTS]);
-                        ++cid;
+                        if (leader) tc::mma_commit(&tfull[cslot]);
+                        cb = 0;
+                        if (++cslot == MAX_SLOTS) cslot = 0;
                     }
                 }
                 if (!ok) break;
@@ -528,13 +535,13 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
             // Output row m of a tile (warpgroup m % nwg) sums three staged-row slots in this
             // thread's lane (= column), all channels.  The commit that covers the newest of
             // the three rows implies the older two.  Every slot takes 3 x 128 arrivals per
-            // fill: one from each output row
-            // that reads it, and for the tile's first and last two staged rows (read by fewer
-            // rows) the extra arrivals come from the tile's first and last output rows.
+            // fill: one from each output row that reads it, and for the tile's first and
+            // last two staged rows (read by fewer rows) the extra arrivals come from the
+            // tile's first and last output rows.  Indices are kept as 32-bit counters.
             const int nwg = g.nwg;
-            const uint32_t ncol = 3u * (uint32_t)a.npad;
+            const uint32_t ncol = (uint32_t)g.slot_cols;
             const int cpt = (g.mb + g.chunk - 1) / g.chunk;   // commits per tile
-            long long jb = 0;
+            int jslot = 0;                                    // slot of the tile's staged row 0
             bool ok = true;
             for (int k = 0; k < ntiles && ok; ++k) {
                 int b, xs, ys;
@@ -542,16 +549,17 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
                 const size_t img_base = (size_t)b * (size_t)(a.npad >> 3) * (size_t)hw_out * 8;
                 const int R = g.rows;
                 for (int m = wg < nwg ? wg : R; m < R; m += nwg) {
-                    const long long newest = jb + m + 2;
-                    const long long cid = (long long)k * cpt + (m + 2) / g.chunk;
+                    const int cid = k * cpt + (m + 2) / g.chunk;
                     if (!wait_bar(&tfull[cid % MAX_SLOTS], (uint32_t)((cid / MAX_SLOTS) & 1), abort_v, 64)) {
                         *abort_v = 1;
                         ok = false;
                         break;
                     }
                     tc::tc_fence_after_sync();
-                    const uint32_t s0 = (uint32_t)((jb + m) % g.nslot), s1 = (uint32_t)((jb + m + 1) % g.nslot),
-                                   s2 = (uint32_t)(newest % g.nslot);
+                    int s0 = jslot + m;
+                    while (s0 >= g.nslot) s0 -= g.nslot;
+                    const int s1 = s0 + 1 == g.nslot ? 0 : s0 + 1;
+                    const int s2 = s1 + 1 == g.nslot ? 0 : s1 + 1;
                     const int ox = xs + row, oy = ys + m;
                     const bool valid = row < g.tw && ox < a.wout && oy < a.hout;
                     const long long pix = (long long)oy * a.wout + ox;
@@ -559,9 +567,9 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
                     const long long p = (long long)b * hw_out + pix;
                     for (int c0 = 0; c0 < a.npad; c0 += 16) {
                         float v0[16], v1[16], v2[16];
-                        tc::tmem_ld16x3(lane_base + s0 * ncol + (uint32_t)c0,
-                                        lane_base + s1 * ncol + (uint32_t)(a.npad + c0),
-                                        lane_base + s2 * ncol + (uint32_t)(2 * a.npad + c0), v0, v1, v2);
+                        tc::tmem_ld16x3(lane_base + (uint32_t)s0 * ncol + (uint32_t)c0,
+                                        lane_base + (uint32_t)s1 * ncol + (uint32_t)(a.npad + c0),
+                                        lane_base + (uint32_t)s2 * ncol + (uint32_t)(2 * a.npad + c0), v0, v1, v2);
                         if (c0 + 16 >= a.npad) {
                             // this thread's reads of the three slots are complete
                             tc::tc_fence_before_sync();
@@ -584,7 +592,8 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
                         if (valid) segment(v0, c0, ob, p);
                     }
                 }
-                jb += g.mb;
+                jslot += g.mb;
+                while (jslot >= g.nslot) jslot -= g.nslot;
             }
         } else if constexpr (MODE == 4) {
             // warpgroup wg drains the slots of parity wg (the slot count is even); row
@@ -844,11 +853,15 @@ Geometry plan(const ConvArgs& a, const TileCfg& t) {
         g.tw = (W + ntx - 1) / ntx;
         g.pw = g.tw + 2;
         g.wbytes = 9 * 2 * a.npad * 16;
+        // 16 channels: 5 slots of 48 columns in 256 (two CTAs per SM, so that two MMA streams
+        // overlap); 32 channels: 5 slots of 96 in 512 (one CTA per SM)
         g.slot_cols = 3 * a.npad;
-        g.nslot = std::min(MAX_SLOTS, 512 / g.slot_cols);
+        g.tmem_cols = a.npad == 16 ? 256 : 512;
+        g.nslot = std::min(MAX_SLOTS, (int)g.tmem_cols / g.slot_cols);
         int rmax = std::min(H, ROWS_RT_MAX);
         if (t.rows_cap > 0 && rmax > t.rows_cap) rmax = t.rows_cap;
-        const size_t ring_budget = t.ring_kb > 0 ? (size_t)t.ring_kb * 1024 : RING_BUDGET_RT;
+        const size_t ring_budget = t.ring_kb > 0 ? (size_t)t.ring_kb * 1024
+                                   : (a.npad == 16 ? RING_BUDGET_RT16 : RING_BUDGET_RT32);
         // the tallest tile whose stages fit a ring holding every group of a tile and one more
         g.rows = 0;
         for (int rows = rmax; rows >= 1; --rows) {
@@ -875,11 +888,10 @@ Geometry plan(const ConvArgs& a, const TileCfg& t) {
         // tile, i.e. at most (2 nwg + 1) / chunk + 2 commits, fewer than MAX_SLOTS.  A chunk
         // of rows can complete only if its last row's slot is released by output rows that
         // wait on earlier commits: chunk <= nslot - 2.
-        g.nwg = 4;
+        g.nwg = epi_warps(6) / 4;
         while (g.nwg > 1 && g.nwg > g.rows) g.nwg >>= 1;
         g.chunk = std::min(RT_CHUNK, g.nslot - 2);
         g.acc_cols = 0;
-        g.tmem_cols = 512;
         g.tiles_x = (W + g.tw - 1) / g.tw;
         g.tiles_y = (H + g.rows - 1) / g.rows;
         g.tx = (uint32_t)(2 * (g.rows + 2) * g.pw * 16 + g.wbytes);

@@ -264,7 +264,8 @@ __global__ void wgrad_reduce_kernel(const float* __restrict__ part, int splits, 
         const int t = (int)(r / Cpad), ci = (int)(r % Cpad);
         if (co >= cout || ci >= cin) continue;
         float acc = 0.0f;
-        for (int s = 0; s < splits; ++s) acc += part[(size_t)s * per + i];
+#pragma unroll 8
+        for (int s = 0; s < splits; ++s) acc += part[(size_t)s * per + i];   // loads in flight, sum in order
         dW[((size_t)co * 9 + t) * cin + ci] += acc;
     }
 }
@@ -297,13 +298,17 @@ __global__ void __launch_bounds__(256) bias_partial_kernel(const __nv_bfloat16* 
     if (threadIdx.x < 8) bpart[(size_t)seg * npad + 8 * c8 + threadIdx.x] = red[0][threadIdx.x];
 }
 
-// db[co] += sum over segments (in order) of bpart[seg][co]
+// db[co] += sum over segments of bpart[seg][co], one warp per channel (grid = cout): lane l
+// adds segments l, l + 32, ... in order, then a fixed shuffle tree adds the lanes (FP64)
 __global__ void bias_reduce_kernel(const float* __restrict__ bpart, int nseg, int npad, int cout, float* __restrict__ db) {
-    const int co = threadIdx.x;
+    const int co = blockIdx.x, lane = threadIdx.x;
     if (co >= cout) return;
     double acc = 0.0;
-    for (int s = 0; s < nseg; ++s) acc += (double)bpart[(size_t)s * npad + co];
-    db[co] += (float)acc;
+#pragma unroll 4
+    for (int s = lane; s < nseg; s += 32) acc += (double)bpart[(size_t)s * npad + co];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) db[co] += (float)acc;
 }
 
 int sm_count_wg() {
@@ -424,7 +429,7 @@ int launch_wgrad_tc(const WgradArgs& a, cudaStream_t st) {
     const long long seg_len = (npix + nseg - 1) / nseg;
     { bias_partial_kernel<<<dim3((unsigned)nseg, (unsigned)(a.npad / 8)), 256, 0, st>>>(a.g, a.npad, hw, npix, seg_len,
                                                                                      a.bias_partials); count_launch(); }
-    { bias_reduce_kernel<<<1, 128, 0, st>>>(a.bias_partials, nseg, a.npad, a.cout, a.db); count_launch(); }
+    { bias_reduce_kernel<<<(unsigned)a.cout, 32, 0, st>>>(a.bias_partials, nseg, a.npad, a.cout, a.db); count_launch(); }
     return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_ECUDA;
 }
 
