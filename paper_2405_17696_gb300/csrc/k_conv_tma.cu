@@ -226,15 +226,19 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
         // ---------------- TMA producer ----------------
         const uint32_t wplane = (uint32_t)a.npad * 16;
         long long j = 0;
+        int s = 0, wraps = 0;   // j % ns and j / ns as counters
         bool ok = true;
         for (int k = 0; k < ntiles && ok; ++k) {
             int b, xs, ys;
             tile_coords(k, b, xs, ys);
             const int b1 = a.c1 ? (a.x1_map ? __ldg(a.x1_map + b) : (a.x1_bcast ? 0 : b)) : 0;
             for (int gi = 0; gi < G; ++gi, ++j) {
-                const int s = (int)(j % g.ns);
-                const long long use = j / g.ns;
-                if (use > 0 && !wait_bar(&empty[s], (uint32_t)((use - 1) & 1), abort_v, 32)) { ok = false; break; }
+                if (gi > 0 || k > 0)
+                    if (++s == g.ns) {
+                        s = 0;
+                        ++wraps;
+                    }
+                if (wraps > 0 && !wait_bar(&empty[s], (uint32_t)((wraps - 1) & 1), abort_v, 32)) { ok = false; break; }
                 unsigned char* st = smem + (size_t)s * g.stage;
                 tc::mbar_arrive_expect_tx(&full[s], g.tx);
                 {
@@ -304,25 +308,25 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
             const uint32_t a4_lo = (uint32_t)adesc4, a4_hi = (uint32_t)(adesc4 >> 32);
             const uint32_t b4_lo = (uint32_t)bdesc4, b4_hi = (uint32_t)(bdesc4 >> 32);
             const uint32_t row_b16 = (6u * wplane) >> 4;   // B of one tap row (2 halves x 3 dx)
-            long long jb = 0;
+            int slot = 0, wraps = 0;                         // counters, no divisions per M block
+            uint32_t a16s[MAX_NS];
             for (int k = 0; k < ntiles && ok; ++k) {
                 for (int gi = 0; gi < G; ++gi) {
                     const long long js = j + gi;
-                    const bool f_ok = wait_bar(&full[js % g.ns], (uint32_t)((js / g.ns) & 1), abort_v, 32);
+                    const int s = (int)(js % g.ns);
+                    const bool f_ok = wait_bar(&full[s], (uint32_t)((js / g.ns) & 1), abort_v, 32);
                     if (!__all_sync(0xffffffffu, f_ok)) { ok = false; break; }
+                    a16s[gi] = (tc::smem_u32(smem + (size_t)s * g.stage) & 0x3FFFFu) >> 4;
                 }
                 if (!ok) break;
                 tc::tc_fence_after_sync();
-                for (int m = 0; m < g.mb; ++m, ++jb) {
-                    const int slot = (int)(jb % g.nslot);
-                    const long long use = jb / g.nslot;
-                    const bool t_ok = use == 0 || wait_bar(&tempty[slot], (uint32_t)((use - 1) & 1), abort_v, 32);
+                for (int m = 0; m < g.mb; ++m) {
+                    const bool t_ok = wraps == 0 || wait_bar(&tempty[slot], (uint32_t)((wraps - 1) & 1), abort_v, 32);
                     if (!__all_sync(0xffffffffu, t_ok)) { ok = false; break; }
                     tc::tc_fence_after_sync();
                     const uint32_t d = tmem + (uint32_t)(slot * g.slot_cols);
                     for (int gi = 0; gi < G; ++gi) {
-                        const int s = (int)((j + gi) % g.ns);
-                        const uint32_t a16 = (tc::smem_u32(smem + (size_t)s * g.stage) & 0x3FFFFu) >> 4;
+                        const uint32_t a16 = a16s[gi];
                         const uint32_t a_m = a4_lo + a16 + (uint32_t)(m * N3_PX);
                         const uint32_t b_s = b4_lo + a16 + ((uint32_t)wofs >> 4);
 #pragma unroll
@@ -336,6 +340,10 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
                     }
                     __syncwarp();
                     if (leader) tc::mma_commit(&tfull[slot]);
+                    if (++slot == g.nslot) {
+                        slot = 0;
+                        ++wraps;
+                    }
                 }
                 if (!ok) break;
                 __syncwarp();
@@ -403,6 +411,7 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
                 j += G;
             }
         } else {
+            int s = 0, wraps = 0;   // j % ns and j / ns as counters
             for (int k = 0; k < ntiles && ok; ++k) {
                 const int acc = k & 1;
                 const int ause = k >> 1;
@@ -412,8 +421,12 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
                 tc::tc_fence_after_sync();
                 const uint32_t dbase = tmem + (uint32_t)acc * g.acc_cols;
                 for (int gi = 0; gi < G; ++gi, ++j) {
-                    const int s = (int)(j % g.ns);
-                    const bool f_ok = wait_bar(&full[s], (uint32_t)((j / g.ns) & 1), abort_v, 32);
+                    if (gi > 0 || k > 0)
+                        if (++s == g.ns) {
+                            s = 0;
+                            ++wraps;
+                        }
+                    const bool f_ok = wait_bar(&full[s], (uint32_t)(wraps & 1), abort_v, 32);
                     if (!__all_sync(0xffffffffu, f_ok)) { ok = false; break; }
                     tc::tc_fence_after_sync();
                     const uint32_t a16 = (tc::smem_u32(smem + (size_t)s * g.stage) & 0x3FFFFu) >> 4;
@@ -599,16 +612,21 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
             // warpgroup wg drains the slots of parity wg (the slot count is even); row
             // (group gr, row i) of an M block is staged pixel 96 m + 6 gr + i
             const int gr = row >> 3, i8 = row & 7;
-            long long jb = 0;
+            int slot = 0, wraps = 0;
             bool ok = true;
             for (int k = 0; k < ntiles && ok; ++k) {
                 int b, xs, ys;
                 tile_coords(k, b, xs, ys);
                 const size_t img_base = (size_t)b * (size_t)(a.npad >> 3) * (size_t)hw_out * 8;
-                for (int m = 0; m < g.mb; ++m, ++jb) {
-                    const int slot = (int)(jb % g.nslot);
-                    if ((slot & 1) != wg) continue;
-                    if (!wait_bar(&tfull[slot], (uint32_t)((jb / g.nslot) & 1), abort_v, 128)) {
+                for (int m = 0; m < g.mb; ++m) {
+                    const int sl = slot;
+                    const uint32_t par = (uint32_t)(wraps & 1);
+                    if (++slot == g.nslot) {
+                        slot = 0;
+                        ++wraps;
+                    }
+                    if ((sl & 1) != wg) continue;
+                    if (!wait_bar(&tfull[sl], par, abort_v, 128)) {
                         *abort_v = 1;
                         ok = false;
                         break;
@@ -621,12 +639,12 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
                     const long long pix = (long long)oy * a.wout + ox;
                     const size_t ob = img_base + (size_t)pix * 8;
                     const long long p = (long long)b * hw_out + pix;
-                    const uint32_t tcol = lane_base + (uint32_t)(slot * g.slot_cols);
+                    const uint32_t tcol = lane_base + (uint32_t)(sl * g.slot_cols);
                     // columns 0-15: dx = -1 (this row); 16-31: dx = 0 (row + 1); 32-47: dx = +1 (row + 2)
                     float d[48];
                     tc::tmem_ld48(tcol, d);
                     tc::tc_fence_before_sync();
-                    tc::mbar_arrive(&tempty[slot]);   // the slot's TMEM reads are done
+                    tc::mbar_arrive(&tempty[sl]);   // the slot's TMEM reads are done
                     float v[16];
 #pragma unroll
                     for (int c = 0; c < 16; ++c)
