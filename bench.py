@@ -471,7 +471,7 @@ def run_retrain_series(args, native, dev, stream, world, rank):
                 if label == "cnn_retrained" and retrain_steps > 0:
                     t0 = time.perf_counter()
                     RT.retrain(native, net, ctx, cfg=RT.RetrainConfig(
-                        initial_size=128, data_epochs=3, epochs=1 << 20, batch=16, lr=1e-4,
+                        initial_size=128, data_epochs=3, epochs=1 << 20, batch=16, lr=args.retrain_lr,
                         max_steps=retrain_steps, relative_loss=True, warmup_steps=50,
                         seed=media.SEED_DATAGEN + 100 * t))
                     torch.cuda.synchronize(dev)
@@ -491,7 +491,7 @@ def run_retrain_series(args, native, dev, stream, world, rank):
             "n_gpus": world, "data": "synthetic",
             "config": {"workload": f"retraining_series_{w.nx}x{w.nz}_{nb}rhs_9media", "freq_hz": 8.0,
                        "media": "m_t = (1 - t/8) G_10(m_true) + (t/8) m_true, t = 0..8 (seeded 12-layer m_true)",
-                       "retrain_steps_per_medium": retrain_steps,
+                       "retrain_steps_per_medium": retrain_steps, "retrain_lr": args.retrain_lr,
                        "initial_weights": os.path.relpath(args.checkpoint, ROOT)},
             "totals": tot, "retrain_seconds": t_retrain, "per_medium": rows}
     if rank == 0:
@@ -872,6 +872,8 @@ def main():
                          "the checkpoint (default: the checkpoint when it exists, else 400 steps)")
     ap.add_argument("--checkpoint", default=CHECKPOINT,
                     help="initial weights (cnn_load) for the cnn workload")
+    ap.add_argument("--retrain-lr", type=float, default=1e-4,
+                    help="retrain workload: Adam learning rate of the Alg. 2 steps on each medium")
     ap.add_argument("--retrain-steps", type=int, default=0,
                     help="Alg. 2 steps on the benchmark medium after loading the checkpoint (set-up, untimed); "
                          "the retraining series (--workload retrain) uses it per medium (default there: 200)")

@@ -55,13 +55,15 @@ __global__ void mask_to_bf16_kernel(const float* __restrict__ G, int cg, const _
 }
 
 // The same for cg == cpad, a multiple of 8: one thread per (pixel, 8-channel chunk) with
-// 16-byte loads and stores (grid.y = chunk).
+// 16-byte loads and stores (grid.y = chunk, grid.z = image: no division per element).
 __global__ void mask_to_bf16_vec_kernel(const float* __restrict__ G, const __nv_bfloat16* __restrict__ y, int cy,
-                                        int cpad, long long n, long long hw, __nv_bfloat16* __restrict__ out,
+                                        int cpad, long long hw, __nv_bfloat16* __restrict__ out,
                                         float* __restrict__ res_grad) {
     const int c8 = blockIdx.y;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        const long long b = p / hw, pix = p - b * hw;
+    const long long b = blockIdx.z;
+    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < hw;
+         pix += (long long)gridDim.x * blockDim.x) {
+        const long long p = b * hw + pix;
         const float4* g4 = reinterpret_cast<const float4*>(G + p * cpad + 8 * c8);
         float4 a = g4[0], c = g4[1];
         float v[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
@@ -541,9 +543,13 @@ class Backward {
                 LaunchScope scope(c_, K_CNN_IO);
                 const __nv_bfloat16* ymask = L.relu ? (const __nv_bfloat16*)op.y : nullptr;
                 if (cg == L.npad && cg % 8 == 0)
-                    { mask_to_bf16_vec_kernel<<<dim3((unsigned)std::min<long long>((nout + 255) / 256, 1184),
-                                                   (unsigned)(cg / 8)), 256, 0, st_>>>(
-                        Gy, ymask, L.npad, L.npad, nout, (long long)op.hout * op.wout, g, rg); count_launch(); }
+                {
+                    const long long hw = (long long)op.hout * op.wout;
+                    const long long bx = std::max<long long>(1, std::min<long long>((hw + 255) / 256, 1184 / op.nb));
+                    mask_to_bf16_vec_kernel<<<dim3((unsigned)bx, (unsigned)(cg / 8), (unsigned)op.nb), 256, 0, st_>>>(
+                        Gy, ymask, L.npad, L.npad, hw, g, rg);
+                    count_launch();
+                }
                 else
                     { mask_to_bf16_kernel<<<1184, 256, 0, st_>>>(Gy, cg, ymask, L.npad, L.npad, nout,
                                                               (long long)op.hout * op.wout, g, rg); count_launch(); }
