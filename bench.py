@@ -872,7 +872,7 @@ def main():
                          "the checkpoint (default: the checkpoint when it exists, else 400 steps)")
     ap.add_argument("--checkpoint", default=CHECKPOINT,
                     help="initial weights (cnn_load) for the cnn workload")
-    ap.add_argument("--retrain-lr", type=float, default=1e-4,
+    ap.add_argument("--retrain-lr", type=float, default=1e-5,
                     help="retrain workload: Adam learning rate of the Alg. 2 steps on each medium")
     ap.add_argument("--retrain-steps", type=int, default=0,
                     help="Alg. 2 steps on the benchmark medium after loading the checkpoint (set-up, untimed); "
