@@ -457,7 +457,8 @@ int cnn_set_conv_path(int path);
  * on a synthetic residual batch of nrhs RHS (1 <= nrhs <= max_rhs) of the
  * context's medium.  The first launch of every layer shape times its candidate
  * tilings and records the fastest: the default stage and ring budgets,
- * 36/110, 56/112, 100/200 and 47/200 KB, at most 4 rows per tile, and for
+ * 36/110, 56/112, 100/200 and 47/200 KB, at most 4 rows per tile, one
+ * accumulator buffer of up to 512 TMEM columns (more M blocks per tile), and for
  * 16-channel same-grid layers the column-taps-in-N variant.  Later launches of
  * that shape, at any batch size and in any context, use it.  The table is
  * process-wide; explicit cnn_set_conv_tiling / cnn_set_conv_ring values take
@@ -474,15 +475,17 @@ void cnn_autotune_reset(void);
  * input grid, nb images; stage_kb / ring_kb / rows_cap as for
  * cnn_set_conv_ring / cnn_set_conv_tiling (0 = default); narrow = 1 selects the
  * column-taps-in-N variant for 16-channel same-grid layers, narrow = 2 the
- * row-taps-in-N variant for 16- and 32-channel ones.  out18 = {tiles,
+ * row-taps-in-N variant for 16- and 32-channel ones, narrow = 3 the tiling with one
+ * accumulator buffer of up to 512 TMEM columns (any mode; an autotuner candidate).
+ * out19 = {tiles,
  * tile width, tile rows, staged row pitch, M blocks per parity, parities,
  * parity sub-planes, plane bytes, parity stride bytes, weight bytes, stage
  * bytes, stages, TMEM columns, TMEM slots, slot columns, mode used (4 or 6 =
- * the variant), epilogue warpgroups and staged rows per commit of mode 6}.
- * HELM_EINVAL for an invalid shape or one the kernel does not take (out18 is filled
- * either way for a valid shape). */
+ * the variant), epilogue warpgroups and staged rows per commit of mode 6,
+ * accumulator buffers}.  HELM_EINVAL for an invalid shape or one the kernel does not
+ * take (out19 is filled either way for a valid shape). */
 int cnn_conv_plan(int mode, int c0, int c1, int npad, int hin, int win, int nb, int stage_kb, int ring_kb,
-                  int rows_cap, int narrow, int* out18);
+                  int rows_cap, int narrow, int* out19);
 /* Launches of the column-taps-in-N convolution since the library was loaded. */
 long long cnn_conv_narrow_launches(void);
 /* Launches of the row-taps-in-N convolution (cnn_set_conv_path(3)) since the library
@@ -492,6 +495,12 @@ long long cnn_conv_rowtaps_launches(void);
  * tile (0 = automatic: as many as two 128-column TMEM accumulator buffers and a
  * 47 KB stage allow).  Process-wide; for tuning.  HELM_EINVAL outside [0, 254]. */
 int cnn_set_conv_tiling(int max_rows);
+/* Accumulator buffers of the TMA halo-tile kernel (modes same, down, up and the
+ * transpose of down): 1 = one TMEM buffer of up to 512 columns, twice the M blocks per
+ * tile, the MMAs of a tile waiting for the previous tile's epilogue; 2 or 0 = the
+ * default (two buffers, or the autotuned choice).  Process-wide; takes precedence over
+ * the tuned table like the other tiling knobs.  HELM_EINVAL outside [0, 2]. */
+int cnn_set_conv_buffers(int nbuf);
 /* Shared-memory budgets of the TMA halo-tile kernel: at most stage_kb KB per
  * stage (one tile's 16-channel group plus its weights; taller tiles are cut
  * until a stage fits) and ring_kb KB for the ring of stages (2 to 6 stages; a

@@ -113,6 +113,8 @@ struct Geometry {
     int wbytes;              // bytes of one group's weights (9 taps x 2 chunks x npad rows x 16 B)
     int w4;                  // weights by one 4-D TMA box (1) or 18 2-D boxes (0)
     int nslot, slot_cols;    // modes 4 and 6: TMEM slots (an M block / a staged row each) and their columns
+    int nbuf;                // modes 0-3: TMEM accumulator buffers (2: the epilogue drains one while
+                             // the MMAs fill the other; 1: twice the M blocks per tile)
     int nwg;                 // mode 6: epilogue warpgroups that take output rows
     int chunk;               // mode 6: staged rows per commit
     int stage;               // bytes of one stage
@@ -413,8 +415,8 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
         } else {
             int s = 0, wraps = 0;   // j % ns and j / ns as counters
             for (int k = 0; k < ntiles && ok; ++k) {
-                const int acc = k & 1;
-                const int ause = k >> 1;
+                const int acc = g.nbuf == 2 ? (k & 1) : 0;
+                const int ause = g.nbuf == 2 ? (k >> 1) : k;
                 // (the lanes agree on every wait's outcome, so that they leave the loop together)
                 const bool t_ok = ause == 0 || wait_bar(&tempty[acc], (uint32_t)((ause - 1) & 1), abort_v, 32);
                 if (!__all_sync(0xffffffffu, t_ok)) { ok = false; break; }
@@ -655,8 +657,9 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
             }
         } else {
             for (int k = 0; k < ntiles; ++k) {
-                const int acc = k & 1;
-                if (!wait_bar(&tfull[acc], (uint32_t)((k >> 1) & 1), abort_v, 128)) { *abort_v = 1; break; }
+                const int acc = g.nbuf == 2 ? (k & 1) : 0;
+                const uint32_t par = (uint32_t)((g.nbuf == 2 ? (k >> 1) : k) & 1);
+                if (!wait_bar(&tfull[acc], par, abort_v, 128)) { *abort_v = 1; break; }
                 tc::tc_fence_after_sync();
                 int b, xs, ys;
                 tile_coords(k, b, xs, ys);
@@ -847,8 +850,10 @@ std::atomic<int> g_rows_cap{0};   // tile-height limit set by cnn_set_conv_tilin
 // (mode 4, 16 output channels); narrow = 2, the row-taps-in-N kernel (mode 6, 16 or 32).
 struct TileCfg {
     int rows_cap = 0, stage_kb = 0, ring_kb = 0, narrow = 0;
+    int single = 0;   // modes 0-3: one accumulator buffer of up to 512 TMEM columns
 };
 std::atomic<int> g_stage_kb{0}, g_ring_kb{0};
+std::atomic<int> g_single{0};   // one accumulator buffer, set by cnn_set_conv_buffers
 std::atomic<long long> g_launch_narrow{0};   // launches of mode 4
 std::atomic<long long> g_launch_rowtaps{0};  // launches of mode 6   // stage / ring budgets set by cnn_set_conv_ring (0 = default)
 int g_last_launch[6] = {0, 0, 0, 0, 0, 0};   // grid, CTAs per SM, CTAs registers/smem allow, shared memory,
@@ -986,6 +991,10 @@ Geometry plan(const ConvArgs& a, const TileCfg& t) {
     // (wide layers: 256, so that packed rows fill the 128-pixel M blocks)
     int acc_max = 128;
     if (g.nph * a.npad > acc_max || a.npad >= 64) acc_max = 256;
+    // one buffer of up to 512 columns: twice the M blocks per stage (the weights of a
+    // stage serve more pixels), but the MMAs of a tile wait for the previous epilogue
+    g.nbuf = t.single ? 1 : 2;
+    if (t.single) acc_max = 512;
     const int maxmb = acc_max / (g.nph * a.npad);
     auto fill = [&](int rows) {
         g.rows = rows;
@@ -1018,7 +1027,7 @@ Geometry plan(const ConvArgs& a, const TileCfg& t) {
     g.tx = (uint32_t)(2 * g.nplanes * staged_px * 16 + g.wbytes);
     g.acc_cols = (uint32_t)(g.nph * g.mb * a.npad);
     uint32_t cols = 32;
-    while (cols < 2 * g.acc_cols) cols <<= 1;
+    while (cols < (uint32_t)g.nbuf * g.acc_cols) cols <<= 1;
     g.tmem_cols = cols;
     g.tiles = g.tiles_x * g.tiles_y * a.nb;
     return g;
@@ -1231,6 +1240,12 @@ int tune_and_launch(const ConvArgs& a, cudaStream_t st, const std::string& key, 
         c.narrow = 0;
         cands.push_back(c);
     }
+    {
+        TileCfg c = base;
+        c.narrow = 0;
+        c.single = 1;
+        cands.push_back(c);
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
@@ -1278,8 +1293,9 @@ int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st, int narrow) {
     t.stage_kb = g_stage_kb.load();
     t.ring_kb = g_ring_kb.load();
     t.narrow = narrow;
+    t.single = g_single.load();
     // explicit tiling knobs take precedence over the tuned table
-    if (t.rows_cap || t.stage_kb || t.ring_kb) return launch_cfg(a, st, t);
+    if (t.rows_cap || t.stage_kb || t.ring_kb || t.single) return launch_cfg(a, st, t);
     const std::string key = shape_key(a);
     bool tune = false;
     {
@@ -1307,6 +1323,15 @@ void conv_tune_reset() {
 
 }  // namespace helm
 
+extern "C" int cnn_set_conv_buffers(int nbuf) {
+    if (nbuf < 0 || nbuf > 2) {
+        helm::set_error("cnn_set_conv_buffers: nbuf must be 0 (automatic), 1 or 2");
+        return HELM_EINVAL;
+    }
+    helm::g_single.store(nbuf == 1 ? 1 : 0);
+    return HELM_OK;
+}
+
 extern "C" int cnn_set_conv_tiling(int max_rows) {
     if (max_rows < 0 || max_rows > 254) {
         helm::set_error("cnn_set_conv_tiling: max_rows must be in [0, 254]");
@@ -1329,13 +1354,14 @@ extern "C" int cnn_set_conv_ring(int stage_kb, int ring_kb) {
 extern "C" long long cnn_conv_narrow_launches(void) { return helm::g_launch_narrow.load(); }
 extern "C" long long cnn_conv_rowtaps_launches(void) { return helm::g_launch_rowtaps.load(); }
 
-// Tile plan of the TMA kernel for a layer shape (host only, no GPU needed): out18 =
+// Tile plan of the TMA kernel for a layer shape (host only, no GPU needed): out19 =
 // {tiles, tw, rows, pw, mb, nph, nplanes, plane, pstride, wbytes, stage, ns, tmem_cols,
-// nslot, slot_cols, mode, nwg, chunk}.  For checking the plan's bounds on the CPU.
+// nslot, slot_cols, mode, nwg, chunk, nbuf}; narrow = 3 asks for the single-buffer tiling.
+// For checking the plan's bounds on the CPU.
 extern "C" int cnn_conv_plan(int mode, int c0, int c1, int npad, int hin, int win, int nb, int stage_kb,
-                             int ring_kb, int rows_cap, int narrow, int* out18) {
-    if (!out18 || mode < 0 || mode > 3 || c0 < 16 || c0 % 16 || c1 < 0 || c1 % 16 || nb < 1 || hin < 1 ||
-        win < 1 || (npad != 16 && npad % 32) || npad > 128 || narrow < 0 || narrow > 2) {
+                             int ring_kb, int rows_cap, int narrow, int* out19) {
+    if (!out19 || mode < 0 || mode > 3 || c0 < 16 || c0 % 16 || c1 < 0 || c1 % 16 || nb < 1 || hin < 1 ||
+        win < 1 || (npad != 16 && npad % 32) || npad > 128 || narrow < 0 || narrow > 3) {
         helm::set_error("cnn_conv_plan: invalid layer shape");
         return HELM_EINVAL;
     }
@@ -1353,13 +1379,14 @@ extern "C" int cnn_conv_plan(int mode, int c0, int c1, int npad, int hin, int wi
     t.rows_cap = rows_cap;
     t.stage_kb = stage_kb;
     t.ring_kb = ring_kb;
-    t.narrow = narrow;
+    t.narrow = narrow == 3 ? 0 : narrow;
+    t.single = narrow == 3 ? 1 : 0;
     helm::Geometry g{};
     int used = mode;
     const int s = helm::plan_launch(a, t, false, &used, &g);
-    const int v[18] = {g.tiles, g.tw, g.rows, g.pw, g.mb, g.nph, g.nplanes, g.plane, g.pstride, g.wbytes,
-                       g.stage, g.ns, (int)g.tmem_cols, g.nslot, g.slot_cols, used, g.nwg, g.chunk};
-    for (int i = 0; i < 18; ++i) out18[i] = v[i];
+    const int v[19] = {g.tiles, g.tw, g.rows, g.pw, g.mb, g.nph, g.nplanes, g.plane, g.pstride, g.wbytes,
+                       g.stage, g.ns, (int)g.tmem_cols, g.nslot, g.slot_cols, used, g.nwg, g.chunk, g.nbuf};
+    for (int i = 0; i < 19; ++i) out19[i] = v[i];
     if (s != HELM_OK) {
         helm::set_error("cnn_conv_plan: the layer does not fit the TMA kernel");
         return HELM_EINVAL;

@@ -126,6 +126,8 @@ def _load():
     lib.cnn_set_conv_path.restype = ip
     lib.cnn_set_conv_tiling.argtypes = [ip]
     lib.cnn_set_conv_tiling.restype = ip
+    lib.cnn_set_conv_buffers.argtypes = [ip]
+    lib.cnn_set_conv_buffers.restype = ip
     lib.cnn_conv_plan.argtypes = [ip] * 11 + [ctypes.POINTER(ctypes.c_int)]
     lib.cnn_conv_plan.restype = ip
     lib.cnn_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
@@ -582,21 +584,26 @@ def cnn_set_conv_path(path: int):
     _check(lib.cnn_set_conv_path(int(path)), "cnn_set_conv_path")
 
 
+def cnn_set_conv_buffers(nbuf: int):
+    """TMEM accumulator buffers of the TMA conv kernel: 1 single buffer, 0/2 default."""
+    _check(lib.cnn_set_conv_buffers(int(nbuf)), "cnn_set_conv_buffers")
+
+
 def cnn_set_conv_tiling(max_rows: int):
     """Tile-height limit of the TMA conv kernel (0 = automatic)."""
     _check(lib.cnn_set_conv_tiling(int(max_rows)), "cnn_set_conv_tiling")
 
 
 CONV_PLAN_FIELDS = ("tiles", "tw", "rows", "pw", "mb", "nph", "nplanes", "plane", "pstride", "wbytes", "stage",
-                    "ns", "tmem_cols", "nslot", "slot_cols", "mode", "nwg", "chunk")
+                    "ns", "tmem_cols", "nslot", "slot_cols", "mode", "nwg", "chunk", "nbuf")
 
 
 def cnn_conv_plan(mode: int, c0: int, c1: int, npad: int, hin: int, win: int, nb: int = 1, stage_kb: int = 0,
                   ring_kb: int = 0, rows_cap: int = 0, narrow: int = 0):
     """Host-side tile plan of the TMA convolution (dict of CONV_PLAN_FIELDS), or None when
     the kernel does not take the layer.  narrow: 0 plain, 1 (or True) the column-taps-in-N
-    variant, 2 the row-taps-in-N variant."""
-    out = (ctypes.c_int * 18)()
+    variant, 2 the row-taps-in-N variant, 3 the single-accumulator-buffer tiling."""
+    out = (ctypes.c_int * 19)()
     st = lib.cnn_conv_plan(mode, c0, c1, npad, hin, win, nb, stage_kb, ring_kb, rows_cap, int(narrow), out)
     if st != HELM_OK:
         return None

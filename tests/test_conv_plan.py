@@ -76,7 +76,7 @@ def _check(g, mode, npad, hin, win, nb):
         assert len(cover) == g["rows"] * g["tw"]
         return
     nph = g["nph"]
-    assert 2 * nph * g["mb"] * npad <= g["tmem_cols"]
+    assert g["nbuf"] in (1, 2) and g["nbuf"] * nph * g["mb"] * npad <= g["tmem_cols"]
     for ph in range(nph):
         py, px = ph >> 1, ph & 1
         taps = _taps(mode, py, px, g["pw"])
@@ -96,12 +96,13 @@ def _check(g, mode, npad, hin, win, nb):
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_tile_plans_stay_in_bounds(n, mode):
     checked = 0
-    for (H, W), c0, npad, (skb, rkb, cap) in itertools.product(SHAPES, (16, 64), (16, 32, 64, 128), BUDGETS):
+    for (H, W), c0, npad, (skb, rkb, cap), single in itertools.product(SHAPES, (16, 64), (16, 32, 64, 128), BUDGETS,
+                                                                       (0, 1)):
         if mode == 1:
             hin, win = 2 * H, 2 * W
         else:
             hin, win = H, W
-        g = n.cnn_conv_plan(mode, c0, 0, npad, hin, win, 2, skb, rkb, cap)
+        g = n.cnn_conv_plan(mode, c0, 0, npad, hin, win, 2, skb, rkb, cap, narrow=3 if single else 0)
         if g is None:
             continue                 # the launcher rejects it too (gather kernel): one shared decision
         _check(g, mode, npad, hin, win, 2)
