@@ -22,10 +22,18 @@ H mu = P_s conj(r): the conjugation identity of Sec. 4.3 (Eq. 4.8), so
 
 Receivers are flat grid indices (iz * nx + ix); P_s^T samples u at them and
 P_s scatters a receiver vector back onto the grid.
+
+Regularisers of the reconstruction (Sec. 5.1), on v = m - m_ref:
+    R_diff(m) = || grad_h v ||_2^2            (diffusion)
+    R_high(m) = || Lap_h v ||_2^2             (spline smoothing)
+with grad_h the forward differences on the grid's interior edges and Lap_h =
+-grad_h^T grad_h, the nodal Laplacian with the grid's natural boundary (the paper
+does not state a boundary for these operators).
 """
 from __future__ import annotations
 
 import numpy as np
+import scipy.sparse as sp
 
 from .helmholtz import DirectSolver
 
@@ -120,14 +128,45 @@ def jacobian_adjoint(kappa, gamma, omegas, hx, hz, sources, receivers, dd):
     return out
 
 
+def nodal_gradient(nx: int, nz: int, hx: float, hz: float):
+    """grad_h of Sec. 5.1's R_diff as a sparse matrix on fields raveled row-major ([nz][nx]):
+    the forward differences (v[i + 1] - v[i]) / hx on the (nx - 1) x nz interior x-edges,
+    then (v[j + 1] - v[j]) / hz on the nx x (nz - 1) interior z-edges."""
+    def diff1(n, h):
+        return sp.diags([-np.ones(n - 1), np.ones(n - 1)], [0, 1], shape=(n - 1, n)) / h
+    gx = sp.kron(sp.identity(nz), diff1(nx, hx))
+    gz = sp.kron(diff1(nz, hz), sp.identity(nx))
+    return sp.vstack([gx, gz]).tocsr()
+
+
+def regularizer(m, m_ref, hx: float, hz: float, kind: int):
+    """R(m) of Sec. 5.1 on v = m - m_ref (m_ref None: zero): kind 1 R_diff = ||grad_h v||^2,
+    kind 2 R_high = ||Lap_h v||^2 with Lap_h = -grad_h^T grad_h, kind 0 none.  Returns
+    (R, grad R, K) with K the symmetric matrix for which R = v^T K v and grad R = 2 K v
+    (G^T G or (G^T G)^2, G = grad_h)."""
+    m = np.asarray(m, dtype=np.float64)
+    nz, nx = m.shape
+    v = (m - (0.0 if m_ref is None else np.asarray(m_ref, dtype=np.float64))).ravel()
+    if kind == 0:
+        return 0.0, np.zeros_like(m), sp.csr_matrix((v.size, v.size))
+    G = nodal_gradient(nx, nz, hx, hz)
+    L = (G.T @ G).tocsr()
+    K = L if kind == 1 else (L @ L).tocsr()
+    Kv = K @ v
+    return float(v @ Kv), (2.0 * Kv).reshape(m.shape), K
+
+
 def gauss_newton_direction(kappa, gamma, omegas, hx, hz, sources, receivers, d_obs, cg_iters: int,
-                           reg: float = 0.0):
-    """The Gauss-Newton step of Sec. 3.3 (Alg. 1): dm approximately solving
-    (J^T J + reg I) dm = -J^T r,  r = d(m) - d_obs  (J^T r = grad Phi / 2 for Eq. 3.5),
-    by cg_iters iterations of conjugate gradients from dm = 0 (Hestenes and Stiefel).
-    Returns (dm, Phi, grad Phi)."""
+                           reg: float = 0.0, reg_kind: int = 0, alpha: float = 0.0, m_ref=None):
+    """The Gauss-Newton step of Sec. 3.3 (Alg. 1) for the objective Phi(m) + alpha R(m)
+    (R of Sec. 5.1, `regularizer`): dm approximately solving
+    (J^T J + alpha K + reg I) dm = -(J^T r + alpha K (m - m_ref)),  r = d(m) - d_obs
+    (J^T r = grad Phi / 2 for Eq. 3.5), by cg_iters iterations of conjugate gradients from
+    dm = 0 (Hestenes and Stiefel).  Returns (dm, Phi, grad Phi)."""
     phi, grad = misfit_and_gradient(kappa, gamma, omegas, hx, hz, sources, receivers, d_obs)
-    b = -0.5 * grad
+    m = np.asarray(kappa, dtype=np.float64) ** 2
+    _, grad_r, K = regularizer(m, m_ref, hx, hz, reg_kind)
+    b = -0.5 * (grad + alpha * grad_r)
     x = np.zeros_like(b)
     r = b.copy()
     p = r.copy()
@@ -135,9 +174,11 @@ def gauss_newton_direction(kappa, gamma, omegas, hx, hz, sources, receivers, d_o
     for _ in range(cg_iters):
         Ap = jacobian_adjoint(kappa, gamma, omegas, hx, hz, sources, receivers,
                               jacobian_apply(kappa, gamma, omegas, hx, hz, sources, receivers, p)) + reg * p
-        alpha = rr / float(np.sum(p * Ap))
-        x = x + alpha * p
-        r = r - alpha * Ap
+        if reg_kind:
+            Ap = Ap + alpha * (K @ p.ravel()).reshape(p.shape)
+        step = rr / float(np.sum(p * Ap))
+        x = x + step * p
+        r = r - step * Ap
         rr_new = float(np.sum(r * r))
         p = r + (rr_new / rr) * p
         rr = rr_new

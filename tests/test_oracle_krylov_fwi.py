@@ -129,3 +129,70 @@ def test_gauss_newton_cg_reaches_the_normal_equations_solution():
     dm, phi, grad = fwi.gauss_newton_direction(k64, gam, omegas, w.h, w.h, sources, receivers, d_obs, n, reg)
     ref = np.linalg.solve(JtJ + reg * np.eye(n), -0.5 * grad.ravel())
     assert np.linalg.norm(dm.ravel() - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_regularizers_by_their_definitions():
+    """Sec. 5.1's R_diff and R_high, pinned without the oracle's sparse operators:
+    an affine field v = a x + b z has R_diff = a^2 (nx - 1) nz + b^2 nx (nz - 1) (every
+    edge difference is a or b); constants cost nothing; R_high equals the squared norm of
+    a nodal Laplacian assembled here by loops over the neighbours (natural boundary:
+    only the neighbours inside the grid); both gradients match central finite
+    differences."""
+    nz, nx, hx, hz = 5, 7, 2.0, 3.0
+    xs, zs = np.meshgrid(np.arange(nx) * hx, np.arange(nz) * hz)
+    a, b = 0.7, -1.3
+    v = a * xs + b * zs
+    r_diff, _, _ = fwi.regularizer(v, None, hx, hz, 1)
+    assert abs(r_diff - (a * a * (nx - 1) * nz + b * b * nx * (nz - 1))) <= 1e-12 * r_diff
+    c = np.full((nz, nx), 3.5)
+    assert abs(fwi.regularizer(c, None, hx, hz, 1)[0]) <= 1e-12
+    assert abs(fwi.regularizer(c, None, hx, hz, 2)[0]) <= 1e-12
+    g = np.random.default_rng(11)
+    m = g.normal(size=(nz, nx))
+    m_ref = g.normal(size=(nz, nx))
+    u = m - m_ref
+    lap = np.zeros_like(u)
+    for j in range(nz):
+        for i in range(nx):
+            for dj, di, h in ((0, -1, hx), (0, 1, hx), (-1, 0, hz), (1, 0, hz)):
+                jj, ii = j + dj, i + di
+                if 0 <= jj < nz and 0 <= ii < nx:
+                    lap[j, i] += (u[jj, ii] - u[j, i]) / (h * h)
+    r_high, _, _ = fwi.regularizer(m, m_ref, hx, hz, 2)
+    assert abs(r_high - float(np.sum(lap * lap))) <= 1e-12 * r_high
+    for kind in (1, 2):
+        _, grad, _ = fwi.regularizer(m, m_ref, hx, hz, kind)
+        eps = 1e-6
+        for (j, i) in ((0, 0), (2, 3), (4, 6)):
+            mp, mm = m.copy(), m.copy()
+            mp[j, i] += eps
+            mm[j, i] -= eps
+            fd = (fwi.regularizer(mp, m_ref, hx, hz, kind)[0] - fwi.regularizer(mm, m_ref, hx, hz, kind)[0]) / (2 * eps)
+            assert abs(fd - grad[j, i]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_regularised_gauss_newton_reaches_its_normal_equations():
+    """With a regulariser of Sec. 5.1 and three times as many CG steps as unknowns, the Gauss-Newton
+    direction solves (J^T J + alpha K) dm = -(grad Phi + alpha grad R) / 2 built from the
+    explicit Jacobian, for R_diff and R_high."""
+    w = media.crop_workload(6, 4, h=50.0, freqs=(2.0,), width=1)
+    k64 = w.kappa.astype(np.float64)
+    gam = w.gamma.astype(np.float64)
+    omegas = [2 * math.pi * 2.0, 2 * math.pi * 3.0]
+    sources = media.point_source_rhs(w.nx, w.nz, [(0, 1), (0, 4)], w.h, w.h)
+    receivers = np.arange(0, w.nx)
+    d_obs, _ = fwi.forward_data(1.0 / (1.0 / k64 * 1.03), gam, omegas, w.h, w.h, sources, receivers)
+    n = k64.size
+    J = np.stack([fwi.jacobian_apply(k64, gam, omegas, w.h, w.h, sources, receivers,
+                                     np.eye(n)[i].reshape(k64.shape)).ravel() for i in range(n)], axis=1)
+    JtJ = np.real(J.conj().T @ J)
+    m_ref = (k64 ** 2) * 1.1
+    for kind in (1, 2):
+        _, grad_r, K = fwi.regularizer(k64 ** 2, m_ref, w.h, w.h, kind)
+        K = K.toarray()
+        alpha = 1e-2 * np.trace(JtJ) / np.trace(K)
+        # (more CG steps than unknowns: the regularised system's condition number is ~1e4)
+        dm, phi, grad = fwi.gauss_newton_direction(k64, gam, omegas, w.h, w.h, sources, receivers, d_obs, 3 * n,
+                                                   reg_kind=kind, alpha=alpha, m_ref=m_ref)
+        ref = np.linalg.solve(JtJ + alpha * K, -0.5 * (grad + alpha * grad_r).ravel())
+        assert np.linalg.norm(dm.ravel() - ref) <= 1e-6 * np.linalg.norm(ref)
