@@ -227,7 +227,12 @@ typedef struct {
     int    cg_iters;        /* conjugate-gradient steps on the Gauss-Newton system       (5) */
     float  reg;             /* Tikhonov term reg I added to J^T J                        (0) */
     float  m_min, m_max;    /* bounds of m = kappa^2 after the step              (0, 1e30) */
-    int    max_backtracks;  /* halvings of the step when the misfit does not drop      (4) */
+    int    max_backtracks;  /* halvings of the step when the objective does not drop   (4) */
+    int    reg_kind;        /* regulariser R of Sec. 5.1 on v = m - m_ref: 0 none, 1 R_diff =
+                               ||grad_h v||^2, 2 R_high = ||Lap_h v||^2, Lap_h = -grad_h^T grad_h
+                               (forward differences on the interior edges, scaled by 1/hx, 1/hz)  (0) */
+    float  alpha;           /* weight of R: the objective is Phi(m) + alpha R(m)            (0) */
+    const float* m_ref;     /* reference model [nz][nx], host or device; NULL: zero     (NULL) */
 } fwi_gn_opts;
 typedef struct {
     double misfit_before, misfit_after;   /* Eq. 3.5 at the model before / after the step */
@@ -235,16 +240,20 @@ typedef struct {
     int    cg_iters;                      /* CG steps taken                               */
     long long iters_forward, iters_adjoint, iters_sensitivity, iters_line_search;
                                           /* Helmholtz (FGMRES) iterations per phase      */
+    double objective_before, objective_after;   /* Phi + alpha R before / after the step */
 } fwi_gn_info;
 void fwi_default_gn_opts(fwi_gn_opts* opts);
 /* kappa = sqrt(m) for n nodes (device arrays): the medium of a model m = kappa^2. */
 int fwi_model_to_kappa(const float* m, float* kappa, long long n);
-/* One Gauss-Newton iteration of Alg. 1 at the context's frequencies: sets the medium
- * from m (clipped to [m_min, m_max]; kappa = sqrt(m), gamma kept), forward fields and the
- * misfit of Eq. 3.5, its gradient 2 J^T r, cg_iters conjugate-gradient steps on
- * (J^T J + reg I) dm = -J^T r from 0 with the forward fields kept (two solves per source
- * and frequency per step), then m <- clip(m + a dm) for a = 1, 1/2, ... (at most
- * max_backtracks halvings) as soon as the misfit drops; if none does, m is unchanged.
+/* One Gauss-Newton iteration of Alg. 1 at the context's frequencies for the objective
+ * Phi(m) + alpha R(m) (Eq. 3.5 and a regulariser of Sec. 5.1): sets the medium from m
+ * (clipped to [m_min, m_max]; kappa = sqrt(m), gamma kept), forward fields and the misfit
+ * Phi, the gradient 2 J^T r + alpha grad R, cg_iters conjugate-gradient steps on
+ * (J^T J + alpha K + reg I) dm = -(J^T r + alpha K (m - m_ref)) from 0 (K = -Lap_h for
+ * R_diff, Lap_h^2 for R_high) with the forward fields kept (two solves per source and
+ * frequency per step), then m <- clip(m + a dm) for a = 1, 1/2, ... (at most
+ * max_backtracks halvings) as soon as the objective drops; if none does, m is unchanged.
+ * info->misfit_* report Phi, info->objective_* Phi + alpha R.
  * d_obs: complex64 [nfreq][nsrc][nrcv] per POINT source (host or device); with
  * simultaneous sources it is encoded here with the survey's weights (d_k = sum_s w_ks d_s).
  * m: float32 [nz][nx] (host or device), updated in place; the context's medium is left

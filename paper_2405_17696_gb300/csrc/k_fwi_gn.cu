@@ -8,10 +8,11 @@
 //   J^T d: mu = H^{-1} P conj(d_jk),  (J^T d) += w_j^2 Re((1 - i gamma) u mu)
 //          (the conjugation identity of Sec. 4.3 turns H^* into a forward solve;
 //           J^T is Re(J^H), the adjoint for real model perturbations)
-//   Gauss-Newton: dm ~ argmin ||J dm + r||^2 + reg ||dm||^2 by cg_iters conjugate
-//   gradient steps on (J^T J + reg I) dm = -J^T r from dm = 0, r = P^T u - d_obs,
-//   then a backtracking step m <- clip(m + alpha dm), alpha = 1, 1/2, ... while the
-//   misfit of Eq. 3.5 does not drop.
+//   Gauss-Newton on Phi(m) + a R(m) (Eq. 3.5 and a regulariser of Sec. 5.1 on
+//   v = m - m_ref, R = v^T K v with K = L or L^2, L = -Lap_h): dm by cg_iters
+//   conjugate gradient steps on (J^T J + a K + reg I) dm = -(J^T r + a K v) from
+//   dm = 0, r = P^T u - d_obs, then a backtracking step m <- clip(m + alpha dm),
+//   alpha = 1, 1/2, ... while the objective does not drop.
 // Every solve is helm_solve with the context's preconditioner (multigrid or the
 // encoder-solver network), and the Helmholtz iterations of every solve are
 // counted.  Model-space vectors are FP64 on the device; their inner products
@@ -146,6 +147,32 @@ __global__ void dot_partial_kernel(const double* __restrict__ a, const double* _
 __global__ void axpby_kernel(double a, const double* __restrict__ x, double b, double* __restrict__ y, size_t n) {
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
         y[p] = a * x[p] + b * y[p];
+}
+
+// y = a L v + b y (b = 0: y is not read), L = G^T G the negative five-point Laplacian of the
+// regularisers of Sec. 5.1: G takes forward differences on the interior edges (scaled by 1/hx,
+// 1/hz), so (L v)_p = sum over the neighbours q of p of (v_p - v_q) / h^2 and the boundary is
+// natural (no edge leaves the grid).  ax = 1/hx^2, az = 1/hz^2.
+__global__ void neg_lap_kernel(const double* __restrict__ v, double* __restrict__ y, int nx, int nz, double ax,
+                               double az, double a, double b) {
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iz = blockIdx.y * blockDim.y + threadIdx.y;
+    if (ix >= nx || iz >= nz) return;
+    const size_t p = (size_t)iz * nx + ix;
+    const double vc = v[p];
+    double s = 0.0;
+    if (ix > 0) s += ax * (vc - v[p - 1]);
+    if (ix < nx - 1) s += ax * (vc - v[p + 1]);
+    if (iz > 0) s += az * (vc - v[p - nx]);
+    if (iz < nz - 1) s += az * (vc - v[p + nx]);
+    y[p] = b == 0.0 ? a * s : a * s + b * y[p];
+}
+
+// v = m - m_ref in FP64 (m_ref null: zero)
+__global__ void model_diff_kernel(const float* __restrict__ m, const float* __restrict__ m_ref, double* __restrict__ v,
+                                  size_t n) {
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+        v[p] = (double)m[p] - (m_ref ? (double)m_ref[p] : 0.0);
 }
 
 __global__ void f64_of_f32_kernel(const float* __restrict__ x, double* __restrict__ y, double s, size_t n) {
@@ -432,6 +459,33 @@ int set_model(helm_ctx* c, Fwi& F, const float* m0, const double* dm, double alp
     return s;
 }
 
+// y = a L v + b y on the context's grid
+int apply_neg_lap(helm_ctx* c, const double* v, double* y, double a, double b) {
+    LaunchScope scope(c, K_MISC);
+    { neg_lap_kernel<<<dim3((c->nx + 31) / 32, (c->nz + 7) / 8), dim3(32, 8), 0, c->stream>>>(
+          v, y, c->nx, c->nz, 1.0 / ((double)c->hx * c->hx), 1.0 / ((double)c->hz * c->hz), a, b); count_launch(); }
+    HELM_CK(cudaGetLastError());
+    return HELM_OK;
+}
+
+// The regulariser of Sec. 5.1 at the model m: R = v^T K v and K v for v = m - m_ref, with
+// K = L (R_diff = ||G v||^2) or K = L^2 (R_high = ||L v||^2, L = -Lap_h).  Scratch v, t of N.
+int regulariser(helm_ctx* c, Fwi& F, int kind, const float* m, const float* m_ref, double* v, double* t, double* kv,
+                double* R) {
+    {
+        LaunchScope scope(c, K_MISC);
+        { model_diff_kernel<<<1184, 256, 0, c->stream>>>(m, m_ref, v, F.N()); count_launch(); }
+        HELM_CK(cudaGetLastError());
+    }
+    if (kind == 1) {
+        HELM_TRY(apply_neg_lap(c, v, kv, 1.0, 0.0));
+        return F.dot(v, kv, R);
+    }
+    HELM_TRY(apply_neg_lap(c, v, t, 1.0, 0.0));
+    HELM_TRY(apply_neg_lap(c, t, kv, 1.0, 0.0));
+    return F.dot(t, t, R);
+}
+
 }  // namespace
 }  // namespace helm
 
@@ -448,6 +502,9 @@ void fwi_default_gn_opts(fwi_gn_opts* o) {
     o->m_min = 0.0f;
     o->m_max = 1e30f;
     o->max_backtracks = 4;
+    o->reg_kind = 0;
+    o->alpha = 0.0f;
+    o->m_ref = nullptr;
 }
 
 int fwi_model_to_kappa(const float* m, float* kappa, long long n) {
@@ -545,10 +602,13 @@ int fwi_gn_iteration(helm_ctx* c, const fwi_survey* sv, const helm_c64* d_obs, c
     fwi_default_gn_opts(&o);
     if (opts) o = *opts;
     if (!(o.tol > 0) || !(o.tol_sens > 0) || o.cg_iters < 0 || !(o.reg >= 0) || !(o.m_max > o.m_min) ||
-        o.max_backtracks < 0) {
+        o.max_backtracks < 0 || o.reg_kind < 0 || o.reg_kind > 2 || !(o.alpha >= 0) || !std::isfinite(o.alpha)) {
         set_error("fwi_gn_iteration: invalid options");
         return HELM_EINVAL;
     }
+    // the regulariser's term (none when its weight is zero)
+    const int rk = o.alpha > 0 ? o.reg_kind : 0;
+    const double ra = rk ? (double)o.alpha : 0.0;
     Fwi F(c, sv);
     HELM_TRY(F.init());
     const size_t N = F.N();
@@ -569,8 +629,19 @@ int fwi_gn_iteration(helm_ctx* c, const fwi_survey* sv, const helm_c64* d_obs, c
         HELM_CK(cudaGetLastError());
         dobs = denc;
     }
+    const float* mref = nullptr;
+    if (rk && o.m_ref) {
+        mref = device_view(F, o.m_ref, N, c->stream, &st);
+        if (st) return st;
+    }
     float *m0 = nullptr, *mt = nullptr;
     double *g = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *ap = nullptr;
+    double *rv = nullptr, *rt = nullptr, *rkv = nullptr;
+    if (rk) {
+        HELM_TRY(F.alloc(&rv, N));
+        HELM_TRY(F.alloc(&rt, N));
+        HELM_TRY(F.alloc(&rkv, N));
+    }
     double2* U = nullptr;
     float2 *R = nullptr, *dd = nullptr;
     HELM_TRY(F.alloc(&m0, N));
@@ -598,7 +669,16 @@ int fwi_gn_iteration(helm_ctx* c, const fwi_survey* sv, const helm_c64* d_obs, c
         HELM_TRY(F.jtd(U + (size_t)b0 * N, R + (size_t)b0 * F.nrcv(), b0, nb, o.tol, 2.0, g));
     }
     const long long it_adj = F.iterations() - it0;
-    // conjugate gradients on (J^T J + reg I) x = -g / 2 from x = 0
+    // the regulariser at the current model: objective Phi + alpha R, gradient += 2 alpha K v
+    double R0 = 0.0;
+    if (rk) {
+        HELM_TRY(regulariser(c, F, rk, m0, mref, rv, rt, rkv, &R0));
+        LaunchScope scope(c, K_MISC);
+        { axpby_kernel<<<1184, 256, 0, c->stream>>>(2.0 * ra, rkv, 1.0, g, N); count_launch(); }
+        HELM_CK(cudaGetLastError());
+    }
+    const double obj0 = phi0 + ra * R0;
+    // conjugate gradients on (J^T J + alpha K + reg I) x = -g / 2 from x = 0
     HELM_CK(cudaMemsetAsync(x, 0, N * sizeof(double), c->stream));
     {
         LaunchScope scope(c, K_MISC);
@@ -622,6 +702,12 @@ int fwi_gn_iteration(helm_ctx* c, const fwi_survey* sv, const helm_c64* d_obs, c
             { axpby_kernel<<<1184, 256, 0, c->stream>>>((double)o.reg, p, 1.0, ap, N); count_launch(); }
             HELM_CK(cudaGetLastError());
         }
+        if (rk == 1) {
+            HELM_TRY(apply_neg_lap(c, p, ap, ra, 1.0));   // ap += alpha L p
+        } else if (rk == 2) {
+            HELM_TRY(apply_neg_lap(c, p, rt, 1.0, 0.0));
+            HELM_TRY(apply_neg_lap(c, rt, ap, ra, 1.0));  // ap += alpha L^2 p
+        }
         double pap = 0.0;
         HELM_TRY(F.dot(p, ap, &pap));
         if (!(pap > 0.0)) break;
@@ -642,14 +728,17 @@ int fwi_gn_iteration(helm_ctx* c, const fwi_survey* sv, const helm_c64* d_obs, c
         rr = rr_new;
     }
     const long long it_sens = F.iterations() - it0;
-    // backtracking: m <- clip(m0 + alpha x) for alpha = 1, 1/2, ... while the misfit does not drop
+    // backtracking: m <- clip(m0 + alpha x) for alpha = 1, 1/2, ... while the objective does not drop
     it0 = F.iterations();
-    double step = 1.0, phi1 = phi0;
+    double step = 1.0, phi1 = phi0, obj1 = obj0;
     bool accepted = false;
     for (int t = 0; t <= o.max_backtracks; ++t, step *= 0.5) {
         HELM_TRY(set_model(c, F, m0, x, step, o.m_min, o.m_max, mt));
         HELM_TRY(F.misfit(dobs, o.tol, nullptr, nullptr, &phi1));
-        if (phi1 < phi0) { accepted = true; break; }
+        double R1 = 0.0;
+        if (rk) HELM_TRY(regulariser(c, F, rk, mt, mref, rv, rt, rkv, &R1));
+        obj1 = phi1 + ra * R1;
+        if (obj1 < obj0) { accepted = true; break; }
     }
     const long long it_ls = F.iterations() - it0;
     if (accepted) {
@@ -659,10 +748,13 @@ int fwi_gn_iteration(helm_ctx* c, const fwi_survey* sv, const helm_c64* d_obs, c
         HELM_TRY(set_model(c, F, m0, nullptr, 0.0, o.m_min, o.m_max, mt));
         step = 0.0;
         phi1 = phi0;
+        obj1 = obj0;
     }
     if (info) {
         info->misfit_before = phi0;
         info->misfit_after = phi1;
+        info->objective_before = obj0;
+        info->objective_after = obj1;
         info->step = step;
         info->cg_iters = cg_done;
         info->iters_forward = it_fwd;

@@ -41,6 +41,8 @@ class FwiConfig:
     mg_levels: int = 3
     max_rhs: int = 64
     seed: int = media.SEED_SOURCES
+    reg_kind: int = 0               # regulariser of Sec. 5.1: 0 none, 1 R_diff, 2 R_high
+    reg_alpha: float = 0.0          # its weight; the reference model is the model the run starts from
 
 
 @dataclass
@@ -136,7 +138,9 @@ def run(native, m, gamma, nx, nz, hx, hz, src_idx, rcv_idx, d_obs, freqs_hz, cfg
     gam = torch.as_tensor(gamma, dtype=torch.float32, device="cuda").contiguous()
     fidx = {f: i for i, f in enumerate(freqs_hz)}
     opts = native.fwi_default_gn_opts(tol=cfg.tol, tol_sens=cfg.tol_sens, cg_iters=cfg.cg_iters,
-                                      m_min=1.0 / cfg.v_max ** 2, m_max=1.0 / cfg.v_min ** 2)
+                                      m_min=1.0 / cfg.v_max ** 2, m_max=1.0 / cfg.v_min ** 2,
+                                      reg_kind=cfg.reg_kind, alpha=cfg.reg_alpha)
+    m_ref = m.clone() if cfg.reg_kind and cfg.reg_alpha > 0 else None
     for wi, window in enumerate(cfg.windows):
         om = torch.tensor([2 * math.pi * f for f in window], dtype=torch.float32, device="cuda")
         dw = torch.stack([d_obs[fidx[f]] for f in window]).contiguous()
@@ -152,7 +156,7 @@ def run(native, m, gamma, nx, nz, hx, hz, src_idx, rcv_idx, d_obs, freqs_hz, cfg
                 w = rademacher(cfg.sim_sources, nsrc, rng) if cfg.sim_sources > 0 else None
                 survey = native.Survey(src_idx, rcv_idx, w)
                 t0 = time.perf_counter()
-                info = native.fwi_gn_iteration(ctx, survey, dw, m, opts)
+                info = native.fwi_gn_iteration(ctx, survey, dw, m, opts, m_ref=m_ref)
                 row = dict(info, window=wi + window_offset, freqs=list(window), iteration=it,
                            seconds=time.perf_counter() - t0, grid=[nx, nz])
                 if net is not None and cfg.retrain_steps > 0:

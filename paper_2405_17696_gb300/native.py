@@ -49,14 +49,16 @@ class fwi_survey_t(ctypes.Structure):
 class fwi_gn_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("tol_sens", ctypes.c_double), ("cg_iters", ctypes.c_int),
                 ("reg", ctypes.c_float), ("m_min", ctypes.c_float), ("m_max", ctypes.c_float),
-                ("max_backtracks", ctypes.c_int)]
+                ("max_backtracks", ctypes.c_int), ("reg_kind", ctypes.c_int), ("alpha", ctypes.c_float),
+                ("m_ref", ctypes.c_void_p)]
 
 
 class fwi_gn_info(ctypes.Structure):
     _fields_ = [("misfit_before", ctypes.c_double), ("misfit_after", ctypes.c_double), ("step", ctypes.c_double),
                 ("cg_iters", ctypes.c_int), ("iters_forward", ctypes.c_longlong),
                 ("iters_adjoint", ctypes.c_longlong), ("iters_sensitivity", ctypes.c_longlong),
-                ("iters_line_search", ctypes.c_longlong)]
+                ("iters_line_search", ctypes.c_longlong), ("objective_before", ctypes.c_double),
+                ("objective_after", ctypes.c_double)]
 
 
 class cnn_retrain_opts(ctypes.Structure):
@@ -383,9 +385,14 @@ def fwi_default_gn_opts(**overrides) -> fwi_gn_opts:
     return o
 
 
-def fwi_gn_iteration(ctx, survey: Survey, d_obs, m, opts=None) -> dict:
-    """One Gauss-Newton iteration; m (float32 [nz][nx]) updated in place.  Returns the info fields."""
+def fwi_gn_iteration(ctx, survey: Survey, d_obs, m, opts=None, m_ref=None) -> dict:
+    """One Gauss-Newton iteration; m (float32 [nz][nx]) updated in place.  m_ref (float32
+    [nz][nx], host or device) is the regulariser's reference model, kept alive by the caller
+    for the call.  Returns the info fields."""
     o = opts if opts is not None else fwi_default_gn_opts()
+    if m_ref is not None:
+        o = fwi_gn_opts.from_buffer_copy(o)
+        o.m_ref = _ptr(m_ref, "float32")
     info = fwi_gn_info()
     _check(lib.fwi_gn_iteration(ctx, ctypes.byref(survey.c), _ptr(d_obs, "complex64"), ctypes.byref(o),
                                 _ptr(m, "float32"), ctypes.byref(info)), "fwi_gn_iteration")

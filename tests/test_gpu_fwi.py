@@ -129,6 +129,58 @@ def test_gauss_newton_iteration_matches_the_oracle(native):
     assert _rel(_f32(m) - _f32(m0), dm_ref) <= 1e-3
 
 
+@pytest.mark.parametrize("kind,alpha", [(1, 4e16), (2, 3e19)])
+def test_regularised_gauss_newton_iteration_matches_the_oracle(native, kind, alpha):
+    """One Gauss-Newton iteration on Phi + alpha R with R_diff (kind 1) or R_high (kind 2)
+    of Sec. 5.1 about a smoother reference model, against the oracle's direction.  The
+    weights make alpha grad R about a third of grad Phi, so the direction moves far from
+    the unregularised one (by 0.9 of its norm in the oracle); the objective Phi + alpha R
+    before the step is checked against the oracle's R."""
+    nx, nz, hx, hz, k_true, k0, gamma, freqs, src, rcv = _case()
+    om = [float(np.float32(2 * math.pi * f)) for f in freqs]
+    g = _sources(nx, nz, hx, hz, src)
+    d_obs, _ = fwi.forward_data(_f32(k_true), _f32(gamma), om, hx, hz, g, np.array(rcv))
+    c_ref = media.gaussian_smooth(media.layered_velocity(nx, nz, seed=4, n_layers=6), 10.0)
+    m_ref = (np.asarray(media.kappa_of(c_ref), np.float32) ** 2).astype(np.float32)
+    alpha = float(np.float32(alpha))
+    dm_ref, phi_ref, _ = fwi.gauss_newton_direction(_f32(k0), _f32(gamma), om, hx, hz, g, np.array(rcv), d_obs, 3,
+                                                    reg_kind=kind, alpha=alpha, m_ref=_f32(m_ref))
+    sv = native.Survey(src, rcv)
+    m = (np.asarray(k0, np.float32) ** 2).astype(np.float32)
+    m0 = m.copy()
+    R_ref = fwi.regularizer(_f32(m0), _f32(m_ref), hx, hz, kind)[0]
+    ctx = _ctx(native, nx, nz, hx, hz, k0, gamma, freqs)
+    try:
+        info = native.fwi_gn_iteration(ctx, sv, np.ascontiguousarray(d_obs, np.complex64), m,
+                                       native.fwi_default_gn_opts(tol=1e-8, tol_sens=1e-8, cg_iters=3,
+                                                                  max_backtracks=0, reg_kind=kind, alpha=alpha),
+                                       m_ref=torch.from_numpy(m_ref).cuda())
+    finally:
+        native.helm_destroy(ctx)
+    assert abs(info["misfit_before"] - phi_ref) <= 1e-5 * phi_ref
+    obj_ref = info["misfit_before"] + alpha * R_ref
+    assert abs(info["objective_before"] - obj_ref) <= 1e-9 * obj_ref
+    assert info["step"] == 1.0 and info["objective_after"] < info["objective_before"]
+    assert info["cg_iters"] == 3
+    assert _rel(_f32(m) - _f32(m0), dm_ref) <= 1e-3
+
+
+def test_gauss_newton_rejects_invalid_regulariser_options(native):
+    """reg_kind outside {0, 1, 2} and a negative weight are refused before any work."""
+    nx, nz, hx, hz, k_true, k0, gamma, freqs, src, rcv = _case()
+    sv = native.Survey(src, rcv)
+    m = (np.asarray(k0, np.float32) ** 2).astype(np.float32)
+    d = np.zeros((len(freqs), len(src), len(rcv)), np.complex64)
+    ctx = _ctx(native, nx, nz, hx, hz, k0, gamma, freqs)
+    try:
+        for bad in (dict(reg_kind=3, alpha=1.0), dict(reg_kind=-1, alpha=1.0), dict(reg_kind=1, alpha=-1.0)):
+            with pytest.raises(native.HelmError) as e:
+                native.fwi_gn_iteration(ctx, sv, d, m, native.fwi_default_gn_opts(**bad))
+            assert e.value.status == native.HELM_EINVAL
+    finally:
+        native.helm_destroy(ctx)
+
+
 def test_frequency_continuation_lowers_the_misfit(native):
     """Alg. 1 through the driver: two frequency windows of Gauss-Newton iterations with
     simultaneous sources, MG-FGMRES and CNN-FGMRES with Alg. 2 retraining after each
