@@ -109,6 +109,24 @@ __global__ void pack_weights_kernel(const float* __restrict__ master, long long 
     }
 }
 
+// master FP32 [cout][9][cin] -> the phase-merged BF16 weights [npad][16][cin_pad] of an up
+// layer: row up_merged_index(py, px, dy, dx) holds the sum, in FP32, of the taps (dy, dx) of
+// output parity (py, px) that read the same coarse node, rounded once
+__global__ void pack_up_weights_kernel(const float* __restrict__ master, long long off, int cin, int cout,
+                                       int cin_pad, int npad, __nv_bfloat16* __restrict__ wup) {
+    const int total = npad * 16 * cin_pad;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int ci = i % cin_pad, r = (i / cin_pad) % 16, co = i / (16 * cin_pad);
+        const int ph = r >> 2;
+        float v = 0.0f;
+        if (co < cout && ci < cin)
+            for (int t = 0; t < 9; ++t)
+                if (up_merged_index(ph >> 1, ph & 1, t / 3 - 1, t % 3 - 1) == r)
+                    v += master[off + ((long long)co * 9 + t) * cin + ci];
+        wup[i] = __float2bfloat16_rn(v);
+    }
+}
+
 // FP32 [n][ny][nx][3] -> BF16 chunked [n][2][ny][nx][8] (channels 3..15 zero); hw = ny nx
 __global__ void pack_input3_kernel(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, long long npix,
                                    long long hw) {
@@ -380,6 +398,7 @@ __global__ void solver_output_kernel(const float* __restrict__ out, const float*
 int cnn_refresh_weights(cnn_model* m, cudaStream_t st) {
     for (const Layer& l : m->layers) {
         { pack_weights_kernel<<<64, 256, 0, st>>>(m->master, l.off, l.cin, l.cout, l.cin_pad, l.npad, l.w, l.b); count_launch(); }
+        if (l.wup) { pack_up_weights_kernel<<<64, 256, 0, st>>>(m->master, l.off, l.cin, l.cout, l.cin_pad, l.npad, l.wup); count_launch(); }
         HELM_CK(cudaGetLastError());
     }
     return HELM_OK;
@@ -693,6 +712,7 @@ int create_zero(cnn_model** out, int levels, const int* widths) {
     for (Layer& l : m->layers) {
         if (s) break;
         s = malloc_m(m, &l.w, (size_t)l.npad * 9 * l.cin_pad);
+        if (!s && l.mode == 2) s = malloc_m(m, &l.wup, (size_t)l.npad * 16 * l.cin_pad);
         if (!s) s = malloc_m(m, &l.b, (size_t)l.npad);
     }
     if (s) { cnn_destroy(m); return s; }
@@ -700,6 +720,7 @@ int create_zero(cnn_model** out, int levels, const int* widths) {
     cudaMemset(m->err, 0, sizeof(int));
     for (Layer& l : m->layers) {
         cudaMemset(l.w, 0, (size_t)l.npad * 9 * l.cin_pad * sizeof(__nv_bfloat16));
+        if (l.wup) cudaMemset(l.wup, 0, (size_t)l.npad * 16 * l.cin_pad * sizeof(__nv_bfloat16));
         cudaMemset(l.b, 0, (size_t)l.npad * sizeof(float));
     }
     if (cudaDeviceSynchronize() != cudaSuccess) { set_error("cnn_create: device error"); cnn_destroy(m); return HELM_ECUDA; }
@@ -842,7 +863,7 @@ int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, 
     const long long nin = (long long)nb * hin * win, nin1 = (long long)(x1_bcast ? 1 : nb) * hin * win;
     const long long nout = (long long)nb * hout * wout;
     float *fx0 = nullptr, *fx1 = nullptr, *fw = nullptr, *fb = nullptr, *fr = nullptr, *fy = nullptr, *bp = nullptr;
-    __nv_bfloat16 *bx0 = nullptr, *bx1 = nullptr, *bw = nullptr, *br = nullptr, *by = nullptr;
+    __nv_bfloat16 *bx0 = nullptr, *bx1 = nullptr, *bw = nullptr, *bwup = nullptr, *br = nullptr, *by = nullptr;
     int* err = nullptr;
     int s = HELM_OK;
     auto ck = [&](cudaError_t e) { if (e != cudaSuccess && s == HELM_OK) { set_error(cudaGetErrorString(e)); s = HELM_ECUDA; } };
@@ -851,6 +872,7 @@ int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, 
     if (c1) { ck(cudaMalloc(&fx1, nin1 * c1 * sizeof(float))); ck(cudaMalloc(&bx1, nin1 * cp1 * sizeof(__nv_bfloat16))); }
     ck(cudaMalloc(&fw, (size_t)cout * 9 * cin * sizeof(float) + cout * sizeof(float)));
     ck(cudaMalloc(&bw, (size_t)npad * 9 * cinp * sizeof(__nv_bfloat16)));
+    if (mode == 2) ck(cudaMalloc(&bwup, (size_t)npad * 16 * cinp * sizeof(__nv_bfloat16)));
     ck(cudaMalloc(&bp, npad * sizeof(float)));
     ck(cudaMalloc(&fy, nout * cout * sizeof(float)));
     ck(cudaMalloc(&by, nout * npad * sizeof(__nv_bfloat16)));
@@ -883,6 +905,23 @@ int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, 
             hb[co] = hw[(size_t)cout * 9 * cin + co];
         }
         ck(cudaMemcpy(bw, hbw.data(), hbw.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+        if (mode == 2) {
+            // the phase-merged weights of the up layer (summed in FP32 in tap order, rounded once)
+            std::vector<float> acc((size_t)npad * 16 * cinp, 0.0f);
+            for (int co = 0; co < cout; ++co)
+                for (int t = 0; t < 9; ++t)
+                    for (int ph = 0; ph < 4; ++ph) {
+                        const int r = up_merged_index(ph >> 1, ph & 1, t / 3 - 1, t % 3 - 1);
+                        if (r >> 2 != ph) continue;
+                        for (int ci = 0; ci < cin; ++ci) {
+                            const int cpi = ci < c0 ? ci : cp0 + (ci - c0);
+                            acc[((size_t)co * 16 + r) * cinp + cpi] += hw[((size_t)co * 9 + t) * cin + ci];
+                        }
+                    }
+            std::vector<__nv_bfloat16> hup(acc.size());
+            for (size_t i = 0; i < acc.size(); ++i) hup[i] = __float2bfloat16_rn(acc[i]);
+            ck(cudaMemcpy(bwup, hup.data(), hup.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+        }
         ck(cudaMemcpy(bp, hb.data(), hb.size() * sizeof(float), cudaMemcpyHostToDevice));
         ck(cudaGetLastError());
     }
@@ -890,7 +929,8 @@ int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, 
         ConvArgs a;
         a.x0 = bx0; a.c0 = cp0; a.x1 = bx1; a.c1 = cp1; a.x1_bcast = x1_bcast; a.x1_map = nullptr;
         a.nb = nb; a.hin = hin; a.win = win; a.hout = hout; a.wout = wout; a.mode = mode;
-        a.w = bw; a.bias = bp; a.res = br; a.y = by; a.npad = npad; a.cstore = cout; a.relu = relu; a.out_fp32 = 0;
+        a.w = bw; a.wup = bwup; a.bias = bp; a.res = br; a.y = by; a.npad = npad; a.cstore = cout; a.relu = relu;
+        a.out_fp32 = 0;
         a.accum = 0;
         a.err = err;
         {
@@ -908,7 +948,7 @@ int cnn_conv3x3(const float* x0, int c0, const float* x1, int c1, int x1_bcast, 
         if (!s) ck(cudaMemcpy(y, fy, nout * cout * sizeof(float), cudaMemcpyDefault));
     }
     cudaFree(fx0); cudaFree(fx1); cudaFree(fw); cudaFree(fb); cudaFree(fr); cudaFree(fy); cudaFree(bp);
-    cudaFree(bx0); cudaFree(bx1); cudaFree(bw); cudaFree(br); cudaFree(by); cudaFree(err);
+    cudaFree(bx0); cudaFree(bx1); cudaFree(bw); cudaFree(bwup); cudaFree(br); cudaFree(by); cudaFree(err);
     return s;
 }
 

@@ -21,6 +21,7 @@ struct Layer {
     int relu;
     long long off;           // offset of this layer's weights in the flat vector
     __nv_bfloat16* w = nullptr;   // [npad][9][cin_pad]
+    __nv_bfloat16* wup = nullptr; // mode 2: phase-merged [npad][16][cin_pad] (up_merged_index)
     float* b = nullptr;           // [npad]
 };
 
@@ -159,7 +160,7 @@ class Runner {
         a.x0 = x0; a.c0 = c0; a.x1 = x1; a.c1 = c1; a.x1_bcast = x1_bcast; a.x1_map = x1_bcast == 2 ? zmap_ : nullptr;
         a.nb1 = x1_bcast == 1 ? 1 : (x1_bcast == 2 ? nctx_ : nb);
         a.nb = nb; a.hin = hin; a.win = win; a.hout = ho; a.wout = wo; a.mode = l.mode;
-        a.w = l.w; a.bias = l.b; a.res = res; a.y = y_fp32 ? y_fp32 : (void*)y;
+        a.w = l.w; a.wup = l.wup; a.bias = l.b; a.res = res; a.y = y_fp32 ? y_fp32 : (void*)y;
         a.npad = l.npad; a.cstore = l.cout; a.relu = l.relu; a.out_fp32 = y_fp32 ? 1 : 0; a.accum = 0;
         a.err = m_->err;
         int s;

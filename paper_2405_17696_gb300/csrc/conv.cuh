@@ -16,6 +16,17 @@ __host__ __device__ __forceinline__ size_t nc8(long long b, int c, long long pix
     return (((size_t)b * (size_t)(C >> 3) + (size_t)(c >> 3)) * (size_t)hw + (size_t)pix) * 8 + (size_t)(c & 7);
 }
 
+// Nearest x2 upsampling followed by a 3x3 convolution (mode 2) is, per output
+// parity p in {0, 1} along an axis, a 2-tap convolution on the coarse grid: the
+// fine node 2Y + p with tap d in {-1, 0, 1} reads the coarse node
+// floor((2Y + p + d) / 2) = Y + floor((p + d) / 2), which is Y + p - 1 + e for
+// e = up_phase_tap(p, d) in {0, 1}.  The weights of the taps that share e add up.
+__host__ __device__ __forceinline__ int up_phase_tap(int p, int d) { return (p + d + 2) / 2 - 1 - p + 1; }
+// merged tap of output parity ph = 2 py + px and coarse offset (ey, ex): row ph * 4 + 2 ey + ex
+__host__ __device__ __forceinline__ int up_merged_index(int py, int px, int dy, int dx) {
+    return (2 * py + px) * 4 + 2 * up_phase_tap(py, dy) + up_phase_tap(px, dx);
+}
+
 struct ConvArgs {
     const __nv_bfloat16* x0;   // [nb][c0/8][hin][win][8] (chunked layout, see nc8)
     int c0;
@@ -29,6 +40,8 @@ struct ConvArgs {
                                // 3 transpose of down: output on the fine grid, tap d of output node f reads
                                //   input node (f - 1 - d) / 2 when that is an integer inside the input
     const __nv_bfloat16* w;    // [npad][9][c0 + c1]
+    const __nv_bfloat16* wup = nullptr;   // mode 2: the phase-merged weights [npad][16][c0 + c1]
+                                          // (up_merged_index), which the tensor-map kernel needs
     const float* bias;         // [npad]
     const __nv_bfloat16* res;  // [nb][npad/8][hout][wout][8] added before the activation, or nullptr
     void* y;                   // bf16 [nb][npad/8][hout][wout][8], or fp32 [nb][hout][wout][cstore]

@@ -18,7 +18,11 @@
 //                                    element strides of 2), so that every tap is again a shift.
 //  2 nearest x2  (2Y+py, 2X+px)   -> coarse ((2Y+py+dy) >> 1, (2X+px+dx) >> 1); the coarse halo
 //                                    tile is staged as in mode 0 and each of the four output
-//                                    parities (py, px) is its own set of M blocks.
+//                                    parities (py, px) is its own set of M blocks.  Per parity
+//                                    the nine taps read only 2 x 2 coarse nodes, so the kernel
+//                                    takes the phase-merged weights (ConvArgs::wup, the taps
+//                                    that read the same node added up): four MMAs per M block
+//                                    and group instead of nine.
 //  3 transpose of mode 1 (the input gradient of a stride-2 layer): fine (2Y+py, 2X+px) takes
 //                                    tap (dy, dx) from coarse (Y + (py-1-dy)/2, X + (px-1-dx)/2)
 //                                    when both are integers; staged as mode 2.
@@ -157,8 +161,11 @@ __device__ __forceinline__ bool tap_source(int t, int py, int px, int pw, int* p
         *off = (dy == 1 ? pw : 0) + (dx == 1 ? 1 : 0);
         return true;
     } else if (MODE == 2) {
+        // merged tap t = 2 ey + ex of parity (py, px): coarse node (Y + py - 1 + ey, X + px - 1 + ex)
+        (void)dy;
+        (void)dx;
         *plane = 0;
-        *off = (((py + dy) >> 1) + 1) * pw + (((px + dx) >> 1) + 1);
+        *off = (py + (t >> 1)) * pw + (px + (t & 1));
         return true;
     } else {
         const int uy = py - 1 - dy, ux = px - 1 - dx;
@@ -269,7 +276,7 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
                 } else if (g.w4) {
                     tc::tma_load_4d(ws, &tm_w, 0, 0, 2 * gi, 0, &full[s]);
                 } else {
-                    for (int tap = 0; tap < 9; ++tap)
+                    for (int tap = 0; tap < (MODE == 2 ? 16 : 9); ++tap)
                         for (int h = 0; h < 2; ++h)
                             tc::tma_load_2d(ws + (tap * 2 + h) * wplane, &tm_w, tap * cin + gi * 16 + h * 8, 0,
                                             &full[s]);
@@ -434,24 +441,27 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
                     const uint32_t a16 = (tc::smem_u32(smem + (size_t)s * g.stage) & 0x3FFFFu) >> 4;
                     const uint32_t bw_lo = b_lo0 + a16 + ((uint32_t)wofs >> 4);
                     for (int ph = 0; ph < g.nph; ++ph) {
-                        uint32_t ao[9];   // A start of each tap for M block 0, descriptor low word
-                        bool use[9];
+                        constexpr int NT = MODE == 2 ? 4 : 9;   // mode 2: the parity's merged taps
+                        uint32_t ao[NT];   // A start of each tap for M block 0, descriptor low word
+                        bool use[NT];
 #pragma unroll
-                        for (int tap = 0; tap < 9; ++tap) {
+                        for (int tap = 0; tap < NT; ++tap) {
                             int pl, off;   // A offset in 16-byte units from the stage
                             use[tap] = tap_source<MODE>(tap, ph >> 1, ph & 1, g.pw, &pl, &off);
                             ao[tap] = a_lo0 + a16 + (uint32_t)(pl * (g.pstride >> 4) + off);
                         }
+                        // B of the parity's first tap (mode 2: the merged weights are [parity][4 taps])
+                        const uint32_t bph = MODE == 2 ? bw_lo + (uint32_t)(ph * 4) * tap_b16 : bw_lo;
                         uint32_t d = dbase + (uint32_t)(ph * g.mb * a.npad);
                         for (int m = 0; m < g.mb; ++m, d += (uint32_t)a.npad) {
                             const uint32_t mo = (uint32_t)(m * 128);   // 128 pixels of 16 bytes
                             uint32_t accum = gi == 0 ? 0u : 1u;
 #pragma unroll
-                            for (int tap = 0; tap < 9; ++tap) {
+                            for (int tap = 0; tap < NT; ++tap) {
                                 if (!use[tap]) continue;
                                 if (leader) {
                                     const uint64_t ad = ((uint64_t)a_hi << 32) | (ao[tap] + mo);
-                                    const uint64_t bd = ((uint64_t)b_hi << 32) | (bw_lo + (uint32_t)tap * tap_b16);
+                                    const uint64_t bd = ((uint64_t)b_hi << 32) | (bph + (uint32_t)tap * tap_b16);
                                     tc::mma_bf16(d, ad, bd, idesc, accum);
                                 }
                                 accum = 1u;
@@ -792,13 +802,14 @@ bool tma_map_act(CUtensorMap* m, const void* base, int c, int w, int h, int n, i
 
 namespace {
 
-// weights [npad][9][cin] viewed as a 4-D tensor (8 channels, npad rows, cin/8
-// chunks, 9 taps); box = (8, npad, 2, 9): the 16-channel group's 18 core-matrix
-// planes (tap, half) in one copy, laid out as [tap][half][npad][8].
-bool encode_w4(CUtensorMap* m, const void* base, int cin, int npad) {
-    const cuuint64_t dims[4] = {8u, (cuuint64_t)npad, (cuuint64_t)(cin / 8), 9u};
-    const cuuint64_t strides[3] = {(cuuint64_t)9 * cin * 2, 16u, (cuuint64_t)cin * 2};
-    const cuuint32_t box[4] = {8u, (cuuint32_t)npad, 2u, 9u};
+// weights [npad][ntap][cin] (ntap 9, or 16 merged taps in mode 2) viewed as a 4-D
+// tensor (8 channels, npad rows, cin/8 chunks, ntap taps); box = (8, npad, 2, ntap):
+// the 16-channel group's 2 ntap core-matrix planes (tap, half) in one copy, laid out
+// as [tap][half][npad][8].
+bool encode_w4(CUtensorMap* m, const void* base, int cin, int npad, int ntap) {
+    const cuuint64_t dims[4] = {8u, (cuuint64_t)npad, (cuuint64_t)(cin / 8), (cuuint64_t)ntap};
+    const cuuint64_t strides[3] = {(cuuint64_t)ntap * cin * 2, 16u, (cuuint64_t)cin * 2};
+    const cuuint32_t box[4] = {8u, (cuuint32_t)npad, 2u, (cuuint32_t)ntap};
     const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
     const CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides,
                                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -832,10 +843,10 @@ bool encode_w6(CUtensorMap* m, const void* base, int cin, int npad) {
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// weights [npad][9 * cin] viewed as 2-D; box = 8 input channels x npad rows.
-bool encode_w(CUtensorMap* m, const void* base, int cin, int npad) {
-    const cuuint64_t dims[2] = {(cuuint64_t)9 * cin, (cuuint64_t)npad};
-    const cuuint64_t strides[1] = {(cuuint64_t)9 * cin * 2};
+// weights [npad][ntap * cin] viewed as 2-D; box = 8 input channels x npad rows.
+bool encode_w(CUtensorMap* m, const void* base, int cin, int npad, int ntap) {
+    const cuuint64_t dims[2] = {(cuuint64_t)ntap * cin, (cuuint64_t)npad};
+    const cuuint64_t strides[1] = {(cuuint64_t)ntap * cin * 2};
     const cuuint32_t box[2] = {8u, (cuuint32_t)npad};
     const cuuint32_t estr[2] = {1u, 1u};
     return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
@@ -985,7 +996,7 @@ Geometry plan(const ConvArgs& a, const TileCfg& t) {
         g.pw = g.tw + 2;
     }
     const int halo = mode == 1 ? 1 : 2;        // extra staged rows
-    g.wbytes = 9 * 2 * a.npad * 16;
+    g.wbytes = (mode == 2 ? 16 : 9) * 2 * a.npad * 16;   // mode 2: 4 parities x 4 merged taps
     // TMEM per accumulator buffer: 128 columns (two CTAs per SM), or 256 when one
     // block per parity already needs more (one CTA per SM)
     // (wide layers: 256, so that packed rows fill the 128-pixel M blocks)
@@ -1158,6 +1169,8 @@ int launch_cfg(const ConvArgs& a_in, cudaStream_t st, const TileCfg& t) {
     if ((reinterpret_cast<uintptr_t>(a.x0) & 15) || (a.c1 && (reinterpret_cast<uintptr_t>(a.x1) & 15)) ||
         (reinterpret_cast<uintptr_t>(a.w) & 15))
         return HELM_EINVAL;
+    // an up layer runs on its phase-merged weights
+    if (a.mode == 2 && (!a.wup || (reinterpret_cast<uintptr_t>(a.wup) & 15))) return HELM_EINVAL;
     Geometry g{};
     int mode = a.mode;
     if (plan_launch(a, t, false, &mode, &g) != HELM_OK) return HELM_EINVAL;
@@ -1183,8 +1196,10 @@ int launch_cfg(const ConvArgs& a_in, cudaStream_t st, const TileCfg& t) {
         tm1 = tm0;
     }
     if (a.mode != 4 && a.mode != 6) {
-        g.w4 = encode_w4(&tmw, a.w, a.c0 + a.c1, a.npad) ? 1 : 0;
-        if (!g.w4 && !encode_w(&tmw, a.w, a.c0 + a.c1, a.npad)) return HELM_EINVAL;
+        const void* wsrc = a.mode == 2 ? (const void*)a.wup : (const void*)a.w;
+        const int ntap = a.mode == 2 ? 16 : 9;
+        g.w4 = encode_w4(&tmw, wsrc, a.c0 + a.c1, a.npad, ntap) ? 1 : 0;
+        if (!g.w4 && !encode_w(&tmw, wsrc, a.c0 + a.c1, a.npad, ntap)) return HELM_EINVAL;
     }
     switch (a.mode) {
         case 4: ++g_launch_narrow; return launch_mode<4>(tm0, tm1, tmw, a, g, st);

@@ -32,12 +32,35 @@ def _taps(mode, py, px, pw):
         elif mode == 1:
             out.append(((2 if dy == 0 else 0) + (1 if dx == 0 else 0), (pw if dy == 1 else 0) + (1 if dx == 1 else 0)))
         elif mode == 2:
-            out.append((0, (((py + dy) >> 1) + 1) * pw + ((px + dx) >> 1) + 1))
+            # the parity's four merged taps (ey, ex): coarse node (Y + py - 1 + ey, X + px - 1 + ex)
+            if t < 4:
+                out.append((0, (py + (t >> 1)) * pw + px + (t & 1)))
         else:
             uy, ux = py - 1 - dy, px - 1 - dx
             if uy % 2 == 0 and ux % 2 == 0:
                 out.append((0, ((uy >> 1) + 1) * pw + (ux >> 1) + 1))
     return out
+
+
+def test_merged_up_taps_read_the_nodes_of_the_nine_taps():
+    """Nearest x2 upsampling then a 3x3 convolution: per output parity the nine taps read
+    the 2 x 2 coarse nodes that the four merged taps of the kernel read, each tap the node
+    of its merged tap (fine node 2Y + p, tap d -> coarse node floor((2Y + p + d) / 2))."""
+    pw = 13
+    for py in (0, 1):
+        for px in (0, 1):
+            merged = [off for _, off in _taps(2, py, px, pw)]
+            assert len(merged) == 4 and len(set(merged)) == 4
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    for Y in range(3):
+                        cy = (2 * Y + py + dy) // 2 - Y           # coarse row offset of the tap
+                        cx = (2 * Y + px + dx) // 2 - Y
+                        ey, ex = (py + dy + 2) // 2 - 1 - py + 1, (px + dx + 2) // 2 - 1 - px + 1
+                        assert ey in (0, 1) and ex in (0, 1)
+                        assert cy == py - 1 + ey and cx == px - 1 + ex
+                        # staged with a one-node halo: offset of node (cy, cx) from the tile's pixel
+                        assert merged[2 * ey + ex] == (cy + 1) * pw + cx + 1
 
 
 def _check(g, mode, npad, hin, win, nb):
@@ -54,7 +77,7 @@ def _check(g, mode, npad, hin, win, nb):
     assert g["plane"] == (g["rows"] + halo) * g["pw"] * 16
     assert g["pstride"] >= 2 * g["plane"] and g["pstride"] % 128 == 0
     assert g["stage"] == g["nplanes"] * g["pstride"] + g["wbytes"] and g["stage"] % 128 == 0
-    assert g["wbytes"] == 9 * 2 * npad * 16
+    assert g["wbytes"] == (16 if mode == 2 else 9) * 2 * npad * 16   # up: 4 parities x 4 merged taps
     assert 2 <= g["ns"] <= 6 and g["ns"] * g["stage"] <= 200 * 1024
     assert g["tmem_cols"] <= 512 and g["tmem_cols"] >= 32 and g["tmem_cols"] & (g["tmem_cols"] - 1) == 0
     stage_end = g["stage"]

@@ -40,6 +40,10 @@ MODES = {"same": 0, "down": 1, "up": 2}
     (16, 16, 0, 16, "same", 12, 20, 2, False, True),     # concat of two 16-channel tensors
     (16, 0, 0, 32, "down", 24, 16, 2, False, True),
     (128, 0, 0, 64, "up", 6, 10, 2, False, True),
+    (32, 0, 0, 16, "up", 40, 70, 2, False, True),        # the last decoder layer's shape: many tiles, ragged
+    (64, 0, 0, 32, "up", 17, 30, 2, True, True),         # residual on the fine grid
+    (32, 16, 0, 16, "up", 9, 14, 2, False, False),       # concat input, no activation
+    (16, 0, 0, 64, "up", 5, 130, 1, False, True),        # 130 coarse columns: two column tiles
     (128, 128, 0, 128, "same", 8, 8, 2, False, True),
     (16, 0, 0, 2, "same", 16, 20, 2, False, False),      # output layer, 2 channels
     (32, 16, 0, 16, "same", 6, 200, 2, True, True),      # 3 channel groups, wide rows: 2 column tiles
@@ -49,7 +53,8 @@ MODES = {"same": 0, "down": 1, "up": 2}
 ])
 @pytest.mark.parametrize("path", [0, 1, 2, 3, "single"])
 def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res, relu, path):
-    """path 0: the TMA halo-tile kernel; path 1: the gather kernel; path 2: the TMA
+    """path 0: the TMA halo-tile kernel (up layers on phase-merged weights); path 1: the
+    gather kernel; path 2: the TMA
     kernel with the column taps in N for 16-channel same-grid layers; path 3: the TMA
     kernel with the three tap rows in N for 16- and 32-channel same-grid layers; "single":
     the TMA kernel with one accumulator buffer."""
@@ -91,6 +96,12 @@ def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res,
     assert native.cnn_conv_rowtaps_launches() - n6 == (1 if rowtaps else 0)
     err = np.abs(y - ref)
     tol = 2.0 ** -7 * np.abs(ref) + 1e-3 * np.abs(ref).max()
+    if mode == "up" and used_tma:
+        # the tensor-map kernel runs an up layer on its phase-merged weights: per output parity
+        # the taps that read the same coarse node are added in FP32 and rounded to BF16 once,
+        # an error of at most 2^-8 |w_a + w_b + ...| <= 2^-8 (|w_a| + |w_b| + ...) per merged
+        # weight, so at most 2^-8 sum |w| |x| over the nine taps per output
+        tol = tol + 2.0 ** -8 * cnn.conv_forward(np.abs(xin), np.abs(w), np.zeros(cout), mode)
     assert np.all(err <= tol), (err.max(), np.abs(ref).max())
 
 
