@@ -41,8 +41,10 @@ class FwiConfig:
     mg_levels: int = 3
     max_rhs: int = 64
     seed: int = media.SEED_SOURCES
-    reg_kind: int = 0               # regulariser of Sec. 5.1: 0 none, 1 R_diff, 2 R_high
-    reg_alpha: float = 0.0          # its weight; the reference model is the model the run starts from
+    reg_kind: object = 0            # regulariser of Sec. 5.1: 0 none, 1 R_diff, 2 R_high; or one per
+                                    # window (e.g. R_high on the first sweeps, then R_diff, Sec. 5.3)
+    reg_alpha: object = 0.0         # its weight (or one per window); the reference model is the model
+                                    # the run starts from, kept fixed
 
 
 @dataclass
@@ -108,17 +110,22 @@ def run_windows(native, m, nx0, nz0, windows, cfg: FwiConfig, net=None, log=None
     iterations update that copy, and the update is resampled back and added to m."""
     import torch
     hist = FwiHistory()
+    pick = lambda v, i: v[i] if isinstance(v, (list, tuple)) else v
+    m_init = m.clone()   # the regulariser's reference model: the initial guess, on every window's grid
     for wi, win in enumerate(windows):
         same = (win.nx, win.nz) == (nx0, nz0)
         if same:
-            mw = m
+            mw, m_ref = m, m_init
         else:
             mw = torch.empty((win.nz, win.nx), dtype=torch.float32, device="cuda")
             native.helm_resample(m, nx0, nz0, mw, win.nx, win.nz)
             mw0 = mw.clone()
-        c = FwiConfig(**{**cfg.__dict__, "windows": [win.freqs]})
+            m_ref = torch.empty_like(mw)
+            native.helm_resample(m_init, nx0, nz0, m_ref, win.nx, win.nz)
+        c = FwiConfig(**{**cfg.__dict__, "windows": [win.freqs], "reg_kind": pick(cfg.reg_kind, wi),
+                         "reg_alpha": pick(cfg.reg_alpha, wi)})
         h = run(native, mw, win.gamma, win.nx, win.nz, win.hx, win.hz, win.src_idx, win.rcv_idx, win.d_obs,
-                win.freqs, c, net=net, log=log, window_offset=wi)
+                win.freqs, c, net=net, log=log, window_offset=wi, m_ref=m_ref)
         hist.rows += h.rows
         if not same:
             native.helm_resample(mw, win.nx, win.nz, m, nx0, nz0, 1.0, 1.0)     # m += R(m_w) - R(m_w0)
@@ -127,21 +134,30 @@ def run_windows(native, m, nx0, nz0, windows, cfg: FwiConfig, net=None, log=None
 
 
 def run(native, m, gamma, nx, nz, hx, hz, src_idx, rcv_idx, d_obs, freqs_hz, cfg: FwiConfig, net=None,
-        log=None, window_offset: int = 0) -> FwiHistory:
+        log=None, window_offset: int = 0, m_ref=None) -> FwiHistory:
     """Alg. 1 on the model m (float32 CUDA tensor [nz][nx] of m = 1 / v^2, updated in
     place).  d_obs: observed data [nfreq][nsrc][nrcv] (CUDA tensor) at freqs_hz, ordered as
     the windows' frequencies are drawn from.  net: the encoder-solver network (CNN-FGMRES
-    with retraining when cfg.retrain_steps > 0), or None for MG-FGMRES."""
+    with retraining when cfg.retrain_steps > 0), or None for MG-FGMRES.  m_ref: the
+    regulariser's reference model on this grid (default: m as the run starts)."""
     import torch
     hist = FwiHistory()
     rng = media.rng(cfg.seed)
     gam = torch.as_tensor(gamma, dtype=torch.float32, device="cuda").contiguous()
     fidx = {f: i for i, f in enumerate(freqs_hz)}
-    opts = native.fwi_default_gn_opts(tol=cfg.tol, tol_sens=cfg.tol_sens, cg_iters=cfg.cg_iters,
-                                      m_min=1.0 / cfg.v_max ** 2, m_max=1.0 / cfg.v_min ** 2,
-                                      reg_kind=cfg.reg_kind, alpha=cfg.reg_alpha)
-    m_ref = m.clone() if cfg.reg_kind and cfg.reg_alpha > 0 else None
+    nwin = len(cfg.windows)
+    per_window = lambda v: list(v) if isinstance(v, (list, tuple)) else [v] * nwin
+    kinds, alphas = per_window(cfg.reg_kind), per_window(cfg.reg_alpha)
+    if len(kinds) != nwin or len(alphas) != nwin:
+        raise ValueError("reg_kind / reg_alpha: one value, or one per window")
+    if not any(k and a > 0 for k, a in zip(kinds, alphas)):
+        m_ref = None
+    elif m_ref is None:
+        m_ref = m.clone()
     for wi, window in enumerate(cfg.windows):
+        opts = native.fwi_default_gn_opts(tol=cfg.tol, tol_sens=cfg.tol_sens, cg_iters=cfg.cg_iters,
+                                          m_min=1.0 / cfg.v_max ** 2, m_max=1.0 / cfg.v_min ** 2,
+                                          reg_kind=int(kinds[wi]), alpha=float(alphas[wi]))
         om = torch.tensor([2 * math.pi * f for f in window], dtype=torch.float32, device="cuda")
         dw = torch.stack([d_obs[fidx[f]] for f in window]).contiguous()
         kappa = torch.empty_like(m)

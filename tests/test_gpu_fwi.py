@@ -242,3 +242,45 @@ def test_windows_on_their_own_grids(native):
     for r in hist.rows:
         assert r["misfit_after"] <= r["misfit_before"], r
     assert err1 < err0, (err0, err1)
+
+
+def test_regulariser_schedule_across_window_grids(native):
+    """Alg. 1 with R_high on the first window and R_diff on the second (the order of
+    Sec. 5.3), each window on its own grid, the reference model the initial guess resampled
+    to that grid: on the first iteration of the first window m = m_ref, so the objective is
+    the misfit; on the second window's grid the model has moved, so alpha R > 0; every
+    accepted step lowers the objective and the model still moves toward the truth."""
+    from paper_2405_17696_gb300 import fwi as FWI
+    nx0, nz0, h0 = 192, 96, 20.0
+    c_true = media.layered_velocity(nx0, nz0, seed=4, n_layers=6)
+    c0 = media.gaussian_smooth(c_true, 6.0)
+    lx, lz = nx0 * h0, nz0 * h0
+    m = torch.from_numpy((1.0 / c0.astype(np.float64) ** 2).astype(np.float32)).cuda()
+    m_true = torch.from_numpy((1.0 / c_true.astype(np.float64) ** 2).astype(np.float32)).cuda()
+    windows = []
+    for f in (3.0, 5.0):
+        nx, nz, hx, hz = FWI.window_grid_size(lx, lz, f)
+        kt = torch.empty((nz, nx), dtype=torch.float32, device="cuda")
+        native.helm_resample(torch.from_numpy(media.kappa_of(c_true)).cuda(), nx0, nz0, kt, nx, nz)
+        gam = media.abl_gamma(nx, nz, max(4, nx // 16))
+        src = [2 * nx + 2 + (nx - 4) * s // 8 for s in range(8)]
+        rcv = [2 * nx + ix for ix in range(1, nx - 1, 2)]
+        d, _ = FWI.observed_data(native, kt, gam, nx, nz, hx, hz, [f], native.Survey(src, rcv))
+        windows.append(FWI.WindowGrid([f], nx, nz, hx, hz, gam, src, rcv, d))
+    err0 = float(torch.linalg.norm(m - m_true) / torch.linalg.norm(m_true))
+    cfg = FWI.FwiConfig(windows=[], gn_iters=2, cg_iters=3, sim_sources=0, max_rhs=8,
+                        reg_kind=[2, 1], reg_alpha=[1e17, 1e14])
+    hist = FWI.run_windows(native, m, nx0, nz0, windows, cfg)
+    err1 = float(torch.linalg.norm(m - m_true) / torch.linalg.norm(m_true))
+    rows = hist.rows
+    assert len(rows) == 4
+    assert rows[0]["objective_before"] == rows[0]["misfit_before"]
+    assert rows[2]["objective_before"] > rows[2]["misfit_before"]
+    for r in rows:
+        assert r["objective_after"] <= r["objective_before"], r
+        assert r["objective_after"] >= r["misfit_after"]
+    assert err1 < err0, (err0, err1)
+    with pytest.raises(ValueError):
+        FWI.run(native, m, windows[0].gamma, windows[0].nx, windows[0].nz, windows[0].hx, windows[0].hz,
+                windows[0].src_idx, windows[0].rcv_idx, windows[0].d_obs, [3.0],
+                FWI.FwiConfig(windows=[[3.0]], reg_kind=[1, 2], reg_alpha=1.0))
