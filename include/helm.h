@@ -485,7 +485,9 @@ void cnn_autotune_reset(void);
  * cnn_set_conv_ring / cnn_set_conv_tiling (0 = default); narrow = 1 selects the
  * column-taps-in-N variant for 16-channel same-grid layers, narrow = 2 the
  * row-taps-in-N variant for 16- and 32-channel ones, narrow = 3 the tiling with one
- * accumulator buffer of up to 512 TMEM columns (any mode; an autotuner candidate).
+ * accumulator buffer of up to 512 TMEM columns (any mode; an autotuner candidate),
+ * narrow = 4 an up layer with a tile per output row parity (cnn_set_conv_upsplit; 2
+ * parities per tile, tiles counted per parity), narrow = 5 both of the last two.
  * out19 = {tiles,
  * tile width, tile rows, staged row pitch, M blocks per parity, parities,
  * parity sub-planes, plane bytes, parity stride bytes, weight bytes, stage
@@ -510,6 +512,13 @@ int cnn_set_conv_tiling(int max_rows);
  * default (two buffers, or the autotuned choice).  Process-wide; takes precedence over
  * the tuned table like the other tiling knobs.  HELM_EINVAL outside [0, 2]. */
 int cnn_set_conv_buffers(int nbuf);
+/* Tiling of the up layers (nearest x2 then a 3x3 convolution) in the TMA halo-tile
+ * kernel: 1 = a tile computes one output row parity (its two column parities), so a
+ * stage holds the 8 merged taps of that parity and a tile twice the rows; the tiles of
+ * the two parities alternate.  0 = the default (all four parities per tile, or the
+ * autotuned choice).  Process-wide; takes precedence over the tuned table like the other
+ * tiling knobs.  HELM_EINVAL outside [0, 1]. */
+int cnn_set_conv_upsplit(int on);
 /* Shared-memory budgets of the TMA halo-tile kernel: at most stage_kb KB per
  * stage (one tile's 16-channel group plus its weights; taller tiles are cut
  * until a stage fits) and ring_kb KB for the ring of stages (2 to 6 stages; a

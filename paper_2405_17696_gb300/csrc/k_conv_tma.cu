@@ -121,6 +121,8 @@ struct Geometry {
                              // the MMAs fill the other; 1: twice the M blocks per tile)
     int nwg;                 // mode 6: epilogue warpgroups that take output rows
     int chunk;               // mode 6: staged rows per commit
+    int psplit;              // mode 2: a tile computes one output row parity py (nph = 2: px), the
+                             // tiles of the two parities alternate; 0: all four parities per tile
     int stage;               // bytes of one stage
     int groups, groups0;     // 16-channel groups in total / taken from x0
     int ns;                  // stages in the ring
@@ -221,8 +223,11 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
     const int chunk_bytes = g.plane;                 // K-adjacent core matrices (LBO)
     const int wofs = g.nplanes * g.pstride;          // the group's weights within a stage
 
+    // the output row parity of tile k when the parities are split (0 otherwise)
+    auto tile_py = [&](int k) { return g.psplit ? (((int)blockIdx.x + k * (int)gridDim.x) & 1) : 0; };
     auto tile_coords = [&](int k, int& b, int& xs, int& ys) {
         int t = (int)blockIdx.x + k * (int)gridDim.x;
+        if (g.psplit) t >>= 1;
         const int tx = t % g.tiles_x;
         t /= g.tiles_x;
         const int ty = t % g.tiles_y;
@@ -274,11 +279,14 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
                     // mode 6 [dx][half][dy][npad][8]: the B operand of column shift dx is 3 npad rows (dy, o)
                     tc::tma_load_5d(ws, &tm_w, 0, 0, 0, 2 * gi, 0, &full[s]);
                 } else if (g.w4) {
-                    tc::tma_load_4d(ws, &tm_w, 0, 0, 2 * gi, 0, &full[s]);
+                    // split parities: the 8 merged taps of the tile's row parity
+                    tc::tma_load_4d(ws, &tm_w, 0, 0, 2 * gi, 8 * tile_py(k), &full[s]);
                 } else {
-                    for (int tap = 0; tap < (MODE == 2 ? 16 : 9); ++tap)
+                    const int t0 = 8 * tile_py(k);
+                    const int nt = MODE == 2 ? (g.psplit ? 8 : 16) : 9;
+                    for (int tap = 0; tap < nt; ++tap)
                         for (int h = 0; h < 2; ++h)
-                            tc::tma_load_2d(ws + (tap * 2 + h) * wplane, &tm_w, tap * cin + gi * 16 + h * 8, 0,
+                            tc::tma_load_2d(ws + (tap * 2 + h) * wplane, &tm_w, (t0 + tap) * cin + gi * 16 + h * 8, 0,
                                             &full[s]);
                 }
             }
@@ -444,10 +452,11 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
                         constexpr int NT = MODE == 2 ? 4 : 9;   // mode 2: the parity's merged taps
                         uint32_t ao[NT];   // A start of each tap for M block 0, descriptor low word
                         bool use[NT];
+                        const int py = g.psplit ? tile_py(k) : ph >> 1, px = g.psplit ? ph : ph & 1;
 #pragma unroll
                         for (int tap = 0; tap < NT; ++tap) {
                             int pl, off;   // A offset in 16-byte units from the stage
-                            use[tap] = tap_source<MODE>(tap, ph >> 1, ph & 1, g.pw, &pl, &off);
+                            use[tap] = tap_source<MODE>(tap, py, px, g.pw, &pl, &off);
                             ao[tap] = a_lo0 + a16 + (uint32_t)(pl * (g.pstride >> 4) + off);
                         }
                         // B of the parity's first tap (mode 2: the merged weights are [parity][4 taps])
@@ -694,8 +703,8 @@ __global__ void __launch_bounds__(threads_of(MODE)) conv3x3_tma_kernel(const __g
                     m_prev = m;
                     int oy = ys + yy, ox = xs + xx;
                     if (MODE == 2 || MODE == 3) {
-                        oy = 2 * oy + (ph >> 1);
-                        ox = 2 * ox + (ph & 1);
+                        oy = 2 * oy + (g.psplit ? tile_py(k) : ph >> 1);
+                        ox = 2 * ox + (g.psplit ? ph : ph & 1);
                     }
                     const bool valid = xx < g.tw && yy < g.rows && oy < a.hout && ox < a.wout;
                     const long long pix = (long long)oy * a.wout + ox;
@@ -803,13 +812,14 @@ bool tma_map_act(CUtensorMap* m, const void* base, int c, int w, int h, int n, i
 namespace {
 
 // weights [npad][ntap][cin] (ntap 9, or 16 merged taps in mode 2) viewed as a 4-D
-// tensor (8 channels, npad rows, cin/8 chunks, ntap taps); box = (8, npad, 2, ntap):
-// the 16-channel group's 2 ntap core-matrix planes (tap, half) in one copy, laid out
-// as [tap][half][npad][8].
-bool encode_w4(CUtensorMap* m, const void* base, int cin, int npad, int ntap) {
+// tensor (8 channels, npad rows, cin/8 chunks, ntap taps); box = (8, npad, 2, box_taps):
+// box_taps consecutive taps' core-matrix planes (tap, half) of a 16-channel group in
+// one copy, laid out as [tap][half][npad][8] (mode 2 with split parities: the 8 taps
+// of one output row parity).
+bool encode_w4(CUtensorMap* m, const void* base, int cin, int npad, int ntap, int box_taps) {
     const cuuint64_t dims[4] = {8u, (cuuint64_t)npad, (cuuint64_t)(cin / 8), (cuuint64_t)ntap};
     const cuuint64_t strides[3] = {(cuuint64_t)ntap * cin * 2, 16u, (cuuint64_t)cin * 2};
-    const cuuint32_t box[4] = {8u, (cuuint32_t)npad, 2u, (cuuint32_t)ntap};
+    const cuuint32_t box[4] = {8u, (cuuint32_t)npad, 2u, (cuuint32_t)box_taps};
     const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
     const CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides,
                                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -862,9 +872,11 @@ std::atomic<int> g_rows_cap{0};   // tile-height limit set by cnn_set_conv_tilin
 struct TileCfg {
     int rows_cap = 0, stage_kb = 0, ring_kb = 0, narrow = 0;
     int single = 0;   // modes 0-3: one accumulator buffer of up to 512 TMEM columns
+    int upsplit = 0;  // mode 2: a tile per output row parity (half the weights per stage, twice the rows)
 };
 std::atomic<int> g_stage_kb{0}, g_ring_kb{0};
 std::atomic<int> g_single{0};   // one accumulator buffer, set by cnn_set_conv_buffers
+std::atomic<int> g_upsplit{0};  // up layers: a tile per output row parity, set by cnn_set_conv_upsplit
 std::atomic<long long> g_launch_narrow{0};   // launches of mode 4
 std::atomic<long long> g_launch_rowtaps{0};  // launches of mode 6   // stage / ring budgets set by cnn_set_conv_ring (0 = default)
 int g_last_launch[6] = {0, 0, 0, 0, 0, 0};   // grid, CTAs per SM, CTAs registers/smem allow, shared memory,
@@ -983,7 +995,8 @@ Geometry plan(const ConvArgs& a, const TileCfg& t) {
     const int H = mode >= 2 ? a.hin : a.hout, W = mode >= 2 ? a.win : a.wout;
     g.groups = (a.c0 + a.c1) / 16;
     g.groups0 = a.c0 / 16;
-    g.nph = mode >= 2 ? 4 : 1;
+    g.psplit = mode == 2 && t.upsplit ? 1 : 0;
+    g.nph = mode >= 2 ? (g.psplit ? 2 : 4) : 1;
     g.nplanes = mode == 1 ? 4 : 1;
     if (mode == 1) {
         g.tw = W >= 127 ? 127 : W;   // 2 (tw + 1) traversed columns fit a 256-element box
@@ -996,7 +1009,7 @@ Geometry plan(const ConvArgs& a, const TileCfg& t) {
         g.pw = g.tw + 2;
     }
     const int halo = mode == 1 ? 1 : 2;        // extra staged rows
-    g.wbytes = (mode == 2 ? 16 : 9) * 2 * a.npad * 16;   // mode 2: 4 parities x 4 merged taps
+    g.wbytes = (mode == 2 ? (g.psplit ? 8 : 16) : 9) * 2 * a.npad * 16;   // mode 2: parities x 4 merged taps
     // TMEM per accumulator buffer: 128 columns (two CTAs per SM), or 256 when one
     // block per parity already needs more (one CTA per SM)
     // (wide layers: 256, so that packed rows fill the 128-pixel M blocks)
@@ -1040,7 +1053,7 @@ Geometry plan(const ConvArgs& a, const TileCfg& t) {
     uint32_t cols = 32;
     while (cols < (uint32_t)g.nbuf * g.acc_cols) cols <<= 1;
     g.tmem_cols = cols;
-    g.tiles = g.tiles_x * g.tiles_y * a.nb;
+    g.tiles = g.tiles_x * g.tiles_y * a.nb * (g.psplit ? 2 : 1);
     return g;
 }
 
@@ -1198,7 +1211,7 @@ int launch_cfg(const ConvArgs& a_in, cudaStream_t st, const TileCfg& t) {
     if (a.mode != 4 && a.mode != 6) {
         const void* wsrc = a.mode == 2 ? (const void*)a.wup : (const void*)a.w;
         const int ntap = a.mode == 2 ? 16 : 9;
-        g.w4 = encode_w4(&tmw, wsrc, a.c0 + a.c1, a.npad, ntap) ? 1 : 0;
+        g.w4 = encode_w4(&tmw, wsrc, a.c0 + a.c1, a.npad, ntap, g.psplit ? 8 : ntap) ? 1 : 0;
         if (!g.w4 && !encode_w(&tmw, wsrc, a.c0 + a.c1, a.npad, ntap)) return HELM_EINVAL;
     }
     switch (a.mode) {
@@ -1261,6 +1274,19 @@ int tune_and_launch(const ConvArgs& a, cudaStream_t st, const std::string& key, 
         c.single = 1;
         cands.push_back(c);
     }
+    if (a.mode == 2) {
+        // a tile per output row parity: with the default budgets, a larger ring, one buffer
+        const int v[][3] = {{0, 0, 0}, {100, 200, 0}, {0, 0, 1}, {47, 200, 1}};
+        for (const auto& x : v) {
+            TileCfg c = base;
+            c.narrow = 0;
+            c.upsplit = 1;
+            c.stage_kb = x[0];
+            c.ring_kb = x[1];
+            c.single = x[2];
+            cands.push_back(c);
+        }
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
@@ -1309,8 +1335,9 @@ int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st, int narrow) {
     t.ring_kb = g_ring_kb.load();
     t.narrow = narrow;
     t.single = g_single.load();
+    t.upsplit = g_upsplit.load();
     // explicit tiling knobs take precedence over the tuned table
-    if (t.rows_cap || t.stage_kb || t.ring_kb || t.single) return launch_cfg(a, st, t);
+    if (t.rows_cap || t.stage_kb || t.ring_kb || t.single || t.upsplit) return launch_cfg(a, st, t);
     const std::string key = shape_key(a);
     bool tune = false;
     {
@@ -1347,6 +1374,15 @@ extern "C" int cnn_set_conv_buffers(int nbuf) {
     return HELM_OK;
 }
 
+extern "C" int cnn_set_conv_upsplit(int on) {
+    if (on < 0 || on > 1) {
+        helm::set_error("cnn_set_conv_upsplit: on must be 0 (automatic) or 1");
+        return HELM_EINVAL;
+    }
+    helm::g_upsplit.store(on);
+    return HELM_OK;
+}
+
 extern "C" int cnn_set_conv_tiling(int max_rows) {
     if (max_rows < 0 || max_rows > 254) {
         helm::set_error("cnn_set_conv_tiling: max_rows must be in [0, 254]");
@@ -1376,7 +1412,7 @@ extern "C" long long cnn_conv_rowtaps_launches(void) { return helm::g_launch_row
 extern "C" int cnn_conv_plan(int mode, int c0, int c1, int npad, int hin, int win, int nb, int stage_kb,
                              int ring_kb, int rows_cap, int narrow, int* out19) {
     if (!out19 || mode < 0 || mode > 3 || c0 < 16 || c0 % 16 || c1 < 0 || c1 % 16 || nb < 1 || hin < 1 ||
-        win < 1 || (npad != 16 && npad % 32) || npad > 128 || narrow < 0 || narrow > 3) {
+        win < 1 || (npad != 16 && npad % 32) || npad > 128 || narrow < 0 || narrow > 5) {
         helm::set_error("cnn_conv_plan: invalid layer shape");
         return HELM_EINVAL;
     }
@@ -1394,8 +1430,9 @@ extern "C" int cnn_conv_plan(int mode, int c0, int c1, int npad, int hin, int wi
     t.rows_cap = rows_cap;
     t.stage_kb = stage_kb;
     t.ring_kb = ring_kb;
-    t.narrow = narrow == 3 ? 0 : narrow;
-    t.single = narrow == 3 ? 1 : 0;
+    t.narrow = narrow >= 3 ? 0 : narrow;
+    t.single = narrow == 3 || narrow == 5 ? 1 : 0;
+    t.upsplit = narrow >= 4 ? 1 : 0;
     helm::Geometry g{};
     int used = mode;
     const int s = helm::plan_launch(a, t, false, &used, &g);

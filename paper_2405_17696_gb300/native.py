@@ -130,6 +130,8 @@ def _load():
     lib.cnn_set_conv_tiling.restype = ip
     lib.cnn_set_conv_buffers.argtypes = [ip]
     lib.cnn_set_conv_buffers.restype = ip
+    lib.cnn_set_conv_upsplit.argtypes = [ip]
+    lib.cnn_set_conv_upsplit.restype = ip
     lib.cnn_conv_plan.argtypes = [ip] * 11 + [ctypes.POINTER(ctypes.c_int)]
     lib.cnn_conv_plan.restype = ip
     lib.cnn_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
@@ -596,6 +598,11 @@ def cnn_set_conv_buffers(nbuf: int):
     _check(lib.cnn_set_conv_buffers(int(nbuf)), "cnn_set_conv_buffers")
 
 
+def cnn_set_conv_upsplit(on: int):
+    """Up layers of the TMA conv kernel: 1 a tile per output row parity, 0 default."""
+    _check(lib.cnn_set_conv_upsplit(int(on)), "cnn_set_conv_upsplit")
+
+
 def cnn_set_conv_tiling(max_rows: int):
     """Tile-height limit of the TMA conv kernel (0 = automatic)."""
     _check(lib.cnn_set_conv_tiling(int(max_rows)), "cnn_set_conv_tiling")
@@ -609,7 +616,8 @@ def cnn_conv_plan(mode: int, c0: int, c1: int, npad: int, hin: int, win: int, nb
                   ring_kb: int = 0, rows_cap: int = 0, narrow: int = 0):
     """Host-side tile plan of the TMA convolution (dict of CONV_PLAN_FIELDS), or None when
     the kernel does not take the layer.  narrow: 0 plain, 1 (or True) the column-taps-in-N
-    variant, 2 the row-taps-in-N variant, 3 the single-accumulator-buffer tiling."""
+    variant, 2 the row-taps-in-N variant, 3 the single-accumulator-buffer tiling, 4 up layers
+    with a tile per output row parity, 5 both of the last two."""
     out = (ctypes.c_int * 19)()
     st = lib.cnn_conv_plan(mode, c0, c1, npad, hin, win, nb, stage_kb, ring_kb, rows_cap, int(narrow), out)
     if st != HELM_OK:

@@ -63,11 +63,13 @@ def test_merged_up_taps_read_the_nodes_of_the_nine_taps():
                         assert merged[2 * ey + ex] == (cy + 1) * pw + cx + 1
 
 
-def _check(g, mode, npad, hin, win, nb):
+def _check(g, mode, npad, hin, win, nb, split=False):
     H, W = (hin, win) if mode >= 2 else ((hin // 2, win // 2) if mode == 1 else (hin, win))
     used = g["mode"]
     halo = 1 if mode == 1 else 2
-    assert g["tiles"] == -(-W // g["tw"]) * -(-H // g["rows"]) * nb
+    split = split and mode == 2      # up layers: a tile per output row parity
+    assert g["nph"] == (1 if mode < 2 else (2 if split else 4))
+    assert g["tiles"] == -(-W // g["tw"]) * -(-H // g["rows"]) * nb * (2 if split else 1)
     # TMA boxes (8-byte elements along a row, rows): at most 256 per dimension
     if mode == 1:
         assert 2 * g["pw"] <= 256 and 2 * (g["rows"] + 1) <= 256 and g["pw"] == g["tw"] + 1
@@ -77,7 +79,8 @@ def _check(g, mode, npad, hin, win, nb):
     assert g["plane"] == (g["rows"] + halo) * g["pw"] * 16
     assert g["pstride"] >= 2 * g["plane"] and g["pstride"] % 128 == 0
     assert g["stage"] == g["nplanes"] * g["pstride"] + g["wbytes"] and g["stage"] % 128 == 0
-    assert g["wbytes"] == (16 if mode == 2 else 9) * 2 * npad * 16   # up: 4 parities x 4 merged taps
+    # up: 4 (split: 2) column/row parities x 4 merged taps
+    assert g["wbytes"] == ((8 if split else 16) if mode == 2 else 9) * 2 * npad * 16
     assert 2 <= g["ns"] <= 6 and g["ns"] * g["stage"] <= 200 * 1024
     assert g["tmem_cols"] <= 512 and g["tmem_cols"] >= 32 and g["tmem_cols"] & (g["tmem_cols"] - 1) == 0
     stage_end = g["stage"]
@@ -100,8 +103,8 @@ def _check(g, mode, npad, hin, win, nb):
         return
     nph = g["nph"]
     assert g["nbuf"] in (1, 2) and g["nbuf"] * nph * g["mb"] * npad <= g["tmem_cols"]
-    for ph in range(nph):
-        py, px = ph >> 1, ph & 1
+    for ph, py in itertools.product(range(nph), (0, 1) if split else (None,)):
+        py, px = (py, ph) if split else (ph >> 1, ph & 1)
         taps = _taps(mode, py, px, g["pw"])
         for m in range(g["mb"]):
             for pl, off in taps:
@@ -111,24 +114,25 @@ def _check(g, mode, npad, hin, win, nb):
             for r in range(128):
                 yy, xx = divmod(m * 128 + r, g["pw"])
                 if xx < g["tw"] and yy < g["rows"]:
-                    assert (ph, yy, xx) not in cover
-                    cover.add((ph, yy, xx))
-    assert len(cover) == nph * g["rows"] * g["tw"]
+                    assert (py, px, yy, xx) not in cover
+                    cover.add((py, px, yy, xx))
+    assert len(cover) == (4 if split else nph) * g["rows"] * g["tw"]
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_tile_plans_stay_in_bounds(n, mode):
     checked = 0
-    for (H, W), c0, npad, (skb, rkb, cap), single in itertools.product(SHAPES, (16, 64), (16, 32, 64, 128), BUDGETS,
-                                                                       (0, 1)):
+    for (H, W), c0, npad, (skb, rkb, cap), single, split in itertools.product(
+            SHAPES, (16, 64), (16, 32, 64, 128), BUDGETS, (0, 1), (0, 1) if mode == 2 else (0,)):
         if mode == 1:
             hin, win = 2 * H, 2 * W
         else:
             hin, win = H, W
-        g = n.cnn_conv_plan(mode, c0, 0, npad, hin, win, 2, skb, rkb, cap, narrow=3 if single else 0)
+        narrow = (5 if single else 4) if split else (3 if single else 0)
+        g = n.cnn_conv_plan(mode, c0, 0, npad, hin, win, 2, skb, rkb, cap, narrow=narrow)
         if g is None:
             continue                 # the launcher rejects it too (gather kernel): one shared decision
-        _check(g, mode, npad, hin, win, 2)
+        _check(g, mode, npad, hin, win, 2, split=bool(split))
         checked += 1
     assert checked > 100
 

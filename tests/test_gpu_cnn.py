@@ -51,13 +51,14 @@ MODES = {"same": 0, "down": 1, "up": 2}
     (64, 0, 0, 64, "same", 37, 40, 1, True, True),       # narrow rows packed into M blocks, ragged rows
     (32, 32, 1, 32, "down", 18, 22, 2, False, True),     # concat in the stride-2 gather path
 ])
-@pytest.mark.parametrize("path", [0, 1, 2, 3, "single"])
+@pytest.mark.parametrize("path", [0, 1, 2, 3, "single", "upsplit"])
 def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res, relu, path):
     """path 0: the TMA halo-tile kernel (up layers on phase-merged weights); path 1: the
     gather kernel; path 2: the TMA
     kernel with the column taps in N for 16-channel same-grid layers; path 3: the TMA
     kernel with the three tap rows in N for 16- and 32-channel same-grid layers; "single":
-    the TMA kernel with one accumulator buffer."""
+    the TMA kernel with one accumulator buffer; "upsplit": up layers with a tile per output
+    row parity."""
     g = np.random.default_rng(c0 * 7 + cout + MODES[mode])
     x0 = cnn.bf16_round(g.normal(size=(nb, hin, win, c0)))
     x1 = cnn.bf16_round(g.normal(size=((1 if bcast else nb), hin, win, c1))) if c1 else None
@@ -77,16 +78,18 @@ def test_conv_layer_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, res,
     t0, g0 = native.cnn_conv_launch_counts()
     n0 = native.cnn_conv_narrow_launches()
     n6 = native.cnn_conv_rowtaps_launches()
-    single = path == "single"
-    path = 0 if single else path
+    single, upsplit = path == "single", path == "upsplit"
+    path = 0 if single or upsplit else path
     native.cnn_set_conv_path(path)
     native.cnn_set_conv_buffers(1 if single else 0)
+    native.cnn_set_conv_upsplit(1 if upsplit else 0)
     try:
         native.cnn_conv3x3(f32(x0), c0, f32(x1), c1, bcast, nb, hin, win, f32(w), f32(b), cout, f32(r),
                            MODES[mode], 1 if relu else 0, y)
     finally:
         native.cnn_set_conv_path(0)
         native.cnn_set_conv_buffers(0)
+        native.cnn_set_conv_upsplit(0)
     t1, g1 = native.cnn_conv_launch_counts()
     used_tma = path != 1
     assert (t1 - t0, g1 - g0) == ((1, 0) if used_tma else (0, 1))

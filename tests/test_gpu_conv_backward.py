@@ -148,6 +148,8 @@ def test_weight_gradient_is_deterministic(native):
     (32, 0, 0, 32, "same", 200, 300, 16, 3),   # 32 channels, three column tiles of 100
     (16, 16, 0, 16, "same", 256, 256, 16, "single"),   # one accumulator buffer: per-tile phases
     (128, 0, 0, 64, "up", 64, 128, 16, "single"),
+    (64, 0, 0, 32, "up", 64, 200, 16, "upsplit"),    # a tile per output row parity, alternating
+    (32, 0, 0, 16, "up", 96, 160, 16, "upsplit"),
 ])
 def test_conv_forward_multi_tile_sampled_parity(native, c0, c1, bcast, cout, mode, hin, win, nb, path):
     """The persistent TMA convolution at sizes where every CTA loops over three or more
@@ -164,22 +166,26 @@ def test_conv_forward_multi_tile_sampled_parity(native, c0, c1, bcast, cout, mod
     ho, wo = cnn.out_shape(hin, win, mode)
     y = torch.zeros((nb, ho, wo, cout), dtype=torch.float32, device="cuda")
     n6 = native.cnn_conv_rowtaps_launches()
-    single = path == "single"
-    path = 0 if single else path
+    single, upsplit = path == "single", path == "upsplit"
+    path = 0 if single or upsplit else path
     native.cnn_set_conv_path(path)
     native.cnn_set_conv_buffers(1 if single else 0)
+    native.cnn_set_conv_upsplit(1 if upsplit else 0)
     try:
         native.cnn_conv3x3(torch.from_numpy(x0).cuda(), c0, None if x1 is None else torch.from_numpy(x1).cuda(),
                            c1, bcast, nb, hin, win, _f32(w), _f32(b), cout, None, MODES[mode], 1, y)
     finally:
         native.cnn_set_conv_path(0)
         native.cnn_set_conv_buffers(0)
+        native.cnn_set_conv_upsplit(0)
     launch = native.cnn_conv_last_launch()
     npad = 16 if cout <= 16 else 32 * -(-cout // 32)
     plan = native.cnn_conv_plan(MODES[mode], 16 * -(-c0 // 16), 16 * -(-c1 // 16) if c1 else 0, npad, hin, win, nb,
-                                narrow=2 if path == 3 else (3 if single else 0))
+                                narrow=2 if path == 3 else (3 if single else (4 if upsplit else 0)))
     assert plan["nbuf"] == (1 if single else (2 if path != 3 else plan["nbuf"]))
     assert plan["mode"] == (6 if path == 3 else MODES[mode])
+    if upsplit:
+        assert plan["nph"] == 2
     assert native.cnn_conv_rowtaps_launches() - n6 == (1 if path == 3 else 0)
     assert plan["tiles"] >= 3 * launch[0], (plan["tiles"], launch)
     y = y.cpu().numpy()
