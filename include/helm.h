@@ -467,8 +467,10 @@ int cnn_set_conv_path(int path);
  * context's medium.  The first launch of every layer shape times its candidate
  * tilings and records the fastest: the default stage and ring budgets,
  * 36/110, 56/112, 100/200 and 47/200 KB, at most 4 rows per tile, one
- * accumulator buffer of up to 512 TMEM columns (more M blocks per tile), and for
- * 16-channel same-grid layers the column-taps-in-N variant.  Later launches of
+ * accumulator buffer of up to 512 TMEM columns (more M blocks per tile), for
+ * 16-channel same-grid layers the column-taps-in-N variant, and for up layers a tile
+ * per output row parity (default budgets, 100/200 KB, one buffer, one buffer with a
+ * 200 KB ring).  Later launches of
  * that shape, at any batch size and in any context, use it.  The table is
  * process-wide; explicit cnn_set_conv_tiling / cnn_set_conv_ring values take
  * precedence.  Layers that accumulate into their output (the backward pass)

@@ -56,7 +56,8 @@ struct ConvArgs {
 int launch_conv3x3(const ConvArgs& a, cudaStream_t st);
 // layers through TMA-staged halo tiles (k_conv_tma.cu); HELM_EINVAL = not launched.
 // narrow: 0 plain; 1, 16-channel same-grid layers take the column-taps-in-N variant;
-// 2, 16- and 32-channel same-grid layers take the A operand from TMEM.
+// 2, 16- and 32-channel same-grid layers take the row-taps-in-N variant (three tap rows
+// of a staged row in one MMA's N).
 int launch_conv3x3_tma(const ConvArgs& a, cudaStream_t st, int narrow);
 // Autotuning of the TMA kernel's tiling: while on, the first launch of each layer
 // shape times the candidate tilings and records the fastest, which every later

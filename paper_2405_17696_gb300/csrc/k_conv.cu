@@ -322,7 +322,7 @@ int launch_conv3x3(const ConvArgs& a, cudaStream_t st) {
 extern "C" int cnn_set_conv_path(int path) {
     if (path < 0 || path > 3) {
         helm::set_error("cnn_set_conv_path: path must be 0 (automatic), 1 (gather kernel only), 2 (TMA "
-                        "kernel with the column-taps-in-N variant) or 3 (TMA kernel with the A operand in TMEM)");
+                        "kernel with the column-taps-in-N variant) or 3 (TMA kernel with the row-taps-in-N variant)");
         return HELM_EINVAL;
     }
     helm::g_conv_path.store(path);
