@@ -133,6 +133,20 @@ def run_windows(native, m, nx0, nz0, windows, cfg: FwiConfig, net=None, log=None
     return hist
 
 
+def regulariser_schedule(cfg: FwiConfig):
+    """(kinds, weights), one per frequency window, from cfg.reg_kind / cfg.reg_alpha (a value
+    for every window, or a list with one per window).  Kinds are 0 (none), 1 (R_diff) or 2
+    (R_high) of Sec. 5.1; weights are >= 0.  ValueError otherwise."""
+    nwin = len(cfg.windows)
+    per_window = lambda v: list(v) if isinstance(v, (list, tuple)) else [v] * nwin
+    kinds, alphas = per_window(cfg.reg_kind), per_window(cfg.reg_alpha)
+    if len(kinds) != nwin or len(alphas) != nwin:
+        raise ValueError("reg_kind / reg_alpha: one value, or one per window")
+    if any(int(k) != k or k not in (0, 1, 2) for k in kinds) or any(not (a >= 0) for a in alphas):
+        raise ValueError("reg_kind must be 0, 1 or 2 and reg_alpha >= 0")
+    return [int(k) for k in kinds], [float(a) for a in alphas]
+
+
 def run(native, m, gamma, nx, nz, hx, hz, src_idx, rcv_idx, d_obs, freqs_hz, cfg: FwiConfig, net=None,
         log=None, window_offset: int = 0, m_ref=None) -> FwiHistory:
     """Alg. 1 on the model m (float32 CUDA tensor [nz][nx] of m = 1 / v^2, updated in
@@ -140,16 +154,12 @@ def run(native, m, gamma, nx, nz, hx, hz, src_idx, rcv_idx, d_obs, freqs_hz, cfg
     the windows' frequencies are drawn from.  net: the encoder-solver network (CNN-FGMRES
     with retraining when cfg.retrain_steps > 0), or None for MG-FGMRES.  m_ref: the
     regulariser's reference model on this grid (default: m as the run starts)."""
+    kinds, alphas = regulariser_schedule(cfg)
     import torch
     hist = FwiHistory()
     rng = media.rng(cfg.seed)
     gam = torch.as_tensor(gamma, dtype=torch.float32, device="cuda").contiguous()
     fidx = {f: i for i, f in enumerate(freqs_hz)}
-    nwin = len(cfg.windows)
-    per_window = lambda v: list(v) if isinstance(v, (list, tuple)) else [v] * nwin
-    kinds, alphas = per_window(cfg.reg_kind), per_window(cfg.reg_alpha)
-    if len(kinds) != nwin or len(alphas) != nwin:
-        raise ValueError("reg_kind / reg_alpha: one value, or one per window")
     if not any(k and a > 0 for k, a in zip(kinds, alphas)):
         m_ref = None
     elif m_ref is None:
