@@ -244,3 +244,32 @@ def test_pointwise_and_tap_by_tap_forms_match_the_layer(mode):
     assert np.allclose(dxp, np.array([dx[p] for p in pts_in]), rtol=0, atol=1e-12)
     dw2, db2 = cnn.conv_weight_grad(x, gy, mode)
     assert np.allclose(dw2, dw, rtol=0, atol=1e-12) and np.allclose(db2, db, rtol=0, atol=1e-12)
+
+
+def test_up_layer_is_four_phase_convolutions_on_the_coarse_grid():
+    """The identity the tensor-core up layer is built on: nearest x2 upsampling followed by
+    a 3x3 convolution (zero padding on the fine grid) equals, for each output parity
+    (py, px), a 2x2 convolution on the coarse grid (zero padding there) whose weights are
+    the sums of the 3x3 taps that read the same coarse node, fine node 2Y + p with tap d
+    reading coarse node floor((2Y + p + d) / 2).  Exact up to FP64 rounding."""
+    g = _rng(29)
+    B, ny, nx, cin, cout = 2, 5, 7, 3, 4
+    x = g.normal(size=(B, ny, nx, cin))
+    w = g.normal(size=(cout, 9, cin))
+    ref = cnn.conv_forward(x, w, np.zeros(cout), "up")
+    xp = np.zeros((B, ny + 2, nx + 2, cin))
+    xp[:, 1:-1, 1:-1] = x
+    y = np.zeros((B, 2 * ny, 2 * nx, cout))
+    for py in (0, 1):
+        for px in (0, 1):
+            wm = np.zeros((2, 2, cout, cin))
+            for t in range(9):
+                dy, dx = t // 3 - 1, t % 3 - 1
+                ey, ex = (py + dy) // 2 - py + 1, (px + dx) // 2 - px + 1
+                wm[ey, ex] += w[:, t, :]
+            for ey in (0, 1):
+                for ex in (0, 1):
+                    # coarse node (Y + py - 1 + ey, X + px - 1 + ex), + 1 for the padding
+                    blk = xp[:, py + ey:py + ey + ny, px + ex:px + ex + nx]
+                    y[:, py::2, px::2] += np.einsum("byxc,oc->byxo", blk, wm[ey, ex])
+    assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref))
